@@ -1,0 +1,183 @@
+"""Pins for the oracle: it is checked against brute force, invariants and
+closed forms -- never against itself -- and each pin is shown to catch a
+planted mistake."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests import pins
+
+M64 = (1 << 64) - 1
+
+
+def _tiny(n, space, seed, stream=1):
+    return gen.tiny_kpa(n, space, seed, stream=stream)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 17, 64])
+@pytest.mark.parametrize("space", [1, 4, 0])  # 0: full 64-bit range
+def test_sort_matches_brute_force(n, space):
+    k, _ = _tiny(n, space, 7 + n)
+    p = np.arange(n, dtype=np.uint32)[::-1].copy()  # non-ascending ptrs too
+    ok, op = oracle.sort(k, p)
+    bk, bp = pins.brute_sort(k, p)
+    assert np.array_equal(ok, bk) and np.array_equal(op, bp)
+
+
+def test_sort_extreme_keys():
+    k = np.array([M64, 0, M64, 1, 0, 1 << 63], dtype=np.uint64)
+    p = np.arange(6, dtype=np.uint32)
+    ok, op = oracle.sort(k, p)
+    assert ok.tolist() == [0, 0, 1, 1 << 63, M64, M64]
+    assert op.tolist() == [1, 4, 3, 5, 0, 2]
+
+
+def test_extract_and_sort_invariants_mixed_keys():
+    col = gen.mixed_keys(200_003)
+    keys, ptrs = oracle.extract(col, 1001, 150_000)
+    assert np.array_equal(keys, col[1001:151001])
+    assert np.array_equal(ptrs, np.arange(1001, 151001, dtype=np.uint32))
+    sk, sp = oracle.sort(keys, ptrs)
+    pins.check_sorted_kpa(col[1001:151001], 1001, sk, sp)
+    # numpy's stable sort of the keys alone gives the same order (ptrs ascend)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(sk, keys[order]) and np.array_equal(sp, ptrs[order])
+
+
+def test_merge_is_sorted_concatenation():
+    col = gen.mixed_keys(50_000, seed=99)
+    runs = []
+    bounds = [0, 1, 7000, 7001, 30000, 50000]
+    for a, b in zip(bounds, bounds[1:]):
+        runs.append(oracle.sort(*oracle.extract(col, a, b - a)))
+    mk, mp = oracle.merge(runs)
+    pins.check_sorted_kpa(col, 0, mk, mp)
+    tk, tp = _tiny(40, 3, 5)
+    r1 = oracle.sort(tk[:25], np.arange(25, dtype=np.uint32))
+    r2 = oracle.sort(tk[25:], np.arange(25, 40, dtype=np.uint32))
+    mk, mp = oracle.merge([r1, r2])
+    bk, bp = pins.brute_sort(tk, np.arange(40, dtype=np.uint32))
+    assert np.array_equal(mk, bk) and np.array_equal(mp, bp)
+
+
+@pytest.mark.parametrize("vb", [4, 8])
+@pytest.mark.parametrize("n,space", [(0, 4), (1, 4), (64, 4), (200, 1), (300, 50)])
+def test_group_matches_brute_force(vb, n, space):
+    k, _ = _tiny(n, space, 11 + n)
+    v = gen.uniform(3, 4, n, 0, 0, np.uint64 if vb == 8 else np.uint32)  # full range: sums wrap
+    p = np.arange(n, dtype=np.uint32)
+    got = oracle.group_sum_count(k, p, v)
+    exp = pins.brute_group(k, p, v)
+    for a, b in zip(got, exp):
+        assert np.array_equal(a, b)
+
+
+def test_group_count_only_and_invariants_tumbling_window():
+    w = gen.tumbling_window(1_000_000)
+    keys, ptrs = oracle.sort(*oracle.extract(w["keys"], 0, 1_000_000))
+    ok, oc, osum = oracle.group_sum_count(keys, ptrs, w["vals"])
+    pins.check_group(keys, w["vals"], ptrs, ok, oc, osum)
+    # distinct-key count of n uniform draws over 2^20 ids: mean 2^20 (1 - (1 - 2^-20)^n)
+    N = float(1 << 20)
+    mean = N * (1.0 - (1.0 - 1.0 / N) ** 1e6)
+    var = N * (1 - 1 / N) ** 1e6 + N * N * (1 - 2 / N) ** 1e6 - N * N * (1 - 1 / N) ** 2e6
+    assert abs(ok.size - mean) < 6.0 * np.sqrt(var)
+    _, oc2, os2 = oracle.group_sum_count(keys, ptrs, None)
+    assert np.array_equal(oc2, oc) and not os2.any()
+
+
+@pytest.mark.parametrize("K", [1, 3, 5])
+@pytest.mark.parametrize("n,space,vspan", [(0, 4, 8), (1, 4, 8), (64, 4, 4), (100, 7, 3), (150, 1, 1000)])
+def test_topk_matches_brute_force(K, n, space, vspan):
+    k, _ = _tiny(n, space, 21 + n)
+    v = gen.uniform(9, 9, n, 0, vspan, np.uint64)  # small value span: many value ties
+    p = np.arange(n, dtype=np.uint32)
+    got = oracle.topk(k, p, v, K)
+    exp = pins.brute_topk(k, p, v, K)
+    for a, b in zip(got, exp):
+        assert np.array_equal(a, b)
+    pins.check_topk(k, p, v, K, *got)
+
+
+@pytest.mark.parametrize("nl,nr,space", [(0, 5, 3), (5, 0, 3), (30, 40, 4), (50, 50, 1000), (64, 64, 1)])
+def test_join_matches_nested_loop(nl, nr, space):
+    lk, _ = _tiny(nl, space, 31 + nl)
+    rk, _ = _tiny(nr, space, 41 + nr, stream=2)
+    lp = np.arange(nl, dtype=np.uint32)
+    rp = np.arange(nr, dtype=np.uint32)
+    a = oracle.join(lk, lp, rk, rp)
+    b = oracle.join_nested(lk, lp, rk, rp)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    pins.check_join(lk, rk, a[0], a[1], pins.join_cardinality(lk, rk))
+
+
+def test_join_cardinality_medium():
+    s = gen.join_streams(20_000, key_space=1 << 12)
+    lk, rk = s["L"]["keys"], s["R"]["keys"]
+    ol, orr = oracle.join(lk, np.arange(lk.size, dtype=np.uint32), rk, np.arange(rk.size, dtype=np.uint32))
+    pins.check_join(lk, rk, ol, orr, pins.join_cardinality(lk, rk))
+
+
+def test_window_ranges_binary_search():
+    ts = np.sort(gen.uniform(5, 5, 5000, 0, 20000, np.uint64))
+    starts = np.array([0, 1, 250, 9999, 19999, 20000, 30000], dtype=np.uint64)
+    b, e = oracle.window_ranges(ts, starts, 1000)
+    assert np.array_equal(b, np.searchsorted(ts, starts, side="left"))
+    assert np.array_equal(e, np.searchsorted(ts, starts + 1000, side="left"))
+    ts32 = np.arange(100, dtype=np.uint32)
+    b, e = oracle.window_ranges(ts32, np.array([10, 95], np.uint64), 25)
+    assert b.tolist() == [10, 95] and e.tolist() == [35, 100]
+
+
+# ------------------------------------------------------------- planted mistakes
+def test_pins_catch_planted_sort_mistakes():
+    col = gen.mixed_keys(5000, seed=3)
+    sk, sp = oracle.sort(*oracle.extract(col, 0, 5000))
+    pins.check_sorted_kpa(col, 0, sk, sp)
+    mutants = []
+    a, b = sk.copy(), sp.copy(); a[[10, 11]] = a[[11, 10]]; b[[10, 11]] = b[[11, 10]]; mutants.append((a, b))  # swap
+    a, b = sk.copy(), sp.copy(); b[5] = b[6]; mutants.append((a, b))  # duplicate ptr
+    a, b = sk[:-1].copy(), sp[:-1].copy(); mutants.append((a, b))  # dropped element
+    a, b = sk.copy(), sp.copy(); a[100] += np.uint64(1); mutants.append((a, b))  # wrong key
+    dup = np.flatnonzero(sk[1:] == sk[:-1])[0]
+    a, b = sk.copy(), sp.copy(); b[[dup, dup + 1]] = b[[dup + 1, dup]]; mutants.append((a, b))  # tie order
+    for a, b in mutants:
+        with pytest.raises(AssertionError):
+            pins.check_sorted_kpa(col, 0, a, b)
+
+
+def test_pins_catch_planted_group_mistakes():
+    w = gen.tumbling_window(20_000, key_bits=10)
+    keys, ptrs = oracle.sort(*oracle.extract(w["keys"], 0, 20_000))
+    ok, oc, osum = oracle.group_sum_count(keys, ptrs, w["vals"])
+    bad = [
+        (ok, oc, osum + np.uint64(1) * (np.arange(ok.size) == 3)),   # a sum off by one
+        (ok, oc - np.uint64(1) * (np.arange(ok.size) == 0), osum),   # a dropped record
+        (ok[::-1], oc[::-1], osum[::-1]),                            # wrong order
+    ]
+    for k2, c2, s2 in bad:
+        with pytest.raises(AssertionError):
+            pins.check_group(keys, w["vals"], ptrs, k2, c2, s2)
+
+
+def test_pins_catch_planted_topk_and_join_mistakes():
+    k, _ = _tiny(300, 20, 77)
+    v = gen.uniform(2, 2, 300, 0, 50, np.uint64)
+    p = np.arange(300, dtype=np.uint32)
+    ok, nv, ov, op = oracle.topk(k, p, v, 3)
+    ov2 = ov.copy(); ov2[0, [0, 1]] = ov2[0, [1, 0]]
+    with pytest.raises(AssertionError):
+        pins.check_topk(k, p, v, 3, ok, nv, ov2, op)
+    nv2 = nv.copy(); nv2[1] -= 1
+    with pytest.raises(AssertionError):
+        pins.check_topk(k, p, v, 3, ok, nv2, ov, op)
+    lk, _ = _tiny(80, 6, 1)
+    rk, _ = _tiny(80, 6, 2, stream=3)
+    ol, orr = oracle.join(lk, p[:80], rk, p[:80])
+    card = pins.join_cardinality(lk, rk)
+    with pytest.raises(AssertionError):
+        pins.check_join(lk, rk, ol[:-1], orr[:-1], card)
+    o2 = orr.copy(); o2[0] = (o2[0] + 1) % 80
+    with pytest.raises(AssertionError):
+        pins.check_join(lk, rk, ol, o2, card)

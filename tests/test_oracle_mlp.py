@@ -1,0 +1,87 @@
+"""Pins for the FP64 statement of the learned partitioner's network."""
+import numpy as np
+import pytest
+
+import gen
+from oracle import mlp
+
+
+def _rand_params(seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, 0.5, mlp.N_PARAMS)
+
+
+def test_backward_matches_central_differences():
+    p = _rand_params(1)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 1, 16)
+    t = rng.uniform(0, 1, 16)
+    g = mlp.backward(p, x, t)
+    h = 1e-6
+    num = np.empty_like(g)
+    for i in range(p.size):
+        e = np.zeros_like(p)
+        e[i] = h
+        num[i] = (mlp.loss(p + e, x, t) - mlp.loss(p - e, x, t)) / (2 * h)
+    assert np.max(np.abs(num - g)) <= 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+def test_forward_closed_form_spline():
+    # W1 = 1, b1_j = -j/32: h1_j = relu(x - j/32); W2 = I, b2 = 0; y = sum_j w3_j relu(x - j/32) + b3,
+    # a linear spline with knots at j/32.
+    H = mlp.H
+    p = np.zeros(mlp.N_PARAMS)
+    p[mlp.SLICES["W1"]] = 1.0
+    p[mlp.SLICES["b1"]] = -np.arange(H) / H
+    p[mlp.SLICES["W2"]] = np.eye(H).reshape(-1)
+    w3 = np.linspace(-1, 1, H)
+    p[mlp.SLICES["w3"]] = w3
+    p[mlp.SLICES["b3"]] = 0.25
+    for x in (0.0, 0.03, 0.5, 0.99):
+        exp = 0.25 + sum(w3[j] * (x - j / H) for j in range(H) if x > j / H)
+        y, _ = mlp.forward(p, np.array([x]))
+        assert abs(y[0] - exp) < 1e-12
+
+
+def test_adam_first_step_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 0.0])
+    p1, m, v = mlp.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    # step 1: mhat = g, vhat = g^2, so each parameter moves by lr * g / (|g| + eps)
+    assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_feature_bit_definition():
+    M64 = (1 << 64) - 1
+    keys = np.array([0, 1, 2, 3, 6, (1 << 17) + 1, 1 << 63, M64], dtype=np.uint64)
+    x = mlp.feature(keys)
+    exp = [0.0, 0.0, 1 / 64, 1.5 / 64, (2 + 0.5) / 64, (17 + 1 / 131072) / 64, 63 / 64,
+           (63 + (131071 / 131072)) / 64]
+    assert np.allclose(x, exp, rtol=0, atol=0)
+    # exact in float32 and non-decreasing in the key
+    ks = np.sort(gen.mixed_keys(20_000, seed=4))
+    xs = mlp.feature(ks)
+    assert np.all(np.diff(xs) >= 0)
+    assert np.array_equal(xs.astype(np.float32).astype(np.float64), xs)
+
+
+def test_cdf_targets():
+    s = np.array([5, 1, 9, 3], dtype=np.uint64)
+    # distinct keys: rank r (from 0) -> (2r + 1) / 2m
+    assert np.allclose(mlp.cdf_targets(s), [5 / 8, 1 / 8, 7 / 8, 3 / 8])
+    assert np.allclose(mlp.cdf_targets(np.full(7, 3, np.uint64)), 0.5)
+    s = np.array([2, 2, 1, 4], dtype=np.uint64)
+    assert np.allclose(mlp.cdf_targets(s), [(1 + 3) / 8, (1 + 3) / 8, (0 + 1) / 8, (3 + 4) / 8])
+
+
+def test_training_learns_uniform_cdf():
+    # keys whose feature is uniform on [0, 1): the CDF of the feature is the identity
+    u = gen.unif01(8, 1, 4096)
+    x = np.floor(u * 64 * 131072) / (64 * 131072)
+    t = np.argsort(np.argsort(x, kind="stable"), kind="stable").astype(np.float64) / x.size + 0.5 / x.size
+    p0 = gen.mlp_init().astype(np.float64)
+    p, losses = mlp.train(p0, x, t, steps=400, batch=512, lr=1e-2)
+    assert losses[-1] < 0.1 * losses[0]
+    y, _ = mlp.forward(p, np.linspace(0.05, 0.95, 19))
+    assert np.max(np.abs(y - np.linspace(0.05, 0.95, 19))) < 0.05
