@@ -1,0 +1,182 @@
+/*
+ * sbh.h -- C ABI of the KPA grouping path (StreamBox-HBM, Miao et al.,
+ * ASPLOS '19), built for NVIDIA B300 (sm_103a).
+ *
+ * A Key Pointer Array (KPA, Sec. 4.1) is held as two device arrays of equal
+ * length n: keys (uint64, the resident key) and ptrs (uint32, the row index
+ * of the full record in its columnar stream).  The canonical order of a
+ * sorted KPA is (key ascending, ptr ascending).
+ *
+ * Common rules for every call below:
+ *  - Pointers named d_* are device pointers (cudaMalloc / PyTorch CUDA
+ *    memory) owned by the caller.  The library never frees or keeps them.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream).  A call returns once its kernels are queued.
+ *  - Calls that need working memory take (d_scratch, scratch_bytes).  With
+ *    d_scratch == NULL the call only stores the required size in
+ *    *scratch_bytes and returns SBH_OK without touching the GPU.  Otherwise
+ *    *scratch_bytes must be at least that size.  Scratch must be 256-byte
+ *    aligned, must not overlap inputs or outputs, and may be reused once the
+ *    call's work on `stream` has finished.  Two calls that run at the same
+ *    time need two scratch buffers.
+ *  - Inputs are never written.
+ *  - Counts that depend on the data (distinct keys, join pairs) are written
+ *    to a caller-supplied device uint64; outputs beyond the caller's
+ *    capacity are not written, but the full count is still stored, so the
+ *    caller can compare it with the capacity after synchronising.
+ *  - Return values: SBH_OK, or a host-side error detected before any launch
+ *    (SBH_EINVAL: bad argument; SBH_ENOSPACE: scratch too small; SBH_ECUDA:
+ *    a CUDA runtime error, text in sbh_last_error()).  Nothing aborts,
+ *    throws or traps.
+ *  - Device-side waits (decoupled look-back between tiles) are bounded.  A
+ *    wait that runs out records SBH_ETIMEOUT in a per-device status word
+ *    that sbh_sync_status() reads; the call's output is then invalid.
+ */
+#ifndef SBH_H
+#define SBH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBH_OK 0
+#define SBH_EINVAL 1
+#define SBH_ENOSPACE 2
+#define SBH_ETIMEOUT 3
+#define SBH_ECUDA 4
+
+/* Unused top-K slots hold this value and pointer. */
+#define SBH_TOPK_PAD_VAL 0ull
+#define SBH_TOPK_PAD_PTR 0xFFFFFFFFu
+#define SBH_TOPK_MAX_K 8
+
+/* Library version string. */
+const char* sbh_version(void);
+
+/* Text of the last host-side error on the calling thread ("" if none). */
+const char* sbh_last_error(void);
+
+/* Wait for `stream`, then return SBH_OK, or SBH_ETIMEOUT if any kernel of
+ * this library on the current device recorded an expired device-side wait
+ * since the last call (the record is cleared), or SBH_ECUDA on a CUDA error. */
+int sbh_sync_status(void* stream);
+
+/* Test hooks.  sbh_set_spin_limit sets the number of polls a device-side
+ * wait makes before it gives up (0 restores the default).
+ * sbh_set_fault(SBH_FAULT_SKIP_PUBLISH) makes every pass of the next
+ * sbh_kpa_sort call leave tile 0's look-back record unpublished, so that the
+ * waits of later tiles run out (n must exceed one tile of 4096 keys); it is
+ * cleared by that call.  Neither hook faults or hangs the device. */
+#define SBH_FAULT_NONE 0
+#define SBH_FAULT_SKIP_PUBLISH 1
+void sbh_set_spin_limit(uint32_t polls);
+void sbh_set_fault(int fault);
+
+/* Per-launch timing.  sbh_profile_enable(1) clears earlier records and
+ * makes every later call record a CUDA event pair around each of its kernel
+ * launches, on the launch's stream; sbh_profile_enable(0) stops recording
+ * (and also clears).  sbh_profile_collect waits for the recorded events and
+ * copies, for the first max_records launches in launch order, the kernel name
+ * (names + i * name_len, NUL-terminated, truncated to name_len - 1 bytes) and
+ * its duration in milliseconds (ms[i]); either buffer may be NULL.  It
+ * returns the number of records. */
+void sbh_profile_enable(int on);
+int sbh_profile_collect(int max_records, char* names, int name_len, double* ms);
+
+/* ---------------------------------------------------------------- A1
+ * Window ranges (Sec. 4.2 "Windowing": Partition on the timestamp column).
+ * Window w holds the rows whose timestamp lies in [d_starts[w], d_starts[w]
+ * + len).  d_ts (n values of ts_bytes = 4 or 8 bytes) must be
+ * non-decreasing and d_starts[w] + len below 2^64; each window is the row
+ * range [d_row_begin[w],
+ * d_row_end[w]), found by binary search.  No scratch. */
+int sbh_window_ranges(const void* d_ts, int ts_bytes, uint64_t n, const uint64_t* d_starts, uint64_t len,
+                      uint64_t nwin, uint64_t* d_row_begin, uint64_t* d_row_end, void* stream);
+
+/* ---------------------------------------------------------------- A2
+ * Extract (Table 2; Sec. 4.2 "Maintenance primitives": copy the key column
+ * and initialise the record pointers).  For i < n:
+ *     d_keys[i] = key_col[row_begin + i],  d_ptrs[i] = row_begin + i.
+ * key_col may be device memory or page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister); in the latter case the kernel reads it over the host
+ * link.  row_begin + n must be < 2^32.
+ * Optional by-products (pass NULL to skip):
+ *   d_key_or   one uint64: bitwise OR of the n keys (significant bits).
+ *   d_samples  ceil(n / sample_stride) keys: d_samples[j] = d_keys[j*stride].
+ * No scratch. */
+int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs,
+                    uint64_t* d_key_or, uint64_t* d_samples, uint64_t sample_stride, void* stream);
+
+/* ---------------------------------------------------------------- A3
+ * Sort (Table 2: order a KPA by its resident key).  Stable LSD radix sort,
+ * 8-bit digits, one pass per digit position whose digit is not the same for
+ * all keys (the histogram of every position is built in one read).  Each
+ * pass is one onesweep kernel: tile load, warp multisplit ranking, decoupled
+ * look-back for the tile's global digit offsets, scatter staged through
+ * shared memory.  Because the sort is stable and ties keep their input
+ * order, the output is in (key, ptr) order when the input ptrs ascend (as
+ * Extract makes them); in general ties keep input order.
+ * In/out: (d_keys_in, d_ptrs_in) -> (d_keys_out, d_ptrs_out), n pairs,
+ * n < 2^32.  The output may alias the input (in-place sort).
+ * Scratch: about 12 n + (n / 6144) * 2 KiB bytes. */
+int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out, uint32_t* d_ptrs_out,
+                 uint64_t n, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------- A5
+ * Merge (Table 2: merge sorted KPAs; Sec. 4.2 "Keyed Aggregation" merges the
+ * sorted KPAs of a window when it closes).  nruns sorted runs, each in (key,
+ * ptr) order, are merged into one run in (key, ptr) order by rounds of
+ * pairwise merge-path merges.  Host arrays d_run_keys[r], d_run_ptrs[r]
+ * hold device pointers; run_lens[r] is a host array.  Total length < 2^32.
+ * Scratch: about 12 * total bytes when nruns > 2. */
+int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const uint32_t* const* d_run_ptrs,
+                  const uint64_t* run_lens, uint64_t* d_keys_out, uint32_t* d_ptrs_out, void* d_scratch,
+                  size_t* scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------- A6
+ * Keyed reduction (Table 2; Sec. 4.2 "Reduction primitives": scan a sorted
+ * KPA, find each contiguous key range, and coalesce a nonresident column
+ * reached through the pointers).  For each distinct key, in key order:
+ *   d_out_keys[j]   the key,
+ *   d_out_counts[j] its number of records,
+ *   d_out_sums[j]   the sum of d_val_col[ptr] over its records, modulo 2^64
+ *                   (d_val_col has val_bytes = 4 or 8 bytes per row).
+ * d_val_col == NULL (or d_out_sums == NULL) computes counts only and reads
+ * no values.  *d_nkeys receives the number of distinct keys; only the first
+ * cap entries are written.  The input must be sorted by key.
+ * Scratch: about 64 * (n / 4096) bytes. */
+int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
+                     int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
+                     uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------- A7
+ * Top-K per key (Sec. 7, benchmark 1 "TopK Per Key": the K largest values of
+ * each key).  For each distinct key j, in key order, the min(K, count)
+ * records with the largest d_val_col[ptr], ordered by (value descending, ptr
+ * ascending): d_out_vals[j*K + s], d_out_ptrs[j*K + s] for s < K, unused
+ * slots padded with SBH_TOPK_PAD_VAL / SBH_TOPK_PAD_PTR; d_out_nvalid[j] =
+ * min(K, count).  1 <= K <= SBH_TOPK_MAX_K.  Input sorted by key; cap and
+ * *d_nkeys as in sbh_group_reduce.
+ * Scratch: about 128 * (n / 4096) bytes. */
+int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col, int val_bytes,
+             int K, uint64_t* d_out_keys, uint8_t* d_out_nvalid, uint64_t* d_out_vals, uint32_t* d_out_ptrs,
+             uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------- A8
+ * Join (Table 2: join two sorted KPAs by resident key; Sec. 4.2 "Temporal
+ * Join" joins the KPAs of one window of each stream).  Emits every pair
+ * (ptrL, ptrR) with keyL == keyR, in (key, ptrL, ptrR) order, into
+ * d_out_l[p], d_out_r[p].  Both inputs sorted in (key, ptr) order.
+ * *d_npairs receives the number of pairs; only the first cap are written.
+ * Scratch: about 16 * nl bytes. */
+int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, const uint64_t* d_rkeys,
+             const uint32_t* d_rptrs, uint64_t nr, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
+             uint64_t* d_npairs, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBH_H */

@@ -1,0 +1,163 @@
+// Shared host and device helpers of the KPA grouping library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstddef>
+
+#include "../../include/sbh.h"
+
+namespace sbh {
+
+// ------------------------------------------------------------------ host side
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Device pointer of this library's per-device status word (bit 0: a bounded
+// device wait expired).  Looked up once per device.
+uint32_t* status_word();
+// Current number of polls a device-side wait makes before giving up.
+uint32_t spin_limit();
+// Returns the pending fault hook and clears it.
+int take_fault();
+// Number of SMs of the current device.
+int num_sms();
+
+// Optional per-launch timing (sbh_profile_enable): a scope records a CUDA
+// event pair around the launches it encloses, on their stream.
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t stream;
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+};
+
+__host__ __device__ __forceinline__ uint64_t min_u64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Checks a CUDA call; records the error text and returns SBH_ECUDA on failure.
+#define SBH_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ::sbh::set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return SBH_ECUDA;                                                                \
+        }                                                                                    \
+    } while (0)
+
+// Runs a kernel launch inside a profiling scope named `name`.
+#define SBH_TIMED(name, stream, ...)             \
+    do {                                         \
+        ::sbh::ProfScope ps_((name), (stream));  \
+        __VA_ARGS__;                             \
+    } while (0)
+
+// Checks the last launch.
+#define SBH_LAUNCHED() SBH_CUDA(cudaGetLastError())
+
+// Carves 256-byte aligned pieces out of one scratch buffer.  With base ==
+// nullptr it only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+// Common scratch-protocol check.  Returns SBH_OK and sets *done when the call
+// was only a size query.
+inline int scratch_check(void* scratch, size_t* scratch_bytes, size_t need, bool* done) {
+    *done = false;
+    if (!scratch_bytes) {
+        set_error("scratch_bytes is NULL");
+        return SBH_EINVAL;
+    }
+    if (!scratch) {
+        *scratch_bytes = need;
+        *done = true;
+        return SBH_OK;
+    }
+    if (*scratch_bytes < need) {
+        set_error("scratch too small: %zu < %zu bytes", *scratch_bytes, need);
+        return SBH_ENOSPACE;
+    }
+    if (reinterpret_cast<uintptr_t>(scratch) & 255) {
+        set_error("scratch is not 256-byte aligned");
+        return SBH_EINVAL;
+    }
+    return SBH_OK;
+}
+
+// ---------------------------------------------------------------- device side
+constexpr uint32_t kStatusTimeout = 1u;
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void record_timeout(uint32_t* status) {
+    if (status) atomicOr(status, kStatusTimeout);
+}
+
+// One poll of a bounded wait.  Returns true when the wait must give up: its
+// own budget is spent, or (checked every 256 polls) another wait of this
+// library already gave up, so that one stuck tile cannot make every later
+// tile wait out a full budget.
+__device__ __forceinline__ bool wait_expired(uint32_t& polls, uint32_t limit, uint32_t* status) {
+    ++polls;
+    if (polls > limit) {
+        record_timeout(status);
+        return true;
+    }
+    if ((polls & 255u) == 0 && status && (ld_relaxed(status) & kStatusTimeout)) return true;
+    __nanosleep(64);
+    return false;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Streaming (evict-first) loads and stores for data touched once.
+__device__ __forceinline__ uint64_t ld_stream(const uint64_t* p) { return __ldcs(reinterpret_cast<const unsigned long long*>(p)); }
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(reinterpret_cast<const unsigned int*>(p)); }
+__device__ __forceinline__ void st_stream(uint64_t* p, uint64_t v) { __stcs(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v); }
+__device__ __forceinline__ void st_stream(uint32_t* p, uint32_t v) { __stcs(reinterpret_cast<unsigned int*>(p), v); }
+
+}  // namespace sbh

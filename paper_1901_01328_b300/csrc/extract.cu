@@ -1,0 +1,163 @@
+// A1 window ranges and A2 Extract.
+#include "common.cuh"
+
+namespace sbh {
+namespace {
+
+// ---------------------------------------------------------------- Extract
+// keys[i] = src[i]; ptrs[i] = row_begin + i.  Four rows per thread step with
+// 16-byte loads and stores when src, keys and ptrs are 16-byte aligned.
+template <bool kVec>
+__global__ void __launch_bounds__(256) extract_kernel(const uint64_t* __restrict__ src, uint32_t row_begin,
+                                                       uint32_t n, uint64_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ ptrs, uint64_t* __restrict__ key_or,
+                                                       uint64_t* __restrict__ samples, uint32_t stride) {
+    uint64_t acc = 0;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kVec) {
+        const uint32_t nq = n / 4;
+        for (uint32_t q = tid; q < nq; q += nthreads) {
+            const uint32_t i = q * 4;
+            ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(src + i));
+            ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(src + i + 2));
+            __stcs(reinterpret_cast<ulonglong2*>(keys + i), a);
+            __stcs(reinterpret_cast<ulonglong2*>(keys + i + 2), b);
+            uint4 p = make_uint4(row_begin + i, row_begin + i + 1, row_begin + i + 2, row_begin + i + 3);
+            __stcs(reinterpret_cast<uint4*>(ptrs + i), p);
+            acc |= a.x | a.y | b.x | b.y;
+            if (samples) {
+                uint32_t first = ((i + stride - 1) / stride) * stride;  // first sampled row >= i
+                if (first < i + 4) {
+                    uint64_t v[4] = {a.x, a.y, b.x, b.y};
+                    for (uint32_t r = first; r < i + 4; r += stride) samples[r / stride] = v[r - i];
+                }
+            }
+        }
+        for (uint32_t i = nq * 4 + tid; i < n; i += nthreads) {
+            uint64_t k = src[i];
+            keys[i] = k;
+            ptrs[i] = row_begin + i;
+            acc |= k;
+            if (samples && i % stride == 0) samples[i / stride] = k;
+        }
+    } else {
+        for (uint32_t i = tid; i < n; i += nthreads) {
+            uint64_t k = src[i];
+            keys[i] = k;
+            ptrs[i] = row_begin + i;
+            acc |= k;
+            if (samples && i % stride == 0) samples[i / stride] = k;
+        }
+    }
+    if (key_or) {
+        for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane_id() == 0 && acc) atomicOr(reinterpret_cast<unsigned long long*>(key_or), (unsigned long long)acc);
+    }
+}
+
+// ---------------------------------------------------------------- windows
+template <typename T>
+__device__ __forceinline__ uint64_t lower_bound_ts(const T* ts, uint64_t n, uint64_t v) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (static_cast<uint64_t>(ts[mid]) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void window_kernel(const T* __restrict__ ts, uint64_t n, const uint64_t* __restrict__ starts,
+                              uint64_t len, uint64_t nwin, uint64_t* __restrict__ rb, uint64_t* __restrict__ re) {
+    uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    const uint64_t s = starts[w];
+    rb[w] = lower_bound_ts(ts, n, s);
+    re[w] = lower_bound_ts(ts, n, s + len);  // the caller keeps s + len below 2^64
+}
+
+// Resolves a key column that may live in page-locked host memory.
+int device_view(const uint64_t* p, const uint64_t** out) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("key_col: cudaPointerGetAttributes failed: %s", cudaGetErrorString(e));
+        return SBH_EINVAL;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *out = p;
+        return SBH_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *out = static_cast<const uint64_t*>(a.devicePointer);
+        return SBH_OK;
+    }
+    set_error("key_col must be device memory or page-locked, mapped host memory");
+    return SBH_EINVAL;
+}
+
+}  // namespace
+}  // namespace sbh
+
+extern "C" {
+
+int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs,
+                    uint64_t* d_key_or, uint64_t* d_samples, uint64_t sample_stride, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n == 0) {
+        if (d_key_or) SBH_CUDA(cudaMemsetAsync(d_key_or, 0, sizeof(uint64_t), as_stream(stream)));
+        return SBH_OK;
+    }
+    if (!key_col || !d_keys || !d_ptrs) { set_error("null pointer"); return SBH_EINVAL; }
+    if (row_begin + n > 0xFFFFFFFFull || row_begin + n < row_begin) {
+        set_error("row_begin + n must be < 2^32 with 32-bit pointers");
+        return SBH_EINVAL;
+    }
+    if (d_samples && sample_stride == 0) { set_error("sample_stride must be > 0"); return SBH_EINVAL; }
+    const uint64_t* col = nullptr;
+    int rc = device_view(key_col, &col);
+    if (rc) return rc;
+    const uint64_t* src = col + row_begin;
+    cudaStream_t s = as_stream(stream);
+    if (d_key_or) SBH_CUDA(cudaMemsetAsync(d_key_or, 0, sizeof(uint64_t), s));
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(d_keys) |
+                       reinterpret_cast<uintptr_t>(d_ptrs)) & 15) == 0;
+    const uint64_t work = vec ? (n + 3) / 4 : n;
+    const uint64_t max_blocks = (uint64_t)num_sms() * 8;
+    uint64_t blocks = (work + 255) / 256;
+    if (blocks > max_blocks) blocks = max_blocks;
+    uint32_t stride = d_samples ? static_cast<uint32_t>(sample_stride > 0xFFFFFFFFull ? 0xFFFFFFFFull : sample_stride) : 1;
+    if (vec)
+        SBH_TIMED("extract", s, extract_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(src, (uint32_t)row_begin, (uint32_t)n, d_keys, d_ptrs,
+                                                             d_key_or, d_samples, stride));
+    else
+        SBH_TIMED("extract", s, extract_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(src, (uint32_t)row_begin, (uint32_t)n, d_keys, d_ptrs,
+                                                              d_key_or, d_samples, stride));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int sbh_window_ranges(const void* d_ts, int ts_bytes, uint64_t n, const uint64_t* d_starts, uint64_t len,
+                      uint64_t nwin, uint64_t* d_row_begin, uint64_t* d_row_end, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (nwin == 0) return SBH_OK;
+    if ((!d_ts && n) || !d_starts || !d_row_begin || !d_row_end) { set_error("null pointer"); return SBH_EINVAL; }
+    if (ts_bytes != 4 && ts_bytes != 8) { set_error("ts_bytes must be 4 or 8"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    unsigned blocks = (unsigned)((nwin + 255) / 256);
+    if (ts_bytes == 4)
+        SBH_TIMED("window_ranges", s, window_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t*>(d_ts), n, d_starts, len, nwin,
+                                                       d_row_begin, d_row_end));
+    else
+        SBH_TIMED("window_ranges", s, window_kernel<uint64_t><<<blocks, 256, 0, s>>>(static_cast<const uint64_t*>(d_ts), n, d_starts, len, nwin,
+                                                       d_row_begin, d_row_end));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+}  // extern "C"

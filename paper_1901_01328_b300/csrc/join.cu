@@ -1,0 +1,181 @@
+// A8 Join of two KPAs sorted in (key, ptr) order: every (ptrL, ptrR) with
+// equal keys, in (key, ptrL, ptrR) order.
+//
+//   count  each row i of L finds its key's row range [lo, hi) in R by binary
+//          search; per-block sums of the match counts hi - lo.
+//   scan   one block scans the block sums; the grand total is the pair count.
+//   emit   each block rescans its rows' counts from its block offset; row i
+//          writes (ptrL[i], ptrR[lo + j]) for j < hi - lo.  Rows of L come in
+//          (key, ptrL) order and each R range in ptrR order, so the pairs come
+//          out in (key, ptrL, ptrR) order.
+#include "common.cuh"
+
+namespace sbh {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kIpt = 8;
+constexpr int kTile = kThreads * kIpt;
+
+__device__ __forceinline__ uint32_t lower_bound_key(const uint64_t* a, uint32_t n, uint64_t v) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ uint32_t upper_bound_key(const uint64_t* a, uint32_t lo, uint32_t n, uint64_t v) {
+    uint32_t hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (a[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane_id() == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    uint64_t t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+join_count_kernel(const uint64_t* __restrict__ lk, uint32_t nl, const uint64_t* __restrict__ rk, uint32_t nr,
+                  uint32_t* __restrict__ rlo, uint32_t* __restrict__ cnt, uint64_t* __restrict__ bsum) {
+    __shared__ uint64_t red[kThreads / 32];
+    const uint32_t base = blockIdx.x * kTile;
+    uint64_t local = 0;
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        const uint32_t i = base + t * kThreads + threadIdx.x;
+        if (i < nl) {
+            const uint64_t k = lk[i];
+            const uint32_t lo = lower_bound_key(rk, nr, k);
+            const uint32_t hi = upper_bound_key(rk, lo, nr, k);
+            rlo[i] = lo;
+            cnt[i] = hi - lo;
+            local += hi - lo;
+        }
+    }
+    const uint64_t t = block_sum(local, red);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+// Exclusive scan of the block sums in place; *total receives the sum.
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(uint64_t* __restrict__ bsum, uint32_t nb,
+                                                           uint64_t* __restrict__ total) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const uint64_t v = i < nb ? bsum[i] : 0;
+        uint64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (uint32_t)o) x += y;
+        }
+        if (lane_id() == 31) warp_tot[threadIdx.x / 32] = x;
+        __syncthreads();
+        uint64_t before = carry;
+        for (uint32_t w = 0; w < threadIdx.x / 32; ++w) before += warp_tot[w];
+        if (i < nb) bsum[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kThreads)
+join_emit_kernel(const uint32_t* __restrict__ lp, uint32_t nl, const uint32_t* __restrict__ rp,
+                 const uint32_t* __restrict__ rlo, const uint32_t* __restrict__ cnt,
+                 const uint64_t* __restrict__ boff, uint32_t* __restrict__ out_l, uint32_t* __restrict__ out_r,
+                 uint64_t cap) {
+    __shared__ uint64_t warp_tot[kThreads / 32];
+    // thread-blocked rows: thread t owns rows base + t*kIpt .. + kIpt - 1
+    const uint32_t base = blockIdx.x * kTile;
+    const uint32_t first = base + threadIdx.x * kIpt;
+    uint32_t c[kIpt];
+    uint64_t mine = 0;
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        c[t] = (first + t < nl) ? cnt[first + t] : 0u;
+        mine += c[t];
+    }
+    uint64_t x = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane_id() >= (uint32_t)o) x += y;
+    }
+    if (lane_id() == 31) warp_tot[threadIdx.x / 32] = x;
+    __syncthreads();
+    uint64_t off = boff[blockIdx.x];
+    for (uint32_t w = 0; w < threadIdx.x / 32; ++w) off += warp_tot[w];
+    off += x - mine;
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        if (c[t]) {
+            const uint32_t i = first + t;
+            const uint32_t pl = lp[i];
+            const uint32_t lo = rlo[i];
+            for (uint32_t j = 0; j < c[t]; ++j) {
+                const uint64_t o = off + j;
+                if (o < cap) {
+                    out_l[o] = pl;
+                    out_r[o] = rp[lo + j];
+                }
+            }
+            off += c[t];
+        }
+    }
+}
+
+}  // namespace
+}  // namespace sbh
+
+extern "C" int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, const uint64_t* d_rkeys,
+                        const uint32_t* d_rptrs, uint64_t nr, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
+                        uint64_t* d_npairs, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (nl > 0xFFFFFFFFull || nr > 0xFFFFFFFFull) { set_error("inputs must be < 2^32 rows"); return SBH_EINVAL; }
+    const uint64_t nblocks = (nl + kTile - 1) / kTile;
+    Carver c(nullptr);
+    c.take<uint32_t>(nl);
+    c.take<uint32_t>(nl);
+    c.take<uint64_t>(nblocks + 1);
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, c.bytes(), &done);
+    if (rc || done) return rc;
+    if (!d_npairs) { set_error("d_npairs is NULL"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    if (nl == 0 || nr == 0) {
+        SBH_CUDA(cudaMemsetAsync(d_npairs, 0, sizeof(uint64_t), s));
+        return SBH_OK;
+    }
+    if (!d_lkeys || !d_lptrs || !d_rkeys || !d_rptrs || (cap && (!d_out_l || !d_out_r))) {
+        set_error("null pointer");
+        return SBH_EINVAL;
+    }
+    Carver w(d_scratch);
+    uint32_t* rlo = w.take<uint32_t>(nl);
+    uint32_t* cnt = w.take<uint32_t>(nl);
+    uint64_t* bsum = w.take<uint64_t>(nblocks + 1);
+    SBH_TIMED("join_count", s, join_count_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lkeys, (uint32_t)nl, d_rkeys, (uint32_t)nr, rlo, cnt,
+                                                              bsum));
+    SBH_LAUNCHED();
+    SBH_TIMED("join_scan", s, scan_blocks_kernel<<<1, 1024, 0, s>>>(bsum, (uint32_t)nblocks, d_npairs));
+    SBH_LAUNCHED();
+    SBH_TIMED("join_emit", s, join_emit_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lptrs, (uint32_t)nl, d_rptrs, rlo, cnt, bsum, d_out_l,
+                                                             d_out_r, cap));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}

@@ -1,0 +1,187 @@
+// A5 Merge: merge-path merge of sorted KPAs in (key, ptr) order.
+//
+// Two runs A and B are merged by output tiles of 2048 pairs.  Each CTA finds
+// where its first and last output diagonal cut A and B (binary search on the
+// merge path), stages the two slices in shared memory, and each thread merges
+// 8 outputs from its own co-rank.  More than two runs are merged in rounds of
+// pairwise merges through a scratch ping-pong buffer.
+#include <vector>
+
+#include "common.cuh"
+
+namespace sbh {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kIpt = 8;
+constexpr int kTile = kThreads * kIpt;
+
+__device__ __forceinline__ bool kp_less(uint64_t ka, uint32_t pa, uint64_t kb, uint32_t pb) {
+    return ka < kb || (ka == kb && pa < pb);
+}
+
+// Number of A elements among the first d outputs of merge(A, B).
+template <typename KA, typename PA, typename KB, typename PB>
+__device__ __forceinline__ uint32_t corank(uint32_t d, const KA ak, const PA ap, uint32_t na, const KB bk,
+                                           const PB bp, uint32_t nb) {
+    uint32_t lo = d > nb ? d - nb : 0;
+    uint32_t hi = d < na ? d : na;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        const uint32_t j = d - mid - 1;
+        if (kp_less(bk[j], bp[j], ak[mid], ap[mid])) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads)
+merge_pair_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ap, uint32_t na,
+                  const uint64_t* __restrict__ bk, const uint32_t* __restrict__ bp, uint32_t nb,
+                  uint64_t* __restrict__ ok, uint32_t* __restrict__ op) {
+    __shared__ uint64_t sk[kTile];
+    __shared__ uint32_t sp[kTile];
+    __shared__ uint32_t cut[2];
+    const uint32_t total = na + nb;
+    const uint32_t d0 = blockIdx.x * kTile;
+    const uint32_t d1 = min(d0 + kTile, total);
+    if (threadIdx.x < 2) cut[threadIdx.x] = corank(threadIdx.x ? d1 : d0, ak, ap, na, bk, bp, nb);
+    __syncthreads();
+    const uint32_t a0 = cut[0], a1 = cut[1];
+    const uint32_t b0 = d0 - a0, b1 = d1 - a1;
+    const uint32_t la = a1 - a0, lb = b1 - b0, len = d1 - d0;
+    // stage A slice then B slice
+    for (uint32_t i = threadIdx.x; i < len; i += kThreads) {
+        if (i < la) { sk[i] = ak[a0 + i]; sp[i] = ap[a0 + i]; }
+        else { sk[i] = bk[b0 + i - la]; sp[i] = bp[b0 + i - la]; }
+    }
+    __syncthreads();
+    // each thread merges kIpt outputs starting at its own diagonal
+    const uint32_t my = min(threadIdx.x * kIpt, len);
+    uint32_t i = corank(my, sk, sp, la, sk + la, sp + la, lb);
+    uint32_t j = my - i;
+    uint64_t rk[kIpt];
+    uint32_t rp[kIpt];
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        const bool ha = i < la, hb = j < lb;
+        bool take_a = ha && (!hb || !kp_less(sk[la + j], sp[la + j], sk[i], sp[i]));
+        if (ha || hb) {
+            const uint32_t idx = take_a ? i : la + j;
+            rk[t] = sk[idx];
+            rp[t] = sp[idx];
+            i += take_a;
+            j += !take_a;
+        } else {
+            rk[t] = 0;
+            rp[t] = 0;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        const uint32_t o = threadIdx.x * kIpt + t;
+        if (o < len) { sk[o] = rk[t]; sp[o] = rp[t]; }
+    }
+    __syncthreads();
+    for (uint32_t o = threadIdx.x; o < len; o += kThreads) {
+        st_stream(ok + d0 + o, sk[o]);
+        st_stream(op + d0 + o, sp[o]);
+    }
+}
+
+__global__ void copy_run_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ p, uint32_t n,
+                                uint64_t* __restrict__ ok, uint32_t* __restrict__ op) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        ok[i] = k[i];
+        op[i] = p[i];
+    }
+}
+
+struct Run {
+    const uint64_t* k;
+    const uint32_t* p;
+    uint64_t n;
+};
+
+int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, cudaStream_t s) {
+    const uint64_t total = a.n + b.n;
+    if (total == 0) return SBH_OK;
+    const unsigned grid = (unsigned)((total + kTile - 1) / kTile);
+    SBH_TIMED("merge_path", s, merge_pair_kernel<<<grid, kThreads, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p, (uint32_t)b.n, ok, op));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int copy_run(const Run& a, uint64_t* ok, uint32_t* op, cudaStream_t s) {
+    if (a.n == 0 || a.k == ok) return SBH_OK;
+    const unsigned grid = (unsigned)min_u64((a.n + 255) / 256, (uint64_t)num_sms() * 8);
+    SBH_TIMED("merge_copy", s, copy_run_kernel<<<grid, 256, 0, s>>>(a.k, a.p, (uint32_t)a.n, ok, op));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+}  // namespace
+}  // namespace sbh
+
+extern "C" int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const uint32_t* const* d_run_ptrs,
+                             const uint64_t* run_lens, uint64_t* d_keys_out, uint32_t* d_ptrs_out, void* d_scratch,
+                             size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (nruns < 0 || (nruns > 0 && (!d_run_keys || !d_run_ptrs || !run_lens))) {
+        set_error("bad run arrays");
+        return SBH_EINVAL;
+    }
+    uint64_t total = 0;
+    for (int r = 0; r < nruns; ++r) total += run_lens[r];
+    if (total > 0xFFFFFFFFull) { set_error("total length must be < 2^32"); return SBH_EINVAL; }
+    Carver c(nullptr);
+    if (nruns > 2) { c.take<uint64_t>(total); c.take<uint32_t>(total); c.take<uint64_t>(total); c.take<uint32_t>(total); }
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, c.bytes(), &done);
+    if (rc || done) return rc;
+    if (total == 0) return SBH_OK;
+    if (!d_keys_out || !d_ptrs_out) { set_error("null output"); return SBH_EINVAL; }
+    for (int r = 0; r < nruns; ++r)
+        if (run_lens[r] && (!d_run_keys[r] || !d_run_ptrs[r])) { set_error("null run pointer"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    std::vector<Run> runs;
+    for (int r = 0; r < nruns; ++r)
+        if (run_lens[r]) runs.push_back({d_run_keys[r], d_run_ptrs[r], run_lens[r]});
+    if (runs.size() == 1) return copy_run(runs[0], d_keys_out, d_ptrs_out, s);
+    if (runs.size() == 2) return merge_two(runs[0], runs[1], d_keys_out, d_ptrs_out, s);
+    // rounds of pairwise merges; each round writes one of two scratch buffers,
+    // the last round writes the output
+    Carver w(d_scratch);
+    uint64_t* bk[2];
+    uint32_t* bp[2];
+    bk[0] = w.take<uint64_t>(total);
+    bp[0] = w.take<uint32_t>(total);
+    bk[1] = w.take<uint64_t>(total);
+    bp[1] = w.take<uint32_t>(total);
+    int cur = 0;
+    while (runs.size() > 1) {
+        const bool last = runs.size() == 2;
+        uint64_t* ok = last ? d_keys_out : bk[cur];
+        uint32_t* op = last ? d_ptrs_out : bp[cur];
+        std::vector<Run> next;
+        uint64_t off = 0;
+        for (size_t r = 0; r + 1 < runs.size(); r += 2) {
+            rc = merge_two(runs[r], runs[r + 1], ok + off, op + off, s);
+            if (rc) return rc;
+            next.push_back({ok + off, op + off, runs[r].n + runs[r + 1].n});
+            off += runs[r].n + runs[r + 1].n;
+        }
+        if (runs.size() % 2) {
+            const Run& odd = runs.back();
+            rc = copy_run(odd, ok + off, op + off, s);
+            if (rc) return rc;
+            next.push_back({ok + off, op + off, odd.n});
+        }
+        runs.swap(next);
+        cur ^= 1;
+    }
+    return SBH_OK;
+}

@@ -1,0 +1,397 @@
+// A3 Sort: stable LSD radix sort of a KPA (uint64 key, uint32 ptr), 8-bit
+// digits, one onesweep kernel per digit position that is not constant.
+//
+// Per call:
+//   upsweep   one read of the keys builds the 256-bin histogram of all eight
+//             digit positions.
+//   plan      exclusive scan of each histogram (global digit offsets); a
+//             position whose digit is the same for every key is skipped; the
+//             ping-pong buffer of each active pass is chosen so that the last
+//             one writes the output.
+//   onesweep  per active position: persistent CTAs take tiles in order from
+//             a counter; each ranks its tile with a warp multisplit
+//             (__match_any_sync), publishes its per-digit counts, looks back
+//             over earlier tiles for its global offsets (decoupled look-back,
+//             bounded wait) and scatters keys and ptrs through shared memory.
+//   copy      only when no pass ran (or an in-place sort ends in the
+//             temporary buffer).
+#include "common.cuh"
+
+namespace sbh {
+namespace {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kPositions = 64 / kRadixBits;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kIpt = 16;                    // keys per thread
+constexpr int kTile = kThreads * kIpt;      // keys per tile
+
+// look-back record: [63:62] flag, [61:56] epoch (pass + 1), [55:0] count
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 56) - 1;
+
+struct Plan {
+    int active[kPositions];
+    int src[kPositions];  // 0 = input, 1 = temporary, 2 = output
+    int dst[kPositions];
+    int copy_src;         // -1 = no copy, else the buffer to copy to the output
+    int npasses;
+};
+
+struct Buffers {
+    const uint64_t* in_k;
+    const uint32_t* in_p;
+    uint64_t* tmp_k;
+    uint32_t* tmp_p;
+    uint64_t* out_k;
+    uint32_t* out_p;
+    __device__ __forceinline__ const uint64_t* keys(int sel) const { return sel == 0 ? in_k : (sel == 1 ? tmp_k : out_k); }
+    __device__ __forceinline__ const uint32_t* ptrs(int sel) const { return sel == 0 ? in_p : (sel == 1 ? tmp_p : out_p); }
+    __device__ __forceinline__ uint64_t* wkeys(int sel) const { return sel == 1 ? tmp_k : out_k; }
+    __device__ __forceinline__ uint32_t* wptrs(int sel) const { return sel == 1 ? tmp_p : out_p; }
+};
+
+// ------------------------------------------------------------------ upsweep
+__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                      uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[kPositions * kRadix];
+    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    // Equal digits in a row are counted in registers first: skewed keys (a
+    // heavy key, constant high bytes) would otherwise serialise on one bin.
+    uint32_t last[kPositions], run[kPositions];
+#pragma unroll
+    for (int p = 0; p < kPositions; ++p) { last[p] = 0; run[p] = 0; }
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = ld_stream(keys + i);
+#pragma unroll
+        for (int p = 0; p < kPositions; ++p) {
+            const uint32_t d = static_cast<uint32_t>(k >> (p * kRadixBits)) & (kRadix - 1);
+            if (d == last[p]) {
+                ++run[p];
+            } else {
+                if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
+                last[p] = d;
+                run[p] = 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < kPositions; ++p)
+        if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
+}
+
+// ------------------------------------------------------------------ plan
+__global__ void __launch_bounds__(kRadix) plan_kernel(const uint32_t* __restrict__ ghist, uint32_t n,
+                                                      uint32_t* __restrict__ gbase, Plan* __restrict__ plan,
+                                                      int in_place) {
+    __shared__ uint32_t warp_sums[kRadix / 32];
+    __shared__ int s_active[kPositions];
+    const int d = threadIdx.x;
+    for (int p = 0; p < kPositions; ++p) {
+        const uint32_t c = ghist[p * kRadix + d];
+        const int constant = __syncthreads_or(c == n);
+        // block exclusive scan of c over the 256 digits
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (uint32_t)o) x += y;
+        }
+        if (lane_id() == 31) warp_sums[d / 32] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < d / 32; ++w) before += warp_sums[w];
+        gbase[p * kRadix + d] = before + x - c;
+        if (d == 0) s_active[p] = !constant;
+        __syncthreads();
+    }
+    if (d == 0) {
+        Plan pl;
+        int a = 0;
+        for (int p = 0; p < kPositions; ++p) a += s_active[p];
+        int i = 0, prev = 0;
+        for (int p = 0; p < kPositions; ++p) {
+            pl.active[p] = s_active[p];
+            pl.src[p] = pl.dst[p] = 0;
+            if (!s_active[p]) continue;
+            int dst;
+            if (in_place) dst = (i % 2 == 0) ? 1 : 2;
+            else dst = ((a - 1 - i) % 2 == 0) ? 2 : 1;
+            pl.src[p] = (i == 0) ? 0 : prev;
+            pl.dst[p] = dst;
+            prev = dst;
+            ++i;
+        }
+        if (a == 0) pl.copy_src = in_place ? -1 : 0;
+        else pl.copy_src = (prev == 2) ? -1 : prev;
+        pl.npasses = a;
+        *plan = pl;
+    }
+}
+
+// ------------------------------------------------------------------ onesweep
+struct SortSmem {
+    union {
+        uint64_t keys[kTile];
+        uint32_t ptrs[kTile];
+    } stage;
+    uint32_t whist[kWarps][kRadix + 1];  // +1: sentinel digit of rows past the end
+    uint32_t local_start[kRadix];
+    uint32_t gbase_rel[kRadix];
+    uint32_t scan_tmp[kWarps];
+    uint32_t tile;
+};
+
+__global__ void __launch_bounds__(kThreads, 2)
+onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, const uint32_t* __restrict__ gbase,
+                uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter, uint32_t spin_limit,
+                int skip_publish_tile0, uint32_t* __restrict__ status) {
+    if (!plan->active[pos]) return;
+    const int src = plan->src[pos], dst = plan->dst[pos];
+    const uint64_t* __restrict__ in_k = buf.keys(src);
+    const uint32_t* __restrict__ in_p = buf.ptrs(src);
+    uint64_t* __restrict__ out_k = buf.wkeys(dst);
+    uint32_t* __restrict__ out_p = buf.wptrs(dst);
+    const int shift = pos * kRadixBits;
+    const uint64_t epoch = static_cast<uint64_t>(pos + 1) << 56;
+    const uint32_t ntiles = (n + kTile - 1) / kTile;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
+
+    for (;;) {
+        if (tid == 0) sm.tile = atomicAdd(tile_counter + pos, 1u);
+        for (int i = tid; i < kWarps * (kRadix + 1); i += kThreads) (&sm.whist[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t tile = sm.tile;
+        if (tile >= ntiles) break;
+        const uint32_t base = tile * kTile;
+        const uint32_t valid = min(n - base, (uint32_t)kTile);
+
+        // ---- load (warp-striped: warp w owns 32*kIpt consecutive rows)
+        uint64_t k[kIpt];
+        uint32_t dig[kIpt];
+        const uint32_t wbase = base + warp * 32 * kIpt + lane;
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t r = wbase + j * 32;
+            const bool ok = r < n;
+            k[j] = ok ? ld_stream(in_k + r) : 0ull;
+            dig[j] = ok ? (static_cast<uint32_t>(k[j] >> shift) & (kRadix - 1)) : kRadix;
+        }
+        uint32_t p[kIpt];
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t r = wbase + j * 32;
+            p[j] = r < n ? ld_stream(in_p + r) : 0u;
+        }
+
+        // ---- warp multisplit: rank of each key among equal digits of its warp
+        uint32_t rank[kIpt];
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if ((int)lane == leader) {
+                b = sm.whist[warp][dig[j]];
+                sm.whist[warp][dig[j]] = b + __popc(peers);
+            }
+            b = __shfl_sync(0xffffffffu, b, leader);
+            rank[j] = b + __popc(peers & lt);
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // ---- per digit (thread = digit): warp offsets, tile count, publish
+        const uint32_t d = tid;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = sm.whist[w][d];
+            sm.whist[w][d] = cnt;
+            cnt += c;
+        }
+        uint64_t* rec = lookback + (uint64_t)tile * kRadix + d;
+        const bool publish = !(skip_publish_tile0 && tile == 0);
+        if (publish) st_release(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
+
+        // block exclusive scan of the tile counts over digits
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) sm.scan_tmp[warp] = x;
+
+        // decoupled look-back over earlier tiles (bounded)
+        uint64_t excl = 0;
+        if (tile > 0) {
+            uint32_t t = tile - 1;
+            uint32_t polls = 0;
+            for (;;) {
+                const uint64_t s = ld_acquire(lookback + (uint64_t)t * kRadix + d);
+                if ((s & (3ull << 62)) == 0 || (s & (63ull << 56)) != epoch) {
+                    if (wait_expired(polls, spin_limit, status)) break;
+                    continue;
+                }
+                excl += s & kValueMask;
+                if ((s & (3ull << 62)) == kFlagPrefix || t == 0) break;
+                --t;
+            }
+            st_release(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
+        }
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
+        const uint32_t lstart = before + x - cnt;
+        sm.local_start[d] = lstart;
+        sm.gbase_rel[d] = gbase[pos * kRadix + d] + static_cast<uint32_t>(excl) - lstart;
+        __syncthreads();
+
+        // ---- keys: scatter into shared memory in digit order, then out
+        uint32_t slot[kIpt];
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            if (dig[j] < kRadix) {
+                slot[j] = sm.local_start[dig[j]] + sm.whist[warp][dig[j]] + rank[j];
+                sm.stage.keys[slot[j]] = k[j];
+            }
+        }
+        __syncthreads();
+        uint32_t gpos[kIpt];
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t s = tid + j * kThreads;
+            if (s < valid) {
+                const uint64_t kk = sm.stage.keys[s];
+                gpos[j] = sm.gbase_rel[static_cast<uint32_t>(kk >> shift) & (kRadix - 1)] + s;
+                if (gpos[j] < n) st_stream(out_k + gpos[j], kk);  // false only after an expired wait
+            }
+        }
+        __syncthreads();
+        // ---- ptrs: same slots
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j)
+            if (dig[j] < kRadix) sm.stage.ptrs[slot[j]] = p[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t s = tid + j * kThreads;
+            if (s < valid && gpos[j] < n) st_stream(out_p + gpos[j], sm.stage.ptrs[s]);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ copy
+__global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ plan) {
+    const int sel = plan->copy_src;
+    if (sel < 0) return;
+    const uint64_t* __restrict__ sk = buf.keys(sel);
+    const uint32_t* __restrict__ sp = buf.ptrs(sel);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        buf.out_k[i] = sk[i];
+        buf.out_p[i] = sp[i];
+    }
+}
+
+struct SortScratch {
+    uint64_t* tmp_k;
+    uint32_t* tmp_p;
+    uint32_t* hist;        // kPositions * kRadix   (zeroed)
+    uint32_t* counters;    // kPositions            (zeroed)
+    uint64_t* lookback;    // ntiles * kRadix       (zeroed)
+    uint32_t* gbase;       // kPositions * kRadix
+    Plan* plan;
+    char* zero_begin;
+    size_t zero_bytes;
+    size_t total;
+};
+
+SortScratch carve(void* scratch, uint64_t n) {
+    Carver c(scratch);
+    SortScratch s;
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    s.tmp_k = c.take<uint64_t>(n);
+    s.tmp_p = c.take<uint32_t>(n);
+    s.gbase = c.take<uint32_t>(kPositions * kRadix);
+    s.plan = c.take<Plan>(1);
+    // zeroed region: histogram, tile counters, look-back records
+    s.hist = c.take<uint32_t>(kPositions * kRadix);
+    const size_t zb = c.off - kPositions * kRadix * sizeof(uint32_t);
+    s.counters = c.take<uint32_t>(kPositions);
+    s.lookback = c.take<uint64_t>(ntiles * kRadix);
+    s.zero_begin = reinterpret_cast<char*>(s.hist);
+    s.zero_bytes = c.off - zb;
+    s.total = c.bytes();
+    return s;
+}
+
+}  // namespace
+
+// Shared with the learned sort: a full radix sort on a caller stream.
+int radix_sort_launch(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
+                      void* scratch, cudaStream_t s) {
+    if (n == 0) return SBH_OK;
+    const int in_place = (in_k == out_k);
+    if (in_place != (in_p == out_p)) { set_error("an in-place sort needs both keys and ptrs aliased"); return SBH_EINVAL; }
+    SortScratch sc = carve(scratch, n);
+    SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
+    const int sms = num_sms();
+    const uint32_t n32 = static_cast<uint32_t>(n);
+    unsigned up_blocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
+    SBH_TIMED("sort_upsweep", s, upsweep_kernel<<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist));
+    SBH_LAUNCHED();
+    SBH_TIMED("sort_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
+    SBH_LAUNCHED();
+    Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
+    const size_t smem = sizeof(SortSmem);
+    SBH_CUDA(cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)sms * per_sm);
+    const uint32_t limit = spin_limit();
+    int fault = take_fault();
+    uint32_t* status = status_word();
+    for (int pos = 0; pos < kPositions; ++pos) {
+        SBH_TIMED("sort_onesweep", s, onesweep_kernel<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
+                                                      fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status));
+        SBH_LAUNCHED();
+    }
+    unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
+    SBH_TIMED("sort_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+size_t radix_sort_scratch(uint64_t n) { return carve(nullptr, n).total; }
+
+}  // namespace sbh
+
+extern "C" int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
+                            uint32_t* d_ptrs_out, uint64_t n, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n > 0xFFFFFFFFull) { set_error("n must be < 2^32"); return SBH_EINVAL; }
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, radix_sort_scratch(n), &done);
+    if (rc || done) return rc;
+    if (n == 0) return SBH_OK;
+    if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out) { set_error("null pointer"); return SBH_EINVAL; }
+    return radix_sort_launch(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, d_scratch, as_stream(stream));
+}

@@ -1,0 +1,293 @@
+"""Python binding of the C ABI in include/sbh.h (ctypes).
+
+Argument marshalling only: every step of the KPA grouping path runs in the
+CUDA kernels of libsbh.so.  Tensors must be CUDA tensors (or, for the key
+column of extract, a page-locked CPU tensor).  Calls run on the current
+PyTorch CUDA stream unless a stream is given.  Working memory is allocated
+with PyTorch.
+
+If libsbh.so cannot be loaded, importing this module raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsbh.so")
+
+SBH_OK, SBH_EINVAL, SBH_ENOSPACE, SBH_ETIMEOUT, SBH_ECUDA = 0, 1, 2, 3, 4
+SBH_FAULT_NONE, SBH_FAULT_SKIP_PUBLISH = 0, 1
+TOPK_PAD_VAL = 0
+TOPK_PAD_PTR = 0xFFFFFFFF
+TOPK_MAX_K = 8
+
+_ERRNAMES = {1: "SBH_EINVAL", 2: "SBH_ENOSPACE", 3: "SBH_ETIMEOUT", 4: "SBH_ECUDA"}
+
+
+class SbhError(RuntimeError):
+    def __init__(self, code: int, where: str, text: str):
+        super().__init__(f"{where}: {_ERRNAMES.get(code, code)}: {text}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1901_01328_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "sbh_version": ([], ctypes.c_char_p),
+        "sbh_last_error": ([], ctypes.c_char_p),
+        "sbh_sync_status": ([vp], i32),
+        "sbh_set_spin_limit": ([u32], None),
+        "sbh_set_fault": ([i32], None),
+        "sbh_profile_enable": ([i32], None),
+        "sbh_profile_collect": ([i32, vp, i32, vp], i32),
+        "sbh_window_ranges": ([vp, i32, u64, vp, u64, u64, vp, vp, vp], i32),
+        "sbh_kpa_extract": ([vp, u64, u64, vp, vp, vp, vp, u64, vp], i32),
+        "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
+        "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
+        "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_topk": ([vp, vp, u64, vp, i32, i32, vp, vp, vp, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_join": ([vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, sz, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
+            "sbh_profile_enable", "sbh_profile_collect",
+            "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_sort", "sbh_kpa_merge", "sbh_group_reduce",
+            "sbh_topk", "sbh_join")
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != SBH_OK:
+        raise SbhError(rc, where, _lib.sbh_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _scratch(fn, args_before, args_after, where, device):
+    """Size query, allocation and call with the (scratch, scratch_bytes) tail."""
+    nbytes = ctypes.c_size_t(0)
+    _check(fn(*args_before, None, ctypes.byref(nbytes), *args_after), where + " (size query)")
+    buf = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=device)
+    _check(fn(*args_before, buf.data_ptr(), ctypes.byref(nbytes), *args_after), where)
+    return buf
+
+
+def version() -> str:
+    return _lib.sbh_version().decode()
+
+
+def sync_status(stream=None) -> int:
+    """Waits for the stream; returns SBH_OK or SBH_ETIMEOUT (device wait expired)."""
+    return _lib.sbh_sync_status(_stream(stream))
+
+
+def set_spin_limit(polls: int):
+    _lib.sbh_set_spin_limit(polls)
+
+
+def set_fault(fault: int):
+    _lib.sbh_set_fault(fault)
+
+
+def profile_enable(on: bool = True):
+    """Start (or stop) recording an event pair around every kernel launch."""
+    _lib.sbh_profile_enable(1 if on else 0)
+
+
+def profile_collect():
+    """[(kernel name, milliseconds)] of the recorded launches, in launch order."""
+    n = _lib.sbh_profile_collect(0, None, 0, None)
+    if n == 0:
+        return []
+    name_len = 48
+    names = ctypes.create_string_buffer(n * name_len)
+    ms = (ctypes.c_double * n)()
+    _lib.sbh_profile_collect(n, ctypes.cast(names, ctypes.c_void_p), name_len, ctypes.cast(ms, ctypes.c_void_p))
+    raw = names.raw
+    return [(raw[i * name_len:(i + 1) * name_len].split(b"\0", 1)[0].decode(), ms[i]) for i in range(n)]
+
+
+# ----------------------------------------------------------------- raw calls
+def sbh_window_ranges(ts, starts, length, row_begin, row_end, stream=None):
+    assert ts.dtype in (torch.int32, torch.uint32, torch.int64, torch.uint64)
+    _check(_lib.sbh_window_ranges(_p(ts), ts.element_size(), ts.numel(), _p(starts), length, starts.numel(),
+                                  _p(row_begin), _p(row_end), _stream(stream)), "sbh_window_ranges")
+
+
+def sbh_kpa_extract(key_col, row_begin, n, keys_out, ptrs_out, key_or=None, samples=None, sample_stride=0,
+                    stream=None):
+    _check(_lib.sbh_kpa_extract(_p(key_col), row_begin, n, _p(keys_out), _p(ptrs_out), _p(key_or), _p(samples),
+                                sample_stride, _stream(stream)), "sbh_kpa_extract")
+
+
+def sbh_kpa_sort(keys_in, ptrs_in, keys_out, ptrs_out, scratch=None, stream=None):
+    """Sorts n = keys_in.numel() pairs.  Allocates scratch if none is given;
+    returns the scratch buffer used."""
+    n = keys_in.numel()
+    args = (_p(keys_in), _p(ptrs_in), _p(keys_out), _p(ptrs_out), n)
+    if scratch is None:
+        return _scratch(_lib.sbh_kpa_sort, args, (_stream(stream),), "sbh_kpa_sort", keys_in.device)
+    nbytes = ctypes.c_size_t(scratch.numel() * scratch.element_size())
+    _check(_lib.sbh_kpa_sort(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_kpa_sort")
+    return scratch
+
+
+def sort_scratch_bytes(n: int) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_kpa_sort(None, None, None, None, n, None, ctypes.byref(nbytes), None), "sbh_kpa_sort")
+    return nbytes.value
+
+
+def sbh_kpa_merge(runs, keys_out, ptrs_out, stream=None):
+    """runs: list of (keys, ptrs) CUDA tensors, each sorted."""
+    r = len(runs)
+    kp = (ctypes.c_void_p * max(1, r))(*[k.data_ptr() for k, _ in runs])
+    pp = (ctypes.c_void_p * max(1, r))(*[p.data_ptr() for _, p in runs])
+    ln = (ctypes.c_uint64 * max(1, r))(*[k.numel() for k, _ in runs])
+    args = (r, ctypes.cast(kp, ctypes.c_void_p), ctypes.cast(pp, ctypes.c_void_p), ctypes.cast(ln, ctypes.c_void_p),
+            _p(keys_out), _p(ptrs_out))
+    _scratch(_lib.sbh_kpa_merge, args, (_stream(stream),), "sbh_kpa_merge", keys_out.device)
+
+
+def sbh_group_reduce(keys, ptrs, vals, out_keys, out_counts, out_sums, cap, nkeys, scratch=None, stream=None):
+    vb = 0 if vals is None else vals.element_size()
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(vals), vb, _p(out_keys), _p(out_counts), _p(out_sums), cap,
+            _p(nkeys))
+    if scratch is None:
+        return _scratch(_lib.sbh_group_reduce, args, (_stream(stream),), "sbh_group_reduce", keys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_group_reduce(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_group_reduce")
+    return scratch
+
+
+def sbh_topk(keys, ptrs, vals, K, out_keys, out_nvalid, out_vals, out_ptrs, cap, nkeys, scratch=None, stream=None):
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(vals), vals.element_size(), K, _p(out_keys), _p(out_nvalid),
+            _p(out_vals), _p(out_ptrs), cap, _p(nkeys))
+    if scratch is None:
+        return _scratch(_lib.sbh_topk, args, (_stream(stream),), "sbh_topk", keys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_topk(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_topk")
+    return scratch
+
+
+def sbh_join(lkeys, lptrs, rkeys, rptrs, out_l, out_r, cap, npairs, scratch=None, stream=None):
+    args = (_p(lkeys), _p(lptrs), lkeys.numel(), _p(rkeys), _p(rptrs), rkeys.numel(), _p(out_l), _p(out_r), cap,
+            _p(npairs))
+    if scratch is None:
+        return _scratch(_lib.sbh_join, args, (_stream(stream),), "sbh_join", lkeys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_join(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_join")
+    return scratch
+
+
+# ----------------------------------------------------------------- conveniences
+def _u64(n, dev):
+    return torch.empty(n, dtype=torch.uint64, device=dev)
+
+
+def _u32(n, dev):
+    return torch.empty(n, dtype=torch.uint32, device=dev)
+
+
+def extract(key_col, row_begin=0, n=None, device="cuda", sample_stride=0):
+    """KPA of rows [row_begin, row_begin + n) -> (keys, ptrs[, key_or, samples])."""
+    if n is None:
+        n = key_col.numel() - row_begin
+    keys, ptrs = _u64(n, device), _u32(n, device)
+    key_or = _u64(1, device)
+    samples = _u64((n + sample_stride - 1) // sample_stride, device) if sample_stride else None
+    sbh_kpa_extract(key_col, row_begin, n, keys, ptrs, key_or, samples, sample_stride)
+    if sample_stride:
+        return keys, ptrs, key_or, samples
+    return keys, ptrs
+
+
+def sort(keys, ptrs, out=None):
+    """Sorted copy (or into out=(keys_out, ptrs_out), which may alias the input)."""
+    if out is None:
+        out = (torch.empty_like(keys), torch.empty_like(ptrs))
+    sbh_kpa_sort(keys, ptrs, out[0], out[1])
+    return out
+
+
+def merge(runs):
+    total = sum(k.numel() for k, _ in runs)
+    dev = runs[0][0].device
+    ok, op = _u64(total, dev), _u32(total, dev)
+    sbh_kpa_merge(runs, ok, op)
+    return ok, op
+
+
+def group_reduce(keys, ptrs, vals=None, cap=None):
+    """Per distinct key: (keys, counts, sums or None); synchronises to size the result."""
+    n = keys.numel()
+    cap = n if cap is None else cap
+    dev = keys.device
+    ok, oc = _u64(max(cap, 1), dev), _u64(max(cap, 1), dev)
+    osum = _u64(max(cap, 1), dev) if vals is not None else None
+    nk = _u64(1, dev)
+    sbh_group_reduce(keys, ptrs, vals, ok, oc, osum, cap, nk)
+    m = int(nk.item())
+    m = min(m, cap)
+    return ok[:m], oc[:m], (osum[:m] if osum is not None else None)
+
+
+def topk(keys, ptrs, vals, K, cap=None):
+    n = keys.numel()
+    cap = n if cap is None else cap
+    dev = keys.device
+    ok = _u64(max(cap, 1), dev)
+    nv = torch.empty(max(cap, 1), dtype=torch.uint8, device=dev)
+    ov = _u64(max(cap, 1) * K, dev)
+    op = _u32(max(cap, 1) * K, dev)
+    nk = _u64(1, dev)
+    sbh_topk(keys, ptrs, vals, K, ok, nv, ov, op, cap, nk)
+    m = min(int(nk.item()), cap)
+    return ok[:m], nv[:m], ov[: m * K].view(m, K) if m else ov[:0].view(0, K), op[: m * K].view(m, K) if m else op[:0].view(0, K)
+
+
+def join(lkeys, lptrs, rkeys, rptrs, cap=None):
+    """All (ptrL, ptrR) pairs; with cap None, counts first (two calls)."""
+    dev = lkeys.device
+    npairs = _u64(1, dev)
+    if cap is None:
+        sbh_join(lkeys, lptrs, rkeys, rptrs, None, None, 0, npairs)
+        cap = int(npairs.item())
+    ol, orr = _u32(max(cap, 1), dev), _u32(max(cap, 1), dev)
+    sbh_join(lkeys, lptrs, rkeys, rptrs, ol, orr, cap, npairs)
+    m = min(int(npairs.item()), cap)
+    return ol[:m], orr[:m]
+
+
+def window_ranges(ts, starts, length):
+    rb = _u64(starts.numel(), ts.device)
+    re_ = _u64(starts.numel(), ts.device)
+    sbh_window_ranges(ts, starts, length, rb, re_)
+    return rb, re_

@@ -1,0 +1,69 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry
+point include/sbh.h declares, and rejects bad arguments on the host before
+any launch (no call below reaches the GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1901_01328_b300 import build
+    build.build()
+    from paper_1901_01328_b300 import sbh
+    return sbh
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "sbh.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbh_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert "sbh_kpa_sort" in names and "sbh_join" in names
+    lib = ctypes.CDLL(L.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(L.EXPORTED)
+
+
+def test_version_and_error_text(L):
+    assert "sm_103a" in L.version()
+
+
+def test_scratch_size_queries_need_no_gpu(L):
+    lib = L.lib()
+    nb = ctypes.c_size_t(0)
+    assert lib.sbh_kpa_sort(None, None, None, None, 256_000_000, None, ctypes.byref(nb), None) == 0
+    # ping-pong copy (12 B per pair) plus look-back records
+    assert 256_000_000 * 12 <= nb.value < 256_000_000 * 12 + 200_000_000
+    for fn, args in ((lib.sbh_group_reduce, (None, None, 10_000, None, 8, None, None, None, 0, None)),
+                     (lib.sbh_topk, (None, None, 10_000, None, 8, 3, None, None, None, None, 0, None)),
+                     (lib.sbh_join, (None, None, 10_000, None, None, 10, None, None, 0, None))):
+        nb = ctypes.c_size_t(0)
+        assert fn(*args, None, ctypes.byref(nb), None) == 0 and nb.value > 0
+
+
+def test_host_side_argument_errors(L):
+    lib = L.lib()
+    nb = ctypes.c_size_t(0)
+    assert lib.sbh_kpa_sort(None, None, None, None, 1 << 33, None, ctypes.byref(nb), None) == L.SBH_EINVAL
+    assert b"2^32" in lib.sbh_last_error()
+    assert lib.sbh_topk(None, None, 10, None, 8, 0, None, None, None, None, 0, None, None, ctypes.byref(nb),
+                        None) == L.SBH_EINVAL
+    assert lib.sbh_topk(None, None, 10, None, 8, 9, None, None, None, None, 0, None, None, ctypes.byref(nb),
+                        None) == L.SBH_EINVAL
+    # scratch present but too small
+    fake = ctypes.c_void_p(1 << 20)
+    small = ctypes.c_size_t(16)
+    assert lib.sbh_kpa_sort(fake, fake, fake, fake, 100_000, fake, ctypes.byref(small), None) == L.SBH_ENOSPACE
+    # scratch_bytes missing
+    assert lib.sbh_group_reduce(None, None, 10, None, 8, None, None, None, 0, None, None, None, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract(fake, (1 << 32) - 5, 10, fake, fake, None, None, 0, None) == L.SBH_EINVAL
+    assert lib.sbh_window_ranges(fake, 3, 10, fake, 5, 2, fake, fake, None) == L.SBH_EINVAL

@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, element by
+element, on seeded inputs: sizes that span several tiles with a ragged tail,
+edge cases, and the full workload sizes (bit-exact where the oracle finishes
+in seconds, by invariants beyond that)."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from tests import pins
+from tests.gpu_util import cuda, host, same, sorted_kpa_on_device
+
+pytestmark = pytest.mark.gpu
+
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import sbh
+    return sbh
+
+
+# ------------------------------------------------------------------ extract
+@pytest.mark.parametrize("n,row_begin", [(0, 0), (1, 0), (5, 3), (4097, 1), (1_000_000, 0), (999_999, 7)])
+def test_extract_parity(S, n, row_begin):
+    col = gen.mixed_keys(row_begin + n + 5)
+    d_col = cuda(col)
+    keys, ptrs, key_or, samples = S.extract(d_col, row_begin, n, sample_stride=100)
+    ok, op = oracle.extract(col, row_begin, n)
+    assert same(keys, ok) and same(ptrs, op)
+    if n:
+        assert int(host(key_or)[0]) == int(np.bitwise_or.reduce(ok))
+        assert same(samples, ok[::100])
+
+
+def test_extract_from_pinned_host(S):
+    col = gen.join_streams(300_001, key_space=1 << 24)["L"]["keys"]
+    pinned = torch.from_numpy(col).pin_memory()
+    keys, ptrs = S.extract(pinned, 1000, 250_000)
+    ok, op = oracle.extract(col, 1000, 250_000)
+    assert same(keys, ok) and same(ptrs, op)
+
+
+# ------------------------------------------------------------------ sort
+def _sort_case(kind, n, seed=1):
+    if kind == "uniform20":
+        return gen.uniform(seed, 1, n, 0, 1 << 20, np.uint64)
+    if kind == "mixed":
+        return gen.mixed_keys(n, seed=seed)
+    if kind == "equal":
+        return np.full(n, 0xDEADBEEF, dtype=np.uint64)
+    if kind == "extremes":
+        return np.where(gen.uniform(seed, 2, n, 0, 2, np.uint64) == 1, np.uint64(M64), np.uint64(0))
+    if kind == "highbyte":  # only the top digit varies: seven passes are skipped
+        return gen.uniform(seed, 3, n, 0, 256, np.uint64) << np.uint64(56)
+    if kind == "full64":
+        return gen.uniform(seed, 4, n, 0, 0, np.uint64)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["uniform20", "mixed", "equal", "extremes", "highbyte", "full64"])
+@pytest.mark.parametrize("n", [0, 1, 2, 4095, 4096, 4097, 100_003])
+def test_sort_parity(S, kind, n):
+    col = _sort_case(kind, n)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp = S.sort(keys, ptrs)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+    assert same(keys, col)  # the input is not written
+
+
+def test_sort_in_place_and_unordered_ptrs(S):
+    n = 50_001
+    col = gen.mixed_keys(n, seed=5)
+    ptrs = gen.uniform(5, 9, n, 0, 1 << 31, np.uint32)  # arbitrary pointers: ties keep input order
+    k, p = cuda(col), cuda(ptrs)
+    S.sort(k, p, out=(k, p))
+    order = np.argsort(col, kind="stable")
+    assert same(k, col[order]) and same(p, ptrs[order])
+    # odd number of passes (20-bit keys: three digits), in place
+    col = _sort_case("uniform20", n)
+    k, p = cuda(col), cuda(np.arange(n, dtype=np.uint32))
+    S.sort(k, p, out=(k, p))
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(k, ok) and same(p, op)
+
+
+def test_sort_tumbling_window_full_size(S):
+    w = gen.tumbling_window(1_000_000)
+    keys, ptrs = S.extract(cuda(w["keys"]), 0, 1_000_000)
+    sk, sp = S.sort(keys, ptrs)
+    ok, op = oracle.sort(*oracle.extract(w["keys"], 0, 1_000_000))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_sort_mixed_keys_16m_bit_exact(S):
+    n = 16_000_000
+    col = gen.mixed_keys(n)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp = S.sort(keys, ptrs)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_sort_mixed_keys_256m_invariants(S):
+    n = 256_000_000
+    col = torch.empty(n, dtype=torch.uint64)
+    gen.mixed_keys(n, out=col.numpy())
+    d_col = col.cuda()
+    keys, ptrs = S.extract(d_col, 0, n)
+    del col
+    S.sort(keys, ptrs, out=(keys, ptrs))
+    sorted_kpa_on_device(d_col, 0, keys, ptrs)
+    # sampled rows against the oracle's sort of the same rows: the rank of a
+    # sampled (key, ptr) pair equals the number of pairs below it
+    idx = torch.linspace(0, n - 1, 257, dtype=torch.int64).cuda()
+    sk = (d_col.view(torch.int64) ^ torch.iinfo(torch.int64).min)
+    for i in host(idx)[:: 32]:
+        kk, pp = keys[i].view(torch.int64) ^ torch.iinfo(torch.int64).min, int(ptrs[i])
+        below = int((sk < kk).sum()) + int(((sk == kk) & (torch.arange(n, device="cuda") < pp)).sum())
+        assert below == int(i)
+
+
+def test_sort_timeout_hook_reports_and_recovers(S):
+    n = 3 * 4096 + 17
+    col = _sort_case("full64", n)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    S.sync_status()
+    S.set_spin_limit(2000)
+    S.set_fault(S.SBH_FAULT_SKIP_PUBLISH)
+    try:
+        S.sort(keys, ptrs)
+        assert S.sync_status() == S.SBH_ETIMEOUT
+    finally:
+        S.set_spin_limit(0)
+        S.set_fault(S.SBH_FAULT_NONE)
+    sk, sp = S.sort(keys, ptrs)
+    assert S.sync_status() == S.SBH_OK
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_sort_scratch_too_small(S):
+    keys, ptrs = S.extract(cuda(_sort_case("full64", 1000)), 0, 1000)
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.SbhError) as e:
+        S.sbh_kpa_sort(keys, ptrs, torch.empty_like(keys), torch.empty_like(ptrs), scratch=small)
+    assert e.value.code == S.SBH_ENOSPACE
+
+
+# ------------------------------------------------------------------ group reduce
+def _sorted_kpa(S, col):
+    n = col.size
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    return S.sort(keys, ptrs)
+
+
+@pytest.mark.parametrize("vbytes", [4, 8])
+@pytest.mark.parametrize("n,space", [(1, 4), (4096, 7), (4097, 1), (100_003, 1000), (100_003, 1 << 40)])
+def test_group_reduce_parity(S, vbytes, n, space):
+    col, _ = gen.tiny_kpa(n, space, seed=n)
+    vals = gen.uniform(7, 7, n, 0, 0, np.uint64 if vbytes == 8 else np.uint32)  # full range: sums wrap
+    sk, sp = _sorted_kpa(S, col)
+    gk, gc, gs = S.group_reduce(sk, sp, cuda(vals))
+    ok, oc, osum = oracle.group_sum_count(host(sk), host(sp), vals)
+    assert same(gk, ok) and same(gc, oc) and same(gs, osum)
+
+
+def test_group_reduce_tumbling_window_and_count_only(S):
+    w = gen.tumbling_window(1_000_000)
+    sk, sp = _sorted_kpa(S, w["keys"])
+    gk, gc, gs = S.group_reduce(sk, sp, cuda(w["vals"]))
+    ok, oc, osum = oracle.group_sum_count(*oracle.sort(*oracle.extract(w["keys"], 0, 1_000_000)), w["vals"])
+    assert same(gk, ok) and same(gc, oc) and same(gs, osum)
+    ck, cc, cs = S.group_reduce(sk, sp, None)
+    assert cs is None and same(ck, ok) and same(cc, oc)
+
+
+def test_group_reduce_heavy_key_spans_tiles_and_cap(S):
+    n = 300_000
+    col = gen.mixed_keys(n, seed=11)
+    col[1000:200_000] = 1  # one key over ~49 tiles
+    vals = gen.uniform(3, 3, n, 0, 0, np.uint64)
+    sk, sp = _sorted_kpa(S, col)
+    gk, gc, gs = S.group_reduce(sk, sp, cuda(vals))
+    ok, oc, osum = oracle.group_sum_count(host(sk), host(sp), vals)
+    assert same(gk, ok) and same(gc, oc) and same(gs, osum)
+    # capacity below the number of keys: the first cap rows, the full count
+    cap = ok.size // 3
+    out_k = torch.zeros(cap, dtype=torch.uint64, device="cuda")
+    out_c = torch.zeros(cap, dtype=torch.uint64, device="cuda")
+    out_s = torch.zeros(cap, dtype=torch.uint64, device="cuda")
+    nk = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    S.sbh_group_reduce(sk, sp, cuda(vals), out_k, out_c, out_s, cap, nk)
+    assert int(host(nk)[0]) == ok.size
+    assert same(out_k, ok[:cap]) and same(out_c, oc[:cap]) and same(out_s, osum[:cap])
+
+
+def test_group_count_mixed_keys_16m(S):
+    n = 16_000_000
+    col = gen.mixed_keys(n)
+    sk, sp = _sorted_kpa(S, col)
+    gk, gc, _ = S.group_reduce(sk, sp, None)
+    ok, oc, _ = oracle.group_sum_count(col, np.arange(n, dtype=np.uint32), None)
+    assert same(gk, ok) and same(gc, oc)
+
+
+# ------------------------------------------------------------------ top-K
+@pytest.mark.parametrize("K", [1, 3, 5, 8])
+@pytest.mark.parametrize("vbytes", [4, 8])
+@pytest.mark.parametrize("n,space,vspan", [(1, 4, 8), (4097, 3, 5), (100_003, 5000, 0), (60_000, 1, 100)])
+def test_topk_parity(S, K, vbytes, n, space, vspan):
+    col, _ = gen.tiny_kpa(n, space, seed=n + K)
+    vals = gen.uniform(4, 4, n, 0, vspan, np.uint64 if vbytes == 8 else np.uint32)
+    sk, sp = _sorted_kpa(S, col)
+    tk, tn, tv, tp = S.topk(sk, sp, cuda(vals), K)
+    ok, onv, ov, op = oracle.topk(host(sk), host(sp), vals, K)
+    assert same(tk, ok) and same(tn, onv) and same(tv, ov) and same(tp, op)
+
+
+def test_topk_batched_window_shape(S):
+    b = gen.batched_windows(8, 4)
+    col, vals = b["keys"], b["vals"]
+    sk, sp = _sorted_kpa(S, col)
+    tk, tn, tv, tp = S.topk(sk, sp, cuda(vals), 3)
+    ok, onv, ov, op = oracle.topk(host(sk), host(sp), vals, 3)
+    assert same(tk, ok) and same(tn, onv) and same(tv, ov) and same(tp, op)
+
+
+# ------------------------------------------------------------------ merge
+@pytest.mark.parametrize("lens", [[5, 0], [4096, 4097], [250_000] * 4, [1, 30_000, 0, 7777, 100_001], [10] * 9])
+def test_merge_parity(S, lens):
+    total = sum(lens)
+    col, _ = gen.tiny_kpa(total, 1 << 12, seed=len(lens))
+    runs_d, runs_h, off = [], [], 0
+    for L in lens:
+        k, p = oracle.sort(*oracle.extract(col, off, L))
+        runs_h.append((k, p))
+        runs_d.append((cuda(k), cuda(p)))
+        off += L
+    mk, mp = S.merge(runs_d)
+    ok, op = oracle.merge(runs_h)
+    assert same(mk, ok) and same(mp, op)
+
+
+# ------------------------------------------------------------------ join
+@pytest.mark.parametrize("nl,nr,space", [(0, 10, 4), (10, 0, 4), (300, 200, 5), (4097, 5000, 1 << 12),
+                                         (100_000, 90_000, 1 << 24)])
+def test_join_parity(S, nl, nr, space):
+    lk, _ = gen.tiny_kpa(nl, space, seed=nl + 1)
+    rk, _ = gen.tiny_kpa(nr, space, seed=nr + 2, stream=3)
+    L = _sorted_kpa(S, lk)
+    R = _sorted_kpa(S, rk)
+    gl, gr = S.join(*L, *R)
+    ol, orr = oracle.join(lk, np.arange(nl, dtype=np.uint32), rk, np.arange(nr, dtype=np.uint32))
+    assert same(gl, ol) and same(gr, orr)
+
+
+def test_join_sliding_window_full_size_and_cap(S):
+    # one 1M-row window of each stream, keys uniform over 2^24
+    s = gen.join_streams(1_250_000)
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    L = S.sort(*S.extract(cuda(lcol), 250_000, 1_000_000))
+    R = S.sort(*S.extract(cuda(rcol), 250_000, 1_000_000))
+    gl, gr = S.join(*L, *R)
+    lk, lp = oracle.sort(*oracle.extract(lcol, 250_000, 1_000_000))
+    rk, rp = oracle.sort(*oracle.extract(rcol, 250_000, 1_000_000))
+    ol, orr = oracle.join(lk, lp, rk, rp)
+    assert same(gl, ol) and same(gr, orr)
+    pins.check_join(lcol, rcol, host(gl), host(gr), pins.join_cardinality(lk, rk))
+    cap = ol.size // 2
+    out_l = torch.zeros(cap, dtype=torch.uint32, device="cuda")
+    out_r = torch.zeros(cap, dtype=torch.uint32, device="cuda")
+    npairs = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    S.sbh_join(*L, *R, out_l, out_r, cap, npairs)
+    assert int(host(npairs)[0]) == ol.size and same(out_l, ol[:cap]) and same(out_r, orr[:cap])
+
+
+# ------------------------------------------------------------------ windows
+def test_window_ranges_parity(S):
+    ts = np.sort(gen.uniform(2, 2, 200_000, 0, 1 << 30, np.uint64))
+    starts = np.sort(gen.uniform(2, 3, 509, 0, 1 << 30, np.uint64))
+    rb, re_ = S.window_ranges(cuda(ts), cuda(starts), 1 << 22)
+    ob, oe = oracle.window_ranges(ts, starts, 1 << 22)
+    assert same(rb, ob) and same(re_, oe)
+    ts32 = np.arange(1_000_000, dtype=np.uint32)
+    starts = np.arange(0, 1_000_000, 250_000, dtype=np.uint64)
+    rb, re_ = S.window_ranges(cuda(ts32), cuda(starts), 1_000_000)
+    ob, oe = oracle.window_ranges(ts32, starts, 1_000_000)
+    assert same(rb, ob) and same(re_, oe)
