@@ -137,61 +137,101 @@ __global__ void __launch_bounds__(kRadix) plan_kernel(const uint32_t* __restrict
 }
 
 // ------------------------------------------------------------------ onesweep
+// Digit of a key in pass `pos` of the plain radix sort.
+struct RadixDigit {
+    int shift;
+    __device__ __forceinline__ uint32_t operator()(uint64_t k) const {
+        return static_cast<uint32_t>(k >> shift) & (kRadix - 1);
+    }
+};
+
 struct SortSmem {
-    union {
-        uint64_t keys[kTile];
-        uint32_t ptrs[kTile];
-    } stage;
+    uint64_t keys[2][kTile];  // double-buffered input tiles, reused to stage
+    uint32_t ptrs[2][kTile];  // the scatter in digit order
     uint32_t whist[kWarps][kRadix + 1];  // +1: sentinel digit of rows past the end
     uint32_t local_start[kRadix];
     uint32_t gbase_rel[kRadix];
     uint32_t scan_tmp[kWarps];
-    uint32_t tile;
+    uint32_t tile_of[2];
+    uint64_t mbar[2];
 };
 
+// One pass of the stable LSD sort.  Persistent CTAs take tile ids in order
+// from a counter.  Each CTA keeps two tiles in flight: while it ranks and
+// scatters one, a bulk copy (TMA) brings the next one into shared memory.
+template <typename DigitFn>
 __global__ void __launch_bounds__(kThreads, 2)
 onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, const uint32_t* __restrict__ gbase,
                 uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter, uint32_t spin_limit,
-                int skip_publish_tile0, uint32_t* __restrict__ status) {
+                int skip_publish_tile0, uint32_t* __restrict__ status, DigitFn digit_of, int bulk_ok) {
     if (!plan->active[pos]) return;
     const int src = plan->src[pos], dst = plan->dst[pos];
     const uint64_t* __restrict__ in_k = buf.keys(src);
     const uint32_t* __restrict__ in_p = buf.ptrs(src);
     uint64_t* __restrict__ out_k = buf.wkeys(dst);
     uint32_t* __restrict__ out_p = buf.wptrs(dst);
-    const int shift = pos * kRadixBits;
     const uint64_t epoch = static_cast<uint64_t>(pos + 1) << 56;
     const uint32_t ntiles = (n + kTile - 1) / kTile;
+    const uint32_t nfull = n / kTile;  // tiles that are loaded with bulk copies (when bulk_ok)
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
 
-    for (;;) {
-        if (tid == 0) sm.tile = atomicAdd(tile_counter + pos, 1u);
-        for (int i = tid; i < kWarps * (kRadix + 1); i += kThreads) (&sm.whist[0][0])[i] = 0;
-        __syncthreads();
-        const uint32_t tile = sm.tile;
-        if (tile >= ntiles) break;
+    auto issue = [&](int b, uint32_t t) {  // thread 0 only
+        if (t < ntiles && bulk_ok && t < nfull) {
+            mbar_expect_tx(&sm.mbar[b], kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
+            bulk_load(sm.keys[b], in_k + (size_t)t * kTile, kTile * sizeof(uint64_t), &sm.mbar[b]);
+            bulk_load(sm.ptrs[b], in_p + (size_t)t * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
+        }
+    };
+
+    uint32_t next_id = 0;
+    if (tid == 0) {
+        mbar_init(&sm.mbar[0], 1);
+        mbar_init(&sm.mbar[1], 1);
+        fence_mbar_init();
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t t = atomicAdd(tile_counter + pos, 1u);
+            sm.tile_of[b] = t;
+            issue(b, t);
+        }
+        next_id = atomicAdd(tile_counter + pos, 1u);
+    }
+    __syncthreads();
+    uint32_t phase[2] = {0u, 0u};
+
+    for (uint32_t it = 0;; ++it) {
+        const int b = it & 1;
+        const uint32_t tile = sm.tile_of[b];
+        if (tile >= ntiles) break;  // ids grow per CTA: the other buffer is past the end too
         const uint32_t base = tile * kTile;
         const uint32_t valid = min(n - base, (uint32_t)kTile);
+        for (int i = tid; i < kWarps * (kRadix + 1); i += kThreads) (&sm.whist[0][0])[i] = 0;
 
-        // ---- load (warp-striped: warp w owns 32*kIpt consecutive rows)
-        uint64_t k[kIpt];
-        uint32_t dig[kIpt];
-        const uint32_t wbase = base + warp * 32 * kIpt + lane;
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t r = wbase + j * 32;
-            const bool ok = r < n;
-            k[j] = ok ? ld_stream(in_k + r) : 0ull;
-            dig[j] = ok ? (static_cast<uint32_t>(k[j] >> shift) & (kRadix - 1)) : kRadix;
+        // ---- wait for the tile (bulk copy) or load it (ragged or unaligned)
+        if (bulk_ok && tile < nfull) {
+            uint32_t polls = 0;
+            while (!mbar_try_wait(&sm.mbar[b], phase[b]))
+                if (wait_expired(polls, spin_limit, status)) break;
+            phase[b] ^= 1u;
+        } else {
+            for (uint32_t s = tid; s < valid; s += kThreads) {
+                sm.keys[b][s] = ld_stream(in_k + base + s);
+                sm.ptrs[b][s] = ld_stream(in_p + base + s);
+            }
         }
+        __syncthreads();
+
+        // ---- registers (warp-striped: warp w owns 32*kIpt consecutive rows)
+        uint64_t k[kIpt];
         uint32_t p[kIpt];
+        const uint32_t wofs = warp * 32 * kIpt + lane;
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
-            const uint32_t r = wbase + j * 32;
-            p[j] = r < n ? ld_stream(in_p + r) : 0u;
+            const uint32_t s = wofs + j * 32;
+            k[j] = sm.keys[b][s];
+            p[j] = sm.ptrs[b][s];
         }
 
         // ---- warp multisplit: rank of each key among equal digits of its warp
@@ -199,15 +239,16 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         const uint32_t lt = lanemask_lt();
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+            const uint32_t d = (wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
-            uint32_t b = 0;
+            uint32_t c = 0;
             if ((int)lane == leader) {
-                b = sm.whist[warp][dig[j]];
-                sm.whist[warp][dig[j]] = b + __popc(peers);
+                c = sm.whist[warp][d];
+                sm.whist[warp][d] = c + __popc(peers);
             }
-            b = __shfl_sync(0xffffffffu, b, leader);
-            rank[j] = b + __popc(peers & lt);
+            c = __shfl_sync(0xffffffffu, c, leader);
+            rank[j] = c + __popc(peers & lt);
             __syncwarp();
         }
         __syncthreads();
@@ -222,11 +263,9 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
             cnt += c;
         }
         uint64_t* rec = lookback + (uint64_t)tile * kRadix + d;
-        const bool publish = !(skip_publish_tile0 && tile == 0);
-        if (publish) st_release(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
+        if (!(skip_publish_tile0 && tile == 0)) st_release(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
 
-        // block exclusive scan of the tile counts over digits
-        uint32_t x = cnt;
+        uint32_t x = cnt;  // block exclusive scan of the tile counts over digits
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -234,19 +273,18 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         }
         if (lane == 31) sm.scan_tmp[warp] = x;
 
-        // decoupled look-back over earlier tiles (bounded)
-        uint64_t excl = 0;
+        uint64_t excl = 0;  // decoupled look-back over earlier tiles (bounded)
         if (tile > 0) {
             uint32_t t = tile - 1;
             uint32_t polls = 0;
             for (;;) {
-                const uint64_t s = ld_acquire(lookback + (uint64_t)t * kRadix + d);
-                if ((s & (3ull << 62)) == 0 || (s & (63ull << 56)) != epoch) {
+                const uint64_t r = ld_acquire(lookback + (uint64_t)t * kRadix + d);
+                if ((r & (3ull << 62)) == 0 || (r & (63ull << 56)) != epoch) {
                     if (wait_expired(polls, spin_limit, status)) break;
                     continue;
                 }
-                excl += s & kValueMask;
-                if ((s & (3ull << 62)) == kFlagPrefix || t == 0) break;
+                excl += r & kValueMask;
+                if ((r & (3ull << 62)) == kFlagPrefix || t == 0) break;
                 --t;
             }
             st_release(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
@@ -260,38 +298,37 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         sm.gbase_rel[d] = gbase[pos * kRadix + d] + static_cast<uint32_t>(excl) - lstart;
         __syncthreads();
 
-        // ---- keys: scatter into shared memory in digit order, then out
-        uint32_t slot[kIpt];
+        // ---- stage keys and ptrs in digit order (the tile's own buffer)
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
-            if (dig[j] < kRadix) {
-                slot[j] = sm.local_start[dig[j]] + sm.whist[warp][dig[j]] + rank[j];
-                sm.stage.keys[slot[j]] = k[j];
+            if (wofs + j * 32 < valid) {
+                const uint32_t dj = digit_of(k[j]);
+                const uint32_t slot = sm.local_start[dj] + sm.whist[warp][dj] + rank[j];
+                sm.keys[b][slot] = k[j];
+                sm.ptrs[b][slot] = p[j];
             }
         }
         __syncthreads();
-        uint32_t gpos[kIpt];
+        // ---- scatter: consecutive slots of one digit go to consecutive rows
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
             const uint32_t s = tid + j * kThreads;
             if (s < valid) {
-                const uint64_t kk = sm.stage.keys[s];
-                gpos[j] = sm.gbase_rel[static_cast<uint32_t>(kk >> shift) & (kRadix - 1)] + s;
-                if (gpos[j] < n) st_stream(out_k + gpos[j], kk);  // false only after an expired wait
+                const uint64_t kk = sm.keys[b][s];
+                const uint32_t g = sm.gbase_rel[digit_of(kk)] + s;
+                if (g < n) {  // false only after an expired wait
+                    out_k[g] = kk;
+                    out_p[g] = sm.ptrs[b][s];
+                }
             }
         }
-        __syncthreads();
-        // ---- ptrs: same slots
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j)
-            if (dig[j] < kRadix) sm.stage.ptrs[slot[j]] = p[j];
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = tid + j * kThreads;
-            if (s < valid && gpos[j] < n) st_stream(out_p + gpos[j], sm.stage.ptrs[s]);
+        __syncthreads();  // the buffer is free again
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            sm.tile_of[b] = next_id;
+            issue(b, next_id);
+            next_id = atomicAdd(tile_counter + pos, 1u);
         }
-        __syncthreads();
     }
 }
 
@@ -359,18 +396,24 @@ int radix_sort_launch(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_
     SBH_LAUNCHED();
     Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
     const size_t smem = sizeof(SortSmem);
-    SBH_CUDA(cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = onesweep_kernel<RadixDigit>;
+    SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kThreads, smem));
+    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)sms * per_sm);
     const uint32_t limit = spin_limit();
-    int fault = take_fault();
+    const int fault = take_fault();
     uint32_t* status = status_word();
+    // bulk copies need 16-byte aligned tile starts in every buffer a pass may read
+    const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
+                          reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     for (int pos = 0; pos < kPositions; ++pos) {
-        SBH_TIMED("sort_onesweep", s, onesweep_kernel<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
-                                                      fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status));
+        SBH_TIMED("sort_onesweep", s,
+                  kern<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
+                                                    fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status,
+                                                    RadixDigit{pos * kRadixBits}, bulk_ok));
         SBH_LAUNCHED();
     }
     unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);

@@ -1,5 +1,4 @@
-// A6 keyed reduction (per-key count and sum) and A7 top-K per key, on a KPA
-// sorted by key.
+// A7 top-K per key, on a KPA sorted by key.
 //
 // One persistent kernel per call.  Each tile of 4096 rows is loaded with
 // coalesced reads, transposed through shared memory so each thread owns 16
@@ -21,17 +20,6 @@ constexpr int kIpt = 16;
 constexpr int kTile = kThreads * kIpt;
 
 // ------------------------------------------------------------ aggregates
-struct SumCount {
-    uint64_t cnt, sum;
-    __device__ __forceinline__ static SumCount identity() { return {0, 0}; }
-    __device__ __forceinline__ void add_row(uint64_t v, uint32_t, int) { cnt += 1; sum += v; }
-    __device__ __forceinline__ void absorb(const SumCount& b, int) { cnt += b.cnt; sum += b.sum; }
-    __device__ __forceinline__ void shfl_up(const SumCount& src, int o) {
-        cnt = __shfl_up_sync(0xffffffffu, src.cnt, o);
-        sum = __shfl_up_sync(0xffffffffu, src.sum, o);
-    }
-};
-
 // The best K (value, ptr) pairs seen, ordered by value descending, then ptr
 // ascending; n of them are valid.
 template <int KMAX>
@@ -156,19 +144,6 @@ __device__ __forceinline__ T load_volatile(const T* src) {
 }
 
 // ------------------------------------------------------------ output sinks
-struct SumSink {
-    uint64_t* keys;
-    uint64_t* counts;
-    uint64_t* sums;
-    uint64_t cap;
-    __device__ __forceinline__ void emit(uint64_t idx, uint64_t key, const SumCount& a) const {
-        if (idx >= cap) return;
-        keys[idx] = key;
-        if (counts) counts[idx] = a.cnt;
-        if (sums) sums[idx] = a.sum;
-    }
-};
-
 template <int KMAX>
 struct TopKSink {
     uint64_t* keys;
@@ -420,42 +395,10 @@ size_t topk_scratch(uint64_t n) {
     return seg_scratch<TopK<8>>(n, &a, &b, &c);
 }
 
-size_t reduce_scratch(uint64_t n) {
-    size_t a, b, c;
-    return seg_scratch<SumCount>(n, &a, &b, &c);
-}
-
 }  // namespace
 }  // namespace sbh
 
 extern "C" {
-
-int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
-                     int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
-                     uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream) {
-    using namespace sbh;
-    clear_error();
-    bool done = false;
-    int rc = scratch_check(d_scratch, scratch_bytes, reduce_scratch(n), &done);
-    if (rc || done) return rc;
-    if (!d_nkeys) { set_error("d_nkeys is NULL"); return SBH_EINVAL; }
-    cudaStream_t s = as_stream(stream);
-    if (n == 0) {
-        SBH_CUDA(cudaMemsetAsync(d_nkeys, 0, sizeof(uint64_t), s));
-        return SBH_OK;
-    }
-    if (!d_keys || (cap && !d_out_keys)) { set_error("null pointer"); return SBH_EINVAL; }
-    const bool with_vals = d_val_col && d_out_sums;
-    if (with_vals && val_bytes != 4 && val_bytes != 8) { set_error("val_bytes must be 4 or 8"); return SBH_EINVAL; }
-    if (with_vals && !d_ptrs) { set_error("d_ptrs is NULL"); return SBH_EINVAL; }
-    SumSink sink{d_out_keys, d_out_counts, with_vals ? d_out_sums : nullptr, cap};
-    if (!with_vals) {
-        return launch_segreduce<SumCount, SumSink, 0>(d_keys, d_ptrs, n, nullptr, sink, 1, d_nkeys, d_scratch, s);
-    }
-    if (val_bytes == 8)
-        return launch_segreduce<SumCount, SumSink, 8>(d_keys, d_ptrs, n, d_val_col, sink, 1, d_nkeys, d_scratch, s);
-    return launch_segreduce<SumCount, SumSink, 4>(d_keys, d_ptrs, n, d_val_col, sink, 1, d_nkeys, d_scratch, s);
-}
 
 int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col, int val_bytes,
              int K, uint64_t* d_out_keys, uint8_t* d_out_nvalid, uint64_t* d_out_vals, uint32_t* d_out_ptrs,
