@@ -117,6 +117,9 @@ __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
     uint64_t v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -143,7 +146,7 @@ __device__ __forceinline__ bool wait_expired(uint32_t& polls, uint32_t limit, ui
         return true;
     }
     if ((polls & 255u) == 0 && status && (ld_relaxed(status) & kStatusTimeout)) return true;
-    __nanosleep(64);
+    if (polls > 8) __nanosleep(32);
     return false;
 }
 

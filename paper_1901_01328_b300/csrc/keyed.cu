@@ -5,12 +5,17 @@
 // of prefix quantities at run boundaries (heads):
 //     count(run) = next head row - head row
 //     sum(run)   = P(next head) - P(head),  P(i) = sum of v over rows < i,
-// exactly, modulo 2^64.  The kernel therefore needs only a plain prefix sum
-// of the gathered values plus the position of the last head, never a
-// segmented reduction.  Tiles of 4096 rows arrive by bulk copy (TMA), two in
-// flight per CTA; tiles chain their running totals with a decoupled
-// look-back (bounded wait); a head writes its key, and the previous run's
-// count and sum, at output index = number of heads before it.
+// exactly, modulo 2^64.  So the reduction needs only a plain prefix sum of the
+// gathered values and the position of the last head -- no segmented scan.
+//
+// Three launches, no waits between CTAs (reduce, then scan):
+//   tile_agg   per tile of 4096 rows: heads, total, last head row, and the
+//              prefix at the last head;
+//   tile_scan  one CTA scans the tile aggregates into tile prefixes;
+//   emit       per tile again: each head writes its key, and the previous
+//              run's count and sum, at output index = number of heads before.
+// Rows are read warp-striped straight from global memory (coalesced), so the
+// kernels need almost no shared memory and many CTAs stay resident.
 #include "common.cuh"
 
 namespace sbh {
@@ -28,7 +33,7 @@ struct Agg {
     uint64_t heads, last_row, sum, last_p;
 };
 
-__device__ __forceinline__ Agg agg_identity() { return {0ull, kNoRow, 0ull, 0ull}; }
+__host__ __device__ __forceinline__ Agg agg_identity() { return {0ull, kNoRow, 0ull, 0ull}; }
 
 __device__ __forceinline__ Agg agg_combine(const Agg& a, const Agg& b) {
     Agg r;
@@ -44,290 +49,234 @@ __device__ __forceinline__ Agg agg_combine(const Agg& a, const Agg& b) {
     return r;
 }
 
-struct TileRec {
-    Agg agg;
-    Agg prefix;
-};
-constexpr uint32_t kRecAgg = 1, kRecPrefix = 2;
-
-__device__ __forceinline__ void store_agg(Agg* dst, const Agg& v) {
-    volatile uint64_t* d = reinterpret_cast<volatile uint64_t*>(dst);
-    d[0] = v.heads;
-    d[1] = v.last_row;
-    d[2] = v.sum;
-    d[3] = v.last_p;
-}
-__device__ __forceinline__ Agg load_agg(const Agg* src) {
-    const volatile uint64_t* s = reinterpret_cast<const volatile uint64_t*>(src);
-    return {s[0], s[1], s[2], s[3]};
-}
-
-struct KeyedSmem {
-    uint64_t keys[2][kTile];
-    uint32_t ptrs[2][kTile];
-    Agg warp_agg[kWarps];
-    Agg warp_prefix[kWarps];
-    uint32_t tile_of[2];
-    uint64_t mbar[2];
-};
-
 __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 
-// kVals: 0 = count only (ptrs and values are not read); 4 or 8 = value bytes.
+// Loads this thread's rows of the tile (warp-striped), their head bits and
+// gathered values.
 template <int kVals>
-__global__ void __launch_bounds__(kThreads, 2)
-keyed_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs, uint32_t n,
-             const void* __restrict__ val_col, uint64_t* __restrict__ out_keys, uint64_t* __restrict__ out_counts,
-             uint64_t* __restrict__ out_sums, uint64_t cap, uint64_t* __restrict__ nkeys_out,
-             uint32_t* __restrict__ flags, TileRec* __restrict__ recs, uint32_t* __restrict__ tile_counter,
-             uint32_t spin_limit, uint32_t* __restrict__ status, int bulk_ok) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    KeyedSmem& sm = *reinterpret_cast<KeyedSmem*>(smem_raw);
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
-    const uint32_t nfull = n / kTile;
-    const uint32_t lt = lanemask_lt();
-    constexpr uint32_t kBytes = kTile * (sizeof(uint64_t) + (kVals ? sizeof(uint32_t) : 0));
-
-    auto issue = [&](int b, uint32_t t) {  // thread 0 only
-        if (t < ntiles && bulk_ok && t < nfull) {
-            mbar_expect_tx(&sm.mbar[b], kBytes);
-            bulk_load(sm.keys[b], keys + (size_t)t * kTile, kTile * sizeof(uint64_t), &sm.mbar[b]);
-            if (kVals) bulk_load(sm.ptrs[b], ptrs + (size_t)t * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
-        }
-    };
-
-    uint32_t next_id = 0;
-    if (tid == 0) {
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
-        fence_mbar_init();
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t t = atomicAdd(tile_counter, 1u);
-            sm.tile_of[b] = t;
-            issue(b, t);
-        }
-        next_id = atomicAdd(tile_counter, 1u);
+__device__ __forceinline__ void load_rows(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs,
+                                          const void* __restrict__ val_col, uint32_t n, uint32_t base, uint32_t wofs,
+                                          uint32_t lane, uint64_t (&k)[kIpt], uint64_t (&v)[kIpt],
+                                          uint32_t& hmask) {
+    const uint32_t first = base + wofs;  // first row of this warp
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        k[j] = r < n ? ld_stream(keys + r) : 0ull;
     }
-    __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
-
-    for (uint32_t it = 0;; ++it) {
-        const int b = it & 1;
-        const uint32_t tile = sm.tile_of[b];
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kTile;
-        const uint32_t valid = min(n - base, (uint32_t)kTile);
-        if (bulk_ok && tile < nfull) {
-            uint32_t polls = 0;
-            while (!mbar_try_wait(&sm.mbar[b], phase[b]))
-                if (wait_expired(polls, spin_limit, status)) break;
-            phase[b] ^= 1u;
-        } else {
-            for (uint32_t s = tid; s < valid; s += kThreads) {
-                sm.keys[b][s] = ld_stream(keys + base + s);
-                if (kVals) sm.ptrs[b][s] = ld_stream(ptrs + base + s);
-            }
-        }
-        __syncthreads();
-
-        // ---- rows of this thread (warp-striped), heads, gathered values
-        const uint32_t wofs = warp * 32 * kIpt;  // first row of this warp in the tile
-        uint64_t k[kIpt];
-        uint64_t v[kIpt];
-        uint32_t hmask = 0;  // bit j: row (j, lane) is a head
+    if (kVals) {
+        uint32_t p[kIpt];
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = wofs + j * 32 + lane;
-            k[j] = s < valid ? sm.keys[b][s] : 0ull;
+            const uint32_t r = first + j * 32 + lane;
+            p[j] = r < n ? ld_stream(ptrs + r) : 0u;
         }
-        {
-            // the row before the warp's first row
-            uint64_t before = 0;
-            bool have_before = true;
-            if (wofs > 0) before = sm.keys[b][wofs - 1];
-            else if (base > 0) before = keys[base - 1];
-            else have_before = false;
-            uint64_t prev31 = before;  // key of lane 31 in the previous item
 #pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                const uint32_t s = wofs + j * 32 + lane;
-                uint64_t pk = shfl_up_u64(k[j], 1);
-                if (lane == 0) pk = prev31;
-                const bool first_row = (j == 0 && lane == 0 && !have_before);
-                if (s < valid && (first_row || pk != k[j])) hmask |= 1u << j;
-                prev31 = shfl_u64(k[j], 31);
-            }
-        }
-        if (kVals) {
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                const uint32_t s = wofs + j * 32 + lane;
-                if (s < valid) {
-                    const uint32_t p = sm.ptrs[b][s];
-                    if (kVals == 8) v[j] = __ldg(static_cast<const unsigned long long*>(val_col) + p);
-                    else v[j] = __ldg(static_cast<const unsigned int*>(val_col) + p);
-                } else {
-                    v[j] = 0;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) v[j] = 0;
-        }
-
-        // ---- warp aggregate (rows in order: item j, then lane)
-        Agg wa = agg_identity();
-        {
-            uint64_t run_sum = 0;  // sum over the warp's rows so far
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
-                uint64_t incl = v[j];
-                if (kVals) {
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint64_t y = shfl_up_u64(incl, o);
-                        if (lane >= (uint32_t)o) incl += y;
-                    }
-                }
-                if (m) {
-                    const int last = 31 - __clz(m);
-                    wa.heads += __popc(m);
-                    wa.last_row = base + wofs + j * 32 + last;
-                    if (kVals) wa.last_p = run_sum + shfl_u64(incl - v[j], last);
-                }
-                if (kVals) run_sum += shfl_u64(incl, 31);
-            }
-            wa.sum = run_sum;
-        }
-        if (lane == 0) sm.warp_agg[warp] = wa;
-        __syncthreads();
-
-        // ---- tile aggregate, publish, look back, per-warp prefixes (thread 0)
-        if (tid == 0) {
-            Agg t = sm.warp_agg[0];
-            for (int w = 1; w < kWarps; ++w) t = agg_combine(t, sm.warp_agg[w]);
-            Agg excl = agg_identity();
-            if (tile == 0) {
-                store_agg(&recs[0].prefix, t);
-                __threadfence();
-                st_release(flags, kRecPrefix);
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t r = first + j * 32 + lane;
+            if (r < n) {
+                if (kVals == 8) v[j] = __ldg(static_cast<const unsigned long long*>(val_col) + p[j]);
+                else v[j] = __ldg(static_cast<const unsigned int*>(val_col) + p[j]);
             } else {
-                store_agg(&recs[tile].agg, t);
-                __threadfence();
-                st_release(flags + tile, kRecAgg);
-                uint32_t j = tile - 1;
-                uint32_t polls = 0;
-                bool have = false;
-                for (;;) {
-                    const uint32_t f = ld_acquire(flags + j);
-                    if (f == 0) {
-                        if (wait_expired(polls, spin_limit, status)) break;
-                        continue;
-                    }
-                    const Agg r = load_agg(f == kRecPrefix ? &recs[j].prefix : &recs[j].agg);
-                    excl = have ? agg_combine(r, excl) : r;
-                    have = true;
-                    if (f == kRecPrefix || j == 0) break;
-                    --j;
-                }
-                store_agg(&recs[tile].prefix, agg_combine(excl, t));
-                __threadfence();
-                st_release(flags + tile, kRecPrefix);
-            }
-            Agg run = excl;
-            for (int w = 0; w < kWarps; ++w) {
-                sm.warp_prefix[w] = run;
-                run = agg_combine(run, sm.warp_agg[w]);
-            }
-            if (base + valid == n) {  // the last tile closes the last run
-                if (run.heads) {
-                    const uint64_t g = run.heads - 1;
-                    if (g < cap) {
-                        if (out_counts) out_counts[g] = n - run.last_row;
-                        if (kVals && out_sums) out_sums[g] = run.sum - run.last_p;
-                    }
-                }
-                *nkeys_out = run.heads;
+                v[j] = 0;
             }
         }
-        __syncthreads();
+    } else {
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) v[j] = 0;
+    }
+    const bool have_before = first > 0;
+    uint64_t prev31 = have_before ? keys[first - 1] : 0ull;  // row before the warp's first row
+    hmask = 0;
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        uint64_t pk = shfl_up_u64(k[j], 1);
+        if (lane == 0) pk = prev31;
+        const bool first_row = (j == 0 && lane == 0 && !have_before);
+        if (r < n && (first_row || pk != k[j])) hmask |= 1u << j;
+        prev31 = shfl_u64(k[j], 31);
+    }
+}
 
-        // ---- emit: each head writes its key and closes the previous run
-        {
-            const Agg wp = sm.warp_prefix[warp];
-            uint64_t heads = wp.heads;          // heads before the current item
-            uint64_t prev_row = wp.last_row;    // last head before the current item
-            uint64_t prev_p = wp.last_p;        // P at that head
-            uint64_t run_p = wp.sum;            // P at the current item's first row
+__device__ __forceinline__ uint64_t warp_incl_sum(uint64_t x, uint32_t lane) {
 #pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
-                uint64_t incl = v[j];
-                if (kVals) {
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = shfl_up_u64(x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+template <int kVals>
+__global__ void __launch_bounds__(kThreads)
+tile_agg_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs, uint32_t n,
+                const void* __restrict__ val_col, Agg* __restrict__ tile_aggs) {
+    __shared__ Agg warp_agg[kWarps];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t base = blockIdx.x * kTile, wofs = warp * 32 * kIpt;
+    uint64_t k[kIpt], v[kIpt];
+    uint32_t hmask;
+    load_rows<kVals>(keys, ptrs, val_col, n, base, wofs, lane, k, v, hmask);
+    Agg wa = agg_identity();
+    uint64_t run_sum = 0;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint64_t y = shfl_up_u64(incl, o);
-                        if (lane >= (uint32_t)o) incl += y;
-                    }
-                }
-                const uint64_t p_row = run_p + incl - v[j];  // P at this row
-                const uint32_t below = m & lt;
-                const int src = below ? 31 - __clz(below) : 0;
-                const uint64_t p_src = kVals ? shfl_u64(p_row, src) : 0ull;
-                if ((m >> lane) & 1u) {
-                    const uint64_t row = base + wofs + j * 32 + lane;
-                    const uint64_t g = heads + __popc(below);
-                    const uint64_t pr = below ? (uint64_t)(base + wofs + j * 32 + src) : prev_row;
-                    const uint64_t pp = below ? p_src : prev_p;
-                    if (g < cap) out_keys[g] = k[j];
-                    if (g >= 1 && g - 1 < cap) {
-                        if (out_counts) out_counts[g - 1] = row - pr;
-                        if (kVals && out_sums) out_sums[g - 1] = p_row - pp;
-                    }
-                }
-                if (m) {
-                    const int last = 31 - __clz(m);
-                    heads += __popc(m);
-                    prev_row = base + wofs + j * 32 + last;
-                    if (kVals) prev_p = shfl_u64(p_row, last);
-                }
-                if (kVals) run_p += shfl_u64(incl, 31);
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
+        uint64_t incl = kVals ? warp_incl_sum(v[j], lane) : 0ull;
+        if (m) {
+            const int last = 31 - __clz(m);
+            wa.heads += __popc(m);
+            wa.last_row = base + wofs + j * 32 + last;
+            if (kVals) wa.last_p = run_sum + shfl_u64(incl - v[j], last);
+        }
+        if (kVals) run_sum += shfl_u64(incl, 31);
+    }
+    wa.sum = run_sum;
+    if (lane == 0) warp_agg[warp] = wa;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Agg t = warp_agg[0];
+        for (int w = 1; w < kWarps; ++w) t = agg_combine(t, warp_agg[w]);
+        tile_aggs[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the tile aggregates (in place), by one CTA.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(Agg* __restrict__ aggs, uint32_t ntiles) {
+    __shared__ Agg warp_tot[32];
+    __shared__ Agg carry;
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) carry = agg_identity();
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const Agg mine = i < ntiles ? aggs[i] : agg_identity();
+        Agg inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Agg y;
+            y.heads = shfl_up_u64(inc.heads, o);
+            y.last_row = shfl_up_u64(inc.last_row, o);
+            y.sum = shfl_up_u64(inc.sum, o);
+            y.last_p = shfl_up_u64(inc.last_p, o);
+            if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
+        }
+        if (lane == 31) warp_tot[warp] = inc;
+        __syncthreads();
+        Agg before = carry;
+        for (uint32_t w = 0; w < warp; ++w) before = agg_combine(before, warp_tot[w]);
+        Agg excl;
+        excl.heads = shfl_up_u64(inc.heads, 1);
+        excl.last_row = shfl_up_u64(inc.last_row, 1);
+        excl.sum = shfl_up_u64(inc.sum, 1);
+        excl.last_p = shfl_up_u64(inc.last_p, 1);
+        if (lane == 0) excl = agg_identity();
+        if (i < ntiles) aggs[i] = agg_combine(before, excl);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = agg_combine(before, inc);
+        __syncthreads();
+    }
+}
+
+template <int kVals>
+__global__ void __launch_bounds__(kThreads)
+emit_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs, uint32_t n,
+            const void* __restrict__ val_col, const Agg* __restrict__ tile_prefix, uint32_t ntiles,
+            uint64_t* __restrict__ out_keys, uint64_t* __restrict__ out_counts, uint64_t* __restrict__ out_sums,
+            uint64_t cap, uint64_t* __restrict__ nkeys_out) {
+    __shared__ Agg warp_agg[kWarps];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t base = blockIdx.x * kTile, wofs = warp * 32 * kIpt;
+    const uint32_t lt = lanemask_lt();
+    uint64_t k[kIpt], v[kIpt];
+    uint32_t hmask;
+    load_rows<kVals>(keys, ptrs, val_col, n, base, wofs, lane, k, v, hmask);
+
+    // warp aggregates again, to place each warp after the ones before it
+    {
+        Agg wa = agg_identity();
+        uint64_t run_sum = 0;
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
+            uint64_t incl = kVals ? warp_incl_sum(v[j], lane) : 0ull;
+            if (m) {
+                const int last = 31 - __clz(m);
+                wa.heads += __popc(m);
+                wa.last_row = base + wofs + j * 32 + last;
+                if (kVals) wa.last_p = run_sum + shfl_u64(incl - v[j], last);
+            }
+            if (kVals) run_sum += shfl_u64(incl, 31);
+        }
+        wa.sum = run_sum;
+        if (lane == 0) warp_agg[warp] = wa;
+    }
+    __syncthreads();
+    Agg wp = tile_prefix[blockIdx.x];
+    for (uint32_t w = 0; w < warp; ++w) wp = agg_combine(wp, warp_agg[w]);
+
+    uint64_t heads = wp.heads;        // heads before the current item
+    uint64_t prev_row = wp.last_row;  // last head before the current item
+    uint64_t prev_p = wp.last_p;      // P at that head
+    uint64_t run_p = wp.sum;          // P at the current item's first row
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
+        const uint64_t incl = kVals ? warp_incl_sum(v[j], lane) : 0ull;
+        const uint64_t p_row = run_p + incl - v[j];  // P at this row
+        const uint32_t below = m & lt;
+        const int src = below ? 31 - __clz(below) : 0;
+        const uint64_t p_src = kVals ? shfl_u64(p_row, src) : 0ull;
+        if ((m >> lane) & 1u) {
+            const uint64_t row = base + wofs + j * 32 + lane;
+            const uint64_t g = heads + __popc(below);
+            const uint64_t pr = below ? (uint64_t)(base + wofs + j * 32 + src) : prev_row;
+            const uint64_t pp = below ? p_src : prev_p;
+            if (g < cap) out_keys[g] = k[j];
+            if (g >= 1 && g - 1 < cap) {
+                if (out_counts) out_counts[g - 1] = row - pr;
+                if (kVals && out_sums) out_sums[g - 1] = p_row - pp;
             }
         }
-        __syncthreads();  // the buffer is free again
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            sm.tile_of[b] = next_id;
-            issue(b, next_id);
-            next_id = atomicAdd(tile_counter, 1u);
+        if (m) {
+            const int last = 31 - __clz(m);
+            heads += __popc(m);
+            prev_row = base + wofs + j * 32 + last;
+            if (kVals) prev_p = shfl_u64(p_row, last);
         }
+        if (kVals) run_p += shfl_u64(incl, 31);
+    }
+    // the thread holding the last row closes the last run
+    if (blockIdx.x == ntiles - 1 && warp == kWarps - 1 && lane == 31) {
+        // heads/prev_row/prev_p/run_p now describe everything up to the tile end
+        const uint64_t total_heads = heads;
+        if (total_heads) {
+            const uint64_t g = total_heads - 1;
+            if (g < cap) {
+                if (out_counts) out_counts[g] = n - prev_row;
+                if (kVals && out_sums) out_sums[g] = run_p - prev_p;
+            }
+        }
+        *nkeys_out = total_heads;
     }
 }
 
 template <int kVals>
 int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* vals, uint64_t* ok,
                  uint64_t* oc, uint64_t* os, uint64_t cap, uint64_t* nkeys, void* scratch, cudaStream_t s) {
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     Carver c(scratch);
-    uint32_t* counter = c.take<uint32_t>(1);
-    uint32_t* flags = c.take<uint32_t>(ntiles);
-    const size_t zero_bytes = c.off;
-    TileRec* recs = c.take<TileRec>(ntiles);
-    SBH_CUDA(cudaMemsetAsync(counter, 0, zero_bytes, s));
-    auto kern = keyed_kernel<kVals>;
-    const size_t smem = sizeof(KeyedSmem);
-    SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)num_sms() * per_sm);
-    const int bulk_ok = ((reinterpret_cast<uintptr_t>(keys) | (kVals ? reinterpret_cast<uintptr_t>(ptrs) : 0)) & 15) == 0;
-    SBH_TIMED("keyed_reduce", s,
-              kern<<<grid, kThreads, smem, s>>>(keys, ptrs, (uint32_t)n, vals, ok, oc, os, cap, nkeys, flags, recs,
-                                                counter, spin_limit(), status_word(), bulk_ok));
+    Agg* aggs = c.take<Agg>(ntiles);
+    SBH_TIMED("keyed_tile_agg", s,
+              tile_agg_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs));
+    SBH_LAUNCHED();
+    SBH_TIMED("keyed_tile_scan", s, tile_scan_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
+    SBH_LAUNCHED();
+    SBH_TIMED("keyed_emit", s,
+              emit_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs, ntiles, ok, oc, os,
+                                                             cap, nkeys));
     SBH_LAUNCHED();
     return SBH_OK;
 }
@@ -335,9 +284,7 @@ int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const v
 size_t keyed_scratch(uint64_t n) {
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     Carver c(nullptr);
-    c.take<uint32_t>(1);
-    c.take<uint32_t>(ntiles);
-    c.take<TileRec>(ntiles);
+    c.take<Agg>(ntiles);
     return c.bytes();
 }
 

@@ -55,19 +55,15 @@ struct Buffers {
 };
 
 // ------------------------------------------------------------------ upsweep
-__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                      uint32_t* __restrict__ ghist) {
-    __shared__ uint32_t h[kPositions * kRadix];
-    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    // Equal digits in a row are counted in registers first: skewed keys (a
-    // heavy key, constant high bytes) would otherwise serialise on one bin.
+// Equal digits in a row are counted in registers first: skewed keys (a heavy
+// key, constant high bytes) would otherwise serialise on one bin.
+struct RunCounter {
     uint32_t last[kPositions], run[kPositions];
+    __device__ __forceinline__ RunCounter() {
 #pragma unroll
-    for (int p = 0; p < kPositions; ++p) { last[p] = 0; run[p] = 0; }
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = ld_stream(keys + i);
+        for (int p = 0; p < kPositions; ++p) { last[p] = 0; run[p] = 0; }
+    }
+    __device__ __forceinline__ void add(uint64_t k, uint32_t* h) {
 #pragma unroll
         for (int p = 0; p < kPositions; ++p) {
             const uint32_t d = static_cast<uint32_t>(k >> (p * kRadixBits)) & (kRadix - 1);
@@ -80,9 +76,38 @@ __global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict
             }
         }
     }
+    __device__ __forceinline__ void flush(uint32_t* h) {
 #pragma unroll
-    for (int p = 0; p < kPositions; ++p)
-        if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
+        for (int p = 0; p < kPositions; ++p)
+            if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
+    }
+};
+
+__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                      uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[kPositions * kRadix];
+    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    RunCounter rc;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+        // four keys per step with two 16-byte loads issued together
+        const uint32_t nq = n / 4;
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
+        for (uint32_t i = tid; i < nq; i += nthreads) {
+            const ulonglong2 a = __ldcs(q + 2 * i);
+            const ulonglong2 b = __ldcs(q + 2 * i + 1);
+            rc.add(a.x, h);
+            rc.add(a.y, h);
+            rc.add(b.x, h);
+            rc.add(b.y, h);
+        }
+        done = nq * 4;
+    }
+    for (uint32_t i = done + tid; i < n; i += nthreads) rc.add(ld_stream(keys + i), h);
+    rc.flush(h);
     __syncthreads();
     for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x)
         if (h[i]) atomicAdd(&ghist[i], h[i]);
@@ -186,6 +211,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         }
     };
 
+    const uint32_t my_gbase = gbase[pos * kRadix + tid];  // global offset of digit tid
     uint32_t next_id = 0;
     if (tid == 0) {
         mbar_init(&sm.mbar[0], 1);
@@ -234,7 +260,10 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
             p[j] = sm.ptrs[b][s];
         }
 
-        // ---- warp multisplit: rank of each key among equal digits of its warp
+        // ---- warp multisplit: rank of each key among equal digits of its warp.
+        // The leader of each group of equal digits adds the group size to the
+        // warp's counter; atomics of one warp to one address take effect in
+        // issue order, so items keep their (item, lane) order.
         uint32_t rank[kIpt];
         const uint32_t lt = lanemask_lt();
 #pragma unroll
@@ -243,13 +272,8 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
             uint32_t c = 0;
-            if ((int)lane == leader) {
-                c = sm.whist[warp][d];
-                sm.whist[warp][d] = c + __popc(peers);
-            }
-            c = __shfl_sync(0xffffffffu, c, leader);
-            rank[j] = c + __popc(peers & lt);
-            __syncwarp();
+            if ((int)lane == leader) c = atomicAdd(&sm.whist[warp][d], (uint32_t)__popc(peers));
+            rank[j] = __popc(peers & lt) + __shfl_sync(0xffffffffu, c, leader);
         }
         __syncthreads();
 
@@ -262,8 +286,10 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
             sm.whist[w][d] = cnt;
             cnt += c;
         }
+        // Records carry their value in the same word, so relaxed accesses
+        // suffice: no other data is published through them.
         uint64_t* rec = lookback + (uint64_t)tile * kRadix + d;
-        if (!(skip_publish_tile0 && tile == 0)) st_release(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
+        if (!(skip_publish_tile0 && tile == 0)) st_relaxed(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
 
         uint32_t x = cnt;  // block exclusive scan of the tile counts over digits
 #pragma unroll
@@ -278,7 +304,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
             uint32_t t = tile - 1;
             uint32_t polls = 0;
             for (;;) {
-                const uint64_t r = ld_acquire(lookback + (uint64_t)t * kRadix + d);
+                const uint64_t r = ld_relaxed(lookback + (uint64_t)t * kRadix + d);
                 if ((r & (3ull << 62)) == 0 || (r & (63ull << 56)) != epoch) {
                     if (wait_expired(polls, spin_limit, status)) break;
                     continue;
@@ -287,7 +313,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
                 if ((r & (3ull << 62)) == kFlagPrefix || t == 0) break;
                 --t;
             }
-            st_release(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
+            st_relaxed(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
         }
         __syncthreads();
         uint32_t before = 0;
@@ -295,7 +321,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         for (int w = 0; w < kWarps; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
         const uint32_t lstart = before + x - cnt;
         sm.local_start[d] = lstart;
-        sm.gbase_rel[d] = gbase[pos * kRadix + d] + static_cast<uint32_t>(excl) - lstart;
+        sm.gbase_rel[d] = my_gbase + static_cast<uint32_t>(excl) - lstart;
         __syncthreads();
 
         // ---- stage keys and ptrs in digit order (the tile's own buffer)
@@ -389,7 +415,7 @@ int radix_sort_launch(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_
     SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
-    unsigned up_blocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
+    unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
     SBH_TIMED("sort_upsweep", s, upsweep_kernel<<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist));
     SBH_LAUNCHED();
     SBH_TIMED("sort_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));

@@ -85,3 +85,55 @@ def test_training_learns_uniform_cdf():
     assert losses[-1] < 0.1 * losses[0]
     y, _ = mlp.forward(p, np.linspace(0.05, 0.95, 19))
     assert np.max(np.abs(y - np.linspace(0.05, 0.95, 19))) < 0.05
+
+
+# ------------------------------------------------------------------ learned partition data
+from oracle import learned  # noqa: E402
+
+
+def test_cells_bit_definition():
+    keys = np.array([0, 1, 2, 3, 1023, 1024, 1025, 2047, 2048, (1 << 40) + (5 << 30), (1 << 64) - 1], dtype=np.uint64)
+    c = learned.cell_of(keys)
+    # key 1: m = 0 -> cell 1; key 2: m = 1, next bits 0 -> 1 + 1024; key 3: next bit 1 -> bits '1000000000' = 512
+    assert c[0] == 0 and c[1] == 1 and c[2] == 1 + 1024 and c[3] == 1 + 1024 + 512
+    assert c[4] == 1 + 1024 * 9 + 1022       # 1023 = 2^10 - 1: m = 9, bits below = 1111111110 (zero-padded)
+    assert c[5] == 1 + 1024 * 10 and c[6] == 1 + 1024 * 10 + 1 and c[7] == 1 + 1024 * 10 + 1023
+    assert c[8] == 1 + 1024 * 11 and c[9] == 1 + 1024 * 40 + 5
+    assert c[10] == learned.NCELL - 1
+    # exact cells hold one key value: distinct keys below 2^11 never share a cell
+    small = np.arange(0, 2048, dtype=np.uint64)
+    assert np.unique(learned.cell_of(small)).size == 2048
+    assert all(learned.cell_is_exact(int(x)) for x in learned.cell_of(small))
+    assert not learned.cell_is_exact(1 + 1024 * 11)
+    # cells are non-decreasing in the key
+    ks = np.sort(gen.mixed_keys(5000, seed=9))
+    assert np.all(np.diff(learned.cell_of(ks)) >= 0)
+
+
+def test_heavy_cells_threshold():
+    # 1000 samples standing for 100000 rows; capacity 2000 -> heavy above 1000 rows, i.e. > 10 samples
+    s = np.concatenate([np.full(11, 7), np.full(10, 9), np.full(50, 5000), np.arange(100, 1029)]).astype(np.uint64)
+    h = learned.heavy_cells(s, 100_000, 2000)
+    c = learned.cell_of(np.array([7, 9, 5000], dtype=np.uint64))
+    assert h[c[0]] and not h[c[1]]
+    assert not h[c[2]]  # 5000 is not in an exact cell
+    assert h.sum() == 1
+
+
+def test_training_set_is_a_permutation_with_cdf_targets():
+    s = np.array([5, 5, 1, 9, 7, 7, 7, 3], dtype=np.uint64)
+    x, t = learned.training_set(s, 8, 1 << 20)  # huge capacity: nothing is heavy
+    nh = np.sort(s)
+    assert sorted(x.tolist()) == sorted(mlp.feature(nh).tolist())
+    # targets of key 7 (three copies, four smaller samples): (4 + 7) / 16
+    xt = dict(zip(x.tolist(), t.tolist()))
+    assert xt[float(mlp.feature(np.array([7], np.uint64))[0])] == 11 / 16
+    assert xt[float(mlp.feature(np.array([1], np.uint64))[0])] == 1 / 16
+    P = learned.stride_multiplier(8)
+    assert np.gcd(P, 8) == 1
+    # heavy keys leave the set: with 1000 rows per sample and capacity 3000, a key
+    # with two or more samples (>= 2000 rows > 1500) is heavy: 7 and 5 leave
+    x2, t2 = learned.training_set(s, 8000, 3000)
+    assert x2.size == 3
+    # the targets are recomputed over the remaining samples {1, 3, 9}
+    assert sorted(t2.tolist()) == [1 / 6, 3 / 6, 5 / 6]
