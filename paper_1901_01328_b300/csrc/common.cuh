@@ -7,7 +7,7 @@
 #include <cstdarg>
 #include <cstddef>
 
-#include "../../include/sbh.h"
+#include "sbh.h"
 
 namespace sbh {
 
