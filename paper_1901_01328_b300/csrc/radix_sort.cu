@@ -1,454 +1,10 @@
-// A3 Sort: stable LSD radix sort of a KPA (uint64 key, uint32 ptr), 8-bit
-// digits, one onesweep kernel per digit position that is not constant.
-//
-// Per call:
-//   upsweep   one read of the keys builds the 256-bin histogram of all eight
-//             digit positions.
-//   plan      exclusive scan of each histogram (global digit offsets); a
-//             position whose digit is the same for every key is skipped; the
-//             ping-pong buffer of each active pass is chosen so that the last
-//             one writes the output.
-//   onesweep  per active position: persistent CTAs take tiles in order from
-//             a counter; each ranks its tile with a warp multisplit
-//             (__match_any_sync), publishes its per-digit counts, looks back
-//             over earlier tiles for its global offsets (decoupled look-back,
-//             bounded wait) and scatters keys and ptrs through shared memory.
-//   copy      only when no pass ran (or an in-place sort ends in the
-//             temporary buffer).
-#include "common.cuh"
+// A3 Sort: stable LSD radix sort of a KPA (uint64 key, uint32 ptr) by the
+// key, 8-bit digits; the passes are described in radix_core.cuh.
+#include "radix_core.cuh"
 
 namespace sbh {
-namespace {
 
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kPositions = 64 / kRadixBits;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kIpt = 16;                    // keys per thread
-constexpr int kTile = kThreads * kIpt;      // keys per tile
-
-// look-back record: [63:62] flag, [61:56] epoch (pass + 1), [55:0] count
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagPrefix = 2ull << 62;
-constexpr uint64_t kValueMask = (1ull << 56) - 1;
-
-struct Plan {
-    int active[kPositions];
-    int src[kPositions];  // 0 = input, 1 = temporary, 2 = output
-    int dst[kPositions];
-    int copy_src;         // -1 = no copy, else the buffer to copy to the output
-    int npasses;
-};
-
-struct Buffers {
-    const uint64_t* in_k;
-    const uint32_t* in_p;
-    uint64_t* tmp_k;
-    uint32_t* tmp_p;
-    uint64_t* out_k;
-    uint32_t* out_p;
-    __device__ __forceinline__ const uint64_t* keys(int sel) const { return sel == 0 ? in_k : (sel == 1 ? tmp_k : out_k); }
-    __device__ __forceinline__ const uint32_t* ptrs(int sel) const { return sel == 0 ? in_p : (sel == 1 ? tmp_p : out_p); }
-    __device__ __forceinline__ uint64_t* wkeys(int sel) const { return sel == 1 ? tmp_k : out_k; }
-    __device__ __forceinline__ uint32_t* wptrs(int sel) const { return sel == 1 ? tmp_p : out_p; }
-};
-
-// ------------------------------------------------------------------ upsweep
-// Equal digits in a row are counted in registers first: skewed keys (a heavy
-// key, constant high bytes) would otherwise serialise on one bin.
-struct RunCounter {
-    uint32_t last[kPositions], run[kPositions];
-    __device__ __forceinline__ RunCounter() {
-#pragma unroll
-        for (int p = 0; p < kPositions; ++p) { last[p] = 0; run[p] = 0; }
-    }
-    __device__ __forceinline__ void add(uint64_t k, uint32_t* h) {
-#pragma unroll
-        for (int p = 0; p < kPositions; ++p) {
-            const uint32_t d = static_cast<uint32_t>(k >> (p * kRadixBits)) & (kRadix - 1);
-            if (d == last[p]) {
-                ++run[p];
-            } else {
-                if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
-                last[p] = d;
-                run[p] = 1;
-            }
-        }
-    }
-    __device__ __forceinline__ void flush(uint32_t* h) {
-#pragma unroll
-        for (int p = 0; p < kPositions; ++p)
-            if (run[p]) atomicAdd(&h[p * kRadix + last[p]], run[p]);
-    }
-};
-
-__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                      uint32_t* __restrict__ ghist) {
-    __shared__ uint32_t h[kPositions * kRadix];
-    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    RunCounter rc;
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t done = 0;
-    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
-        // four keys per step with two 16-byte loads issued together
-        const uint32_t nq = n / 4;
-        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
-        for (uint32_t i = tid; i < nq; i += nthreads) {
-            const ulonglong2 a = __ldcs(q + 2 * i);
-            const ulonglong2 b = __ldcs(q + 2 * i + 1);
-            rc.add(a.x, h);
-            rc.add(a.y, h);
-            rc.add(b.x, h);
-            rc.add(b.y, h);
-        }
-        done = nq * 4;
-    }
-    for (uint32_t i = done + tid; i < n; i += nthreads) rc.add(ld_stream(keys + i), h);
-    rc.flush(h);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
-}
-
-// ------------------------------------------------------------------ plan
-__global__ void __launch_bounds__(kRadix) plan_kernel(const uint32_t* __restrict__ ghist, uint32_t n,
-                                                      uint32_t* __restrict__ gbase, Plan* __restrict__ plan,
-                                                      int in_place) {
-    __shared__ uint32_t warp_sums[kRadix / 32];
-    __shared__ int s_active[kPositions];
-    const int d = threadIdx.x;
-    for (int p = 0; p < kPositions; ++p) {
-        const uint32_t c = ghist[p * kRadix + d];
-        const int constant = __syncthreads_or(c == n);
-        // block exclusive scan of c over the 256 digits
-        uint32_t x = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane_id() >= (uint32_t)o) x += y;
-        }
-        if (lane_id() == 31) warp_sums[d / 32] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < d / 32; ++w) before += warp_sums[w];
-        gbase[p * kRadix + d] = before + x - c;
-        if (d == 0) s_active[p] = !constant;
-        __syncthreads();
-    }
-    if (d == 0) {
-        Plan pl;
-        int a = 0;
-        for (int p = 0; p < kPositions; ++p) a += s_active[p];
-        int i = 0, prev = 0;
-        for (int p = 0; p < kPositions; ++p) {
-            pl.active[p] = s_active[p];
-            pl.src[p] = pl.dst[p] = 0;
-            if (!s_active[p]) continue;
-            int dst;
-            if (in_place) dst = (i % 2 == 0) ? 1 : 2;
-            else dst = ((a - 1 - i) % 2 == 0) ? 2 : 1;
-            pl.src[p] = (i == 0) ? 0 : prev;
-            pl.dst[p] = dst;
-            prev = dst;
-            ++i;
-        }
-        if (a == 0) pl.copy_src = in_place ? -1 : 0;
-        else pl.copy_src = (prev == 2) ? -1 : prev;
-        pl.npasses = a;
-        *plan = pl;
-    }
-}
-
-// ------------------------------------------------------------------ onesweep
-// Digit of a key in pass `pos` of the plain radix sort.
-struct RadixDigit {
-    int shift;
-    __device__ __forceinline__ uint32_t operator()(uint64_t k) const {
-        return static_cast<uint32_t>(k >> shift) & (kRadix - 1);
-    }
-};
-
-struct SortSmem {
-    uint64_t keys[2][kTile];  // double-buffered input tiles, reused to stage
-    uint32_t ptrs[2][kTile];  // the scatter in digit order
-    uint32_t whist[kWarps][kRadix + 1];  // +1: sentinel digit of rows past the end
-    uint32_t local_start[kRadix];
-    uint32_t gbase_rel[kRadix];
-    uint32_t scan_tmp[kWarps];
-    uint32_t tile_of[2];
-    uint64_t mbar[2];
-};
-
-// One pass of the stable LSD sort.  Persistent CTAs take tile ids in order
-// from a counter.  Each CTA keeps two tiles in flight: while it ranks and
-// scatters one, a bulk copy (TMA) brings the next one into shared memory.
-template <typename DigitFn>
-__global__ void __launch_bounds__(kThreads, 2)
-onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, const uint32_t* __restrict__ gbase,
-                uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter, uint32_t spin_limit,
-                int skip_publish_tile0, uint32_t* __restrict__ status, DigitFn digit_of, int bulk_ok) {
-    if (!plan->active[pos]) return;
-    const int src = plan->src[pos], dst = plan->dst[pos];
-    const uint64_t* __restrict__ in_k = buf.keys(src);
-    const uint32_t* __restrict__ in_p = buf.ptrs(src);
-    uint64_t* __restrict__ out_k = buf.wkeys(dst);
-    uint32_t* __restrict__ out_p = buf.wptrs(dst);
-    const uint64_t epoch = static_cast<uint64_t>(pos + 1) << 56;
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
-    const uint32_t nfull = n / kTile;  // tiles that are loaded with bulk copies (when bulk_ok)
-
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-
-    auto issue = [&](int b, uint32_t t) {  // thread 0 only
-        if (t < ntiles && bulk_ok && t < nfull) {
-            mbar_expect_tx(&sm.mbar[b], kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
-            bulk_load(sm.keys[b], in_k + (size_t)t * kTile, kTile * sizeof(uint64_t), &sm.mbar[b]);
-            bulk_load(sm.ptrs[b], in_p + (size_t)t * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
-        }
-    };
-
-    const uint32_t my_gbase = gbase[pos * kRadix + tid];  // global offset of digit tid
-    uint32_t next_id = 0;
-    if (tid == 0) {
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
-        fence_mbar_init();
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t t = atomicAdd(tile_counter + pos, 1u);
-            sm.tile_of[b] = t;
-            issue(b, t);
-        }
-        next_id = atomicAdd(tile_counter + pos, 1u);
-    }
-    __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
-
-    for (uint32_t it = 0;; ++it) {
-        const int b = it & 1;
-        const uint32_t tile = sm.tile_of[b];
-        if (tile >= ntiles) break;  // ids grow per CTA: the other buffer is past the end too
-        const uint32_t base = tile * kTile;
-        const uint32_t valid = min(n - base, (uint32_t)kTile);
-        for (int i = tid; i < kWarps * (kRadix + 1); i += kThreads) (&sm.whist[0][0])[i] = 0;
-
-        // ---- wait for the tile (bulk copy) or load it (ragged or unaligned)
-        if (bulk_ok && tile < nfull) {
-            uint32_t polls = 0;
-            while (!mbar_try_wait(&sm.mbar[b], phase[b]))
-                if (wait_expired(polls, spin_limit, status)) break;
-            phase[b] ^= 1u;
-        } else {
-            for (uint32_t s = tid; s < valid; s += kThreads) {
-                sm.keys[b][s] = ld_stream(in_k + base + s);
-                sm.ptrs[b][s] = ld_stream(in_p + base + s);
-            }
-        }
-        __syncthreads();
-
-        // ---- registers (warp-striped: warp w owns 32*kIpt consecutive rows)
-        uint64_t k[kIpt];
-        uint32_t p[kIpt];
-        const uint32_t wofs = warp * 32 * kIpt + lane;
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = wofs + j * 32;
-            k[j] = sm.keys[b][s];
-            p[j] = sm.ptrs[b][s];
-        }
-
-        // ---- warp multisplit: rank of each key among equal digits of its warp.
-        // The leader of each group of equal digits adds the group size to the
-        // warp's counter; atomics of one warp to one address take effect in
-        // issue order, so items keep their (item, lane) order.
-        uint32_t rank[kIpt];
-        const uint32_t lt = lanemask_lt();
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t d = (wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t c = 0;
-            if ((int)lane == leader) c = atomicAdd(&sm.whist[warp][d], (uint32_t)__popc(peers));
-            rank[j] = __popc(peers & lt) + __shfl_sync(0xffffffffu, c, leader);
-        }
-        __syncthreads();
-
-        // ---- per digit (thread = digit): warp offsets, tile count, publish
-        const uint32_t d = tid;
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = sm.whist[w][d];
-            sm.whist[w][d] = cnt;
-            cnt += c;
-        }
-        // Records carry their value in the same word, so relaxed accesses
-        // suffice: no other data is published through them.
-        uint64_t* rec = lookback + (uint64_t)tile * kRadix + d;
-        if (!(skip_publish_tile0 && tile == 0)) st_relaxed(rec, (tile == 0 ? kFlagPrefix : kFlagAgg) | epoch | cnt);
-
-        uint32_t x = cnt;  // block exclusive scan of the tile counts over digits
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= (uint32_t)o) x += y;
-        }
-        if (lane == 31) sm.scan_tmp[warp] = x;
-
-        uint64_t excl = 0;  // decoupled look-back over earlier tiles (bounded)
-        if (tile > 0) {
-            uint32_t t = tile - 1;
-            uint32_t polls = 0;
-            for (;;) {
-                const uint64_t r = ld_relaxed(lookback + (uint64_t)t * kRadix + d);
-                if ((r & (3ull << 62)) == 0 || (r & (63ull << 56)) != epoch) {
-                    if (wait_expired(polls, spin_limit, status)) break;
-                    continue;
-                }
-                excl += r & kValueMask;
-                if ((r & (3ull << 62)) == kFlagPrefix || t == 0) break;
-                --t;
-            }
-            st_relaxed(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
-        }
-        __syncthreads();
-        uint32_t before = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
-        const uint32_t lstart = before + x - cnt;
-        sm.local_start[d] = lstart;
-        sm.gbase_rel[d] = my_gbase + static_cast<uint32_t>(excl) - lstart;
-        __syncthreads();
-
-        // ---- stage keys and ptrs in digit order (the tile's own buffer)
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            if (wofs + j * 32 < valid) {
-                const uint32_t dj = digit_of(k[j]);
-                const uint32_t slot = sm.local_start[dj] + sm.whist[warp][dj] + rank[j];
-                sm.keys[b][slot] = k[j];
-                sm.ptrs[b][slot] = p[j];
-            }
-        }
-        __syncthreads();
-        // ---- scatter: consecutive slots of one digit go to consecutive rows
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = tid + j * kThreads;
-            if (s < valid) {
-                const uint64_t kk = sm.keys[b][s];
-                const uint32_t g = sm.gbase_rel[digit_of(kk)] + s;
-                if (g < n) {  // false only after an expired wait
-                    out_k[g] = kk;
-                    out_p[g] = sm.ptrs[b][s];
-                }
-            }
-        }
-        __syncthreads();  // the buffer is free again
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            sm.tile_of[b] = next_id;
-            issue(b, next_id);
-            next_id = atomicAdd(tile_counter + pos, 1u);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ copy
-__global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ plan) {
-    const int sel = plan->copy_src;
-    if (sel < 0) return;
-    const uint64_t* __restrict__ sk = buf.keys(sel);
-    const uint32_t* __restrict__ sp = buf.ptrs(sel);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        buf.out_k[i] = sk[i];
-        buf.out_p[i] = sp[i];
-    }
-}
-
-struct SortScratch {
-    uint64_t* tmp_k;
-    uint32_t* tmp_p;
-    uint32_t* hist;        // kPositions * kRadix   (zeroed)
-    uint32_t* counters;    // kPositions            (zeroed)
-    uint64_t* lookback;    // ntiles * kRadix       (zeroed)
-    uint32_t* gbase;       // kPositions * kRadix
-    Plan* plan;
-    char* zero_begin;
-    size_t zero_bytes;
-    size_t total;
-};
-
-SortScratch carve(void* scratch, uint64_t n) {
-    Carver c(scratch);
-    SortScratch s;
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    s.tmp_k = c.take<uint64_t>(n);
-    s.tmp_p = c.take<uint32_t>(n);
-    s.gbase = c.take<uint32_t>(kPositions * kRadix);
-    s.plan = c.take<Plan>(1);
-    // zeroed region: histogram, tile counters, look-back records
-    s.hist = c.take<uint32_t>(kPositions * kRadix);
-    const size_t zb = c.off - kPositions * kRadix * sizeof(uint32_t);
-    s.counters = c.take<uint32_t>(kPositions);
-    s.lookback = c.take<uint64_t>(ntiles * kRadix);
-    s.zero_begin = reinterpret_cast<char*>(s.hist);
-    s.zero_bytes = c.off - zb;
-    s.total = c.bytes();
-    return s;
-}
-
-}  // namespace
-
-// Shared with the learned sort: a full radix sort on a caller stream.
-int radix_sort_launch(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
-                      void* scratch, cudaStream_t s) {
-    if (n == 0) return SBH_OK;
-    const int in_place = (in_k == out_k);
-    if (in_place != (in_p == out_p)) { set_error("an in-place sort needs both keys and ptrs aliased"); return SBH_EINVAL; }
-    SortScratch sc = carve(scratch, n);
-    SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
-    const int sms = num_sms();
-    const uint32_t n32 = static_cast<uint32_t>(n);
-    unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
-    SBH_TIMED("sort_upsweep", s, upsweep_kernel<<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist));
-    SBH_LAUNCHED();
-    SBH_TIMED("sort_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
-    SBH_LAUNCHED();
-    Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
-    const size_t smem = sizeof(SortSmem);
-    auto kern = onesweep_kernel<RadixDigit>;
-    SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)sms * per_sm);
-    const uint32_t limit = spin_limit();
-    const int fault = take_fault();
-    uint32_t* status = status_word();
-    // bulk copies need 16-byte aligned tile starts in every buffer a pass may read
-    const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
-                          reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
-    for (int pos = 0; pos < kPositions; ++pos) {
-        SBH_TIMED("sort_onesweep", s,
-                  kern<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
-                                                    fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status,
-                                                    RadixDigit{pos * kRadixBits}, bulk_ok));
-        SBH_LAUNCHED();
-    }
-    unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
-    SBH_TIMED("sort_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan));
-    SBH_LAUNCHED();
-    return SBH_OK;
-}
-
-size_t radix_sort_scratch(uint64_t n) { return carve(nullptr, n).total; }
+size_t radix_sort_scratch(uint64_t n) { return sort_carve(nullptr, n).total; }
 
 }  // namespace sbh
 
@@ -462,5 +18,6 @@ extern "C" int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in
     if (rc || done) return rc;
     if (n == 0) return SBH_OK;
     if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out) { set_error("null pointer"); return SBH_EINVAL; }
-    return radix_sort_launch(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, d_scratch, as_stream(stream));
+    return sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, d_scratch, as_stream(stream), RadixValue{},
+                         kPositions);
 }

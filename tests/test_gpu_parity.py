@@ -292,3 +292,27 @@ def test_window_ranges_parity(S):
     rb, re_ = S.window_ranges(cuda(ts32), cuda(starts), 1_000_000)
     ob, oe = oracle.window_ranges(ts32, starts, 1_000_000)
     assert same(rb, ob) and same(re_, oe)
+
+
+@pytest.mark.parametrize("kind", ["uniform20", "mixed", "highbyte", "extremes"])
+def test_sort_chunked_path_ragged(S, kind):
+    # above the size where passes switch to per-chunk count/scan/scatter,
+    # with a ragged last tile
+    n = (1 << 21) + 4097
+    col = _sort_case(kind, n, seed=3)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp = S.sort(keys, ptrs)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_sort_unaligned_views(S):
+    # views that start 8 bytes into a buffer cannot use bulk copies
+    for n in (50_001, (1 << 21) + 11):
+        col = gen.mixed_keys(n + 1, seed=6)
+        keys, ptrs = S.extract(cuda(col), 0, n + 1)
+        kv, pv = keys[1:], ptrs[1:]
+        ok_, op_ = torch.empty_like(keys)[1:], torch.empty_like(ptrs)[1:]
+        S.sbh_kpa_sort(kv, pv, ok_, op_)
+        ek, ep = oracle.sort(col[1:], np.arange(1, n + 1, dtype=np.uint32))
+        assert same(ok_, ek) and same(op_, ep)
