@@ -152,6 +152,26 @@ int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n,
                      int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
                      uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
 
+/* The keyed reduction above without the scratch argument, for callers that
+ * cannot allocate device memory when they call: a serving loop that fixes
+ * its device memory at start-up (cudaMalloc may also synchronise the device
+ * and stall other streams), or a host that hands this library only its
+ * input and output buffers.  The paper has no counterpart; it is an
+ * interface of this library.
+ * Arguments and results are those of sbh_group_reduce; n is at most 2^28
+ * rows, and a larger n returns SBH_EINVAL without launching.  Its working
+ * memory is one fixed 2 MiB device array, which every GPU that loads the
+ * library holds until the process exits; the call allocates and frees
+ * nothing.  The first call on a device looks up that array's device address
+ * (once per device, with that device current), so make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (nothing in it needs to start at zero): two
+ * calls whose work overlaps on the GPU race and give wrong results, so
+ * serialise them, e.g. on one stream. */
+int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
+                             int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
+                             uint64_t cap, uint64_t* d_nkeys, void* stream);
+
 /* ---------------------------------------------------------------- A7
  * Top-K per key (Sec. 7, benchmark 1 "TopK Per Key": the K largest values of
  * each key).  For each distinct key j, in key order, the min(K, count)

@@ -16,6 +16,8 @@
 //              run's count and sum, at output index = number of heads before.
 // Rows are read warp-striped straight from global memory (coalesced), so the
 // kernels need almost no shared memory and many CTAs stay resident.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace sbh {
@@ -315,4 +317,65 @@ extern "C" int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, 
     if (val_bytes == 8)
         return launch_keyed<8>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, d_out_sums, cap, d_nkeys, d_scratch, s);
     return launch_keyed<4>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, d_out_sums, cap, d_nkeys, d_scratch, s);
+}
+
+// ---------------------------------------------------------------------------
+// sbh_group_reduce_noalloc: the keyed reduction with its working memory in a
+// fixed device array instead of caller scratch, for callers that cannot
+// allocate device memory at the point of the call.
+namespace sbh {
+namespace {
+
+constexpr uint64_t kNoAllocMaxRows = 1ull << 28;  // 268,435,456 rows
+constexpr size_t kNoAllocTiles = (kNoAllocMaxRows + kTile - 1) / kTile;
+constexpr size_t kNoAllocBytes = kNoAllocTiles * sizeof(Agg);  // 2 MiB on every GPU that loads the library
+
+// One copy per device.  Host code must not use this name as an address: it
+// is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (with that device current).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    SBH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device ordinal %d out of range", dev);
+        return SBH_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        SBH_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SBH_OK;
+}
+
+}  // namespace
+}  // namespace sbh
+
+extern "C" int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n,
+                                        const void* d_val_col, int val_bytes, uint64_t* d_out_keys,
+                                        uint64_t* d_out_counts, uint64_t* d_out_sums, uint64_t cap,
+                                        uint64_t* d_nkeys, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n > kNoAllocMaxRows) {
+        set_error("sbh_group_reduce_noalloc handles at most %llu rows (got %llu); use sbh_group_reduce",
+                  (unsigned long long)kNoAllocMaxRows, (unsigned long long)n);
+        return SBH_EINVAL;
+    }
+    void* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    size_t bytes = kNoAllocBytes;
+    return sbh_group_reduce(d_keys, d_ptrs, n, d_val_col, val_bytes, d_out_keys, d_out_counts, d_out_sums, cap,
+                            d_nkeys, scratch, &bytes, stream);
 }

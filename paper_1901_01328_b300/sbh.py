@@ -52,6 +52,7 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
         "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_group_reduce_noalloc": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp], i32),
         "sbh_topk": ([vp, vp, u64, vp, i32, i32, vp, vp, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_join": ([vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, sz, vp], i32),
     }
@@ -66,6 +67,7 @@ _lib = _load()
 EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
             "sbh_profile_enable", "sbh_profile_collect",
             "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_sort", "sbh_kpa_merge", "sbh_group_reduce",
+            "sbh_group_reduce_noalloc",
             "sbh_topk", "sbh_join")
 
 
