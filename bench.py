@@ -2,7 +2,10 @@
 
 One step = one pass of the hot path over one window of the mixed-key
 workload: Extract of 256M (uint64 key, uint32 row) pairs from a device key
-column, Sort, and per-key count (Keyed reduction).  Keys are the seeded
+column with a 1% key sample, training of the learned partitioner's network on
+that sample, the learned partition sort, and per-key count (Keyed
+reduction).  The plain radix sort step is timed on the same window for the
+comparison (--sort radix makes it the headline).  Keys are the seeded
 mixture of 70% Zipf(1.1) ranks over 2^24 ids and 30% floor(lognormal(30, 4))
 below 2^64.  The KPA (3 GB) is larger than the 126 MB L2, so no flush is
 needed between steps.
@@ -160,6 +163,10 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+SAMPLE_STRIDE = 100        # 1% sample for the learned partitioner
+TRAIN = dict(steps=150, batch=4096, lr=2e-2)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -173,26 +180,42 @@ def run_gpu(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
     n = args.rows
+    m = (n + SAMPLE_STRIDE - 1) // SAMPLE_STRIDE
 
     # ---- inputs: each rank draws its own window (seed offset by rank)
     col_h = torch.empty(n, dtype=torch.uint64).pin_memory()
     gen.mixed_keys(n, seed=gen.SEED_MIXED + rank, out=col_h.numpy())
     col = col_h.to(dev)
+    init = torch.from_numpy(gen.mlp_init()).to(dev)
     keys = torch.empty(n, dtype=torch.uint64, device=dev)
     ptrs = torch.empty(n, dtype=torch.uint32, device=dev)
+    samples = torch.empty(m, dtype=torch.uint64, device=dev)
+    sk = torch.empty(n, dtype=torch.uint64, device=dev)
+    sp = torch.empty(n, dtype=torch.uint32, device=dev)
     sort_scratch = torch.empty(sbh.sort_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    lsort_scratch = torch.empty(sbh.sort_learned_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    model = torch.zeros(sbh.LEARNED_MODEL_BYTES, dtype=torch.uint8, device=dev)
     out_keys = torch.empty(n, dtype=torch.uint64, device=dev)
     out_counts = torch.empty(n, dtype=torch.uint64, device=dev)
     nkeys = torch.zeros(1, dtype=torch.uint64, device=dev)
-    red_scratch = None
+    scr = {}
+    stats = {}
     stream = torch.cuda.current_stream(dev)
 
-    def step(src=col):
-        nonlocal red_scratch
+    def step_learned(src=col):
+        sbh.sbh_kpa_extract(src, 0, n, keys, ptrs, None, samples, SAMPLE_STRIDE)
+        scr["train"] = sbh.sbh_learned_train(samples, n, init, TRAIN["steps"], TRAIN["batch"], TRAIN["lr"], model)
+        stats.update(sbh.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, scratch=lsort_scratch))
+        scr["red"] = sbh.sbh_group_reduce(sk, None, None, out_keys, out_counts, None, n, nkeys,
+                                          scratch=scr.get("red"))
+
+    def step_plain(src=col):
         sbh.sbh_kpa_extract(src, 0, n, keys, ptrs)
-        sbh.sbh_kpa_sort(keys, ptrs, keys, ptrs, scratch=sort_scratch)
-        red_scratch = sbh.sbh_group_reduce(keys, None, None, out_keys, out_counts, None, n, nkeys,
-                                           scratch=red_scratch)
+        sbh.sbh_kpa_sort(keys, ptrs, sk, sp, scratch=sort_scratch)
+        scr["red"] = sbh.sbh_group_reduce(sk, None, None, out_keys, out_counts, None, n, nkeys,
+                                          scratch=scr.get("red"))
+
+    step = step_plain if args.sort == "radix" else step_learned
 
     def barrier():
         if ws > 1:
@@ -206,39 +229,53 @@ def run_gpu(args):
             return float(t.item())
         return x
 
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    def profiled(fn, steps):
+        sbh.profile_enable(True)
+        for _ in range(steps):
+            fn()
+        recs = sbh.profile_collect()
+        sbh.profile_enable(False)
+        per = {}
+        for name, t in recs:
+            per.setdefault(name, []).append(t)
+        return per, len(recs) / steps
+
     for _ in range(args.warmup):
         step()
     assert sbh.sync_status() == sbh.SBH_OK
     n_unique = int(nkeys.item())
 
-    # ---- device-resident timing
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- device-resident timing of the headline step
     with Clocks(local) as clk:
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = timed(step, args.steps)
     clocks = clk.summary()
     value = args.steps * n * ws / (ms / 1e3)
     assert sbh.sync_status() == sbh.SBH_OK
 
-    # ---- per-kernel breakdown (a separate, profiled run of the same steps)
-    sbh.profile_enable(True)
-    for _ in range(args.steps):
-        step()
-    recs = sbh.profile_collect()
-    sbh.profile_enable(False)
-    per = {}
-    for name, t in recs:
-        per.setdefault(name, []).append(t)
+    # ---- the other sort path on the same window, for the comparison
+    other = step_plain if step is step_learned else step_learned
+    for _ in range(2):
+        other()
+    ms_other = timed(other, args.steps)
+
+    # ---- per-kernel breakdown (separate, profiled runs of the same steps)
+    per, launches_per_step = profiled(step, args.steps)
     tot = {k: sum(v) for k, v in per.items()}
-    launches_per_step = len(recs) / args.steps
     dominant = max(tot, key=tot.get)
-    algo_bytes = {"sort_onesweep": PAIR_BYTES * 2 * n, "extract": (8 + PAIR_BYTES) * n,
-                  "sort_upsweep": 8 * n, "segreduce": 8 * n + 16 * n_unique}
+    algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
+                  "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
+                  "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
+                  "learned_bucket_sort": PAIR_BYTES * 2 * n, "learned_bounds": 8 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9
@@ -265,28 +302,35 @@ def run_gpu(args):
             step()
             nk_h.copy_(nkeys, non_blocking=True)
             torch.cuda.synchronize(dev)
-            m = int(nk_h[0])
-            res_k[:m].copy_(out_keys[:m], non_blocking=True)
-            res_c[:m].copy_(out_counts[:m], non_blocking=True)
-            d2h += 8 + 16 * m
+            mk = int(nk_h[0])
+            res_k[:mk].copy_(out_keys[:mk], non_blocking=True)
+            res_c[:mk].copy_(out_counts[:mk], non_blocking=True)
+            d2h += 8 + 16 * mk
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": args.steps * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": d2h // args.steps}
 
     if rank == 0:
+        learned_ms = ms if step is step_learned else ms_other
+        radix_ms = ms if step is step_plain else ms_other
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "text": WORKLOAD_TEXT, "rows_per_gpu": n, "sort": "radix",
+            "config": {"workload": WORKLOAD, "text": WORKLOAD_TEXT, "rows_per_gpu": n, "sort": args.sort,
                        "distinct_keys": n_unique, "l2": "inputs larger than L2 (3 GB KPA per step)",
-                       "parallelism": f"replicas{ws}"},
+                       "parallelism": f"replicas{ws}", "train": TRAIN, "sample_stride": SAMPLE_STRIDE},
             "roofline": roofline,
             "cpu_baseline": cpu_baseline() if ws == 1 and not args.no_cpu else None,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,
+            "learned_vs_radix": {"learned_ms_per_step": learned_ms / args.steps,
+                                 "radix_ms_per_step": radix_ms / args.steps,
+                                 "speedup": radix_ms / learned_ms,
+                                 "learned_stats": stats,
+                                 "overflow_row_rate": stats.get("overflow_rows", 0) / n},
             "stages": stages,
         }
         print(json.dumps(line), flush=True)
@@ -303,6 +347,7 @@ def main():
     ap.add_argument("--rows", type=int, default=N_FULL)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sort", default="learned", choices=["learned", "radix"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -196,6 +196,65 @@ int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, cons
              const uint32_t* d_rptrs, uint64_t nr, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
              uint64_t* d_npairs, void* d_scratch, size_t* scratch_bytes, void* stream);
 
+/* ---------------------------------------------------------------- A4
+ * Learned MSD partition sort.  The paper has no learned component (its Sort
+ * splits a KPA into chunks sorted in-core, Sec. 4.2 "Primitive
+ * Implementation"); this path produces exactly the output of sbh_kpa_sort.
+ *
+ * The network is a 1-32-32-1 ReLU MLP in FP32 with SBH_MLP_PARAMS parameters
+ * laid out as W1[32], b1[32], W2[32][32] (row = output unit), b2[32],
+ * w3[32], b3.  Its input is a key's feature x(k) = (m + f / 2^17) / 64, m the
+ * index of the highest set bit and f the 17 bits below it (x(0) = 0). */
+#define SBH_MLP_PARAMS 1153
+#define SBH_LEARNED_MODEL_BYTES 16384
+#define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
+#define SBH_LEARNED_STATS 8
+
+/* y[i] = MLP(x[i]) for i < m.  No scratch. */
+int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream);
+
+/* Gradient of the mean squared error (1/m) sum_i (MLP(x[i]) - t[i])^2 with
+ * respect to the parameters into d_grad (SBH_MLP_PARAMS floats), and the
+ * loss into *d_loss (nullable).  Sums run in a fixed order, so repeated
+ * calls give identical results.  Scratch: about 4.6 KB per 256 rows. */
+int sbh_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t m, float* d_grad,
+                 float* d_loss, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* Fits a model to a key sample (d_samples, m keys standing for n_rows rows,
+ * e.g. every 100th row from sbh_kpa_extract).  Steps:
+ *  1. sort the sample;
+ *  2. heavy cells: an exact cell (one key value: key 0, or a key below 2^11)
+ *     whose sample count times n_rows exceeds (SBH_LEARNED_CAPACITY / 2)
+ *     times m gets a dedicated bucket; its samples leave the training set;
+ *  3. training set of m' rows: row r takes the sorted non-heavy sample
+ *     j = (r * P) mod m' (P = first integer >= 2654435761 mod m' coprime
+ *     with m'), input x(key), target (#samples < key + #samples <= key) / 2m';
+ *  4. `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, rate lr) on batches of
+ *     `batch` rows, step j using rows (j * batch + q) mod m', starting from
+ *     d_init_params.  batch is a multiple of 32, at most 8192.
+ * d_model (SBH_LEARNED_MODEL_BYTES, device) receives the weights and the
+ * heavy cells.  d_losses (nullable, `steps` floats) receives each step's
+ * batch loss before its update; d_train_x / d_train_t (nullable, m floats
+ * each) receive the training set (the first m' entries are meaningful).
+ * Scratch: about 32 m bytes plus the sort scratch for m. */
+int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, const float* d_init_params,
+                      int steps, int batch, float lr, void* d_model, float* d_losses, float* d_train_x,
+                      float* d_train_t, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* Sorts a KPA with the model: bucket ids from the model's CDF (monotone in
+ * the key by construction), a stable scatter by bucket id, a shared-memory
+ * sort of every bucket of at most SBH_LEARNED_CAPACITY rows and more than one
+ * key, and the plain radix sort for the rows of larger buckets.  The output
+ * is identical to sbh_kpa_sort's; input and output must not alias.  The
+ * call synchronises `stream` once (the overflow size decides the last step).
+ * h_stats (nullable, host, SBH_LEARNED_STATS values): bucket ids, heavy
+ * cells, buckets sorted in shared memory, one-key buckets, heavy buckets,
+ * overflow buckets, overflow rows, largest bucket.
+ * Scratch: about 24 n bytes. */
+int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
+                         uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats, void* d_scratch,
+                         size_t* scratch_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,1069 @@
+// A4 Learned MSD partition sort.  The paper sorts KPAs with an in-core merge
+// sort (Sec. 4.2, "Primitive Implementation"); this path instead derives MSD
+// bucket boundaries from a small network fitted to the keys' CDF, so that
+// one scatter by bucket (two or three digit passes over a short bucket id)
+// leaves buckets small enough to sort in shared memory.
+//
+// Cells.  Key 0 is cell 0; a key k >= 1 with highest set bit m lies in cell
+// 1 + 1024 m + (the 10 bits below bit m); the next 32 bits are its offset in
+// the cell.  Cells with m <= 10 hold exactly one key value.
+//
+// Training (sbh_learned_train).  The sample is sorted; exact cells whose
+// sample count stands for more than half a bucket are heavy and get one
+// dedicated bucket; the other samples form the training set: row r takes the
+// sorted non-heavy sample (r * P) mod m', input x = feature(key) (exact in
+// FP32), target = midpoint of the key's CDF step among those samples.  A
+// 1-32-32-1 ReLU network is fitted by Adam on mean squared error; G CTAs
+// each compute the gradient of a slice of every batch, meet at a grid
+// barrier, each CTA sums one slice of the parameters over all partial
+// gradients in a fixed order and applies Adam to it, and meet again.
+//
+// Partition (sbh_kpa_sort_learned).  F(c) = the prefix maximum of the
+// clamped network output at each cell's lowest key; cell c's first bucket is
+// floor(F(c) * NB) plus two per heavy cell before it; a heavy cell's keys all
+// go to its own bucket; other keys are spread over their cell's buckets by
+// their 32-bit offset.  Bucket ids are therefore non-decreasing in the key
+// (integer arithmetic only), so a stable sort by bucket id followed by a sort
+// inside each bucket sorts the KPA.  Buckets of one key are already in ptr
+// order; buckets above the shared-memory capacity go to the plain radix sort.
+#include <algorithm>
+#include <vector>
+
+#include "radix_core.cuh"
+
+namespace sbh {
+namespace {
+
+constexpr int kH = 32;
+constexpr int kNP = 4 * kH + kH * kH + 1;  // 1153
+constexpr int oW1 = 0, oB1 = kH, oW2 = 2 * kH, oB2 = 2 * kH + kH * kH, oW3 = 3 * kH + kH * kH, oB3 = 4 * kH + kH * kH;
+constexpr uint32_t kNCell = 1 + 64 * 1024;
+constexpr uint32_t kHeavyWords = (kNCell + 31) / 32;
+
+struct Model {
+    float params[kNP];
+    uint32_t capacity;     // rows a bucket may hold to be sorted in shared memory
+    uint32_t heavy_count;  // heavy cells
+    uint32_t m_train;      // rows of the training set
+    uint32_t reserved;
+    uint32_t heavy_bits[kHeavyWords];
+};
+static_assert(sizeof(Model) <= SBH_LEARNED_MODEL_BYTES, "model blob");
+
+// ------------------------------------------------------------------ key features
+__device__ __forceinline__ float key_feature(uint64_t k) {
+    if (!k) return 0.f;
+    const int m = 63 - __clzll(static_cast<long long>(k));
+    const uint64_t top = k << (63 - m);
+    const uint32_t f = static_cast<uint32_t>(top >> 46) & 0x1FFFFu;
+    return (static_cast<float>(m) + static_cast<float>(f) * (1.0f / 131072.0f)) * (1.0f / 64.0f);
+}
+
+__device__ __forceinline__ uint32_t key_cell(uint64_t k, uint32_t* frac) {
+    if (!k) {
+        *frac = 0;
+        return 0;
+    }
+    const int m = 63 - __clzll(static_cast<long long>(k));
+    const uint64_t top = k << (63 - m);
+    *frac = static_cast<uint32_t>((top << 11) >> 32);
+    return 1u + 1024u * static_cast<uint32_t>(m) + static_cast<uint32_t>((top >> 53) & 1023u);
+}
+
+__host__ __device__ __forceinline__ bool cell_exact(uint32_t c) { return c == 0 || (c - 1) / 1024 <= 10; }
+
+// feature of the lowest key of cell c (c == kNCell: the end of key space)
+__device__ __forceinline__ float cell_x(uint32_t c) {
+    if (c == 0) return 0.f;
+    if (c >= kNCell) return 1.f;
+    const uint32_t m = (c - 1) / 1024, b = (c - 1) % 1024;
+    return (static_cast<float>(m) + static_cast<float>(b) * (1.0f / 1024.0f)) * (1.0f / 64.0f);
+}
+
+// ------------------------------------------------------------------ network
+__device__ __forceinline__ float mlp_eval(const float* __restrict__ P, float x) {
+    float h1[kH];
+#pragma unroll
+    for (int i = 0; i < kH; ++i) h1[i] = fmaxf(fmaf(P[oW1 + i], x, P[oB1 + i]), 0.f);
+    float y = P[oB3];
+#pragma unroll 4
+    for (int o = 0; o < kH; ++o) {
+        float a = P[oB2 + o];
+#pragma unroll
+        for (int i = 0; i < kH; ++i) a = fmaf(P[oW2 + o * kH + i], h1[i], a);
+        y = fmaf(P[oW3 + o], fmaxf(a, 0.f), y);
+    }
+    return y;
+}
+
+constexpr int kGThreads = 256;
+constexpr int kMaxSlice = 256;
+
+struct GradSmem {
+    float P[kNP];
+    float G[kNP];
+    float X[kMaxSlice], T[kMaxSlice], DY[kMaxSlice];
+    float A1[kMaxSlice][kH + 1];
+    float A2[kMaxSlice][kH + 1];
+    float red[kGThreads / 32];
+};
+
+// Gradient of sum_s (y_s - t_s)^2 / norm over the S rows in sm.X, sm.T into
+// sm.G (and the sum of squared errors, returned to thread 0).  sm.P holds the
+// parameters.  Every sum runs in a fixed order.
+__device__ float slice_grad(GradSmem& sm, int S, float norm) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < S * kH; e += kGThreads) {
+        const int s = e / kH, i = e % kH;
+        sm.A1[s][i] = fmaf(sm.P[oW1 + i], sm.X[s], sm.P[oB1 + i]);
+    }
+    __syncthreads();
+    for (int e = tid; e < S * kH; e += kGThreads) {
+        const int s = e / kH, o = e % kH;
+        float a = sm.P[oB2 + o];
+#pragma unroll 8
+        for (int i = 0; i < kH; ++i) a = fmaf(sm.P[oW2 + o * kH + i], fmaxf(sm.A1[s][i], 0.f), a);
+        sm.A2[s][o] = a;
+    }
+    __syncthreads();
+    float sq = 0.f;
+    for (int s = tid; s < S; s += kGThreads) {
+        float y = sm.P[oB3];
+#pragma unroll 8
+        for (int o = 0; o < kH; ++o) y = fmaf(sm.P[oW3 + o], fmaxf(sm.A2[s][o], 0.f), y);
+        const float r = y - sm.T[s];
+        sm.DY[s] = 2.f * r / norm;
+        sq += r * r;
+    }
+    __syncthreads();
+    // w3, b3
+    for (int o = tid; o <= kH; o += kGThreads) {
+        float g = 0.f;
+        if (o < kH) {
+            for (int s = 0; s < S; ++s) g = fmaf(sm.DY[s], fmaxf(sm.A2[s][o], 0.f), g);
+            sm.G[oW3 + o] = g;
+        } else {
+            for (int s = 0; s < S; ++s) g += sm.DY[s];
+            sm.G[oB3] = g;
+        }
+    }
+    __syncthreads();
+    // A2 <- dL/da2
+    for (int e = tid; e < S * kH; e += kGThreads) {
+        const int s = e / kH, o = e % kH;
+        sm.A2[s][o] = sm.A2[s][o] > 0.f ? sm.DY[s] * sm.P[oW3 + o] : 0.f;
+    }
+    __syncthreads();
+    // W2, b2
+    for (int e = tid; e < kH * kH + kH; e += kGThreads) {
+        float g = 0.f;
+        if (e < kH * kH) {
+            const int o = e / kH, i = e % kH;
+            for (int s = 0; s < S; ++s) g = fmaf(sm.A2[s][o], fmaxf(sm.A1[s][i], 0.f), g);
+            sm.G[oW2 + e] = g;
+        } else {
+            const int o = e - kH * kH;
+            for (int s = 0; s < S; ++s) g += sm.A2[s][o];
+            sm.G[oB2 + o] = g;
+        }
+    }
+    __syncthreads();
+    // A1 <- dL/da1 (through W2 and the ReLU)
+    for (int e = tid; e < S * kH; e += kGThreads) {
+        const int s = e / kH, i = e % kH;
+        float g = 0.f;
+#pragma unroll 8
+        for (int o = 0; o < kH; ++o) g = fmaf(sm.A2[s][o], sm.P[oW2 + o * kH + i], g);
+        // each (s, i) is read and written by this thread only; the reads of
+        // A1 for W2 finished at the barrier above
+        sm.A1[s][i] = sm.A1[s][i] > 0.f ? g : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < 2 * kH; i += kGThreads) {
+        float g = 0.f;
+        if (i < kH) {
+            for (int s = 0; s < S; ++s) g = fmaf(sm.A1[s][i], sm.X[s], g);
+            sm.G[oW1 + i] = g;
+        } else {
+            for (int s = 0; s < S; ++s) g += sm.A1[s][i - kH];
+            sm.G[oB1 + i - kH] = g;
+        }
+    }
+    // sum of squared errors: warp shuffles, then warp totals in order
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if ((tid & 31) == 0) sm.red[tid / 32] = sq;
+    __syncthreads();
+    float tot = 0.f;
+    if (tid == 0)
+        for (int w = 0; w < kGThreads / 32; ++w) tot += sm.red[w];
+    return tot;
+}
+
+// ---- forward and gradient entry kernels (tests and tools)
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restrict__ params, const float* __restrict__ x,
+                                                          uint64_t m, float* __restrict__ y) {
+    __shared__ float P[kNP];
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) P[i] = params[i];
+    __syncthreads();
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < m) y[i] = mlp_eval(P, x[i]);
+}
+
+__global__ void __launch_bounds__(kGThreads) mlp_grad_partial_kernel(const float* __restrict__ params,
+                                                                     const float* __restrict__ x,
+                                                                     const float* __restrict__ t, uint64_t m,
+                                                                     float* __restrict__ partial,
+                                                                     float* __restrict__ partial_sq) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
+    for (int i = threadIdx.x; i < kNP; i += kGThreads) sm.P[i] = params[i];
+    const uint64_t lo = blockIdx.x * (uint64_t)kMaxSlice;
+    const int S = (int)min_u64(kMaxSlice, m - lo);
+    for (int s = threadIdx.x; s < S; s += kGThreads) {
+        sm.X[s] = x[lo + s];
+        sm.T[s] = t[lo + s];
+    }
+    __syncthreads();
+    const float sq = slice_grad(sm, S, static_cast<float>(m));
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNP; i += kGThreads) partial[blockIdx.x * (size_t)kNP + i] = sm.G[i];
+    if (threadIdx.x == 0) partial_sq[blockIdx.x] = sq;
+}
+
+__global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, const float* __restrict__ partial_sq,
+                                    uint32_t nparts, uint64_t m, float* __restrict__ grad, float* __restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNP) {
+        float g = 0.f;
+        for (uint32_t c = 0; c < nparts; ++c) g += partial[c * (size_t)kNP + i];
+        grad[i] = g;
+    }
+    if (i == 0 && loss) {
+        float l = 0.f;
+        for (uint32_t c = 0; c < nparts; ++c) l += partial_sq[c];
+        *loss = l / static_cast<float>(m);
+    }
+}
+
+// ------------------------------------------------------------------ training data
+struct TrainScratch {
+    uint64_t* s_keys;    // sorted sample (m)
+    uint32_t* s_ptrs;
+    uint64_t* nh;        // non-heavy sorted samples (m)
+    uint32_t* flags;     // m + 1 (compaction)
+    uint64_t* block_sums;
+    float* X;
+    float* T;
+    float* partial;      // G * kNP
+    float* partial_sq;   // G
+    float* adam_m;
+    float* adam_v;
+    float* params;       // current parameters (global copy)
+    uint32_t* bar;       // grid barrier: count, generation
+    uint32_t* m_train;
+    void* sort_scratch;
+    size_t total;
+};
+
+constexpr int kTrainCtas = 32;
+constexpr int kCompactTile = 1024;
+
+TrainScratch train_carve(void* base, uint64_t m) {
+    Carver c(base);
+    TrainScratch t;
+    t.s_keys = c.take<uint64_t>(m);
+    t.s_ptrs = c.take<uint32_t>(m);
+    t.nh = c.take<uint64_t>(m);
+    t.flags = c.take<uint32_t>(m + 1);
+    t.block_sums = c.take<uint64_t>((m + kCompactTile - 1) / kCompactTile + 1);
+    t.X = c.take<float>(m);
+    t.T = c.take<float>(m);
+    t.partial = c.take<float>(kTrainCtas * (size_t)kNP);
+    t.partial_sq = c.take<float>(kTrainCtas);
+    t.adam_m = c.take<float>(kNP);
+    t.adam_v = c.take<float>(kNP);
+    t.params = c.take<float>(kNP);
+    t.bar = c.take<uint32_t>(2);
+    t.m_train = c.take<uint32_t>(1);
+    t.sort_scratch = c.take<char>(sort_carve(nullptr, m).total);
+    t.total = c.bytes();
+    return t;
+}
+
+__global__ void iota_kernel(uint32_t* p, uint64_t m) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < m) p[i] = static_cast<uint32_t>(i);
+}
+
+// Heavy cells from the sorted sample: the first sample of each exact cell
+// measures its run by binary search and marks the cell.
+__global__ void heavy_kernel(const uint64_t* __restrict__ srt, uint64_t m, uint64_t n_rows, uint32_t capacity,
+                             Model* __restrict__ model) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t f;
+    const uint32_t c = key_cell(srt[i], &f);
+    if (!cell_exact(c)) return;
+    if (i > 0) {
+        uint32_t pf;
+        if (key_cell(srt[i - 1], &pf) == c) return;
+    }
+    // exact cell = one key value: its run ends at the first larger key
+    const uint64_t key = srt[i];
+    uint64_t lo = i, hi = m;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (srt[mid] <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    const uint64_t count = lo - i;
+    if ((unsigned __int128)count * n_rows > (unsigned __int128)(capacity / 2) * m) {
+        atomicOr(&model->heavy_bits[c >> 5], 1u << (c & 31));
+        atomicAdd(&model->heavy_count, 1u);
+    }
+}
+
+__device__ __forceinline__ bool is_heavy(const uint32_t* bits, uint32_t c) { return (bits[c >> 5] >> (c & 31)) & 1u; }
+
+// Compaction of the non-heavy samples: per-tile counts, one-CTA scan, scatter.
+__global__ void __launch_bounds__(kCompactTile) keep_count_kernel(const uint64_t* __restrict__ srt, uint64_t m,
+                                                                  const Model* __restrict__ model,
+                                                                  uint64_t* __restrict__ block_sums) {
+    __shared__ uint32_t wsum[kCompactTile / 32];
+    const uint64_t i = blockIdx.x * (uint64_t)kCompactTile + threadIdx.x;
+    uint32_t keep = 0;
+    if (i < m) {
+        uint32_t f;
+        keep = !is_heavy(model->heavy_bits, key_cell(srt[i], &f));
+    }
+    const uint32_t b = __popc(__ballot_sync(0xffffffffu, keep));
+    if (lane_id() == 0) wsum[threadIdx.x / 32] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < kCompactTile / 32; ++w) t += wsum[w];
+        block_sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) scan_u64_kernel(uint64_t* __restrict__ v, uint32_t nb,
+                                                        uint32_t* __restrict__ total32) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const uint64_t x0 = i < nb ? v[i] : 0;
+        uint64_t x = x0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (uint32_t)o) x += y;
+        }
+        if (lane_id() == 31) warp_tot[threadIdx.x / 32] = x;
+        __syncthreads();
+        uint64_t before = carry;
+        for (uint32_t w = 0; w < threadIdx.x / 32; ++w) before += warp_tot[w];
+        if (i < nb) v[i] = before + x - x0;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total32 = static_cast<uint32_t>(carry);
+}
+
+__global__ void __launch_bounds__(kCompactTile) keep_scatter_kernel(const uint64_t* __restrict__ srt, uint64_t m,
+                                                                    const Model* __restrict__ model,
+                                                                    const uint64_t* __restrict__ block_off,
+                                                                    uint64_t* __restrict__ nh) {
+    __shared__ uint32_t wsum[kCompactTile / 32];
+    const uint64_t i = blockIdx.x * (uint64_t)kCompactTile + threadIdx.x;
+    uint32_t keep = 0;
+    uint64_t key = 0;
+    if (i < m) {
+        uint32_t f;
+        key = srt[i];
+        keep = !is_heavy(model->heavy_bits, key_cell(key, &f));
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+    if (lane_id() == 0) wsum[threadIdx.x / 32] = __popc(bal);
+    __syncthreads();
+    uint64_t off = block_off[blockIdx.x];
+    for (uint32_t w = 0; w < threadIdx.x / 32; ++w) off += wsum[w];
+    off += __popc(bal & lanemask_lt());
+    if (keep) nh[off] = key;
+}
+
+__device__ __forceinline__ uint32_t gcd_u32(uint32_t a, uint32_t b) {
+    while (b) {
+        const uint32_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Training rows: row r takes sorted non-heavy sample (r * P) mod m'.
+__global__ void trainset_kernel(const uint64_t* __restrict__ nh, const uint32_t* __restrict__ m_train,
+                                float* __restrict__ X, float* __restrict__ T) {
+    const uint32_t mt = *m_train;
+    const uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (r >= mt) return;
+    uint32_t P = static_cast<uint32_t>(2654435761ull % mt);
+    while (gcd_u32(P, mt) != 1) ++P;
+    const uint64_t j = (r * (uint64_t)P) % mt;
+    const uint64_t key = nh[j];
+    uint64_t lo = 0, hi = mt;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (nh[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    const uint64_t lt = lo;
+    hi = mt;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (nh[mid] <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    X[r] = key_feature(key);
+    T[r] = static_cast<float>(lt + lo) / (2.0f * static_cast<float>(mt));
+}
+
+// ------------------------------------------------------------------ training
+// Bounded grid barrier for the co-resident CTAs of a cooperative launch.
+__device__ bool grid_barrier(uint32_t* bar, uint32_t nblocks, uint32_t spin_limit, uint32_t* status) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        volatile uint32_t* gen = bar + 1;
+        const uint32_t g = *gen;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(bar, 1u) + 1;
+        if (arrived == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*gen == g) {
+                if (wait_expired(polls, spin_limit, status)) {
+                    ok = false;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+struct TrainArgs {
+    const float* X;
+    const float* T;
+    const uint32_t* m_train;
+    float* params;   // global parameter copy, starts at the initial weights
+    float* adam_m;
+    float* adam_v;
+    float* partial;
+    float* partial_sq;
+    uint32_t* bar;
+    float* losses;   // nullable, one per step
+    int steps;
+    int batch;
+    float lr;
+    uint32_t spin_limit;
+    uint32_t* status;
+};
+
+__global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
+    const uint32_t mt = *a.m_train;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int S = a.batch / G;
+    const int chunk = (kNP + G - 1) / G;
+    const int p0 = min(kNP, c * chunk), p1 = min(kNP, p0 + chunk);
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float b1t = 1.f, b2t = 1.f;
+    if (mt == 0) return;
+    for (int step = 0; step < a.steps; ++step) {
+        for (int i = threadIdx.x; i < kNP; i += kGThreads) sm.P[i] = a.params[i];
+        for (int s = threadIdx.x; s < S; s += kGThreads) {
+            const uint64_t row = ((uint64_t)step * a.batch + (uint64_t)c * S + s) % mt;
+            sm.X[s] = a.X[row];
+            sm.T[s] = a.T[row];
+        }
+        __syncthreads();
+        const float sq = slice_grad(sm, S, static_cast<float>(a.batch));
+        __syncthreads();
+        for (int i = threadIdx.x; i < kNP; i += kGThreads) a.partial[c * (size_t)kNP + i] = sm.G[i];
+        if (threadIdx.x == 0) a.partial_sq[c] = sq;
+        __threadfence();
+        if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+        b1t *= b1;
+        b2t *= b2;
+        for (int i = p0 + threadIdx.x; i < p1; i += kGThreads) {
+            float g = 0.f;
+            for (int q = 0; q < G; ++q) g += a.partial[q * (size_t)kNP + i];
+            const float mi = b1 * a.adam_m[i] + (1.f - b1) * g;
+            const float vi = b2 * a.adam_v[i] + (1.f - b2) * g * g;
+            a.adam_m[i] = mi;
+            a.adam_v[i] = vi;
+            const float mhat = mi / (1.f - b1t), vhat = vi / (1.f - b2t);
+            a.params[i] -= a.lr * mhat / (sqrtf(vhat) + eps);
+        }
+        if (c == 0 && threadIdx.x == 0 && a.losses) {
+            float l = 0.f;
+            for (int q = 0; q < G; ++q) l += a.partial_sq[q];
+            a.losses[step] = l / static_cast<float>(a.batch);
+        }
+        __threadfence();
+        if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+    }
+}
+
+__global__ void finish_model_kernel(const float* __restrict__ params, const uint32_t* __restrict__ m_train,
+                                    uint32_t capacity, Model* __restrict__ model) {
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) model->params[i] = params[i];
+    if (threadIdx.x == 0) {
+        model->capacity = capacity;
+        model->m_train = *m_train;
+    }
+}
+
+// ------------------------------------------------------------------ partition
+// Bucket id of a key (see the file comment).
+struct BucketValue {
+    const uint32_t* tbl;         // kNCell + 1 first-bucket ids
+    const uint32_t* heavy_bits;  // heavy cells
+    __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
+        uint32_t f;
+        const uint32_t c = key_cell(k, &f);
+        const uint32_t b0 = __ldg(tbl + c);
+        if ((__ldg(heavy_bits + (c >> 5)) >> (c & 31)) & 1u) return b0 + 1;
+        const uint32_t cnt = __ldg(tbl + c + 1) - b0;
+        return b0 + static_cast<uint32_t>((static_cast<uint64_t>(f) * cnt) >> 32);
+    }
+};
+
+__global__ void __launch_bounds__(256) cell_cdf_kernel(const Model* __restrict__ model, float* __restrict__ F) {
+    __shared__ float P[kNP];
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) P[i] = model->params[i];
+    __syncthreads();
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c <= kNCell) F[c] = fminf(fmaxf(mlp_eval(P, cell_x(c)), 0.f), 1.f);
+}
+
+// One CTA: prefix maximum of F, heavy prefix counts, first-bucket table and
+// the bitmap of heavy buckets.  nbid receives the bound on bucket ids.
+constexpr int kTblThreads = 1024;
+__global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __restrict__ model,
+                                                                 const float* __restrict__ F, uint32_t nb,
+                                                                 uint32_t* __restrict__ tbl,
+                                                                 uint32_t* __restrict__ heavy_bucket_bits,
+                                                                 uint32_t* __restrict__ nbid) {
+    __shared__ float s_max[kTblThreads];
+    __shared__ uint32_t s_cnt[kTblThreads];
+    const uint32_t total = kNCell + 1;
+    const uint32_t per = (total + kTblThreads - 1) / kTblThreads;
+    const uint32_t c0 = min(total, threadIdx.x * per), c1 = min(total, c0 + per);
+    float mx = 0.f;
+    uint32_t hc = 0;
+    for (uint32_t c = c0; c < c1; ++c) {
+        mx = fmaxf(mx, F[c]);
+        hc += (c < kNCell) && is_heavy(model->heavy_bits, c);
+    }
+    s_max[threadIdx.x] = mx;
+    s_cnt[threadIdx.x] = hc;
+    __syncthreads();
+    // inclusive scans (max, +) over the threads, Hillis-Steele in shared memory
+    for (uint32_t o = 1; o < kTblThreads; o <<= 1) {
+        const float pm = threadIdx.x >= o ? s_max[threadIdx.x - o] : 0.f;
+        const uint32_t pc = threadIdx.x >= o ? s_cnt[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s_max[threadIdx.x] = fmaxf(s_max[threadIdx.x], pm);
+        s_cnt[threadIdx.x] += pc;
+        __syncthreads();
+    }
+    float run_max = threadIdx.x ? s_max[threadIdx.x - 1] : 0.f;
+    uint32_t heavy_before = threadIdx.x ? s_cnt[threadIdx.x - 1] : 0u;
+    // Keep every id below 2^16 when that costs at most a quarter of the
+    // buckets: the scatter by bucket id then takes two digit passes, not three.
+    const uint32_t heavy_total = s_cnt[kTblThreads - 1];
+    const uint32_t fit16 = 65536u - 2u * heavy_total - 2u;
+    if (heavy_total < 16384u && nb > fit16 && fit16 >= nb - nb / 4) nb = fit16;
+    const float fnb = static_cast<float>(nb);
+    for (uint32_t c = c0; c < c1; ++c) {
+        run_max = fmaxf(run_max, F[c]);
+        const uint32_t base = static_cast<uint32_t>(floorf(run_max * fnb));
+        const uint32_t t = base + 2u * heavy_before;
+        tbl[c] = t;
+        if (c < kNCell && is_heavy(model->heavy_bits, c)) {
+            atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
+            ++heavy_before;
+        }
+        if (c == kNCell) *nbid = t + 1;
+    }
+}
+
+// bstart[b] = first row whose bucket id is >= b, for b in [0, nbid].
+__global__ void bucket_bounds_kernel(const uint64_t* __restrict__ keys, uint32_t n, BucketValue fn,
+                                     const uint32_t* __restrict__ nbid_p, uint32_t* __restrict__ bstart) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t nbid = *nbid_p;
+    const uint32_t id = static_cast<uint32_t>(fn(keys[i]));
+    const int64_t prev = i ? static_cast<int64_t>(fn(keys[i - 1])) : -1;
+    for (int64_t b = prev + 1; b <= (int64_t)id; ++b) bstart[b] = i;
+    if (i == n - 1)
+        for (uint32_t b = id + 1; b <= nbid; ++b) bstart[b] = n;
+}
+
+// In-shared-memory sort of each bucket of at most kCap rows.
+constexpr uint32_t kCap = SBH_LEARNED_CAPACITY;
+constexpr int kBThreads = 512;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBIpt = kCap / kBThreads;
+
+struct BucketSmem {
+    uint64_t keys[2][kCap];
+    uint32_t ptrs[2][kCap];
+    uint32_t whist2[kBWarps][kRadix / 2 + 1];
+    uint32_t local_start[kRadix];
+    uint32_t scan_tmp[4];
+    uint64_t red[2][kBWarps];
+    uint32_t bucket;
+};
+
+struct BucketStats {
+    unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
+        max_bucket;
+};
+
+__global__ void __launch_bounds__(kBThreads, 1)
+bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
+                   const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
+                   uint32_t* __restrict__ counter, uint32_t* __restrict__ ov_flag, BucketStats* __restrict__ st) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BucketSmem& sm = *reinterpret_cast<BucketSmem*>(smem_raw);
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
+    const uint32_t nbid = *nbid_p;
+    const uint32_t lt = lanemask_lt();
+    for (;;) {
+        if (tid == 0) sm.bucket = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t b = sm.bucket;
+        __syncthreads();
+        if (b >= nbid) break;
+        const uint32_t s = bstart[b], e = bstart[b + 1], cnt = e - s;
+        if (tid == 0 && cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
+        if (cnt <= 1) continue;
+        if ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) {
+            if (tid == 0) atomicAdd(&st->heavy_buckets, 1ull);
+            continue;  // one key: the stable scatter left it in ptr order
+        }
+        if (cnt > kCap) {
+            if (tid == 0) {
+                ov_flag[b] = 1;
+                atomicAdd(&st->overflow_buckets, 1ull);
+                atomicAdd(&st->overflow_rows, (unsigned long long)cnt);
+            }
+            continue;
+        }
+        // load, and the key range
+        uint64_t kmin = ~0ull, kmax = 0;
+        for (uint32_t r = tid; r < cnt; r += kBThreads) {
+            const uint64_t k = keys[s + r];
+            sm.keys[0][r] = k;
+            sm.ptrs[0][r] = ptrs[s + r];
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) {
+            sm.red[0][warp] = kmin;
+            sm.red[1][warp] = kmax;
+        }
+        __syncthreads();
+        kmin = sm.red[0][0];
+        kmax = sm.red[1][0];
+        for (int w = 1; w < kBWarps; ++w) {
+            kmin = min(kmin, sm.red[0][w]);
+            kmax = max(kmax, sm.red[1][w]);
+        }
+        if (kmin == kmax) {
+            if (tid == 0) atomicAdd(&st->single_key_buckets, 1ull);
+            continue;  // one key value: already in ptr order
+        }
+        const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
+        const int passes = (bits + kRadixBits - 1) / kRadixBits;
+        int a = 0;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int sh = pass * kRadixBits;
+            for (int x = tid; x < kBWarps * (kRadix / 2 + 1); x += kBThreads) (&sm.whist2[0][0])[x] = 0;
+            __syncthreads();
+            uint32_t dg[kBIpt], rank[kBIpt];
+            const uint32_t wofs = warp * 32 * kBIpt + lane;
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t r = wofs + j * 32;
+                dg[j] = r < cnt ? static_cast<uint32_t>((sm.keys[a][r] - kmin) >> sh) & (kRadix - 1) : kRadix;
+            }
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t hs = (dg[j] & 1u) * 16u;
+                uint32_t c = 0;
+                if ((int)lane == leader) c = atomicAdd(&sm.whist2[warp][dg[j] >> 1], (uint32_t)__popc(peers) << hs);
+                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> hs) & 0xFFFFu);
+            }
+            __syncthreads();
+            uint32_t c0 = 0, c1 = 0, x = 0;
+            if (tid < kRadix / 2) {
+#pragma unroll
+                for (int w = 0; w < kBWarps; ++w) {
+                    const uint32_t word = sm.whist2[w][tid];
+                    sm.whist2[w][tid] = c0 | (c1 << 16);
+                    c0 += word & 0xFFFFu;
+                    c1 += word >> 16;
+                }
+                x = c0 + c1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                if (lane == 31) sm.scan_tmp[warp] = x;
+            }
+            __syncthreads();
+            if (tid < kRadix / 2) {
+                uint32_t before = 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
+                const uint32_t l0 = before + x - c0 - c1;
+                sm.local_start[2 * tid] = l0;
+                sm.local_start[2 * tid + 1] = l0 + c0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                if (dg[j] < kRadix) {
+                    const uint32_t r = wofs + j * 32;
+                    const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
+                    const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
+                    sm.keys[a ^ 1][slot] = sm.keys[a][r];
+                    sm.ptrs[a ^ 1][slot] = sm.ptrs[a][r];
+                }
+            }
+            __syncthreads();
+            a ^= 1;
+        }
+        for (uint32_t r = tid; r < cnt; r += kBThreads) {
+            keys[s + r] = sm.keys[a][r];
+            ptrs[s + r] = sm.ptrs[a][r];
+        }
+        if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
+        __syncthreads();
+    }
+}
+
+// Ordered list of overflow buckets with their row offsets in a compact
+// buffer (one CTA).  ov_rows_total receives the total.
+__global__ void __launch_bounds__(1024) overflow_list_kernel(const uint32_t* __restrict__ ov_flag,
+                                                             const uint32_t* __restrict__ nbid_p,
+                                                             const uint32_t* __restrict__ bstart,
+                                                             uint32_t* __restrict__ list, uint32_t* __restrict__ offs,
+                                                             uint32_t* __restrict__ nlist,
+                                                             uint32_t* __restrict__ rows_total) {
+    __shared__ uint32_t wc[32], wr[32];
+    __shared__ uint32_t carry_c, carry_r;
+    const uint32_t nbid = *nbid_p;
+    if (threadIdx.x == 0) carry_c = carry_r = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nbid; c0 += blockDim.x) {
+        const uint32_t b = c0 + threadIdx.x;
+        const uint32_t f = b < nbid ? ov_flag[b] : 0u;
+        const uint32_t len = f ? bstart[b + 1] - bstart[b] : 0u;
+        uint32_t xc = f, xr = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yc = __shfl_up_sync(0xffffffffu, xc, o), yr = __shfl_up_sync(0xffffffffu, xr, o);
+            if (lane_id() >= (uint32_t)o) { xc += yc; xr += yr; }
+        }
+        if (lane_id() == 31) { wc[threadIdx.x / 32] = xc; wr[threadIdx.x / 32] = xr; }
+        __syncthreads();
+        uint32_t bc = carry_c, br = carry_r;
+        for (uint32_t w = 0; w < threadIdx.x / 32; ++w) { bc += wc[w]; br += wr[w]; }
+        if (f) {
+            list[bc + xc - 1] = b;
+            offs[bc + xc - 1] = br + xr - len;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) { carry_c = bc + xc; carry_r = br + xr; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { *nlist = carry_c; *rows_total = carry_r; }
+}
+
+// One CTA per overflow bucket: copy its rows to (to_gather) or from the
+// compact buffer.
+__global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs,
+                                     const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ list,
+                                     const uint32_t* __restrict__ offs, uint64_t* __restrict__ ck,
+                                     uint32_t* __restrict__ cp, int to_gather) {
+    const uint32_t b = list[blockIdx.x];
+    const uint32_t s = bstart[b], len = bstart[b + 1] - s, o = offs[blockIdx.x];
+    for (uint32_t r = threadIdx.x; r < len; r += blockDim.x) {
+        if (to_gather) {
+            ck[o + r] = keys[s + r];
+            cp[o + r] = ptrs[s + r];
+        } else {
+            keys[s + r] = ck[o + r];
+            ptrs[s + r] = cp[o + r];
+        }
+    }
+}
+
+struct SortLearnedScratch {
+    uint32_t* tbl;          // kNCell + 1
+    float* F;               // kNCell + 1
+    uint32_t* heavy_bucket_bits;
+    uint32_t* bstart;       // max ids + 1
+    uint32_t* ov_flag;      // max ids
+    uint32_t* list;
+    uint32_t* offs;
+    uint32_t* small;        // nbid, counter, nlist, rows_total
+    BucketStats* stats;
+    uint64_t* ck;           // compact overflow rows (n)
+    uint32_t* cp;
+    void* sort_scratch;     // for the id passes and the overflow sort
+    size_t zero_bytes;      // from heavy_bucket_bits through stats
+    size_t total;
+};
+
+inline uint64_t learned_nb(uint64_t n) { return (2 * n + kCap - 1) / kCap; }
+// every id is below NB + 2 * (heavy cells) + 2, and heavy cells are cells
+inline uint64_t learned_max_ids(uint64_t n) { return learned_nb(n) + 2ull * kNCell + 4; }
+
+SortLearnedScratch learned_carve(void* base, uint64_t n) {
+    Carver c(base);
+    SortLearnedScratch t;
+    const uint64_t ids = learned_max_ids(n);
+    t.tbl = c.take<uint32_t>(kNCell + 1);
+    t.F = c.take<float>(kNCell + 1);
+    t.list = c.take<uint32_t>(ids);
+    t.offs = c.take<uint32_t>(ids);
+    t.bstart = c.take<uint32_t>(ids + 1);
+    t.heavy_bucket_bits = c.take<uint32_t>(ids / 32 + 1);
+    const size_t z0 = c.off - (ids / 32 + 1) * sizeof(uint32_t);
+    t.ov_flag = c.take<uint32_t>(ids);
+    t.small = c.take<uint32_t>(8);
+    t.stats = c.take<BucketStats>(1);
+    t.zero_bytes = c.off - z0;
+    t.ck = c.take<uint64_t>(n);
+    t.cp = c.take<uint32_t>(n);
+    t.sort_scratch = c.take<char>(sort_carve(nullptr, n).total);
+    t.total = c.bytes();
+    return t;
+}
+
+}  // namespace
+}  // namespace sbh
+
+// ============================================================== C ABI
+extern "C" {
+
+int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (m == 0) return SBH_OK;
+    if (!d_params || !d_x || !d_y) { set_error("null pointer"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    SBH_TIMED("mlp_forward", s,
+              mlp_forward_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_params, d_x, m, d_y));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int sbh_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint64_t m, float* d_grad,
+                 float* d_loss, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    const uint64_t nparts = (m + kMaxSlice - 1) / kMaxSlice;
+    if (nparts > 0xFFFFFFFFull) { set_error("m too large"); return SBH_EINVAL; }
+    Carver c(nullptr);
+    c.take<float>(nparts * kNP);
+    c.take<float>(nparts);
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, c.bytes(), &done);
+    if (rc || done) return rc;
+    if (m == 0) { set_error("m must be > 0"); return SBH_EINVAL; }
+    if (!d_params || !d_x || !d_t || !d_grad) { set_error("null pointer"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    Carver w(d_scratch);
+    float* partial = w.take<float>(nparts * kNP);
+    float* partial_sq = w.take<float>(nparts);
+    const size_t smem = sizeof(GradSmem);
+    SBH_CUDA(cudaFuncSetAttribute(mlp_grad_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SBH_TIMED("mlp_grad", s,
+              mlp_grad_partial_kernel<<<(unsigned)nparts, kGThreads, smem, s>>>(d_params, d_x, d_t, m, partial,
+                                                                                partial_sq));
+    SBH_LAUNCHED();
+    SBH_TIMED("mlp_grad_sum", s,
+              mlp_grad_sum_kernel<<<(kNP + 255) / 256, 256, 0, s>>>(partial, partial_sq, (uint32_t)nparts, m, d_grad,
+                                                                    d_loss));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, const float* d_init_params,
+                      int steps, int batch, float lr, void* d_model, float* d_losses, float* d_train_x,
+                      float* d_train_t, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (m > 0xFFFFFFFFull) { set_error("m must be < 2^32"); return SBH_EINVAL; }
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, train_carve(nullptr, m).total, &done);
+    if (rc || done) return rc;
+    if (m == 0 || !d_samples || !d_init_params || !d_model) { set_error("empty sample or null pointer"); return SBH_EINVAL; }
+    if (steps < 0 || batch < kTrainCtas || batch % kTrainCtas || batch / kTrainCtas > kMaxSlice) {
+        set_error("batch must be a multiple of %d in [%d, %d]", kTrainCtas, kTrainCtas, kTrainCtas * kMaxSlice);
+        return SBH_EINVAL;
+    }
+    cudaStream_t s = as_stream(stream);
+    TrainScratch t = train_carve(d_scratch, m);
+    Model* model = static_cast<Model*>(d_model);
+    SBH_CUDA(cudaMemsetAsync(model, 0, sizeof(Model), s));
+    SBH_CUDA(cudaMemsetAsync(t.bar, 0, 2 * sizeof(uint32_t), s));
+    SBH_CUDA(cudaMemsetAsync(t.adam_m, 0, kNP * sizeof(float), s));
+    SBH_CUDA(cudaMemsetAsync(t.adam_v, 0, kNP * sizeof(float), s));
+    SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // sort the sample
+    const unsigned gm = (unsigned)((m + 255) / 256);
+    SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.s_ptrs, m));
+    SBH_LAUNCHED();
+    rc = sort_by_value(d_samples, t.s_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions);
+    if (rc) return rc;
+    // heavy cells, non-heavy compaction, training rows
+    SBH_TIMED("learned_heavy", s, heavy_kernel<<<gm, 256, 0, s>>>(t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY, model));
+    SBH_LAUNCHED();
+    const uint32_t nb = (uint32_t)((m + kCompactTile - 1) / kCompactTile);
+    SBH_TIMED("learned_keep", s, keep_count_kernel<<<nb, kCompactTile, 0, s>>>(t.s_keys, m, model, t.block_sums));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_keep_scan", s, scan_u64_kernel<<<1, 1024, 0, s>>>(t.block_sums, nb, t.m_train));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_keep", s,
+              keep_scatter_kernel<<<nb, kCompactTile, 0, s>>>(t.s_keys, m, model, t.block_sums, t.nh));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_trainset", s, trainset_kernel<<<gm, 256, 0, s>>>(t.nh, t.m_train, t.X, t.T));
+    SBH_LAUNCHED();
+    if (d_train_x) SBH_CUDA(cudaMemcpyAsync(d_train_x, t.X, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (d_train_t) SBH_CUDA(cudaMemcpyAsync(d_train_t, t.T, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // train
+    if (steps > 0) {
+        TrainArgs a{t.X, t.T, t.m_train, t.params, t.adam_m, t.adam_v, t.partial, t.partial_sq, t.bar, d_losses,
+                    steps, batch, lr, spin_limit(), status_word()};
+        const size_t smem = sizeof(GradSmem);
+        SBH_CUDA(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, train_kernel, kGThreads, smem));
+        if (per_sm * num_sms() < kTrainCtas) { set_error("cannot co-schedule %d training CTAs", kTrainCtas); return SBH_ECUDA; }
+        void* args[] = {&a};
+        {
+            ProfScope ps("learned_train", s);
+            SBH_CUDA(cudaLaunchCooperativeKernel((const void*)train_kernel, dim3(kTrainCtas), dim3(kGThreads), args,
+                                                 smem, s));
+        }
+    }
+    SBH_TIMED("learned_finish", s,
+              finish_model_kernel<<<1, 256, 0, s>>>(t.params, t.m_train, SBH_LEARNED_CAPACITY, model));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+}  // extern "C"
+
+extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
+                                    uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats,
+                                    void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n > 0xFFFFFFFFull) { set_error("n must be < 2^32"); return SBH_EINVAL; }
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, learned_carve(nullptr, n).total, &done);
+    if (rc || done) return rc;
+    if (h_stats)
+        for (int i = 0; i < SBH_LEARNED_STATS; ++i) h_stats[i] = 0;
+    if (n == 0) return SBH_OK;
+    if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out || !d_model) { set_error("null pointer"); return SBH_EINVAL; }
+    if (d_keys_in == d_keys_out) { set_error("the learned sort needs distinct input and output buffers"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    SortLearnedScratch t = learned_carve(d_scratch, n);
+    const Model* model = static_cast<const Model*>(d_model);
+    SBH_CUDA(cudaMemsetAsync(t.heavy_bucket_bits, 0, t.zero_bytes, s));
+    const uint32_t nb = (uint32_t)learned_nb(n);
+    uint32_t* nbid = t.small + 0;
+    uint32_t* counter = t.small + 1;
+    uint32_t* nlist = t.small + 2;
+    uint32_t* rows_total = t.small + 3;
+    SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<(kNCell + 1 + 255) / 256, 256, 0, s>>>(model, t.F));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_table", s,
+              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.heavy_bucket_bits, nbid));
+    SBH_LAUNCHED();
+    const BucketValue fn{t.tbl, model->heavy_bits};
+    // stable scatter by bucket id (ids fit in 24 bits: three digit positions)
+    rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3);
+    if (rc) return rc;
+    SBH_TIMED("learned_bounds", s,
+              bucket_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_keys_out, (uint32_t)n, fn, nbid,
+                                                                               t.bstart));
+    SBH_LAUNCHED();
+    const size_t smem = sizeof(BucketSmem);
+    SBH_CUDA(cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SBH_TIMED("learned_bucket_sort", s,
+              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, nbid,
+                                                                    t.heavy_bucket_bits, counter, t.ov_flag,
+                                                                    t.stats));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_overflow_list", s,
+              overflow_list_kernel<<<1, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.list, t.offs, nlist, rows_total));
+    SBH_LAUNCHED();
+    // the overflow is data-dependent: read its size (one stream synchronisation)
+    uint32_t small_h[4];
+    BucketStats st_h;
+    uint32_t heavy_h = 0;
+    SBH_CUDA(cudaMemcpyAsync(small_h, t.small, sizeof(small_h), cudaMemcpyDeviceToHost, s));
+    SBH_CUDA(cudaMemcpyAsync(&st_h, t.stats, sizeof(st_h), cudaMemcpyDeviceToHost, s));
+    SBH_CUDA(cudaMemcpyAsync(&heavy_h, &model->heavy_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SBH_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nl = small_h[2], rows = small_h[3];
+    if (nl > 0) {
+        SBH_TIMED("learned_overflow_move", s,
+                  overflow_move_kernel<<<nl, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, t.ck, t.cp,
+                                                          1));
+        SBH_LAUNCHED();
+        rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, rows, t.sort_scratch, s, RadixValue{}, kPositions);
+        if (rc) return rc;
+        SBH_TIMED("learned_overflow_move", s,
+                  overflow_move_kernel<<<nl, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, t.ck, t.cp,
+                                                          0));
+        SBH_LAUNCHED();
+    }
+    if (h_stats) {
+        h_stats[0] = small_h[0];
+        h_stats[1] = heavy_h;
+        h_stats[2] = st_h.sorted_buckets;
+        h_stats[3] = st_h.single_key_buckets;
+        h_stats[4] = st_h.heavy_buckets;
+        h_stats[5] = st_h.overflow_buckets;
+        h_stats[6] = st_h.overflow_rows;
+        h_stats[7] = st_h.max_bucket;
+    }
+    return SBH_OK;
+}

@@ -393,13 +393,27 @@ __global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ pl
     }
 }
 
+// Lanes of the warp whose digit equals this lane's, from one ballot per digit
+// bit (digits below 2^nbits).
+template <int kBits>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit < kBits; ++bit) {
+        const uint32_t on = (d >> bit) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        peers &= on ? bal : ~bal;
+    }
+    return peers;
+}
+
 // ------------------------------------------------------------------ chunked passes
 constexpr uint32_t kMaxChunks = 1024;
 constexpr uint64_t kChunkedMinRows = 1u << 21;  // below this the onesweep kernel is used
 
 // Digit histogram of each chunk.
 template <typename ValueFn>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                    uint32_t* __restrict__ chunk_hist, ValueFn value_of) {
     if (!plan->active[pos]) return;
@@ -468,8 +482,27 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
 }
 
 // Ranks and scatters one chunk, tile by tile, with running digit offsets.
+// 512 threads x 8 rows per tile: twice the warps of the onesweep kernel for
+// the same tile, to hide the latency of the ranking chain.
+constexpr int kSThreads = 512;
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kSIpt = kTile / kSThreads;
+
+struct ScatterSmem {
+    uint64_t keys[2][kTile];  // double-buffered input tiles, reused to stage
+    uint32_t ptrs[2][kTile];  // the scatter in digit order
+    uint8_t dig[kTile];       // digit of each staged row
+    // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
+    // word 128 holds the sentinel digit of rows past the end)
+    uint32_t whist2[kSWarps][kRadix / 2 + 1];
+    uint32_t local_start[kRadix];
+    uint32_t gbase_rel[kRadix];
+    uint32_t scan_tmp[4];
+    uint64_t mbar[2];
+};
+
 template <typename ValueFn>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kSThreads, 2)
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
                      uint32_t* __restrict__ status) {
@@ -486,9 +519,14 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint32_t ntl = (hi - lo + kTile - 1) / kTile;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
+    ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    uint32_t running = chunk_base[blockIdx.x * kRadix + tid];  // thread d carries digit d's next row
+    // thread t < 128 carries the next output rows of digits 2t and 2t + 1
+    uint32_t run0 = 0, run1 = 0;
+    if (tid < kRadix / 2) {
+        run0 = chunk_base[blockIdx.x * kRadix + 2 * tid];
+        run1 = chunk_base[blockIdx.x * kRadix + 2 * tid + 1];
+    }
 
     auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * kTile <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
@@ -512,85 +550,96 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         const int b = i & 1;
         const uint32_t base = lo + i * kTile;
         const uint32_t valid = min(hi - base, (uint32_t)kTile);
-        for (int x = tid; x < kWarps * (kRadix + 1); x += kThreads) (&sm.whist[0][0])[x] = 0;
+        for (int x = tid; x < kSWarps * (kRadix / 2 + 1); x += kSThreads) (&sm.whist2[0][0])[x] = 0;
         if (bulk_tile(i)) {
             uint32_t polls = 0;
             while (!mbar_try_wait(&sm.mbar[b], phase[b]))
                 if (wait_expired(polls, spin_limit, status)) break;
             phase[b] ^= 1u;
         } else {
-            for (uint32_t s = tid; s < valid; s += kThreads) {
+            for (uint32_t s = tid; s < valid; s += kSThreads) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
             }
         }
         __syncthreads();
 
-        uint64_t k[kIpt];
-        uint32_t p[kIpt];
-        const uint32_t wofs = warp * 32 * kIpt + lane;
+        // rows of this thread: warp w owns 32 * kSIpt consecutive rows
+        uint64_t k[kSIpt];
+        uint32_t p[kSIpt], dg[kSIpt], rank[kSIpt];
+        const uint32_t wofs = warp * 32 * kSIpt + lane;
 #pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
+        for (int j = 0; j < kSIpt; ++j) {
             k[j] = sm.keys[b][wofs + j * 32];
             p[j] = sm.ptrs[b][wofs + j * 32];
+            dg[j] = (wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
         }
-        // warp multisplit (see onesweep_kernel)
-        uint32_t rank[kIpt];
+        // warp multisplit (see onesweep_kernel); the peers of a row come from
+        // digit-bit ballots (9 bits when the tile has rows past the end)
         const uint32_t lt = lanemask_lt();
+        const bool full = valid == (uint32_t)kTile;
 #pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t d = (wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        for (int j = 0; j < kSIpt; ++j) {
+            const uint32_t peers = full ? warp_peers<kRadixBits>(dg[j]) : warp_peers<kRadixBits + 1>(dg[j]);
             const int leader = __ffs(peers) - 1;
             uint32_t c = 0;
-            if ((int)lane == leader) c = atomicAdd(&sm.whist[warp][d], (uint32_t)__popc(peers));
-            rank[j] = __popc(peers & lt) + __shfl_sync(0xffffffffu, c, leader);
+            const uint32_t sh = (dg[j] & 1u) * 16u;
+            if ((int)lane == leader) c = atomicAdd(&sm.whist2[warp][dg[j] >> 1], (uint32_t)__popc(peers) << sh);
+            rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
         }
         __syncthreads();
 
-        const uint32_t d = tid;
-        uint32_t cnt = 0;
+        // per digit pair (threads 0..127): warp offsets, tile counts, local starts
+        uint32_t c0 = 0, c1 = 0, x = 0;
+        if (tid < kRadix / 2) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = sm.whist[w][d];
-            sm.whist[w][d] = cnt;
-            cnt += c;
-        }
-        uint32_t x = cnt;
+            for (int w = 0; w < kSWarps; ++w) {
+                const uint32_t word = sm.whist2[w][tid];
+                sm.whist2[w][tid] = c0 | (c1 << 16);
+                c0 += word & 0xFFFFu;
+                c1 += word >> 16;
+            }
+            x = c0 + c1;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= (uint32_t)o) x += y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane == 31) sm.scan_tmp[warp] = x;
         }
-        if (lane == 31) sm.scan_tmp[warp] = x;
         __syncthreads();
-        uint32_t before = 0;
+        if (tid < kRadix / 2) {
+            uint32_t before = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
-        const uint32_t lstart = before + x - cnt;
-        sm.local_start[d] = lstart;
-        sm.gbase_rel[d] = running - lstart;
-        running += cnt;
+            for (int w = 0; w < 4; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
+            const uint32_t l0 = before + x - c0 - c1, l1 = l0 + c0;
+            sm.local_start[2 * tid] = l0;
+            sm.local_start[2 * tid + 1] = l1;
+            sm.gbase_rel[2 * tid] = run0 - l0;
+            sm.gbase_rel[2 * tid + 1] = run1 - l1;
+            run0 += c0;
+            run1 += c1;
+        }
         __syncthreads();
 
 #pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            if (wofs + j * 32 < valid) {
-                const uint32_t dj = digit_of(k[j]);
-                const uint32_t slot = sm.local_start[dj] + sm.whist[warp][dj] + rank[j];
+        for (int j = 0; j < kSIpt; ++j) {
+            if (dg[j] < kRadix) {
+                const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
+                const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
                 sm.keys[b][slot] = k[j];
                 sm.ptrs[b][slot] = p[j];
+                sm.dig[slot] = static_cast<uint8_t>(dg[j]);
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = tid + j * kThreads;
+        for (int j = 0; j < kSIpt; ++j) {
+            const uint32_t s = tid + j * kSThreads;
             if (s < valid) {
-                const uint64_t kk = sm.keys[b][s];
-                const uint32_t g = sm.gbase_rel[digit_of(kk)] + s;
+                const uint32_t g = sm.gbase_rel[sm.dig[s]] + s;
                 if (g < n) {
-                    out_k[g] = kk;
+                    out_k[g] = sm.keys[b][s];
                     out_p[g] = sm.ptrs[b][s];
                 }
             }
@@ -670,16 +719,17 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     if (n >= kChunkedMinRows) {
         auto scat = chunk_scatter_kernel<ValueFn>;
-        SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const size_t ssmem = sizeof(ScatterSmem);
+        SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
         int per_sm = 0;
-        SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kThreads, smem));
+        SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, ssmem));
         if (per_sm < 1) per_sm = 1;
         const uint64_t want = min_u64(min_u64(ntiles, (uint64_t)sms * per_sm), kMaxChunks);
         const uint32_t chunk = (uint32_t)(((ntiles + want - 1) / want) * kTile);
         const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
         for (int pos = 0; pos < kPositions; ++pos) {
             SBH_TIMED("sort_count", s,
-                      chunk_count_kernel<ValueFn><<<nchunks, 256, 0, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_hist,
+                      chunk_count_kernel<ValueFn><<<nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_hist,
                                                                           value_of));
             SBH_LAUNCHED();
             SBH_TIMED("sort_chunk_scan", s,
@@ -687,7 +737,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                                                            sc.chunk_base));
             SBH_LAUNCHED();
             SBH_TIMED("sort_scatter", s,
-                      scat<<<nchunks, kThreads, smem, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_base, value_of,
+                      scat<<<nchunks, kSThreads, ssmem, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_base, value_of,
                                                            bulk_ok, limit, status));
             SBH_LAUNCHED();
         }

@@ -24,6 +24,11 @@ SBH_FAULT_NONE, SBH_FAULT_SKIP_PUBLISH = 0, 1
 TOPK_PAD_VAL = 0
 TOPK_PAD_PTR = 0xFFFFFFFF
 TOPK_MAX_K = 8
+MLP_PARAMS = 1153
+LEARNED_MODEL_BYTES = 16384
+LEARNED_CAPACITY = 8192
+LEARNED_STATS = ("bucket_ids", "heavy_cells", "sorted_buckets", "one_key_buckets", "heavy_buckets",
+                 "overflow_buckets", "overflow_rows", "largest_bucket")
 
 _ERRNAMES = {1: "SBH_EINVAL", 2: "SBH_ENOSPACE", 3: "SBH_ETIMEOUT", 4: "SBH_ECUDA"}
 
@@ -55,6 +60,10 @@ def _load() -> ctypes.CDLL:
         "sbh_group_reduce_noalloc": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp], i32),
         "sbh_topk": ([vp, vp, u64, vp, i32, i32, vp, vp, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_join": ([vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_mlp_forward": ([vp, vp, u64, vp, vp], i32),
+        "sbh_mlp_grad": ([vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
+        "sbh_learned_train": ([vp, u64, u64, vp, i32, i32, ctypes.c_float, vp, vp, vp, vp, vp, sz, vp], i32),
+        "sbh_kpa_sort_learned": ([vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -67,7 +76,8 @@ _lib = _load()
 EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
             "sbh_profile_enable", "sbh_profile_collect",
             "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_sort", "sbh_kpa_merge", "sbh_group_reduce",
-            "sbh_group_reduce_noalloc",
+            "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
+            "sbh_kpa_sort_learned",
             "sbh_topk", "sbh_join")
 
 
@@ -293,3 +303,61 @@ def window_ranges(ts, starts, length):
     re_ = _u64(starts.numel(), ts.device)
     sbh_window_ranges(ts, starts, length, rb, re_)
     return rb, re_
+
+
+# ----------------------------------------------------------------- learned partition
+def sbh_mlp_forward(params, x, y, stream=None):
+    _check(_lib.sbh_mlp_forward(_p(params), _p(x), x.numel(), _p(y), _stream(stream)), "sbh_mlp_forward")
+
+
+def sbh_mlp_grad(params, x, t, grad, loss=None, stream=None):
+    args = (_p(params), _p(x), _p(t), x.numel(), _p(grad), _p(loss))
+    return _scratch(_lib.sbh_mlp_grad, args, (_stream(stream),), "sbh_mlp_grad", x.device)
+
+
+def sbh_learned_train(samples, n_rows, init_params, steps, batch, lr, model, losses=None, train_x=None,
+                      train_t=None, stream=None):
+    args = (_p(samples), samples.numel(), n_rows, _p(init_params), steps, batch, ctypes.c_float(lr), _p(model),
+            _p(losses), _p(train_x), _p(train_t))
+    return _scratch(_lib.sbh_learned_train, args, (_stream(stream),), "sbh_learned_train", samples.device)
+
+
+def sbh_kpa_sort_learned(keys_in, ptrs_in, keys_out, ptrs_out, model, scratch=None, stream=None):
+    """Returns the stats as a dict (the call synchronises the stream once)."""
+    st = (ctypes.c_uint64 * len(LEARNED_STATS))()
+    args = (_p(keys_in), _p(ptrs_in), _p(keys_out), _p(ptrs_out), keys_in.numel(), _p(model),
+            ctypes.cast(st, ctypes.c_void_p))
+    if scratch is None:
+        _scratch(_lib.sbh_kpa_sort_learned, args, (_stream(stream),), "sbh_kpa_sort_learned", keys_in.device)
+    else:
+        nbytes = ctypes.c_size_t(scratch.numel())
+        _check(_lib.sbh_kpa_sort_learned(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)),
+               "sbh_kpa_sort_learned")
+    return dict(zip(LEARNED_STATS, list(st)))
+
+
+def sort_learned_scratch_bytes(n: int) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_kpa_sort_learned(None, None, None, None, n, None, None, None, ctypes.byref(nbytes), None),
+           "sbh_kpa_sort_learned")
+    return nbytes.value
+
+
+def learned_train(samples, n_rows, init_params, steps=150, batch=4096, lr=2e-2):
+    """Model blob (uint8 CUDA tensor) and the per-step batch losses."""
+    dev = samples.device
+    model = torch.zeros(LEARNED_MODEL_BYTES, dtype=torch.uint8, device=dev)
+    losses = torch.zeros(max(1, steps), dtype=torch.float32, device=dev)
+    sbh_learned_train(samples, n_rows, init_params, steps, batch, lr, model, losses)
+    return model, losses[:steps]
+
+
+def model_params(model):
+    """The network weights inside a model blob (a float32 view)."""
+    return model[: MLP_PARAMS * 4].view(torch.float32)
+
+
+def sort_learned(keys, ptrs, model):
+    out = (torch.empty_like(keys), torch.empty_like(ptrs))
+    stats = sbh_kpa_sort_learned(keys, ptrs, out[0], out[1], model)
+    return out[0], out[1], stats

@@ -1,0 +1,147 @@
+"""The learned partition sort on the GPU: its network's forward pass and
+gradient against the FP64 oracle (tolerances, not bit-exact: FP32 sums), the
+training set against the oracle's (exact inputs, FP32 targets), and the
+sorted output, which must equal the plain sort bit for bit.  The last test
+shows what the trained network gains over the untrained one."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from oracle import learned as olearned
+from oracle import mlp as omlp
+from tests.gpu_util import cuda, host, same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import sbh
+    return sbh
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, 0.5, omlp.N_PARAMS).astype(np.float32)
+
+
+def test_mlp_forward_matches_oracle(S):
+    p = _params(1)
+    x = gen.unif01(3, 1, 10_000).astype(np.float32)
+    y = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    S.sbh_mlp_forward(cuda(p), cuda(x), y)
+    ref, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64))
+    # FP32 evaluation of 32-term sums: error well below 1e-5 of the output scale
+    assert np.max(np.abs(host(y) - ref)) <= 2e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("m", [1, 255, 256, 4097, 20_000])
+def test_mlp_grad_matches_oracle(S, m):
+    p = _params(2)
+    x = gen.unif01(4, 1, m).astype(np.float32)
+    t = gen.unif01(4, 2, m).astype(np.float32)
+    g = torch.empty(S.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    S.sbh_mlp_grad(cuda(p), cuda(x), cuda(t), g, loss)
+    ref = omlp.backward(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    got = host(g).astype(np.float64)
+    # FP32 accumulation over m rows in blocks of 256: relative error ~1e-6;
+    # the bound is 1e-4 of the largest gradient plus 1e-4 of each entry
+    tol = 1e-4 * np.max(np.abs(ref)) + 1e-4 * np.abs(ref)
+    assert np.all(np.abs(got - ref) <= tol)
+    ref_loss = omlp.loss(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(float(host(loss)[0]) - ref_loss) <= 1e-4 * ref_loss
+    # repeated calls give identical bits
+    g2 = torch.empty_like(g)
+    S.sbh_mlp_grad(cuda(p), cuda(x), cuda(t), g2)
+    assert torch.equal(g, g2)
+
+
+def _sample(n, seed=gen.SEED_MIXED):
+    col = gen.mixed_keys(n, seed=seed)
+    return col, col[::100].copy()
+
+
+def test_training_set_and_heavy_cells_match_oracle(S):
+    n = 4_000_000
+    col, sample = _sample(n)
+    init = gen.mlp_init()
+    model = torch.zeros(S.LEARNED_MODEL_BYTES, dtype=torch.uint8, device="cuda")
+    tx = torch.zeros(sample.size, dtype=torch.float32, device="cuda")
+    tt = torch.zeros(sample.size, dtype=torch.float32, device="cuda")
+    S.sbh_learned_train(cuda(sample), n, cuda(init), 0, 4096, 1e-2, model, None, tx, tt)
+    torch.cuda.synchronize()
+    heavy = olearned.heavy_cells(sample, n, S.LEARNED_CAPACITY)
+    ox, ot = olearned.training_set(sample, n, S.LEARNED_CAPACITY)
+    blob = host(model)
+    words = blob.view(np.uint32)
+    hdr = omlp.N_PARAMS
+    assert words[hdr + 1] == heavy.sum() and words[hdr + 2] == ox.size
+    bits = words[hdr + 4: hdr + 4 + (olearned.NCELL + 31) // 32]
+    got_heavy = np.unpackbits(bits.view(np.uint8), bitorder="little")[: olearned.NCELL].astype(bool)
+    assert np.array_equal(got_heavy, heavy)
+    m2 = ox.size
+    assert np.array_equal(host(tx)[:m2], ox.astype(np.float32))  # features are exact in FP32
+    assert np.max(np.abs(host(tt)[:m2] - ot)) <= 1e-6
+    # the weights are the initial ones when no step runs
+    assert np.array_equal(blob[: hdr * 4].view(np.float32), init)
+
+
+def test_training_follows_oracle_first_steps_and_learns(S):
+    n = 4_000_000
+    col, sample = _sample(n)
+    init = gen.mlp_init()
+    ox, ot = olearned.training_set(sample, n, S.LEARNED_CAPACITY)
+    # one step: Adam's first update against the FP64 statement, on parameters
+    # whose gradient is not near zero (the first step moves by lr * sign(g))
+    model1, _ = S.learned_train(cuda(sample), n, cuda(init), steps=1, batch=4096, lr=1e-3)
+    p1 = host(S.model_params(model1)).astype(np.float64)
+    g = omlp.backward(init.astype(np.float64), ox[:4096], ot[:4096])
+    e1, _, _ = omlp.adam_step(init.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    big = np.abs(g) > 1e-2 * np.max(np.abs(g))
+    assert np.max(np.abs(p1[big] - e1[big])) <= 1e-5
+    # many steps: the batch loss falls by more than 20x
+    model, losses = S.learned_train(cuda(sample), n, cuda(init), steps=150, batch=4096, lr=2e-2)
+    L = host(losses)
+    assert L[-10:].mean() < L[:3].mean() / 20
+
+
+@pytest.mark.parametrize("n,kind", [(1, "mixed"), (5000, "mixed"), (3_000_017, "mixed"), (2_500_000, "uniform"),
+                                    (2_100_000, "equal"), (2_200_000, "highbyte")])
+def test_learned_sort_equals_plain_sort(S, n, kind):
+    if kind == "mixed":
+        col = gen.mixed_keys(n, seed=7)
+    elif kind == "uniform":
+        col = gen.uniform(7, 1, n, 0, 0, np.uint64)
+    elif kind == "equal":
+        col = np.full(n, 12345, dtype=np.uint64)
+    else:
+        col = gen.uniform(7, 2, n, 0, 256, np.uint64) << np.uint64(56)
+    sample = col[::100].copy()
+    model, _ = S.learned_train(cuda(sample), n, cuda(gen.mlp_init()), steps=150, batch=4096, lr=2e-2)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp, stats = S.sort_learned(keys, ptrs, model)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+    assert stats["overflow_rows"] <= n
+
+
+def test_learned_sort_mixed_keys_32m_and_trained_vs_untrained(S):
+    n = 32_000_000
+    col, sample = _sample(n)
+    d_sample, init = cuda(sample), cuda(gen.mlp_init())
+    trained, _ = S.learned_train(d_sample, n, init, steps=150, batch=4096, lr=2e-2)
+    untrained, _ = S.learned_train(d_sample, n, init, steps=0, batch=4096, lr=2e-2)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp, st_tr = S.sort_learned(keys, ptrs, trained)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+    sk2, sp2, st_un = S.sort_learned(keys, ptrs, untrained)
+    assert same(sk2, ok) and same(sp2, op)
+    # the trained network keeps far more rows out of the fallback sort
+    assert st_tr["overflow_rows"] < 0.05 * n
+    assert st_un["overflow_rows"] > 5 * max(st_tr["overflow_rows"], 1)
