@@ -249,6 +249,7 @@ __global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, const flo
 struct TrainScratch {
     uint64_t* s_keys;    // sorted sample (m)
     uint32_t* s_ptrs;
+    uint32_t* i_ptrs;    // 0 .. m-1, the sort's input pointers
     uint64_t* nh;        // non-heavy sorted samples (m)
     uint32_t* flags;     // m + 1 (compaction)
     uint64_t* block_sums;
@@ -273,6 +274,7 @@ TrainScratch train_carve(void* base, uint64_t m) {
     TrainScratch t;
     t.s_keys = c.take<uint64_t>(m);
     t.s_ptrs = c.take<uint32_t>(m);
+    t.i_ptrs = c.take<uint32_t>(m);
     t.nh = c.take<uint64_t>(m);
     t.flags = c.take<uint32_t>(m + 1);
     t.block_sums = c.take<uint64_t>((m + kCompactTile - 1) / kCompactTile + 1);
@@ -945,9 +947,9 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // sort the sample
     const unsigned gm = (unsigned)((m + 255) / 256);
-    SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.s_ptrs, m));
+    SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.i_ptrs, m));
     SBH_LAUNCHED();
-    rc = sort_by_value(d_samples, t.s_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions);
+    rc = sort_by_value(d_samples, t.i_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions);
     if (rc) return rc;
     // heavy cells, non-heavy compaction, training rows
     SBH_TIMED("learned_heavy", s, heavy_kernel<<<gm, 256, 0, s>>>(t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY, model));
