@@ -231,7 +231,7 @@ int sbh_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint
  *     with m'), input x(key), target (#samples < key + #samples <= key) / 2m';
  *  4. `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, rate lr) on batches of
  *     `batch` rows, step j using rows (j * batch + q) mod m', starting from
- *     d_init_params.  batch is a multiple of 32, at most 8192.
+ *     d_init_params.  batch is a multiple of 128, at most 32768.
  * d_model (SBH_LEARNED_MODEL_BYTES, device) receives the weights and the
  * heavy cells.  d_losses (nullable, `steps` floats) receives each step's
  * batch loss before its update; d_train_x / d_train_t (nullable, m floats

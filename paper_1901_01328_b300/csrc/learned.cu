@@ -136,15 +136,15 @@ __device__ float slice_grad(GradSmem& sm, int S, float norm) {
         sq += r * r;
     }
     __syncthreads();
-    // w3, b3
+    // w3, b3 (four interleaved partial sums, combined in a fixed order)
     for (int o = tid; o <= kH; o += kGThreads) {
-        float g = 0.f;
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
         if (o < kH) {
-            for (int s = 0; s < S; ++s) g = fmaf(sm.DY[s], fmaxf(sm.A2[s][o], 0.f), g);
-            sm.G[oW3 + o] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.DY[s], fmaxf(sm.A2[s][o], 0.f), g[s & 3]);
+            sm.G[oW3 + o] = (g[0] + g[1]) + (g[2] + g[3]);
         } else {
-            for (int s = 0; s < S; ++s) g += sm.DY[s];
-            sm.G[oB3] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] += sm.DY[s];
+            sm.G[oB3] = (g[0] + g[1]) + (g[2] + g[3]);
         }
     }
     __syncthreads();
@@ -156,15 +156,15 @@ __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     __syncthreads();
     // W2, b2
     for (int e = tid; e < kH * kH + kH; e += kGThreads) {
-        float g = 0.f;
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
         if (e < kH * kH) {
             const int o = e / kH, i = e % kH;
-            for (int s = 0; s < S; ++s) g = fmaf(sm.A2[s][o], fmaxf(sm.A1[s][i], 0.f), g);
-            sm.G[oW2 + e] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.A2[s][o], fmaxf(sm.A1[s][i], 0.f), g[s & 3]);
+            sm.G[oW2 + e] = (g[0] + g[1]) + (g[2] + g[3]);
         } else {
             const int o = e - kH * kH;
-            for (int s = 0; s < S; ++s) g += sm.A2[s][o];
-            sm.G[oB2 + o] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] += sm.A2[s][o];
+            sm.G[oB2 + o] = (g[0] + g[1]) + (g[2] + g[3]);
         }
     }
     __syncthreads();
@@ -180,13 +180,13 @@ __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     }
     __syncthreads();
     for (int i = tid; i < 2 * kH; i += kGThreads) {
-        float g = 0.f;
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
         if (i < kH) {
-            for (int s = 0; s < S; ++s) g = fmaf(sm.A1[s][i], sm.X[s], g);
-            sm.G[oW1 + i] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.A1[s][i], sm.X[s], g[s & 3]);
+            sm.G[oW1 + i] = (g[0] + g[1]) + (g[2] + g[3]);
         } else {
-            for (int s = 0; s < S; ++s) g += sm.A1[s][i - kH];
-            sm.G[oB1 + i - kH] = g;
+            for (int s = 0; s < S; ++s) g[s & 3] += sm.A1[s][i - kH];
+            sm.G[oB1 + i - kH] = (g[0] + g[1]) + (g[2] + g[3]);
         }
     }
     // sum of squared errors: warp shuffles, then warp totals in order
@@ -266,7 +266,7 @@ struct TrainScratch {
     size_t total;
 };
 
-constexpr int kTrainCtas = 32;
+constexpr int kTrainCtas = 128;  // batch rows per CTA = batch / 128
 constexpr int kCompactTile = 1024;
 
 TrainScratch train_carve(void* base, uint64_t m) {
@@ -610,17 +610,20 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
     }
 }
 
-// bstart[b] = first row whose bucket id is >= b, for b in [0, nbid].
-__global__ void bucket_bounds_kernel(const uint64_t* __restrict__ keys, uint32_t n, BucketValue fn,
-                                     const uint32_t* __restrict__ nbid_p, uint32_t* __restrict__ bstart) {
+// bstart[b] = first row whose bucket id is >= b, for b in [0, nbid].  Each
+// row's id is computed once; lane 0 also computes the id of the row before.
+__global__ void __launch_bounds__(256) bucket_bounds_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                            BucketValue fn, const uint32_t* __restrict__ nbid_p,
+                                                            uint32_t* __restrict__ bstart) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const uint32_t nbid = *nbid_p;
-    const uint32_t id = static_cast<uint32_t>(fn(keys[i]));
-    const int64_t prev = i ? static_cast<int64_t>(fn(keys[i - 1])) : -1;
-    for (int64_t b = prev + 1; b <= (int64_t)id; ++b) bstart[b] = i;
+    const int64_t id = i < n ? static_cast<int64_t>(fn(ld_stream(keys + i))) : 0;
+    int64_t prev = __shfl_up_sync(0xffffffffu, id, 1);
+    if (lane_id() == 0) prev = (i > 0 && i <= n) ? static_cast<int64_t>(fn(keys[i - 1])) : -1;
+    if (i >= n) return;
+    for (int64_t b = prev + 1; b <= id; ++b) bstart[b] = i;
     if (i == n - 1)
-        for (uint32_t b = id + 1; b <= nbid; ++b) bstart[b] = n;
+        for (uint32_t b = static_cast<uint32_t>(id) + 1; b <= nbid; ++b) bstart[b] = n;
 }
 
 // In-shared-memory sort of each bucket of at most kCap rows.
@@ -629,6 +632,10 @@ constexpr int kBThreads = 512;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBIpt = kCap / kBThreads;
 
+constexpr int kFineBits = 12;
+constexpr int kFineBins = 1 << kFineBits;
+constexpr uint32_t kFineMaxBin = 32;  // larger sub-buckets take the radix passes
+
 struct BucketSmem {
     uint64_t keys[2][kCap];
     uint32_t ptrs[2][kCap];
@@ -636,6 +643,8 @@ struct BucketSmem {
     uint32_t local_start[kRadix];
     uint32_t scan_tmp[4];
     uint64_t red[2][kBWarps];
+    uint32_t bins[kFineBins];  // counting placement by the top bits of key - kmin
+    uint32_t bin_tmp[kBWarps];
     uint32_t bucket;
 };
 
@@ -703,6 +712,80 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             continue;  // one key value: already in ptr order
         }
         const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
+        if (bits > kRadixBits) {
+            // Counting placement by the top 12 bits of key - kmin (keys spread
+            // almost evenly inside a bucket), then an insertion sort by (key,
+            // ptr) inside every sub-bucket.  Taken only when no sub-bucket
+            // exceeds kFineMaxBin rows.
+            const int fsh = bits > kFineBits ? bits - kFineBits : 0;
+            for (int x = tid; x < kFineBins; x += kBThreads) sm.bins[x] = 0;
+            __syncthreads();
+            for (uint32_t r = tid; r < cnt; r += kBThreads)
+                atomicAdd(&sm.bins[static_cast<uint32_t>((sm.keys[0][r] - kmin) >> fsh)], 1u);
+            __syncthreads();
+            // exclusive scan over the bins: 8 consecutive bins per thread
+            constexpr int kPer = kFineBins / kBThreads;
+            uint32_t v[kPer], tsum = 0, bmax = 0;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                v[q] = sm.bins[tid * kPer + q];
+                tsum += v[q];
+                bmax = max(bmax, v[q]);
+            }
+            uint32_t x = tsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            const int big = __syncthreads_or(bmax > kFineMaxBin);
+            if (lane == 31) sm.bin_tmp[warp] = x;
+            __syncthreads();
+            if (!big) {
+                uint32_t run = x - tsum;
+                for (int w = 0; w < (int)warp; ++w) run += sm.bin_tmp[w];
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    sm.bins[tid * kPer + q] = run;  // next free row of the bin
+                    run += v[q];
+                }
+                __syncthreads();
+                for (uint32_t r = tid; r < cnt; r += kBThreads) {
+                    const uint64_t k = sm.keys[0][r];
+                    const uint32_t pos = atomicAdd(&sm.bins[static_cast<uint32_t>((k - kmin) >> fsh)], 1u);
+                    sm.keys[1][pos] = k;
+                    sm.ptrs[1][pos] = sm.ptrs[0][r];
+                }
+                __syncthreads();
+                // bins[d] now holds the end of bin d
+#pragma unroll 1
+                for (int q = 0; q < kPer; ++q) {
+                    const int d = tid * kPer + q;
+                    const uint32_t e2 = sm.bins[d], b2 = e2 - v[q];
+                    for (uint32_t i2 = b2 + 1; i2 < e2; ++i2) {
+                        const uint64_t kk = sm.keys[1][i2];
+                        const uint32_t pp = sm.ptrs[1][i2];
+                        uint32_t j2 = i2;
+                        while (j2 > b2 && (sm.keys[1][j2 - 1] > kk ||
+                                           (sm.keys[1][j2 - 1] == kk && sm.ptrs[1][j2 - 1] > pp))) {
+                            sm.keys[1][j2] = sm.keys[1][j2 - 1];
+                            sm.ptrs[1][j2] = sm.ptrs[1][j2 - 1];
+                            --j2;
+                        }
+                        sm.keys[1][j2] = kk;
+                        sm.ptrs[1][j2] = pp;
+                    }
+                }
+                __syncthreads();
+                for (uint32_t r = tid; r < cnt; r += kBThreads) {
+                    keys[s + r] = sm.keys[1][r];
+                    ptrs[s + r] = sm.ptrs[1][r];
+                }
+                if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
+                __syncthreads();
+                continue;
+            }
+        }
         const int passes = (bits + kRadixBits - 1) / kRadixBits;
         int a = 0;
         for (int pass = 0; pass < passes; ++pass) {
@@ -812,21 +895,28 @@ __global__ void __launch_bounds__(1024) overflow_list_kernel(const uint32_t* __r
     if (threadIdx.x == 0) { *nlist = carry_c; *rows_total = carry_r; }
 }
 
-// One CTA per overflow bucket: copy its rows to (to_gather) or from the
-// compact buffer.
+// Copies the rows of the listed overflow buckets to (to_gather) or from the
+// compact buffer; row r of the compact buffer belongs to the last listed
+// bucket whose offset is <= r.
 __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs,
                                      const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ list,
-                                     const uint32_t* __restrict__ offs, uint64_t* __restrict__ ck,
-                                     uint32_t* __restrict__ cp, int to_gather) {
-    const uint32_t b = list[blockIdx.x];
-    const uint32_t s = bstart[b], len = bstart[b + 1] - s, o = offs[blockIdx.x];
-    for (uint32_t r = threadIdx.x; r < len; r += blockDim.x) {
+                                     const uint32_t* __restrict__ offs, uint32_t nl, uint32_t rows,
+                                     uint64_t* __restrict__ ck, uint32_t* __restrict__ cp, int to_gather) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        uint32_t lo = 0, hi = nl;  // last j with offs[j] <= r
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (offs[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t src = bstart[list[lo]] + (r - offs[lo]);
         if (to_gather) {
-            ck[o + r] = keys[s + r];
-            cp[o + r] = ptrs[s + r];
+            ck[r] = keys[src];
+            cp[r] = ptrs[src];
         } else {
-            keys[s + r] = ck[o + r];
-            ptrs[s + r] = cp[o + r];
+            keys[src] = ck[r];
+            ptrs[src] = cp[r];
         }
     }
 }
@@ -1046,15 +1136,16 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SBH_CUDA(cudaStreamSynchronize(s));
     const uint32_t nl = small_h[2], rows = small_h[3];
     if (nl > 0) {
+        const unsigned mg = (unsigned)min_u64((rows + 255) / 256, (uint64_t)num_sms() * 8);
         SBH_TIMED("learned_overflow_move", s,
-                  overflow_move_kernel<<<nl, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, t.ck, t.cp,
-                                                          1));
+                  overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,
+                                                          t.ck, t.cp, 1));
         SBH_LAUNCHED();
         rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, rows, t.sort_scratch, s, RadixValue{}, kPositions);
         if (rc) return rc;
         SBH_TIMED("learned_overflow_move", s,
-                  overflow_move_kernel<<<nl, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, t.ck, t.cp,
-                                                          0));
+                  overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,
+                                                          t.ck, t.cp, 0));
         SBH_LAUNCHED();
     }
     if (h_stats) {
