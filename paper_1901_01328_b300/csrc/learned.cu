@@ -507,8 +507,15 @@ __global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
         b1t *= b1;
         b2t *= b2;
         for (int i = p0 + threadIdx.x; i < p1; i += kGThreads) {
+            // sum in CTA order; loads issued sixteen at a time
             float g = 0.f;
-            for (int q = 0; q < G; ++q) g += a.partial[q * (size_t)kNP + i];
+            for (int q0 = 0; q0 < G; q0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = q0 + u < G ? a.partial[(q0 + u) * (size_t)kNP + i] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) g += v[u];
+            }
             const float mi = b1 * a.adam_m[i] + (1.f - b1) * g;
             const float vi = b2 * a.adam_v[i] + (1.f - b2) * g * g;
             a.adam_m[i] = mi;
@@ -518,7 +525,13 @@ __global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
         }
         if (c == 0 && threadIdx.x == 0 && a.losses) {
             float l = 0.f;
-            for (int q = 0; q < G; ++q) l += a.partial_sq[q];
+            for (int q0 = 0; q0 < G; q0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = q0 + u < G ? a.partial_sq[q0 + u] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) l += v[u];
+            }
             a.losses[step] = l / static_cast<float>(a.batch);
         }
         __threadfence();
@@ -1039,7 +1052,8 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     const unsigned gm = (unsigned)((m + 255) / 256);
     SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.i_ptrs, m));
     SBH_LAUNCHED();
-    rc = sort_by_value(d_samples, t.i_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions);
+    rc = sort_by_value(d_samples, t.i_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions,
+                       "learned_sample");
     if (rc) return rc;
     // heavy cells, non-heavy compaction, training rows
     SBH_TIMED("learned_heavy", s, heavy_kernel<<<gm, 256, 0, s>>>(t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY, model));
@@ -1110,7 +1124,7 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SBH_LAUNCHED();
     const BucketValue fn{t.tbl, model->heavy_bits};
     // stable scatter by bucket id (ids fit in 24 bits: three digit positions)
-    rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3);
+    rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3, "learned_ids");
     if (rc) return rc;
     SBH_TIMED("learned_bounds", s,
               bucket_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_keys_out, (uint32_t)n, fn, nbid,
@@ -1141,7 +1155,8 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                   overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,
                                                           t.ck, t.cp, 1));
         SBH_LAUNCHED();
-        rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, rows, t.sort_scratch, s, RadixValue{}, kPositions);
+        rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, rows, t.sort_scratch, s, RadixValue{}, kPositions,
+                           "learned_overflow");
         if (rc) return rc;
         SBH_TIMED("learned_overflow_move", s,
                   overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,

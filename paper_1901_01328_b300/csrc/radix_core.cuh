@@ -23,6 +23,8 @@
 //             temporary buffer).
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace sbh {
@@ -693,7 +695,11 @@ inline SortScratch sort_carve(void* scratch, uint64_t n) {
 // positions at or above npos of the value are treated as zero.
 template <typename ValueFn>
 int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
-                  void* scratch, cudaStream_t s, ValueFn value_of, int npos) {
+                  void* scratch, cudaStream_t s, ValueFn value_of, int npos, const char* tag = "sort") {
+    // profile names: <tag>_upsweep, <tag>_scatter, ...
+    const std::string t(tag);
+    const std::string n_up = t + "_upsweep", n_plan = t + "_plan", n_count = t + "_count", n_scan = t + "_chunk_scan",
+                      n_scat = t + "_scatter", n_one = t + "_onesweep", n_copy = t + "_copy";
     if (n == 0) return SBH_OK;
     const int in_place = (in_k == out_k);
     if (in_place != (in_p == out_p)) {
@@ -705,9 +711,9 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
     const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
-    SBH_TIMED("sort_upsweep", s, upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
+    SBH_TIMED(n_up.c_str(), s, upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
     SBH_LAUNCHED();
-    SBH_TIMED("sort_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
+    SBH_TIMED(n_plan.c_str(), s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
     SBH_LAUNCHED();
     Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
     const size_t smem = sizeof(SortSmem);
@@ -728,15 +734,15 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
         const uint32_t chunk = (uint32_t)(((ntiles + want - 1) / want) * kTile);
         const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
         for (int pos = 0; pos < kPositions; ++pos) {
-            SBH_TIMED("sort_count", s,
+            SBH_TIMED(n_count.c_str(), s,
                       chunk_count_kernel<ValueFn><<<nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_hist,
                                                                           value_of));
             SBH_LAUNCHED();
-            SBH_TIMED("sort_chunk_scan", s,
+            SBH_TIMED(n_scan.c_str(), s,
                       chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, nchunks, sc.gbase,
                                                            sc.chunk_base));
             SBH_LAUNCHED();
-            SBH_TIMED("sort_scatter", s,
+            SBH_TIMED(n_scat.c_str(), s,
                       scat<<<nchunks, kSThreads, ssmem, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_base, value_of,
                                                            bulk_ok, limit, status));
             SBH_LAUNCHED();
@@ -750,7 +756,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
         const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)sms * per_sm);
         const int fault = take_fault();
         for (int pos = 0; pos < kPositions; ++pos) {
-            SBH_TIMED("sort_onesweep", s,
+            SBH_TIMED(n_one.c_str(), s,
                       kern<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
                                                         fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status, value_of,
                                                         bulk_ok));
@@ -758,7 +764,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
         }
     }
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
-    SBH_TIMED("sort_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan));
+    SBH_TIMED(n_copy.c_str(), s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan));
     SBH_LAUNCHED();
     return SBH_OK;
 }
