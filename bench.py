@@ -275,7 +275,9 @@ def run_gpu(args):
     algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
                   "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
                   "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
-                  "learned_bucket_sort": PAIR_BYTES * 2 * n, "learned_bounds": 8 * n}
+                  "learned_ids_scatter": PAIR_BYTES * 2 * n, "learned_ids_count": 8 * n,
+                  "learned_ids_upsweep": 8 * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
+                  "learned_bounds": 8 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9

@@ -550,16 +550,18 @@ __global__ void finish_model_kernel(const float* __restrict__ params, const uint
 
 // ------------------------------------------------------------------ partition
 // Bucket id of a key (see the file comment).
+// One 8-byte entry per cell, so an id costs a single table load: x = the
+// cell's first bucket id, y = its number of buckets, or kHeavyCell.
+constexpr uint32_t kHeavyCell = 0xFFFFFFFFu;
+
 struct BucketValue {
-    const uint32_t* tbl;         // kNCell + 1 first-bucket ids
-    const uint32_t* heavy_bits;  // heavy cells
+    const uint2* cells;  // kNCell + 1 entries
     __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
         uint32_t f;
         const uint32_t c = key_cell(k, &f);
-        const uint32_t b0 = __ldg(tbl + c);
-        if ((__ldg(heavy_bits + (c >> 5)) >> (c & 31)) & 1u) return b0 + 1;
-        const uint32_t cnt = __ldg(tbl + c + 1) - b0;
-        return b0 + static_cast<uint32_t>((static_cast<uint64_t>(f) * cnt) >> 32);
+        const uint2 e = __ldg(cells + c);
+        if (e.y == kHeavyCell) return e.x + 1;
+        return e.x + static_cast<uint32_t>((static_cast<uint64_t>(f) * e.y) >> 32);
     }
 };
 
@@ -577,6 +579,7 @@ constexpr int kTblThreads = 1024;
 __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __restrict__ model,
                                                                  const float* __restrict__ F, uint32_t nb,
                                                                  uint32_t* __restrict__ tbl,
+                                                                 uint2* __restrict__ cells,
                                                                  uint32_t* __restrict__ heavy_bucket_bits,
                                                                  uint32_t* __restrict__ nbid) {
     __shared__ float s_max[kTblThreads];
@@ -620,6 +623,14 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
             ++heavy_before;
         }
         if (c == kNCell) *nbid = t + 1;
+    }
+    __syncthreads();
+    for (uint32_t c = c0; c < c1; ++c) {
+        uint2 e;
+        e.x = tbl[c];
+        if (c == kNCell) e.y = 0;
+        else e.y = is_heavy(model->heavy_bits, c) ? kHeavyCell : tbl[c + 1] - tbl[c];
+        cells[c] = e;
     }
 }
 
@@ -936,6 +947,7 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 
 struct SortLearnedScratch {
     uint32_t* tbl;          // kNCell + 1
+    uint2* cells;           // kNCell + 1
     float* F;               // kNCell + 1
     uint32_t* heavy_bucket_bits;
     uint32_t* bstart;       // max ids + 1
@@ -960,6 +972,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     SortLearnedScratch t;
     const uint64_t ids = learned_max_ids(n);
     t.tbl = c.take<uint32_t>(kNCell + 1);
+    t.cells = c.take<uint2>(kNCell + 1);
     t.F = c.take<float>(kNCell + 1);
     t.list = c.take<uint32_t>(ids);
     t.offs = c.take<uint32_t>(ids);
@@ -1120,9 +1133,10 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<(kNCell + 1 + 255) / 256, 256, 0, s>>>(model, t.F));
     SBH_LAUNCHED();
     SBH_TIMED("learned_table", s,
-              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.heavy_bucket_bits, nbid));
+              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.cells, t.heavy_bucket_bits,
+                                                          nbid));
     SBH_LAUNCHED();
-    const BucketValue fn{t.tbl, model->heavy_bits};
+    const BucketValue fn{t.cells};
     // stable scatter by bucket id (ids fit in 24 bits: three digit positions)
     rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3, "learned_ids");
     if (rc) return rc;

@@ -23,6 +23,7 @@
 //             temporary buffer).
 #pragma once
 
+#include <cstdlib>
 #include <string>
 
 #include "common.cuh"
@@ -488,12 +489,12 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
 // the same tile, to hide the latency of the ranking chain.
 constexpr int kSThreads = 512;
 constexpr int kSWarps = kSThreads / 32;
-constexpr int kSIpt = kTile / kSThreads;
 
+template <int TILE>
 struct ScatterSmem {
-    uint64_t keys[2][kTile];  // double-buffered input tiles, reused to stage
-    uint32_t ptrs[2][kTile];  // the scatter in digit order
-    uint8_t dig[kTile];       // digit of each staged row
+    uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
+    uint32_t ptrs[2][TILE];  // the scatter in digit order
+    uint8_t dig[TILE];       // digit of each staged row
     // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
     // word 128 holds the sentinel digit of rows past the end)
     uint32_t whist2[kSWarps][kRadix / 2 + 1];
@@ -503,8 +504,8 @@ struct ScatterSmem {
     uint64_t mbar[2];
 };
 
-template <typename ValueFn>
-__global__ void __launch_bounds__(kSThreads, 2)
+template <typename ValueFn, int TILE>
+__global__ void __launch_bounds__(kSThreads, TILE <= 4096 ? 2 : 1)
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
                      uint32_t* __restrict__ status) {
@@ -518,10 +519,11 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint32_t lo = blockIdx.x * chunk;
     const uint32_t hi = min(n, lo + chunk);
     if (lo >= hi) return;
-    const uint32_t ntl = (hi - lo + kTile - 1) / kTile;
+    const uint32_t ntl = (hi - lo + TILE - 1) / TILE;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    ScatterSmem<TILE>& sm = *reinterpret_cast<ScatterSmem<TILE>*>(smem_raw);
+    constexpr int kSIpt = TILE / kSThreads;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
     // thread t < 128 carries the next output rows of digits 2t and 2t + 1
     uint32_t run0 = 0, run1 = 0;
@@ -530,12 +532,12 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         run1 = chunk_base[blockIdx.x * kRadix + 2 * tid + 1];
     }
 
-    auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * kTile <= hi; };
+    auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * TILE <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
         if (i < ntl && bulk_tile(i)) {
-            mbar_expect_tx(&sm.mbar[b], kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
-            bulk_load(sm.keys[b], in_k + lo + (size_t)i * kTile, kTile * sizeof(uint64_t), &sm.mbar[b]);
-            bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
+            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t)));
+            bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b]);
+            bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
         }
     };
     if (tid == 0) {
@@ -550,8 +552,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
 
     for (uint32_t i = 0; i < ntl; ++i) {
         const int b = i & 1;
-        const uint32_t base = lo + i * kTile;
-        const uint32_t valid = min(hi - base, (uint32_t)kTile);
+        const uint32_t base = lo + i * TILE;
+        const uint32_t valid = min(hi - base, (uint32_t)TILE);
         for (int x = tid; x < kSWarps * (kRadix / 2 + 1); x += kSThreads) (&sm.whist2[0][0])[x] = 0;
         if (bulk_tile(i)) {
             uint32_t polls = 0;
@@ -579,7 +581,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         // warp multisplit (see onesweep_kernel); the peers of a row come from
         // digit-bit ballots (9 bits when the tile has rows past the end)
         const uint32_t lt = lanemask_lt();
-        const bool full = valid == (uint32_t)kTile;
+        const bool full = valid == (uint32_t)TILE;
 #pragma unroll
         for (int j = 0; j < kSIpt; ++j) {
             const uint32_t peers = full ? warp_peers<kRadixBits>(dg[j]) : warp_peers<kRadixBits + 1>(dg[j]);
@@ -724,14 +726,20 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     if (n >= kChunkedMinRows) {
-        auto scat = chunk_scatter_kernel<ValueFn>;
-        const size_t ssmem = sizeof(ScatterSmem);
+        // scatter tile: 4096 rows (two CTAs per SM) or, with SBH_SCATTER_TILE=8192, 8192 rows (one CTA per SM)
+        static const int tile_rows = [] {
+            const char* e = getenv("SBH_SCATTER_TILE");
+            return (e && atoi(e) == 8192) ? 8192 : 4096;
+        }();
+        auto scat = tile_rows == 8192 ? chunk_scatter_kernel<ValueFn, 8192> : chunk_scatter_kernel<ValueFn, 4096>;
+        const size_t ssmem = tile_rows == 8192 ? sizeof(ScatterSmem<8192>) : sizeof(ScatterSmem<4096>);
         SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
         int per_sm = 0;
         SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, ssmem));
         if (per_sm < 1) per_sm = 1;
         const uint64_t want = min_u64(min_u64(ntiles, (uint64_t)sms * per_sm), kMaxChunks);
-        const uint32_t chunk = (uint32_t)(((ntiles + want - 1) / want) * kTile);
+        const uint64_t ttiles = (n + tile_rows - 1) / tile_rows;
+        const uint32_t chunk = (uint32_t)(((ttiles + want - 1) / want) * tile_rows);
         const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
         for (int pos = 0; pos < kPositions; ++pos) {
             SBH_TIMED(n_count.c_str(), s,
