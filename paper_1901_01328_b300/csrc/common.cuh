@@ -189,6 +189,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Shared-memory atomic add done only where pred holds, without a branch
+// (returns the old value there, 0 elsewhere).
+__device__ __forceinline__ uint32_t smem_atomic_add_if(bool pred, uint32_t* addr, uint32_t v) {
+    uint32_t old = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n @p atom.shared.add.u32 %0, [%1], %3;\n}\n"
+        : "+r"(old)
+        : "r"(smem_addr(addr)), "r"(static_cast<uint32_t>(pred)), "r"(v)
+        : "memory");
+    return old;
+}
+
 // Streaming (evict-first) loads and stores for data touched once.
 __device__ __forceinline__ uint64_t ld_stream(const uint64_t* p) { return __ldcs(reinterpret_cast<const unsigned long long*>(p)); }
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(reinterpret_cast<const unsigned int*>(p)); }

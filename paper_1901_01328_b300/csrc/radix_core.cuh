@@ -555,10 +555,14 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         const uint32_t base = lo + i * TILE;
         const uint32_t valid = min(hi - base, (uint32_t)TILE);
         for (int x = tid; x < kSWarps * (kRadix / 2 + 1); x += kSThreads) (&sm.whist2[0][0])[x] = 0;
+        bool expired = false;
         if (bulk_tile(i)) {
             uint32_t polls = 0;
             while (!mbar_try_wait(&sm.mbar[b], phase[b]))
-                if (wait_expired(polls, spin_limit, status)) break;
+                if (wait_expired(polls, spin_limit, status)) {
+                    expired = true;
+                    break;
+                }
             phase[b] ^= 1u;
         } else {
             for (uint32_t s = tid; s < valid; s += kSThreads) {
@@ -566,30 +570,44 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
             }
         }
-        __syncthreads();
+        // a tile whose data never arrived is not scattered (its rows stay unwritten)
+        const bool tile_ok = !__syncthreads_or(expired);
 
         // rows of this thread: warp w owns 32 * kSIpt consecutive rows
         uint64_t k[kSIpt];
         uint32_t p[kSIpt], dg[kSIpt], rank[kSIpt];
         const uint32_t wofs = warp * 32 * kSIpt + lane;
+        const bool full = valid == (uint32_t)TILE;
 #pragma unroll
         for (int j = 0; j < kSIpt; ++j) {
             k[j] = sm.keys[b][wofs + j * 32];
             p[j] = sm.ptrs[b][wofs + j * 32];
-            dg[j] = (wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
+            dg[j] = (full || wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
         }
-        // warp multisplit (see onesweep_kernel); the peers of a row come from
-        // digit-bit ballots (9 bits when the tile has rows past the end)
+        // warp multisplit (see onesweep_kernel): the peers of a row come from
+        // digit-bit ballots (a ninth bit when the tile has rows past the end);
+        // the group leader's counter update is predicated, not branched
         const uint32_t lt = lanemask_lt();
-        const bool full = valid == (uint32_t)TILE;
+        if (full) {
 #pragma unroll
-        for (int j = 0; j < kSIpt; ++j) {
-            const uint32_t peers = full ? warp_peers<kRadixBits>(dg[j]) : warp_peers<kRadixBits + 1>(dg[j]);
-            const int leader = __ffs(peers) - 1;
-            uint32_t c = 0;
-            const uint32_t sh = (dg[j] & 1u) * 16u;
-            if ((int)lane == leader) c = atomicAdd(&sm.whist2[warp][dg[j] >> 1], (uint32_t)__popc(peers) << sh);
-            rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
+            for (int j = 0; j < kSIpt; ++j) {
+                const uint32_t peers = warp_peers<kRadixBits>(dg[j]);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t sh = (dg[j] & 1u) * 16u;
+                const uint32_t c = smem_atomic_add_if((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
+                                                      (uint32_t)__popc(peers) << sh);
+                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kSIpt; ++j) {
+                const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t sh = (dg[j] & 1u) * 16u;
+                const uint32_t c = smem_atomic_add_if((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
+                                                      (uint32_t)__popc(peers) << sh);
+                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
+            }
         }
         __syncthreads();
 
@@ -626,23 +644,42 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         }
         __syncthreads();
 
+        if (full) {
 #pragma unroll
-        for (int j = 0; j < kSIpt; ++j) {
-            if (dg[j] < kRadix) {
+            for (int j = 0; j < kSIpt; ++j) {
                 const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
                 const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
                 sm.keys[b][slot] = k[j];
                 sm.ptrs[b][slot] = p[j];
                 sm.dig[slot] = static_cast<uint8_t>(dg[j]);
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kSIpt; ++j) {
+                if (dg[j] < kRadix) {
+                    const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
+                    const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
+                    sm.keys[b][slot] = k[j];
+                    sm.ptrs[b][slot] = p[j];
+                    sm.dig[slot] = static_cast<uint8_t>(dg[j]);
+                }
+            }
         }
         __syncthreads();
+        if (tile_ok && full) {
 #pragma unroll
-        for (int j = 0; j < kSIpt; ++j) {
-            const uint32_t s = tid + j * kSThreads;
-            if (s < valid) {
+            for (int j = 0; j < kSIpt; ++j) {
+                const uint32_t s = tid + j * kSThreads;
                 const uint32_t g = sm.gbase_rel[sm.dig[s]] + s;
-                if (g < n) {
+                out_k[g] = sm.keys[b][s];
+                out_p[g] = sm.ptrs[b][s];
+            }
+        } else if (tile_ok) {
+#pragma unroll
+            for (int j = 0; j < kSIpt; ++j) {
+                const uint32_t s = tid + j * kSThreads;
+                if (s < valid) {
+                    const uint32_t g = sm.gbase_rel[sm.dig[s]] + s;
                     out_k[g] = sm.keys[b][s];
                     out_p[g] = sm.ptrs[b][s];
                 }
