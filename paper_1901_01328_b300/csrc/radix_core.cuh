@@ -589,9 +589,12 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         // the group leader's counter update is predicated, not branched
         const uint32_t lt = lanemask_lt();
         if (full) {
+            // half the items find their peers with match.any, half with digit
+            // ballots: the two run on different pipes, so neither saturates
 #pragma unroll
             for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t peers = warp_peers<kRadixBits>(dg[j]);
+                const uint32_t peers =
+                    (j & 1) ? __match_any_sync(0xffffffffu, dg[j]) : warp_peers<kRadixBits>(dg[j]);
                 const int leader = __ffs(peers) - 1;
                 const uint32_t sh = (dg[j] & 1u) * 16u;
                 const uint32_t c = smem_atomic_add_if((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
