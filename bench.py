@@ -164,7 +164,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 SAMPLE_STRIDE = 100        # 1% sample for the learned partitioner
-TRAIN = dict(steps=150, batch=4096, lr=2e-2)
+TRAIN = dict(steps=40, batch=16384, lr=4e-2)
 
 
 def run_gpu(args):
