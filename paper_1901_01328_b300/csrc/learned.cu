@@ -607,11 +607,6 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
     }
     float run_max = threadIdx.x ? s_max[threadIdx.x - 1] : 0.f;
     uint32_t heavy_before = threadIdx.x ? s_cnt[threadIdx.x - 1] : 0u;
-    // Keep every id below 2^16 when that costs at most a quarter of the
-    // buckets: the scatter by bucket id then takes two digit passes, not three.
-    const uint32_t heavy_total = s_cnt[kTblThreads - 1];
-    const uint32_t fit16 = 65536u - 2u * heavy_total - 2u;
-    if (heavy_total < 16384u && nb > fit16 && fit16 >= nb - nb / 4) nb = fit16;
     const float fnb = static_cast<float>(nb);
     for (uint32_t c = c0; c < c1; ++c) {
         run_max = fmaxf(run_max, F[c]);
@@ -945,6 +940,156 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
     }
 }
 
+// ------------------------------------------------------------------ carried bucket ids
+// When every bucket id fits in 16 bits, each row's id is computed once, kept
+// in a 16-bit array, and moved with the row through both digit passes; the
+// counts and the bucket bounds then read ids instead of recomputing them.
+constexpr int kCarryTile = 3072;
+
+__global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                          BucketValue fn, uint16_t* __restrict__ ids,
+                                                          uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[2 * kRadix];
+    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    uint32_t last0 = 0, run0 = 0, last1 = 0, run1 = 0;
+    auto add = [&](uint32_t id) {
+        const uint32_t d0 = id & 255u, d1 = id >> 8;
+        if (d0 == last0) ++run0;
+        else { if (run0) atomicAdd(&h[last0], run0); last0 = d0; run0 = 1; }
+        if (d1 == last1) ++run1;
+        else { if (run1) atomicAdd(&h[kRadix + last1], run1); last1 = d1; run1 = 1; }
+    };
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+        const uint32_t id = static_cast<uint32_t>(fn(ld_stream(keys + i)));
+        ids[i] = static_cast<uint16_t>(id);
+        add(id);
+    }
+    if (run0) atomicAdd(&h[last0], run0);
+    if (run1) atomicAdd(&h[kRadix + last1], run1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int p = 2; p < kPositions; ++p) atomicAdd(&ghist[p * kRadix], n);
+}
+
+__global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
+                                                         uint32_t chunk, uint32_t* __restrict__ chunk_hist) {
+    if (!plan->active[pos]) return;
+    __shared__ uint32_t h[kRadix];
+    const uint16_t* __restrict__ v = buf.vals(plan->src[pos]);
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    const int sh = pos * kRadixBits;
+    uint32_t last = 0, run = 0;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t d = (static_cast<uint32_t>(v[i]) >> sh) & (kRadix - 1);
+        if (d == last) ++run;
+        else { if (run) atomicAdd(&h[last], run); last = d; run = 1; }
+    }
+    if (run) atomicAdd(&h[last], run);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
+}
+
+// Bucket bounds from the sorted ids (the plan tells where they ended up).
+__global__ void __launch_bounds__(256) ids_bounds_kernel(Buffers buf, const Plan* __restrict__ plan, uint32_t n,
+                                                         const uint32_t* __restrict__ nbid_p,
+                                                         uint32_t* __restrict__ bstart) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint16_t* __restrict__ v = plan->npasses ? buf.out_v : buf.in_v;
+    const uint32_t nbid = *nbid_p;
+    const int64_t id = v[i];
+    const int64_t prev = i ? static_cast<int64_t>(v[i - 1]) : -1;
+    for (int64_t b = prev + 1; b <= id; ++b) bstart[b] = i;
+    if (i == n - 1)
+        for (uint32_t b = static_cast<uint32_t>(id) + 1; b <= nbid; ++b) bstart[b] = n;
+}
+
+struct CarryScratch {
+    uint64_t* tmp_k;
+    uint32_t* tmp_p;
+    uint16_t* ids_in;
+    uint16_t* ids_tmp;
+    uint16_t* ids_out;
+    uint32_t* gbase;
+    Plan* plan;
+    uint32_t* chunk_hist;
+    uint32_t* chunk_base;
+    uint32_t* hist;  // zeroed
+    size_t total;
+};
+
+CarryScratch carry_carve(void* base, uint64_t n) {
+    Carver c(base);
+    CarryScratch t;
+    t.tmp_k = c.take<uint64_t>(n);
+    t.tmp_p = c.take<uint32_t>(n);
+    t.ids_in = c.take<uint16_t>(n);
+    t.ids_tmp = c.take<uint16_t>(n);
+    t.ids_out = c.take<uint16_t>(n);
+    t.gbase = c.take<uint32_t>(kPositions * kRadix);
+    t.plan = c.take<Plan>(1);
+    t.chunk_hist = c.take<uint32_t>(kMaxChunks * kRadix);
+    t.chunk_base = c.take<uint32_t>(kMaxChunks * kRadix);
+    t.hist = c.take<uint32_t>(kPositions * kRadix);
+    t.total = c.bytes();
+    return t;
+}
+
+// Stable sort by 16-bit bucket id with the ids carried along; fills bstart.
+int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
+                        void* scratch, cudaStream_t s, BucketValue fn, const uint32_t* nbid, uint32_t* bstart) {
+    CarryScratch cs = carry_carve(scratch, n);
+    const uint32_t n32 = static_cast<uint32_t>(n);
+    const int sms = num_sms();
+    SBH_CUDA(cudaMemsetAsync(cs.hist, 0, kPositions * kRadix * sizeof(uint32_t), s));
+    const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
+    SBH_TIMED("learned_ids_upsweep", s, ids_upsweep_kernel<<<up_blocks, 256, 0, s>>>(in_k, n32, fn, cs.ids_in, cs.hist));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_ids_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(cs.hist, n32, cs.gbase, cs.plan, 0));
+    SBH_LAUNCHED();
+    Buffers b{in_k, in_p, cs.tmp_k, cs.tmp_p, out_k, out_p};
+    b.in_v = cs.ids_in;
+    b.tmp_v = cs.ids_tmp;
+    b.out_v = cs.ids_out;
+    auto scat = chunk_scatter_kernel<RadixValue, kCarryTile, true>;
+    const size_t smem = sizeof(ScatterSmem<kCarryTile, true>);
+    SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ttiles = (n + kCarryTile - 1) / kCarryTile;
+    const uint64_t want = min_u64(min_u64(ttiles, (uint64_t)sms * per_sm), kMaxChunks);
+    const uint32_t chunk = (uint32_t)(((ttiles + want - 1) / want) * kCarryTile);
+    const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
+    const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
+                          reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
+    for (int pos = 0; pos < 2; ++pos) {
+        SBH_TIMED("learned_ids_count", s,
+                  ids_count_kernel<<<nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, chunk, cs.chunk_hist));
+        SBH_LAUNCHED();
+        SBH_TIMED("learned_ids_chunk_scan", s,
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, nchunks, cs.gbase, cs.chunk_base));
+        SBH_LAUNCHED();
+        SBH_TIMED("learned_ids_scatter", s,
+                  scat<<<nchunks, kSThreads, smem, s>>>(b, n32, pos, cs.plan, chunk, cs.chunk_base, RadixValue{},
+                                                        bulk_ok, spin_limit(), status_word()));
+        SBH_LAUNCHED();
+    }
+    const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
+    SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_bounds", s,
+              ids_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
 struct SortLearnedScratch {
     uint32_t* tbl;          // kNCell + 1
     uint2* cells;           // kNCell + 1
@@ -985,7 +1130,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.zero_bytes = c.off - z0;
     t.ck = c.take<uint64_t>(n);
     t.cp = c.take<uint32_t>(n);
-    t.sort_scratch = c.take<char>(sort_carve(nullptr, n).total);
+    t.sort_scratch = c.take<char>(std::max(sort_carve(nullptr, n).total, carry_carve(nullptr, n).total));
     t.total = c.bytes();
     return t;
 }
@@ -1125,7 +1270,19 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SortLearnedScratch t = learned_carve(d_scratch, n);
     const Model* model = static_cast<const Model*>(d_model);
     SBH_CUDA(cudaMemsetAsync(t.heavy_bucket_bits, 0, t.zero_bytes, s));
-    const uint32_t nb = (uint32_t)learned_nb(n);
+    // bucket count: about two buckets per capacity; when every id can stay
+    // below 2^16 for at most a quarter fewer buckets, keep them there so the
+    // ids are carried in 16 bits through two digit passes
+    uint32_t heavy = 0;
+    SBH_CUDA(cudaMemcpyAsync(&heavy, &model->heavy_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SBH_CUDA(cudaStreamSynchronize(s));
+    uint64_t nb64 = learned_nb(n);
+    if (heavy < 16384) {
+        const uint64_t fit16 = 65536ull - 2ull * heavy - 2ull;
+        if (nb64 > fit16 && fit16 >= nb64 - nb64 / 4) nb64 = fit16;
+    }
+    const uint32_t nb = (uint32_t)nb64;
+    const bool carry = nb64 + 2ull * heavy + 2ull <= 65536ull;
     uint32_t* nbid = t.small + 0;
     uint32_t* counter = t.small + 1;
     uint32_t* nlist = t.small + 2;
@@ -1137,13 +1294,19 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                                                           nbid));
     SBH_LAUNCHED();
     const BucketValue fn{t.cells};
-    // stable scatter by bucket id (ids fit in 24 bits: three digit positions)
-    rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3, "learned_ids");
-    if (rc) return rc;
-    SBH_TIMED("learned_bounds", s,
-              bucket_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_keys_out, (uint32_t)n, fn, nbid,
-                                                                               t.bstart));
-    SBH_LAUNCHED();
+    if (carry) {
+        rc = sort_by_carried_ids(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, nbid,
+                                 t.bstart);
+        if (rc) return rc;
+    } else {
+        // stable scatter by bucket id computed from the key (ids below 2^24)
+        rc = sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, 3, "learned_ids");
+        if (rc) return rc;
+        SBH_TIMED("learned_bounds", s,
+                  bucket_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_keys_out, (uint32_t)n, fn, nbid,
+                                                                                   t.bstart));
+        SBH_LAUNCHED();
+    }
     const size_t smem = sizeof(BucketSmem);
     SBH_CUDA(cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SBH_TIMED("learned_bucket_sort", s,

@@ -25,6 +25,7 @@
 
 #include <cstdlib>
 #include <string>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -60,6 +61,13 @@ struct Buffers {
     uint32_t* tmp_p;
     uint64_t* out_k;
     uint32_t* out_p;
+    // optional 16-bit values carried with the rows (the learned sort's bucket
+    // ids); null when the digit comes from the key
+    const uint16_t* in_v = nullptr;
+    uint16_t* tmp_v = nullptr;
+    uint16_t* out_v = nullptr;
+    __device__ __forceinline__ const uint16_t* vals(int sel) const { return sel == 0 ? in_v : (sel == 1 ? tmp_v : out_v); }
+    __device__ __forceinline__ uint16_t* wvals(int sel) const { return sel == 1 ? tmp_v : out_v; }
     __device__ __forceinline__ const uint64_t* keys(int sel) const { return sel == 0 ? in_k : (sel == 1 ? tmp_k : out_k); }
     __device__ __forceinline__ const uint32_t* ptrs(int sel) const { return sel == 0 ? in_p : (sel == 1 ? tmp_p : out_p); }
     __device__ __forceinline__ uint64_t* wkeys(int sel) const { return sel == 1 ? tmp_k : out_k; }
@@ -490,21 +498,22 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
 constexpr int kSThreads = 512;
 constexpr int kSWarps = kSThreads / 32;
 
-template <int TILE>
+template <int TILE, bool kCarry>
 struct ScatterSmem {
+    using Tag = typename std::conditional<kCarry, uint16_t, uint8_t>::type;
     uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
     uint32_t ptrs[2][TILE];  // the scatter in digit order
-    uint8_t dig[TILE];       // digit of each staged row
+    Tag dig[TILE];           // digit (or carried value) of each staged row
     // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
     // word 128 holds the sentinel digit of rows past the end)
     uint32_t whist2[kSWarps][kRadix / 2 + 1];
-    uint32_t local_start[kRadix];
+    uint16_t local_start[kRadix];
     uint32_t gbase_rel[kRadix];
     uint32_t scan_tmp[4];
     uint64_t mbar[2];
 };
 
-template <typename ValueFn, int TILE>
+template <typename ValueFn, int TILE, bool kCarry = false>
 __global__ void __launch_bounds__(kSThreads, TILE <= 4096 ? 2 : 1)
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
@@ -516,13 +525,15 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint32_t* __restrict__ in_p = buf.ptrs(src);
     uint64_t* __restrict__ out_k = buf.wkeys(dst);
     uint32_t* __restrict__ out_p = buf.wptrs(dst);
+    const uint16_t* __restrict__ in_v = kCarry ? buf.vals(src) : nullptr;
+    uint16_t* __restrict__ out_v = kCarry ? buf.wvals(dst) : nullptr;
     const uint32_t lo = blockIdx.x * chunk;
     const uint32_t hi = min(n, lo + chunk);
     if (lo >= hi) return;
     const uint32_t ntl = (hi - lo + TILE - 1) / TILE;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    ScatterSmem<TILE>& sm = *reinterpret_cast<ScatterSmem<TILE>*>(smem_raw);
+    ScatterSmem<TILE, kCarry>& sm = *reinterpret_cast<ScatterSmem<TILE, kCarry>*>(smem_raw);
     constexpr int kSIpt = TILE / kSThreads;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
     // thread t < 128 carries the next output rows of digits 2t and 2t + 1
@@ -575,14 +586,21 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
 
         // rows of this thread: warp w owns 32 * kSIpt consecutive rows
         uint64_t k[kSIpt];
-        uint32_t p[kSIpt], dg[kSIpt], rank[kSIpt];
+        uint32_t p[kSIpt], dg[kSIpt], rank[kSIpt], cv[kSIpt];
         const uint32_t wofs = warp * 32 * kSIpt + lane;
         const bool full = valid == (uint32_t)TILE;
+        if (kCarry) {
+            // carried values come straight from global memory (coalesced)
+#pragma unroll
+            for (int j = 0; j < kSIpt; ++j)
+                cv[j] = (full || wofs + j * 32 < valid) ? in_v[base + wofs + j * 32] : 0u;
+        }
 #pragma unroll
         for (int j = 0; j < kSIpt; ++j) {
             k[j] = sm.keys[b][wofs + j * 32];
             p[j] = sm.ptrs[b][wofs + j * 32];
-            dg[j] = (full || wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
+            if (kCarry) dg[j] = (full || wofs + j * 32 < valid) ? (cv[j] >> (pos * kRadixBits)) & (kRadix - 1) : kRadix;
+            else dg[j] = (full || wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
         }
         // warp multisplit (see onesweep_kernel): the peers of a row come from
         // digit-bit ballots (a ninth bit when the tile has rows past the end);
@@ -654,7 +672,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                 const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
                 sm.keys[b][slot] = k[j];
                 sm.ptrs[b][slot] = p[j];
-                sm.dig[slot] = static_cast<uint8_t>(dg[j]);
+                sm.dig[slot] = static_cast<typename ScatterSmem<TILE, kCarry>::Tag>(kCarry ? cv[j] : dg[j]);
             }
         } else {
 #pragma unroll
@@ -664,27 +682,32 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                     const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
                     sm.keys[b][slot] = k[j];
                     sm.ptrs[b][slot] = p[j];
-                    sm.dig[slot] = static_cast<uint8_t>(dg[j]);
+                    sm.dig[slot] = static_cast<typename ScatterSmem<TILE, kCarry>::Tag>(kCarry ? cv[j] : dg[j]);
                 }
             }
         }
         __syncthreads();
+        auto digit_at = [&](uint32_t s) -> uint32_t {
+            return kCarry ? (static_cast<uint32_t>(sm.dig[s]) >> (pos * kRadixBits)) & (kRadix - 1) : sm.dig[s];
+        };
         if (tile_ok && full) {
 #pragma unroll
             for (int j = 0; j < kSIpt; ++j) {
                 const uint32_t s = tid + j * kSThreads;
-                const uint32_t g = sm.gbase_rel[sm.dig[s]] + s;
+                const uint32_t g = sm.gbase_rel[digit_at(s)] + s;
                 out_k[g] = sm.keys[b][s];
                 out_p[g] = sm.ptrs[b][s];
+                if (kCarry) out_v[g] = sm.dig[s];
             }
         } else if (tile_ok) {
 #pragma unroll
             for (int j = 0; j < kSIpt; ++j) {
                 const uint32_t s = tid + j * kSThreads;
                 if (s < valid) {
-                    const uint32_t g = sm.gbase_rel[sm.dig[s]] + s;
+                    const uint32_t g = sm.gbase_rel[digit_at(s)] + s;
                     out_k[g] = sm.keys[b][s];
                     out_p[g] = sm.ptrs[b][s];
+                    if (kCarry) out_v[g] = sm.dig[s];
                 }
             }
         }
@@ -772,7 +795,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
             return (e && atoi(e) == 8192) ? 8192 : 4096;
         }();
         auto scat = tile_rows == 8192 ? chunk_scatter_kernel<ValueFn, 8192> : chunk_scatter_kernel<ValueFn, 4096>;
-        const size_t ssmem = tile_rows == 8192 ? sizeof(ScatterSmem<8192>) : sizeof(ScatterSmem<4096>);
+        const size_t ssmem = tile_rows == 8192 ? sizeof(ScatterSmem<8192, false>) : sizeof(ScatterSmem<4096, false>);
         SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
         int per_sm = 0;
         SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, ssmem));
