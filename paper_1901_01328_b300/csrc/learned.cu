@@ -985,29 +985,66 @@ __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n
     const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
     const int sh = pos * kRadixBits;
     uint32_t last = 0, run = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const uint32_t d = (static_cast<uint32_t>(v[i]) >> sh) & (kRadix - 1);
+    auto add = [&](uint32_t id) {
+        const uint32_t d = (id >> sh) & (kRadix - 1);
         if (d == last) ++run;
         else { if (run) atomicAdd(&h[last], run); last = d; run = 1; }
+    };
+    uint32_t done = lo;
+    if (lo < hi && (reinterpret_cast<uintptr_t>(v + lo) & 15) == 0) {
+        // eight ids per 16-byte load
+        const uint32_t nq = (hi - lo) / 8;
+        const uint4* q = reinterpret_cast<const uint4*>(v + lo);
+        for (uint32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+            const uint4 w = __ldcs(q + i);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                add(ws[u] & 0xFFFFu);
+                add(ws[u] >> 16);
+            }
+        }
+        done = lo + nq * 8;
     }
+    for (uint32_t i = done + threadIdx.x; i < hi; i += blockDim.x) add(v[i]);
     if (run) atomicAdd(&h[last], run);
     __syncthreads();
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
 }
 
 // Bucket bounds from the sorted ids (the plan tells where they ended up).
+// Each thread takes eight consecutive rows.
 __global__ void __launch_bounds__(256) ids_bounds_kernel(Buffers buf, const Plan* __restrict__ plan, uint32_t n,
                                                          const uint32_t* __restrict__ nbid_p,
                                                          uint32_t* __restrict__ bstart) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 8;
+    if (i0 >= n) return;
     const uint16_t* __restrict__ v = plan->npasses ? buf.out_v : buf.in_v;
     const uint32_t nbid = *nbid_p;
-    const int64_t id = v[i];
-    const int64_t prev = i ? static_cast<int64_t>(v[i - 1]) : -1;
-    for (int64_t b = prev + 1; b <= id; ++b) bstart[b] = i;
-    if (i == n - 1)
-        for (uint32_t b = static_cast<uint32_t>(id) + 1; b <= nbid; ++b) bstart[b] = n;
+    uint32_t id[8];
+    if (i0 + 8 <= n && (reinterpret_cast<uintptr_t>(v + i0) & 15) == 0) {
+        const uint4 w = *reinterpret_cast<const uint4*>(v + i0);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            id[2 * u] = ws[u] & 0xFFFFu;
+            id[2 * u + 1] = ws[u] >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) id[u] = i0 + u < n ? v[i0 + u] : 0u;
+    }
+    int64_t prev = i0 ? static_cast<int64_t>(v[i0 - 1]) : -1;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const uint64_t i = i0 + u;
+        if (i < n) {
+            for (int64_t b = prev + 1; b <= (int64_t)id[u]; ++b) bstart[b] = static_cast<uint32_t>(i);
+            if (i == n - 1)
+                for (uint32_t b = id[u] + 1; b <= nbid; ++b) bstart[b] = n;
+            prev = id[u];
+        }
+    }
 }
 
 struct CarryScratch {
@@ -1085,7 +1122,7 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds", s,
-              ids_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
+              ids_bounds_kernel<<<(unsigned)((n + 2047) / 2048), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
     SBH_LAUNCHED();
     return SBH_OK;
 }

@@ -503,6 +503,7 @@ struct ScatterSmem {
     using Tag = typename std::conditional<kCarry, uint16_t, uint8_t>::type;
     uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
     uint32_t ptrs[2][TILE];  // the scatter in digit order
+    uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried values of the input tiles
     Tag dig[TILE];           // digit (or carried value) of each staged row
     // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
     // word 128 holds the sentinel digit of rows past the end)
@@ -546,9 +547,10 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * TILE <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
         if (i < ntl && bulk_tile(i)) {
-            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t)));
+            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t) + (kCarry ? sizeof(uint16_t) : 0)));
             bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b]);
             bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
+            if (kCarry) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
         }
     };
     if (tid == 0) {
@@ -579,6 +581,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             for (uint32_t s = tid; s < valid; s += kSThreads) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
+                if (kCarry) sm.vals[b][s] = in_v[base + s];
             }
         }
         // a tile whose data never arrived is not scattered (its rows stay unwritten)
@@ -590,10 +593,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         const uint32_t wofs = warp * 32 * kSIpt + lane;
         const bool full = valid == (uint32_t)TILE;
         if (kCarry) {
-            // carried values come straight from global memory (coalesced)
 #pragma unroll
-            for (int j = 0; j < kSIpt; ++j)
-                cv[j] = (full || wofs + j * 32 < valid) ? in_v[base + wofs + j * 32] : 0u;
+            for (int j = 0; j < kSIpt; ++j) cv[j] = sm.vals[b][wofs + j * 32];
         }
 #pragma unroll
         for (int j = 0; j < kSIpt; ++j) {
