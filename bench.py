@@ -334,10 +334,133 @@ def run_gpu(args):
                                  "learned_stats": stats,
                                  "overflow_row_rate": stats.get("overflow_rows", 0) / n},
             "stages": stages,
+            "rows": row_suite(peak) if ws == 1 and not args.no_rows else None,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ per-row measurements
+def row_suite(peak):
+    """Each remaining row of the path on its workload shape: device time by
+    CUDA events (median of 5 after 2 warm-ups), algorithmic GB/s against the
+    HBM peak, and the oracle on the same input (one host thread)."""
+    import torch
+
+    import gen
+    import oracle
+    from paper_1901_01328_b300 import sbh
+
+    dev = torch.device("cuda")
+    out = {}
+
+    def dev_ms(fn, reps=5):
+        ts = []
+        for r in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def cpu_ms(fn):
+        t0 = time.perf_counter()
+        fn()
+        return 1e3 * (time.perf_counter() - t0)
+
+    def entry(ms, nbytes, shape, oms):
+        gbs = nbytes / (ms / 1e3) / 1e9 if nbytes else None
+        return {"ms": ms, "algorithmic_gbs": gbs, "frac_of_hbm": (gbs / peak if gbs else None), "shape": shape,
+                "oracle_ms": oms}
+
+    # A1 window ranges: 509 sliding windows (1M rows, stride 250K) over 128M timestamps
+    nrow = 128_000_000
+    ts = torch.arange(nrow, dtype=torch.int64, device=dev).to(torch.uint64)
+    starts = torch.arange(0, 509 * 250_000, 250_000, dtype=torch.int64, device=dev).to(torch.uint64)
+    rb = torch.empty(509, dtype=torch.uint64, device=dev)
+    re_ = torch.empty_like(rb)
+    ms = dev_ms(lambda: sbh.sbh_window_ranges(ts, starts, 1_000_000, rb, re_))
+    ts_h = np.arange(4_000_000, dtype=np.uint64)
+    oms = cpu_ms(lambda: oracle.window_ranges(ts_h, np.array([0, 250_000, 500_000, 750_000], np.uint64), 1_000_000))
+    out["A1_window_ranges"] = entry(ms, None, "509 windows over 128M u64 timestamps (oracle: 4 windows over 4M rows)",
+                                    oms)
+    del ts
+
+    # A5 merge: one window of the join workload = 4 sorted panes of 250K rows
+    s = gen.join_streams(1_000_000)
+    col = s["L"]["keys"]
+    d_col = torch.from_numpy(col).to(dev)
+    panes = [sbh.sort(*sbh.extract(d_col, i * 250_000, 250_000)) for i in range(4)]
+    total = 1_000_000
+    mk = torch.empty(total, dtype=torch.uint64, device=dev)
+    mp = torch.empty(total, dtype=torch.uint32, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_kpa_merge(panes, mk, mp))
+    hp = [(p[0].cpu().numpy(), p[1].cpu().numpy()) for p in panes]
+    oms = cpu_ms(lambda: oracle.merge(hp))
+    out["A5_merge"] = entry(ms, 2 * 24 * total, "4 sorted panes x 250K -> 1M (two rounds of pairwise merges)", oms)
+    # and a large two-run merge
+    big = 128_000_000
+    bcol = gen.uniform(5, 5, big, 0, 1 << 40, np.uint64)
+    d_b = torch.from_numpy(bcol).to(dev)
+    r1 = sbh.sort(*sbh.extract(d_b, 0, big // 2))
+    r2 = sbh.sort(*sbh.extract(d_b, big // 2, big // 2))
+    bk = torch.empty(big, dtype=torch.uint64, device=dev)
+    bp = torch.empty(big, dtype=torch.uint32, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_kpa_merge([r1, r2], bk, bp))
+    out["A5_merge_large"] = entry(ms, 24 * big, "2 sorted runs x 64M -> 128M", None)
+    del d_b, r1, r2, bk, bp
+
+    # A6 keyed sum/count: the tumbling window (1M rows, u32 values)
+    w = gen.tumbling_window(1_000_000)
+    sk, sp = sbh.sort(*sbh.extract(torch.from_numpy(w["keys"]).to(dev), 0, 1_000_000))
+    vals = torch.from_numpy(w["vals"]).to(dev)
+    ok = torch.empty(1_000_000, dtype=torch.uint64, device=dev)
+    oc = torch.empty_like(ok)
+    osum = torch.empty_like(ok)
+    nk = torch.empty(1, dtype=torch.uint64, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_group_reduce(sk, sp, vals, ok, oc, osum, 1_000_000, nk))
+    hk, hp_ = sk.cpu().numpy(), sp.cpu().numpy()
+    oms = cpu_ms(lambda: oracle.group_sum_count(hk, hp_, w["vals"]))
+    nkeys = int(nk.item())
+    out["A6_keyed_sum_count"] = entry(ms, 1_000_000 * (12 + 4) + 24 * nkeys,
+                                      "1M-row tumbling window, u32 values (L2-resident)", oms)
+
+    # A7 top-3: one 4M-row window of the batched workload (Zipf(1.0) keys, u64 values)
+    nb_ = 4_000_000
+    bk_ = gen.zipf(gen.SEED_BATCHED, 2, nb_, 1.0, 10_000_000)
+    bv_ = gen.uniform(gen.SEED_BATCHED, 3, nb_, 0, 0, np.uint64)
+    tsk, tsp = sbh.sort(*sbh.extract(torch.from_numpy(bk_).to(dev), 0, nb_))
+    tv = torch.from_numpy(bv_).to(dev)
+    K = 3
+    tk = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    tn = torch.empty(nb_, dtype=torch.uint8, device=dev)
+    tvo = torch.empty(nb_ * K, dtype=torch.uint64, device=dev)
+    tpo = torch.empty(nb_ * K, dtype=torch.uint32, device=dev)
+    tnk = torch.empty(1, dtype=torch.uint64, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_topk(tsk, tsp, tv, K, tk, tn, tvo, tpo, nb_, tnk))
+    hk, hp_ = tsk.cpu().numpy(), tsp.cpu().numpy()
+    oms = cpu_ms(lambda: oracle.topk(hk, hp_, bv_, K))
+    m = int(tnk.item())
+    out["A7_topk"] = entry(ms, nb_ * (12 + 8) + m * (8 + 1 + K * 12), "4M-row window, K=3, Zipf(1.0) keys", oms)
+
+    # A8 join: one 1M x 1M sliding window of the two join streams
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    L = sbh.sort(*sbh.extract(torch.from_numpy(lcol).to(dev), 0, 1_000_000))
+    R = sbh.sort(*sbh.extract(torch.from_numpy(rcol).to(dev), 0, 1_000_000))
+    cap = 1 << 20
+    jl = torch.empty(cap, dtype=torch.uint32, device=dev)
+    jr = torch.empty(cap, dtype=torch.uint32, device=dev)
+    npairs = torch.empty(1, dtype=torch.uint64, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_join(L[0], L[1], R[0], R[1], jl, jr, cap, npairs))
+    lh, rh = (L[0].cpu().numpy(), L[1].cpu().numpy()), (R[0].cpu().numpy(), R[1].cpu().numpy())
+    oms = cpu_ms(lambda: oracle.join(lh[0], lh[1], rh[0], rh[1]))
+    pairs = int(npairs.item())
+    out["A8_join"] = entry(ms, 2 * 1_000_000 * 12 + pairs * 8, f"1M x 1M window, keys U[0,2^24), {pairs} pairs", oms)
+    return out
 
 
 def main():
@@ -350,6 +473,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sort", default="learned", choices=["learned", "radix"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -101,6 +101,7 @@ constexpr int kMaxSlice = 256;
 
 struct GradSmem {
     float P[kNP];
+    float W2T[kH * kH];  // W2 transposed: lanes that differ in the output unit read consecutive words
     float G[kNP];
     float X[kMaxSlice], T[kMaxSlice], DY[kMaxSlice];
     float A1[kMaxSlice][kH + 1];
@@ -113,6 +114,7 @@ struct GradSmem {
 // parameters.  Every sum runs in a fixed order.
 __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     const int tid = threadIdx.x;
+    for (int e = tid; e < kH * kH; e += kGThreads) sm.W2T[(e % kH) * kH + e / kH] = sm.P[oW2 + e];
     for (int e = tid; e < S * kH; e += kGThreads) {
         const int s = e / kH, i = e % kH;
         sm.A1[s][i] = fmaf(sm.P[oW1 + i], sm.X[s], sm.P[oB1 + i]);
@@ -122,7 +124,7 @@ __device__ float slice_grad(GradSmem& sm, int S, float norm) {
         const int s = e / kH, o = e % kH;
         float a = sm.P[oB2 + o];
 #pragma unroll 8
-        for (int i = 0; i < kH; ++i) a = fmaf(sm.P[oW2 + o * kH + i], fmaxf(sm.A1[s][i], 0.f), a);
+        for (int i = 0; i < kH; ++i) a = fmaf(sm.W2T[i * kH + o], fmaxf(sm.A1[s][i], 0.f), a);
         sm.A2[s][o] = a;
     }
     __syncthreads();
