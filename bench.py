@@ -202,18 +202,18 @@ def run_gpu(args):
     stats = {}
     stream = torch.cuda.current_stream(dev)
 
-    def step_learned(src=col):
+    outs0 = (out_keys, out_counts, nkeys)
+
+    def step_learned(src=col, outs=outs0):
         sbh.sbh_kpa_extract(src, 0, n, keys, ptrs, None, samples, SAMPLE_STRIDE)
         scr["train"] = sbh.sbh_learned_train(samples, n, init, TRAIN["steps"], TRAIN["batch"], TRAIN["lr"], model)
         stats.update(sbh.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, scratch=lsort_scratch))
-        scr["red"] = sbh.sbh_group_reduce(sk, None, None, out_keys, out_counts, None, n, nkeys,
-                                          scratch=scr.get("red"))
+        scr["red"] = sbh.sbh_group_reduce(sk, None, None, outs[0], outs[1], None, n, outs[2], scratch=scr.get("red"))
 
-    def step_plain(src=col):
+    def step_plain(src=col, outs=outs0):
         sbh.sbh_kpa_extract(src, 0, n, keys, ptrs)
         sbh.sbh_kpa_sort(keys, ptrs, sk, sp, scratch=sort_scratch)
-        scr["red"] = sbh.sbh_group_reduce(sk, None, None, out_keys, out_counts, None, n, nkeys,
-                                          scratch=scr.get("red"))
+        scr["red"] = sbh.sbh_group_reduce(sk, None, None, outs[0], outs[1], None, n, outs[2], scratch=scr.get("red"))
 
     step = step_plain if args.sort == "radix" else step_learned
 
@@ -275,43 +275,31 @@ def run_gpu(args):
     algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
                   "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
                   "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
-                  "learned_ids_scatter": PAIR_BYTES * 2 * n, "learned_ids_count": 8 * n,
-                  "learned_ids_upsweep": 8 * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
-                  "learned_bounds": 8 * n}
+                  "learned_ids_scatter": (PAIR_BYTES + 2) * 2 * n, "learned_ids_count": 2 * n,
+                  "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
+                  "learned_bounds": 2 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                 "algorithmic_bytes_per_launch": algo_bytes.get(dominant)}
-    stages = {k: {"launches_per_step": len(v) / args.steps, "ms_per_step": sum(v) / args.steps,
+    def stage_table(per):
+        tot = {k: sum(v) for k, v in per.items()}
+        st = {k: {"launches_per_step": len(v) / args.steps, "ms_per_step": sum(v) / args.steps,
                   "share": sum(v) / sum(tot.values())} for k, v in per.items()}
-    for k, b in algo_bytes.items():
-        if k in per:
-            stages[k]["gbs"] = b / (statistics.mean(per[k]) / 1e3) / 1e9
+        for k, b in algo_bytes.items():
+            if k in per:
+                st[k]["gbs"] = b / (statistics.mean(per[k]) / 1e3) / 1e9
+        return st
+
+    stages = stage_table(per)
+    other_stages = stage_table(profiled(other, args.steps)[0])
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        res_k = torch.empty(n, dtype=torch.uint64).pin_memory()
-        res_c = torch.empty(n, dtype=torch.uint64).pin_memory()
-        nk_h = torch.empty(1, dtype=torch.uint64).pin_memory()
-        d2h = 0
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            col.copy_(col_h, non_blocking=True)
-            step()
-            nk_h.copy_(nkeys, non_blocking=True)
-            torch.cuda.synchronize(dev)
-            mk = int(nk_h[0])
-            res_k[:mk].copy_(out_keys[:mk], non_blocking=True)
-            res_c[:mk].copy_(out_counts[:mk], non_blocking=True)
-            d2h += 8 + 16 * mk
-        barrier()
-        dt = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": args.steps * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-               "d2h_bytes_per_step": d2h // args.steps}
+        e2e = end_to_end(step, col, col_h, outs0, n, args.steps, dev, barrier, max_over_ranks, ws)
 
     if rank == 0:
         learned_ms = ms if step is step_learned else ms_other
@@ -332,13 +320,77 @@ def run_gpu(args):
                                  "radix_ms_per_step": radix_ms / args.steps,
                                  "speedup": radix_ms / learned_ms,
                                  "learned_stats": stats,
-                                 "overflow_row_rate": stats.get("overflow_rows", 0) / n},
+                                 "overflow_row_rate": stats.get("overflow_rows", 0) / n,
+                                 "other_stages": other_stages},
             "stages": stages,
             "rows": row_suite(peak) if ws == 1 and not args.no_rows else None,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, ws):
+    """The step through the public API with the key column in page-locked
+    host memory and the grouped result (distinct keys and their counts) read
+    back, every step.  Steps are pipelined over three streams: the copy-in of
+    step i + 1 and the copy-out of step i - 1 run while step i computes (the
+    input column and the outputs are double-buffered)."""
+    import torch
+
+    cur = torch.cuda.current_stream(dev)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    cols = [col, torch.empty_like(col)]
+    outs = [outs0, tuple(torch.empty_like(t) for t in outs0)]
+    res_k = torch.empty(n, dtype=torch.uint64).pin_memory()
+    res_c = torch.empty(n, dtype=torch.uint64).pin_memory()
+    nk_h = torch.empty(2, dtype=torch.uint64).pin_memory()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    d2h = [0]
+
+    def copy_in(i):
+        b = i % 2
+        with torch.cuda.stream(s_in):
+            if i >= 2:
+                s_in.wait_event(ev_done[b])  # step i - 2 has finished reading this buffer
+            cols[b].copy_(col_h, non_blocking=True)
+            ev_in[b].record(s_in)
+
+    def copy_out(i):
+        b = i % 2
+        ev_done[b].synchronize()
+        m = int(nk_h[b])
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_done[b])
+            res_k[:m].copy_(outs[b][0][:m], non_blocking=True)
+            res_c[:m].copy_(outs[b][1][:m], non_blocking=True)
+            ev_out[b].record(s_out)
+        d2h[0] += 8 + 16 * m
+
+    barrier()
+    t0 = time.perf_counter()
+    copy_in(0)
+    for i in range(steps):
+        b = i % 2
+        if i + 1 < steps:
+            copy_in(i + 1)
+        if i >= 1:
+            copy_out(i - 1)
+        cur.wait_event(ev_in[b])
+        if i >= 2:
+            cur.wait_event(ev_out[b])  # the copy-out of step i - 2 has read these outputs
+        step(cols[b], outs[b])
+        nk_h[b:b + 1].copy_(outs[b][2], non_blocking=True)
+        ev_done[b].record(cur)
+    copy_out(steps - 1)
+    torch.cuda.synchronize(dev)
+    barrier()
+    dt = max_over_ranks(time.perf_counter() - t0)
+    return {"value": steps * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+            "d2h_bytes_per_step": d2h[0] // steps, "pipelined": "copy-in of step i+1 and copy-out of step i-1 "
+                                                                 "overlap step i (three streams)"}
 
 
 # ------------------------------------------------------------------ per-row measurements
@@ -460,6 +512,78 @@ def row_suite(peak):
     oms = cpu_ms(lambda: oracle.join(lh[0], lh[1], rh[0], rh[1]))
     pairs = int(npairs.item())
     out["A8_join"] = entry(ms, 2 * 1_000_000 * 12 + pairs * 8, f"1M x 1M window, keys U[0,2^24), {pairs} pairs", oms)
+    del L, R, jl, jr, tsk, tsp, tv, tk, tn, tvo, tpo
+    out.update(pipeline_rows())
+    return out
+
+
+def pipeline_rows():
+    """The two window pipelines on their full workloads, wall-clock (each
+    includes its host synchronisations), with the oracle on sampled windows."""
+    import torch
+
+    import gen
+    import oracle
+    from paper_1901_01328_b300 import pipeline
+
+    dev = torch.device("cuda")
+    out = {}
+
+    def wall_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts)
+
+    # batched windows: 4096 tumbling windows, per-key count, sum and top-3
+    b = gen.batched_windows()
+    keys, vals, off = b["keys"], b["vals"], b["offsets"]
+    n = int(off[-1])
+    kd, vd = torch.from_numpy(keys).to(dev), torch.from_numpy(vals).to(dev)
+    ms_b = wall_ms(lambda: pipeline.batched_windows(kd, vd, off, K=3, schedule="batched"))
+    ms_l = wall_ms(lambda: pipeline.batched_windows(kd, vd, off, K=3, schedule="loop"), reps=1)
+    sample = range(0, 4096, 512)
+    rows_s = int(sum(off[w + 1] - off[w] for w in sample))
+    t0 = time.perf_counter()
+    for w in sample:
+        k, p = oracle.sort(*oracle.extract(keys, int(off[w]), int(off[w + 1] - off[w])))
+        oracle.group_sum_count(k, p, vals)
+        oracle.topk(k, p, vals, 3)
+    oms = 1e3 * (time.perf_counter() - t0)
+    out["batched_windows_4096"] = {
+        "rows": n, "windows": 4096, "batched_ms": ms_b, "loop_ms": ms_l,
+        "batched_rows_per_s": n / (ms_b / 1e3), "loop_rows_per_s": n / (ms_l / 1e3),
+        "oracle_rows_per_s": rows_s / (oms / 1e3), "oracle_sample": f"8 windows, {rows_s} rows, one thread",
+        "shape": "4096 windows, sizes lognormal(10.4, 1.5) in [1K, 4M], Zipf(1.0) keys over 10M, u64 values, K=3"}
+    del kd, vd, b, keys, vals
+    torch.cuda.empty_cache()
+
+    # sliding-window temporal join: 2 x 128M rows in page-locked host memory
+    s = gen.join_streams()
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    lh = torch.from_numpy(lcol.view(np.int64)).pin_memory().view(torch.uint64)
+    rh = torch.from_numpy(rcol.view(np.int64)).pin_memory().view(torch.uint64)
+    res = {}
+
+    def run():
+        res["r"] = pipeline.sliding_join(lh, rh, lcol.size)
+
+    ms_j = wall_ms(run, reps=1)
+    pairs = int(res["r"][0].npairs.sum())
+    t0 = time.perf_counter()
+    lk, lp = oracle.sort(*oracle.extract(lcol, 0, 1_000_000))
+    rk, rp = oracle.sort(*oracle.extract(rcol, 0, 1_000_000))
+    oracle.join(lk, lp, rk, rp)
+    oms = 1e3 * (time.perf_counter() - t0)
+    out["sliding_join_509"] = {
+        "rows_per_side": int(lcol.size), "windows": 509, "ms": ms_j, "windows_per_s": 509 / (ms_j / 1e3),
+        "pairs": pairs, "h2d_bytes": 2 * 8 * int(lcol.size), "oracle_ms_per_window": oms,
+        "shape": "2 x 128M keys U[0, 2^24) in pinned host memory; 1M-row windows, stride 250K; panes sorted once"}
     return out
 
 

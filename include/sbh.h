@@ -110,18 +110,41 @@ int sbh_window_ranges(const void* d_ts, int ts_bytes, uint64_t n, const uint64_t
 int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs,
                     uint64_t* d_key_or, uint64_t* d_samples, uint64_t sample_stride, void* stream);
 
+/* Extract of many tumbling windows at once (Sec. 4.2 "Windowing": records
+ * are partitioned into windows; the paper gives no batched form, which is
+ * this library's design).  Window w holds rows [d_offsets[w], d_offsets[w +
+ * 1]) of key_col; d_offsets (device, nwin + 1 non-decreasing values) covers
+ * rows [row_begin, row_begin + n) = [d_offsets[0], d_offsets[nwin]).  For
+ * i < n, row r = row_begin + i of window w gives
+ *     d_keys[i] = (w << (64 - sbh_window_bits(nwin))) | key_col[r],
+ *     d_ptrs[i] = r.
+ * Sorting these composite keys orders the rows by (window, key, ptr), so one
+ * sort, one keyed reduction and one top-K serve every window, and the
+ * results of window w are the output keys in [w << shift, (w + 1) << shift)
+ * (found with sbh_window_ranges).  The composite is exact only when every
+ * key is below 2^(64 - sbh_window_bits(nwin)); d_key_or (nullable, device)
+ * receives the OR of the raw keys so that the caller can check.  key_col may
+ * be device memory or page-locked host memory.  No scratch. */
+int sbh_kpa_extract_windows(const uint64_t* key_col, const uint64_t* d_offsets, uint64_t nwin, uint64_t row_begin,
+                            uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs, uint64_t* d_key_or, void* stream);
+/* Bits of the window field of the composite keys: the bit length of nwin. */
+int sbh_window_bits(uint64_t nwin);
+
 /* ---------------------------------------------------------------- A3
  * Sort (Table 2: order a KPA by its resident key).  Stable LSD radix sort,
  * 8-bit digits, one pass per digit position whose digit is not the same for
- * all keys (the histogram of every position is built in one read).  Each
- * pass is one onesweep kernel: tile load, warp multisplit ranking, decoupled
- * look-back for the tile's global digit offsets, scatter staged through
- * shared memory.  Because the sort is stable and ties keep their input
+ * all keys (the histogram of every position is built in one read).  Below
+ * 2^21 pairs each pass is one onesweep kernel: tile load, warp multisplit
+ * ranking, decoupled look-back for the tile's global digit offsets, scatter
+ * staged through shared memory.  From 2^21 pairs each pass is three kernels:
+ * per-chunk digit counts, their scan, and a scatter in which every CTA walks
+ * its own chunk of tiles (bulk-copied, ranked, staged) with its digit offsets
+ * known up front.  Because the sort is stable and ties keep their input
  * order, the output is in (key, ptr) order when the input ptrs ascend (as
  * Extract makes them); in general ties keep input order.
  * In/out: (d_keys_in, d_ptrs_in) -> (d_keys_out, d_ptrs_out), n pairs,
  * n < 2^32.  The output may alias the input (in-place sort).
- * Scratch: about 12 n + (n / 6144) * 2 KiB bytes. */
+ * Scratch: about 12 n bytes plus 2 MiB (the sizing call gives the exact figure). */
 int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out, uint32_t* d_ptrs_out,
                  uint64_t n, void* d_scratch, size_t* scratch_bytes, void* stream);
 
@@ -208,7 +231,7 @@ int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, cons
 #define SBH_MLP_PARAMS 1153
 #define SBH_LEARNED_MODEL_BYTES 16384
 #define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
-#define SBH_LEARNED_STATS 8
+#define SBH_LEARNED_STATS 10
 
 /* y[i] = MLP(x[i]) for i < m.  No scratch. */
 int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream);
@@ -249,7 +272,9 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * call synchronises `stream` once (the overflow size decides the last step).
  * h_stats (nullable, host, SBH_LEARNED_STATS values): bucket ids, heavy
  * cells, buckets sorted in shared memory, one-key buckets, heavy buckets,
- * overflow buckets, overflow rows, largest bucket.
+ * overflow buckets, overflow rows, largest bucket, buckets sorted by radix
+ * passes in shared memory (their sub-buckets were too uneven for the
+ * counting placement), and their rows.
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
                          uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats, void* d_scratch,

@@ -189,6 +189,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Asynchronous element copies global -> shared (no register staging): the
+// issuing thread waits for all of its copies with cp_async_wait_all, and a
+// CTA barrier after that makes them visible to the other threads.
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory atomic add done only where pred holds, without a branch
 // (returns the old value there, 0 elsewhere).
 __device__ __forceinline__ uint32_t smem_atomic_add_if(bool pred, uint32_t* addr, uint32_t v) {
@@ -198,6 +209,17 @@ __device__ __forceinline__ uint32_t smem_atomic_add_if(bool pred, uint32_t* addr
         : "+r"(old)
         : "r"(smem_addr(addr)), "r"(static_cast<uint32_t>(pred)), "r"(v)
         : "memory");
+    return old;
+}
+
+// The same without a compiler memory barrier, so that independent loads and
+// arithmetic may be scheduled around it; the counters it updates must be
+// read only after a CTA barrier.
+__device__ __forceinline__ uint32_t smem_atomic_add_if_relaxed(bool pred, uint32_t* addr, uint32_t v) {
+    uint32_t old = 0;
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n @p atom.shared.add.u32 %0, [%1], %3;\n}\n"
+                 : "+r"(old)
+                 : "r"(smem_addr(addr)), "r"(static_cast<uint32_t>(pred)), "r"(v));
     return old;
 }
 

@@ -56,6 +56,37 @@ __global__ void __launch_bounds__(256) extract_kernel(const uint64_t* __restrict
     }
 }
 
+// ---------------------------------------------------------------- Extract of many windows
+// Row r of window w (offsets[w] <= r < offsets[w + 1]) becomes the pair
+// ((w << wshift) | key_col[r], r).  The window of a row is found by binary
+// search over the offsets (a few KB, cached).
+__global__ void __launch_bounds__(256) extract_windows_kernel(const uint64_t* __restrict__ col,
+                                                              const uint64_t* __restrict__ offsets, uint32_t nwin,
+                                                              uint32_t row_begin, uint32_t n, int wshift,
+                                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs,
+                                                              uint64_t* __restrict__ key_or) {
+    uint64_t acc = 0;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+        const uint64_t r = (uint64_t)row_begin + i;
+        // last w with offsets[w] <= r
+        uint32_t lo = 0, hi = nwin;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (__ldg(offsets + mid) <= r) lo = mid;
+            else hi = mid;
+        }
+        const uint64_t k = __ldcs(reinterpret_cast<const unsigned long long*>(col + r));
+        acc |= k;
+        __stcs(reinterpret_cast<unsigned long long*>(keys + i), (unsigned long long)((static_cast<uint64_t>(lo) << wshift) | k));
+        __stcs(reinterpret_cast<unsigned int*>(ptrs + i), static_cast<unsigned int>(r));
+    }
+    if (key_or) {
+        for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane_id() == 0 && acc) atomicOr(reinterpret_cast<unsigned long long*>(key_or), (unsigned long long)acc);
+    }
+}
+
 // ---------------------------------------------------------------- windows
 template <typename T>
 __device__ __forceinline__ uint64_t lower_bound_ts(const T* ts, uint64_t n, uint64_t v) {
@@ -140,6 +171,35 @@ int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uin
     SBH_LAUNCHED();
     return SBH_OK;
 }
+
+int sbh_kpa_extract_windows(const uint64_t* key_col, const uint64_t* d_offsets, uint64_t nwin, uint64_t row_begin,
+                            uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs, uint64_t* d_key_or, void* stream) {
+    using namespace sbh;
+    clear_error();
+    cudaStream_t s = as_stream(stream);
+    if (nwin == 0 || nwin > 0xFFFFFFFFull) { set_error("nwin must be in 1 .. 2^32 - 1"); return SBH_EINVAL; }
+    if (row_begin + n > 0xFFFFFFFFull || row_begin + n < row_begin) {
+        set_error("row_begin + n must be < 2^32 with 32-bit pointers");
+        return SBH_EINVAL;
+    }
+    if (n && (!key_col || !d_offsets || !d_keys || !d_ptrs)) { set_error("null pointer"); return SBH_EINVAL; }
+    if (d_key_or) SBH_CUDA(cudaMemsetAsync(d_key_or, 0, sizeof(uint64_t), s));
+    if (n == 0) return SBH_OK;
+    const uint64_t* col = nullptr;
+    int rc = device_view(key_col, &col);
+    if (rc) return rc;
+    const int wshift = 64 - sbh_window_bits(nwin);
+    const uint64_t max_blocks = (uint64_t)num_sms() * 8;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > max_blocks) blocks = max_blocks;
+    SBH_TIMED("extract_windows", s,
+              extract_windows_kernel<<<(unsigned)blocks, 256, 0, s>>>(col, d_offsets, (uint32_t)nwin, (uint32_t)row_begin,
+                                                                      (uint32_t)n, wshift, d_keys, d_ptrs, d_key_or));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int sbh_window_bits(uint64_t nwin) { return nwin ? 64 - __builtin_clzll(nwin) : 0; }
 
 int sbh_window_ranges(const void* d_ts, int ts_bytes, uint64_t n, const uint64_t* d_starts, uint64_t len,
                       uint64_t nwin, uint64_t* d_row_begin, uint64_t* d_row_end, void* stream) {

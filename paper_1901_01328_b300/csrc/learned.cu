@@ -649,31 +649,41 @@ __global__ void __launch_bounds__(256) bucket_bounds_kernel(const uint64_t* __re
 
 // In-shared-memory sort of each bucket of at most kCap rows.
 constexpr uint32_t kCap = SBH_LEARNED_CAPACITY;
-constexpr int kBThreads = 512;
+constexpr int kBThreads = 1024;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBIpt = kCap / kBThreads;
+constexpr int kBGroups = kBThreads / 128;  // warp groups of the radix passes' count scan
+constexpr int kBWpg = kBWarps / kBGroups;
 
 constexpr int kFineBits = 12;
 constexpr int kFineBins = 1 << kFineBits;
-constexpr uint32_t kFineMaxBin = 32;  // larger sub-buckets take the radix passes
+constexpr int kFinePer = kFineBins / kBThreads;  // bins scanned by each thread
+constexpr uint32_t kFineMaxBin = 32;             // larger sub-buckets take the radix passes
 
 struct BucketSmem {
     uint64_t keys[2][kCap];
     uint32_t ptrs[2][kCap];
-    uint32_t whist2[kBWarps][kRadix / 2 + 1];
-    uint32_t local_start[kRadix];
-    uint32_t scan_tmp[4];
+    union {
+        uint32_t bins[kFineBins];                   // counting placement by the top bits of key - kmin
+        uint32_t whist2[kBWarps][kRadix / 2 + 1];  // radix passes: per-warp digit-pair counts
+    };
+    uint32_t gsum[kBGroups][kRadix / 2];
+    uint16_t gstart[kBGroups][kRadix];
     uint64_t red[2][kBWarps];
-    uint32_t bins[kFineBins];  // counting placement by the top bits of key - kmin
     uint32_t bin_tmp[kBWarps];
-    uint32_t bucket;
+    uint32_t next[2];  // the bucket taken after the current one (alternating slots)
 };
 
 struct BucketStats {
     unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
-        max_bucket;
+        max_bucket, radix_buckets, radix_rows;
 };
 
+// Persistent CTAs take buckets in order from a counter and sort each one in
+// shared memory: a counting placement by the top 12 bits of key - kmin and
+// insertion sorts inside the sub-buckets, or (a sub-bucket over 32 rows)
+// stable 8-bit radix passes on key - kmin.  Rows of one key stay in ptr
+// order because the scatter that formed the bucket was stable.
 __global__ void __launch_bounds__(kBThreads, 1)
 bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
                    const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
@@ -683,36 +693,47 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
     const uint32_t nbid = *nbid_p;
     const uint32_t lt = lanemask_lt();
-    for (;;) {
-        if (tid == 0) sm.bucket = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t b = sm.bucket;
-        __syncthreads();
+    if (tid == 0) sm.next[0] = atomicAdd(counter, 1u);
+    __syncthreads();
+    uint32_t b = sm.next[0];
+    for (uint32_t it = 1;; ++it) {
         if (b >= nbid) break;
+        // the bucket after this one; read after this bucket's first barrier,
+        // rewritten two buckets later
+        if (tid == 0) sm.next[it & 1] = atomicAdd(counter, 1u);
         const uint32_t s = bstart[b], e = bstart[b + 1], cnt = e - s;
-        if (tid == 0 && cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
-        if (cnt <= 1) continue;
-        if ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) {
-            if (tid == 0) atomicAdd(&st->heavy_buckets, 1ull);
-            continue;  // one key: the stable scatter left it in ptr order
-        }
-        if (cnt > kCap) {
+        const bool heavy = ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) != 0;
+        if (cnt <= 1 || heavy || cnt > kCap) {
             if (tid == 0) {
-                ov_flag[b] = 1;
-                atomicAdd(&st->overflow_buckets, 1ull);
-                atomicAdd(&st->overflow_rows, (unsigned long long)cnt);
+                if (cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
+                if (cnt > 1 && heavy) {
+                    atomicAdd(&st->heavy_buckets, 1ull);  // one key: the stable scatter left it in ptr order
+                } else if (cnt > 1) {
+                    ov_flag[b] = 1;
+                    atomicAdd(&st->overflow_buckets, 1ull);
+                    atomicAdd(&st->overflow_rows, (unsigned long long)cnt);
+                }
             }
+            __syncthreads();
+            b = sm.next[it & 1];
             continue;
         }
-        // load, and the key range
+        if (tid == 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
+        // load (buffer 0), the key range, and clear the bins
         uint64_t kmin = ~0ull, kmax = 0;
-        for (uint32_t r = tid; r < cnt; r += kBThreads) {
-            const uint64_t k = keys[s + r];
-            sm.keys[0][r] = k;
-            sm.ptrs[0][r] = ptrs[s + r];
-            kmin = min(kmin, k);
-            kmax = max(kmax, k);
+#pragma unroll
+        for (int j = 0; j < kBIpt; ++j) {
+            const uint32_t r = tid + j * kBThreads;
+            if (r < cnt) {
+                const uint64_t k = keys[s + r];
+                sm.keys[0][r] = k;
+                sm.ptrs[0][r] = ptrs[s + r];
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
         }
+#pragma unroll
+        for (int q = 0; q < kFinePer; ++q) sm.bins[tid * kFinePer + q] = 0;
         for (int o = 16; o > 0; o >>= 1) {
             kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
             kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
@@ -721,35 +742,36 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             sm.red[0][warp] = kmin;
             sm.red[1][warp] = kmax;
         }
-        __syncthreads();
-        kmin = sm.red[0][0];
-        kmax = sm.red[1][0];
-        for (int w = 1; w < kBWarps; ++w) {
-            kmin = min(kmin, sm.red[0][w]);
-            kmax = max(kmax, sm.red[1][w]);
+        __syncthreads();  // (a)
+        const uint32_t nb = sm.next[it & 1];
+        kmin = sm.red[0][lane];
+        kmax = sm.red[1][lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         }
         if (kmin == kmax) {
             if (tid == 0) atomicAdd(&st->single_key_buckets, 1ull);
-            continue;  // one key value: already in ptr order
+            __syncthreads();  // buffer 0 is read no more
+            b = nb;
+            continue;  // one key value: already in ptr order, nothing to write
         }
         const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
+        int res = -1;  // buffer holding the sorted bucket
         if (bits > kRadixBits) {
-            // Counting placement by the top 12 bits of key - kmin (keys spread
-            // almost evenly inside a bucket), then an insertion sort by (key,
-            // ptr) inside every sub-bucket.  Taken only when no sub-bucket
-            // exceeds kFineMaxBin rows.
             const int fsh = bits > kFineBits ? bits - kFineBits : 0;
-            for (int x = tid; x < kFineBins; x += kBThreads) sm.bins[x] = 0;
-            __syncthreads();
-            for (uint32_t r = tid; r < cnt; r += kBThreads)
-                atomicAdd(&sm.bins[static_cast<uint32_t>((sm.keys[0][r] - kmin) >> fsh)], 1u);
-            __syncthreads();
-            // exclusive scan over the bins: 8 consecutive bins per thread
-            constexpr int kPer = kFineBins / kBThreads;
-            uint32_t v[kPer], tsum = 0, bmax = 0;
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                v[q] = sm.bins[tid * kPer + q];
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t r = tid + j * kBThreads;
+                if (r < cnt) atomicAdd(&sm.bins[static_cast<uint32_t>((sm.keys[0][r] - kmin) >> fsh)], 1u);
+            }
+            __syncthreads();  // (b)
+            // exclusive scan over the bins, kFinePer consecutive bins per
+            // thread; a warp's total and whether one of its bins is too big
+            uint32_t v[kFinePer], tsum = 0, bmax = 0;
+#pragma unroll
+            for (int q = 0; q < kFinePer; ++q) {
+                v[q] = sm.bins[tid * kFinePer + q];
                 tsum += v[q];
                 bmax = max(bmax, v[q]);
             }
@@ -759,29 +781,36 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= (uint32_t)o) x += y;
             }
-            const int big = __syncthreads_or(bmax > kFineMaxBin);
-            if (lane == 31) sm.bin_tmp[warp] = x;
-            __syncthreads();
+            const uint32_t wbig = __any_sync(0xffffffffu, bmax > kFineMaxBin) ? 0x80000000u : 0u;
+            if (lane == 31) sm.bin_tmp[warp] = x | wbig;
+            __syncthreads();  // (c)
+            const uint32_t bt = sm.bin_tmp[lane];
+            const bool big = __any_sync(0xffffffffu, (bt & 0x80000000u) != 0);
             if (!big) {
                 uint32_t run = x - tsum;
                 for (int w = 0; w < (int)warp; ++w) run += sm.bin_tmp[w];
 #pragma unroll
-                for (int q = 0; q < kPer; ++q) {
-                    sm.bins[tid * kPer + q] = run;  // next free row of the bin
+                for (int q = 0; q < kFinePer; ++q) {
+                    sm.bins[tid * kFinePer + q] = run;  // next free row of the bin
                     run += v[q];
                 }
-                __syncthreads();
-                for (uint32_t r = tid; r < cnt; r += kBThreads) {
-                    const uint64_t k = sm.keys[0][r];
-                    const uint32_t pos = atomicAdd(&sm.bins[static_cast<uint32_t>((k - kmin) >> fsh)], 1u);
-                    sm.keys[1][pos] = k;
-                    sm.ptrs[1][pos] = sm.ptrs[0][r];
+                __syncthreads();  // (d)
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t r = tid + j * kBThreads;
+                    if (r < cnt) {
+                        const uint64_t k = sm.keys[0][r];
+                        const uint32_t pos = atomicAdd(&sm.bins[static_cast<uint32_t>((k - kmin) >> fsh)], 1u);
+                        sm.keys[1][pos] = k;
+                        sm.ptrs[1][pos] = sm.ptrs[0][r];
+                    }
                 }
-                __syncthreads();
-                // bins[d] now holds the end of bin d
+                __syncthreads();  // (e)
+                // bins[d] now holds the end of bin d: insertion sort by (key,
+                // ptr) inside each of this thread's bins
 #pragma unroll 1
-                for (int q = 0; q < kPer; ++q) {
-                    const int d = tid * kPer + q;
+                for (int q = 0; q < kFinePer; ++q) {
+                    const int d = tid * kFinePer + q;
                     const uint32_t e2 = sm.bins[d], b2 = e2 - v[q];
                     for (uint32_t i2 = b2 + 1; i2 < e2; ++i2) {
                         const uint64_t kk = sm.keys[1][i2];
@@ -797,85 +826,111 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                         sm.ptrs[1][j2] = pp;
                     }
                 }
-                __syncthreads();
-                for (uint32_t r = tid; r < cnt; r += kBThreads) {
-                    keys[s + r] = sm.keys[1][r];
-                    ptrs[s + r] = sm.ptrs[1][r];
-                }
-                if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
-                __syncthreads();
-                continue;
+                __syncthreads();  // (f)
+                res = 1;
             }
         }
-        const int passes = (bits + kRadixBits - 1) / kRadixBits;
-        int a = 0;
-        for (int pass = 0; pass < passes; ++pass) {
-            const int sh = pass * kRadixBits;
-            for (int x = tid; x < kBWarps * (kRadix / 2 + 1); x += kBThreads) (&sm.whist2[0][0])[x] = 0;
-            __syncthreads();
-            uint32_t dg[kBIpt], rank[kBIpt];
-            const uint32_t wofs = warp * 32 * kBIpt + lane;
-#pragma unroll
-            for (int j = 0; j < kBIpt; ++j) {
-                const uint32_t r = wofs + j * 32;
-                dg[j] = r < cnt ? static_cast<uint32_t>((sm.keys[a][r] - kmin) >> sh) & (kRadix - 1) : kRadix;
+        if (res < 0) {
+            // stable radix passes on key - kmin, ping-pong from buffer 0
+            const int passes = (bits + kRadixBits - 1) / kRadixBits;
+            if (tid == 0) {
+                atomicAdd(&st->radix_buckets, 1ull);
+                atomicAdd(&st->radix_rows, (unsigned long long)cnt);
             }
+            int a = 0;
+            for (int pass = 0; pass < passes; ++pass) {
+                const int sh = pass * kRadixBits;
+                for (int x = tid; x < kBWarps * (kRadix / 2 + 1); x += kBThreads) (&sm.whist2[0][0])[x] = 0;
+                __syncthreads();
+                uint32_t dg[kBIpt], rank[kBIpt];
+                const uint32_t wofs = warp * 32 * kBIpt + lane;
 #pragma unroll
-            for (int j = 0; j < kBIpt; ++j) {
-                const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
-                const int leader = __ffs(peers) - 1;
-                const uint32_t hs = (dg[j] & 1u) * 16u;
-                uint32_t c = 0;
-                if ((int)lane == leader) c = atomicAdd(&sm.whist2[warp][dg[j] >> 1], (uint32_t)__popc(peers) << hs);
-                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> hs) & 0xFFFFu);
-            }
-            __syncthreads();
-            uint32_t c0 = 0, c1 = 0, x = 0;
-            if (tid < kRadix / 2) {
-#pragma unroll
-                for (int w = 0; w < kBWarps; ++w) {
-                    const uint32_t word = sm.whist2[w][tid];
-                    sm.whist2[w][tid] = c0 | (c1 << 16);
-                    c0 += word & 0xFFFFu;
-                    c1 += word >> 16;
-                }
-                x = c0 + c1;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= (uint32_t)o) x += y;
-                }
-                if (lane == 31) sm.scan_tmp[warp] = x;
-            }
-            __syncthreads();
-            if (tid < kRadix / 2) {
-                uint32_t before = 0;
-#pragma unroll
-                for (int w = 0; w < 4; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
-                const uint32_t l0 = before + x - c0 - c1;
-                sm.local_start[2 * tid] = l0;
-                sm.local_start[2 * tid + 1] = l0 + c0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < kBIpt; ++j) {
-                if (dg[j] < kRadix) {
+                for (int j = 0; j < kBIpt; ++j) {
                     const uint32_t r = wofs + j * 32;
-                    const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
-                    const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
-                    sm.keys[a ^ 1][slot] = sm.keys[a][r];
-                    sm.ptrs[a ^ 1][slot] = sm.ptrs[a][r];
+                    dg[j] = r < cnt ? static_cast<uint32_t>((sm.keys[a][r] - kmin) >> sh) & (kRadix - 1) : kRadix;
                 }
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
+                    const int leader = __ffs(peers) - 1;
+                    const uint32_t hs = (dg[j] & 1u) * 16u;
+                    const uint32_t c = smem_atomic_add_if_relaxed((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
+                                                                  (uint32_t)__popc(peers) << hs);
+                    rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> hs) & 0xFFFFu);
+                }
+                __syncthreads();
+                {  // exclusive counts over each group's warps; group totals
+                    const uint32_t pr = tid & (kRadix / 2 - 1), g = tid / (kRadix / 2);
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int w = 0; w < kBWpg; ++w) {
+                        const uint32_t word = sm.whist2[g * kBWpg + w][pr];
+                        sm.whist2[g * kBWpg + w][pr] = acc;
+                        acc += word;
+                    }
+                    sm.gsum[g][pr] = acc;
+                }
+                __syncthreads();
+                if (warp < (uint32_t)kBGroups) {  // first slot of each (group, digit)
+                    uint32_t lsum = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int gg = 0; gg < kBGroups; ++gg) {
+                            const uint32_t v = sm.gsum[gg][4 * lane + q];
+                            lsum += (v & 0xFFFFu) + (v >> 16);
+                        }
+                    uint32_t x = lsum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= (uint32_t)o) x += y;
+                    }
+                    uint32_t stt = x - lsum;
+#pragma unroll 1
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t tot = 0, pre = 0;
+#pragma unroll
+                        for (int gg = 0; gg < kBGroups; ++gg) {
+                            const uint32_t v = sm.gsum[gg][4 * lane + q];
+                            tot += v;
+                            pre += (gg < (int)warp) ? v : 0u;
+                        }
+                        const uint32_t c0 = tot & 0xFFFFu;
+                        const uint32_t d0 = 8 * lane + 2 * q;
+                        sm.gstart[warp][d0] = static_cast<uint16_t>(stt + (pre & 0xFFFFu));
+                        sm.gstart[warp][d0 + 1] = static_cast<uint16_t>(stt + c0 + (pre >> 16));
+                        stt += c0 + (tot >> 16);
+                    }
+                }
+                __syncthreads();
+                const uint32_t grp = warp / kBWpg;
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    if (dg[j] < kRadix) {
+                        const uint32_t r = wofs + j * 32;
+                        const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
+                        const uint32_t slot = sm.gstart[grp][dg[j]] + wo + rank[j];
+                        sm.keys[a ^ 1][slot] = sm.keys[a][r];
+                        sm.ptrs[a ^ 1][slot] = sm.ptrs[a][r];
+                    }
+                }
+                __syncthreads();
+                a ^= 1;
             }
-            __syncthreads();
-            a ^= 1;
+            res = a;
         }
-        for (uint32_t r = tid; r < cnt; r += kBThreads) {
-            keys[s + r] = sm.keys[a][r];
-            ptrs[s + r] = sm.ptrs[a][r];
+#pragma unroll
+        for (int j = 0; j < kBIpt; ++j) {
+            const uint32_t r = tid + j * kBThreads;
+            if (r < cnt) {
+                keys[s + r] = sm.keys[res][r];
+                ptrs[s + r] = sm.ptrs[res][r];
+            }
         }
         if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
-        __syncthreads();
+        if (res == 0) __syncthreads();  // the next bucket is loaded into buffer 0
+        b = nb;
     }
 }
 
@@ -946,8 +1001,13 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 // When every bucket id fits in 16 bits, each row's id is computed once, kept
 // in a 16-bit array, and moved with the row through both digit passes; the
 // counts and the bucket bounds then read ids instead of recomputing them.
-constexpr int kCarryTile = 3072;
+constexpr int kCarryTile = 3584;
 
+// Bucket id of every row (kept as 16 bits) and the histograms of its two
+// digits.  With 16-byte aligned keys each lane takes two consecutive rows per
+// step, four steps at a time: every load and store instruction of a warp
+// covers one contiguous span, and the eight cell-table lookups of a lane are
+// independent.
 __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
                                                           BucketValue fn, uint16_t* __restrict__ ids,
                                                           uint32_t* __restrict__ ghist) {
@@ -962,8 +1022,33 @@ __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __rest
         if (d1 == last1) ++run1;
         else { if (run1) atomicAdd(&h[kRadix + last1], run1); last1 = d1; run1 = 1; }
     };
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+        // a warp step covers 256 rows: lane l takes row pairs 32 j + l, j < 4
+        const uint32_t nsteps = n / 256;
+        const uint32_t lane = lane_id();
+        const uint32_t warps = gridDim.x * (blockDim.x / 32);
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
+        uint32_t* ids2 = reinterpret_cast<uint32_t*>(ids);
+        for (uint32_t st = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; st < nsteps; st += warps) {
+            ulonglong2 k[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = __ldcs(q + st * 128 + j * 32 + lane);
+            uint32_t id[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                id[2 * j] = static_cast<uint32_t>(fn(k[j].x));
+                id[2 * j + 1] = static_cast<uint32_t>(fn(k[j].y));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) __stcs(ids2 + st * 128 + j * 32 + lane, id[2 * j] | (id[2 * j + 1] << 16));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) add(id[j]);
+        }
+        done = nsteps * 256;
+    }
     const uint32_t nthreads = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    for (uint32_t i = done + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
         const uint32_t id = static_cast<uint32_t>(fn(ld_stream(keys + i)));
         ids[i] = static_cast<uint16_t>(id);
         add(id);
@@ -1080,6 +1165,31 @@ CarryScratch carry_carve(void* base, uint64_t n) {
     return t;
 }
 
+// The two passes by carried bucket id: per pass, chunk counts of the id
+// digit -> chunk offsets -> scatter carrying the ids along.
+template <int TILE, int THREADS>
+int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaStream_t s) {
+    ChunkGeom g;
+    const int rc = chunk_geometry<RadixValue, TILE, THREADS, true>(n32, &g);
+    if (rc) return rc;
+    const int bulk_ok = ((reinterpret_cast<uintptr_t>(b.in_k) | reinterpret_cast<uintptr_t>(b.in_p) |
+                          reinterpret_cast<uintptr_t>(b.out_k) | reinterpret_cast<uintptr_t>(b.out_p)) & 15) == 0;
+    for (int pos = 0; pos < 2; ++pos) {
+        SBH_TIMED("learned_ids_count", s,
+                  ids_count_kernel<<<g.nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, g.chunk, cs.chunk_hist));
+        SBH_LAUNCHED();
+        SBH_TIMED("learned_ids_chunk_scan", s,
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, cs.gbase, cs.chunk_base));
+        SBH_LAUNCHED();
+        SBH_TIMED("learned_ids_scatter", s,
+                  (chunk_scatter_kernel<RadixValue, TILE, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
+                      b, n32, pos, cs.plan, g.chunk, cs.chunk_base, RadixValue{}, bulk_ok, spin_limit(),
+                      status_word())));
+        SBH_LAUNCHED();
+    }
+    return SBH_OK;
+}
+
 // Stable sort by 16-bit bucket id with the ids carried along; fills bstart.
 int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
                         void* scratch, cudaStream_t s, BucketValue fn, const uint32_t* nbid, uint32_t* bstart) {
@@ -1096,30 +1206,8 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     b.in_v = cs.ids_in;
     b.tmp_v = cs.ids_tmp;
     b.out_v = cs.ids_out;
-    auto scat = chunk_scatter_kernel<RadixValue, kCarryTile, true>;
-    const size_t smem = sizeof(ScatterSmem<kCarryTile, true>);
-    SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const uint64_t ttiles = (n + kCarryTile - 1) / kCarryTile;
-    const uint64_t want = min_u64(min_u64(ttiles, (uint64_t)sms * per_sm), kMaxChunks);
-    const uint32_t chunk = (uint32_t)(((ttiles + want - 1) / want) * kCarryTile);
-    const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
-    const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
-                          reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
-    for (int pos = 0; pos < 2; ++pos) {
-        SBH_TIMED("learned_ids_count", s,
-                  ids_count_kernel<<<nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, chunk, cs.chunk_hist));
-        SBH_LAUNCHED();
-        SBH_TIMED("learned_ids_chunk_scan", s,
-                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, nchunks, cs.gbase, cs.chunk_base));
-        SBH_LAUNCHED();
-        SBH_TIMED("learned_ids_scatter", s,
-                  scat<<<nchunks, kSThreads, smem, s>>>(b, n32, pos, cs.plan, chunk, cs.chunk_base, RadixValue{},
-                                                        bulk_ok, spin_limit(), status_word()));
-        SBH_LAUNCHED();
-    }
+    const int rc = carried_passes<kCarryTile, 512>(b, n32, cs, s);
+    if (rc) return rc;
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
@@ -1388,6 +1476,8 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
         h_stats[5] = st_h.overflow_buckets;
         h_stats[6] = st_h.overflow_rows;
         h_stats[7] = st_h.max_bucket;
+        h_stats[8] = st_h.radix_buckets;
+        h_stats[9] = st_h.radix_rows;
     }
     return SBH_OK;
 }

@@ -493,34 +493,62 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
 }
 
 // Ranks and scatters one chunk, tile by tile, with running digit offsets.
-// 512 threads x 8 rows per tile: twice the warps of the onesweep kernel for
-// the same tile, to hide the latency of the ranking chain.
-constexpr int kSThreads = 512;
-constexpr int kSWarps = kSThreads / 32;
-
-template <int TILE, bool kCarry>
+// THREADS x (TILE / THREADS) rows per tile; five CTA barriers per tile:
+//   B0  tile data present (bulk copy complete); the other buffer is free, so
+//       the next tile's copy is issued
+//   B1  ranked: per-warp digit counts final
+//   B2  per warp group: exclusive counts over the group's warps, group totals
+//   B3  per (group, digit): first staged slot; per digit: global offset
+//   B4  staged in digit order; then the coalesced scatter (and the counters
+//       are cleared for the next tile)
+template <int TILE, int THREADS, bool kCarry, bool kDig>
 struct ScatterSmem {
-    using Tag = typename std::conditional<kCarry, uint16_t, uint8_t>::type;
+    static constexpr int kW = THREADS / 32;
+    static constexpr int kG = THREADS / 128;  // warp groups of the count scan
     uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
     uint32_t ptrs[2][TILE];  // the scatter in digit order
-    uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried values of the input tiles
-    Tag dig[TILE];           // digit (or carried value) of each staged row
+    uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried values, staged the same way
+    uint8_t dig[kDig ? TILE : 16];                     // digit of each staged row (derived values only)
     // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
     // word 128 holds the sentinel digit of rows past the end)
-    uint32_t whist2[kSWarps][kRadix / 2 + 1];
-    uint16_t local_start[kRadix];
-    uint32_t gbase_rel[kRadix];
-    uint32_t scan_tmp[4];
+    uint32_t whist2[kW][kRadix / 2 + 1];
+    uint32_t gsum[kG][kRadix / 2];   // per warp group, packed digit-pair totals
+    uint16_t gstart[kG][kRadix];     // first staged slot of each (group, digit)
+    uint32_t run[kRadix];            // next output row of each digit in this chunk
+    uint32_t gbase_rel[kRadix];      // output row minus staged slot, per digit
     uint64_t mbar[2];
 };
 
-template <typename ValueFn, int TILE, bool kCarry = false>
-__global__ void __launch_bounds__(kSThreads, TILE <= 4096 ? 2 : 1)
+// The digit of a staged row is re-derived from its key when the value is
+// the key itself; other values keep it in shared memory.
+template <typename ValueFn, bool kCarry>
+struct ScatterDig {
+    static constexpr bool value = !kCarry && !std::is_same<ValueFn, RadixValue>::value;
+};
+
+template <int TILE, int THREADS>
+struct ScatterBlocks {  // CTAs per SM the launch bounds ask for (64 registers a thread at most)
+    static constexpr int value = TILE * 12 * 2 > 120 * 1024 ? 1 : 65536 / (THREADS * 64);
+};
+
+// rows j of a thread (j % 8) whose peers come from match.any (the others use ballots)
+#ifndef SBH_MATCH_MASK
+#define SBH_MATCH_MASK 0xAA
+#endif
+template <typename ValueFn, int TILE, int THREADS, bool kCarry = false>
+__global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value))
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
                      uint32_t* __restrict__ status) {
+    constexpr bool kDig = ScatterDig<ValueFn, kCarry>::value;
+    using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig>;
+    constexpr int kW = Smem::kW, kG = Smem::kG, kWpg = kW / kG;
+    constexpr int kIt = TILE / THREADS;
+    static_assert(TILE % THREADS == 0 && THREADS % 128 == 0 && THREADS <= 1024, "tile geometry");
+    static_assert(TILE < 65536, "16-bit counters");
     if (!plan->active[pos]) return;
-    const DigitOf<ValueFn> digit_of{value_of, pos * kRadixBits};
+    const int shift = pos * kRadixBits;
+    const DigitOf<ValueFn> digit_of{value_of, shift};
     const int src = plan->src[pos], dst = plan->dst[pos];
     const uint64_t* __restrict__ in_k = buf.keys(src);
     const uint32_t* __restrict__ in_p = buf.ptrs(src);
@@ -534,15 +562,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint32_t ntl = (hi - lo + TILE - 1) / TILE;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    ScatterSmem<TILE, kCarry>& sm = *reinterpret_cast<ScatterSmem<TILE, kCarry>*>(smem_raw);
-    constexpr int kSIpt = TILE / kSThreads;
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    // thread t < 128 carries the next output rows of digits 2t and 2t + 1
-    uint32_t run0 = 0, run1 = 0;
-    if (tid < kRadix / 2) {
-        run0 = chunk_base[blockIdx.x * kRadix + 2 * tid];
-        run1 = chunk_base[blockIdx.x * kRadix + 2 * tid + 1];
-    }
 
     auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * TILE <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
@@ -553,6 +574,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             if (kCarry) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
         }
     };
+    for (int x = tid; x < kW * (kRadix / 2 + 1); x += THREADS) (&sm.whist2[0][0])[x] = 0;
+    for (int x = tid; x < kRadix; x += THREADS) sm.run[x] = chunk_base[blockIdx.x * kRadix + x];
     if (tid == 0) {
         mbar_init(&sm.mbar[0], 1);
         mbar_init(&sm.mbar[1], 1);
@@ -567,7 +590,6 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         const int b = i & 1;
         const uint32_t base = lo + i * TILE;
         const uint32_t valid = min(hi - base, (uint32_t)TILE);
-        for (int x = tid; x < kSWarps * (kRadix / 2 + 1); x += kSThreads) (&sm.whist2[0][0])[x] = 0;
         bool expired = false;
         if (bulk_tile(i)) {
             uint32_t polls = 0;
@@ -578,147 +600,193 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                 }
             phase[b] ^= 1u;
         } else {
-            for (uint32_t s = tid; s < valid; s += kSThreads) {
+            for (uint32_t s = tid; s < valid; s += THREADS) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
                 if (kCarry) sm.vals[b][s] = in_v[base + s];
             }
         }
-        // a tile whose data never arrived is not scattered (its rows stay unwritten)
+        // B0.  A tile whose data never arrived is not scattered (its rows
+        // stay unwritten).  Tile i - 1 is done with the other buffer.
         const bool tile_ok = !__syncthreads_or(expired);
-
-        // rows of this thread: warp w owns 32 * kSIpt consecutive rows
-        uint64_t k[kSIpt];
-        uint32_t p[kSIpt], dg[kSIpt], rank[kSIpt], cv[kSIpt];
-        const uint32_t wofs = warp * 32 * kSIpt + lane;
-        const bool full = valid == (uint32_t)TILE;
-        if (kCarry) {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) cv[j] = sm.vals[b][wofs + j * 32];
-        }
-#pragma unroll
-        for (int j = 0; j < kSIpt; ++j) {
-            k[j] = sm.keys[b][wofs + j * 32];
-            p[j] = sm.ptrs[b][wofs + j * 32];
-            if (kCarry) dg[j] = (full || wofs + j * 32 < valid) ? (cv[j] >> (pos * kRadixBits)) & (kRadix - 1) : kRadix;
-            else dg[j] = (full || wofs + j * 32 < valid) ? digit_of(k[j]) : kRadix;
-        }
-        // warp multisplit (see onesweep_kernel): the peers of a row come from
-        // digit-bit ballots (a ninth bit when the tile has rows past the end);
-        // the group leader's counter update is predicated, not branched
-        const uint32_t lt = lanemask_lt();
-        if (full) {
-            // half the items find their peers with match.any, half with digit
-            // ballots: the two run on different pipes, so neither saturates
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t peers =
-                    (j & 1) ? __match_any_sync(0xffffffffu, dg[j]) : warp_peers<kRadixBits>(dg[j]);
-                const int leader = __ffs(peers) - 1;
-                const uint32_t sh = (dg[j] & 1u) * 16u;
-                const uint32_t c = smem_atomic_add_if((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
-                                                      (uint32_t)__popc(peers) << sh);
-                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
-                const int leader = __ffs(peers) - 1;
-                const uint32_t sh = (dg[j] & 1u) * 16u;
-                const uint32_t c = smem_atomic_add_if((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
-                                                      (uint32_t)__popc(peers) << sh);
-                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, c, leader) >> sh) & 0xFFFFu);
-            }
-        }
-        __syncthreads();
-
-        // per digit pair (threads 0..127): warp offsets, tile counts, local starts
-        uint32_t c0 = 0, c1 = 0, x = 0;
-        if (tid < kRadix / 2) {
-#pragma unroll
-            for (int w = 0; w < kSWarps; ++w) {
-                const uint32_t word = sm.whist2[w][tid];
-                sm.whist2[w][tid] = c0 | (c1 << 16);
-                c0 += word & 0xFFFFu;
-                c1 += word >> 16;
-            }
-            x = c0 + c1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            if (lane == 31) sm.scan_tmp[warp] = x;
-        }
-        __syncthreads();
-        if (tid < kRadix / 2) {
-            uint32_t before = 0;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) before += (w < (int)warp) ? sm.scan_tmp[w] : 0u;
-            const uint32_t l0 = before + x - c0 - c1, l1 = l0 + c0;
-            sm.local_start[2 * tid] = l0;
-            sm.local_start[2 * tid + 1] = l1;
-            sm.gbase_rel[2 * tid] = run0 - l0;
-            sm.gbase_rel[2 * tid + 1] = run1 - l1;
-            run0 += c0;
-            run1 += c1;
-        }
-        __syncthreads();
-
-        if (full) {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
-                const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
-                sm.keys[b][slot] = k[j];
-                sm.ptrs[b][slot] = p[j];
-                sm.dig[slot] = static_cast<typename ScatterSmem<TILE, kCarry>::Tag>(kCarry ? cv[j] : dg[j]);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                if (dg[j] < kRadix) {
-                    const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
-                    const uint32_t slot = sm.local_start[dg[j]] + wo + rank[j];
-                    sm.keys[b][slot] = k[j];
-                    sm.ptrs[b][slot] = p[j];
-                    sm.dig[slot] = static_cast<typename ScatterSmem<TILE, kCarry>::Tag>(kCarry ? cv[j] : dg[j]);
-                }
-            }
-        }
-        __syncthreads();
-        auto digit_at = [&](uint32_t s) -> uint32_t {
-            return kCarry ? (static_cast<uint32_t>(sm.dig[s]) >> (pos * kRadixBits)) & (kRadix - 1) : sm.dig[s];
-        };
-        if (tile_ok && full) {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t s = tid + j * kSThreads;
-                const uint32_t g = sm.gbase_rel[digit_at(s)] + s;
-                out_k[g] = sm.keys[b][s];
-                out_p[g] = sm.ptrs[b][s];
-                if (kCarry) out_v[g] = sm.dig[s];
-            }
-        } else if (tile_ok) {
-#pragma unroll
-            for (int j = 0; j < kSIpt; ++j) {
-                const uint32_t s = tid + j * kSThreads;
-                if (s < valid) {
-                    const uint32_t g = sm.gbase_rel[digit_at(s)] + s;
-                    out_k[g] = sm.keys[b][s];
-                    out_p[g] = sm.ptrs[b][s];
-                    if (kCarry) out_v[g] = sm.dig[s];
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && i >= 1) {
             fence_proxy_async_smem();
-            issue(b, i + 2);
+            issue(b ^ 1, i + 1);
         }
+
+        // the tile body, compiled separately for full tiles (no per-row
+        // bounds) and for the ragged last tile
+        auto tile = [&](auto full_tag) {
+            constexpr bool full = decltype(full_tag)::value;
+            uint64_t* __restrict__ kb = sm.keys[b];
+            uint32_t* __restrict__ pb = sm.ptrs[b];
+            uint16_t* __restrict__ vb = sm.vals[kCarry ? b : 0];
+            // rows of this thread: warp w owns 32 * kIt consecutive rows
+            uint64_t k[kIt];
+            uint32_t p[kIt], dg[kIt], rank[kIt], cv[kIt];
+            const uint32_t wofs = warp * 32 * kIt + lane;
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) {
+                k[j] = kb[wofs + j * 32];
+                p[j] = pb[wofs + j * 32];
+                if (kCarry) cv[j] = vb[wofs + j * 32];
+            }
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) {
+                const bool in = full || wofs + j * 32 < valid;
+                if (kCarry) dg[j] = in ? (cv[j] >> shift) & (kRadix - 1) : kRadix;
+                else dg[j] = in ? digit_of(k[j]) : kRadix;
+            }
+            // warp multisplit: the peers of a row (lanes with its digit) from
+            // match.any or from digit-bit ballots (a ninth bit when the tile has
+            // rows past the end); the group leader adds the group's size to the
+            // warp's counter, predicated rather than branched, and the old value
+            // is broadcast.
+            const uint32_t lt = lanemask_lt();
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) {
+                uint32_t peers;
+                if constexpr (full)  // alternate pipes: half match.any, half ballots
+                    peers = ((SBH_MATCH_MASK >> (j & 7)) & 1) ? __match_any_sync(0xffffffffu, dg[j])
+                                                              : warp_peers<kRadixBits>(dg[j]);
+                else
+                    peers = warp_peers<kRadixBits + 1>(dg[j]);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t sh = (dg[j] & 1u) * 16u;
+                const uint32_t old = smem_atomic_add_if_relaxed((int)lane == leader, &sm.whist2[warp][dg[j] >> 1],
+                                                                (uint32_t)__popc(peers) << sh);
+                rank[j] = __popc(peers & lt) + ((__shfl_sync(0xffffffffu, old, leader) >> sh) & 0xFFFFu);
+            }
+            __syncthreads();  // B1
+
+            // exclusive counts over the warps of each group (all threads: digit
+            // pair tid % 128, group tid / 128), and the group totals
+            {
+                const uint32_t pr = tid & (kRadix / 2 - 1), g = tid / (kRadix / 2);
+                uint32_t acc = 0;
+#pragma unroll
+                for (int w = 0; w < kWpg; ++w) {
+                    const uint32_t word = sm.whist2[g * kWpg + w][pr];
+                    sm.whist2[g * kWpg + w][pr] = acc;
+                    acc += word;
+                }
+                sm.gsum[g][pr] = acc;
+            }
+            __syncthreads();  // B2
+
+            // warp g < kG: lane l takes digits 8l .. 8l + 7; the tile's exclusive
+            // digit scan, plus the counts of earlier groups, gives each (group,
+            // digit) its first staged slot; warp 0 also moves the digits' output
+            // rows on
+            if (warp < (uint32_t)kG) {
+                // (gsum is read twice so that few registers are live next to the rows)
+                uint32_t lsum = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int gg = 0; gg < kG; ++gg) {
+                        const uint32_t v = sm.gsum[gg][4 * lane + q];
+                        lsum += (v & 0xFFFFu) + (v >> 16);
+                    }
+                uint32_t x = lsum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                uint32_t st = x - lsum;
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t tot = 0, pre = 0;
+#pragma unroll
+                    for (int gg = 0; gg < kG; ++gg) {
+                        const uint32_t v = sm.gsum[gg][4 * lane + q];
+                        tot += v;
+                        pre += (gg < (int)warp) ? v : 0u;
+                    }
+                    const uint32_t c0 = tot & 0xFFFFu, c1 = tot >> 16;
+                    const uint32_t d0 = 8 * lane + 2 * q;
+                    sm.gstart[warp][d0] = static_cast<uint16_t>(st + (pre & 0xFFFFu));
+                    sm.gstart[warp][d0 + 1] = static_cast<uint16_t>(st + c0 + (pre >> 16));
+                    if (warp == 0) {
+                        const uint32_t r0 = sm.run[d0], r1 = sm.run[d0 + 1];
+                        sm.gbase_rel[d0] = r0 - st;
+                        sm.gbase_rel[d0 + 1] = r1 - (st + c0);
+                        sm.run[d0] = r0 + c0;
+                        sm.run[d0 + 1] = r1 + c1;
+                    }
+                    st += c0 + c1;
+                }
+            }
+            __syncthreads();  // B3
+
+            // stage the tile in digit order (in place: all rows are in registers)
+            {
+                const uint32_t grp = warp / kWpg;
+#pragma unroll
+                for (int j = 0; j < kIt; ++j) {
+                    if (full || dg[j] < kRadix) {
+                        const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
+                        const uint32_t slot = sm.gstart[grp][dg[j]] + wo + rank[j];
+                        kb[slot] = k[j];
+                        pb[slot] = p[j];
+                        if (kCarry) vb[slot] = static_cast<uint16_t>(cv[j]);
+                        if (kDig) sm.dig[slot] = static_cast<uint8_t>(dg[j]);
+                    }
+                }
+            }
+            __syncthreads();  // B4
+
+            if (tile_ok) {
+#pragma unroll
+                for (int j = 0; j < kIt; ++j) {
+                    const uint32_t s = tid + j * THREADS;
+                    if (full || s < valid) {
+                        const uint64_t key = kb[s];
+                        uint32_t d;
+                        if (kCarry) d = (static_cast<uint32_t>(vb[s]) >> shift) & (kRadix - 1);
+                        else if (kDig) d = sm.dig[s];
+                        else d = static_cast<uint32_t>(key >> shift) & (kRadix - 1);
+                        const uint32_t g = sm.gbase_rel[d] + s;
+                        out_k[g] = key;
+                        out_p[g] = pb[s];
+                        if (kCarry) out_v[g] = vb[s];
+                    }
+                }
+            }
+        };
+        if (valid == (uint32_t)TILE)
+            tile(std::true_type{});
+        else
+            tile(std::false_type{});
+        // counters of the next tile (B0 orders this before its ranking)
+        for (int x = tid; x < kW * (kRadix / 2 + 1); x += THREADS) (&sm.whist2[0][0])[x] = 0;
     }
 }
+
+// Launch geometry of the chunked scatter: one chunk of whole tiles per
+// resident CTA (at most kMaxChunks).
+struct ChunkGeom {
+    uint32_t chunk = 0, nchunks = 0;
+    size_t smem = 0;
+};
+
+template <typename ValueFn, int TILE, int THREADS, bool kCarry>
+int chunk_geometry(uint64_t n, ChunkGeom* g) {
+    auto kern = chunk_scatter_kernel<ValueFn, TILE, THREADS, kCarry>;
+    const size_t smem = sizeof(ScatterSmem<TILE, THREADS, kCarry, ScatterDig<ValueFn, kCarry>::value>);
+    SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ttiles = (n + TILE - 1) / TILE;
+    const uint64_t want = min_u64(min_u64(ttiles, (uint64_t)num_sms() * per_sm), kMaxChunks);
+    g->chunk = (uint32_t)(((ttiles + want - 1) / want) * TILE);
+    g->nchunks = (uint32_t)((n + g->chunk - 1) / g->chunk);
+    g->smem = smem;
+    return SBH_OK;
+}
+
 
 // ------------------------------------------------------------------ scratch and launch
 struct SortScratch {
@@ -757,6 +825,33 @@ inline SortScratch sort_carve(void* scratch, uint64_t n) {
     return s;
 }
 
+// The passes of a large sort: per pass, chunk digit counts -> chunk offsets
+// -> scatter.
+template <typename ValueFn, int TILE, int THREADS>
+int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, ValueFn value_of, int bulk_ok,
+                   cudaStream_t s, const std::string& n_count, const std::string& n_scan, const std::string& n_scat) {
+    ChunkGeom g;
+    const int rc = chunk_geometry<ValueFn, TILE, THREADS, false>(n32, &g);
+    if (rc) return rc;
+    const uint32_t limit = spin_limit();
+    uint32_t* status = status_word();
+    for (int pos = 0; pos < kPositions; ++pos) {
+        SBH_TIMED(n_count.c_str(), s,
+                  chunk_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk, sc.chunk_hist,
+                                                                        value_of));
+        SBH_LAUNCHED();
+        SBH_TIMED(n_scan.c_str(), s,
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, g.nchunks, sc.gbase,
+                                                       sc.chunk_base));
+        SBH_LAUNCHED();
+        SBH_TIMED(n_scat.c_str(), s,
+                  (chunk_scatter_kernel<ValueFn, TILE, THREADS, false><<<g.nchunks, THREADS, g.smem, s>>>(
+                      b, n32, pos, sc.plan, g.chunk, sc.chunk_base, value_of, bulk_ok, limit, status)));
+        SBH_LAUNCHED();
+    }
+    return SBH_OK;
+}
+
 // Stable sort of (in_k, in_p) by value_of(key) into (out_k, out_p); the
 // positions at or above npos of the value are treated as zero.
 template <typename ValueFn>
@@ -790,35 +885,8 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     if (n >= kChunkedMinRows) {
-        // scatter tile: 4096 rows (two CTAs per SM) or, with SBH_SCATTER_TILE=8192, 8192 rows (one CTA per SM)
-        static const int tile_rows = [] {
-            const char* e = getenv("SBH_SCATTER_TILE");
-            return (e && atoi(e) == 8192) ? 8192 : 4096;
-        }();
-        auto scat = tile_rows == 8192 ? chunk_scatter_kernel<ValueFn, 8192> : chunk_scatter_kernel<ValueFn, 4096>;
-        const size_t ssmem = tile_rows == 8192 ? sizeof(ScatterSmem<8192, false>) : sizeof(ScatterSmem<4096, false>);
-        SBH_CUDA(cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
-        int per_sm = 0;
-        SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scat, kSThreads, ssmem));
-        if (per_sm < 1) per_sm = 1;
-        const uint64_t want = min_u64(min_u64(ntiles, (uint64_t)sms * per_sm), kMaxChunks);
-        const uint64_t ttiles = (n + tile_rows - 1) / tile_rows;
-        const uint32_t chunk = (uint32_t)(((ttiles + want - 1) / want) * tile_rows);
-        const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
-        for (int pos = 0; pos < kPositions; ++pos) {
-            SBH_TIMED(n_count.c_str(), s,
-                      chunk_count_kernel<ValueFn><<<nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_hist,
-                                                                          value_of));
-            SBH_LAUNCHED();
-            SBH_TIMED(n_scan.c_str(), s,
-                      chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, nchunks, sc.gbase,
-                                                           sc.chunk_base));
-            SBH_LAUNCHED();
-            SBH_TIMED(n_scat.c_str(), s,
-                      scat<<<nchunks, kSThreads, ssmem, s>>>(b, n32, pos, sc.plan, chunk, sc.chunk_base, value_of,
-                                                           bulk_ok, limit, status));
-            SBH_LAUNCHED();
-        }
+        const int rc = chunked_passes<ValueFn, 4096, 512>(b, n32, sc, value_of, bulk_ok, s, n_count, n_scan, n_scat);
+        if (rc) return rc;
     } else {
         auto kern = onesweep_kernel<ValueFn>;
         SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,0 +1,190 @@
+"""Window pipelines composed of the C ABI calls (orchestration only: every
+step runs in the kernels of libsbh.so).
+
+batched_windows  per-key count, sum and top-K inside each of many tumbling
+    windows laid end to end (Sec. 4.2 "Windowing" and "Keyed Aggregation";
+    the TopK Per Key and Sum Per Key benchmarks of Sec. 7).  Two schedules
+    with identical results:
+      "batched"  one pass over all windows: Extract writes composite keys
+                 (window << (64 - window_bits)) | key, so one sort, one keyed
+                 reduction and one top-K group every window at once; window
+                 w's results are the output keys in [w << shift, (w + 1) <<
+                 shift), found by binary search (the window-range kernel).
+      "loop"     one Extract, Sort, keyed reduction and top-K per window.
+sliding_join  the temporal join of two streams over sliding windows built
+    from panes (Sec. 4.2 "Temporal Join" and "Windowing"): every pane of
+    every stream is extracted (from page-locked host memory when the key
+    column lives there) and sorted once; each window merges its panes per
+    side and joins the two sides.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sbh
+
+
+def _u64(n, dev):
+    return torch.empty(max(1, n), dtype=torch.uint64, device=dev)
+
+
+def _u32(n, dev):
+    return torch.empty(max(1, n), dtype=torch.uint32, device=dev)
+
+
+class WindowResults:
+    """Per-window grouping results held on the device.
+
+    For window w, rows [begin[w], end[w]) of keys / counts / sums and of the
+    top-K arrays belong to it, in key order.  keys hold the raw keys (window
+    bits removed) once `window()` is called."""
+
+    def __init__(self, keys, counts, sums, nvalid, tvals, tptrs, begin, end, shift, K):
+        self.keys, self.counts, self.sums = keys, counts, sums
+        self.nvalid, self.tvals, self.tptrs = nvalid, tvals, tptrs
+        self.begin, self.end, self.shift, self.K = begin, end, shift, K
+
+    def window(self, w):
+        """(keys, counts, sums, nvalid, top values [m, K], top ptrs [m, K]) as host arrays."""
+        b, e = int(self.begin[w]), int(self.end[w])
+        mask = np.uint64((1 << self.shift) - 1) if self.shift < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+        keys = self.keys[b:e].cpu().numpy() & mask
+        K = self.K
+        return (keys, self.counts[b:e].cpu().numpy(), self.sums[b:e].cpu().numpy(), self.nvalid[b:e].cpu().numpy(),
+                self.tvals[b * K:e * K].cpu().numpy().reshape(-1, K), self.tptrs[b * K:e * K].cpu().numpy().reshape(-1, K))
+
+
+def batched_windows(key_col, val_col, offsets, K=3, schedule="batched"):
+    """key_col, val_col: device uint64 columns; offsets: host array of
+    nwin + 1 non-decreasing row offsets.  Returns WindowResults.  The
+    batched schedule needs every key below 2^(64 - window_bits(nwin)) and
+    falls back to the loop when one is not."""
+    offsets = np.asarray(offsets, dtype=np.uint64)
+    nwin = offsets.size - 1
+    if schedule == "batched":
+        res = _batched(key_col, val_col, offsets, K)
+        if res is not None:
+            return res
+    return _loop(key_col, val_col, offsets, K)
+
+
+def _batched(key_col, val_col, offsets, K):
+    dev = key_col.device
+    nwin = offsets.size - 1
+    row0, n = int(offsets[0]), int(offsets[-1] - offsets[0])
+    shift = 64 - sbh.window_bits(nwin)
+    d_off = torch.from_numpy(offsets.astype(np.int64)).to(dev).view(torch.uint64)
+    keys, ptrs, key_or = _u64(n, dev), _u32(n, dev), _u64(1, dev)
+    sbh.sbh_kpa_extract_windows(key_col, d_off, row0, n, keys, ptrs, key_or)
+    if shift < 64 and int(key_or.item()) >> shift:
+        return None  # some key uses the window bits
+    sk, sp = _u64(n, dev), _u32(n, dev)
+    sbh.sbh_kpa_sort(keys[:n], ptrs[:n], sk, sp)
+    del keys, ptrs
+    ok, oc, osum, nk = _u64(n, dev), _u64(n, dev), _u64(n, dev), _u64(1, dev)
+    sbh.sbh_group_reduce(sk[:n], sp[:n], val_col, ok, oc, osum, n, nk)
+    tk, tnv, tv, tp, nkt = (_u64(n, dev), torch.empty(max(1, n), dtype=torch.uint8, device=dev), _u64(n * K, dev),
+                            _u32(n * K, dev), _u64(1, dev))
+    sbh.sbh_topk(sk[:n], sp[:n], val_col, K, tk, tnv, tv, tp, n, nkt)
+    m = int(nk.item())
+    starts = (torch.arange(nwin, dtype=torch.int64, device=dev) << shift).view(torch.uint64) if shift < 64 else \
+        torch.zeros(1, dtype=torch.uint64, device=dev)
+    rb, re_ = _u64(nwin, dev), _u64(nwin, dev)
+    if shift < 64:
+        sbh.sbh_window_ranges(ok[:m], starts, 1 << shift, rb[:nwin], re_[:nwin])
+        begin, end = rb[:nwin].cpu().numpy(), re_[:nwin].cpu().numpy()
+    else:
+        begin, end = np.zeros(1, np.uint64), np.array([m], np.uint64)
+    return WindowResults(ok, oc, osum, tnv, tv, tp, begin, end, shift, K)
+
+
+def _loop(key_col, val_col, offsets, K):
+    dev = key_col.device
+    nwin = offsets.size - 1
+    row0, n = int(offsets[0]), int(offsets[-1] - offsets[0])
+    sizes = np.diff(offsets).astype(np.int64)
+    big = int(sizes.max()) if nwin else 0
+    keys, ptrs, sk, sp = _u64(big, dev), _u32(big, dev), _u64(big, dev), _u32(big, dev)
+    sort_scr = torch.empty(max(1, sbh.sort_scratch_bytes(big)), dtype=torch.uint8, device=dev)
+    ok, oc, osum = _u64(n, dev), _u64(n, dev), _u64(n, dev)
+    tk, tnv, tv, tp = _u64(n, dev), torch.empty(max(1, n), dtype=torch.uint8, device=dev), _u64(n * K, dev), \
+        _u32(n * K, dev)
+    nk, nkt = _u64(nwin, dev), _u64(nwin, dev)
+    red_scr = top_scr = None
+    for w in range(nwin):
+        o, m = int(offsets[w]) - row0, int(sizes[w])
+        if m == 0:
+            nk[w:w + 1].zero_()
+            nkt[w:w + 1].zero_()
+            continue
+        sbh.sbh_kpa_extract(key_col, row0 + o, m, keys, ptrs)
+        sbh.sbh_kpa_sort(keys[:m], ptrs[:m], sk, sp, scratch=sort_scr)
+        red_scr = sbh.sbh_group_reduce(sk[:m], sp[:m], val_col, ok[o:], oc[o:], osum[o:], m, nk[w:w + 1],
+                                       scratch=_fit(red_scr, sbh.group_reduce_scratch_bytes(m, 8), dev))
+        top_scr = sbh.sbh_topk(sk[:m], sp[:m], val_col, K, tk[o:], tnv[o:], tv[o * K:], tp[o * K:], m, nkt[w:w + 1],
+                               scratch=_fit(top_scr, sbh.topk_scratch_bytes(m, K, 8), dev))
+    begin = offsets[:-1] - offsets[0]
+    end = begin + nk.cpu().numpy()[:nwin]
+    return WindowResults(ok, oc, osum, tnv, tv, tp, begin, end, 64, K)
+
+
+def _fit(buf, nbytes, dev):
+    if buf is None or buf.numel() < nbytes:
+        return torch.empty(max(1, nbytes), dtype=torch.uint8, device=dev)
+    return buf
+
+
+class JoinResults:
+    """Pairs of every window: window w's pairs are rows [w * cap, w * cap +
+    npairs[w]) of ptr_l / ptr_r, in (key, ptrL, ptrR) order."""
+
+    def __init__(self, ptr_l, ptr_r, npairs, cap):
+        self.ptr_l, self.ptr_r, self.npairs, self.cap = ptr_l, ptr_r, npairs, cap
+
+    def window(self, w):
+        b = w * self.cap
+        e = b + int(self.npairs[w])
+        return self.ptr_l[b:e].cpu().numpy(), self.ptr_r[b:e].cpu().numpy()
+
+
+def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, pair_cap=262_144, windows=None):
+    """Equi-join of L and R inside every sliding window [w * stride, w *
+    stride + window) of the first n_rows rows (ts = row index).  Key columns
+    may be device tensors or page-locked host tensors.  `windows` (an
+    iterable of window indices) restricts the windows joined; all panes are
+    still prepared.  Returns JoinResults."""
+    dev = torch.device("cuda")
+    if window % stride:
+        raise ValueError("window must be a multiple of stride")
+    per = window // stride
+    npanes = n_rows // stride
+    nwin = max(0, npanes - per + 1)
+    sides = []
+    for col in (lkey_col, rkey_col):
+        keys, ptrs = _u64(npanes * stride, dev), _u32(npanes * stride, dev)
+        sbh.sbh_kpa_extract(col, 0, npanes * stride, keys, ptrs)
+        scr = torch.empty(max(1, sbh.sort_scratch_bytes(stride)), dtype=torch.uint8, device=dev)
+        for p in range(npanes):
+            seg = slice(p * stride, (p + 1) * stride)
+            sbh.sbh_kpa_sort(keys[seg], ptrs[seg], keys[seg], ptrs[seg], scratch=scr)  # in place
+        sides.append((keys, ptrs))
+    wl = list(range(nwin)) if windows is None else list(windows)
+    ml, mlp, mr, mrp = _u64(window, dev), _u32(window, dev), _u64(window, dev), _u32(window, dev)
+    out_l, out_r = _u32(len(wl) * pair_cap, dev), _u32(len(wl) * pair_cap, dev)
+    npairs = _u64(len(wl), dev)
+    join_scr = None
+    for i, w in enumerate(wl):
+        merged = []
+        for (keys, ptrs), mk, mp in ((sides[0], ml, mlp), (sides[1], mr, mrp)):
+            runs = [(keys[(w + j) * stride:(w + j + 1) * stride], ptrs[(w + j) * stride:(w + j + 1) * stride])
+                    for j in range(per)]
+            sbh.sbh_kpa_merge(runs, mk, mp)
+            merged.append((mk, mp))
+        join_scr = sbh.sbh_join(*merged[0], *merged[1], out_l[i * pair_cap:], out_r[i * pair_cap:], pair_cap,
+                                npairs[i:i + 1], scratch=_fit(join_scr, sbh.join_scratch_bytes(window, window), dev))
+    counts = npairs.cpu().numpy()[:len(wl)]
+    if len(wl) and counts.max() > pair_cap:
+        over = [w for w, c in zip(wl, counts) if c > pair_cap]
+        raise RuntimeError(f"windows {over[:4]} have more than pair_cap={pair_cap} pairs; raise pair_cap")
+    return JoinResults(out_l, out_r, counts, pair_cap), wl

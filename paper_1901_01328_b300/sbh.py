@@ -28,7 +28,7 @@ MLP_PARAMS = 1153
 LEARNED_MODEL_BYTES = 16384
 LEARNED_CAPACITY = 8192
 LEARNED_STATS = ("bucket_ids", "heavy_cells", "sorted_buckets", "one_key_buckets", "heavy_buckets",
-                 "overflow_buckets", "overflow_rows", "largest_bucket")
+                 "overflow_buckets", "overflow_rows", "largest_bucket", "radix_buckets", "radix_rows")
 
 _ERRNAMES = {1: "SBH_EINVAL", 2: "SBH_ENOSPACE", 3: "SBH_ETIMEOUT", 4: "SBH_ECUDA"}
 
@@ -54,6 +54,8 @@ def _load() -> ctypes.CDLL:
         "sbh_profile_collect": ([i32, vp, i32, vp], i32),
         "sbh_window_ranges": ([vp, i32, u64, vp, u64, u64, vp, vp, vp], i32),
         "sbh_kpa_extract": ([vp, u64, u64, vp, vp, vp, vp, u64, vp], i32),
+        "sbh_kpa_extract_windows": ([vp, vp, u64, u64, u64, vp, vp, vp, vp], i32),
+        "sbh_window_bits": ([u64], i32),
         "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
         "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
@@ -75,7 +77,8 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
             "sbh_profile_enable", "sbh_profile_collect",
-            "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_sort", "sbh_kpa_merge", "sbh_group_reduce",
+            "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_extract_windows", "sbh_window_bits", "sbh_kpa_sort",
+            "sbh_kpa_merge", "sbh_group_reduce",
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
             "sbh_kpa_sort_learned",
             "sbh_topk", "sbh_join")
@@ -159,6 +162,16 @@ def sbh_kpa_extract(key_col, row_begin, n, keys_out, ptrs_out, key_or=None, samp
                                 sample_stride, _stream(stream)), "sbh_kpa_extract")
 
 
+def sbh_kpa_extract_windows(key_col, offsets, row_begin, n, keys_out, ptrs_out, key_or=None, stream=None):
+    """offsets: device uint64 tensor of nwin + 1 row offsets."""
+    _check(_lib.sbh_kpa_extract_windows(_p(key_col), _p(offsets), offsets.numel() - 1, row_begin, n, _p(keys_out),
+                                        _p(ptrs_out), _p(key_or), _stream(stream)), "sbh_kpa_extract_windows")
+
+
+def window_bits(nwin: int) -> int:
+    return _lib.sbh_window_bits(nwin)
+
+
 def sbh_kpa_sort(keys_in, ptrs_in, keys_out, ptrs_out, scratch=None, stream=None):
     """Sorts n = keys_in.numel() pairs.  Allocates scratch if none is given;
     returns the scratch buffer used."""
@@ -174,6 +187,27 @@ def sbh_kpa_sort(keys_in, ptrs_in, keys_out, ptrs_out, scratch=None, stream=None
 def sort_scratch_bytes(n: int) -> int:
     nbytes = ctypes.c_size_t(0)
     _check(_lib.sbh_kpa_sort(None, None, None, None, n, None, ctypes.byref(nbytes), None), "sbh_kpa_sort")
+    return nbytes.value
+
+
+def group_reduce_scratch_bytes(n: int, val_bytes: int = 8) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_group_reduce(None, None, n, None, val_bytes, None, None, None, 0, None, None, ctypes.byref(nbytes),
+                                 None), "sbh_group_reduce")
+    return nbytes.value
+
+
+def topk_scratch_bytes(n: int, K: int, val_bytes: int = 8) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_topk(None, None, n, None, val_bytes, K, None, None, None, None, 0, None, None,
+                         ctypes.byref(nbytes), None), "sbh_topk")
+    return nbytes.value
+
+
+def join_scratch_bytes(nl: int, nr: int) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_join(None, None, nl, None, None, nr, None, None, 0, None, None, ctypes.byref(nbytes), None),
+           "sbh_join")
     return nbytes.value
 
 

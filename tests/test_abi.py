@@ -67,3 +67,13 @@ def test_host_side_argument_errors(L):
     assert lib.sbh_group_reduce(None, None, 10, None, 8, None, None, None, 0, None, None, None, None) == L.SBH_EINVAL
     assert lib.sbh_kpa_extract(fake, (1 << 32) - 5, 10, fake, fake, None, None, 0, None) == L.SBH_EINVAL
     assert lib.sbh_window_ranges(fake, 3, 10, fake, 5, 2, fake, fake, None) == L.SBH_EINVAL
+
+
+def test_window_bits_and_batched_extract_arguments(L):
+    assert [L.window_bits(x) for x in (1, 2, 3, 4096, 4097)] == [1, 2, 2, 13, 13]
+    lib = L.lib()
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.sbh_kpa_extract_windows(fake, fake, 0, 0, 10, fake, fake, None, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract_windows(fake, fake, 4, (1 << 32) - 5, 10, fake, fake, None, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract_windows(None, fake, 4, 0, 10, fake, fake, None, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract_windows(None, None, 4, 0, 0, None, None, None, None) == L.SBH_OK

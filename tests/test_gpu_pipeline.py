@@ -1,0 +1,117 @@
+"""The window pipelines on the GPU against the oracle, window by window:
+many uneven tumbling windows (per-key count, sum and top-3 in each; both
+schedules) and the sliding-window temporal join over panes (key columns in
+page-locked host memory).  Small cases check every window; the full-size
+workloads check sampled windows."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from tests.gpu_util import cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import pipeline
+    return pipeline
+
+
+def _oracle_window(keys, vals, lo, m, K):
+    k, p = oracle.sort(*oracle.extract(keys, lo, m))
+    uk, uc, us = oracle.group_sum_count(k, p, vals)
+    tk, tn, tv, tp = oracle.topk(k, p, vals, K)
+    assert np.array_equal(tk, uk)
+    return uk, uc, us, tn, tv, tp
+
+
+def _check_window(res, w, keys, vals, offsets, K):
+    got = res.window(w)
+    exp = _oracle_window(keys, vals, int(offsets[w]), int(offsets[w + 1] - offsets[w]), K)
+    for g, e in zip(got, exp):
+        assert np.array_equal(g, e.reshape(g.shape)), f"window {w}"
+
+
+@pytest.mark.parametrize("schedule", ["batched", "loop"])
+def test_batched_windows_every_window(P, schedule):
+    b = gen.batched_windows(48, 8, size_hi=60_000)
+    keys, vals, off = b["keys"], b["vals"], b["offsets"]
+    res = P.batched_windows(cuda(keys), cuda(vals), off, K=3, schedule=schedule)
+    for w in range(off.size - 1):
+        _check_window(res, w, keys, vals, off, 3)
+
+
+def test_batched_windows_edge_cases(P):
+    # one window; an empty window; windows that are one row; a heavy key
+    keys = np.concatenate([np.full(5000, 7, np.uint64), gen.uniform(3, 1, 3000, 0, 100, np.uint64)])
+    vals = gen.uniform(3, 2, keys.size, 0, 0, np.uint64)
+    for off in (np.array([0, keys.size], np.uint64), np.array([0, 1, 1, 2, 4000, keys.size], np.uint64)):
+        for schedule in ("batched", "loop"):
+            res = P.batched_windows(cuda(keys), cuda(vals), off, K=3, schedule=schedule)
+            for w in range(off.size - 1):
+                _check_window(res, w, keys, vals, off, 3)
+
+
+def test_batched_windows_falls_back_when_keys_use_window_bits(P):
+    b = gen.batched_windows(16, 4, size_hi=20_000)
+    keys, vals, off = b["keys"].copy(), b["vals"], b["offsets"]
+    keys[5] |= np.uint64(1) << np.uint64(63)
+    res = P.batched_windows(cuda(keys), cuda(vals), off, K=3, schedule="batched")
+    assert res.shift == 64  # the loop ran
+    for w in (0, 15):
+        _check_window(res, w, keys, vals, off, 3)
+
+
+def test_batched_windows_full_size_sampled(P):
+    # 4096 windows (64 streams), sizes lognormal(10.4, 1.5) in [1K, 4M],
+    # keys Zipf(1.0) over 10M: the batched schedule, sampled windows checked
+    b = gen.batched_windows()
+    keys, vals, off = b["keys"], b["vals"], b["offsets"]
+    res = P.batched_windows(cuda(keys), cuda(vals), off, K=3, schedule="batched")
+    sizes = np.diff(off)
+    for w in {0, int(np.argmax(sizes)), int(np.argmin(sizes)), 4095}:
+        _check_window(res, w, keys, vals, off, 3)
+    # every window's counts add up to its size
+    cnt = res.counts[: int(res.end[-1])].cpu().numpy()
+    per = np.add.reduceat(cnt, res.begin.astype(np.int64)) if cnt.size else cnt
+    assert np.array_equal(per.astype(np.uint64), sizes)
+
+
+def _pinned(a):
+    t = torch.from_numpy(a.astype(np.int64, copy=False).view(np.int64)).pin_memory()
+    return t.view(torch.uint64)
+
+
+def _check_join(res, i, w, lcol, rcol, window, stride):
+    gl, gr = res.window(i)
+    lo = w * stride
+    lk, lp = oracle.sort(*oracle.extract(lcol, lo, window))
+    rk, rp = oracle.sort(*oracle.extract(rcol, lo, window))
+    ol, orr = oracle.join(lk, lp, rk, rp)
+    assert np.array_equal(gl, ol) and np.array_equal(gr, orr), f"window {w}"
+
+
+def test_sliding_join_every_window(P):
+    s = gen.join_streams(3_000_000, key_space=1 << 20)
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    res, wl = P.sliding_join(_pinned(lcol), _pinned(rcol), 3_000_000, pair_cap=1 << 21)
+    assert wl == list(range(9))
+    for i, w in enumerate(wl):
+        _check_join(res, i, w, lcol, rcol, 1_000_000, 250_000)
+
+
+def test_sliding_join_full_size_sampled(P):
+    # 2 x 128M rows in page-locked host memory, 509 windows of 1M rows
+    s = gen.join_streams()
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    res, wl = P.sliding_join(_pinned(lcol), _pinned(rcol), lcol.size)
+    assert len(wl) == 509
+    for w in (0, 254, 508):
+        _check_join(res, w, w, lcol, rcol, 1_000_000, 250_000)
+    # pair counts near 10^12 / 2^24 per window
+    assert abs(float(res.npairs.mean()) - 1e12 / (1 << 24)) < 0.02 * 1e12 / (1 << 24)
