@@ -41,6 +41,11 @@ WORKLOAD_TEXT = ("256M KPA pairs (uint64 key, uint32 row): 70% Zipf(s=1.1) over 
 METRIC = "records/s grouped"
 UNIT = "records/s"
 CPU_SAMPLE = 4_000_000
+# DRAM bytes per row of one launch (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on the 16M-row mixed-key window).
+# Traffic grows in proportion to the rows, so a launch on n rows moves about
+# n times these.
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 32.96, "sort_scatter": 24.56}
 
 
 def _dist():
@@ -281,8 +286,12 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9
+    traffic = DRAM_BYTES_PER_ROW.get(dominant)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic * n if traffic else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 16M rows, "
+                                   "per row, times the rows of a launch" if traffic else None),
                 "algorithmic_bytes_per_launch": algo_bytes.get(dominant)}
     def stage_table(per):
         tot = {k: sum(v) for k, v in per.items()}
@@ -324,6 +333,8 @@ def run_gpu(args):
                                  "other_stages": other_stages},
             "stages": stages,
             "rows": row_suite(peak) if ws == 1 and not args.no_rows else None,
+            "serving": (serving_rows([float(x) for x in args.serve_loads.split(",")], args.serve_windows)
+                        if ws == 1 and not args.no_rows else None),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -391,6 +402,46 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
     return {"value": steps * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
             "d2h_bytes_per_step": d2h[0] // steps, "pipelined": "copy-in of step i+1 and copy-out of step i-1 "
                                                                  "overlap step i (three streams)"}
+
+
+def serving_rows(loads, n_windows, budget=40e9):
+    """The serving loop (cfg5) in real time: Poisson bundles of U[64K, 1M]
+    rows (keys Zipf(0.8) over 50M, u64 values, 5% of rows up to 100 ms
+    late), 1 s tumbling windows closed by watermark, per-key sum, count and
+    top-3 of every window copied back, memory planned for a 40 GB HBM
+    budget.  p50 / p99 window-close latency over the full windows."""
+    import torch
+
+    import gen
+    from paper_1901_01328_b300 import serve
+
+    win, late = 1_000_000_000, 100_000_000
+    seed = gen.SEED_BASE + 5
+    pool = serve.BundlePool(gen, 48, 65_536, 1_048_576, 0.8, 50_000_000, 0.05, late, seed)
+    mean = float(pool.sizes.mean())
+    out = {}
+    for load in loads:
+        slot_rows, arena_rows, out_rows = serve.plan(budget, load, win, late, 50_000_000)
+        server = serve.WindowServer(win, late, slot_rows, arena_rows, 1_048_576, K=3, keep=False, out_rows=out_rows)
+        arr = serve.poisson_schedule(gen, seed + int(load // 1e6), (n_windows + 1) * win, load, mean)
+        torch.cuda.synchronize()
+        wall = serve.run_loop(server, pool, arr, realtime=True, t0_ns=10 * win)
+        res = [r for r in server.results if r.rows]
+        full = res[1:-1] if len(res) > 2 else res  # the first window starts mid-way; the last closes at the end
+        lat = np.array([r.latency_s for r in full]) * 1e3
+        dlat = np.array([r.device_latency_s for r in full]) * 1e3
+        st = server.stats()
+        offered = int(pool.sizes[np.arange(arr.size) % len(pool.bundles)].sum())
+        out[f"{load / 1e6:g}M_rows_per_s"] = {
+            "offered_rows_per_s": load, "windows": len(full), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "p50_device_ms": float(np.percentile(dlat, 50)), "p99_device_ms": float(np.percentile(dlat, 99)),
+            "admitted_rows_per_s": st["admitted_rows"] / (arr[-1] * 1e-9) if arr.size else 0.0,
+            "shed_fraction": st["shed_rows"] / max(1, offered), "wall_s": wall,
+            "slot_rows": slot_rows, "arena_rows": arena_rows, **st}
+        del server
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ per-row measurements
@@ -598,8 +649,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sort", default="learned", choices=["learned", "radix"])
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--serve-windows", type=int, default=6, help="1 s windows per offered load (serving loop)")
+    ap.add_argument("--serve-loads", default="2.5e8,1e9", help="offered loads, rows/s")
+    ap.add_argument("--serve-only", action="store_true", help="print only the serving-loop measurement")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.serve_only:
+        loads = [float(x) for x in args.serve_loads.split(",")]
+        print(json.dumps({"metric": "window-close latency", "unit": "ms", "serving": serving_rows(loads, args.serve_windows)}),
+              flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

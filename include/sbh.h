@@ -130,6 +130,25 @@ int sbh_kpa_extract_windows(const uint64_t* key_col, const uint64_t* d_offsets, 
 /* Bits of the window field of the composite keys: the bit length of nwin. */
 int sbh_window_bits(uint64_t nwin);
 
+/* Split of an arriving bundle into window slots by timestamp (Sec. 4.2
+ * "Windowing": records belong to the window of their timestamp; Sec. 3
+ * watermarks decide when a window closes).  Row i of the bundle (device
+ * columns key_col[i], ts_rel[i], i < n) has timestamp ts_base + ts_rel[i]
+ * and window w = timestamp / win_len.  Rows of window first_win or
+ * first_win + 1 are appended, in row order, to slot w & 1: pairs
+ * (key_col[i], ptr_base + i) go to (d_keys0, d_ptrs0) or (d_keys1,
+ * d_ptrs1) at index d_fill[slot] onwards, and d_fill[slot] (device, two
+ * uint64) moves on; other rows (late, or more than one window ahead, or a
+ * negative timestamp) are dropped and added to *d_dropped.  A slot never
+ * grows past cap0 / cap1: the rows that do not fit are not written and
+ * *d_overflow is set to 1.  Several bundles in a row on one stream append
+ * after one another; no host synchronisation is needed.
+ * Scratch: 12 bytes per 4096 rows. */
+int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n, int64_t ts_base, uint64_t win_len,
+                     uint64_t first_win, uint32_t ptr_base, uint64_t* d_keys0, uint32_t* d_ptrs0, uint64_t cap0,
+                     uint64_t* d_keys1, uint32_t* d_ptrs1, uint64_t cap1, uint64_t* d_fill, uint64_t* d_dropped,
+                     uint32_t* d_overflow, void* d_scratch, size_t* scratch_bytes, void* stream);
+
 /* ---------------------------------------------------------------- A3
  * Sort (Table 2: order a KPA by its resident key).  Stable LSD radix sort,
  * 8-bit digits, one pass per digit position whose digit is not the same for
@@ -202,8 +221,11 @@ int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* d_ptrs, uin
  * ascending): d_out_vals[j*K + s], d_out_ptrs[j*K + s] for s < K, unused
  * slots padded with SBH_TOPK_PAD_VAL / SBH_TOPK_PAD_PTR; d_out_nvalid[j] =
  * min(K, count).  1 <= K <= SBH_TOPK_MAX_K.  Input sorted by key; cap and
- * *d_nkeys as in sbh_group_reduce.
- * Scratch: about 128 * (n / 4096) bytes. */
+ * *d_nkeys as in sbh_group_reduce; n < 2^32 - 1.  The keys' runs are found
+ * first; runs of at most 64 rows are reduced by one thread each, runs of up
+ * to 4096 rows by one warp each, longer ones in chunks of 16384 rows by one
+ * CTA each, no CTA waiting on another.
+ * Scratch: about 4 n bytes. */
 int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col, int val_bytes,
              int K, uint64_t* d_out_keys, uint8_t* d_out_nvalid, uint64_t* d_out_vals, uint32_t* d_out_ptrs,
              uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);

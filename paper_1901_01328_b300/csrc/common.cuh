@@ -189,17 +189,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Asynchronous element copies global -> shared (no register staging): the
-// issuing thread waits for all of its copies with cp_async_wait_all, and a
-// CTA barrier after that makes them visible to the other threads.
-__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Shared-memory atomic add done only where pred holds, without a branch
 // (returns the old value there, 0 elsewhere).
 __device__ __forceinline__ uint32_t smem_atomic_add_if(bool pred, uint32_t* addr, uint32_t v) {

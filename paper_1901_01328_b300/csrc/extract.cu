@@ -87,6 +87,146 @@ __global__ void __launch_bounds__(256) extract_windows_kernel(const uint64_t* __
     }
 }
 
+// ---------------------------------------------------------------- bundle split by timestamp
+// A bundle's rows go to the window slots of their timestamps: window w =
+// (ts_base + ts_rel[r]) / win_len; w == first_win or first_win + 1 goes to
+// slot w & 1, anything else is dropped (counted).  Stable within each slot:
+// per tile counts -> one-CTA scan that also moves the slots' fill counters
+// -> emit at the tile's offset plus the row's rank among its tile's rows of
+// the same slot.
+constexpr int kSplitThreads = 256;
+constexpr int kSplitIpt = 16;
+constexpr int kSplitTile = kSplitThreads * kSplitIpt;
+
+__device__ __forceinline__ uint32_t split_tag(int64_t ts, uint64_t win_len, uint64_t first_win) {
+    if (ts < 0) return 2u;
+    const uint64_t w = static_cast<uint64_t>(ts) / win_len;
+    if (w == first_win || w == first_win + 1) return static_cast<uint32_t>(w & 1u);
+    return 2u;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) split_count_kernel(const int64_t* __restrict__ ts_rel, uint32_t n,
+                                                                    int64_t ts_base, uint64_t win_len,
+                                                                    uint64_t first_win, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t c[3];
+    if (threadIdx.x < 3) c[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kSplitTile;
+    uint32_t mine[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < kSplitIpt; ++j) {
+        const uint32_t r = base + j * kSplitThreads + threadIdx.x;
+        if (r < n) ++mine[split_tag(ts_base + ts_rel[r], win_len, first_win)];
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const uint32_t x = __reduce_add_sync(0xffffffffu, mine[t]);
+        if (lane_id() == 0 && x) atomicAdd(&c[t], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) cnt[blockIdx.x * 3 + threadIdx.x] = c[threadIdx.x];
+}
+
+// One CTA: tile offsets per slot (starting at the slot's fill), new fills,
+// dropped rows, and the overflow flag when a slot would pass its capacity.
+__global__ void __launch_bounds__(1024) split_scan_kernel(uint32_t* __restrict__ cnt, uint32_t ntiles,
+                                                          uint64_t* __restrict__ fill, uint64_t cap0, uint64_t cap1,
+                                                          uint64_t* __restrict__ dropped,
+                                                          uint32_t* __restrict__ overflow) {
+    __shared__ uint64_t wt[3][32];
+    __shared__ uint64_t carry[3];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (threadIdx.x < 3) carry[threadIdx.x] = threadIdx.x < 2 ? fill[threadIdx.x] : 0ull;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        uint64_t v[3], x[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            v[t] = i < ntiles ? cnt[i * 3 + t] : 0u;
+            x[t] = v[t];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, x[t], o);
+                if (lane >= (uint32_t)o) x[t] += y;
+            }
+            if (lane == 31) wt[t][warp] = x[t];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            uint64_t before = carry[t];
+            for (uint32_t w = 0; w < warp; ++w) before += wt[t][w];
+            if (i < ntiles) cnt[i * 3 + t] = static_cast<uint32_t>(before + x[t] - v[t]);  // offset into the slot
+            x[t] += before;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1)
+            for (int t = 0; t < 3; ++t) carry[t] = x[t];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const uint64_t f0 = carry[0], f1 = carry[1];
+        if (f0 > cap0 || f1 > cap1) *overflow = 1u;
+        fill[0] = f0 < cap0 ? f0 : cap0;
+        fill[1] = f1 < cap1 ? f1 : cap1;
+        *dropped += carry[2];
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads) split_emit_kernel(const uint64_t* __restrict__ col,
+                                                                   const int64_t* __restrict__ ts_rel, uint32_t n,
+                                                                   int64_t ts_base, uint64_t win_len,
+                                                                   uint64_t first_win, uint32_t ptr_base,
+                                                                   const uint32_t* __restrict__ off,
+                                                                   uint64_t* __restrict__ k0, uint32_t* __restrict__ p0,
+                                                                   uint64_t cap0, uint64_t* __restrict__ k1,
+                                                                   uint32_t* __restrict__ p1, uint64_t cap1) {
+    __shared__ uint32_t wc[2][kSplitThreads / 32];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t first = blockIdx.x * kSplitTile + warp * 32 * kSplitIpt;  // warp-striped rows
+    uint32_t tag[kSplitIpt];
+    uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int j = 0; j < kSplitIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        tag[j] = r < n ? split_tag(ts_base + ts_rel[r], win_len, first_win) : 3u;
+        c0 += __popc(__ballot_sync(0xffffffffu, tag[j] == 0));
+        c1 += __popc(__ballot_sync(0xffffffffu, tag[j] == 1));
+    }
+    if (lane == 0) {
+        wc[0][warp] = c0;
+        wc[1][warp] = c1;
+    }
+    __syncthreads();
+    uint64_t o0 = off[blockIdx.x * 3], o1 = off[blockIdx.x * 3 + 1];
+    for (uint32_t w = 0; w < warp; ++w) {
+        o0 += wc[0][w];
+        o1 += wc[1][w];
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kSplitIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        const uint32_t m0 = __ballot_sync(0xffffffffu, tag[j] == 0), m1 = __ballot_sync(0xffffffffu, tag[j] == 1);
+        if (tag[j] == 0) {
+            const uint64_t g = o0 + __popc(m0 & lt);
+            if (g < cap0) {
+                k0[g] = col[r];
+                p0[g] = ptr_base + r;
+            }
+        } else if (tag[j] == 1) {
+            const uint64_t g = o1 + __popc(m1 & lt);
+            if (g < cap1) {
+                k1[g] = col[r];
+                p1[g] = ptr_base + r;
+            }
+        }
+        o0 += __popc(m0);
+        o1 += __popc(m1);
+    }
+}
+
 // ---------------------------------------------------------------- windows
 template <typename T>
 __device__ __forceinline__ uint64_t lower_bound_ts(const T* ts, uint64_t n, uint64_t v) {
@@ -195,6 +335,41 @@ int sbh_kpa_extract_windows(const uint64_t* key_col, const uint64_t* d_offsets, 
     SBH_TIMED("extract_windows", s,
               extract_windows_kernel<<<(unsigned)blocks, 256, 0, s>>>(col, d_offsets, (uint32_t)nwin, (uint32_t)row_begin,
                                                                       (uint32_t)n, wshift, d_keys, d_ptrs, d_key_or));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
+int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n, int64_t ts_base, uint64_t win_len,
+                     uint64_t first_win, uint32_t ptr_base, uint64_t* d_keys0, uint32_t* d_ptrs0, uint64_t cap0,
+                     uint64_t* d_keys1, uint32_t* d_ptrs1, uint64_t cap1, uint64_t* d_fill, uint64_t* d_dropped,
+                     uint32_t* d_overflow, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    const uint64_t ntiles = (n + kSplitTile - 1) / kSplitTile;
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, (ntiles ? ntiles : 1) * 3 * sizeof(uint32_t), &done);
+    if (rc || done) return rc;
+    if (n == 0) return SBH_OK;
+    if (win_len == 0) { set_error("win_len must be > 0"); return SBH_EINVAL; }
+    if ((uint64_t)ptr_base + n > 0xFFFFFFFFull) { set_error("ptr_base + n must be < 2^32"); return SBH_EINVAL; }
+    if (!key_col || !ts_rel || !d_fill || !d_dropped || !d_overflow || (cap0 && (!d_keys0 || !d_ptrs0)) ||
+        (cap1 && (!d_keys1 || !d_ptrs1))) {
+        set_error("null pointer");
+        return SBH_EINVAL;
+    }
+    cudaStream_t s = as_stream(stream);
+    uint32_t* cnt = static_cast<uint32_t*>(d_scratch);
+    const uint32_t n32 = static_cast<uint32_t>(n);
+    SBH_TIMED("split_count", s, split_count_kernel<<<(unsigned)ntiles, kSplitThreads, 0, s>>>(ts_rel, n32, ts_base, win_len,
+                                                                                          first_win, cnt));
+    SBH_LAUNCHED();
+    SBH_TIMED("split_scan", s, split_scan_kernel<<<1, 1024, 0, s>>>(cnt, (uint32_t)ntiles, d_fill, cap0, cap1, d_dropped,
+                                                                    d_overflow));
+    SBH_LAUNCHED();
+    SBH_TIMED("split_emit", s,
+              split_emit_kernel<<<(unsigned)ntiles, kSplitThreads, 0, s>>>(key_col, ts_rel, n32, ts_base, win_len,
+                                                                           first_win, ptr_base, cnt, d_keys0, d_ptrs0,
+                                                                           cap0, d_keys1, d_ptrs1, cap1));
     SBH_LAUNCHED();
     return SBH_OK;
 }

@@ -145,40 +145,57 @@ tile_agg_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
     }
 }
 
-// Exclusive scan of the tile aggregates (in place), by one CTA.
+// Exclusive scan of the tile aggregates (in place), by one CTA: each thread
+// combines a contiguous range of tiles (eight loads in flight at a time), the
+// CTA scans the range totals, and each thread walks its range again writing
+// the prefixes.
+__device__ __forceinline__ Agg shfl_up_agg(const Agg& a, int o) {
+    Agg y;
+    y.heads = shfl_up_u64(a.heads, o);
+    y.last_row = shfl_up_u64(a.last_row, o);
+    y.sum = shfl_up_u64(a.sum, o);
+    y.last_p = shfl_up_u64(a.last_p, o);
+    return y;
+}
+
 __global__ void __launch_bounds__(1024) tile_scan_kernel(Agg* __restrict__ aggs, uint32_t ntiles) {
     __shared__ Agg warp_tot[32];
-    __shared__ Agg carry;
+    constexpr int kBatch = 8;
     const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
-    if (threadIdx.x == 0) carry = agg_identity();
-    __syncthreads();
-    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
-        const uint32_t i = c0 + threadIdx.x;
-        const Agg mine = i < ntiles ? aggs[i] : agg_identity();
-        Agg inc = mine;
+    const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = min(ntiles, threadIdx.x * per), b1 = min(ntiles, b0 + per);
+    Agg local = agg_identity();
+    for (uint32_t i = b0; i < b1; i += kBatch) {
+        Agg a[kBatch];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Agg y;
-            y.heads = shfl_up_u64(inc.heads, o);
-            y.last_row = shfl_up_u64(inc.last_row, o);
-            y.sum = shfl_up_u64(inc.sum, o);
-            y.last_p = shfl_up_u64(inc.last_p, o);
-            if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
+        for (int u = 0; u < kBatch; ++u) a[u] = i + u < b1 ? aggs[i + u] : agg_identity();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) local = agg_combine(local, a[u]);
+    }
+    Agg inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Agg y = shfl_up_agg(inc, o);
+        if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    Agg run = agg_identity();
+    for (uint32_t w = 0; w < warp; ++w) run = agg_combine(run, warp_tot[w]);
+    Agg excl = shfl_up_agg(inc, 1);
+    if (lane == 0) excl = agg_identity();
+    run = agg_combine(run, excl);
+    for (uint32_t i = b0; i < b1; i += kBatch) {
+        Agg a[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) a[u] = i + u < b1 ? aggs[i + u] : agg_identity();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (i + u < b1) {
+                aggs[i + u] = run;
+                run = agg_combine(run, a[u]);
+            }
         }
-        if (lane == 31) warp_tot[warp] = inc;
-        __syncthreads();
-        Agg before = carry;
-        for (uint32_t w = 0; w < warp; ++w) before = agg_combine(before, warp_tot[w]);
-        Agg excl;
-        excl.heads = shfl_up_u64(inc.heads, 1);
-        excl.last_row = shfl_up_u64(inc.last_row, 1);
-        excl.sum = shfl_up_u64(inc.sum, 1);
-        excl.last_p = shfl_up_u64(inc.last_p, 1);
-        if (lane == 0) excl = agg_identity();
-        if (i < ntiles) aggs[i] = agg_combine(before, excl);
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = agg_combine(before, inc);
-        __syncthreads();
     }
 }
 

@@ -673,6 +673,7 @@ struct BucketSmem {
     uint32_t bin_tmp[kBWarps];
     uint32_t next[2];  // the bucket taken after the current one (alternating slots)
 };
+static_assert(sizeof(BucketSmem) <= 232448, "bucket sort shared memory");
 
 struct BucketStats {
     unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
@@ -683,7 +684,10 @@ struct BucketStats {
 // shared memory: a counting placement by the top 12 bits of key - kmin and
 // insertion sorts inside the sub-buckets, or (a sub-bucket over 32 rows)
 // stable 8-bit radix passes on key - kmin.  Rows of one key stay in ptr
-// order because the scatter that formed the bucket was stable.
+// order because the scatter that formed the bucket was stable.  (Bringing
+// the next bucket in by asynchronous copies during the current sort, and
+// sorting sub-buckets of 9 to 32 rows by a warp's bitonic network, were both
+// measured and neither was faster.)
 __global__ void __launch_bounds__(kBThreads, 1)
 bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
                    const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
@@ -889,17 +893,17 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                     uint32_t stt = x - lsum;
 #pragma unroll 1
                     for (int q = 0; q < 4; ++q) {
-                        uint32_t tot = 0, pre = 0;
+                        uint32_t tot = 0, gpre = 0;
 #pragma unroll
                         for (int gg = 0; gg < kBGroups; ++gg) {
                             const uint32_t v = sm.gsum[gg][4 * lane + q];
                             tot += v;
-                            pre += (gg < (int)warp) ? v : 0u;
+                            gpre += (gg < (int)warp) ? v : 0u;
                         }
                         const uint32_t c0 = tot & 0xFFFFu;
                         const uint32_t d0 = 8 * lane + 2 * q;
-                        sm.gstart[warp][d0] = static_cast<uint16_t>(stt + (pre & 0xFFFFu));
-                        sm.gstart[warp][d0 + 1] = static_cast<uint16_t>(stt + c0 + (pre >> 16));
+                        sm.gstart[warp][d0] = static_cast<uint16_t>(stt + (gpre & 0xFFFFu));
+                        sm.gstart[warp][d0 + 1] = static_cast<uint16_t>(stt + c0 + (gpre >> 16));
                         stt += c0 + (tot >> 16);
                     }
                 }
@@ -1004,10 +1008,7 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 constexpr int kCarryTile = 3584;
 
 // Bucket id of every row (kept as 16 bits) and the histograms of its two
-// digits.  With 16-byte aligned keys each lane takes two consecutive rows per
-// step, four steps at a time: every load and store instruction of a warp
-// covers one contiguous span, and the eight cell-table lookups of a lane are
-// independent.
+// digits.
 __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
                                                           BucketValue fn, uint16_t* __restrict__ ids,
                                                           uint32_t* __restrict__ ghist) {
@@ -1022,33 +1023,8 @@ __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __rest
         if (d1 == last1) ++run1;
         else { if (run1) atomicAdd(&h[kRadix + last1], run1); last1 = d1; run1 = 1; }
     };
-    uint32_t done = 0;
-    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
-        // a warp step covers 256 rows: lane l takes row pairs 32 j + l, j < 4
-        const uint32_t nsteps = n / 256;
-        const uint32_t lane = lane_id();
-        const uint32_t warps = gridDim.x * (blockDim.x / 32);
-        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
-        uint32_t* ids2 = reinterpret_cast<uint32_t*>(ids);
-        for (uint32_t st = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; st < nsteps; st += warps) {
-            ulonglong2 k[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) k[j] = __ldcs(q + st * 128 + j * 32 + lane);
-            uint32_t id[8];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                id[2 * j] = static_cast<uint32_t>(fn(k[j].x));
-                id[2 * j + 1] = static_cast<uint32_t>(fn(k[j].y));
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) __stcs(ids2 + st * 128 + j * 32 + lane, id[2 * j] | (id[2 * j + 1] << 16));
-#pragma unroll
-            for (int j = 0; j < 8; ++j) add(id[j]);
-        }
-        done = nsteps * 256;
-    }
     const uint32_t nthreads = gridDim.x * blockDim.x;
-    for (uint32_t i = done + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
         const uint32_t id = static_cast<uint32_t>(fn(ld_stream(keys + i)));
         ids[i] = static_cast<uint16_t>(id);
         add(id);

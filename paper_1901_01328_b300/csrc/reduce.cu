@@ -1,14 +1,26 @@
 // A7 top-K per key, on a KPA sorted by key.
 //
-// One persistent kernel per call.  Each tile of 4096 rows is loaded with
-// coalesced reads, transposed through shared memory so each thread owns 16
-// consecutive rows, and reduced as a segmented scan whose element is
-//     (number of segment heads, aggregate of the open segment).
-// Combining (h1, a1) then (h2, a2) gives (h1 + h2, h2 ? a2 : a1 + a2).  Tiles
-// chain their scan results with a decoupled look-back (bounded wait), so a
-// key's rows may span any number of tiles.  A segment is written out by the
-// thread that meets the next head (or holds the last row), at output index =
-// number of heads before it.
+// A key's rows are one contiguous run (a segment), so the work splits by
+// segment once the segments are known:
+//   heads_count   per tile of 4096 rows: number of segment heads;
+//   heads_scan    one CTA: exclusive scan of the tile counts, and the
+//                 number of segments;
+//   heads_emit    per tile: each head writes its key to the output and its
+//                 row to seg_start, at index = number of heads before it;
+//   small         grid-stride over segments: a segment of at most 64 rows is
+//                 reduced by one thread (its pointers read in order, values
+//                 gathered), a longer one is listed as medium (up to 4096
+//                 rows) or long;
+//   medium        one warp per listed medium segment, then a warp merge;
+//   long_scan     one CTA: every listed segment is cut into chunks of 16384
+//                 rows; exclusive scan of the chunk counts;
+//   long_chunks   grid-stride over chunks: a CTA reduces a chunk (each
+//                 thread a strided share, then warp and CTA merges); a
+//                 one-chunk segment writes its result, otherwise the chunk's
+//                 list goes to scratch and the CTA that finishes last (an
+//                 atomic count per segment, no waiting) merges the segment's
+//                 lists and writes the result.
+// No kernel waits on another CTA.
 #include "common.cuh"
 
 namespace sbh {
@@ -18,6 +30,9 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kIpt = 16;
 constexpr int kTile = kThreads * kIpt;
+constexpr uint32_t kLaneMax = 64;     // longest segment reduced by one thread
+constexpr uint32_t kWarpMax = 4096;   // longest segment reduced by one warp
+constexpr uint32_t kChunk = 16384;    // rows of a long segment per CTA
 
 // ------------------------------------------------------------ aggregates
 // The best K (value, ptr) pairs seen, ordered by value descending, then ptr
@@ -40,7 +55,6 @@ struct TopK {
     // insert one pair, keeping at most k
     __device__ __forceinline__ void add_row(uint64_t val, uint32_t ptr, int k) {
         if (n == (uint32_t)k && !better(val, ptr, v[k - 1], p[k - 1])) return;
-        // shift down the entries that are worse than (val, ptr)
         uint32_t pos = n < (uint32_t)k ? n : (uint32_t)k - 1;
 #pragma unroll
         for (int s = KMAX - 1; s > 0; --s) {
@@ -56,327 +70,422 @@ struct TopK {
     }
     // merge another list into this one, keeping at most k
     __device__ __forceinline__ void absorb(const TopK& b, int k) {
-        TopK r;
-        r.n = 0;
-        uint32_t i = 0, j = 0;
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            r.v[s] = 0;
-            r.p[s] = 0xFFFFFFFFu;
-            if (s < k) {
-                const bool ha = i < n, hb = j < b.n;
-                if (ha || hb) {
-                    // read by dynamic index from the small arrays
-                    uint64_t av = 0, bv = 0;
-                    uint32_t ap = 0, bp = 0;
-#pragma unroll
-                    for (int q = 0; q < KMAX; ++q) {
-                        if ((uint32_t)q == i) { av = v[q]; ap = p[q]; }
-                        if ((uint32_t)q == j) { bv = b.v[q]; bp = b.p[q]; }
-                    }
-                    const bool take_a = ha && (!hb || better(av, ap, bv, bp));
-                    r.v[s] = take_a ? av : bv;
-                    r.p[s] = take_a ? ap : bp;
-                    i += take_a;
-                    j += !take_a;
-                    r.n = s + 1;
-                }
-            }
-        }
-        *this = r;
+        for (int s = 0; s < KMAX; ++s)
+            if (s < (int)b.n) add_row(b.v[s], b.p[s], k);
     }
-    __device__ __forceinline__ void shfl_up(const TopK& src, int o) {
-        n = __shfl_up_sync(0xffffffffu, src.n, o);
+    __device__ __forceinline__ void shfl_xor(const TopK& src, int o) {
+        n = __shfl_xor_sync(0xffffffffu, src.n, o);
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) {
-            v[s] = __shfl_up_sync(0xffffffffu, src.v[s], o);
-            p[s] = __shfl_up_sync(0xffffffffu, src.p[s], o);
+            v[s] = __shfl_xor_sync(0xffffffffu, src.v[s], o);
+            p[s] = __shfl_xor_sync(0xffffffffu, src.p[s], o);
         }
     }
 };
 
-// segmented-scan element
-template <typename Agg>
-struct Seg {
-    uint32_t heads;
-    Agg open;
-};
-
-template <typename Agg>
-__device__ __forceinline__ Seg<Agg> seg_combine(const Seg<Agg>& a, const Seg<Agg>& b, int k) {
-    Seg<Agg> r;
-    r.heads = a.heads + b.heads;
-    if (b.heads) {
-        r.open = b.open;
-    } else {
-        r.open = a.open;
-        r.open.absorb(b.open, k);
-    }
-    return r;
-}
-
-// look-back record of one tile: a flag word plus two immutable payloads
-// (the tile's own aggregate, then its inclusive prefix).
-template <typename Agg>
-struct TileRec {
-    Seg<Agg> agg;
-    Seg<Agg> prefix;
-};
-
-constexpr uint32_t kRecAgg = 1, kRecPrefix = 2;
-
-template <typename T>
-__device__ __forceinline__ void store_volatile(T* dst, const T& v) {
-    static_assert(sizeof(T) % 4 == 0, "word-sized payload");
-    volatile uint32_t* d = reinterpret_cast<volatile uint32_t*>(dst);
-    const uint32_t* s = reinterpret_cast<const uint32_t*>(&v);
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) d[i] = s[i];
-}
-template <typename T>
-__device__ __forceinline__ T load_volatile(const T* src) {
-    T v;
-    const volatile uint32_t* s = reinterpret_cast<const volatile uint32_t*>(src);
-    uint32_t* d = reinterpret_cast<uint32_t*>(&v);
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) d[i] = s[i];
-    return v;
-}
-
-// ------------------------------------------------------------ output sinks
 template <int KMAX>
-struct TopKSink {
-    uint64_t* keys;
-    uint8_t* nvalid;
-    uint64_t* vals;
-    uint32_t* ptrs;
-    uint64_t cap;
-    int k;
-    __device__ __forceinline__ void emit(uint64_t idx, uint64_t key, const TopK<KMAX>& a) const {
-        if (idx >= cap) return;
-        keys[idx] = key;
-        nvalid[idx] = static_cast<uint8_t>(a.n);
+__device__ __forceinline__ void emit(uint64_t g, const TopK<KMAX>& a, int k, uint64_t cap, uint8_t* nvalid,
+                                     uint64_t* vals, uint32_t* ptrs) {
+    if (g >= cap) return;
+    nvalid[g] = static_cast<uint8_t>(a.n);
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            if (s < k) {
-                vals[idx * k + s] = s < (int)a.n ? a.v[s] : 0ull;
-                ptrs[idx * k + s] = s < (int)a.n ? a.p[s] : 0xFFFFFFFFu;
-            }
+    for (int s = 0; s < KMAX; ++s) {
+        if (s < k) {
+            vals[g * k + s] = s < (int)a.n ? a.v[s] : SBH_TOPK_PAD_VAL;
+            ptrs[g * k + s] = s < (int)a.n ? a.p[s] : SBH_TOPK_PAD_PTR;
         }
     }
-};
+}
 
-template <typename Agg>
-struct ReduceSmem {
-    union {
-        uint64_t keys[kTile];
-        uint32_t ptrs[kTile];
-    } stage;
-    Seg<Agg> warp_tot[kWarps];
-    Seg<Agg> tile_excl;
-    uint64_t prev_key_of_tile;
-    uint32_t tile;
-};
+template <int kVals>
+__device__ __forceinline__ uint64_t gather(const void* col, uint32_t p) {
+    if (kVals == 8) return __ldg(static_cast<const unsigned long long*>(col) + p);
+    return __ldg(static_cast<const unsigned int*>(col) + p);
+}
 
-// kVals: 0 = count only (no ptrs or values read), 4 or 8 = value bytes.
-template <typename Agg, typename Sink, int kVals>
-__global__ void __launch_bounds__(kThreads)
-segreduce_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs, uint64_t n,
-                 const void* __restrict__ val_col, Sink sink, int k, uint64_t* __restrict__ nkeys_out,
-                 uint32_t* __restrict__ flags, TileRec<Agg>* __restrict__ recs, uint32_t* __restrict__ tile_counter,
-                 uint32_t spin_limit, uint32_t* __restrict__ status) {
-    __shared__ ReduceSmem<Agg> sm;
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
+// ------------------------------------------------------------ segment heads
+// Head bits of this thread's rows (warp-striped: row = base + warp's first
+// row + j * 32 + lane).
+__device__ __forceinline__ uint32_t head_bits(const uint64_t* __restrict__ keys, uint32_t n, uint32_t first,
+                                              uint32_t lane, uint64_t (&k)[kIpt]) {
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        k[j] = r < n ? ld_stream(keys + r) : 0ull;
+    }
+    uint64_t prev = first > 0 ? keys[first - 1] : 0ull;
+    uint32_t hmask = 0;
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t r = first + j * 32 + lane;
+        uint64_t pk = __shfl_up_sync(0xffffffffu, k[j], 1);
+        if (lane == 0) pk = prev;
+        if (r < n && (r == 0 || pk != k[j])) hmask |= 1u << j;
+        prev = __shfl_sync(0xffffffffu, k[j], 31);
+    }
+    return hmask;
+}
 
-    for (;;) {
-        if (tid == 0) sm.tile = atomicAdd(tile_counter, 1u);
-        __syncthreads();
-        const uint64_t tile = sm.tile;
-        if (tile >= ntiles) break;
-        const uint64_t base = tile * kTile;
-        const uint32_t valid = (uint32_t)min_u64(n - base, kTile);
-        if (tid == 0) sm.prev_key_of_tile = tile ? keys[base - 1] : 0ull;
+__global__ void __launch_bounds__(kThreads) heads_count_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                               uint32_t* __restrict__ tile_cnt) {
+    __shared__ uint32_t wc[kWarps];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t first = blockIdx.x * kTile + warp * 32 * kIpt;
+    uint64_t k[kIpt];
+    const uint32_t hmask = head_bits(keys, n, first, lane, k);
+    const uint32_t c = __reduce_add_sync(0xffffffffu, __popc(hmask));
+    if (lane == 0) wc[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kWarps; ++w) t += wc[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
 
-        // ---- keys: coalesced load, then each thread reads 16 consecutive rows
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            const uint32_t s = tid + j * kThreads;
-            if (s < valid) sm.stage.keys[s] = ld_stream(keys + base + s);
-        }
-        __syncthreads();
-        const uint32_t first = tid * kIpt;
-        uint64_t kk[kIpt];
-#pragma unroll
-        for (int j = 0; j < kIpt; ++j) kk[j] = (first + j < valid) ? sm.stage.keys[first + j] : 0ull;
-        uint64_t prev = first == 0 ? sm.prev_key_of_tile : (first - 1 < valid ? sm.stage.keys[first - 1] : 0ull);
-        __syncthreads();
-
-        uint32_t pp[kIpt];
-        uint64_t vv[kIpt];
-        if (kVals) {
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                const uint32_t s = tid + j * kThreads;
-                if (s < valid) sm.stage.ptrs[s] = ld_stream(ptrs + base + s);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) pp[j] = (first + j < valid) ? sm.stage.ptrs[first + j] : 0u;
-            // gather the nonresident value column through the pointers
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                if (first + j < valid) {
-                    if (kVals == 8) vv[j] = __ldg(static_cast<const unsigned long long*>(val_col) + pp[j]);
-                    else vv[j] = __ldg(static_cast<const unsigned int*>(val_col) + pp[j]);
-                } else {
-                    vv[j] = 0;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) { pp[j] = 0; vv[j] = 0; }
-        }
-
-        // ---- thread summary
-        uint32_t headmask = 0;
-        Seg<Agg> x;
-        x.heads = 0;
-        x.open = Agg::identity();
-        {
-            uint64_t pk = prev;
-#pragma unroll
-            for (int j = 0; j < kIpt; ++j) {
-                if (first + j < valid) {
-                    const bool h = (base + first + j == 0) || kk[j] != pk;
-                    if (h) {
-                        headmask |= 1u << j;
-                        x.heads += 1;
-                        x.open = Agg::identity();
-                    }
-                    x.open.add_row(vv[j], pp[j], k);
-                    pk = kk[j];
-                }
-            }
-        }
-
-        // ---- warp inclusive scan of the summaries
-        Seg<Agg> inc = x;
+// Exclusive scan of the tile head counts in place (one CTA); the number of
+// segments goes to *nseg_out (and to nseg32 for the later kernels).
+__global__ void __launch_bounds__(1024) heads_scan_kernel(uint32_t* __restrict__ cnt, uint32_t ntiles,
+                                                          uint64_t* __restrict__ nseg_out,
+                                                          uint32_t* __restrict__ nseg32, uint32_t* __restrict__ seg_start,
+                                                          uint32_t n) {
+    __shared__ uint32_t wt[32];
+    __shared__ uint32_t carry;
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const uint32_t v = i < ntiles ? cnt[i] : 0u;
+        uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            Seg<Agg> y;
-            y.heads = __shfl_up_sync(0xffffffffu, inc.heads, o);
-            y.open.shfl_up(inc.open, o);
-            if (lane >= (uint32_t)o) inc = seg_combine(y, inc, k);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
         }
-        if (lane == 31) sm.warp_tot[warp] = inc;
-        // exclusive within the warp
-        Seg<Agg> wexcl;
-        wexcl.heads = __shfl_up_sync(0xffffffffu, inc.heads, 1);
-        wexcl.open.shfl_up(inc.open, 1);
-        if (lane == 0) { wexcl.heads = 0; wexcl.open = Agg::identity(); }
+        if (lane == 31) wt[warp] = x;
         __syncthreads();
-
-        // ---- tile aggregate, publish, look back (thread 0)
-        if (tid == 0) {
-            Seg<Agg> t = sm.warp_tot[0];
-            for (int w = 1; w < kWarps; ++w) t = seg_combine(t, sm.warp_tot[w], k);
-            Seg<Agg> excl;
-            excl.heads = 0;
-            excl.open = Agg::identity();
-            if (tile == 0) {
-                store_volatile(&recs[0].prefix, t);
-                __threadfence();
-                st_release(flags, kRecPrefix);
-            } else {
-                store_volatile(&recs[tile].agg, t);
-                __threadfence();
-                st_release(flags + tile, kRecAgg);
-                // walk back, accumulating excl = rec[j] (+) excl
-                uint64_t j = tile - 1;
-                uint32_t polls = 0;
-                bool have = false;
-                for (;;) {
-                    const uint32_t f = ld_acquire(flags + j);
-                    if (f == 0) {
-                        if (wait_expired(polls, spin_limit, status)) break;
-                        continue;
-                    }
-                    const Seg<Agg> r = load_volatile(f == kRecPrefix ? &recs[j].prefix : &recs[j].agg);
-                    excl = have ? seg_combine(r, excl, k) : r;
-                    have = true;
-                    if (f == kRecPrefix || j == 0) break;
-                    --j;
-                }
-                const Seg<Agg> incl = seg_combine(excl, t, k);
-                store_volatile(&recs[tile].prefix, incl);
-                __threadfence();
-                st_release(flags + tile, kRecPrefix);
-            }
-            sm.tile_excl = excl;
-        }
+        uint32_t before = carry;
+        for (uint32_t w = 0; w < warp; ++w) before += wt[w];
+        if (i < ntiles) cnt[i] = before + x - v;
         __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *nseg_out = carry;
+        *nseg32 = carry;
+        seg_start[carry] = n;  // the end of the last segment
+    }
+}
 
-        // ---- this thread's exclusive prefix, then walk its rows and emit
-        Seg<Agg> pre = sm.tile_excl;
-        for (uint32_t w = 0; w < warp; ++w) pre = seg_combine(pre, sm.warp_tot[w], k);
-        pre = seg_combine(pre, wexcl, k);
-
-        Agg cur = pre.open;
-        int64_t seg = (int64_t)pre.heads - 1;
-        uint64_t pk = prev;
+__global__ void __launch_bounds__(kThreads) heads_emit_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                              const uint32_t* __restrict__ tile_base,
+                                                              uint64_t* __restrict__ out_keys, uint64_t cap,
+                                                              uint32_t* __restrict__ seg_start) {
+    __shared__ uint32_t wc[kWarps];
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t first = blockIdx.x * kTile + warp * 32 * kIpt;
+    uint64_t k[kIpt];
+    const uint32_t hmask = head_bits(keys, n, first, lane, k);
+    const uint32_t c = __reduce_add_sync(0xffffffffu, __popc(hmask));
+    if (lane == 0) wc[warp] = c;
+    __syncthreads();
+    uint32_t g = tile_base[blockIdx.x];
+    for (uint32_t w = 0; w < warp; ++w) g += wc[w];
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
-        for (int j = 0; j < kIpt; ++j) {
-            if (first + j < valid) {
-                if (headmask & (1u << j)) {
-                    if (seg >= 0) sink.emit((uint64_t)seg, pk, cur);
-                    ++seg;
-                    cur = Agg::identity();
-                }
-                cur.add_row(vv[j], pp[j], k);
-                pk = kk[j];
-                if (base + first + j == n - 1) {
-                    sink.emit((uint64_t)seg, pk, cur);
-                    *nkeys_out = (uint64_t)(seg + 1);
-                }
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (hmask >> j) & 1u);
+        if ((m >> lane) & 1u) {
+            const uint32_t gi = g + __popc(m & lt);
+            seg_start[gi] = first + j * 32 + lane;
+            if (gi < cap) out_keys[gi] = k[j];
+        }
+        g += __popc(m);
+    }
+}
+
+// ------------------------------------------------------------ short segments
+template <int KMAX, int kVals>
+__global__ void __launch_bounds__(kThreads) small_kernel(const uint32_t* __restrict__ ptrs,
+                                                         const void* __restrict__ val_col,
+                                                         const uint32_t* __restrict__ seg_start,
+                                                         const uint32_t* __restrict__ nseg_p, int k, uint64_t cap,
+                                                         uint8_t* __restrict__ nvalid, uint64_t* __restrict__ vals,
+                                                         uint32_t* __restrict__ optrs,
+                                                         uint32_t* __restrict__ long_list,
+                                                         uint32_t* __restrict__ nlong,
+                                                         uint32_t* __restrict__ mid_list,
+                                                         uint32_t* __restrict__ nmid) {
+    const uint32_t nseg = *nseg_p;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += stride) {
+        const uint32_t s = seg_start[g], e = seg_start[g + 1];
+        if (e - s > kWarpMax) {
+            long_list[atomicAdd(nlong, 1u)] = g;
+            continue;
+        }
+        if (e - s > kLaneMax) {
+            mid_list[atomicAdd(nmid, 1u)] = g;
+            continue;
+        }
+        // four rows at a time: loads first, so that they are in flight together
+        TopK<KMAX> t = TopK<KMAX>::identity();
+        for (uint32_t rb = s; rb < e; rb += 4) {
+            uint32_t p[4];
+            uint64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] = rb + u < e ? __ldg(ptrs + rb + u) : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = rb + u < e ? gather<kVals>(val_col, p[u]) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (rb + u < e) t.add_row(v[u], p[u], k);
+        }
+        emit(g, t, k, cap, nvalid, vals, optrs);
+    }
+}
+
+// ------------------------------------------------------------ medium segments
+template <int KMAX, int kVals>
+__global__ void __launch_bounds__(kThreads) medium_kernel(const uint32_t* __restrict__ ptrs,
+                                                          const void* __restrict__ val_col,
+                                                          const uint32_t* __restrict__ seg_start,
+                                                          const uint32_t* __restrict__ mid_list,
+                                                          const uint32_t* __restrict__ nmid_p, int k, uint64_t cap,
+                                                          uint8_t* __restrict__ nvalid, uint64_t* __restrict__ vals,
+                                                          uint32_t* __restrict__ optrs) {
+    const uint32_t nmid = *nmid_p;
+    const uint32_t lane = lane_id();
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; i < nmid; i += warps) {
+        const uint32_t g = mid_list[i];
+        const uint32_t s = seg_start[g], e = seg_start[g + 1];
+        TopK<KMAX> t = TopK<KMAX>::identity();
+        for (uint32_t rb = s + lane; rb < e; rb += 4 * 32) {
+            uint32_t p[4];
+            uint64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] = rb + u * 32 < e ? __ldg(ptrs + rb + u * 32) : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = rb + u * 32 < e ? gather<kVals>(val_col, p[u]) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (rb + u * 32 < e) t.add_row(v[u], p[u], k);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            TopK<KMAX> y;
+            y.shfl_xor(t, o);
+            t.absorb(y, k);
+        }
+        if (lane == 0) emit(g, t, k, cap, nvalid, vals, optrs);
+    }
+}
+
+// ------------------------------------------------------------ long segments
+// Chunk counts of the listed segments, scanned (one CTA); chunk_off[i] is the
+// first chunk of list entry i, chunk_off[nlong] the total.
+__global__ void __launch_bounds__(1024) long_scan_kernel(const uint32_t* __restrict__ long_list,
+                                                         const uint32_t* __restrict__ nlong_p,
+                                                         const uint32_t* __restrict__ seg_start,
+                                                         uint32_t* __restrict__ chunk_off) {
+    __shared__ uint32_t wt[32];
+    __shared__ uint32_t carry;
+    const uint32_t nlong = *nlong_p;
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nlong; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        uint32_t v = 0;
+        if (i < nlong) {
+            const uint32_t g = long_list[i];
+            v = (seg_start[g + 1] - seg_start[g] + kChunk - 1) / kChunk;
+        }
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) wt[warp] = x;
+        __syncthreads();
+        uint32_t before = carry;
+        for (uint32_t w = 0; w < warp; ++w) before += wt[w];
+        if (i < nlong) chunk_off[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk_off[nlong] = carry;
+}
+
+// Merge of the CTA's per-thread lists into thread 0's.
+template <int KMAX>
+__device__ __forceinline__ TopK<KMAX> block_merge(TopK<KMAX> t, int k, TopK<KMAX>* wsm) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        TopK<KMAX> y;
+        y.shfl_xor(t, o);
+        t.absorb(y, k);
+    }
+    if (lane == 0) wsm[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kWarps; ++w) t.absorb(wsm[w], k);
+    __syncthreads();
+    return t;
+}
+
+template <int KMAX, int kVals>
+__global__ void __launch_bounds__(kThreads) long_kernel(const uint32_t* __restrict__ ptrs,
+                                                        const void* __restrict__ val_col,
+                                                        const uint32_t* __restrict__ seg_start,
+                                                        const uint32_t* __restrict__ long_list,
+                                                        const uint32_t* __restrict__ nlong_p,
+                                                        const uint32_t* __restrict__ chunk_off,
+                                                        uint32_t* __restrict__ done, TopK<KMAX>* __restrict__ partial,
+                                                        int k, uint64_t cap, uint8_t* __restrict__ nvalid,
+                                                        uint64_t* __restrict__ vals, uint32_t* __restrict__ optrs) {
+    __shared__ TopK<KMAX> wsm[kWarps];
+    __shared__ uint32_t last;
+    const uint32_t nlong = *nlong_p;
+    const uint32_t total = chunk_off[nlong];
+    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x) {
+        // list entry of chunk w: last i with chunk_off[i] <= w
+        uint32_t lo = 0, hi = nlong;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (chunk_off[mid] <= w) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t g = long_list[lo];
+        const uint32_t c = w - chunk_off[lo], nch = chunk_off[lo + 1] - chunk_off[lo];
+        const uint32_t s = seg_start[g], e = seg_start[g + 1];
+        const uint32_t r0 = s + c * kChunk, r1 = min(e, r0 + kChunk);
+        // eight rows of a thread at a time: their pointer loads, then their
+        // value gathers, are all in flight together
+        TopK<KMAX> t = TopK<KMAX>::identity();
+        for (uint32_t rb = r0 + threadIdx.x; rb < r1; rb += 8 * kThreads) {
+            uint32_t p[8];
+            uint64_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t r = rb + u * kThreads;
+                p[u] = r < r1 ? ld_stream(ptrs + r) : 0u;
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = rb + u * kThreads < r1 ? gather<kVals>(val_col, p[u]) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (rb + u * kThreads < r1) t.add_row(v[u], p[u], k);
+        }
+        t = block_merge(t, k, wsm);
+        if (nch == 1) {
+            if (threadIdx.x == 0) emit(g, t, k, cap, nvalid, vals, optrs);
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            partial[w] = t;
+            __threadfence();
+            last = atomicAdd(done + lo, 1u) == nch - 1;
+        }
+        __syncthreads();
+        if (last) {
+            // every other chunk of the segment has published its list
+            __threadfence();
+            TopK<KMAX> m = TopK<KMAX>::identity();
+            for (uint32_t q = threadIdx.x; q < nch; q += kThreads) {
+                const TopK<KMAX>* src = partial + chunk_off[lo] + q;
+                TopK<KMAX> y;
+                y.n = __ldcg(&src->n);
+#pragma unroll
+                for (int i = 0; i < KMAX; ++i) {
+                    y.v[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->v[i]));
+                    y.p[i] = __ldcg(&src->p[i]);
+                }
+                m.absorb(y, k);
+            }
+            m = block_merge(m, k, wsm);
+            if (threadIdx.x == 0) emit(g, m, k, cap, nvalid, vals, optrs);
         }
         __syncthreads();
     }
 }
 
-template <typename Agg>
-size_t seg_scratch(uint64_t n, size_t* flags_off, size_t* recs_off, size_t* counter_off) {
-    Carver c(nullptr);
+// ------------------------------------------------------------ scratch and launch
+struct TopkScratch {
+    uint32_t* tile_cnt;   // ntiles
+    uint32_t* seg_start;  // n + 1
+    uint32_t* long_list;  // n / (kLaneMax + 1) + 1
+    uint32_t* chunk_off;  // n / (kLaneMax + 1) + 2
+    uint32_t* mid_list;   // n / (kLaneMax + 1) + 1
+    uint32_t* small;      // nseg, nlong, nmid
+    uint32_t* done;       // n / (kWarpMax + 1) + 1 (zeroed with small)
+    void* partial;        // max chunks
+    size_t zero_bytes;
+    size_t total;
+};
+
+template <int KMAX>
+TopkScratch topk_carve(void* base, uint64_t n) {
+    Carver c(base);
+    TopkScratch t;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
-    c.take<uint32_t>(1);
-    *counter_off = 0;
-    *flags_off = c.off;
-    c.take<uint32_t>(ntiles);
-    const size_t zero_end = c.off;
-    (void)zero_end;
-    c.take<TileRec<Agg>>(ntiles);
-    *recs_off = c.off - ntiles * sizeof(TileRec<Agg>);
-    return c.bytes();
+    const uint64_t maxmid = n / (kLaneMax + 1) + 1;
+    const uint64_t maxlong = n / (kWarpMax + 1) + 1;
+    t.tile_cnt = c.take<uint32_t>(ntiles);
+    t.seg_start = c.take<uint32_t>(n + 1);
+    t.long_list = c.take<uint32_t>(maxlong);
+    t.chunk_off = c.take<uint32_t>(maxlong + 1);
+    t.mid_list = c.take<uint32_t>(maxmid);
+    t.small = c.take<uint32_t>(3);
+    const size_t z0 = c.off - 3 * sizeof(uint32_t);
+    t.done = c.take<uint32_t>(maxlong);
+    t.zero_bytes = c.off - z0;
+    t.partial = c.take<TopK<KMAX>>(n / kChunk + maxlong);
+    t.total = c.bytes();
+    return t;
 }
 
-template <typename Agg, typename Sink, int kVals>
-int launch_segreduce(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* vals, Sink sink, int k,
-                     uint64_t* nkeys, void* scratch, cudaStream_t s) {
-    size_t flags_off, recs_off, counter_off;
-    seg_scratch<Agg>(n, &flags_off, &recs_off, &counter_off);
-    char* base = static_cast<char*>(scratch);
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    // zero the tile counter and the flags
-    SBH_CUDA(cudaMemsetAsync(base, 0, flags_off + ntiles * sizeof(uint32_t), s));
-    int per_sm = 0;
-    SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, segreduce_kernel<Agg, Sink, kVals>, kThreads, 0));
-    if (per_sm < 1) per_sm = 1;
-    const unsigned grid = (unsigned)min_u64(ntiles, (uint64_t)num_sms() * per_sm);
-    SBH_TIMED("segreduce", s, segreduce_kernel<Agg, Sink, kVals><<<grid, kThreads, 0, s>>>(
-        keys, ptrs, n, vals, sink, k, nkeys, reinterpret_cast<uint32_t*>(base + flags_off),
-        reinterpret_cast<TileRec<Agg>*>(base + recs_off), reinterpret_cast<uint32_t*>(base + counter_off),
-        spin_limit(), status_word()));
+template <int KMAX, int kVals>
+int topk_run(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* vals, int K, uint64_t* ok,
+             uint8_t* onv, uint64_t* ov, uint32_t* op, uint64_t cap, uint64_t* nkeys, void* scratch, cudaStream_t s) {
+    TopkScratch t = topk_carve<KMAX>(scratch, n);
+    const uint32_t n32 = static_cast<uint32_t>(n);
+    const uint32_t ntiles = static_cast<uint32_t>((n + kTile - 1) / kTile);
+    const int sms = num_sms();
+    SBH_CUDA(cudaMemsetAsync(t.small, 0, t.zero_bytes, s));
+    SBH_TIMED("topk_heads_count", s, heads_count_kernel<<<ntiles, kThreads, 0, s>>>(keys, n32, t.tile_cnt));
+    SBH_LAUNCHED();
+    SBH_TIMED("topk_heads_scan", s,
+              heads_scan_kernel<<<1, 1024, 0, s>>>(t.tile_cnt, ntiles, nkeys, t.small, t.seg_start, n32));
+    SBH_LAUNCHED();
+    SBH_TIMED("topk_heads_emit", s,
+              heads_emit_kernel<<<ntiles, kThreads, 0, s>>>(keys, n32, t.tile_cnt, ok, cap, t.seg_start));
+    SBH_LAUNCHED();
+    const unsigned sgrid = (unsigned)min_u64((n + kThreads - 1) / kThreads, (uint64_t)sms * 8);
+    SBH_TIMED("topk_small", s,
+              (small_kernel<KMAX, kVals><<<sgrid, kThreads, 0, s>>>(ptrs, vals, t.seg_start, t.small, K, cap, onv, ov,
+                                                                   op, t.long_list, t.small + 1, t.mid_list,
+                                                                   t.small + 2)));
+    SBH_LAUNCHED();
+    SBH_TIMED("topk_medium", s,
+              (medium_kernel<KMAX, kVals><<<(unsigned)sms * 8, kThreads, 0, s>>>(ptrs, vals, t.seg_start, t.mid_list,
+                                                                               t.small + 2, K, cap, onv, ov, op)));
+    SBH_LAUNCHED();
+    SBH_TIMED("topk_long_scan", s,
+              long_scan_kernel<<<1, 1024, 0, s>>>(t.long_list, t.small + 1, t.seg_start, t.chunk_off));
+    SBH_LAUNCHED();
+    const unsigned lgrid = (unsigned)min_u64(n / kChunk + 64, (uint64_t)sms * 4);
+    SBH_TIMED("topk_long", s,
+              (long_kernel<KMAX, kVals><<<lgrid, kThreads, 0, s>>>(
+                  ptrs, vals, t.seg_start, t.long_list, t.small + 1, t.chunk_off, t.done,
+                  static_cast<TopK<KMAX>*>(t.partial), K, cap, onv, ov, op)));
     SBH_LAUNCHED();
     return SBH_OK;
 }
@@ -385,14 +494,8 @@ template <int KMAX>
 int topk_dispatch(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* vals, int vb, int K,
                   uint64_t* ok, uint8_t* onv, uint64_t* ov, uint32_t* op, uint64_t cap, uint64_t* nkeys,
                   void* scratch, cudaStream_t s) {
-    TopKSink<KMAX> sink{ok, onv, ov, op, cap, K};
-    if (vb == 8) return launch_segreduce<TopK<KMAX>, TopKSink<KMAX>, 8>(keys, ptrs, n, vals, sink, K, nkeys, scratch, s);
-    return launch_segreduce<TopK<KMAX>, TopKSink<KMAX>, 4>(keys, ptrs, n, vals, sink, K, nkeys, scratch, s);
-}
-
-size_t topk_scratch(uint64_t n) {
-    size_t a, b, c;
-    return seg_scratch<TopK<8>>(n, &a, &b, &c);
+    if (vb == 8) return topk_run<KMAX, 8>(keys, ptrs, n, vals, K, ok, onv, ov, op, cap, nkeys, scratch, s);
+    return topk_run<KMAX, 4>(keys, ptrs, n, vals, K, ok, onv, ov, op, cap, nkeys, scratch, s);
 }
 
 }  // namespace
@@ -406,8 +509,10 @@ int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const v
     using namespace sbh;
     clear_error();
     if (K < 1 || K > SBH_TOPK_MAX_K) { set_error("K must be in [1, %d]", SBH_TOPK_MAX_K); return SBH_EINVAL; }
+    if (n >= 0xFFFFFFFFull) { set_error("n must be < 2^32 - 1"); return SBH_EINVAL; }
     bool done = false;
-    int rc = scratch_check(d_scratch, scratch_bytes, topk_scratch(n), &done);
+    const size_t need = K <= 4 ? topk_carve<4>(nullptr, n).total : topk_carve<8>(nullptr, n).total;
+    int rc = scratch_check(d_scratch, scratch_bytes, need, &done);
     if (rc || done) return rc;
     if (!d_nkeys) { set_error("d_nkeys is NULL"); return SBH_EINVAL; }
     cudaStream_t s = as_stream(stream);
@@ -420,11 +525,11 @@ int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const v
         return SBH_EINVAL;
     }
     if (val_bytes != 4 && val_bytes != 8) { set_error("val_bytes must be 4 or 8"); return SBH_EINVAL; }
-    if (K == 1) return topk_dispatch<1>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals, d_out_ptrs, cap, d_nkeys, d_scratch, s);
-    if (K == 2) return topk_dispatch<2>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals, d_out_ptrs, cap, d_nkeys, d_scratch, s);
-    if (K == 3) return topk_dispatch<3>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals, d_out_ptrs, cap, d_nkeys, d_scratch, s);
-    if (K == 4) return topk_dispatch<4>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals, d_out_ptrs, cap, d_nkeys, d_scratch, s);
-    return topk_dispatch<8>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals, d_out_ptrs, cap, d_nkeys, d_scratch, s);
+    if (K <= 4)
+        return topk_dispatch<4>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals,
+                                d_out_ptrs, cap, d_nkeys, d_scratch, s);
+    return topk_dispatch<8>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals,
+                            d_out_ptrs, cap, d_nkeys, d_scratch, s);
 }
 
 }  // extern "C"

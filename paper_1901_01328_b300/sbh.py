@@ -44,6 +44,7 @@ def _load() -> ctypes.CDLL:
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1901_01328_b300.build`")
     lib = ctypes.CDLL(LIB_PATH)
     vp, u64, u32, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)
+    i64 = ctypes.c_int64
     sig = {
         "sbh_version": ([], ctypes.c_char_p),
         "sbh_last_error": ([], ctypes.c_char_p),
@@ -56,6 +57,7 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_extract": ([vp, u64, u64, vp, vp, vp, vp, u64, vp], i32),
         "sbh_kpa_extract_windows": ([vp, vp, u64, u64, u64, vp, vp, vp, vp], i32),
         "sbh_window_bits": ([u64], i32),
+        "sbh_kpa_split_ts": ([vp, vp, u64, i64, u64, u64, u32, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
         "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
@@ -77,7 +79,8 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
             "sbh_profile_enable", "sbh_profile_collect",
-            "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_extract_windows", "sbh_window_bits", "sbh_kpa_sort",
+            "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_extract_windows", "sbh_window_bits", "sbh_kpa_split_ts",
+            "sbh_kpa_sort",
             "sbh_kpa_merge", "sbh_group_reduce",
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
             "sbh_kpa_sort_learned",
@@ -166,6 +169,25 @@ def sbh_kpa_extract_windows(key_col, offsets, row_begin, n, keys_out, ptrs_out, 
     """offsets: device uint64 tensor of nwin + 1 row offsets."""
     _check(_lib.sbh_kpa_extract_windows(_p(key_col), _p(offsets), offsets.numel() - 1, row_begin, n, _p(keys_out),
                                         _p(ptrs_out), _p(key_or), _stream(stream)), "sbh_kpa_extract_windows")
+
+
+def sbh_kpa_split_ts(keys, ts_rel, n, ts_base, win_len, first_win, ptr_base, slot0, slot1, fill, dropped, overflow,
+                     scratch=None, stream=None):
+    """slot0, slot1: (keys, ptrs) device tensors (their lengths are the capacities)."""
+    args = (_p(keys), _p(ts_rel), n, ts_base, win_len, first_win, ptr_base, _p(slot0[0]), _p(slot0[1]),
+            slot0[0].numel(), _p(slot1[0]), _p(slot1[1]), slot1[0].numel(), _p(fill), _p(dropped), _p(overflow))
+    if scratch is None:
+        return _scratch(_lib.sbh_kpa_split_ts, args, (_stream(stream),), "sbh_kpa_split_ts", keys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_kpa_split_ts(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_kpa_split_ts")
+    return scratch
+
+
+def split_scratch_bytes(n: int) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_kpa_split_ts(None, None, n, 0, 1, 0, 0, None, None, 0, None, None, 0, None, None, None, None,
+                                 ctypes.byref(nbytes), None), "sbh_kpa_split_ts")
+    return nbytes.value
 
 
 def window_bits(nwin: int) -> int:

@@ -1,0 +1,288 @@
+"""Serving loop: record bundles arrive, tumbling windows close by watermark,
+and each closed window's per-key sum, count and top-K come back to the host
+(Sec. 3: bundles, watermarks and windows; Sec. 4.2 "Windowing" and "Keyed
+Aggregation"; Sec. 5: the engine admits data only while memory allows).
+Orchestration only: every step on the data runs in libsbh.so kernels.
+
+Window state lives on the device.  Two window slots (the window being
+filled and the one before it, which stays open until the watermark passes
+its end) each hold an unsorted KPA of (key, arena row); the value column of
+every admitted bundle sits in an arena ring in HBM until the last window
+that uses it has closed.  Per bundle: copy its columns in (keys and
+timestamps to a staging area, values to the arena), and split its rows into
+the two slots by timestamp (`sbh_kpa_split_ts`, no host synchronisation).
+When the watermark (max timestamp seen minus the allowed lateness) passes a
+window's end, the window closes: its slot is sorted, reduced (sum and count)
+and top-K'd against the arena, the results are copied to the host, and the
+slot is emptied for the window after next.
+
+Memory is fixed at start-up from the HBM budget: a bundle that does not fit
+in the arena is shed (counted); a slot that would pass its capacity sets an
+overflow flag (counted).  Window-close latency is measured from the moment
+the bundle that moved the watermark past the window's end was admitted to the
+moment the window's results are in host memory.
+"""
+from __future__ import annotations
+
+import collections
+import time
+
+import numpy as np
+import torch
+
+from . import sbh
+
+
+def _u64(n, dev):
+    return torch.empty(max(1, n), dtype=torch.uint64, device=dev)
+
+
+def _u32(n, dev):
+    return torch.empty(max(1, n), dtype=torch.uint32, device=dev)
+
+
+class WindowResult:
+    """One closed window, in host memory: keys (ascending), counts, sums,
+    nvalid [m], top values and ptrs [m, K] (ptr = arena row)."""
+
+    def __init__(self, w, keys, counts, sums, nvalid, tvals, tptrs, latency_s, rows):
+        self.w, self.keys, self.counts, self.sums = w, keys, counts, sums
+        self.nvalid, self.tvals, self.tptrs = nvalid, tvals, tptrs
+        self.latency_s, self.rows = latency_s, rows
+
+
+class ArenaRing:
+    """Rows of the value arena as a ring: bundles are placed whole (wrapping
+    to the start when the end has no room) and released in arrival order
+    once the last window that uses them has closed."""
+
+    def __init__(self, rows):
+        self.rows = rows
+        self.head = 0                     # next free row
+        self.live = collections.deque()   # (offset, rows, last window)
+
+    def alloc(self, n, last_w):
+        if n > self.rows:
+            return None
+        if not self.live:
+            off = 0
+        else:
+            tail = self.live[0][0]
+            if self.head > tail:  # free: [head, end) and [0, tail)
+                off = self.head if self.rows - self.head >= n else (0 if tail >= n else None)
+            elif self.head < tail:  # free: [head, tail)
+                off = self.head if tail - self.head >= n else None
+            else:  # head == tail with bundles live: full
+                off = None
+        if off is None:
+            return None
+        self.head = off + n
+        self.live.append((off, n, last_w))
+        return off
+
+    def release(self, closed_w):
+        while self.live and self.live[0][2] <= closed_w:
+            self.live.popleft()
+        if not self.live:
+            self.head = 0
+
+
+class WindowServer:
+    def __init__(self, win_len, lateness, slot_rows, arena_rows, max_bundle, K=3, device="cuda", keep=True,
+                 out_rows=None):
+        dev = torch.device(device)
+        self.dev, self.win_len, self.lateness, self.K = dev, int(win_len), int(lateness), K
+        self.slots = [(_u64(slot_rows, dev), _u32(slot_rows, dev)) for _ in range(2)]
+        self.fill = torch.zeros(2, dtype=torch.uint64, device=dev)
+        self.dropped = torch.zeros(1, dtype=torch.uint64, device=dev)
+        self.overflow = torch.zeros(1, dtype=torch.uint32, device=dev)
+        self.arena = _u64(arena_rows, dev)
+        self.arena_rows = arena_rows
+        self.stage_keys = _u64(max_bundle, dev)
+        self.stage_ts = torch.empty(max(1, max_bundle), dtype=torch.int64, device=dev)
+        self.split_scr = torch.empty(sbh.split_scratch_bytes(max_bundle), dtype=torch.uint8, device=dev)
+        self.slot_rows = slot_rows
+        out = slot_rows if out_rows is None else min(out_rows, slot_rows)  # distinct keys a window may have
+        self.out_rows = out
+        self.sort_scr = torch.empty(max(1, sbh.sort_scratch_bytes(slot_rows)), dtype=torch.uint8, device=dev)
+        self.red = (_u64(out, dev), _u64(out, dev), _u64(out, dev), _u64(1, dev))
+        self.red_scr = torch.empty(max(1, sbh.group_reduce_scratch_bytes(slot_rows, 8)), dtype=torch.uint8, device=dev)
+        self.top = (_u64(out, dev), torch.empty(max(1, out), dtype=torch.uint8, device=dev),
+                    _u64(out * K, dev), _u32(out * K, dev), _u64(1, dev))
+        self.top_scr = torch.empty(max(1, sbh.topk_scratch_bytes(slot_rows, K, 8)), dtype=torch.uint8, device=dev)
+        self.fill_h = torch.zeros(2, dtype=torch.uint64).pin_memory()
+        self.nk_h = torch.zeros(1, dtype=torch.uint64).pin_memory()
+        # page-locked host copies of a window's results
+        self.host = (torch.empty(out, dtype=torch.uint64).pin_memory(), torch.empty(out, dtype=torch.uint64).pin_memory(),
+                     torch.empty(out, dtype=torch.uint64).pin_memory(), torch.empty(out, dtype=torch.uint8).pin_memory(),
+                     torch.empty(out * K, dtype=torch.uint64).pin_memory(),
+                     torch.empty(out * K, dtype=torch.uint32).pin_memory())
+        self.wm = None
+        self.first_win = None  # oldest open window
+        self.ring = ArenaRing(arena_rows)
+        self.log = []          # (arena offset, rows, ts_base) of every admitted bundle
+        self.results = []
+        self.keep = keep
+        self.shed_bundles = 0
+        self.shed_rows = 0
+        self.admitted_rows = 0
+        self.est = {}  # host estimate of each open window's rows (a bundle counts in its newest window)
+        self.truncated = 0
+
+    # ---------------------------------------------------------------- bundles
+    def admit(self, keys_h, vals_h, ts_rel_h, ts_base, max_ts):
+        """keys_h, vals_h (uint64) and ts_rel_h (int64) are page-locked host
+        tensors of one bundle; row i has timestamp ts_base + ts_rel_h[i] and
+        max_ts is the largest.  Returns False when the bundle is shed."""
+        n = keys_h.numel()
+        t_admit = time.perf_counter()
+        new_wm = max_ts - self.lateness if self.wm is None else max(self.wm, max_ts - self.lateness)
+        if self.first_win is None:
+            self.first_win = max(0, (ts_base + int(ts_rel_h.min()) if n else ts_base)) // self.win_len
+        # windows whose end the watermark has passed close before this bundle lands
+        while (self.first_win + 1) * self.win_len <= new_wm:
+            self._close(self.first_win, t_admit)
+            self.first_win += 1
+        self.wm = new_wm
+        w_new = max_ts // self.win_len
+        # admission: the arena must have room, and the bundle's newest
+        # window must stay below its slot's capacity (2% kept for late rows)
+        if self.est.get(w_new, 0) + n > 0.98 * self.slot_rows:
+            off = None
+        else:
+            off = self.ring.alloc(n, w_new)
+        if off is None:
+            self.shed_bundles += 1
+            self.shed_rows += n
+            return False
+        self.est[w_new] = self.est.get(w_new, 0) + n
+        if self.keep:
+            self.log.append((off, n, ts_base))
+        self.stage_keys[:n].copy_(keys_h, non_blocking=True)
+        self.stage_ts[:n].copy_(ts_rel_h, non_blocking=True)
+        self.arena[off:off + n].copy_(vals_h, non_blocking=True)
+        s0, s1 = (self.slots[0], self.slots[1])
+        self.split_scr = sbh.sbh_kpa_split_ts(self.stage_keys, self.stage_ts, n, ts_base, self.win_len, self.first_win,
+                                              off, s0, s1, self.fill, self.dropped, self.overflow,
+                                              scratch=self.split_scr)
+        self.admitted_rows += n
+        return True
+
+    def finish(self, t_now=None):
+        """Close every open window (end of stream)."""
+        t = time.perf_counter() if t_now is None else t_now
+        if self.first_win is None:
+            return
+        last = (self.wm + self.lateness) // self.win_len if self.wm is not None else self.first_win
+        while self.first_win <= last:
+            self._close(self.first_win, t)
+            self.first_win += 1
+
+    # ---------------------------------------------------------------- window close
+    def _close(self, w, t_trigger):
+        s = w & 1
+        keys, ptrs = self.slots[s]
+        self.fill_h.copy_(self.fill, non_blocking=True)
+        torch.cuda.current_stream(self.dev).synchronize()
+        m = int(self.fill_h[s])
+        K = self.K
+        res = None
+        t_dev = None
+        if m:
+            ok, op = keys[:m], ptrs[:m]
+            sbh.sbh_kpa_sort(ok, op, ok, op, scratch=self.sort_scr)  # in place
+            cap = self.out_rows
+            rk, rc, rs, rn = self.red
+            sbh.sbh_group_reduce(ok, op, self.arena, rk, rc, rs, cap, rn, scratch=self.red_scr)
+            tk, tn, tv, tp, tnk = self.top
+            sbh.sbh_topk(ok, op, self.arena, K, tk, tn, tv, tp, cap, tnk, scratch=self.top_scr)
+            self.nk_h.copy_(rn, non_blocking=True)
+            torch.cuda.current_stream(self.dev).synchronize()
+            t_dev = time.perf_counter()
+            u = int(self.nk_h[0])
+            if u > cap:
+                self.truncated += 1
+                u = cap
+            hk, hc, hs, hn, hv, hp = self.host
+            for h, d, m_ in ((hk, rk, u), (hc, rc, u), (hs, rs, u), (hn, tn, u), (hv, tv, u * K), (hp, tp, u * K)):
+                h[:m_].copy_(d[:m_], non_blocking=True)
+            torch.cuda.current_stream(self.dev).synchronize()
+            if self.keep:
+                res = [hk[:u].clone(), hc[:u].clone(), hs[:u].clone(), hn[:u].clone(), hv[:u * K].clone().view(u, K),
+                       hp[:u * K].clone().view(u, K)]
+        lat = time.perf_counter() - t_trigger
+        self.fill[s:s + 1].zero_()
+        r = (WindowResult(w, *(x.numpy() for x in res), lat, m) if res else
+             WindowResult(w, None, None, None, None, None, None, lat, m))
+        r.device_latency_s = (t_dev - t_trigger) if m else lat
+        self.results.append(r)
+        self.ring.release(w)
+        self.est.pop(w, None)
+
+    def stats(self):
+        return {"shed_bundles": self.shed_bundles, "shed_rows": self.shed_rows,
+                "admitted_rows": self.admitted_rows, "dropped_rows": int(self.dropped.item()),
+                "overflow": int(self.overflow.item()), "truncated_windows": self.truncated}
+
+
+def plan(budget_bytes, load, win_len_ns, lateness_ns, max_keys, K=3):
+    """Slot, arena and output sizes (rows) that fit the HBM budget for an
+    offered load (rows/s): each slot row costs 12 B (KPA) x 2 slots + 12 B
+    of sort scratch + about 5 B of top-K scratch; the arena holds a window
+    plus the lateness and a margin (8 B a row); outputs hold max_keys keys
+    (24 B for count and sum, 9 + 12 K B for the top-K)."""
+    win_rows = load * (win_len_ns + lateness_ns) * 1e-9
+    arena_rows = int(1.3 * win_rows)
+    out_rows = int(max_keys * 1.02) + 1024
+    out_bytes = out_rows * (24 + 9 + 12 * K)
+    slot_rows = int((budget_bytes - 8 * arena_rows - out_bytes) / 41)
+    slot_rows = max(0, min(slot_rows, int(1.15 * load * win_len_ns * 1e-9) + (1 << 20)))
+    return slot_rows, arena_rows, out_rows
+
+
+# -------------------------------------------------------------------- synthetic source
+class BundlePool:
+    """A pool of synthetic bundles in page-locked host memory (keys Zipf(s)
+    over n_ids, values uniform u64, timestamps relative to the bundle's
+    arrival: 0, or for a fraction `late` of the rows minus U(0, lateness))."""
+
+    def __init__(self, gen, n_bundles, lo, hi, s, n_ids, late, lateness, seed):
+        sizes = gen.uniform(seed, 1, n_bundles, lo, hi - lo + 1, np.uint64).astype(np.int64)
+        self.bundles = []
+        for b in range(n_bundles):
+            m = int(sizes[b])
+            keys = gen.zipf(seed, 100 + b, m, s, n_ids)
+            vals = gen.uniform(seed, 10_000 + b, m, 0, 0, np.uint64)
+            u = gen.unif01(seed, 20_000 + b, 2 * m)
+            lag = np.where(u[:m] < late, np.floor(u[m:] * lateness), 0).astype(np.int64)
+            self.bundles.append(tuple(torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).pin_memory()
+                                      for a in (keys, vals, -lag)))
+        self.sizes = sizes
+
+    def get(self, i):
+        k, v, t = self.bundles[i % len(self.bundles)]
+        return k.view(torch.uint64), v.view(torch.uint64), t
+
+
+def poisson_schedule(gen, seed, duration_ns, load, mean_rows):
+    """Arrival times (ns) of a Poisson bundle stream offering `load` rows/s."""
+    rate = load / mean_rows  # bundles per second
+    n = int(duration_ns * 1e-9 * rate * 1.2) + 16
+    gaps = -np.log1p(-gen.unif01(seed, 7, n)) / rate * 1e9
+    t = np.cumsum(gaps)
+    return t[t < duration_ns].astype(np.int64)
+
+
+def run_loop(server, pool, arrivals, realtime=True, t0_ns=0):
+    """Feeds the bundles at their arrival times (wall clock when realtime)."""
+    start = time.perf_counter()
+    for i, a in enumerate(arrivals):
+        if realtime:
+            due = start + (a - arrivals[0]) * 1e-9
+            while time.perf_counter() < due:
+                pass
+        k, v, t = pool.get(i)
+        base = int(t0_ns + a)
+        server.admit(k, v, t, base, base)
+    server.finish()
+    return time.perf_counter() - start

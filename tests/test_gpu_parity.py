@@ -222,6 +222,32 @@ def test_topk_parity(S, K, vbytes, n, space, vspan):
     assert same(tk, ok) and same(tn, onv) and same(tv, ov) and same(tp, op)
 
 
+@pytest.mark.parametrize("K", [3, 8])
+def test_topk_segment_size_boundaries_and_cap(S, K):
+    # runs at the per-thread limit (64 / 65 rows), the per-warp limit (4096 /
+    # 4097) and the chunk size (16384 / 16385 rows), runs of several chunks,
+    # short runs between them
+    counts = [1, 64, 65, 2, 4096, 4097, 16384, 16385, 40_000, 3, 100_000, 7]
+    col = np.repeat(np.arange(len(counts), dtype=np.uint64) * 11, counts)
+    n = col.size
+    vals = gen.uniform(6, 6, n, 0, 50, np.uint64)
+    sk, sp = _sorted_kpa(S, col)
+    tk, tn, tv, tp = S.topk(sk, sp, cuda(vals), K)
+    ok, onv, ov, op = oracle.topk(host(sk), host(sp), vals, K)
+    assert same(tk, ok) and same(tn, onv) and same(tv, ov) and same(tp, op)
+    # a capacity below the number of keys: the first cap keys are written
+    cap = 4
+    okk = torch.zeros(cap, dtype=torch.uint64, device="cuda")
+    onn = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    ovv = torch.zeros(cap * K, dtype=torch.uint64, device="cuda")
+    opp = torch.zeros(cap * K, dtype=torch.uint32, device="cuda")
+    nk = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    S.sbh_topk(sk, sp, cuda(vals), K, okk, onn, ovv, opp, cap, nk)
+    assert int(host(nk)[0]) == len(counts)
+    assert same(okk, ok[:cap]) and same(onn, onv[:cap]) and same(ovv, ov[:cap].reshape(-1))
+    assert same(opp, op[:cap].reshape(-1))
+
+
 def test_topk_batched_window_shape(S):
     b = gen.batched_windows(8, 4)
     col, vals = b["keys"], b["vals"]

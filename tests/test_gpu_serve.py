@@ -1,0 +1,130 @@
+"""The serving loop on the GPU against the oracle: bundles with late rows
+arrive in event time, windows close by watermark, and every closed window's
+per-key count, sum and top-3 equal the oracle's over the rows whose
+timestamps fall in it (ptr = the arena row the bundle was given)."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SEED = gen.SEED_BASE + 5
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import serve
+    return serve
+
+
+def _run(V, arena_rows, n_windows=8, load=3.3e8, slot_rows=1 << 20):
+    win, late = 1_000_000, 100_000  # 1 ms windows, 0.1 ms allowed lateness (ns)
+    pool = V.BundlePool(gen, 8, 2000, 20_000, 0.8, 50_000_000, 0.05, late, SEED)
+    arr = V.poisson_schedule(gen, SEED, n_windows * win, load, float(pool.sizes.mean()))
+    server = V.WindowServer(win, late, slot_rows=slot_rows, arena_rows=arena_rows, max_bundle=20_000, K=3)
+    t0 = 10 * win
+    admitted = []
+    for i, a in enumerate(arr):
+        k, v, t = pool.get(i)
+        base = int(t0 + a)
+        if server.admit(k, v, t, base, base):
+            admitted.append(i)
+    server.finish()
+    return server, pool, admitted, win
+
+
+def _oracle_windows(server, pool, admitted, win, arena_rows):
+    rows = {}
+    for i, (off, n, base) in zip(admitted, server.log):
+        k, v, t = (x.numpy() for x in pool.get(i))
+        ts = base + t
+        for w in np.unique(ts // win):
+            m = ts // win == w
+            idx = np.nonzero(m)[0]
+            rows.setdefault(int(w), []).append((k.view(np.uint64)[m], (off + idx).astype(np.uint32),
+                                                v.view(np.uint64)[m]))
+    out = {}
+    for w, parts in rows.items():
+        keys = np.concatenate([p[0] for p in parts])
+        ptrs = np.concatenate([p[1] for p in parts])
+        col = np.zeros(arena_rows, np.uint64)
+        for p in parts:
+            col[p[1]] = p[2]
+        sk, sp = oracle.sort(keys, ptrs)
+        uk, uc, us = oracle.group_sum_count(sk, sp, col)
+        tk, tn, tv, tp = oracle.topk(sk, sp, col, 3)
+        out[w] = (uk, uc, us, tn, tv, tp, keys.size)
+    return out
+
+
+def test_serving_windows_match_oracle(V):
+    arena_rows = 900_000  # about 2.7 windows of rows: the arena ring wraps
+    server, pool, admitted, win = _run(V, arena_rows)
+    st = server.stats()
+    assert st["overflow"] == 0 and st["dropped_rows"] == 0 and st["shed_bundles"] == 0
+    exp = _oracle_windows(server, pool, admitted, win, arena_rows)
+    got = {r.w: r for r in server.results}
+    assert set(w for w in exp) <= set(got)
+    for w, (uk, uc, us, tn, tv, tp, n) in exp.items():
+        r = got[w]
+        assert r.rows == n
+        assert np.array_equal(r.keys, uk) and np.array_equal(r.counts, uc) and np.array_equal(r.sums, us)
+        assert np.array_equal(r.nvalid, tn) and np.array_equal(r.tvals, tv) and np.array_equal(r.tptrs, tp)
+        assert r.latency_s >= 0
+    assert sum(r.rows for r in server.results) == st["admitted_rows"]
+
+
+def test_serving_sheds_bundles_when_the_arena_is_full(V):
+    server, pool, admitted, win = _run(V, arena_rows=300_000, n_windows=4)
+    st = server.stats()
+    assert st["shed_bundles"] > 0 and st["shed_rows"] > 0
+    # the admitted rows are all accounted for in the windows
+    assert sum(r.rows for r in server.results) == st["admitted_rows"]
+    exp = _oracle_windows(server, pool, admitted, win, 300_000)
+    got = {r.w: r for r in server.results}
+    for w, (uk, uc, us, tn, tv, tp, n) in exp.items():
+        assert np.array_equal(got[w].keys, uk) and np.array_equal(got[w].sums, us)
+
+
+def test_serving_admission_keeps_windows_under_slot_capacity(V):
+    server, pool, admitted, win = _run(V, arena_rows=900_000, n_windows=3, slot_rows=50_000)
+    st = server.stats()
+    assert st["overflow"] == 0 and st["shed_bundles"] > 0
+    exp = _oracle_windows(server, pool, admitted, win, 900_000)
+    got = {r.w: r for r in server.results}
+    for w, (uk, uc, us, tn, tv, tp, n) in exp.items():
+        assert got[w].rows == n <= 50_000
+        assert np.array_equal(got[w].keys, uk) and np.array_equal(got[w].tvals, tv)
+
+
+def test_split_by_timestamp_slots_capacity_and_drops(V):
+    from paper_1901_01328_b300 import sbh
+    win = 1000
+    n = 10_000
+    ts = gen.uniform(SEED, 9, n, 0, 4 * win, np.uint64).astype(np.int64)  # windows 0 .. 3
+    keys = gen.uniform(SEED, 10, n, 0, 1 << 40, np.uint64)
+    dk, dt = torch.from_numpy(keys).cuda(), torch.from_numpy(ts).cuda()
+    cap = 1500
+    s0 = (torch.zeros(cap, dtype=torch.uint64, device="cuda"), torch.zeros(cap, dtype=torch.uint32, device="cuda"))
+    s1 = (torch.zeros(cap, dtype=torch.uint64, device="cuda"), torch.zeros(cap, dtype=torch.uint32, device="cuda"))
+    fill = torch.zeros(2, dtype=torch.uint64, device="cuda")
+    dropped = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    over = torch.zeros(1, dtype=torch.uint32, device="cuda")
+    # windows 1 and 2 are open; rows of windows 0 and 3 are dropped
+    sbh.sbh_kpa_split_ts(dk, dt, n, 0, win, 1, 7, s0, s1, fill, dropped, over)
+    w = ts // win
+    f = fill.cpu().numpy()
+    for slot, wid in ((1, 1), (0, 2)):
+        idx = np.nonzero(w == wid)[0]
+        m = min(idx.size, cap)
+        assert f[slot] == m
+        sk, sp = (s1 if slot == 1 else s0)
+        assert np.array_equal(sk[:m].cpu().numpy(), keys[idx[:m]])          # stable: row order kept
+        assert np.array_equal(sp[:m].cpu().numpy(), (idx[:m] + 7).astype(np.uint32))
+    assert int(dropped.item()) == int(np.sum((w == 0) | (w == 3)))
+    assert int(over.item()) == (1 if max(np.sum(w == 1), np.sum(w == 2)) > cap else 0) == 1
