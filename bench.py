@@ -64,6 +64,29 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+def window_seed(base, rank):
+    """Each rank sorts its own window: the seed of rank r's keys."""
+    return base + rank
+
+
+def max_over_ranks_on(x, ws, device):
+    """The largest x over the ranks (every rank gets it)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def whole_job_rate(steps, rows_per_rank, ws, ms_max):
+    """Records per second of the whole job: every rank's rows over the
+    slowest rank's time."""
+    return steps * rows_per_rank * ws / (ms_max / 1e3)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi while running."""
 
@@ -189,7 +212,7 @@ def run_gpu(args):
 
     # ---- inputs: each rank draws its own window (seed offset by rank)
     col_h = torch.empty(n, dtype=torch.uint64).pin_memory()
-    gen.mixed_keys(n, seed=gen.SEED_MIXED + rank, out=col_h.numpy())
+    gen.mixed_keys(n, seed=window_seed(gen.SEED_MIXED, rank), out=col_h.numpy())
     col = col_h.to(dev)
     init = torch.from_numpy(gen.mlp_init()).to(dev)
     keys = torch.empty(n, dtype=torch.uint64, device=dev)
@@ -228,11 +251,7 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if ws > 1:
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return max_over_ranks_on(x, ws, dev)
 
     def timed(fn, steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -264,7 +283,7 @@ def run_gpu(args):
     with Clocks(local) as clk:
         ms = timed(step, args.steps)
     clocks = clk.summary()
-    value = args.steps * n * ws / (ms / 1e3)
+    value = whole_job_rate(args.steps, n, ws, ms)
     assert sbh.sync_status() == sbh.SBH_OK
 
     # ---- the other sort path on the same window, for the comparison
@@ -563,7 +582,33 @@ def row_suite(peak):
     oms = cpu_ms(lambda: oracle.join(lh[0], lh[1], rh[0], rh[1]))
     pairs = int(npairs.item())
     out["A8_join"] = entry(ms, 2 * 1_000_000 * 12 + pairs * 8, f"1M x 1M window, keys U[0,2^24), {pairs} pairs", oms)
-    del L, R, jl, jr, tsk, tsp, tv, tk, tn, tvo, tpo
+
+    # Table 2 record primitives and per-key statistics, on the 4M-row top-K window
+    mat = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_kpa_materialize(tsp, tv, mat))
+    hp_ = tsp.cpu().numpy()
+    oms = cpu_ms(lambda: oracle.materialize(hp_, bv_))
+    out["materialize"] = entry(ms, nb_ * (4 + 32 + 8), "4M ptrs, u64 column gathered (a 32-byte sector per row)", oms)
+    lo_, hi_ = 0, 1 << 63
+    sel_k = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    sel_p = torch.empty(nb_, dtype=torch.uint32, device=dev)
+    sel_n = torch.empty(1, dtype=torch.uint64, device=dev)
+    scr_sel = sbh.sbh_kpa_select(tsk, tsp, tv, lo_, hi_, sel_k, sel_p, nb_, sel_n)
+    ms = dev_ms(lambda: sbh.sbh_kpa_select(tsk, tsp, tv, lo_, hi_, sel_k, sel_p, nb_, sel_n, scratch=scr_sel))
+    kept = int(sel_n.item())
+    hk_ = tsk.cpu().numpy()
+    oms = cpu_ms(lambda: oracle.select(hk_, hp_, bv_, lo_, hi_))
+    out["select"] = entry(ms, 2 * nb_ * (4 + 32) + kept * 12, f"4M rows, values in [0, 2^63): {kept} kept", oms)
+    mk_ = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    mm_ = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    mu_ = torch.empty(nb_, dtype=torch.uint64, device=dev)
+    mn_ = torch.empty(1, dtype=torch.uint64, device=dev)
+    scr_mu = sbh.sbh_median_unique(tsk, tsp, tv, mk_, mm_, mu_, nb_, mn_)
+    ms = dev_ms(lambda: sbh.sbh_median_unique(tsk, tsp, tv, mk_, mm_, mu_, nb_, mn_, scratch=scr_mu))
+    oms = cpu_ms(lambda: oracle.median_unique(hk_, hp_, bv_))
+    out["median_unique"] = entry(ms, None, "4M-row window, Zipf(1.0) keys: lower median and distinct values per key "
+                                 "(two stable radix sorts)", oms)
+    del L, R, jl, jr, tsk, tsp, tv, tk, tn, tvo, tpo, mat, sel_k, sel_p, mk_, mm_, mu_, scr_sel, scr_mu
     out.update(pipeline_rows())
     return out
 

@@ -230,6 +230,42 @@ int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const v
              int K, uint64_t* d_out_keys, uint8_t* d_out_nvalid, uint64_t* d_out_vals, uint32_t* d_out_ptrs,
              uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
 
+/* Median and distinct values per key (Sec. 7, benchmarks "Median" and
+ * "Unique Count"; Average is sum / count from sbh_group_reduce).  For each
+ * distinct key j of a KPA sorted by key, in key order: d_out_keys[j],
+ * d_out_median[j] = the lower median of its values d_val_col[ptr] (the value
+ * at index (count - 1) / 2 of the key's values in ascending order), and
+ * d_out_unique[j] = the number of distinct values.  The rows are re-ordered
+ * by (key, value) with two stable radix sorts (by value, then by key), so
+ * inside each key's run the values ascend.  val_bytes 4 or 8; cap and
+ * *d_nkeys as in sbh_group_reduce; n < 2^32 - 1.
+ * Scratch: about 70 n bytes. */
+int sbh_median_unique(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
+                      int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_median, uint64_t* d_out_unique,
+                      uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* Materialize (Table 2: the values of a column for the records of a KPA, in
+ * KPA order): d_out[i] = d_col[d_ptrs[i]] for i < n, col_bytes 4 or 8 (d_out
+ * holds n such values).  n < 2^32.  No scratch. */
+int sbh_kpa_materialize(const uint32_t* d_ptrs, uint64_t n, const void* d_col, int col_bytes, void* d_out,
+                        void* stream);
+
+/* KeySwap (Table 2: make another key column the KPA's resident key):
+ * d_keys_out[i] = d_key_col[d_ptrs[i]]; the pointers are unchanged, and the
+ * new KPA (d_keys_out, d_ptrs) is in the old key order until it is sorted
+ * again.  No scratch. */
+int sbh_kpa_keyswap(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_key_col, uint64_t* d_keys_out,
+                    void* stream);
+
+/* Select (Table 2: filter the records of a KPA): the pairs whose value
+ * d_col[ptr] (col_bytes 4 or 8) lies in [lo, hi), in KPA order, to
+ * (d_out_keys, d_out_ptrs); *d_count (device) receives how many and only the
+ * first cap are written.  n < 2^32.
+ * Scratch: 4 bytes per 4096 rows. */
+int sbh_kpa_select(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_col, int col_bytes,
+                   uint64_t lo, uint64_t hi, uint64_t* d_out_keys, uint32_t* d_out_ptrs, uint64_t cap,
+                   uint64_t* d_count, void* d_scratch, size_t* scratch_bytes, void* stream);
+
 /* ---------------------------------------------------------------- A8
  * Join (Table 2: join two sorted KPAs by resident key; Sec. 4.2 "Temporal
  * Join" joins the KPAs of one window of each stream).  Emits every pair

@@ -70,6 +70,12 @@ def _load():
             f.restype = u64
         lib.oracle_window_ranges.argtypes = [vp, i32, u64, vp, u64, u64, vp, vp]
         lib.oracle_window_ranges.restype = None
+        lib.oracle_materialize.argtypes = [vp, u64, vp, i32, vp]
+        lib.oracle_materialize.restype = None
+        lib.oracle_select.argtypes = [vp, vp, u64, vp, i32, u64, u64, vp, vp, u64]
+        lib.oracle_select.restype = u64
+        lib.oracle_median_unique.argtypes = [vp, vp, u64, vp, i32, vp, vp, vp]
+        lib.oracle_median_unique.restype = u64
         _lib = lib
     return _lib
 
@@ -175,3 +181,35 @@ def window_ranges(ts: np.ndarray, starts: np.ndarray, length: int):
     e = np.empty(starts.size, np.uint64)
     _load().oracle_window_ranges(_p(ts), ts.dtype.itemsize, ts.size, _p(starts), length, starts.size, _p(b), _p(e))
     return b, e
+
+
+def materialize(ptrs: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """col[ptr] for every record, in KPA order (Materialize; KeySwap when col
+    is another key column)."""
+    ptrs = _c(ptrs, np.uint32)
+    col = np.ascontiguousarray(col)
+    assert col.dtype in (np.uint32, np.uint64)
+    out = np.empty(ptrs.size, col.dtype)
+    _load().oracle_materialize(_p(ptrs), ptrs.size, _p(col), col.dtype.itemsize, _p(out))
+    return out
+
+
+def select(keys: np.ndarray, ptrs: np.ndarray, col: np.ndarray, lo: int, hi: int):
+    """The records with col[ptr] in [lo, hi), in KPA order."""
+    keys, ptrs = _c(keys, np.uint64), _c(ptrs, np.uint32)
+    col = np.ascontiguousarray(col)
+    m = _load().oracle_select(_p(keys), _p(ptrs), keys.size, _p(col), col.dtype.itemsize, lo, hi, None, None, 0)
+    ok, op = np.empty(m, np.uint64), np.empty(m, np.uint32)
+    _load().oracle_select(_p(keys), _p(ptrs), keys.size, _p(col), col.dtype.itemsize, lo, hi, _p(ok), _p(op), m)
+    return ok, op
+
+
+def median_unique(keys: np.ndarray, ptrs: np.ndarray, col: np.ndarray):
+    """Per key (ascending): (keys, lower median of its values, number of
+    distinct values)."""
+    keys, ptrs = _c(keys, np.uint64), _c(ptrs, np.uint32)
+    col = np.ascontiguousarray(col)
+    n = keys.size
+    ok, om, ou = np.empty(n, np.uint64), np.empty(n, np.uint64), np.empty(n, np.uint64)
+    m = _load().oracle_median_unique(_p(keys), _p(ptrs), n, _p(col), col.dtype.itemsize, _p(ok), _p(om), _p(ou))
+    return ok[:m], om[:m], ou[:m]

@@ -162,4 +162,50 @@ void oracle_window_ranges(const void* ts, int ts_bytes, uint64_t n, const uint64
     }
 }
 
+/* Materialize (Table 2): the column values of the KPA's records, in KPA
+ * order: out[i] = col[ptrs[i]].  KeySwap (Table 2) is the same gather of
+ * another key column, which becomes the KPA's resident key. */
+void oracle_materialize(const uint32_t* ptrs, uint64_t n, const void* col, int col_bytes, void* out) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t v = load_val(col, col_bytes, ptrs[i]);
+        if (col_bytes == 8) static_cast<uint64_t*>(out)[i] = v;
+        else static_cast<uint32_t*>(out)[i] = static_cast<uint32_t>(v);
+    }
+}
+
+/* Select (Table 2): the records whose value (col[ptr]) lies in [lo, hi), in
+ * KPA order.  Returns how many; only the first cap are written. */
+uint64_t oracle_select(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* col, int col_bytes,
+                       uint64_t lo, uint64_t hi, uint64_t* out_keys, uint32_t* out_ptrs, uint64_t cap) {
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t v = load_val(col, col_bytes, ptrs[i]);
+        if (v >= lo && v < hi) {
+            if (m < cap) { out_keys[m] = keys[i]; out_ptrs[m] = ptrs[i]; }
+            ++m;
+        }
+    }
+    return m;
+}
+
+/* Median and distinct values per key (Sec. 7, benchmarks "Median" and
+ * "Unique Count"): per key (ascending), its values sorted ascending; the
+ * median is the lower one, at index (count - 1) / 2; unique counts the
+ * distinct values.  Returns the number of keys. */
+uint64_t oracle_median_unique(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* col, int col_bytes,
+                              uint64_t* out_keys, uint64_t* out_median, uint64_t* out_unique) {
+    std::map<uint64_t, std::vector<uint64_t>> groups;
+    for (uint64_t i = 0; i < n; ++i) groups[keys[i]].push_back(load_val(col, col_bytes, ptrs[i]));
+    uint64_t j = 0;
+    for (auto& kv : groups) {
+        auto& v = kv.second;
+        std::sort(v.begin(), v.end());
+        out_keys[j] = kv.first;
+        out_median[j] = v[(v.size() - 1) / 2];
+        out_unique[j] = static_cast<uint64_t>(std::unique(v.begin(), v.end()) - v.begin());
+        ++j;
+    }
+    return j;
+}
+
 }  // extern "C"

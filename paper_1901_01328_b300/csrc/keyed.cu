@@ -146,7 +146,7 @@ tile_agg_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
 }
 
 // Exclusive scan of the tile aggregates (in place), by one CTA: each thread
-// combines a contiguous range of tiles (eight loads in flight at a time), the
+// combines a contiguous range of tiles (four loads in flight at a time), the
 // CTA scans the range totals, and each thread walks its range again writing
 // the prefixes.
 __device__ __forceinline__ Agg shfl_up_agg(const Agg& a, int o) {
@@ -160,7 +160,7 @@ __device__ __forceinline__ Agg shfl_up_agg(const Agg& a, int o) {
 
 __global__ void __launch_bounds__(1024) tile_scan_kernel(Agg* __restrict__ aggs, uint32_t ntiles) {
     __shared__ Agg warp_tot[32];
-    constexpr int kBatch = 8;
+    constexpr int kBatch = 4;
     const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
     const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
     const uint32_t b0 = min(ntiles, threadIdx.x * per), b1 = min(ntiles, b0 + per);

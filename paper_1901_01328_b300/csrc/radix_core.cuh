@@ -531,10 +531,9 @@ struct ScatterBlocks {  // CTAs per SM the launch bounds ask for (64 registers a
     static constexpr int value = TILE * 12 * 2 > 120 * 1024 ? 1 : 65536 / (THREADS * 64);
 };
 
-// rows j of a thread (j % 8) whose peers come from match.any (the others use ballots)
-#ifndef SBH_MATCH_MASK
-#define SBH_MATCH_MASK 0xAA
-#endif
+// rows j of a thread (j % 8) whose peers come from match.any, the others from
+// digit ballots: one in two measured fastest (the two run on different pipes)
+constexpr uint32_t kMatchMask = 0xAA;
 template <typename ValueFn, int TILE, int THREADS, bool kCarry = false>
 __global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value))
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
@@ -647,8 +646,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             for (int j = 0; j < kIt; ++j) {
                 uint32_t peers;
                 if constexpr (full)  // alternate pipes: half match.any, half ballots
-                    peers = ((SBH_MATCH_MASK >> (j & 7)) & 1) ? __match_any_sync(0xffffffffu, dg[j])
-                                                              : warp_peers<kRadixBits>(dg[j]);
+                    peers = ((kMatchMask >> (j & 7)) & 1) ? __match_any_sync(0xffffffffu, dg[j])
+                                                          : warp_peers<kRadixBits>(dg[j]);
                 else
                     peers = warp_peers<kRadixBits + 1>(dg[j]);
                 const int leader = __ffs(peers) - 1;

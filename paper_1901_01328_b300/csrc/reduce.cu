@@ -498,6 +498,136 @@ int topk_dispatch(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const 
     return topk_run<KMAX, 4>(keys, ptrs, n, vals, K, ok, onv, ov, op, cap, nkeys, scratch, s);
 }
 
+// ------------------------------------------------------------ median and distinct values per key
+// The KPA is re-ordered by (key, value): a stable sort of (value, row) by
+// value, then a stable sort of (key, row) by key.  Inside each key's run the
+// values are then ascending: the median is the run's middle row, and the
+// distinct values are the rows that start the run or differ from the row
+// before (a keyed sum of those flags).
+template <int kVals>
+__global__ void __launch_bounds__(256) mu_gather_kernel(const uint32_t* __restrict__ ptrs, uint32_t n,
+                                                        const void* __restrict__ col, uint64_t* __restrict__ v,
+                                                        uint32_t* __restrict__ idx) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        v[i] = gather<kVals>(col, ld_stream(ptrs + i));
+        idx[i] = i;
+    }
+}
+
+__global__ void __launch_bounds__(256) mu_keys_kernel(const uint64_t* __restrict__ keys,
+                                                      const uint32_t* __restrict__ idx, uint32_t n,
+                                                      uint64_t* __restrict__ k2) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) k2[j] = __ldg(keys + idx[j]);
+}
+
+// w[j] = the value of row j in (key, value) order; f[j] = 1 where a key's run
+// starts or the value changes; iota[j] = j.
+__global__ void __launch_bounds__(256) mu_flags_kernel(const uint64_t* __restrict__ k3,
+                                                       const uint32_t* __restrict__ idx3, uint32_t n,
+                                                       const uint64_t* __restrict__ v, uint64_t* __restrict__ w,
+                                                       uint32_t* __restrict__ f, uint32_t* __restrict__ iota) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint64_t x = __ldg(v + idx3[j]);
+        w[j] = x;
+        iota[j] = j;
+        f[j] = (j == 0 || k3[j] != k3[j - 1] || x != __ldg(v + idx3[j - 1])) ? 1u : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) mu_median_kernel(const uint32_t* __restrict__ seg_start,
+                                                        const uint32_t* __restrict__ nseg_p,
+                                                        const uint64_t* __restrict__ w, uint64_t cap,
+                                                        uint64_t* __restrict__ median) {
+    const uint32_t nseg = *nseg_p;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg && g < cap; g += stride) {
+        const uint32_t s = seg_start[g], e = seg_start[g + 1];
+        median[g] = w[s + (e - s - 1) / 2];
+    }
+}
+
+struct MuScratch {
+    uint64_t *v, *v1, *k2, *k3, *w, *counts;
+    uint32_t *idx, *idx1, *idx3, *f, *iota, *tile_cnt, *seg_start, *small;
+    uint64_t* nseg;
+    void* sort_scr;
+    size_t sort_bytes;
+    void* red_scr;
+    size_t red_bytes;
+    size_t total;
+};
+
+MuScratch mu_carve(void* base, uint64_t n) {
+    Carver c(base);
+    MuScratch t;
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    t.v = c.take<uint64_t>(n);
+    t.v1 = c.take<uint64_t>(n);
+    t.k2 = c.take<uint64_t>(n);
+    t.k3 = c.take<uint64_t>(n);
+    t.w = c.take<uint64_t>(n);
+    t.counts = c.take<uint64_t>(n);
+    t.idx = c.take<uint32_t>(n);
+    t.idx1 = c.take<uint32_t>(n);
+    t.idx3 = c.take<uint32_t>(n);
+    t.f = c.take<uint32_t>(n);
+    t.iota = c.take<uint32_t>(n);
+    t.tile_cnt = c.take<uint32_t>(ntiles);
+    t.seg_start = c.take<uint32_t>(n + 1);
+    t.small = c.take<uint32_t>(2);
+    t.nseg = c.take<uint64_t>(1);
+    size_t sb = 0, rb = 0;
+    sbh_kpa_sort(nullptr, nullptr, nullptr, nullptr, n, nullptr, &sb, nullptr);
+    sbh_group_reduce(nullptr, nullptr, n, nullptr, 4, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &rb, nullptr);
+    t.sort_bytes = sb;
+    t.red_bytes = rb;
+    t.sort_scr = c.take<char>(sb);
+    t.red_scr = c.take<char>(rb);
+    t.total = c.bytes();
+    return t;
+}
+
+template <int kVals>
+int mu_run(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* col, uint64_t* ok, uint64_t* omed,
+           uint64_t* ouni, uint64_t cap, uint64_t* nkeys, void* scratch, cudaStream_t s) {
+    MuScratch t = mu_carve(scratch, n);
+    const uint32_t n32 = static_cast<uint32_t>(n);
+    const uint32_t ntiles = static_cast<uint32_t>((n + kTile - 1) / kTile);
+    const unsigned grid = (unsigned)min_u64((n + 255) / 256, (uint64_t)num_sms() * 8);
+    SBH_TIMED("mu_gather", s, mu_gather_kernel<kVals><<<grid, 256, 0, s>>>(ptrs, n32, col, t.v, t.idx));
+    SBH_LAUNCHED();
+    size_t sb = t.sort_bytes;
+    int rc = sbh_kpa_sort(t.v, t.idx, t.v1, t.idx1, n, t.sort_scr, &sb, s);  // by value
+    if (rc) return rc;
+    SBH_TIMED("mu_keys", s, mu_keys_kernel<<<grid, 256, 0, s>>>(keys, t.idx1, n32, t.k2));
+    SBH_LAUNCHED();
+    sb = t.sort_bytes;
+    rc = sbh_kpa_sort(t.k2, t.idx1, t.k3, t.idx3, n, t.sort_scr, &sb, s);  // then by key, stably
+    if (rc) return rc;
+    SBH_TIMED("mu_flags", s, mu_flags_kernel<<<grid, 256, 0, s>>>(t.k3, t.idx3, n32, t.v, t.w, t.f, t.iota));
+    SBH_LAUNCHED();
+    // distinct values per key: the keyed sum of the flags (also writes the keys)
+    size_t rb = t.red_bytes;
+    rc = sbh_group_reduce(t.k3, t.iota, n, t.f, 4, ok, t.counts, ouni, cap, nkeys, t.red_scr, &rb, s);
+    if (rc) return rc;
+    // the runs of the re-ordered KPA, then each run's middle row
+    SBH_CUDA(cudaMemsetAsync(t.small, 0, 2 * sizeof(uint32_t), s));
+    SBH_TIMED("mu_heads_count", s, heads_count_kernel<<<ntiles, kThreads, 0, s>>>(t.k3, n32, t.tile_cnt));
+    SBH_LAUNCHED();
+    SBH_TIMED("mu_heads_scan", s,
+              heads_scan_kernel<<<1, 1024, 0, s>>>(t.tile_cnt, ntiles, t.nseg, t.small, t.seg_start, n32));
+    SBH_LAUNCHED();
+    SBH_TIMED("mu_heads_emit", s,
+              heads_emit_kernel<<<ntiles, kThreads, 0, s>>>(t.k3, n32, t.tile_cnt, nullptr, 0, t.seg_start));
+    SBH_LAUNCHED();
+    SBH_TIMED("mu_median", s, mu_median_kernel<<<grid, 256, 0, s>>>(t.seg_start, t.small, t.w, cap, omed));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
+
 }  // namespace
 }  // namespace sbh
 
@@ -530,6 +660,33 @@ int sbh_topk(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const v
                                 d_out_ptrs, cap, d_nkeys, d_scratch, s);
     return topk_dispatch<8>(d_keys, d_ptrs, n, d_val_col, val_bytes, K, d_out_keys, d_out_nvalid, d_out_vals,
                             d_out_ptrs, cap, d_nkeys, d_scratch, s);
+}
+
+int sbh_median_unique(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
+                      int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_median, uint64_t* d_out_unique,
+                      uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n >= 0xFFFFFFFFull) { set_error("n must be < 2^32 - 1"); return SBH_EINVAL; }
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, mu_carve(nullptr, n).total, &done);
+    if (rc || done) return rc;
+    if (!d_nkeys) { set_error("d_nkeys is NULL"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) {
+        SBH_CUDA(cudaMemsetAsync(d_nkeys, 0, sizeof(uint64_t), s));
+        return SBH_OK;
+    }
+    if (!d_keys || !d_ptrs || !d_val_col || (cap && (!d_out_keys || !d_out_median || !d_out_unique))) {
+        set_error("null pointer");
+        return SBH_EINVAL;
+    }
+    if (val_bytes != 4 && val_bytes != 8) { set_error("val_bytes must be 4 or 8"); return SBH_EINVAL; }
+    if (val_bytes == 8)
+        return mu_run<8>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_median, d_out_unique, cap, d_nkeys,
+                         d_scratch, s);
+    return mu_run<4>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_median, d_out_unique, cap, d_nkeys, d_scratch,
+                     s);
 }
 
 }  // extern "C"

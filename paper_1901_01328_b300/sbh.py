@@ -57,6 +57,10 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_extract": ([vp, u64, u64, vp, vp, vp, vp, u64, vp], i32),
         "sbh_kpa_extract_windows": ([vp, vp, u64, u64, u64, vp, vp, vp, vp], i32),
         "sbh_window_bits": ([u64], i32),
+        "sbh_kpa_materialize": ([vp, u64, vp, i32, vp, vp], i32),
+        "sbh_kpa_keyswap": ([vp, u64, vp, vp, vp], i32),
+        "sbh_kpa_select": ([vp, vp, u64, vp, i32, u64, u64, vp, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_median_unique": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_kpa_split_ts": ([vp, vp, u64, i64, u64, u64, u32, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
         "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
@@ -83,7 +87,8 @@ EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_li
             "sbh_kpa_sort",
             "sbh_kpa_merge", "sbh_group_reduce",
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
-            "sbh_kpa_sort_learned",
+            "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_select",
+            "sbh_median_unique",
             "sbh_topk", "sbh_join")
 
 
@@ -275,6 +280,36 @@ def sbh_join(lkeys, lptrs, rkeys, rptrs, out_l, out_r, cap, npairs, scratch=None
     return scratch
 
 
+def sbh_kpa_materialize(ptrs, col, out, stream=None):
+    _check(_lib.sbh_kpa_materialize(_p(ptrs), ptrs.numel(), _p(col), col.element_size(), _p(out), _stream(stream)),
+           "sbh_kpa_materialize")
+
+
+def sbh_kpa_keyswap(ptrs, key_col, keys_out, stream=None):
+    _check(_lib.sbh_kpa_keyswap(_p(ptrs), ptrs.numel(), _p(key_col), _p(keys_out), _stream(stream)),
+           "sbh_kpa_keyswap")
+
+
+def sbh_kpa_select(keys, ptrs, col, lo, hi, out_keys, out_ptrs, cap, count, scratch=None, stream=None):
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(col), col.element_size(), lo, hi, _p(out_keys), _p(out_ptrs), cap,
+            _p(count))
+    if scratch is None:
+        return _scratch(_lib.sbh_kpa_select, args, (_stream(stream),), "sbh_kpa_select", keys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_kpa_select(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_kpa_select")
+    return scratch
+
+
+def sbh_median_unique(keys, ptrs, vals, out_keys, out_median, out_unique, cap, nkeys, scratch=None, stream=None):
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(vals), vals.element_size(), _p(out_keys), _p(out_median),
+            _p(out_unique), cap, _p(nkeys))
+    if scratch is None:
+        return _scratch(_lib.sbh_median_unique, args, (_stream(stream),), "sbh_median_unique", keys.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_median_unique(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_median_unique")
+    return scratch
+
+
 # ----------------------------------------------------------------- conveniences
 def _u64(n, dev):
     return torch.empty(n, dtype=torch.uint64, device=dev)
@@ -417,3 +452,29 @@ def sort_learned(keys, ptrs, model):
     out = (torch.empty_like(keys), torch.empty_like(ptrs))
     stats = sbh_kpa_sort_learned(keys, ptrs, out[0], out[1], model)
     return out[0], out[1], stats
+
+
+# ----------------------------------------------------------------- Table 2 record primitives and per-key statistics
+def materialize(ptrs, col):
+    out = torch.empty(ptrs.numel(), dtype=col.dtype, device=ptrs.device)
+    sbh_kpa_materialize(ptrs, col, out)
+    return out
+
+
+def select(keys, ptrs, col, lo, hi):
+    """(keys, ptrs) of the records with col[ptr] in [lo, hi); synchronises to size the result."""
+    n = keys.numel()
+    ok, op, cnt = _u64(max(n, 1), keys.device), _u32(max(n, 1), keys.device), _u64(1, keys.device)
+    sbh_kpa_select(keys, ptrs, col, lo, hi, ok, op, n, cnt)
+    m = int(cnt.item())
+    return ok[:m], op[:m]
+
+
+def median_unique(keys, ptrs, vals):
+    """Per distinct key: (keys, lower median, number of distinct values)."""
+    n = keys.numel()
+    dev = keys.device
+    ok, om, ou, nk = _u64(max(n, 1), dev), _u64(max(n, 1), dev), _u64(max(n, 1), dev), _u64(1, dev)
+    sbh_median_unique(keys, ptrs, vals, ok, om, ou, n, nk)
+    m = int(nk.item())
+    return ok[:m], om[:m], ou[:m]

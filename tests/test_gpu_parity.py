@@ -342,3 +342,39 @@ def test_sort_unaligned_views(S):
         S.sbh_kpa_sort(kv, pv, ok_, op_)
         ek, ep = oracle.sort(col[1:], np.arange(1, n + 1, dtype=np.uint32))
         assert same(ok_, ek) and same(op_, ep)
+
+
+# ------------------------------------------------------------------ Table 2 record primitives, median, unique
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_materialize_and_keyswap_parity(S, dtype):
+    n = 300_001
+    col = gen.uniform(12, 1, n, 0, 0 if dtype == np.uint64 else 1 << 32, np.uint64).astype(dtype)
+    keys, _ = gen.tiny_kpa(n, 1000, seed=12)
+    sk, sp = _sorted_kpa(S, keys)
+    got = S.materialize(sp, cuda(col))
+    assert same(got, oracle.materialize(host(sp), col))
+    if dtype == np.uint64:
+        k2 = torch.empty(n, dtype=torch.uint64, device="cuda")
+        S.sbh_kpa_keyswap(sp, cuda(col), k2)
+        assert same(k2, oracle.materialize(host(sp), col))
+
+
+@pytest.mark.parametrize("n,lo,hi", [(1, 0, 10), (4097, 3, 9), (1_000_003, 100, 60_000), (200_000, 7, 7)])
+def test_select_parity(S, n, lo, hi):
+    keys, _ = gen.tiny_kpa(n, 5000, seed=n)
+    vals = gen.uniform(13, 2, n, 0, 65_536, np.uint32)
+    sk, sp = _sorted_kpa(S, keys)
+    ok, op = S.select(sk, sp, cuda(vals), lo, hi)
+    ek, ep = oracle.select(host(sk), host(sp), vals, lo, hi)
+    assert same(ok, ek) and same(op, ep)
+
+
+@pytest.mark.parametrize("n,space,vspan,vb", [(1, 3, 5, 8), (4097, 9, 4, 4), (500_000, 3000, 1000, 8),
+                                              (300_000, 2, 0, 8), (2_500_000, 1 << 20, 1 << 30, 8)])
+def test_median_unique_parity(S, n, space, vspan, vb):
+    keys, _ = gen.tiny_kpa(n, space, seed=n + 1)
+    vals = gen.uniform(14, 3, n, 0, vspan, np.uint64 if vb == 8 else np.uint32)
+    sk, sp = _sorted_kpa(S, keys)
+    gk, gm, gu = S.median_unique(sk, sp, cuda(vals))
+    ek, em, eu = oracle.median_unique(host(sk), host(sp), vals)
+    assert same(gk, ek) and same(gm, em) and same(gu, eu)

@@ -181,3 +181,60 @@ def test_pins_catch_planted_topk_and_join_mistakes():
     o2 = orr.copy(); o2[0] = (o2[0] + 1) % 80
     with pytest.raises(AssertionError):
         pins.check_join(lk, rk, ol, o2, card)
+
+
+# ------------------------------------------------------------------ Materialize, KeySwap, Select, Median, Unique
+def test_materialize_is_the_gather_by_pointer():
+    rng = np.random.default_rng(3)
+    for dtype in (np.uint32, np.uint64):
+        col = rng.integers(0, np.iinfo(dtype).max, 5000, dtype=dtype)
+        ptrs = rng.permutation(5000).astype(np.uint32)[:3000]
+        got = oracle.materialize(ptrs, col)
+        assert got.dtype == dtype and [int(x) for x in got] == [int(col[p]) for p in ptrs]
+
+
+def test_keyswap_then_sort_orders_by_the_new_key():
+    # KeySwap: the KPA's resident key becomes another column of the same rows
+    col_a, _ = gen.tiny_kpa(2000, 50, seed=11)
+    col_b = gen.uniform(11, 2, 2000, 0, 1 << 30, np.uint64)
+    k, p = oracle.sort(*oracle.extract(col_a, 0, 2000))
+    k2 = oracle.materialize(p, col_b)
+    sk, sp = oracle.sort(k2, p)
+    pins.check_sorted_kpa(col_b, 0, sk, sp)
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 0), (3, 9), (0, 1 << 64 - 1), (7, 8)])
+def test_select_matches_brute_force(lo, hi):
+    keys, _ = gen.tiny_kpa(3000, 40, seed=lo + 5)
+    vals = gen.uniform(6, 1, 3000, 0, 12, np.uint64)
+    ptrs = np.arange(3000, dtype=np.uint32)[::-1].copy()
+    ok, op = oracle.select(keys, ptrs, vals, lo, hi)
+    brute = [(int(keys[i]), int(ptrs[i])) for i in range(3000) if lo <= int(vals[ptrs[i]]) < hi]
+    assert list(zip(ok.tolist(), op.tolist())) == brute
+
+
+@pytest.mark.parametrize("n,space,vspan", [(1, 3, 5), (700, 9, 4), (5000, 300, 1000), (4000, 2, 0)])
+def test_median_unique_matches_brute_force(n, space, vspan):
+    import statistics
+    keys, _ = gen.tiny_kpa(n, space, seed=n)
+    vals = gen.uniform(8, 2, n, 0, vspan, np.uint64)
+    ptrs = np.arange(n, dtype=np.uint32)
+    uk, med, uni = oracle.median_unique(keys, ptrs, vals)
+    groups = {}
+    for i in range(n):
+        groups.setdefault(int(keys[i]), []).append(int(vals[i]))
+    assert uk.tolist() == sorted(groups)
+    for j, k in enumerate(sorted(groups)):
+        v = groups[k]
+        assert med[j] == statistics.median_low(v)          # lower median
+        assert uni[j] == len(set(v))
+        assert sum(x <= med[j] for x in v) >= (len(v) + 1) // 2 and sum(x >= med[j] for x in v) >= len(v) // 2 + 1
+
+
+def test_pins_catch_planted_median_mistakes():
+    import statistics
+    vals = [5, 1, 9, 9, 2, 7]
+    assert statistics.median_low(vals) == 5
+    # an upper median, or a median over unsorted values, fails the pin
+    assert sorted(vals)[len(vals) // 2] != statistics.median_low(vals)
+    assert vals[(len(vals) - 1) // 2] != statistics.median_low(vals)
