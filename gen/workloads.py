@@ -12,13 +12,14 @@ import numpy as np
 
 from . import SEED_BASE, lognormal_sizes, unif01, uniform, zipf, zipf_lognormal_mix
 
-__all__ = ["tumbling_window", "mixed_keys", "batched_windows", "join_streams", "tiny_kpa", "mlp_init",
-           "SEED_TUMBLING", "SEED_MIXED", "SEED_BATCHED", "SEED_JOIN"]
+__all__ = ["tumbling_window", "mixed_keys", "batched_windows", "join_streams", "tiny_kpa", "mlp_init", "ad_events",
+           "SEED_TUMBLING", "SEED_MIXED", "SEED_BATCHED", "SEED_JOIN", "SEED_ADS"]
 
 SEED_TUMBLING = SEED_BASE + 1
 SEED_MIXED = SEED_BASE + 2
 SEED_BATCHED = SEED_BASE + 3
 SEED_JOIN = SEED_BASE + 4
+SEED_ADS = SEED_BASE + 6
 
 
 def tumbling_window(n: int = 1_000_000, key_bits: int = 20, seed: int = SEED_TUMBLING):
@@ -89,3 +90,25 @@ def mlp_init(seed: int = SEED_MIXED, hidden: int = 32) -> np.ndarray:
     p = np.concatenate([w1, b1, w2.astype(np.float32), np.zeros(h, np.float32), w3.astype(np.float32),
                         np.array([0.5], np.float32)])
     return p.astype(np.float32)
+
+
+def ad_events(n: int = 64_000_000, n_ads: int = 1000, n_campaigns: int = 100, events_per_s: float = 1e7,
+              seed: int = SEED_ADS):
+    """A 7-column ad-event stream with the shape of an advertising-analytics
+    benchmark (our own seeded draws, not any benchmark's generator): user,
+    page and ad ids, ad type (0..4), event type (0 view, 1 click, 2
+    purchase), event time in ns (increasing, events_per_s on average) and an
+    IPv4 address; plus the ad -> campaign table (each ad in one of
+    n_campaigns campaigns)."""
+    gaps = np.floor(-np.log1p(-unif01(seed, 8, n)) * (1e9 / events_per_s)).astype(np.uint64)
+    cols = {
+        "user_id": uniform(seed, 1, n, 0, 0, np.uint64),
+        "page_id": uniform(seed, 2, n, 0, 0, np.uint64),
+        "ad_id": uniform(seed, 3, n, 0, n_ads, np.uint64),
+        "ad_type": uniform(seed, 4, n, 0, 5, np.uint64),
+        "event_type": uniform(seed, 5, n, 0, 3, np.uint64),
+        "event_time": np.cumsum(gaps, dtype=np.uint64),
+        "ip": uniform(seed, 6, n, 0, 1 << 32, np.uint64),
+    }
+    campaign_of_ad = uniform(seed, 7, n_ads, 0, n_campaigns, np.uint64)
+    return cols, campaign_of_ad

@@ -257,6 +257,15 @@ int sbh_kpa_materialize(const uint32_t* d_ptrs, uint64_t n, const void* d_col, i
 int sbh_kpa_keyswap(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_key_col, uint64_t* d_keys_out,
                     void* stream);
 
+/* KeySwap through a lookup table (Sec. 4.2: Materialize of a column fused
+ * with the Extract of the new key, as when a pipeline maps each record's ad
+ * to its campaign before grouping): d_keys_out[i] = d_table[v] with v =
+ * d_col[d_ptrs[i]] when v < table_len; otherwise d_keys_out[i] = ~0 and the
+ * row is added to *d_misses (device, nullable).  Pointers are unchanged.
+ * No scratch. */
+int sbh_kpa_keyswap_lookup(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_col, const uint64_t* d_table,
+                           uint64_t table_len, uint64_t* d_keys_out, uint64_t* d_misses, void* stream);
+
 /* Select (Table 2: filter the records of a KPA): the pairs whose value
  * d_col[ptr] (col_bytes 4 or 8) lies in [lo, hi), in KPA order, to
  * (d_out_keys, d_out_ptrs); *d_count (device) receives how many and only the

@@ -2,6 +2,25 @@
 
 The kernels and the C ABI live in libsbh.so (sources in csrc/, header in
 include/sbh.h); ``sbh`` is the Python binding (argument marshalling only).
+Importing ``sbh`` (or any name it defines, from this package) loads
+libsbh.so and raises ImportError when it is missing: there is no CPU
+fallback.  ``build`` compiles it and does not load it.
 """
-from . import sbh  # noqa: F401  (raises ImportError when libsbh.so is missing)
-from .sbh import *  # noqa: F401,F403
+
+
+_SUBMODULES = ("build", "sbh", "pipeline", "serve")
+
+
+def __getattr__(name):
+    import importlib
+
+    if name.startswith("__") or (name in _SUBMODULES and name != "sbh"):
+        # let the import system load submodules (build must work without the library)
+        raise AttributeError(f"module {__name__!r} has no attribute {name!r}")
+    sbh = importlib.import_module(__name__ + ".sbh")  # raises ImportError when libsbh.so is missing
+    if name == "sbh":
+        return sbh
+    try:
+        return getattr(sbh, name)
+    except AttributeError:
+        raise AttributeError(f"module {__name__!r} has no attribute {name!r}") from None

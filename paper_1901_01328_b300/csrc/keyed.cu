@@ -145,6 +145,44 @@ tile_agg_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
     }
 }
 
+// Exclusive scan of the tile aggregates (in place), by one CTA, 1024 tiles
+// at a time (faster than the per-thread ranges below for many tiles).
+__global__ void __launch_bounds__(1024) tile_scan_blocked_kernel(Agg* __restrict__ aggs, uint32_t ntiles) {
+    __shared__ Agg warp_tot[32];
+    __shared__ Agg carry;
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) carry = agg_identity();
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const Agg mine = i < ntiles ? aggs[i] : agg_identity();
+        Agg inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Agg y;
+            y.heads = shfl_up_u64(inc.heads, o);
+            y.last_row = shfl_up_u64(inc.last_row, o);
+            y.sum = shfl_up_u64(inc.sum, o);
+            y.last_p = shfl_up_u64(inc.last_p, o);
+            if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
+        }
+        if (lane == 31) warp_tot[warp] = inc;
+        __syncthreads();
+        Agg before = carry;
+        for (uint32_t w = 0; w < warp; ++w) before = agg_combine(before, warp_tot[w]);
+        Agg excl;
+        excl.heads = shfl_up_u64(inc.heads, 1);
+        excl.last_row = shfl_up_u64(inc.last_row, 1);
+        excl.sum = shfl_up_u64(inc.sum, 1);
+        excl.last_p = shfl_up_u64(inc.last_p, 1);
+        if (lane == 0) excl = agg_identity();
+        if (i < ntiles) aggs[i] = agg_combine(before, excl);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = agg_combine(before, inc);
+        __syncthreads();
+    }
+}
+
 // Exclusive scan of the tile aggregates (in place), by one CTA: each thread
 // combines a contiguous range of tiles (four loads in flight at a time), the
 // CTA scans the range totals, and each thread walks its range again writing
@@ -291,7 +329,10 @@ int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const v
     SBH_TIMED("keyed_tile_agg", s,
               tile_agg_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs));
     SBH_LAUNCHED();
-    SBH_TIMED("keyed_tile_scan", s, tile_scan_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
+    if (ntiles > 4096)
+        SBH_TIMED("keyed_tile_scan", s, tile_scan_blocked_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
+    else
+        SBH_TIMED("keyed_tile_scan", s, tile_scan_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
     SBH_LAUNCHED();
     SBH_TIMED("keyed_emit", s,
               emit_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs, ntiles, ok, oc, os,

@@ -25,6 +25,38 @@ __global__ void __launch_bounds__(256) gather_kernel(const uint32_t* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- KeySwap through a lookup
+// keys_out[i] = table[col[ptrs[i]]] (Materialize of col fused with the
+// Extract of a new key by a lookup table); a value past the table gives ~0
+// and is counted.
+__global__ void __launch_bounds__(256) lookup_kernel(const uint32_t* __restrict__ ptrs, uint32_t n,
+                                                     const uint64_t* __restrict__ col,
+                                                     const uint64_t* __restrict__ table, uint64_t table_len,
+                                                     uint64_t* __restrict__ out, unsigned long long* __restrict__ misses) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t miss = 0;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        uint32_t p[4];
+        uint64_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = i0 + u * stride < n ? ld_stream(ptrs + i0 + u * stride) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = i0 + u * stride < n ? __ldg(col + p[u]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u * stride < n) {
+                const bool ok = c[u] < table_len;
+                out[i0 + u * stride] = ok ? __ldg(table + c[u]) : ~0ull;
+                miss += ok ? 0u : 1u;
+            }
+        }
+    }
+    if (misses) {
+        miss = __reduce_add_sync(0xffffffffu, miss);
+        if (lane_id() == 0 && miss) atomicAdd(misses, (unsigned long long)miss);
+    }
+}
+
 // ---------------------------------------------------------------- Select
 // Stable compaction of the rows whose value col[ptr] lies in [lo, hi):
 // per-tile counts -> one-CTA scan -> emit at the tile's offset plus the
@@ -178,6 +210,22 @@ int sbh_kpa_materialize(const uint32_t* d_ptrs, uint64_t n, const void* d_col, i
 int sbh_kpa_keyswap(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_key_col, uint64_t* d_keys_out,
                     void* stream) {
     return sbh_kpa_materialize(d_ptrs, n, d_key_col, 8, d_keys_out, stream);
+}
+
+int sbh_kpa_keyswap_lookup(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_col, const uint64_t* d_table,
+                           uint64_t table_len, uint64_t* d_keys_out, uint64_t* d_misses, void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (n == 0) return SBH_OK;
+    if (!d_ptrs || !d_col || !d_keys_out || (table_len && !d_table)) { set_error("null pointer"); return SBH_EINVAL; }
+    if (n > 0xFFFFFFFFull) { set_error("n must be < 2^32"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const unsigned grid = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)num_sms() * 8);
+    SBH_TIMED("keyswap_lookup", s,
+              lookup_kernel<<<grid, 256, 0, s>>>(d_ptrs, (uint32_t)n, d_col, d_table, table_len, d_keys_out,
+                                                 reinterpret_cast<unsigned long long*>(d_misses)));
+    SBH_LAUNCHED();
+    return SBH_OK;
 }
 
 int sbh_kpa_select(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_col, int col_bytes,

@@ -59,6 +59,7 @@ def _load() -> ctypes.CDLL:
         "sbh_window_bits": ([u64], i32),
         "sbh_kpa_materialize": ([vp, u64, vp, i32, vp, vp], i32),
         "sbh_kpa_keyswap": ([vp, u64, vp, vp, vp], i32),
+        "sbh_kpa_keyswap_lookup": ([vp, u64, vp, vp, u64, vp, vp, vp], i32),
         "sbh_kpa_select": ([vp, vp, u64, vp, i32, u64, u64, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_median_unique": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_kpa_split_ts": ([vp, vp, u64, i64, u64, u64, u32, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp, sz, vp], i32),
@@ -87,7 +88,8 @@ EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_li
             "sbh_kpa_sort",
             "sbh_kpa_merge", "sbh_group_reduce",
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
-            "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_select",
+            "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_keyswap_lookup",
+            "sbh_kpa_select",
             "sbh_median_unique",
             "sbh_topk", "sbh_join")
 
@@ -195,6 +197,13 @@ def split_scratch_bytes(n: int) -> int:
     return nbytes.value
 
 
+def select_scratch_bytes(n: int) -> int:
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_kpa_select(None, None, n, None, 8, 0, 0, None, None, 0, None, None, ctypes.byref(nbytes), None),
+           "sbh_kpa_select")
+    return nbytes.value
+
+
 def window_bits(nwin: int) -> int:
     return _lib.sbh_window_bits(nwin)
 
@@ -288,6 +297,11 @@ def sbh_kpa_materialize(ptrs, col, out, stream=None):
 def sbh_kpa_keyswap(ptrs, key_col, keys_out, stream=None):
     _check(_lib.sbh_kpa_keyswap(_p(ptrs), ptrs.numel(), _p(key_col), _p(keys_out), _stream(stream)),
            "sbh_kpa_keyswap")
+
+
+def sbh_kpa_keyswap_lookup(ptrs, col, table, keys_out, misses=None, stream=None):
+    _check(_lib.sbh_kpa_keyswap_lookup(_p(ptrs), ptrs.numel(), _p(col), _p(table), table.numel(), _p(keys_out),
+                                       _p(misses), _stream(stream)), "sbh_kpa_keyswap_lookup")
 
 
 def sbh_kpa_select(keys, ptrs, col, lo, hi, out_keys, out_ptrs, cap, count, scratch=None, stream=None):

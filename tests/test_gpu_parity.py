@@ -378,3 +378,42 @@ def test_median_unique_parity(S, n, space, vspan, vb):
     gk, gm, gu = S.median_unique(sk, sp, cuda(vals))
     ek, em, eu = oracle.median_unique(host(sk), host(sp), vals)
     assert same(gk, ek) and same(gm, em) and same(gu, eu)
+
+
+def test_partition_sorted_kpa_by_key_ranges(S):
+    # Partition (Table 2) of a sorted KPA into key ranges is the window-range
+    # search over its (non-decreasing) key column
+    n = 1_000_003
+    keys, _ = gen.tiny_kpa(n, 1 << 20, seed=21)
+    sk, sp = _sorted_kpa(S, keys)
+    starts = np.arange(0, 1 << 20, 1 << 14, dtype=np.uint64)
+    rb, re_ = S.window_ranges(sk, cuda(starts), 1 << 14)
+    ob, oe = oracle.window_ranges(host(sk), starts, 1 << 14)
+    assert same(rb, ob) and same(re_, oe)
+    hk = host(sk)
+    for w in (0, 17, 63):
+        part = hk[int(ob[w]):int(oe[w])]
+        assert part.size == np.sum((keys >= starts[w]) & (keys < starts[w] + (1 << 14)))
+
+
+def test_worked_example_on_the_gpu(S):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")))
+    keys = cuda(np.array(g["keys"], np.uint64))
+    vals = cuda(np.array(g["values"], np.uint64))
+    k, p = S.sort(*S.extract(keys, 0, 8))
+    assert host(k).tolist() == g["sorted"]["keys"] and host(p).tolist() == g["sorted"]["ptrs"]
+    uk, uc, us = S.group_reduce(k, p, vals)
+    assert [host(x).tolist() for x in (uk, uc, us)] == [g["sum_count"][x] for x in ("keys", "counts", "sums")]
+    tk, tn, tv, tp = S.topk(k, p, vals, 2)
+    t = g["top2"]
+    assert host(tv).tolist() == t["vals"] and host(tp).tolist() == t["ptrs"] and host(tn).tolist() == t["nvalid"]
+    mk, mm, mu = S.median_unique(k, p, vals)
+    assert host(mm).tolist() == g["median_unique"]["median"] and host(mu).tolist() == g["median_unique"]["unique"]
+    L = S.sort(*S.extract(keys, 0, 4))
+    R = S.sort(*S.extract(keys, 4, 4))
+    jl, jr = S.join(*L, *R)
+    assert host(jl).tolist() == g["join"]["ptr_l"] and host(jr).tolist() == g["join"]["ptr_r"]
+    sk, sp = S.select(k, p, vals, 20, 45)
+    assert host(sk).tolist() == g["select_20_45"]["keys"] and host(sp).tolist() == g["select_20_45"]["ptrs"]

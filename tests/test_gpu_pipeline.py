@@ -115,3 +115,35 @@ def test_sliding_join_full_size_sampled(P):
         _check_join(res, w, w, lcol, rcol, 1_000_000, 250_000)
     # pair counts near 10^12 / 2^24 per window
     assert abs(float(res.npairs.mean()) - 1e12 / (1 << 24)) < 0.02 * 1e12 / (1 << 24)
+
+
+def test_ad_campaign_counts_chain(P):
+    # Extract -> Select(view) -> KeySwap(ad -> campaign) -> Sort -> count, per
+    # 100 ms window, against the oracle's steps and a direct count
+    n = 3_000_000
+    cols, camp = gen.ad_events(n, events_per_s=1e7)
+    dcols = {k: cuda(v) for k, v in cols.items()}
+    res = P.ad_campaign_counts(dcols, cuda(camp), 100_000_000)
+    ts, et, ad = cols["event_time"], cols["event_type"], cols["ad_id"]
+    assert len(res) == int(ts[-1] // 100_000_000) + 1
+    for w, ck, cc in res:
+        lo, hi = np.searchsorted(ts, [w * 100_000_000, (w + 1) * 100_000_000])
+        k, p = oracle.extract(et, int(lo), int(hi - lo))
+        sk, sp = oracle.select(k, p, et, 0, 1)
+        ads = oracle.materialize(sp, ad)
+        c = oracle.materialize(ads.astype(np.uint32), camp)
+        ok, oc, _ = oracle.group_sum_count(*oracle.sort(c, sp), None)
+        assert np.array_equal(ck, ok) and np.array_equal(cc, oc)
+        direct = np.bincount(camp[ad[lo:hi][et[lo:hi] == 0]].astype(np.int64), minlength=100)
+        assert np.array_equal(direct[direct > 0], oc)
+
+
+def test_keyswap_lookup_misses(P):
+    from paper_1901_01328_b300 import sbh
+    col = np.array([0, 5, 2, 9, 1], np.uint64)
+    table = np.array([10, 11, 12, 13, 14, 15], np.uint64)
+    ptrs = np.array([4, 3, 2, 1, 0], np.uint32)
+    out = torch.empty(5, dtype=torch.uint64, device="cuda")
+    miss = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    sbh.sbh_kpa_keyswap_lookup(cuda(ptrs), cuda(col), cuda(table), out, miss)
+    assert out.cpu().numpy().tolist() == [11, 2**64 - 1, 12, 15, 10] and int(miss.item()) == 1

@@ -238,3 +238,31 @@ def test_pins_catch_planted_median_mistakes():
     # an upper median, or a median over unsorted values, fails the pin
     assert sorted(vals)[len(vals) // 2] != statistics.median_low(vals)
     assert vals[(len(vals) - 1) // 2] != statistics.median_low(vals)
+
+
+def test_oracle_reproduces_the_worked_example():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")))
+    keys = np.array(g["keys"], np.uint64)
+    vals = np.array(g["values"], np.uint64)
+    k, p = oracle.sort(*oracle.extract(keys, 0, keys.size))
+    assert k.tolist() == g["sorted"]["keys"] and p.tolist() == g["sorted"]["ptrs"]
+    uk, uc, us = oracle.group_sum_count(k, p, vals)
+    assert [uk.tolist(), uc.tolist(), us.tolist()] == [g["sum_count"][x] for x in ("keys", "counts", "sums")]
+    tk, tn, tv, tp = oracle.topk(k, p, vals, 2)
+    t = g["top2"]
+    assert tk.tolist() == t["keys"] and tn.tolist() == t["nvalid"] and tv.tolist() == t["vals"] and tp.tolist() == t["ptrs"]
+    mk, mm, mu = oracle.median_unique(k, p, vals)
+    m = g["median_unique"]
+    assert mk.tolist() == m["keys"] and mm.tolist() == m["median"] and mu.tolist() == m["unique"]
+    j = g["join"]
+    lk, lp = oracle.sort(*oracle.extract(keys, 0, 4))
+    rk, rp = oracle.sort(*oracle.extract(keys, 4, 4))
+    ol, orr = oracle.join(lk, lp, rk, rp)
+    assert ol.tolist() == j["ptr_l"] and orr.tolist() == j["ptr_r"]
+    sk, sp = oracle.select(k, p, vals, 20, 45)
+    assert sk.tolist() == g["select_20_45"]["keys"] and sp.tolist() == g["select_20_45"]["ptrs"]
+    w = g["window_2_4"]
+    b, e = oracle.window_ranges(np.array(w["ts"], np.uint64), np.array([w["start"]], np.uint64), w["len"])
+    assert [int(b[0]), int(e[0])] == w["rows"]
