@@ -45,7 +45,7 @@ CPU_SAMPLE = 4_000_000
 # dram__bytes_write.sum of one launch on the 16M-row mixed-key window).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 32.96, "sort_scatter": 24.56}
+DRAM_BYTES_PER_ROW = {"sort_scatter": 24.56}
 
 
 def _dist():
@@ -299,9 +299,11 @@ def run_gpu(args):
     algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
                   "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
                   "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
-                  "learned_ids_scatter": (PAIR_BYTES + 2) * 2 * n, "learned_ids_count": 2 * n,
+                  # per launch, the mean of the two passes: the first reads and writes the 2-byte
+                  # ids (28 B/row), the last reads them and records bucket starts (26 B/row)
+                  "learned_ids_scatter": 27 * n, "learned_ids_count": 2 * n,
                   "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
-                  "learned_bounds": 2 * n}
+                  "learned_bounds": 2 * n, "learned_bounds_fill": 0}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9

@@ -173,7 +173,7 @@ int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t*
  * ptr) order, are merged into one run in (key, ptr) order by rounds of
  * pairwise merge-path merges.  Host arrays d_run_keys[r], d_run_ptrs[r]
  * hold device pointers; run_lens[r] is a host array.  Total length < 2^32.
- * Scratch: about 12 * total bytes when nruns > 2. */
+ * Scratch: 4 bytes per 2048 output pairs, plus 24 * total bytes when nruns > 2. */
 int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const uint32_t* const* d_run_ptrs,
                   const uint64_t* run_lens, uint64_t* d_keys_out, uint32_t* d_ptrs_out, void* d_scratch,
                   size_t* scratch_bytes, void* stream);

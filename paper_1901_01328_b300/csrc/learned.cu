@@ -1006,6 +1006,7 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 // in a 16-bit array, and moved with the row through both digit passes; the
 // counts and the bucket bounds then read ids instead of recomputing them.
 constexpr int kCarryTile = 3584;
+constexpr uint32_t kMaxBucketIds = 1u << 16;  // carried ids are 16 bits
 
 // Bucket id of every row (kept as 16 bits) and the histograms of its two
 // digits.
@@ -1075,11 +1076,13 @@ __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
 }
 
-// Bucket bounds from the sorted ids (the plan tells where they ended up).
-// Each thread takes eight consecutive rows.
+// Bucket bounds from the ids when no pass ran (all ids equal; otherwise the
+// last pass recorded each id's first row).  Each thread takes eight
+// consecutive rows.
 __global__ void __launch_bounds__(256) ids_bounds_kernel(Buffers buf, const Plan* __restrict__ plan, uint32_t n,
                                                          const uint32_t* __restrict__ nbid_p,
                                                          uint32_t* __restrict__ bstart) {
+    if (plan->npasses) return;
     const uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 8;
     if (i0 >= n) return;
     const uint16_t* __restrict__ v = plan->npasses ? buf.out_v : buf.in_v;
@@ -1141,10 +1144,46 @@ CarryScratch carry_carve(void* base, uint64_t n) {
     return t;
 }
 
+// After the passes: bstart[b] = the first row of an id >= b (suffix minimum
+// of the recorded first rows; bstart[nbid] = n).  One CTA: each thread a
+// contiguous range, backwards.
+__global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restrict__ plan, uint32_t n,
+                                                           const uint32_t* __restrict__ nbid_p,
+                                                           uint32_t* __restrict__ bstart) {
+    if (!plan->npasses) return;
+    __shared__ uint32_t wmin[32];
+    const uint32_t nbid = *nbid_p;
+    const uint32_t tot = nbid + 1;
+    const uint32_t per = (tot + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = min(tot, threadIdx.x * per), b1 = min(tot, b0 + per);
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    uint32_t m = 0xFFFFFFFFu;
+    for (uint32_t b = b0; b < b1; ++b) m = min(m, b == nbid ? n : bstart[b]);
+    // minimum over the ranges of all later threads
+    uint32_t x = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
+        if (lane + o < 32) x = min(x, y);
+    }
+    if (lane == 0) wmin[warp] = x;
+    __syncthreads();
+    uint32_t after = 0xFFFFFFFFu;
+    for (uint32_t w = warp + 1; w < blockDim.x / 32; ++w) after = min(after, wmin[w]);
+    const uint32_t nxt = __shfl_down_sync(0xffffffffu, x, 1);
+    if (lane < 31) after = min(after, nxt);
+    __syncthreads();
+    for (uint32_t b = b1; b-- > b0;) {
+        const uint32_t v = b == nbid ? n : min(bstart[b], after);
+        bstart[b] = v;
+        after = v;
+    }
+}
+
 // The two passes by carried bucket id: per pass, chunk counts of the id
 // digit -> chunk offsets -> scatter carrying the ids along.
 template <int TILE, int THREADS>
-int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaStream_t s) {
+int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaStream_t s, uint32_t* first_row) {
     ChunkGeom g;
     const int rc = chunk_geometry<RadixValue, TILE, THREADS, true>(n32, &g);
     if (rc) return rc;
@@ -1160,7 +1199,7 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaS
         SBH_TIMED("learned_ids_scatter", s,
                   (chunk_scatter_kernel<RadixValue, TILE, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
                       b, n32, pos, cs.plan, g.chunk, cs.chunk_base, RadixValue{}, bulk_ok, spin_limit(),
-                      status_word())));
+                      status_word(), first_row)));
         SBH_LAUNCHED();
     }
     return SBH_OK;
@@ -1182,13 +1221,18 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     b.in_v = cs.ids_in;
     b.tmp_v = cs.ids_tmp;
     b.out_v = cs.ids_out;
-    const int rc = carried_passes<kCarryTile, 512>(b, n32, cs, s);
+    // bucket starts: the last pass records each id's first output row, then a
+    // suffix minimum fills the empty buckets (with no pass, read the ids)
+    SBH_CUDA(cudaMemsetAsync(bstart, 0xFF, (kMaxBucketIds + 1) * sizeof(uint32_t), s));
+    const int rc = carried_passes<kCarryTile, 512>(b, n32, cs, s, bstart);
     if (rc) return rc;
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds", s,
               ids_bounds_kernel<<<(unsigned)((n + 2047) / 2048), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_bounds_fill", s, bounds_fill_kernel<<<1, 1024, 0, s>>>(cs.plan, n32, nbid, bstart));
     SBH_LAUNCHED();
     return SBH_OK;
 }

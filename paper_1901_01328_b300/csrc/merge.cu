@@ -1,9 +1,11 @@
 // A5 Merge: merge-path merge of sorted KPAs in (key, ptr) order.
 //
-// Two runs A and B are merged by output tiles of 2048 pairs.  Each CTA finds
-// where its first and last output diagonal cut A and B (binary search on the
-// merge path), stages the two slices in shared memory, and each thread merges
-// 8 outputs from its own co-rank.  More than two runs are merged in rounds of
+// Two runs A and B are merged by output tiles of 2048 pairs.  For large
+// merges one small kernel first finds where every tile's first output
+// diagonal cuts A and B (a binary search on the merge path per tile, all
+// tiles in parallel; small merges let each CTA search its own); each CTA of
+// the merge then stages its two slices in shared memory, and each thread
+// merges 8 outputs from its own co-rank.  More than two runs are merged in rounds of
 // pairwise merges through a scratch ping-pong buffer.
 #include <vector>
 
@@ -15,6 +17,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kIpt = 8;
 constexpr int kTile = kThreads * kIpt;
+constexpr uint32_t kOwnCutsMaxTiles = 1024;  // up to 2M outputs each CTA finds its own cuts
 
 __device__ __forceinline__ bool kp_less(uint64_t ka, uint32_t pa, uint64_t kb, uint32_t pb) {
     return ka < kb || (ka == kb && pa < pb);
@@ -35,19 +38,32 @@ __device__ __forceinline__ uint32_t corank(uint32_t d, const KA ak, const PA ap,
     return lo;
 }
 
+// cuts[t] = co-rank of diagonal min(t * kTile, na + nb), t <= ntiles.
+__global__ void __launch_bounds__(256)
+merge_cuts_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ap, uint32_t na,
+                  const uint64_t* __restrict__ bk, const uint32_t* __restrict__ bp, uint32_t nb, uint32_t ntiles,
+                  uint32_t* __restrict__ cuts) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const uint32_t d = (uint32_t)min_u64((uint64_t)t * kTile, (uint64_t)na + nb);
+    cuts[t] = corank(d, ak, ap, na, bk, bp, nb);
+}
+
 __global__ void __launch_bounds__(kThreads)
 merge_pair_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ap, uint32_t na,
                   const uint64_t* __restrict__ bk, const uint32_t* __restrict__ bp, uint32_t nb,
-                  uint64_t* __restrict__ ok, uint32_t* __restrict__ op) {
+                  const uint32_t* __restrict__ cuts, uint64_t* __restrict__ ok, uint32_t* __restrict__ op) {
     __shared__ uint64_t sk[kTile];
     __shared__ uint32_t sp[kTile];
     __shared__ uint32_t cut[2];
     const uint32_t total = na + nb;
     const uint32_t d0 = blockIdx.x * kTile;
     const uint32_t d1 = min(d0 + kTile, total);
-    if (threadIdx.x < 2) cut[threadIdx.x] = corank(threadIdx.x ? d1 : d0, ak, ap, na, bk, bp, nb);
-    __syncthreads();
-    const uint32_t a0 = cut[0], a1 = cut[1];
+    if (!cuts) {  // small merges find their own cuts (one launch fewer)
+        if (threadIdx.x < 2) cut[threadIdx.x] = corank(threadIdx.x ? d1 : d0, ak, ap, na, bk, bp, nb);
+        __syncthreads();
+    }
+    const uint32_t a0 = cuts ? cuts[blockIdx.x] : cut[0], a1 = cuts ? cuts[blockIdx.x + 1] : cut[1];
     const uint32_t b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = a1 - a0, lb = b1 - b0, len = d1 - d0;
     // stage A slice then B slice
@@ -105,11 +121,21 @@ struct Run {
     uint64_t n;
 };
 
-int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, cudaStream_t s) {
+int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, uint32_t* cuts, cudaStream_t s) {
     const uint64_t total = a.n + b.n;
     if (total == 0) return SBH_OK;
-    const unsigned grid = (unsigned)((total + kTile - 1) / kTile);
-    SBH_TIMED("merge_path", s, merge_pair_kernel<<<grid, kThreads, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p, (uint32_t)b.n, ok, op));
+    const uint32_t ntiles = (uint32_t)((total + kTile - 1) / kTile);
+    if (ntiles > kOwnCutsMaxTiles) {
+        SBH_TIMED("merge_cuts", s,
+                  merge_cuts_kernel<<<(ntiles + 256) / 256, 256, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p,
+                                                                       (uint32_t)b.n, ntiles, cuts));
+        SBH_LAUNCHED();
+    } else {
+        cuts = nullptr;
+    }
+    SBH_TIMED("merge_path", s,
+              merge_pair_kernel<<<ntiles, kThreads, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p, (uint32_t)b.n, cuts,
+                                                            ok, op));
     SBH_LAUNCHED();
     return SBH_OK;
 }
@@ -138,6 +164,7 @@ extern "C" int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const
     for (int r = 0; r < nruns; ++r) total += run_lens[r];
     if (total > 0xFFFFFFFFull) { set_error("total length must be < 2^32"); return SBH_EINVAL; }
     Carver c(nullptr);
+    c.take<uint32_t>(total / kTile + 2);  // tile cuts
     if (nruns > 2) { c.take<uint64_t>(total); c.take<uint32_t>(total); c.take<uint64_t>(total); c.take<uint32_t>(total); }
     bool done = false;
     int rc = scratch_check(d_scratch, scratch_bytes, c.bytes(), &done);
@@ -150,11 +177,12 @@ extern "C" int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const
     std::vector<Run> runs;
     for (int r = 0; r < nruns; ++r)
         if (run_lens[r]) runs.push_back({d_run_keys[r], d_run_ptrs[r], run_lens[r]});
+    Carver w(d_scratch);
+    uint32_t* cuts = w.take<uint32_t>(total / kTile + 2);
     if (runs.size() == 1) return copy_run(runs[0], d_keys_out, d_ptrs_out, s);
-    if (runs.size() == 2) return merge_two(runs[0], runs[1], d_keys_out, d_ptrs_out, s);
+    if (runs.size() == 2) return merge_two(runs[0], runs[1], d_keys_out, d_ptrs_out, cuts, s);
     // rounds of pairwise merges; each round writes one of two scratch buffers,
     // the last round writes the output
-    Carver w(d_scratch);
     uint64_t* bk[2];
     uint32_t* bp[2];
     bk[0] = w.take<uint64_t>(total);
@@ -169,7 +197,7 @@ extern "C" int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const
         std::vector<Run> next;
         uint64_t off = 0;
         for (size_t r = 0; r + 1 < runs.size(); r += 2) {
-            rc = merge_two(runs[r], runs[r + 1], ok + off, op + off, s);
+            rc = merge_two(runs[r], runs[r + 1], ok + off, op + off, cuts, s);
             if (rc) return rc;
             next.push_back({ok + off, op + off, runs[r].n + runs[r + 1].n});
             off += runs[r].n + runs[r + 1].n;

@@ -538,7 +538,7 @@ template <typename ValueFn, int TILE, int THREADS, bool kCarry = false>
 __global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value))
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
-                     uint32_t* __restrict__ status) {
+                     uint32_t* __restrict__ status, uint32_t* __restrict__ first_row = nullptr) {
     constexpr bool kDig = ScatterDig<ValueFn, kCarry>::value;
     using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig>;
     constexpr int kW = Smem::kW, kG = Smem::kG, kWpg = kW / kG;
@@ -555,6 +555,12 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     uint32_t* __restrict__ out_p = buf.wptrs(dst);
     const uint16_t* __restrict__ in_v = kCarry ? buf.vals(src) : nullptr;
     uint16_t* __restrict__ out_v = kCarry ? buf.wvals(dst) : nullptr;
+    // Carried 16-bit values, last of the two passes, first_row given: the
+    // values are not written out; instead every value's first output row is
+    // recorded (atomicMin into first_row[value]).  A staged tile of the last
+    // pass is in value order, so a row whose value differs from the staged
+    // row before it is the first of its value in this tile.
+    const bool rows_pass = kCarry && first_row != nullptr && (pos == 1 || !plan->active[1]);
     const uint32_t lo = blockIdx.x * chunk;
     const uint32_t hi = min(n, lo + chunk);
     if (lo >= hi) return;
@@ -749,7 +755,14 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                         const uint32_t g = sm.gbase_rel[d] + s;
                         out_k[g] = key;
                         out_p[g] = pb[s];
-                        if (kCarry) out_v[g] = vb[s];
+                        if (kCarry) {
+                            if (rows_pass) {
+                                const uint16_t v = vb[s];
+                                if (s == 0 || vb[s - 1] != v) atomicMin(first_row + v, g);
+                            } else {
+                                out_v[g] = vb[s];
+                            }
+                        }
                     }
                 }
             }
