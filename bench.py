@@ -42,10 +42,11 @@ METRIC = "records/s grouped"
 UNIT = "records/s"
 CPU_SAMPLE = 4_000_000
 # DRAM bytes per row of one launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch on the 16M-row mixed-key window).
+# dram__bytes_write.sum on the 16M-row mixed-key window; for the carried-id
+# scatter the mean of its two passes).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"sort_scatter": 24.56}
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 28.15, "sort_scatter": 24.57}
 
 
 def _dist():
@@ -303,7 +304,7 @@ def run_gpu(args):
                   # ids (28 B/row), the last reads them and records bucket starts (26 B/row)
                   "learned_ids_scatter": 27 * n, "learned_ids_count": 2 * n,
                   "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
-                  "learned_bounds": 2 * n, "learned_bounds_fill": 0}
+                  "learned_bounds": 2 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9
