@@ -83,6 +83,24 @@ void sbh_set_fault(int fault);
  * (names + i * name_len, NUL-terminated, truncated to name_len - 1 bytes) and
  * its duration in milliseconds (ms[i]); either buffer may be NULL.  It
  * returns the number of records. */
+/* Tuning knobs, process-wide, read by every later call (the autotuner in
+ * the Python package measures and sets them; the defaults are measured on
+ * B300):
+ *   SBH_KNOB_SORT_CHUNKED_MIN        sorts of at least this many pairs take
+ *                                    per-chunk count / scan / scatter passes,
+ *                                    smaller ones one onesweep kernel a pass
+ *                                    (default 2^21);
+ *   SBH_KNOB_MERGE_SEARCH_MIN_TILES  merges of more than this many 2048-row
+ *                                    output tiles find the tiles' cuts in a
+ *                                    separate parallel search (default 1024).
+ * A sort's scratch size depends on the first knob: size it after setting.
+ * sbh_set_knob returns SBH_EINVAL for an unknown knob; sbh_get_knob 0. */
+#define SBH_KNOB_SORT_CHUNKED_MIN 0
+#define SBH_KNOB_MERGE_SEARCH_MIN_TILES 1
+#define SBH_KNOB_COUNT 2
+int sbh_set_knob(int knob, uint64_t value);
+uint64_t sbh_get_knob(int knob);
+
 void sbh_profile_enable(int on);
 int sbh_profile_collect(int max_records, char* names, int name_len, double* ms);
 

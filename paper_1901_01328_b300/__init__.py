@@ -8,7 +8,7 @@ fallback.  ``build`` compiles it and does not load it.
 """
 
 
-_SUBMODULES = ("build", "sbh", "pipeline", "serve")
+_SUBMODULES = ("build", "sbh", "pipeline", "serve", "autotune")
 
 
 def __getattr__(name):

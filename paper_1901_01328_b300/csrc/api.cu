@@ -23,6 +23,9 @@ int g_sms[kMaxDevices] = {0};
 
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;  // a few seconds of polls
 std::atomic<uint32_t> g_spin_limit{kDefaultSpinLimit};
+// tuning knobs (sbh_set_knob): the sorts' chunked-pass threshold and the
+// merges' separate cut-search threshold
+std::atomic<uint64_t> g_knob[SBH_KNOB_COUNT] = {{1ull << 21}, {1024}};
 std::atomic<int> g_fault{SBH_FAULT_NONE};
 
 struct ProfRecord {
@@ -66,6 +69,8 @@ uint32_t* status_word() {
 
 uint32_t spin_limit() { return g_spin_limit.load(); }
 
+uint64_t knob(int k) { return (k >= 0 && k < SBH_KNOB_COUNT) ? g_knob[k].load() : 0; }
+
 int take_fault() { return g_fault.exchange(SBH_FAULT_NONE); }
 
 int num_sms() {
@@ -101,6 +106,16 @@ ProfScope::~ProfScope() {
 }  // namespace sbh
 
 extern "C" {
+
+int sbh_set_knob(int k, uint64_t value) {
+    using namespace sbh;
+    clear_error();
+    if (k < 0 || k >= SBH_KNOB_COUNT) { set_error("unknown knob %d", k); return SBH_EINVAL; }
+    g_knob[k].store(value);
+    return SBH_OK;
+}
+
+uint64_t sbh_get_knob(int k) { return sbh::knob(k); }
 
 void sbh_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

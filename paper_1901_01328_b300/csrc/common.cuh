@@ -24,6 +24,8 @@ uint32_t spin_limit();
 int take_fault();
 // Number of SMs of the current device.
 int num_sms();
+// Current value of a tuning knob (SBH_KNOB_*).
+uint64_t knob(int k);
 
 // Optional per-launch timing (sbh_profile_enable): a scope records a CUDA
 // event pair around the launches it encloses, on their stream.

@@ -17,7 +17,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kIpt = 8;
 constexpr int kTile = kThreads * kIpt;
-constexpr uint32_t kOwnCutsMaxTiles = 1024;  // up to 2M outputs each CTA finds its own cuts
 
 __device__ __forceinline__ bool kp_less(uint64_t ka, uint32_t pa, uint64_t kb, uint32_t pb) {
     return ka < kb || (ka == kb && pa < pb);
@@ -125,7 +124,7 @@ int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, uint32_t* 
     const uint64_t total = a.n + b.n;
     if (total == 0) return SBH_OK;
     const uint32_t ntiles = (uint32_t)((total + kTile - 1) / kTile);
-    if (ntiles > kOwnCutsMaxTiles) {
+    if (ntiles > knob(SBH_KNOB_MERGE_SEARCH_MIN_TILES)) {  // default 1024 tiles (2M outputs)
         SBH_TIMED("merge_cuts", s,
                   merge_cuts_kernel<<<(ntiles + 256) / 256, 256, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p,
                                                                        (uint32_t)b.n, ntiles, cuts));

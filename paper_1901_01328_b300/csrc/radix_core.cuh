@@ -420,7 +420,9 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 
 // ------------------------------------------------------------------ chunked passes
 constexpr uint32_t kMaxChunks = 1024;
-constexpr uint64_t kChunkedMinRows = 1u << 21;  // below this the onesweep kernel is used
+// sorts of at least knob(SBH_KNOB_SORT_CHUNKED_MIN) pairs (default 2^21) take
+// the chunked passes, smaller ones the onesweep kernel
+inline bool use_chunked(uint64_t n) { return n >= knob(SBH_KNOB_SORT_CHUNKED_MIN); }
 
 // Digit histogram of each chunk.
 template <typename ValueFn>
@@ -819,7 +821,7 @@ struct SortScratch {
 inline SortScratch sort_carve(void* scratch, uint64_t n) {
     Carver c(scratch);
     SortScratch s;
-    const bool chunked = n >= kChunkedMinRows;
+    const bool chunked = use_chunked(n);
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     s.tmp_k = c.take<uint64_t>(n);
     s.tmp_p = c.take<uint32_t>(n);
@@ -896,7 +898,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
-    if (n >= kChunkedMinRows) {
+    if (use_chunked(n)) {
         const int rc = chunked_passes<ValueFn, 4096, 512>(b, n32, sc, value_of, bulk_ok, s, n_count, n_scan, n_scat);
         if (rc) return rc;
     } else {

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libsbh.so")
 
 SBH_OK, SBH_EINVAL, SBH_ENOSPACE, SBH_ETIMEOUT, SBH_ECUDA = 0, 1, 2, 3, 4
 SBH_FAULT_NONE, SBH_FAULT_SKIP_PUBLISH = 0, 1
+KNOB_SORT_CHUNKED_MIN, KNOB_MERGE_SEARCH_MIN_TILES = 0, 1
 TOPK_PAD_VAL = 0
 TOPK_PAD_PTR = 0xFFFFFFFF
 TOPK_MAX_K = 8
@@ -51,6 +52,8 @@ def _load() -> ctypes.CDLL:
         "sbh_sync_status": ([vp], i32),
         "sbh_set_spin_limit": ([u32], None),
         "sbh_set_fault": ([i32], None),
+        "sbh_set_knob": ([i32, u64], i32),
+        "sbh_get_knob": ([i32], u64),
         "sbh_profile_enable": ([i32], None),
         "sbh_profile_collect": ([i32, vp, i32, vp], i32),
         "sbh_window_ranges": ([vp, i32, u64, vp, u64, u64, vp, vp, vp], i32),
@@ -83,6 +86,7 @@ def _load() -> ctypes.CDLL:
 
 _lib = _load()
 EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_limit", "sbh_set_fault",
+            "sbh_set_knob", "sbh_get_knob",
             "sbh_profile_enable", "sbh_profile_collect",
             "sbh_window_ranges", "sbh_kpa_extract", "sbh_kpa_extract_windows", "sbh_window_bits", "sbh_kpa_split_ts",
             "sbh_kpa_sort",
@@ -139,6 +143,14 @@ def set_spin_limit(polls: int):
 
 def set_fault(fault: int):
     _lib.sbh_set_fault(fault)
+
+
+def set_knob(knob: int, value: int):
+    _check(_lib.sbh_set_knob(knob, value), "sbh_set_knob")
+
+
+def get_knob(knob: int) -> int:
+    return _lib.sbh_get_knob(knob)
 
 
 def profile_enable(on: bool = True):
