@@ -89,10 +89,10 @@ void sbh_set_fault(int fault);
  *   SBH_KNOB_SORT_CHUNKED_MIN        sorts of at least this many pairs take
  *                                    per-chunk count / scan / scatter passes,
  *                                    smaller ones one onesweep kernel a pass
- *                                    (default 2^21);
+ *                                    (default 2^23);
  *   SBH_KNOB_MERGE_SEARCH_MIN_TILES  merges of more than this many 2048-row
  *                                    output tiles find the tiles' cuts in a
- *                                    separate parallel search (default 1024).
+ *                                    separate parallel search (default 2047).
  * A sort's scratch size depends on the first knob: size it after setting.
  * sbh_set_knob returns SBH_EINVAL for an unknown knob; sbh_get_knob 0. */
 #define SBH_KNOB_SORT_CHUNKED_MIN 0
@@ -171,9 +171,9 @@ int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n,
  * Sort (Table 2: order a KPA by its resident key).  Stable LSD radix sort,
  * 8-bit digits, one pass per digit position whose digit is not the same for
  * all keys (the histogram of every position is built in one read).  Below
- * 2^21 pairs each pass is one onesweep kernel: tile load, warp multisplit
+ * 2^23 pairs (SBH_KNOB_SORT_CHUNKED_MIN) each pass is one onesweep kernel: tile load, warp multisplit
  * ranking, decoupled look-back for the tile's global digit offsets, scatter
- * staged through shared memory.  From 2^21 pairs each pass is three kernels:
+ * staged through shared memory.  From 2^23 pairs each pass is three kernels:
  * per-chunk digit counts, their scan, and a scatter in which every CTA walks
  * its own chunk of tiles (bulk-copied, ranked, staged) with its digit offsets
  * known up front.  Because the sort is stable and ties keep their input

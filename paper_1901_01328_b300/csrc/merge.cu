@@ -124,7 +124,7 @@ int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, uint32_t* 
     const uint64_t total = a.n + b.n;
     if (total == 0) return SBH_OK;
     const uint32_t ntiles = (uint32_t)((total + kTile - 1) / kTile);
-    if (ntiles > knob(SBH_KNOB_MERGE_SEARCH_MIN_TILES)) {  // default 1024 tiles (2M outputs)
+    if (ntiles > knob(SBH_KNOB_MERGE_SEARCH_MIN_TILES)) {  // default 2047 tiles (4M outputs)
         SBH_TIMED("merge_cuts", s,
                   merge_cuts_kernel<<<(ntiles + 256) / 256, 256, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p,
                                                                        (uint32_t)b.n, ntiles, cuts));

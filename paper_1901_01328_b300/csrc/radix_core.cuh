@@ -420,7 +420,7 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 
 // ------------------------------------------------------------------ chunked passes
 constexpr uint32_t kMaxChunks = 1024;
-// sorts of at least knob(SBH_KNOB_SORT_CHUNKED_MIN) pairs (default 2^21) take
+// sorts of at least knob(SBH_KNOB_SORT_CHUNKED_MIN) pairs (default 2^23) take
 // the chunked passes, smaller ones the onesweep kernel
 inline bool use_chunked(uint64_t n) { return n >= knob(SBH_KNOB_SORT_CHUNKED_MIN); }
 

@@ -80,11 +80,11 @@ def test_window_bits_and_batched_extract_arguments(L):
 
 
 def test_knobs_set_and_get_without_a_gpu(L):
-    assert L.get_knob(L.KNOB_SORT_CHUNKED_MIN) == 1 << 21
-    assert L.get_knob(L.KNOB_MERGE_SEARCH_MIN_TILES) == 1024
+    assert L.get_knob(L.KNOB_SORT_CHUNKED_MIN) == 1 << 23
+    assert L.get_knob(L.KNOB_MERGE_SEARCH_MIN_TILES) == 2047
     L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 12345)
     assert L.get_knob(L.KNOB_SORT_CHUNKED_MIN) == 12345
-    L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 1 << 21)
+    L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 1 << 23)
     lib = L.lib()
     assert lib.sbh_set_knob(7, 1) == L.SBH_EINVAL and lib.sbh_get_knob(7) == 0
     # the sort's scratch depends on the path the knob picks
@@ -93,5 +93,5 @@ def test_knobs_set_and_get_without_a_gpu(L):
     assert lib.sbh_kpa_sort(None, None, None, None, 1 << 22, None, ctypes.byref(nb_small), None) == 0
     L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 0)         # chunked: chunk tables
     assert lib.sbh_kpa_sort(None, None, None, None, 1 << 22, None, ctypes.byref(nb_large), None) == 0
-    L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 1 << 21)
+    L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 1 << 23)
     assert nb_small.value != nb_large.value

@@ -18,8 +18,8 @@ def A():
         pytest.skip("no CUDA device")
     from paper_1901_01328_b300 import autotune, sbh
     yield autotune
-    sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 21)
-    sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, 1024)
+    sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 23)
+    sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, 2047)
 
 
 def test_tuning_sets_knobs_from_measurements(A, tmp_path):
@@ -54,8 +54,8 @@ def test_both_sort_paths_and_both_merge_searches_are_exact(A, thr):
         mk, mp = sbh.merge([a, b])
         assert same(mk, ok) and same(mp, op)
     finally:
-        sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 21)
-        sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, 1024)
+        sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 23)
+        sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, 2047)
 
 
 def test_batched_schedule_choice(A):

@@ -320,8 +320,17 @@ def test_window_ranges_parity(S):
     assert same(rb, ob) and same(re_, oe)
 
 
+@pytest.fixture
+def chunked_from_2m(S):
+    """Sorts from 2^21 pairs take the per-chunk count/scan/scatter passes."""
+    old = S.get_knob(S.KNOB_SORT_CHUNKED_MIN)
+    S.set_knob(S.KNOB_SORT_CHUNKED_MIN, 1 << 21)
+    yield
+    S.set_knob(S.KNOB_SORT_CHUNKED_MIN, old)
+
+
 @pytest.mark.parametrize("kind", ["uniform20", "mixed", "highbyte", "extremes"])
-def test_sort_chunked_path_ragged(S, kind):
+def test_sort_chunked_path_ragged(S, kind, chunked_from_2m):
     # above the size where passes switch to per-chunk count/scan/scatter,
     # with a ragged last tile
     n = (1 << 21) + 4097
@@ -332,8 +341,17 @@ def test_sort_chunked_path_ragged(S, kind):
     assert same(sk, ok) and same(sp, op)
 
 
-def test_sort_unaligned_views(S):
-    # views that start 8 bytes into a buffer cannot use bulk copies
+def test_sort_chunked_path_default_threshold(S):
+    # just above the default threshold (2^23 pairs), mixed keys
+    n = (1 << 23) + 3
+    col = gen.mixed_keys(n, seed=8)
+    sk, sp = S.sort(*S.extract(cuda(col), 0, n))
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_sort_unaligned_views(S, chunked_from_2m):
+    # views that start 8 bytes into a buffer cannot use bulk copies (both paths)
     for n in (50_001, (1 << 21) + 11):
         col = gen.mixed_keys(n + 1, seed=6)
         keys, ptrs = S.extract(cuda(col), 0, n + 1)
