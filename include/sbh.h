@@ -220,8 +220,8 @@ int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n,
  * interface of this library.
  * Arguments and results are those of sbh_group_reduce; n is at most 2^28
  * rows, and a larger n returns SBH_EINVAL without launching.  Its working
- * memory is one fixed 2 MiB device array, which every GPU that loads the
- * library holds until the process exits; the call allocates and frees
+ * memory is one fixed device array of just over 2 MiB, which every GPU that
+ * loads the library holds until the process exits; the call allocates and frees
  * nothing.  The first call on a device looks up that array's device address
  * (once per device, with that device current), so make that first call
  * before any stream capture.  All calls on a device share the array and it

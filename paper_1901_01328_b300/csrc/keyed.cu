@@ -8,10 +8,11 @@
 // exactly, modulo 2^64.  So the reduction needs only a plain prefix sum of the
 // gathered values and the position of the last head -- no segmented scan.
 //
-// Three launches, no waits between CTAs (reduce, then scan):
+// Three launches (five above 4096 tiles), no waits between CTAs:
 //   tile_agg   per tile of 4096 rows: heads, total, last head row, and the
 //              prefix at the last head;
-//   tile_scan  one CTA scans the tile aggregates into tile prefixes;
+//   tile_scan  scans the tile aggregates into tile prefixes (one CTA; above
+//              4096 tiles, block totals up, one CTA over those, then add);
 //   emit       per tile again: each head writes its key, and the previous
 //              run's count and sum, at output index = number of heads before.
 // Rows are read warp-striped straight from global memory (coalesced), so the
@@ -145,44 +146,6 @@ tile_agg_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
     }
 }
 
-// Exclusive scan of the tile aggregates (in place), by one CTA, 1024 tiles
-// at a time (faster than the per-thread ranges below for many tiles).
-__global__ void __launch_bounds__(1024) tile_scan_blocked_kernel(Agg* __restrict__ aggs, uint32_t ntiles) {
-    __shared__ Agg warp_tot[32];
-    __shared__ Agg carry;
-    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
-    if (threadIdx.x == 0) carry = agg_identity();
-    __syncthreads();
-    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
-        const uint32_t i = c0 + threadIdx.x;
-        const Agg mine = i < ntiles ? aggs[i] : agg_identity();
-        Agg inc = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Agg y;
-            y.heads = shfl_up_u64(inc.heads, o);
-            y.last_row = shfl_up_u64(inc.last_row, o);
-            y.sum = shfl_up_u64(inc.sum, o);
-            y.last_p = shfl_up_u64(inc.last_p, o);
-            if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
-        }
-        if (lane == 31) warp_tot[warp] = inc;
-        __syncthreads();
-        Agg before = carry;
-        for (uint32_t w = 0; w < warp; ++w) before = agg_combine(before, warp_tot[w]);
-        Agg excl;
-        excl.heads = shfl_up_u64(inc.heads, 1);
-        excl.last_row = shfl_up_u64(inc.last_row, 1);
-        excl.sum = shfl_up_u64(inc.sum, 1);
-        excl.last_p = shfl_up_u64(inc.last_p, 1);
-        if (lane == 0) excl = agg_identity();
-        if (i < ntiles) aggs[i] = agg_combine(before, excl);
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = agg_combine(before, inc);
-        __syncthreads();
-    }
-}
-
 // Exclusive scan of the tile aggregates (in place), by one CTA: each thread
 // combines a contiguous range of tiles (four loads in flight at a time), the
 // CTA scans the range totals, and each thread walks its range again writing
@@ -235,6 +198,47 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(Agg* __restrict__ aggs,
             }
         }
     }
+}
+
+// Many tiles: the scan runs over blocks of 1024 tile aggregates in three
+// launches.  tile_scan_up writes each block's total, tile_scan_kernel scans
+// the block totals (one CTA; at most 1024 of them), and tile_scan_add scans
+// each block's aggregates in place from its block prefix.
+__device__ __forceinline__ Agg cta_scan(const Agg& mine, Agg (&warp_tot)[32], Agg& incl) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    Agg inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Agg y = shfl_up_agg(inc, o);
+        if (lane >= (uint32_t)o) inc = agg_combine(y, inc);
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    Agg before = agg_identity();
+    for (uint32_t w = 0; w < warp; ++w) before = agg_combine(before, warp_tot[w]);
+    Agg excl = shfl_up_agg(inc, 1);
+    if (lane == 0) excl = agg_identity();
+    incl = agg_combine(before, inc);
+    return agg_combine(before, excl);
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_up_kernel(const Agg* __restrict__ aggs, uint32_t ntiles,
+                                                            Agg* __restrict__ btot) {
+    __shared__ Agg warp_tot[32];
+    const uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+    Agg incl;
+    cta_scan(i < ntiles ? aggs[i] : agg_identity(), warp_tot, incl);
+    if (threadIdx.x == 1023) btot[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_add_kernel(Agg* __restrict__ aggs, uint32_t ntiles,
+                                                             const Agg* __restrict__ bpre) {
+    __shared__ Agg warp_tot[32];
+    const uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+    const Agg mine = i < ntiles ? aggs[i] : agg_identity();
+    Agg incl;
+    const Agg excl = cta_scan(mine, warp_tot, incl);
+    if (i < ntiles) aggs[i] = agg_combine(bpre[blockIdx.x], excl);
 }
 
 template <int kVals>
@@ -326,13 +330,20 @@ int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const v
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     Carver c(scratch);
     Agg* aggs = c.take<Agg>(ntiles);
+    Agg* btot = c.take<Agg>(ntiles / 1024 + 1);
     SBH_TIMED("keyed_tile_agg", s,
               tile_agg_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs));
     SBH_LAUNCHED();
-    if (ntiles > 4096)
-        SBH_TIMED("keyed_tile_scan", s, tile_scan_blocked_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
-    else
+    if (ntiles > 4096) {
+        const uint32_t nblk = (ntiles + 1023) / 1024;
+        SBH_TIMED("keyed_tile_scan_up", s, tile_scan_up_kernel<<<nblk, 1024, 0, s>>>(aggs, ntiles, btot));
+        SBH_LAUNCHED();
+        SBH_TIMED("keyed_tile_scan", s, tile_scan_kernel<<<1, 1024, 0, s>>>(btot, nblk));
+        SBH_LAUNCHED();
+        SBH_TIMED("keyed_tile_scan_add", s, tile_scan_add_kernel<<<nblk, 1024, 0, s>>>(aggs, ntiles, btot));
+    } else {
         SBH_TIMED("keyed_tile_scan", s, tile_scan_kernel<<<1, 1024, 0, s>>>(aggs, ntiles));
+    }
     SBH_LAUNCHED();
     SBH_TIMED("keyed_emit", s,
               emit_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs, ntiles, ok, oc, os,
@@ -345,6 +356,7 @@ size_t keyed_scratch(uint64_t n) {
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     Carver c(nullptr);
     c.take<Agg>(ntiles);
+    c.take<Agg>(ntiles / 1024 + 1);
     return c.bytes();
 }
 
@@ -386,7 +398,10 @@ namespace {
 
 constexpr uint64_t kNoAllocMaxRows = 1ull << 28;  // 268,435,456 rows
 constexpr size_t kNoAllocTiles = (kNoAllocMaxRows + kTile - 1) / kTile;
-constexpr size_t kNoAllocBytes = kNoAllocTiles * sizeof(Agg);  // 2 MiB on every GPU that loads the library
+// the tile aggregates (2 MiB) and the block totals of the tile scan, laid
+// out as keyed_scratch carves them; held on every GPU that loads the library
+constexpr size_t kNoAllocBytes =
+    kNoAllocTiles * sizeof(Agg) + (((kNoAllocTiles / 1024 + 1) * sizeof(Agg) + 255) & ~size_t(255));
 
 // One copy per device.  Host code must not use this name as an address: it
 // is a host-side stand-in; the device address comes from

@@ -567,6 +567,23 @@ struct BucketValue {
     }
 };
 
+// The same ids from a 4-byte entry per cell (half the table, so more of it
+// stays in L1), usable when every id is below 2^16: first id in the low 16
+// bits, number of buckets (at most 2^16 - 2 then) or kHeavyCell16 in the high.
+constexpr uint32_t kHeavyCell16 = 0xFFFFu;
+
+struct BucketValue16 {
+    const uint32_t* cells;  // kNCell + 1 entries
+    __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
+        uint32_t f;
+        const uint32_t c = key_cell(k, &f);
+        const uint32_t e = __ldg(cells + c);
+        const uint32_t x = e & 0xFFFFu, y = e >> 16;
+        if (y == kHeavyCell16) return x + 1;
+        return x + static_cast<uint32_t>((static_cast<uint64_t>(f) * y) >> 32);
+    }
+};
+
 __global__ void __launch_bounds__(256) cell_cdf_kernel(const Model* __restrict__ model, float* __restrict__ F) {
     __shared__ float P[kNP];
     for (int i = threadIdx.x; i < kNP; i += blockDim.x) P[i] = model->params[i];
@@ -582,6 +599,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
                                                                  const float* __restrict__ F, uint32_t nb,
                                                                  uint32_t* __restrict__ tbl,
                                                                  uint2* __restrict__ cells,
+                                                                 uint32_t* __restrict__ cells16,
                                                                  uint32_t* __restrict__ heavy_bucket_bits,
                                                                  uint32_t* __restrict__ nbid) {
     __shared__ float s_max[kTblThreads];
@@ -628,6 +646,8 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
         if (c == kNCell) e.y = 0;
         else e.y = is_heavy(model->heavy_bits, c) ? kHeavyCell : tbl[c + 1] - tbl[c];
         cells[c] = e;
+        // meaningful only when every id is below 2^16 (the carried-id path)
+        cells16[c] = (e.x & 0xFFFFu) | ((e.y == kHeavyCell ? kHeavyCell16 : (e.y & 0xFFFFu)) << 16);
     }
 }
 
@@ -1011,7 +1031,7 @@ constexpr uint32_t kMaxBucketIds = 1u << 16;  // carried ids are 16 bits
 // Bucket id of every row (kept as 16 bits) and the histograms of its two
 // digits.
 __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                          BucketValue fn, uint16_t* __restrict__ ids,
+                                                          BucketValue16 fn, uint16_t* __restrict__ ids,
                                                           uint32_t* __restrict__ ghist) {
     __shared__ uint32_t h[2 * kRadix];
     for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) h[i] = 0;
@@ -1207,7 +1227,7 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaS
 
 // Stable sort by 16-bit bucket id with the ids carried along; fills bstart.
 int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
-                        void* scratch, cudaStream_t s, BucketValue fn, const uint32_t* nbid, uint32_t* bstart) {
+                        void* scratch, cudaStream_t s, BucketValue16 fn, const uint32_t* nbid, uint32_t* bstart) {
     CarryScratch cs = carry_carve(scratch, n);
     const uint32_t n32 = static_cast<uint32_t>(n);
     const int sms = num_sms();
@@ -1240,6 +1260,7 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
 struct SortLearnedScratch {
     uint32_t* tbl;          // kNCell + 1
     uint2* cells;           // kNCell + 1
+    uint32_t* cells16;      // kNCell + 1
     float* F;               // kNCell + 1
     uint32_t* heavy_bucket_bits;
     uint32_t* bstart;       // max ids + 1
@@ -1265,6 +1286,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     const uint64_t ids = learned_max_ids(n);
     t.tbl = c.take<uint32_t>(kNCell + 1);
     t.cells = c.take<uint2>(kNCell + 1);
+    t.cells16 = c.take<uint32_t>(kNCell + 1);
     t.F = c.take<float>(kNCell + 1);
     t.list = c.take<uint32_t>(ids);
     t.offs = c.take<uint32_t>(ids);
@@ -1437,13 +1459,13 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<(kNCell + 1 + 255) / 256, 256, 0, s>>>(model, t.F));
     SBH_LAUNCHED();
     SBH_TIMED("learned_table", s,
-              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.cells, t.heavy_bucket_bits,
-                                                          nbid));
+              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.cells, t.cells16,
+                                                          t.heavy_bucket_bits, nbid));
     SBH_LAUNCHED();
     const BucketValue fn{t.cells};
     if (carry) {
-        rc = sort_by_carried_ids(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s, fn, nbid,
-                                 t.bstart);
+        rc = sort_by_carried_ids(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s,
+                                 BucketValue16{t.cells16}, nbid, t.bstart);
         if (rc) return rc;
     } else {
         // stable scatter by bucket id computed from the key (ids below 2^24)
