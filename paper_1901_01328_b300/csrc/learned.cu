@@ -584,71 +584,127 @@ struct BucketValue16 {
     }
 };
 
-__global__ void __launch_bounds__(256) cell_cdf_kernel(const Model* __restrict__ model, float* __restrict__ F) {
+// The cell table is built over blocks of 1024 cells in two launches:
+// cell_cdf writes F and each block's maximum of F and number of heavy cells;
+// cell_table combines the blocks before its own and scans its block.
+constexpr int kTblThreads = 1024;
+constexpr uint32_t kTblBlocks = (kNCell + 1 + kTblThreads - 1) / kTblThreads;
+
+__global__ void __launch_bounds__(kTblThreads) cell_cdf_kernel(const Model* __restrict__ model, float* __restrict__ F,
+                                                               float* __restrict__ bmax,
+                                                               uint32_t* __restrict__ bheavy) {
     __shared__ float P[kNP];
+    __shared__ float wm[32];
+    __shared__ uint32_t wc[32];
     for (int i = threadIdx.x; i < kNP; i += blockDim.x) P[i] = model->params[i];
     __syncthreads();
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c <= kNCell) F[c] = fminf(fmaxf(mlp_eval(P, cell_x(c)), 0.f), 1.f);
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, lane = lane_id(), warp = threadIdx.x / 32;
+    float f = 0.f;
+    uint32_t h = 0;
+    if (c <= kNCell) {
+        f = fminf(fmaxf(mlp_eval(P, cell_x(c)), 0.f), 1.f);
+        F[c] = f;
+        h = c < kNCell && is_heavy(model->heavy_bits, c);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+    }
+    if (lane == 0) {
+        wm[warp] = f;
+        wc[warp] = h;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        f = wm[lane];
+        h = wc[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
+            h += __shfl_xor_sync(0xffffffffu, h, o);
+        }
+        if (lane == 0) {
+            bmax[blockIdx.x] = f;
+            bheavy[blockIdx.x] = h;
+        }
+    }
 }
 
-// One CTA: prefix maximum of F, heavy prefix counts, first-bucket table and
-// the bitmap of heavy buckets.  nbid receives the bound on bucket ids.
-constexpr int kTblThreads = 1024;
+// Cell c's first bucket id is t(c) = floor(max(F[0..c]) * nb) + 2 * (heavy
+// cells before c); a heavy cell's bucket t + 1 is marked in the bitmap of
+// heavy buckets; nbid receives t(kNCell) + 1, the bound on bucket ids.
 __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __restrict__ model,
-                                                                 const float* __restrict__ F, uint32_t nb,
-                                                                 uint32_t* __restrict__ tbl,
+                                                                 const float* __restrict__ F,
+                                                                 const float* __restrict__ bmax,
+                                                                 const uint32_t* __restrict__ bheavy, uint32_t nb,
                                                                  uint2* __restrict__ cells,
                                                                  uint32_t* __restrict__ cells16,
                                                                  uint32_t* __restrict__ heavy_bucket_bits,
                                                                  uint32_t* __restrict__ nbid) {
-    __shared__ float s_max[kTblThreads];
-    __shared__ uint32_t s_cnt[kTblThreads];
-    const uint32_t total = kNCell + 1;
-    const uint32_t per = (total + kTblThreads - 1) / kTblThreads;
-    const uint32_t c0 = min(total, threadIdx.x * per), c1 = min(total, c0 + per);
-    float mx = 0.f;
-    uint32_t hc = 0;
-    for (uint32_t c = c0; c < c1; ++c) {
-        mx = fmaxf(mx, F[c]);
-        hc += (c < kNCell) && is_heavy(model->heavy_bits, c);
-    }
-    s_max[threadIdx.x] = mx;
-    s_cnt[threadIdx.x] = hc;
-    __syncthreads();
-    // inclusive scans (max, +) over the threads, Hillis-Steele in shared memory
-    for (uint32_t o = 1; o < kTblThreads; o <<= 1) {
-        const float pm = threadIdx.x >= o ? s_max[threadIdx.x - o] : 0.f;
-        const uint32_t pc = threadIdx.x >= o ? s_cnt[threadIdx.x - o] : 0u;
-        __syncthreads();
-        s_max[threadIdx.x] = fmaxf(s_max[threadIdx.x], pm);
-        s_cnt[threadIdx.x] += pc;
-        __syncthreads();
-    }
-    float run_max = threadIdx.x ? s_max[threadIdx.x - 1] : 0.f;
-    uint32_t heavy_before = threadIdx.x ? s_cnt[threadIdx.x - 1] : 0u;
-    const float fnb = static_cast<float>(nb);
-    for (uint32_t c = c0; c < c1; ++c) {
-        run_max = fmaxf(run_max, F[c]);
-        const uint32_t base = static_cast<uint32_t>(floorf(run_max * fnb));
-        const uint32_t t = base + 2u * heavy_before;
-        tbl[c] = t;
-        if (c < kNCell && is_heavy(model->heavy_bits, c)) {
-            atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
-            ++heavy_before;
+    __shared__ float wm[32];
+    __shared__ uint32_t wc[32];
+    __shared__ float pre_m;
+    __shared__ uint32_t pre_h;
+    const uint32_t blk = blockIdx.x, c = blk * kTblThreads + threadIdx.x, lane = lane_id(), warp = threadIdx.x / 32;
+    if (warp == 0) {  // the blocks before this one
+        float m = 0.f;
+        uint32_t h = 0;
+        for (uint32_t j = lane; j < blk; j += 32) {
+            m = fmaxf(m, bmax[j]);
+            h += bheavy[j];
         }
-        if (c == kNCell) *nbid = t + 1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            h += __shfl_xor_sync(0xffffffffu, h, o);
+        }
+        if (lane == 0) {
+            pre_m = m;
+            pre_h = h;
+        }
+    }
+    const float f = c <= kNCell ? F[c] : 0.f;
+    const uint32_t hv = c < kNCell && is_heavy(model->heavy_bits, c);
+    float m = f;
+    uint32_t h = hv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ym = __shfl_up_sync(0xffffffffu, m, o);
+        const uint32_t yh = __shfl_up_sync(0xffffffffu, h, o);
+        if (lane >= (uint32_t)o) {
+            m = fmaxf(m, ym);
+            h += yh;
+        }
+    }
+    if (lane == 31) {
+        wm[warp] = m;
+        wc[warp] = h;
     }
     __syncthreads();
-    for (uint32_t c = c0; c < c1; ++c) {
-        uint2 e;
-        e.x = tbl[c];
-        if (c == kNCell) e.y = 0;
-        else e.y = is_heavy(model->heavy_bits, c) ? kHeavyCell : tbl[c + 1] - tbl[c];
-        cells[c] = e;
-        // meaningful only when every id is below 2^16 (the carried-id path)
-        cells16[c] = (e.x & 0xFFFFu) | ((e.y == kHeavyCell ? kHeavyCell16 : (e.y & 0xFFFFu)) << 16);
+    float bm = pre_m;
+    uint32_t bh = pre_h;
+    for (uint32_t w = 0; w < warp; ++w) {
+        bm = fmaxf(bm, wm[w]);
+        bh += wc[w];
     }
+    const float run_max = fmaxf(bm, m);  // max of F[0..c]
+    const uint32_t heavy_incl = bh + h;  // heavy cells in [0, c]
+    const float fnb = static_cast<float>(nb);
+    const uint32_t t = static_cast<uint32_t>(floorf(run_max * fnb)) + 2u * (heavy_incl - hv);
+    // the next cell's first id (the same arithmetic as its own thread's)
+    float f_next = __shfl_down_sync(0xffffffffu, f, 1);
+    if (lane == 31) f_next = c + 1 <= kNCell ? F[c + 1] : 0.f;
+    const uint32_t t_next = static_cast<uint32_t>(floorf(fmaxf(run_max, f_next) * fnb)) + 2u * heavy_incl;
+    if (c > kNCell) return;
+    if (hv) atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
+    if (c == kNCell) *nbid = t + 1;
+    uint2 e;
+    e.x = t;
+    e.y = c == kNCell ? 0u : (hv ? kHeavyCell : t_next - t);
+    cells[c] = e;
+    // meaningful only when every id is below 2^16 (the carried-id path)
+    cells16[c] = (e.x & 0xFFFFu) | ((e.y == kHeavyCell ? kHeavyCell16 : (e.y & 0xFFFFu)) << 16);
 }
 
 // bstart[b] = first row whose bucket id is >= b, for b in [0, nbid].  Each
@@ -959,40 +1015,103 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
 }
 
 // Ordered list of overflow buckets with their row offsets in a compact
-// buffer (one CTA).  ov_rows_total receives the total.
+// buffer, in two launches over blocks of 1024 buckets: each block's count of
+// overflow buckets and rows, then each block's exclusive scan from the totals
+// of the blocks before it.  The last block writes the totals to nlist and
+// ov_rows_total.
+__global__ void __launch_bounds__(1024) overflow_count_kernel(const uint32_t* __restrict__ ov_flag,
+                                                              const uint32_t* __restrict__ nbid_p,
+                                                              const uint32_t* __restrict__ bstart,
+                                                              uint2* __restrict__ bagg) {
+    __shared__ uint32_t wc[32], wr[32];
+    const uint32_t nbid = *nbid_p, lane = lane_id(), warp = threadIdx.x / 32;
+    const uint32_t b = blockIdx.x * 1024u + threadIdx.x;
+    uint32_t c = b < nbid ? ov_flag[b] : 0u;
+    uint32_t r = c ? bstart[b + 1] - bstart[b] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if (lane == 0) {
+        wc[warp] = c;
+        wr[warp] = r;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        c = wc[lane];
+        r = wr[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+        }
+        if (lane == 0) bagg[blockIdx.x] = make_uint2(c, r);
+    }
+}
+
 __global__ void __launch_bounds__(1024) overflow_list_kernel(const uint32_t* __restrict__ ov_flag,
                                                              const uint32_t* __restrict__ nbid_p,
                                                              const uint32_t* __restrict__ bstart,
+                                                             const uint2* __restrict__ bagg,
                                                              uint32_t* __restrict__ list, uint32_t* __restrict__ offs,
                                                              uint32_t* __restrict__ nlist,
                                                              uint32_t* __restrict__ rows_total) {
     __shared__ uint32_t wc[32], wr[32];
-    __shared__ uint32_t carry_c, carry_r;
-    const uint32_t nbid = *nbid_p;
-    if (threadIdx.x == 0) carry_c = carry_r = 0;
-    __syncthreads();
-    for (uint32_t c0 = 0; c0 < nbid; c0 += blockDim.x) {
-        const uint32_t b = c0 + threadIdx.x;
-        const uint32_t f = b < nbid ? ov_flag[b] : 0u;
-        const uint32_t len = f ? bstart[b + 1] - bstart[b] : 0u;
-        uint32_t xc = f, xr = len;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t yc = __shfl_up_sync(0xffffffffu, xc, o), yr = __shfl_up_sync(0xffffffffu, xr, o);
-            if (lane_id() >= (uint32_t)o) { xc += yc; xr += yr; }
-        }
-        if (lane_id() == 31) { wc[threadIdx.x / 32] = xc; wr[threadIdx.x / 32] = xr; }
-        __syncthreads();
-        uint32_t bc = carry_c, br = carry_r;
-        for (uint32_t w = 0; w < threadIdx.x / 32; ++w) { bc += wc[w]; br += wr[w]; }
-        if (f) {
-            list[bc + xc - 1] = b;
-            offs[bc + xc - 1] = br + xr - len;
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) { carry_c = bc + xc; carry_r = br + xr; }
-        __syncthreads();
+    const uint32_t nbid = *nbid_p, lane = lane_id(), warp = threadIdx.x / 32;
+    // totals of the blocks before this one
+    uint32_t pc = 0, pr = 0;
+    for (uint32_t j = threadIdx.x; j < blockIdx.x; j += 1024u) {
+        const uint2 v = bagg[j];
+        pc += v.x;
+        pr += v.y;
     }
-    if (threadIdx.x == 0) { *nlist = carry_c; *rows_total = carry_r; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pc += __shfl_xor_sync(0xffffffffu, pc, o);
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    }
+    if (lane == 0) {
+        wc[warp] = pc;
+        wr[warp] = pr;
+    }
+    __syncthreads();
+    pc = pr = 0;
+#pragma unroll 8
+    for (int w = 0; w < 32; ++w) {
+        pc += wc[w];
+        pr += wr[w];
+    }
+    __syncthreads();
+    const uint32_t b = blockIdx.x * 1024u + threadIdx.x;
+    const uint32_t f = b < nbid ? ov_flag[b] : 0u;
+    const uint32_t len = f ? bstart[b + 1] - bstart[b] : 0u;
+    uint32_t xc = f, xr = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yc = __shfl_up_sync(0xffffffffu, xc, o), yr = __shfl_up_sync(0xffffffffu, xr, o);
+        if (lane >= (uint32_t)o) {
+            xc += yc;
+            xr += yr;
+        }
+    }
+    if (lane == 31) {
+        wc[warp] = xc;
+        wr[warp] = xr;
+    }
+    __syncthreads();
+    for (uint32_t w = 0; w < warp; ++w) {
+        pc += wc[w];
+        pr += wr[w];
+    }
+    if (f) {
+        list[pc + xc - 1] = b;
+        offs[pc + xc - 1] = pr + xr - len;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 1023) {
+        *nlist = pc + xc;
+        *rows_total = pr + xr;
+    }
 }
 
 // Copies the rows of the listed overflow buckets to (to_gather) or from the
@@ -1044,8 +1163,26 @@ __global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __rest
         if (d1 == last1) ++run1;
         else { if (run1) atomicAdd(&h[kRadix + last1], run1); last1 = d1; run1 = 1; }
     };
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nthreads) {
+    const uint32_t nthreads = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0 && (reinterpret_cast<uintptr_t>(ids) & 7) == 0) {
+        // four keys per thread and iteration (two 16-byte loads in flight),
+        // their ids stored as one 8-byte word
+        const uint32_t nq = n / 4;
+        const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+        for (uint32_t q = t0; q < nq; q += nthreads) {
+            const ulonglong2 a = __ldcs(k2 + 2 * q), b = __ldcs(k2 + 2 * q + 1);
+            const uint32_t i0 = static_cast<uint32_t>(fn(a.x)), i1 = static_cast<uint32_t>(fn(a.y));
+            const uint32_t i2 = static_cast<uint32_t>(fn(b.x)), i3 = static_cast<uint32_t>(fn(b.y));
+            *reinterpret_cast<uint2*>(ids + 4 * q) = make_uint2((i0 & 0xFFFFu) | (i1 << 16), (i2 & 0xFFFFu) | (i3 << 16));
+            add(i0);
+            add(i1);
+            add(i2);
+            add(i3);
+        }
+        done = nq * 4;
+    }
+    for (uint32_t i = done + t0; i < n; i += nthreads) {
         const uint32_t id = static_cast<uint32_t>(fn(ld_stream(keys + i)));
         ids[i] = static_cast<uint16_t>(id);
         add(id);
@@ -1144,6 +1281,7 @@ struct CarryScratch {
     uint32_t* chunk_hist;
     uint32_t* chunk_base;
     uint32_t* hist;  // zeroed
+    uint32_t* bmin;  // per block of bucket starts: minimum
     size_t total;
 };
 
@@ -1160,27 +1298,62 @@ CarryScratch carry_carve(void* base, uint64_t n) {
     t.chunk_hist = c.take<uint32_t>(kMaxChunks * kRadix);
     t.chunk_base = c.take<uint32_t>(kMaxChunks * kRadix);
     t.hist = c.take<uint32_t>(kPositions * kRadix);
+    t.bmin = c.take<uint32_t>(kMaxBucketIds / 1024 + 1);
     t.total = c.bytes();
     return t;
 }
 
 // After the passes: bstart[b] = the first row of an id >= b (suffix minimum
-// of the recorded first rows; bstart[nbid] = n).  One CTA: each thread a
-// contiguous range, backwards.
-__global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restrict__ plan, uint32_t n,
-                                                           const uint32_t* __restrict__ nbid_p,
-                                                           uint32_t* __restrict__ bstart) {
+// of the recorded first rows; bstart[nbid] = n), in two launches over blocks
+// of 1024 entries: each block's minimum, then each block's suffix minimum
+// from the minimum of the blocks after it.
+constexpr uint32_t kFillBlocks = kMaxBucketIds / 1024 + 1;
+
+__device__ __forceinline__ uint32_t first_row_entry(const uint32_t* bstart, uint32_t b, uint32_t nbid, uint32_t n) {
+    return b < nbid ? bstart[b] : (b == nbid ? n : 0xFFFFFFFFu);
+}
+
+__global__ void __launch_bounds__(1024) bounds_min_kernel(const Plan* __restrict__ plan, uint32_t n,
+                                                          const uint32_t* __restrict__ nbid_p,
+                                                          const uint32_t* __restrict__ bstart,
+                                                          uint32_t* __restrict__ bmin) {
     if (!plan->npasses) return;
     __shared__ uint32_t wmin[32];
     const uint32_t nbid = *nbid_p;
-    const uint32_t tot = nbid + 1;
-    const uint32_t per = (tot + blockDim.x - 1) / blockDim.x;
-    const uint32_t b0 = min(tot, threadIdx.x * per), b1 = min(tot, b0 + per);
+    if (blockIdx.x * 1024u > nbid) return;
     const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
-    uint32_t m = 0xFFFFFFFFu;
-    for (uint32_t b = b0; b < b1; ++b) m = min(m, b == nbid ? n : bstart[b]);
-    // minimum over the ranges of all later threads
-    uint32_t x = m;
+    uint32_t x = first_row_entry(bstart, blockIdx.x * 1024u + threadIdx.x, nbid, n);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) wmin[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        x = wmin[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) bmin[blockIdx.x] = x;
+    }
+}
+
+__global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restrict__ plan, uint32_t n,
+                                                           const uint32_t* __restrict__ nbid_p,
+                                                           const uint32_t* __restrict__ bmin,
+                                                           uint32_t* __restrict__ bstart) {
+    if (!plan->npasses) return;
+    __shared__ uint32_t wmin[32];
+    __shared__ uint32_t after_s;
+    const uint32_t nbid = *nbid_p, blk = blockIdx.x;
+    if (blk * 1024u > nbid) return;
+    const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+    if (warp == 0) {  // the blocks after this one
+        uint32_t a = 0xFFFFFFFFu;
+        for (uint32_t j = blk + 1 + lane; j <= nbid / 1024u; j += 32) a = min(a, bmin[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+        if (lane == 0) after_s = a;
+    }
+    const uint32_t b = blk * 1024u + threadIdx.x;
+    uint32_t x = first_row_entry(bstart, b, nbid, n);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
@@ -1188,16 +1361,9 @@ __global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restric
     }
     if (lane == 0) wmin[warp] = x;
     __syncthreads();
-    uint32_t after = 0xFFFFFFFFu;
-    for (uint32_t w = warp + 1; w < blockDim.x / 32; ++w) after = min(after, wmin[w]);
-    const uint32_t nxt = __shfl_down_sync(0xffffffffu, x, 1);
-    if (lane < 31) after = min(after, nxt);
-    __syncthreads();
-    for (uint32_t b = b1; b-- > b0;) {
-        const uint32_t v = b == nbid ? n : min(bstart[b], after);
-        bstart[b] = v;
-        after = v;
-    }
+    uint32_t after = after_s;
+    for (uint32_t w = warp + 1; w < 32; ++w) after = min(after, wmin[w]);
+    if (b <= nbid) bstart[b] = min(x, after);
 }
 
 // The two passes by carried bucket id: per pass, chunk counts of the id
@@ -1252,13 +1418,18 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_bounds", s,
               ids_bounds_kernel<<<(unsigned)((n + 2047) / 2048), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
     SBH_LAUNCHED();
-    SBH_TIMED("learned_bounds_fill", s, bounds_fill_kernel<<<1, 1024, 0, s>>>(cs.plan, n32, nbid, bstart));
+    SBH_TIMED("learned_bounds_min", s,
+              bounds_min_kernel<<<kFillBlocks, 1024, 0, s>>>(cs.plan, n32, nbid, bstart, cs.bmin));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_bounds_fill", s,
+              bounds_fill_kernel<<<kFillBlocks, 1024, 0, s>>>(cs.plan, n32, nbid, cs.bmin, bstart));
     SBH_LAUNCHED();
     return SBH_OK;
 }
 
 struct SortLearnedScratch {
-    uint32_t* tbl;          // kNCell + 1
+    float* bmax;            // per block of cells: maximum of F
+    uint32_t* bheavy;       // per block of cells: heavy cells
     uint2* cells;           // kNCell + 1
     uint32_t* cells16;      // kNCell + 1
     float* F;               // kNCell + 1
@@ -1266,6 +1437,7 @@ struct SortLearnedScratch {
     uint32_t* bstart;       // max ids + 1
     uint32_t* ov_flag;      // max ids
     uint32_t* list;
+    uint2* bagg;            // per block of buckets: overflow buckets, rows
     uint32_t* offs;
     uint32_t* small;        // nbid, counter, nlist, rows_total
     BucketStats* stats;
@@ -1284,11 +1456,13 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     Carver c(base);
     SortLearnedScratch t;
     const uint64_t ids = learned_max_ids(n);
-    t.tbl = c.take<uint32_t>(kNCell + 1);
+    t.bmax = c.take<float>(kTblBlocks);
+    t.bheavy = c.take<uint32_t>(kTblBlocks);
     t.cells = c.take<uint2>(kNCell + 1);
     t.cells16 = c.take<uint32_t>(kNCell + 1);
     t.F = c.take<float>(kNCell + 1);
     t.list = c.take<uint32_t>(ids);
+    t.bagg = c.take<uint2>(ids / 1024 + 1);
     t.offs = c.take<uint32_t>(ids);
     t.bstart = c.take<uint32_t>(ids + 1);
     t.heavy_bucket_bits = c.take<uint32_t>(ids / 32 + 1);
@@ -1456,11 +1630,11 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     uint32_t* counter = t.small + 1;
     uint32_t* nlist = t.small + 2;
     uint32_t* rows_total = t.small + 3;
-    SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<(kNCell + 1 + 255) / 256, 256, 0, s>>>(model, t.F));
+    SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.bmax, t.bheavy));
     SBH_LAUNCHED();
     SBH_TIMED("learned_table", s,
-              cell_table_kernel<<<1, kTblThreads, 0, s>>>(model, t.F, nb, t.tbl, t.cells, t.cells16,
-                                                          t.heavy_bucket_bits, nbid));
+              cell_table_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.bmax, t.bheavy, nb, t.cells,
+                                                                   t.cells16, t.heavy_bucket_bits, nbid));
     SBH_LAUNCHED();
     const BucketValue fn{t.cells};
     if (carry) {
@@ -1483,8 +1657,13 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                                                                     t.heavy_bucket_bits, counter, t.ov_flag,
                                                                     t.stats));
     SBH_LAUNCHED();
+    const unsigned lblocks = (unsigned)(learned_max_ids(n) / 1024 + 1);
+    SBH_TIMED("learned_overflow_count", s,
+              overflow_count_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg));
+    SBH_LAUNCHED();
     SBH_TIMED("learned_overflow_list", s,
-              overflow_list_kernel<<<1, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.list, t.offs, nlist, rows_total));
+              overflow_list_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nlist,
+                                                           rows_total));
     SBH_LAUNCHED();
     // the overflow is data-dependent: read its size (one stream synchronisation)
     uint32_t small_h[4];
