@@ -96,8 +96,11 @@ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, float x) 
     return y;
 }
 
-constexpr int kGThreads = 256;
+constexpr int kGThreads = 1024;
 constexpr int kMaxSlice = 256;
+constexpr int kTrainCtas = 128;  // batch rows per CTA = batch / 128
+constexpr int kRedParams = (kNP + kTrainCtas - 1) / kTrainCtas;  // parameters each training CTA updates
+static_assert(kRedParams < kGThreads / 32, "one warp per updated parameter, and one for the loss");
 
 struct GradSmem {
     float P[kNP];
@@ -107,6 +110,7 @@ struct GradSmem {
     float A1[kMaxSlice][kH + 1];
     float A2[kMaxSlice][kH + 1];
     float red[kGThreads / 32];
+    float gred[kRedParams][kTrainCtas];  // training: the partial gradients of this CTA's parameters
 };
 
 // Gradient of sum_s (y_s - t_s)^2 / norm over the S rows in sm.X, sm.T into
@@ -268,7 +272,6 @@ struct TrainScratch {
     size_t total;
 };
 
-constexpr int kTrainCtas = 128;  // batch rows per CTA = batch / 128
 constexpr int kCompactTile = 1024;
 
 TrainScratch train_carve(void* base, uint64_t m) {
@@ -508,33 +511,37 @@ __global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
         if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
         b1t *= b1;
         b2t *= b2;
-        for (int i = p0 + threadIdx.x; i < p1; i += kGThreads) {
-            // sum in CTA order; loads issued sixteen at a time
-            float g = 0.f;
-            for (int q0 = 0; q0 < G; q0 += 16) {
-                float v[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = q0 + u < G ? a.partial[(q0 + u) * (size_t)kNP + i] : 0.f;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) g += v[u];
-            }
-            const float mi = b1 * a.adam_m[i] + (1.f - b1) * g;
-            const float vi = b2 * a.adam_v[i] + (1.f - b2) * g * g;
-            a.adam_m[i] = mi;
-            a.adam_v[i] = vi;
-            const float mhat = mi / (1.f - b1t), vhat = vi / (1.f - b2t);
-            a.params[i] -= a.lr * mhat / (sqrtf(vhat) + eps);
+        // this CTA's parameters: the partial gradients of every CTA, loaded
+        // by all threads at once, then one warp per parameter sums them
+        // (lane q sums CTAs q, q + 32, ..., then a butterfly)
+        const int np = p1 - p0;
+        for (int e = threadIdx.x; e < np * G; e += kGThreads) {
+            const int pi = e / G, q = e - pi * G;
+            sm.gred[pi][q] = a.partial[q * (size_t)kNP + p0 + pi];
         }
-        if (c == 0 && threadIdx.x == 0 && a.losses) {
-            float l = 0.f;
-            for (int q0 = 0; q0 < G; q0 += 16) {
-                float v[16];
+        __syncthreads();
+        const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+        if (warp < np) {
+            float g = 0.f;
+            for (int q = lane; q < G; q += 32) g += sm.gred[warp][q];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = q0 + u < G ? a.partial_sq[q0 + u] : 0.f;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) l += v[u];
+            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+            if (lane == 0) {
+                const int i = p0 + warp;
+                const float mi = b1 * a.adam_m[i] + (1.f - b1) * g;
+                const float vi = b2 * a.adam_v[i] + (1.f - b2) * g * g;
+                a.adam_m[i] = mi;
+                a.adam_v[i] = vi;
+                const float mhat = mi / (1.f - b1t), vhat = vi / (1.f - b2t);
+                a.params[i] -= a.lr * mhat / (sqrtf(vhat) + eps);
             }
-            a.losses[step] = l / static_cast<float>(a.batch);
+        }
+        if (c == 0 && warp == kGThreads / 32 - 1 && a.losses) {
+            float l = 0.f;
+            for (int q = lane; q < G; q += 32) l += a.partial_sq[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+            if (lane == 0) a.losses[step] = l / static_cast<float>(a.batch);
         }
         __threadfence();
         if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
@@ -1240,32 +1247,33 @@ __global__ void __launch_bounds__(256) ids_bounds_kernel(Buffers buf, const Plan
                                                          const uint32_t* __restrict__ nbid_p,
                                                          uint32_t* __restrict__ bstart) {
     if (plan->npasses) return;
-    const uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 8;
-    if (i0 >= n) return;
-    const uint16_t* __restrict__ v = plan->npasses ? buf.out_v : buf.in_v;
+    const uint16_t* __restrict__ v = buf.in_v;
     const uint32_t nbid = *nbid_p;
-    uint32_t id[8];
-    if (i0 + 8 <= n && (reinterpret_cast<uintptr_t>(v + i0) & 15) == 0) {
-        const uint4 w = *reinterpret_cast<const uint4*>(v + i0);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x * 8;
+    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 8; i0 < n; i0 += stride) {
+        uint32_t id[8];
+        if (i0 + 8 <= n && (reinterpret_cast<uintptr_t>(v + i0) & 15) == 0) {
+            const uint4 w = *reinterpret_cast<const uint4*>(v + i0);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            id[2 * u] = ws[u] & 0xFFFFu;
-            id[2 * u + 1] = ws[u] >> 16;
+            for (int u = 0; u < 4; ++u) {
+                id[2 * u] = ws[u] & 0xFFFFu;
+                id[2 * u + 1] = ws[u] >> 16;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) id[u] = i0 + u < n ? v[i0 + u] : 0u;
         }
-    } else {
+        int64_t prev = i0 ? static_cast<int64_t>(v[i0 - 1]) : -1;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) id[u] = i0 + u < n ? v[i0 + u] : 0u;
-    }
-    int64_t prev = i0 ? static_cast<int64_t>(v[i0 - 1]) : -1;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const uint64_t i = i0 + u;
-        if (i < n) {
-            for (int64_t b = prev + 1; b <= (int64_t)id[u]; ++b) bstart[b] = static_cast<uint32_t>(i);
-            if (i == n - 1)
-                for (uint32_t b = id[u] + 1; b <= nbid; ++b) bstart[b] = n;
-            prev = id[u];
+        for (int u = 0; u < 8; ++u) {
+            const uint64_t i = i0 + u;
+            if (i < n) {
+                for (int64_t b = prev + 1; b <= (int64_t)id[u]; ++b) bstart[b] = static_cast<uint32_t>(i);
+                if (i == n - 1)
+                    for (uint32_t b = id[u] + 1; b <= nbid; ++b) bstart[b] = n;
+                prev = id[u];
+            }
         }
     }
 }
@@ -1416,7 +1424,8 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds", s,
-              ids_bounds_kernel<<<(unsigned)((n + 2047) / 2048), 256, 0, s>>>(b, cs.plan, n32, nbid, bstart));
+              ids_bounds_kernel<<<(unsigned)min_u64((n + 2047) / 2048, (uint64_t)sms * 8), 256, 0, s>>>(
+                  b, cs.plan, n32, nbid, bstart));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds_min", s,
               bounds_min_kernel<<<kFillBlocks, 1024, 0, s>>>(cs.plan, n32, nbid, bstart, cs.bmin));
