@@ -109,27 +109,54 @@ struct GradSmem {
     float X[kMaxSlice], T[kMaxSlice], DY[kMaxSlice];
     float A1[kMaxSlice][kH + 1];
     float A2[kMaxSlice][kH + 1];
+    float D2[kMaxSlice][kH + 1];  // dL/da2
+    float part[4][kNP];           // gradient sums over the rows s = k (mod 4), laid out like G
     float red[kGThreads / 32];
     float gred[kRedParams][kTrainCtas];  // training: the partial gradients of this CTA's parameters
 };
 
 // Gradient of sum_s (y_s - t_s)^2 / norm over the S rows in sm.X, sm.T into
 // sm.G (and the sum of squared errors, returned to thread 0).  sm.P holds the
-// parameters.  Every sum runs in a fixed order.
+// parameters.  Every sum runs in a fixed order: a sum over rows keeps four
+// partial sums (rows s = k mod 4, each in row order) combined as
+// (k0 + k1) + (k2 + k3); a sum over units runs in unit order.  The three
+// 32-wide products (second layer forward, its weight gradient and the
+// gradient back to the first layer) take 4 x 4 register tiles, so each
+// shared-memory load feeds four multiply-adds.
 __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     const int tid = threadIdx.x;
+    const int stiles = (S + 3) / 4;  // groups of four rows
     for (int e = tid; e < kH * kH; e += kGThreads) sm.W2T[(e % kH) * kH + e / kH] = sm.P[oW2 + e];
     for (int e = tid; e < S * kH; e += kGThreads) {
         const int s = e / kH, i = e % kH;
         sm.A1[s][i] = fmaf(sm.P[oW1 + i], sm.X[s], sm.P[oB1 + i]);
     }
     __syncthreads();
-    for (int e = tid; e < S * kH; e += kGThreads) {
-        const int s = e / kH, o = e % kH;
-        float a = sm.P[oB2 + o];
-#pragma unroll 8
-        for (int i = 0; i < kH; ++i) a = fmaf(sm.W2T[i * kH + o], fmaxf(sm.A1[s][i], 0.f), a);
-        sm.A2[s][o] = a;
+    // a2[s][o] = b2[o] + sum_i W2[o][i] relu(a1[s][i]), rows s0..s0+3, units o0..o0+3
+    for (int t = tid; t < stiles * (kH / 4); t += kGThreads) {
+        const int s0 = (t / (kH / 4)) * 4, o0 = (t % (kH / 4)) * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = sm.P[oB2 + o0 + c];
+#pragma unroll 4
+        for (int i = 0; i < kH; ++i) {
+            float h[4], w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) h[r] = fmaxf(sm.A1[s0 + r][i], 0.f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) w[c] = sm.W2T[i * kH + o0 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(w[c], h[r], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (s0 + r < S)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sm.A2[s0 + r][o0 + c] = acc[r][c];
     }
     __syncthreads();
     float sq = 0.f;
@@ -142,63 +169,107 @@ __device__ float slice_grad(GradSmem& sm, int S, float norm) {
         sq += r * r;
     }
     __syncthreads();
-    // w3, b3 (four interleaved partial sums, combined in a fixed order)
-    for (int o = tid; o <= kH; o += kGThreads) {
-        float g[4] = {0.f, 0.f, 0.f, 0.f};
+    // w3, b3 partial sums (threads 0..131); dL/da2 (all threads)
+    if (tid < 4 * (kH + 1)) {
+        const int k = tid / (kH + 1), o = tid % (kH + 1);
+        float g = 0.f;
         if (o < kH) {
-            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.DY[s], fmaxf(sm.A2[s][o], 0.f), g[s & 3]);
-            sm.G[oW3 + o] = (g[0] + g[1]) + (g[2] + g[3]);
+            for (int s = k; s < S; s += 4) g = fmaf(sm.DY[s], fmaxf(sm.A2[s][o], 0.f), g);
+            sm.part[k][oW3 + o] = g;
         } else {
-            for (int s = 0; s < S; ++s) g[s & 3] += sm.DY[s];
-            sm.G[oB3] = (g[0] + g[1]) + (g[2] + g[3]);
+            for (int s = k; s < S; s += 4) g += sm.DY[s];
+            sm.part[k][oB3] = g;
         }
     }
-    __syncthreads();
-    // A2 <- dL/da2
     for (int e = tid; e < S * kH; e += kGThreads) {
         const int s = e / kH, o = e % kH;
-        sm.A2[s][o] = sm.A2[s][o] > 0.f ? sm.DY[s] * sm.P[oW3 + o] : 0.f;
+        sm.D2[s][o] = sm.A2[s][o] > 0.f ? sm.DY[s] * sm.P[oW3 + o] : 0.f;
     }
     __syncthreads();
-    // W2, b2
-    for (int e = tid; e < kH * kH + kH; e += kGThreads) {
-        float g[4] = {0.f, 0.f, 0.f, 0.f};
-        if (e < kH * kH) {
-            const int o = e / kH, i = e % kH;
-            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.A2[s][o], fmaxf(sm.A1[s][i], 0.f), g[s & 3]);
-            sm.G[oW2 + e] = (g[0] + g[1]) + (g[2] + g[3]);
-        } else {
-            const int o = e - kH * kH;
-            for (int s = 0; s < S; ++s) g[s & 3] += sm.A2[s][o];
-            sm.G[oB2 + o] = (g[0] + g[1]) + (g[2] + g[3]);
+    // W2 partial sums in 4 x 4 tiles of (o, i) (threads 0..255), b2 partial
+    // sums (threads 256..383); w3, b3 combined (threads 384..416)
+    if (tid < 4 * 64) {
+        const int k = tid / 64, tile = tid % 64;
+        const int o0 = (tile / 8) * 4, i0 = (tile % 8) * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+        for (int s = k; s < S; s += 4) {
+            float d[4], h[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) d[r] = sm.D2[s][o0 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h[c] = fmaxf(sm.A1[s][i0 + c], 0.f);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(d[r], h[c], acc[r][c]);
         }
-    }
-    __syncthreads();
-    // A1 <- dL/da1 (through W2 and the ReLU)
-    for (int e = tid; e < S * kH; e += kGThreads) {
-        const int s = e / kH, i = e % kH;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sm.part[k][oW2 + (o0 + r) * kH + i0 + c] = acc[r][c];
+    } else if (tid < 4 * 64 + 4 * kH) {
+        const int k = (tid - 4 * 64) / kH, o = (tid - 4 * 64) % kH;
         float g = 0.f;
-#pragma unroll 8
-        for (int o = 0; o < kH; ++o) g = fmaf(sm.A2[s][o], sm.P[oW2 + o * kH + i], g);
-        // each (s, i) is read and written by this thread only; the reads of
-        // A1 for W2 finished at the barrier above
-        sm.A1[s][i] = sm.A1[s][i] > 0.f ? g : 0.f;
+        for (int s = k; s < S; s += 4) g += sm.D2[s][o];
+        sm.part[k][oB2 + o] = g;
+    } else if (tid < 4 * 64 + 4 * kH + kH + 1) {
+        const int j = tid - (4 * 64 + 4 * kH) + oW3;  // oW3 .. oB3
+        sm.G[j] = (sm.part[0][j] + sm.part[1][j]) + (sm.part[2][j] + sm.part[3][j]);
     }
     __syncthreads();
-    for (int i = tid; i < 2 * kH; i += kGThreads) {
-        float g[4] = {0.f, 0.f, 0.f, 0.f};
+    // W2, b2 combined; dL/da1 = (sum_o dL/da2[s][o] W2[o][i]) where a1 > 0,
+    // in 4 x 4 tiles of (s, i), written over A1 (each entry by its own thread;
+    // the reads of A1 for W2 ended at the barrier above)
+    for (int j = oW2 + tid; j < oW3; j += kGThreads)
+        sm.G[j] = (sm.part[0][j] + sm.part[1][j]) + (sm.part[2][j] + sm.part[3][j]);
+    for (int t = tid; t < stiles * (kH / 4); t += kGThreads) {
+        const int s0 = (t / (kH / 4)) * 4, i0 = (t % (kH / 4)) * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+        for (int o = 0; o < kH; ++o) {
+            float d[4], w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) d[r] = sm.D2[s0 + r][o];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) w[c] = sm.P[oW2 + o * kH + i0 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(d[r], w[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (s0 + r < S)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    sm.A1[s0 + r][i0 + c] = sm.A1[s0 + r][i0 + c] > 0.f ? acc[r][c] : 0.f;
+    }
+    __syncthreads();
+    // W1, b1 partial sums (threads 0..255)
+    if (tid < 4 * 2 * kH) {
+        const int k = tid / (2 * kH), i = tid % (2 * kH);
+        float g = 0.f;
         if (i < kH) {
-            for (int s = 0; s < S; ++s) g[s & 3] = fmaf(sm.A1[s][i], sm.X[s], g[s & 3]);
-            sm.G[oW1 + i] = (g[0] + g[1]) + (g[2] + g[3]);
+            for (int s = k; s < S; s += 4) g = fmaf(sm.A1[s][i], sm.X[s], g);
+            sm.part[k][oW1 + i] = g;
         } else {
-            for (int s = 0; s < S; ++s) g[s & 3] += sm.A1[s][i - kH];
-            sm.G[oB1 + i - kH] = (g[0] + g[1]) + (g[2] + g[3]);
+            for (int s = k; s < S; s += 4) g += sm.A1[s][i - kH];
+            sm.part[k][oB1 + i - kH] = g;
         }
     }
     // sum of squared errors: warp shuffles, then warp totals in order
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
     if ((tid & 31) == 0) sm.red[tid / 32] = sq;
     __syncthreads();
+    if (tid < 2 * kH) sm.G[tid] = (sm.part[0][tid] + sm.part[1][tid]) + (sm.part[2][tid] + sm.part[3][tid]);
     float tot = 0.f;
     if (tid == 0)
         for (int w = 0; w < kGThreads / 32; ++w) tot += sm.red[w];
