@@ -1226,50 +1226,50 @@ constexpr int kCarryTile = 3584;
 constexpr uint32_t kMaxBucketIds = 1u << 16;  // carried ids are 16 bits
 
 // Bucket id of every row (kept as 16 bits) and the histograms of its two
-// digits.
-__global__ void __launch_bounds__(256) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                          BucketValue16 fn, uint16_t* __restrict__ ids,
-                                                          uint32_t* __restrict__ ghist) {
+// digits.  CTA c takes the rows of chunk c of the first digit pass, so the
+// chunk's histogram of the first digit (what that pass's count kernel would
+// produce) comes out here too.
+__global__ void __launch_bounds__(1024) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                           uint32_t chunk, BucketValue16 fn,
+                                                           uint16_t* __restrict__ ids, uint32_t* __restrict__ ghist,
+                                                           uint32_t* __restrict__ chunk_hist) {
     __shared__ uint32_t h[2 * kRadix];
     for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    uint32_t last0 = 0, run0 = 0, last1 = 0, run1 = 0;
     auto add = [&](uint32_t id) {
-        const uint32_t d0 = id & 255u, d1 = id >> 8;
-        if (d0 == last0) ++run0;
-        else { if (run0) atomicAdd(&h[last0], run0); last0 = d0; run0 = 1; }
-        if (d1 == last1) ++run1;
-        else { if (run1) atomicAdd(&h[kRadix + last1], run1); last1 = d1; run1 = 1; }
+        atomicAdd(&h[id & 255u], 1u);
+        atomicAdd(&h[kRadix + (id >> 8)], 1u);
     };
-    const uint32_t nthreads = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t done = 0;
-    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0 && (reinterpret_cast<uintptr_t>(ids) & 7) == 0) {
+    const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    uint32_t done = lo;
+    if (lo < hi && (reinterpret_cast<uintptr_t>(keys + lo) & 15) == 0 && (reinterpret_cast<uintptr_t>(ids + lo) & 7) == 0) {
         // four keys per thread and iteration (two 16-byte loads in flight),
         // their ids stored as one 8-byte word
-        const uint32_t nq = n / 4;
-        const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
-        for (uint32_t q = t0; q < nq; q += nthreads) {
+        const uint32_t nq = (hi - lo) / 4;
+        const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys + lo);
+        uint2* i4 = reinterpret_cast<uint2*>(ids + lo);
+        for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
             const ulonglong2 a = __ldcs(k2 + 2 * q), b = __ldcs(k2 + 2 * q + 1);
             const uint32_t i0 = static_cast<uint32_t>(fn(a.x)), i1 = static_cast<uint32_t>(fn(a.y));
             const uint32_t i2 = static_cast<uint32_t>(fn(b.x)), i3 = static_cast<uint32_t>(fn(b.y));
-            *reinterpret_cast<uint2*>(ids + 4 * q) = make_uint2((i0 & 0xFFFFu) | (i1 << 16), (i2 & 0xFFFFu) | (i3 << 16));
+            i4[q] = make_uint2((i0 & 0xFFFFu) | (i1 << 16), (i2 & 0xFFFFu) | (i3 << 16));
             add(i0);
             add(i1);
             add(i2);
             add(i3);
         }
-        done = nq * 4;
+        done = lo + nq * 4;
     }
-    for (uint32_t i = done + t0; i < n; i += nthreads) {
+    for (uint32_t i = done + threadIdx.x; i < hi; i += blockDim.x) {
         const uint32_t id = static_cast<uint32_t>(fn(ld_stream(keys + i)));
         ids[i] = static_cast<uint16_t>(id);
         add(id);
     }
-    if (run0) atomicAdd(&h[last0], run0);
-    if (run1) atomicAdd(&h[kRadix + last1], run1);
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x)
+    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) {
+        if (i < kRadix) chunk_hist[blockIdx.x * kRadix + i] = h[i];
         if (h[i]) atomicAdd(&ghist[i], h[i]);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int p = 2; p < kPositions; ++p) atomicAdd(&ghist[p * kRadix], n);
 }
@@ -1447,17 +1447,18 @@ __global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restric
 
 // The two passes by carried bucket id: per pass, chunk counts of the id
 // digit -> chunk offsets -> scatter carrying the ids along.
+// The first pass's chunk counts come from the id upsweep (the same chunks).
 template <int TILE, int THREADS>
-int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, cudaStream_t s, uint32_t* first_row) {
-    ChunkGeom g;
-    const int rc = chunk_geometry<RadixValue, TILE, THREADS, true>(n32, &g);
-    if (rc) return rc;
+int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const ChunkGeom& g, cudaStream_t s,
+                   uint32_t* first_row) {
     const int bulk_ok = ((reinterpret_cast<uintptr_t>(b.in_k) | reinterpret_cast<uintptr_t>(b.in_p) |
                           reinterpret_cast<uintptr_t>(b.out_k) | reinterpret_cast<uintptr_t>(b.out_p)) & 15) == 0;
     for (int pos = 0; pos < 2; ++pos) {
-        SBH_TIMED("learned_ids_count", s,
-                  ids_count_kernel<<<g.nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, g.chunk, cs.chunk_hist));
-        SBH_LAUNCHED();
+        if (pos > 0) {
+            SBH_TIMED("learned_ids_count", s,
+                      ids_count_kernel<<<g.nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, g.chunk, cs.chunk_hist));
+            SBH_LAUNCHED();
+        }
         SBH_TIMED("learned_ids_chunk_scan", s,
                   chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, cs.gbase, cs.chunk_base));
         SBH_LAUNCHED();
@@ -1477,8 +1478,11 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     const uint32_t n32 = static_cast<uint32_t>(n);
     const int sms = num_sms();
     SBH_CUDA(cudaMemsetAsync(cs.hist, 0, kPositions * kRadix * sizeof(uint32_t), s));
-    const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
-    SBH_TIMED("learned_ids_upsweep", s, ids_upsweep_kernel<<<up_blocks, 256, 0, s>>>(in_k, n32, fn, cs.ids_in, cs.hist));
+    ChunkGeom g;
+    int rc = chunk_geometry<RadixValue, kCarryTile, 512, true>(n32, &g);
+    if (rc) return rc;
+    SBH_TIMED("learned_ids_upsweep", s,
+              ids_upsweep_kernel<<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, fn, cs.ids_in, cs.hist, cs.chunk_hist));
     SBH_LAUNCHED();
     SBH_TIMED("learned_ids_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(cs.hist, n32, cs.gbase, cs.plan, 0));
     SBH_LAUNCHED();
@@ -1489,7 +1493,7 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     // bucket starts: the last pass records each id's first output row, then a
     // suffix minimum fills the empty buckets (with no pass, read the ids)
     SBH_CUDA(cudaMemsetAsync(bstart, 0xFF, (kMaxBucketIds + 1) * sizeof(uint32_t), s));
-    const int rc = carried_passes<kCarryTile, 512>(b, n32, cs, s, bstart);
+    rc = carried_passes<kCarryTile, 512>(b, n32, cs, g, s, bstart);
     if (rc) return rc;
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
