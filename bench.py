@@ -155,14 +155,28 @@ def cpu_oracle_step(col: np.ndarray):
 
 
 def cpu_baseline(sample_rows=CPU_SAMPLE):
+    """The oracle on one host thread, and on all host cores (up to 64) with one
+    independent window of sample_rows per thread (the oracle's C calls release
+    the GIL, so the threads run in parallel)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import gen
     col = gen.mixed_keys(sample_rows)
     t0 = time.perf_counter()
     cpu_oracle_step(col)
     dt = time.perf_counter() - t0
+    cores = max(1, min(64, os.cpu_count() or 1))
+    cols = [gen.mixed_keys(sample_rows, seed=window_seed(gen.SEED_MIXED, 1 + i)) for i in range(cores)]
+    with ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(cpu_oracle_step, cols))
+        dt_all = time.perf_counter() - t0
     return {"value": sample_rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sample_rows:,} rows of the same seeded mixed-key column; std::sort + std::map count, "
-                      f"one thread"}
+                      f"one thread",
+            "all_cores": {"value": cores * sample_rows / dt_all, "unit": UNIT, "cores": cores,
+                          "sample": f"{cores} independent windows of {sample_rows:,} rows of the same distribution, "
+                                    f"one per thread"}}
 
 
 def run_reference(args):
@@ -193,7 +207,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 SAMPLE_STRIDE = 100        # 1% sample for the learned partitioner
-TRAIN = dict(steps=40, batch=16384, lr=4e-2)
+TRAIN = dict(steps=40, batch=16384, lr=3e-5, init="quantile knots")
 
 
 def run_gpu(args):
@@ -215,7 +229,7 @@ def run_gpu(args):
     col_h = torch.empty(n, dtype=torch.uint64).pin_memory()
     gen.mixed_keys(n, seed=window_seed(gen.SEED_MIXED, rank), out=col_h.numpy())
     col = col_h.to(dev)
-    init = torch.from_numpy(gen.mlp_init()).to(dev)
+    init = None  # start from the CDF interpolated between 33 sample quantiles
     keys = torch.empty(n, dtype=torch.uint64, device=dev)
     ptrs = torch.empty(n, dtype=torch.uint32, device=dev)
     samples = torch.empty(m, dtype=torch.uint64, device=dev)
@@ -293,6 +307,46 @@ def run_gpu(args):
         other()
     ms_other = timed(other, args.steps)
 
+    # ---- robustness variant and an external library sort, on the same window size
+    variants = None
+    if not args.no_rows:
+        variants = {}
+        # the Zipf ranks through mix64: the same multiplicities, spread over all 64 bits
+        col2 = torch.from_numpy(gen.mixed_keys(n, seed=window_seed(gen.SEED_MIXED, rank), hashed=True)).to(dev)
+        for _ in range(2):
+            step_learned(col2)
+        ms_l2 = timed(lambda: step_learned(col2), args.steps)
+        st2 = dict(stats)
+        for _ in range(2):
+            step_plain(col2)
+        ms_p2 = timed(lambda: step_plain(col2), args.steps)
+        per2, _ = profiled(lambda: step_learned(col2), args.steps)
+        assert sbh.sync_status() == sbh.SBH_OK
+        variants["hashed_zipf"] = {
+            "learned_ms_per_step": ms_l2 / args.steps, "radix_ms_per_step": ms_p2 / args.steps,
+            "speedup": ms_p2 / ms_l2, "learned_stats": st2, "overflow_row_rate": st2.get("overflow_rows", 0) / n,
+            "stages_ms": {k: sum(v) / args.steps for k, v in per2.items() if sum(v) / args.steps >= 0.05},
+            "text": "the headline window with each Zipf rank r replaced by mix64(r) (SplitMix64 output function)"}
+        del col2
+        # a library sort for context: PyTorch's stable sort of the same keys, mapped order-preservingly
+        # to int64 (top bit flipped), with int64 indices (16 B per pair against the KPA's 12)
+        sbh.sbh_kpa_extract(col, 0, n, keys, ptrs)
+        k64 = (keys.view(torch.int64) ^ torch.iinfo(torch.int64).min)
+        ts = []
+        for r in range(3 + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.sort(k64, stable=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        variants["library_sort_ms"] = {"ms": statistics.median(ts),
+                                       "text": "torch.sort(stable=True) on the 256M keys as int64 (values and int64 "
+                                               "indices out); our sorts on the same keys: see learned_vs_radix stages"}
+        del k64
+        torch.cuda.empty_cache()
+
     # ---- per-kernel breakdown (separate, profiled runs of the same steps)
     per, launches_per_step = profiled(step, args.steps)
     tot = {k: sum(v) for k, v in per.items()}
@@ -352,7 +406,8 @@ def run_gpu(args):
                                  "speedup": radix_ms / learned_ms,
                                  "learned_stats": stats,
                                  "overflow_row_rate": stats.get("overflow_rows", 0) / n,
-                                 "other_stages": other_stages},
+                                 "other_stages": other_stages,
+                                 "variants": variants},
             "stages": stages,
             "rows": row_suite(peak) if ws == 1 and not args.no_rows else None,
             "serving": (serving_rows([float(x) for x in args.serve_loads.split(",")], args.serve_windows)

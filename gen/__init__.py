@@ -39,7 +39,7 @@ def _load():
         lib = ctypes.CDLL(build())
         u64, dbl, i32, vp = ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         lib.sbhgen_uniform.argtypes = [u64, u64, u64, u64, u64, vp, i32, i32]
-        lib.sbhgen_zipf_lognormal_mix.argtypes = [u64, u64, dbl, dbl, u64, dbl, dbl, vp, i32]
+        lib.sbhgen_zipf_lognormal_mix.argtypes = [u64, u64, dbl, dbl, u64, dbl, dbl, vp, i32, i32]
         lib.sbhgen_zipf.argtypes = [u64, u64, u64, dbl, u64, vp, i32]
         lib.sbhgen_lognormal_sizes.argtypes = [u64, u64, u64, dbl, dbl, u64, u64, vp]
         lib.sbhgen_unif01.argtypes = [u64, u64, u64, vp]
@@ -76,12 +76,15 @@ def zipf(seed: int, stream: int, n: int, s: float, n_ids: int, out=None) -> np.n
 
 
 def zipf_lognormal_mix(seed: int, n: int, zipf_frac: float, s: float, n_ids: int, mu: float, sigma: float,
-                       out=None) -> np.ndarray:
+                       out=None, hashed: bool = False) -> np.ndarray:
     """Per element: a Zipf(s) rank over [1, n_ids] with probability zipf_frac, else
-    floor(exp(N(mu, sigma^2))) redrawn until it is below 2^64."""
+    floor(exp(N(mu, sigma^2))) redrawn until it is below 2^64.  hashed: each
+    Zipf rank r is replaced by mix64(r), the SplitMix64 output function (a
+    bijection of 64-bit words), which keeps the multiplicities but spreads the
+    ranks over the whole key range."""
     a = np.empty(n, dtype=np.uint64) if out is None else out
     _load().sbhgen_zipf_lognormal_mix(seed, n, float(zipf_frac), float(s), n_ids, float(mu), float(sigma),
-                                      _ptr(a), _threads())
+                                      _ptr(a), _threads(), int(bool(hashed)))
     return a
 
 

@@ -141,6 +141,7 @@ typedef struct {
     double zipf_frac;
     zipf_t z;
     double mu, sigma;
+    int hashed;  /* Zipf ranks passed through the bijection sm64 */
     uint64_t* out;
 } mix_ctx;
 
@@ -150,17 +151,23 @@ static void mix_range(void* p, uint64_t a, uint64_t b) {
     mix_ctx* c = (mix_ctx*)p;
     for (uint64_t i = a; i < b; ++i) {
         double sel = unif01(draw(c->seed, ST_SELECT, i, 0));
-        c->out[i] = sel < c->zipf_frac ? zipf_draw(&c->z, c->seed, ST_ZIPF, i)
-                                       : lognormal_u64(c->mu, c->sigma, c->seed, ST_LOGN, i);
+        if (sel < c->zipf_frac) {
+            const uint64_t r = zipf_draw(&c->z, c->seed, ST_ZIPF, i);
+            c->out[i] = c->hashed ? sm64(r) : r;
+        } else {
+            c->out[i] = lognormal_u64(c->mu, c->sigma, c->seed, ST_LOGN, i);
+        }
     }
 }
 
 /* Mixture of Zipf(s) ranks over [1, zipf_n] (weight zipf_frac) and
- * floor(lognormal(mu, sigma)) below 2^64 (weight 1 - zipf_frac). */
+ * floor(lognormal(mu, sigma)) below 2^64 (weight 1 - zipf_frac).  With hashed,
+ * a Zipf rank r becomes sm64(r) (a bijection of the 64-bit words: the same
+ * multiplicities, spread over the whole key range). */
 void sbhgen_zipf_lognormal_mix(uint64_t seed, uint64_t n, double zipf_frac, double s, uint64_t zipf_n,
-                               double mu, double sigma, uint64_t* out, int nthreads) {
+                               double mu, double sigma, uint64_t* out, int nthreads, int hashed) {
     mix_ctx c;
-    c.seed = seed; c.zipf_frac = zipf_frac; c.mu = mu; c.sigma = sigma; c.out = out;
+    c.seed = seed; c.zipf_frac = zipf_frac; c.mu = mu; c.sigma = sigma; c.out = out; c.hashed = hashed;
     zipf_init(&c.z, s, zipf_n);
     parallel_for(n, nthreads, mix_range, &c);
 }

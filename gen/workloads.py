@@ -32,10 +32,12 @@ def tumbling_window(n: int = 1_000_000, key_bits: int = 20, seed: int = SEED_TUM
 
 
 def mixed_keys(n: int = 256_000_000, seed: int = SEED_MIXED, zipf_frac: float = 0.7, s: float = 1.1,
-               n_ids: int = 1 << 24, mu: float = 30.0, sigma: float = 4.0, out=None) -> np.ndarray:
+               n_ids: int = 1 << 24, mu: float = 30.0, sigma: float = 4.0, out=None, hashed: bool = False) -> np.ndarray:
     """Skewed 64-bit keys: 70% Zipf(1.1) ranks over 2^24 ids, 30%
-    floor(lognormal(30, 4)) redrawn until below 2^64."""
-    return zipf_lognormal_mix(seed, n, zipf_frac, s, n_ids, mu, sigma, out=out)
+    floor(lognormal(30, 4)) redrawn until below 2^64.  hashed: the Zipf ranks
+    pass through mix64 (the robustness variant: same multiplicities, keys
+    spread over all 64 bits)."""
+    return zipf_lognormal_mix(seed, n, zipf_frac, s, n_ids, mu, sigma, out=out, hashed=hashed)
 
 
 def batched_windows(n_windows: int = 4096, n_streams: int = 64, seed: int = SEED_BATCHED,

@@ -314,8 +314,9 @@ int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, cons
  * w3[32], b3.  Its input is a key's feature x(k) = (m + f / 2^17) / 64, m the
  * index of the highest set bit and f the 17 bits below it (x(0) = 0). */
 #define SBH_MLP_PARAMS 1153
-#define SBH_LEARNED_MODEL_BYTES 16384
+#define SBH_LEARNED_MODEL_BYTES 139264
 #define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
+#define SBH_LEARNED_MAX_HEAVY 16384 /* heavy keys a model holds */
 #define SBH_LEARNED_STATS 10
 
 /* y[i] = MLP(x[i]) for i < m.  No scratch. */
@@ -331,19 +332,27 @@ int sbh_mlp_grad(const float* d_params, const float* d_x, const float* d_t, uint
 /* Fits a model to a key sample (d_samples, m keys standing for n_rows rows,
  * e.g. every 100th row from sbh_kpa_extract).  Steps:
  *  1. sort the sample;
- *  2. heavy cells: an exact cell (one key value: key 0, or a key below 2^11)
- *     whose sample count times n_rows exceeds (SBH_LEARNED_CAPACITY / 2)
- *     times m gets a dedicated bucket; its samples leave the training set;
+ *  2. heavy keys: a key value whose sample count times n_rows exceeds
+ *     (SBH_LEARNED_CAPACITY / 2) times m gets a dedicated bucket (the
+ *     smallest SBH_LEARNED_MAX_HEAVY such keys, if there are more); its
+ *     samples leave the training set;
  *  3. training set of m' rows: row r takes the sorted non-heavy sample
  *     j = (r * P) mod m' (P = first integer >= 2654435761 mod m' coprime
  *     with m'), input x(key), target (#samples < key + #samples <= key) / 2m';
  *  4. `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, rate lr) on batches of
  *     `batch` rows, step j using rows (j * batch + q) mod m', starting from
- *     d_init_params.  batch is a multiple of 128, at most 32768.
+ *     d_init_params, or, when it is NULL, from the network that interpolates
+ *     the training set's CDF linearly between 33 quantiles (knot i: sorted
+ *     non-heavy sample floor(i (m' - 1) / 32), at its feature and CDF target;
+ *     knots of equal feature merge, keeping the later target; first-layer
+ *     unit u kinks at knot u, the second layer is the identity, the output
+ *     weights are the changes of slope).  batch is a multiple of 128, at most
+ *     32768.
  * d_model (SBH_LEARNED_MODEL_BYTES, device) receives the weights and the
- * heavy cells.  d_losses (nullable, `steps` floats) receives each step's
- * batch loss before its update; d_train_x / d_train_t (nullable, m floats
- * each) receive the training set (the first m' entries are meaningful).
+ * heavy keys (ascending).  d_losses (nullable, `steps` floats) receives each
+ * step's batch loss before its update; d_train_x / d_train_t (nullable, m
+ * floats each) receive the training set (the first m' entries are
+ * meaningful).
  * Scratch: about 32 m bytes plus the sort scratch for m. */
 int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, const float* d_init_params,
                       int steps, int batch, float lr, void* d_model, float* d_losses, float* d_train_x,
@@ -356,7 +365,7 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * is identical to sbh_kpa_sort's; input and output must not alias.  The
  * call synchronises `stream` once (the overflow size decides the last step).
  * h_stats (nullable, host, SBH_LEARNED_STATS values): bucket ids, heavy
- * cells, buckets sorted in shared memory, one-key buckets, heavy buckets,
+ * keys, buckets sorted in shared memory, one-key buckets, heavy buckets,
  * overflow buckets, overflow rows, largest bucket, buckets sorted by radix
  * passes in shared memory (their sub-buckets were too uneven for the
  * counting placement), and their rows.

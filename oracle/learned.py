@@ -1,16 +1,20 @@
 """ORACLE -- test infrastructure only.
 
-Plain statement of the learned partitioner's data preparation: which cells of
-key space get a dedicated bucket (heavy keys), and the training set the
-network is fitted to.  The sort that uses the partition is pinned by the plain
+Plain statement of the learned partitioner's data preparation: which key
+values get a dedicated bucket (heavy keys), and the training set the network
+is fitted to.  The sort that uses the partition is pinned by the plain
 sort (its output must be identical); these functions pin the pieces the CUDA
 path computes on the way.
 
 Cells.  Key 0 is cell 0.  A key k >= 1 with highest set bit m lies in cell
 1 + 1024 m + (the 10 bits just below bit m); the 32 bits below those are its
 offset inside the cell.  A cell with m <= 10 holds exactly one key value
-("exact" cell).  A cell is heavy when it is exact and its sample count,
-scaled to the rows the sample stands for, exceeds half the bucket capacity.
+("exact" cell).
+
+Heavy keys.  A key value is heavy when its sample count, scaled to the rows
+the sample stands for, exceeds half the bucket capacity: count * n_rows >
+(capacity / HEAVY_DIV) * m.  The heavy keys are taken in ascending order, at most
+MAX_HEAVY of them (the smallest, if there are more).
 
 Training set.  The non-heavy samples, sorted; row r of the set takes sorted
 sample j = (r * P) mod m', with P the first integer >= 2654435761 mod m'
@@ -28,6 +32,8 @@ from . import mlp
 
 NCELL = 1 + 64 * 1024
 EXACT_MAX_MSB = 10
+MAX_HEAVY = 16384
+HEAVY_DIV = 2
 
 
 def cell_of(keys) -> np.ndarray:
@@ -45,18 +51,15 @@ def cell_is_exact(c: int) -> bool:
     return c == 0 or (c - 1) // 1024 <= EXACT_MAX_MSB
 
 
-def heavy_cells(sample, n_rows: int, capacity: int) -> np.ndarray:
-    """Boolean mask over the NCELL cells."""
+def heavy_keys(sample, n_rows: int, capacity: int) -> np.ndarray:
+    """The heavy key values, ascending (uint64), at most MAX_HEAVY."""
     sample = np.asarray(sample, dtype=np.uint64)
     m = sample.size
-    heavy = np.zeros(NCELL, dtype=bool)
-    if m == 0:
-        return heavy
-    counts = np.bincount(cell_of(sample), minlength=NCELL)
-    for c in np.nonzero(counts)[0]:
-        if cell_is_exact(int(c)) and counts[c] * n_rows > (capacity // 2) * m:
-            heavy[c] = True
-    return heavy
+    counts = {}
+    for k in sample.tolist():
+        counts[k] = counts.get(k, 0) + 1
+    heavy = sorted(k for k, c in counts.items() if c * n_rows > (capacity // HEAVY_DIV) * m)
+    return np.array(heavy[:MAX_HEAVY], dtype=np.uint64)
 
 
 def stride_multiplier(m: int) -> int:
@@ -69,9 +72,9 @@ def stride_multiplier(m: int) -> int:
 def training_set(sample, n_rows: int, capacity: int):
     """(x, t) in training order, as float64."""
     sample = np.asarray(sample, dtype=np.uint64)
-    heavy = heavy_cells(sample, n_rows, capacity)
+    heavy = heavy_keys(sample, n_rows, capacity)
     srt = np.sort(sample)
-    keep = ~heavy[cell_of(srt)]
+    keep = ~np.isin(srt, heavy)
     nh = srt[keep]
     m = nh.size
     if m == 0:

@@ -128,3 +128,43 @@ def train(p0, x, t, steps, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         p, m, v = adam_step(p, g, m, v, j + 1, lr, beta1, beta2, eps)
         losses.append(loss(p, x, t))
     return p, losses
+
+
+def quantile_init(nh_sorted) -> np.ndarray:
+    """Parameters that make the network the piecewise-linear interpolation of
+    the training set's CDF at 33 quantiles (the start when no initial weights
+    are given).  With m' sorted non-heavy samples, knot i (0..32) is sample
+    j = floor(i (m' - 1) / 32): x = feature(key), F = its CDF target
+    (#samples < key + #samples <= key) / (2 m').  Knots with the x of the
+    previous kept knot are merged into it (it takes the later F).  Hidden unit
+    u of the first layer kinks at kept knot u (W1 = 1, b1 = -x_u); the second
+    layer passes it on (W2 = I, b2 = 0); w3_u is the change of slope at knot u
+    and b3 the first knot's F, so the output passes through every kept knot.
+    Units without a segment are zero."""
+    nh = np.asarray(nh_sorted, dtype=np.uint64)
+    m = nh.size
+    p = np.zeros(N_PARAMS, dtype=np.float64)
+    if m == 0:
+        return p
+    xs, fs = [], []
+    for i in range(H + 1):
+        j = (i * (m - 1)) // H
+        k = nh[j]
+        lt = int(np.searchsorted(nh, k, side="left"))
+        le = int(np.searchsorted(nh, k, side="right"))
+        x = float(feature(np.array([k], dtype=np.uint64))[0])
+        f = (lt + le) / (2.0 * m)
+        if xs and x <= xs[-1]:
+            fs[-1] = f
+        else:
+            xs.append(x)
+            fs.append(f)
+    W1, b1, W2, b2, w3 = (np.zeros(H), np.zeros(H), np.eye(H), np.zeros(H), np.zeros(H))
+    prev = 0.0
+    for u in range(len(xs) - 1):
+        slope = (fs[u + 1] - fs[u]) / (xs[u + 1] - xs[u])
+        W1[u], b1[u], w3[u] = 1.0, -xs[u], slope - prev
+        prev = slope
+    p[SLICES["W1"]], p[SLICES["b1"]], p[SLICES["W2"]] = W1, b1, W2.reshape(-1)
+    p[SLICES["b2"]], p[SLICES["w3"]], p[SLICES["b3"]] = b2, w3, fs[0]
+    return p

@@ -8,9 +8,9 @@
 // 1 + 1024 m + (the 10 bits below bit m); the next 32 bits are its offset in
 // the cell.  Cells with m <= 10 hold exactly one key value.
 //
-// Training (sbh_learned_train).  The sample is sorted; exact cells whose
+// Training (sbh_learned_train).  The sample is sorted; key values whose
 // sample count stands for more than half a bucket are heavy and get one
-// dedicated bucket; the other samples form the training set: row r takes the
+// dedicated bucket each; the other samples form the training set: row r takes the
 // sorted non-heavy sample (r * P) mod m', input x = feature(key) (exact in
 // FP32), target = midpoint of the key's CDF step among those samples.  A
 // 1-32-32-1 ReLU network is fitted by Adam on mean squared error; G CTAs
@@ -19,13 +19,18 @@
 // gradients in a fixed order and applies Adam to it, and meet again.
 //
 // Partition (sbh_kpa_sort_learned).  F(c) = the prefix maximum of the
-// clamped network output at each cell's lowest key; cell c's first bucket is
-// floor(F(c) * NB) plus two per heavy cell before it; a heavy cell's keys all
-// go to its own bucket; other keys are spread over their cell's buckets by
-// their 32-bit offset.  Bucket ids are therefore non-decreasing in the key
-// (integer arithmetic only), so a stable sort by bucket id followed by a sort
-// inside each bucket sorts the KPA.  Buckets of one key are already in ptr
-// order; buckets above the shared-memory capacity go to the plain radix sort.
+// clamped network output at each cell's lowest key; cell c spans
+// y(c) = floor(F(c + 1) NB) - floor(F(c) NB) spread buckets plus two per
+// heavy key in it, and its first bucket t(c) is floor(F(c) NB) plus two per
+// heavy key in the cells before it.  Key k of cell c goes to bucket
+//   t(c) + floor(offset(k) * y(c) / 2^32) + 2 * (heavy keys of c below k)
+//        + (1 if k is heavy),
+// so a heavy key has a bucket of its own (its neighbours' buckets differ by
+// the parity of the heavy term).  Bucket ids are therefore non-decreasing in
+// the key (integer arithmetic only), so a stable sort by bucket id followed
+// by a sort inside each bucket sorts the KPA.  Buckets of one key are already
+// in ptr order; buckets above the shared-memory capacity go to the plain
+// radix sort.
 #include <algorithm>
 #include <vector>
 
@@ -38,17 +43,30 @@ constexpr int kH = 32;
 constexpr int kNP = 4 * kH + kH * kH + 1;  // 1153
 constexpr int oW1 = 0, oB1 = kH, oW2 = 2 * kH, oB2 = 2 * kH + kH * kH, oW3 = 3 * kH + kH * kH, oB3 = 4 * kH + kH * kH;
 constexpr uint32_t kNCell = 1 + 64 * 1024;
-constexpr uint32_t kHeavyWords = (kNCell + 31) / 32;
+constexpr uint32_t kMaxHeavy = SBH_LEARNED_MAX_HEAVY;
+constexpr uint32_t kHeavyDiv = 2;
 
 struct Model {
     float params[kNP];
     uint32_t capacity;     // rows a bucket may hold to be sorted in shared memory
-    uint32_t heavy_count;  // heavy cells
+    uint32_t heavy_count;  // heavy keys (at most kMaxHeavy once trained)
     uint32_t m_train;      // rows of the training set
-    uint32_t reserved;
-    uint32_t heavy_bits[kHeavyWords];
+    uint32_t reserved[2];
+    uint64_t heavy_keys[kMaxHeavy];  // ascending
 };
 static_assert(sizeof(Model) <= SBH_LEARNED_MODEL_BYTES, "model blob");
+static_assert(offsetof(Model, heavy_keys) == 4 * (kNP + 5), "model layout");
+
+// Index of key k in the model's heavy keys, or -1 (binary search).
+__device__ __forceinline__ int heavy_index(const Model* __restrict__ model, uint64_t k) {
+    uint32_t lo = 0, hi = min(model->heavy_count, kMaxHeavy);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (model->heavy_keys[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < min(model->heavy_count, kMaxHeavy) && model->heavy_keys[lo] == k) ? static_cast<int>(lo) : -1;
+}
 
 // ------------------------------------------------------------------ key features
 __device__ __forceinline__ float key_feature(uint64_t k) {
@@ -373,47 +391,43 @@ __global__ void iota_kernel(uint32_t* p, uint64_t m) {
     if (i < m) p[i] = static_cast<uint32_t>(i);
 }
 
-// Heavy cells from the sorted sample: the first sample of each exact cell
-// measures its run by binary search and marks the cell.
-__global__ void heavy_kernel(const uint64_t* __restrict__ srt, uint64_t m, uint64_t n_rows, uint32_t capacity,
-                             Model* __restrict__ model) {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    uint32_t f;
-    const uint32_t c = key_cell(srt[i], &f);
-    if (!cell_exact(c)) return;
-    if (i > 0) {
-        uint32_t pf;
-        if (key_cell(srt[i - 1], &pf) == c) return;
+// Heavy keys from the sorted sample: the first sample of each run of equal
+// keys measures the run by binary search; a run of count samples is heavy
+// when count * n_rows > (capacity / kHeavyDiv) * m: a key of more than half
+// a bucket gets a bucket of its own (an eighth measured the same: fewer rows
+// left to sort, but more ids that take the heavy-cell path).
+struct HeavyRunStart {
+    const uint64_t* srt;
+    uint64_t m, n_rows;
+    uint32_t capacity;
+    __device__ __forceinline__ bool operator()(uint64_t i) const {
+        const uint64_t key = srt[i];
+        if (i > 0 && srt[i - 1] == key) return false;
+        uint64_t lo = i, hi = m;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (srt[mid] <= key) lo = mid + 1;
+            else hi = mid;
+        }
+        return (unsigned __int128)(lo - i) * n_rows > (unsigned __int128)(capacity / kHeavyDiv) * m;
     }
-    // exact cell = one key value: its run ends at the first larger key
-    const uint64_t key = srt[i];
-    uint64_t lo = i, hi = m;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) / 2;
-        if (srt[mid] <= key) lo = mid + 1;
-        else hi = mid;
-    }
-    const uint64_t count = lo - i;
-    if ((unsigned __int128)count * n_rows > (unsigned __int128)(capacity / 2) * m) {
-        atomicOr(&model->heavy_bits[c >> 5], 1u << (c & 31));
-        atomicAdd(&model->heavy_count, 1u);
-    }
-}
+};
 
-__device__ __forceinline__ bool is_heavy(const uint32_t* bits, uint32_t c) { return (bits[c >> 5] >> (c & 31)) & 1u; }
+// Samples that are not heavy keys (the training set's rows).
+struct NotHeavy {
+    const uint64_t* srt;
+    const Model* model;
+    __device__ __forceinline__ bool operator()(uint64_t i) const { return heavy_index(model, srt[i]) < 0; }
+};
 
-// Compaction of the non-heavy samples: per-tile counts, one-CTA scan, scatter.
-__global__ void __launch_bounds__(kCompactTile) keep_count_kernel(const uint64_t* __restrict__ srt, uint64_t m,
-                                                                  const Model* __restrict__ model,
-                                                                  uint64_t* __restrict__ block_sums) {
+// Ordered compaction of the sorted samples that satisfy a predicate: per-tile
+// counts, one-CTA scan, scatter (the first cap of them are written).
+template <typename Pred>
+__global__ void __launch_bounds__(kCompactTile) compact_count_kernel(uint64_t m, Pred pred,
+                                                                     uint64_t* __restrict__ block_sums) {
     __shared__ uint32_t wsum[kCompactTile / 32];
     const uint64_t i = blockIdx.x * (uint64_t)kCompactTile + threadIdx.x;
-    uint32_t keep = 0;
-    if (i < m) {
-        uint32_t f;
-        keep = !is_heavy(model->heavy_bits, key_cell(srt[i], &f));
-    }
+    const uint32_t keep = i < m && pred(i);
     const uint32_t b = __popc(__ballot_sync(0xffffffffu, keep));
     if (lane_id() == 0) wsum[threadIdx.x / 32] = b;
     __syncthreads();
@@ -450,26 +464,21 @@ __global__ void __launch_bounds__(1024) scan_u64_kernel(uint64_t* __restrict__ v
     if (threadIdx.x == 0) *total32 = static_cast<uint32_t>(carry);
 }
 
-__global__ void __launch_bounds__(kCompactTile) keep_scatter_kernel(const uint64_t* __restrict__ srt, uint64_t m,
-                                                                    const Model* __restrict__ model,
-                                                                    const uint64_t* __restrict__ block_off,
-                                                                    uint64_t* __restrict__ nh) {
+template <typename Pred>
+__global__ void __launch_bounds__(kCompactTile) compact_scatter_kernel(const uint64_t* __restrict__ srt, uint64_t m,
+                                                                       Pred pred,
+                                                                       const uint64_t* __restrict__ block_off,
+                                                                       uint64_t* __restrict__ out, uint64_t cap) {
     __shared__ uint32_t wsum[kCompactTile / 32];
     const uint64_t i = blockIdx.x * (uint64_t)kCompactTile + threadIdx.x;
-    uint32_t keep = 0;
-    uint64_t key = 0;
-    if (i < m) {
-        uint32_t f;
-        key = srt[i];
-        keep = !is_heavy(model->heavy_bits, key_cell(key, &f));
-    }
+    const uint32_t keep = i < m && pred(i);
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
     if (lane_id() == 0) wsum[threadIdx.x / 32] = __popc(bal);
     __syncthreads();
     uint64_t off = block_off[blockIdx.x];
     for (uint32_t w = 0; w < threadIdx.x / 32; ++w) off += wsum[w];
     off += __popc(bal & lanemask_lt());
-    if (keep) nh[off] = key;
+    if (keep && off < cap) out[off] = srt[i];
 }
 
 __device__ __forceinline__ uint32_t gcd_u32(uint32_t a, uint32_t b) {
@@ -506,6 +515,62 @@ __global__ void trainset_kernel(const uint64_t* __restrict__ nh, const uint32_t*
     }
     X[r] = key_feature(key);
     T[r] = static_cast<float>(lt + lo) / (2.0f * static_cast<float>(mt));
+}
+
+// Start from the piecewise-linear interpolation of the training set's CDF at
+// 33 quantiles (when no initial weights are given).  Knot i is the sorted
+// non-heavy sample j = floor(i (m' - 1) / 32): x = feature(key), F = its CDF
+// target; a knot with the x of the previous kept knot merges into it (taking
+// the later F).  Unit u kinks at kept knot u (W1 = 1, b1 = -x_u), the second
+// layer passes it on (W2 = I), w3_u is the change of slope at knot u and b3
+// the first F, so the output passes through the kept knots.  One CTA.
+__global__ void quantile_init_kernel(const uint64_t* __restrict__ nh, const uint32_t* __restrict__ m_train,
+                                     float* __restrict__ params) {
+    __shared__ float qx[kH + 1], qf[kH + 1];
+    const uint32_t mt = *m_train;
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) params[i] = 0.f;
+    if (threadIdx.x <= kH && mt > 0) {
+        const uint32_t j = static_cast<uint32_t>((static_cast<uint64_t>(threadIdx.x) * (mt - 1)) / kH);
+        const uint64_t key = nh[j];
+        uint32_t lo = 0, hi = mt;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (nh[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t lt = lo;
+        hi = mt;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (nh[mid] <= key) lo = mid + 1;
+            else hi = mid;
+        }
+        qx[threadIdx.x] = key_feature(key);
+        qf[threadIdx.x] = static_cast<float>(lt + lo) / (2.0f * static_cast<float>(mt));
+    }
+    __syncthreads();
+    if (threadIdx.x != 0 || mt == 0) return;
+    float kx[kH + 1], kf[kH + 1];
+    int k = 0;
+    for (int i = 0; i <= kH; ++i) {
+        if (k > 0 && qx[i] <= kx[k - 1]) {
+            kf[k - 1] = qf[i];
+        } else {
+            kx[k] = qx[i];
+            kf[k] = qf[i];
+            ++k;
+        }
+    }
+    for (int u = 0; u < kH; ++u) params[oW2 + u * kH + u] = 1.f;
+    float prev = 0.f;
+    for (int u = 0; u + 1 < k; ++u) {
+        const float slope = (kf[u + 1] - kf[u]) / (kx[u + 1] - kx[u]);
+        params[oW1 + u] = 1.f;
+        params[oB1 + u] = -kx[u];
+        params[oW3 + u] = slope - prev;
+        prev = slope;
+    }
+    params[oB3] = kf[0];
 }
 
 // ------------------------------------------------------------------ training
@@ -625,42 +690,80 @@ __global__ void finish_model_kernel(const float* __restrict__ params, const uint
     if (threadIdx.x == 0) {
         model->capacity = capacity;
         model->m_train = *m_train;
+        model->heavy_count = min(model->heavy_count, kMaxHeavy);
     }
 }
 
 // ------------------------------------------------------------------ partition
 // Bucket id of a key (see the file comment).
-// One 8-byte entry per cell, so an id costs a single table load: x = the
-// cell's first bucket id, y = its number of buckets, or kHeavyCell.
+// One 8-byte entry per cell, so an id mostly costs a single table load:
+// x = the cell's first bucket id, y = its number of spread buckets; a cell
+// holding heavy keys has y = kHeavyCell and x = the index of its first heavy
+// key, under which hcells keeps (first bucket id, spread buckets, first heavy
+// key, heavy keys in the cell).  An exact cell (one key value) that is heavy
+// has y = kHeavyExact: its key's bucket is x + 1.
 constexpr uint32_t kHeavyCell = 0xFFFFFFFFu;
+constexpr uint32_t kHeavyExact = 0xFFFFFFFEu;
+
+// The id of key k (offset f) in a cell holding heavy keys.
+__device__ __forceinline__ uint32_t heavy_cell_id(const uint4* __restrict__ hcells,
+                                                  const uint64_t* __restrict__ hkeys, uint32_t idx, uint32_t f,
+                                                  uint64_t k) {
+    const uint4 h = hcells[idx];
+    uint32_t id = h.x + static_cast<uint32_t>((static_cast<uint64_t>(f) * h.y) >> 32);
+#pragma unroll 4
+    for (uint32_t j = 0; j < h.w; ++j) {  // no early exit: the loads are independent
+        const uint64_t hk = hkeys[h.z + j];
+        id += hk < k ? 2u : (hk == k ? 1u : 0u);
+    }
+    return id;
+}
 
 struct BucketValue {
-    const uint2* cells;  // kNCell + 1 entries
+    const uint2* cells;      // kNCell + 1 entries
+    const uint4* hcells;     // by first heavy key index
+    const uint64_t* hkeys;   // the model's heavy keys
     __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
         uint32_t f;
         const uint32_t c = key_cell(k, &f);
         const uint2 e = __ldg(cells + c);
-        if (e.y == kHeavyCell) return e.x + 1;
+        if (e.y >= kHeavyExact) return e.y == kHeavyExact ? e.x + 1 : heavy_cell_id(hcells, hkeys, e.x, f, k);
         return e.x + static_cast<uint32_t>((static_cast<uint64_t>(f) * e.y) >> 32);
     }
 };
 
 // The same ids from a 4-byte entry per cell (half the table, so more of it
-// stays in L1), usable when every id is below 2^16: first id in the low 16
-// bits, number of buckets (at most 2^16 - 2 then) or kHeavyCell16 in the high.
+// stays in L1), usable when every id is below 2^16: first id (or first heavy
+// key index) in the low 16 bits, spread buckets (at most 2^16 - 2 then) or
+// kHeavyCell16 / kHeavyExact16 in the high.
 constexpr uint32_t kHeavyCell16 = 0xFFFFu;
+constexpr uint32_t kHeavyExact16 = 0xFFFEu;
 
 struct BucketValue16 {
-    const uint32_t* cells;  // kNCell + 1 entries
+    const uint32_t* cells;   // kNCell + 1 entries
+    const uint4* hcells;
+    const uint64_t* hkeys;
     __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
         uint32_t f;
         const uint32_t c = key_cell(k, &f);
         const uint32_t e = __ldg(cells + c);
         const uint32_t x = e & 0xFFFFu, y = e >> 16;
-        if (y == kHeavyCell16) return x + 1;
+        if (y >= kHeavyExact16) return y == kHeavyExact16 ? x + 1 : heavy_cell_id(hcells, hkeys, x, f, k);
         return x + static_cast<uint32_t>((static_cast<uint64_t>(f) * y) >> 32);
     }
 };
+
+// Heavy keys per cell: their number and the index of the first (cell_hc
+// zeroed, cell_hidx filled with 0xFF bytes beforehand).
+__global__ void heavy_cells_kernel(const Model* __restrict__ model, uint32_t* __restrict__ cell_hc,
+                                   uint32_t* __restrict__ cell_hidx) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(model->heavy_count, kMaxHeavy)) return;
+    uint32_t f;
+    const uint32_t c = key_cell(model->heavy_keys[i], &f);
+    atomicAdd(&cell_hc[c], 1u);
+    atomicMin(&cell_hidx[c], i);
+}
 
 // The cell table is built over blocks of 1024 cells in two launches:
 // cell_cdf writes F and each block's maximum of F and number of heavy cells;
@@ -669,6 +772,7 @@ constexpr int kTblThreads = 1024;
 constexpr uint32_t kTblBlocks = (kNCell + 1 + kTblThreads - 1) / kTblThreads;
 
 __global__ void __launch_bounds__(kTblThreads) cell_cdf_kernel(const Model* __restrict__ model, float* __restrict__ F,
+                                                               const uint32_t* __restrict__ cell_hc,
                                                                float* __restrict__ bmax,
                                                                uint32_t* __restrict__ bheavy) {
     __shared__ float P[kNP];
@@ -682,7 +786,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_cdf_kernel(const Model* __re
     if (c <= kNCell) {
         f = fminf(fmaxf(mlp_eval(P, cell_x(c)), 0.f), 1.f);
         F[c] = f;
-        h = c < kNCell && is_heavy(model->heavy_bits, c);
+        h = c < kNCell ? cell_hc[c] : 0u;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -710,10 +814,14 @@ __global__ void __launch_bounds__(kTblThreads) cell_cdf_kernel(const Model* __re
 }
 
 // Cell c's first bucket id is t(c) = floor(max(F[0..c]) * nb) + 2 * (heavy
-// cells before c); a heavy cell's bucket t + 1 is marked in the bitmap of
-// heavy buckets; nbid receives t(kNCell) + 1, the bound on bucket ids.
+// keys in the cells before c); each heavy key's own bucket is marked in the
+// bitmap of heavy buckets; nbid receives t(kNCell) + 1, the bound on bucket
+// ids.
 __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __restrict__ model,
                                                                  const float* __restrict__ F,
+                                                                 const uint32_t* __restrict__ cell_hc,
+                                                                 const uint32_t* __restrict__ cell_hidx,
+                                                                 uint4* __restrict__ hcells,
                                                                  const float* __restrict__ bmax,
                                                                  const uint32_t* __restrict__ bheavy, uint32_t nb,
                                                                  uint2* __restrict__ cells,
@@ -743,7 +851,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
         }
     }
     const float f = c <= kNCell ? F[c] : 0.f;
-    const uint32_t hv = c < kNCell && is_heavy(model->heavy_bits, c);
+    const uint32_t hv = c < kNCell ? cell_hc[c] : 0u;  // heavy keys in this cell
     float m = f;
     uint32_t h = hv;
 #pragma unroll
@@ -767,7 +875,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
         bh += wc[w];
     }
     const float run_max = fmaxf(bm, m);  // max of F[0..c]
-    const uint32_t heavy_incl = bh + h;  // heavy cells in [0, c]
+    const uint32_t heavy_incl = bh + h;  // heavy keys in the cells [0, c]
     const float fnb = static_cast<float>(nb);
     const uint32_t t = static_cast<uint32_t>(floorf(run_max * fnb)) + 2u * (heavy_incl - hv);
     // the next cell's first id (the same arithmetic as its own thread's)
@@ -775,14 +883,30 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
     if (lane == 31) f_next = c + 1 <= kNCell ? F[c + 1] : 0.f;
     const uint32_t t_next = static_cast<uint32_t>(floorf(fmaxf(run_max, f_next) * fnb)) + 2u * heavy_incl;
     if (c > kNCell) return;
-    if (hv) atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
     if (c == kNCell) *nbid = t + 1;
+    const uint32_t y = c == kNCell ? 0u : t_next - t - 2u * hv;  // spread buckets
     uint2 e;
-    e.x = t;
-    e.y = c == kNCell ? 0u : (hv ? kHeavyCell : t_next - t);
+    if (hv && cell_exact(c)) {  // one key value, heavy: bucket t + 1
+        e = make_uint2(t, kHeavyExact);
+        atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
+    } else if (hv) {
+        const uint32_t idx = cell_hidx[c];
+        hcells[idx] = make_uint4(t, y, idx, hv);
+        e = make_uint2(idx, kHeavyCell);
+        for (uint32_t j = 0; j < hv; ++j) {  // the heavy keys' own buckets
+            uint32_t fh;
+            key_cell(model->heavy_keys[idx + j], &fh);
+            const uint32_t id = t + static_cast<uint32_t>((static_cast<uint64_t>(fh) * y) >> 32) + 2u * j + 1u;
+            atomicOr(&heavy_bucket_bits[id >> 5], 1u << (id & 31));
+        }
+    } else {
+        e = make_uint2(t, y);
+    }
     cells[c] = e;
-    // meaningful only when every id is below 2^16 (the carried-id path)
-    cells16[c] = (e.x & 0xFFFFu) | ((e.y == kHeavyCell ? kHeavyCell16 : (e.y & 0xFFFFu)) << 16);
+    // meaningful only when every id is below 2^16 (the carried-id path,
+    // where spread counts stay below kHeavyExact16)
+    const uint32_t y16 = e.y == kHeavyCell ? kHeavyCell16 : (e.y == kHeavyExact ? kHeavyExact16 : (e.y & 0xFFFFu));
+    cells16[c] = (e.x & 0xFFFFu) | (y16 << 16);
 }
 
 // bstart[b] = first row whose bucket id is >= b, for b in [0, nbid].  Each
@@ -1513,9 +1637,12 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
 
 struct SortLearnedScratch {
     float* bmax;            // per block of cells: maximum of F
-    uint32_t* bheavy;       // per block of cells: heavy cells
+    uint32_t* bheavy;       // per block of cells: heavy keys
     uint2* cells;           // kNCell + 1
     uint32_t* cells16;      // kNCell + 1
+    uint32_t* cell_hc;      // kNCell + 1: heavy keys per cell (zeroed)
+    uint32_t* cell_hidx;    // kNCell + 1: first heavy key per cell (0xFF bytes)
+    uint4* hcells;          // kMaxHeavy: cells holding heavy keys, by first heavy key
     float* F;               // kNCell + 1
     uint32_t* heavy_bucket_bits;
     uint32_t* bstart;       // max ids + 1
@@ -1544,6 +1671,9 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.bheavy = c.take<uint32_t>(kTblBlocks);
     t.cells = c.take<uint2>(kNCell + 1);
     t.cells16 = c.take<uint32_t>(kNCell + 1);
+    t.cell_hc = c.take<uint32_t>(kNCell + 1);
+    t.cell_hidx = c.take<uint32_t>(kNCell + 1);
+    t.hcells = c.take<uint4>(kMaxHeavy);
     t.F = c.take<float>(kNCell + 1);
     t.list = c.take<uint32_t>(ids);
     t.bagg = c.take<uint2>(ids / 1024 + 1);
@@ -1620,7 +1750,7 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     bool done = false;
     int rc = scratch_check(d_scratch, scratch_bytes, train_carve(nullptr, m).total, &done);
     if (rc || done) return rc;
-    if (m == 0 || !d_samples || !d_init_params || !d_model) { set_error("empty sample or null pointer"); return SBH_EINVAL; }
+    if (m == 0 || !d_samples || !d_model) { set_error("empty sample or null pointer"); return SBH_EINVAL; }
     if (steps < 0 || batch < kTrainCtas || batch % kTrainCtas || batch / kTrainCtas > kMaxSlice) {
         set_error("batch must be a multiple of %d in [%d, %d]", kTrainCtas, kTrainCtas, kTrainCtas * kMaxSlice);
         return SBH_EINVAL;
@@ -1632,7 +1762,8 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     SBH_CUDA(cudaMemsetAsync(t.bar, 0, 2 * sizeof(uint32_t), s));
     SBH_CUDA(cudaMemsetAsync(t.adam_m, 0, kNP * sizeof(float), s));
     SBH_CUDA(cudaMemsetAsync(t.adam_v, 0, kNP * sizeof(float), s));
-    SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (d_init_params)
+        SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // sort the sample
     const unsigned gm = (unsigned)((m + 255) / 256);
     SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.i_ptrs, m));
@@ -1640,19 +1771,34 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     rc = sort_by_value(d_samples, t.i_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions,
                        "learned_sample");
     if (rc) return rc;
-    // heavy cells, non-heavy compaction, training rows
-    SBH_TIMED("learned_heavy", s, heavy_kernel<<<gm, 256, 0, s>>>(t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY, model));
-    SBH_LAUNCHED();
+    // heavy keys (in key order, the first kMaxHeavy), the non-heavy samples,
+    // training rows
     const uint32_t nb = (uint32_t)((m + kCompactTile - 1) / kCompactTile);
-    SBH_TIMED("learned_keep", s, keep_count_kernel<<<nb, kCompactTile, 0, s>>>(t.s_keys, m, model, t.block_sums));
+    const HeavyRunStart heavy_pred{t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY};
+    SBH_TIMED("learned_heavy", s,
+              compact_count_kernel<HeavyRunStart><<<nb, kCompactTile, 0, s>>>(m, heavy_pred, t.block_sums));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_heavy", s, scan_u64_kernel<<<1, 1024, 0, s>>>(t.block_sums, nb, &model->heavy_count));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_heavy", s,
+              compact_scatter_kernel<HeavyRunStart><<<nb, kCompactTile, 0, s>>>(t.s_keys, m, heavy_pred, t.block_sums,
+                                                                               model->heavy_keys, kMaxHeavy));
+    SBH_LAUNCHED();
+    const NotHeavy keep_pred{t.s_keys, model};
+    SBH_TIMED("learned_keep", s, compact_count_kernel<NotHeavy><<<nb, kCompactTile, 0, s>>>(m, keep_pred, t.block_sums));
     SBH_LAUNCHED();
     SBH_TIMED("learned_keep_scan", s, scan_u64_kernel<<<1, 1024, 0, s>>>(t.block_sums, nb, t.m_train));
     SBH_LAUNCHED();
     SBH_TIMED("learned_keep", s,
-              keep_scatter_kernel<<<nb, kCompactTile, 0, s>>>(t.s_keys, m, model, t.block_sums, t.nh));
+              compact_scatter_kernel<NotHeavy><<<nb, kCompactTile, 0, s>>>(t.s_keys, m, keep_pred, t.block_sums, t.nh,
+                                                                          m));
     SBH_LAUNCHED();
     SBH_TIMED("learned_trainset", s, trainset_kernel<<<gm, 256, 0, s>>>(t.nh, t.m_train, t.X, t.T));
     SBH_LAUNCHED();
+    if (!d_init_params) {
+        SBH_TIMED("learned_init", s, quantile_init_kernel<<<1, 64, 0, s>>>(t.nh, t.m_train, t.params));
+        SBH_LAUNCHED();
+    }
     if (d_train_x) SBH_CUDA(cudaMemcpyAsync(d_train_x, t.X, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (d_train_t) SBH_CUDA(cudaMemcpyAsync(d_train_t, t.T, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // train
@@ -1704,26 +1850,34 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     SBH_CUDA(cudaMemcpyAsync(&heavy, &model->heavy_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SBH_CUDA(cudaStreamSynchronize(s));
     uint64_t nb64 = learned_nb(n);
+    // (a cell's spread count stays below the 16-bit markers 0xFFFE, 0xFFFF)
     if (heavy < 16384) {
-        const uint64_t fit16 = 65536ull - 2ull * heavy - 2ull;
+        const uint64_t fit16 = std::min<uint64_t>(65536ull - 2ull * heavy - 2ull, 65533ull);
         if (nb64 > fit16 && fit16 >= nb64 - nb64 / 4) nb64 = fit16;
     }
     const uint32_t nb = (uint32_t)nb64;
-    const bool carry = nb64 + 2ull * heavy + 2ull <= 65536ull;
+    const bool carry = nb64 + 2ull * heavy + 2ull <= 65536ull && nb64 <= 65533ull;
     uint32_t* nbid = t.small + 0;
     uint32_t* counter = t.small + 1;
     uint32_t* nlist = t.small + 2;
     uint32_t* rows_total = t.small + 3;
-    SBH_TIMED("learned_cdf", s, cell_cdf_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.bmax, t.bheavy));
+    SBH_CUDA(cudaMemsetAsync(t.cell_hc, 0, (kNCell + 1) * sizeof(uint32_t), s));
+    SBH_CUDA(cudaMemsetAsync(t.cell_hidx, 0xFF, (kNCell + 1) * sizeof(uint32_t), s));
+    SBH_TIMED("learned_heavy_cells", s,
+              heavy_cells_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(model, t.cell_hc, t.cell_hidx));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_cdf", s,
+              cell_cdf_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.cell_hc, t.bmax, t.bheavy));
     SBH_LAUNCHED();
     SBH_TIMED("learned_table", s,
-              cell_table_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.bmax, t.bheavy, nb, t.cells,
-                                                                   t.cells16, t.heavy_bucket_bits, nbid));
+              cell_table_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.cell_hc, t.cell_hidx, t.hcells,
+                                                                   t.bmax, t.bheavy, nb, t.cells, t.cells16,
+                                                                   t.heavy_bucket_bits, nbid));
     SBH_LAUNCHED();
-    const BucketValue fn{t.cells};
+    const BucketValue fn{t.cells, t.hcells, model->heavy_keys};
     if (carry) {
         rc = sort_by_carried_ids(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s,
-                                 BucketValue16{t.cells16}, nbid, t.bstart);
+                                 BucketValue16{t.cells16, t.hcells, model->heavy_keys}, nbid, t.bstart);
         if (rc) return rc;
     } else {
         // stable scatter by bucket id computed from the key (ids below 2^24)

@@ -26,9 +26,10 @@ TOPK_PAD_VAL = 0
 TOPK_PAD_PTR = 0xFFFFFFFF
 TOPK_MAX_K = 8
 MLP_PARAMS = 1153
-LEARNED_MODEL_BYTES = 16384
+LEARNED_MODEL_BYTES = 139264
 LEARNED_CAPACITY = 8192
-LEARNED_STATS = ("bucket_ids", "heavy_cells", "sorted_buckets", "one_key_buckets", "heavy_buckets",
+LEARNED_MAX_HEAVY = 16384
+LEARNED_STATS = ("bucket_ids", "heavy_keys", "sorted_buckets", "one_key_buckets", "heavy_buckets",
                  "overflow_buckets", "overflow_rows", "largest_bucket", "radix_buckets", "radix_rows")
 
 _ERRNAMES = {1: "SBH_EINVAL", 2: "SBH_ENOSPACE", 3: "SBH_ETIMEOUT", 4: "SBH_ECUDA"}

@@ -110,14 +110,18 @@ def test_cells_bit_definition():
     assert np.all(np.diff(learned.cell_of(ks)) >= 0)
 
 
-def test_heavy_cells_threshold():
+def test_heavy_keys_threshold():
     # 1000 samples standing for 100000 rows; capacity 2000 -> heavy above 1000 rows, i.e. > 10 samples
-    s = np.concatenate([np.full(11, 7), np.full(10, 9), np.full(50, 5000), np.arange(100, 1029)]).astype(np.uint64)
-    h = learned.heavy_cells(s, 100_000, 2000)
-    c = learned.cell_of(np.array([7, 9, 5000], dtype=np.uint64))
-    assert h[c[0]] and not h[c[1]]
-    assert not h[c[2]]  # 5000 is not in an exact cell
-    assert h.sum() == 1
+    s = np.concatenate([np.full(11, 7), np.full(10, 9), np.full(50, 5000), np.full(12, 1 << 60),
+                        np.arange(100, 1017)]).astype(np.uint64)
+    h = learned.heavy_keys(s, 100_000, 2000)
+    # any key value counts, in or out of an exact cell; 9 (10 samples) is at the threshold
+    assert h.tolist() == [7, 5000, 1 << 60]
+    assert not learned.cell_is_exact(int(learned.cell_of(np.array([5000], dtype=np.uint64))[0]))
+    # at most MAX_HEAVY, the smallest keys
+    many = np.repeat(np.arange(1, learned.MAX_HEAVY + 11, dtype=np.uint64), 3)
+    hm = learned.heavy_keys(many, many.size * 1000, 4000)  # 3 samples = 3000 rows > 2000
+    assert hm.size == learned.MAX_HEAVY and hm[0] == 1 and hm[-1] == learned.MAX_HEAVY
 
 
 def test_training_set_is_a_permutation_with_cdf_targets():
@@ -137,3 +141,28 @@ def test_training_set_is_a_permutation_with_cdf_targets():
     assert x2.size == 3
     # the targets are recomputed over the remaining samples {1, 3, 9}
     assert sorted(t2.tolist()) == [1 / 6, 3 / 6, 5 / 6]
+
+
+def test_quantile_init_passes_through_its_knots():
+    # the network is the interpolation of the CDF through the kept knots; merged
+    # knots (equal x) keep the later CDF value
+    keys = np.sort(np.concatenate([np.full(50, 3), np.arange(1000, 1300) ** 2, np.full(40, 1 << 40)])).astype(np.uint64)
+    p = mlp.quantile_init(keys)
+    m = keys.size
+    seen = {}
+    for i in range(mlp.H + 1):
+        k = keys[(i * (m - 1)) // mlp.H]
+        x = float(mlp.feature(np.array([k], np.uint64))[0])
+        f = (np.searchsorted(keys, k, "left") + np.searchsorted(keys, k, "right")) / (2.0 * m)
+        seen[x] = f
+    xs = np.array(sorted(seen))
+    y, _ = mlp.forward(p, xs)
+    assert np.allclose(y, [seen[x] for x in xs], rtol=0, atol=1e-12)
+    assert len(seen) < mlp.H + 1  # the repeated keys merged knots
+    # between knots the output is linear (the midpoint of two kept knots)
+    ym, _ = mlp.forward(p, (xs[:-1] + xs[1:]) / 2)
+    fs = np.array([seen[x] for x in xs])
+    assert np.allclose(ym, (fs[:-1] + fs[1:]) / 2, atol=1e-12)
+    # a single key value: the constant network
+    p1 = mlp.quantile_init(np.full(10, 7, dtype=np.uint64))
+    assert np.allclose(mlp.forward(p1, np.array([0.0, 0.5, 1.0]))[0], 0.5)
