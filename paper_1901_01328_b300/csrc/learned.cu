@@ -391,25 +391,19 @@ __global__ void iota_kernel(uint32_t* p, uint64_t m) {
     if (i < m) p[i] = static_cast<uint32_t>(i);
 }
 
-// Heavy keys from the sorted sample: the first sample of each run of equal
-// keys measures the run by binary search; a run of count samples is heavy
-// when count * n_rows > (capacity / kHeavyDiv) * m: a key of more than half
-// a bucket gets a bucket of its own (an eighth measured the same: fewer rows
-// left to sort, but more ids that take the heavy-cell path).
+// Heavy keys from the sorted sample: a run of count samples is heavy when
+// count * n_rows > (capacity / kHeavyDiv) * m, i.e. count >= c_min =
+// floor((capacity / kHeavyDiv) * m / n_rows) + 1, so the first sample of a
+// run compares itself with the sample c_min - 1 places on.  A key of more
+// than half a bucket gets a bucket of its own (an eighth measured the same:
+// fewer rows left to sort, but more ids that take the heavy-cell path).
 struct HeavyRunStart {
     const uint64_t* srt;
-    uint64_t m, n_rows;
-    uint32_t capacity;
+    uint64_t m, c_min;
     __device__ __forceinline__ bool operator()(uint64_t i) const {
         const uint64_t key = srt[i];
         if (i > 0 && srt[i - 1] == key) return false;
-        uint64_t lo = i, hi = m;
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi) / 2;
-            if (srt[mid] <= key) lo = mid + 1;
-            else hi = mid;
-        }
-        return (unsigned __int128)(lo - i) * n_rows > (unsigned __int128)(capacity / kHeavyDiv) * m;
+        return i + c_min - 1 < m && srt[i + c_min - 1] == key;
     }
 };
 
@@ -1774,7 +1768,8 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     // heavy keys (in key order, the first kMaxHeavy), the non-heavy samples,
     // training rows
     const uint32_t nb = (uint32_t)((m + kCompactTile - 1) / kCompactTile);
-    const HeavyRunStart heavy_pred{t.s_keys, m, n_rows, SBH_LEARNED_CAPACITY};
+    const uint64_t c_min = n_rows ? (uint64_t)(SBH_LEARNED_CAPACITY / kHeavyDiv) * m / n_rows + 1 : m + 1;
+    const HeavyRunStart heavy_pred{t.s_keys, m, c_min};
     SBH_TIMED("learned_heavy", s,
               compact_count_kernel<HeavyRunStart><<<nb, kCompactTile, 0, s>>>(m, heavy_pred, t.block_sums));
     SBH_LAUNCHED();
