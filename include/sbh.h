@@ -317,7 +317,7 @@ int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, cons
 #define SBH_LEARNED_MODEL_BYTES 139264
 #define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
 #define SBH_LEARNED_MAX_HEAVY 16384 /* heavy keys a model holds */
-#define SBH_LEARNED_STATS 10
+#define SBH_LEARNED_STATS 12
 
 /* y[i] = MLP(x[i]) for i < m.  No scratch. */
 int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream);
@@ -368,7 +368,9 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * keys, buckets sorted in shared memory, one-key buckets, heavy buckets,
  * overflow buckets, overflow rows, largest bucket, buckets sorted by radix
  * passes in shared memory (their sub-buckets were too uneven for the
- * counting placement), and their rows.
+ * counting placement) and their rows, and wide buckets and their rows (too
+ * uneven, with a key range wider than 2^40: they join the overflow rows in
+ * the plain radix sort, cheaper than six or more passes in shared memory).
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
                          uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats, void* d_scratch,

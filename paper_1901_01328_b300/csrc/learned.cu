@@ -931,6 +931,7 @@ constexpr int kFineBits = 12;
 constexpr int kFineBins = 1 << kFineBits;
 constexpr int kFinePer = kFineBins / kBThreads;  // bins scanned by each thread
 constexpr uint32_t kFineMaxBin = 32;             // larger sub-buckets take the radix passes
+constexpr int kWideBits = 40;  // ... unless the key range is wider: then the bucket overflows
 
 struct BucketSmem {
     uint64_t keys[2][kCap];
@@ -949,7 +950,7 @@ static_assert(sizeof(BucketSmem) <= 232448, "bucket sort shared memory");
 
 struct BucketStats {
     unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
-        max_bucket, radix_buckets, radix_rows;
+        max_bucket, radix_buckets, radix_rows, wide_buckets, wide_rows;
 };
 
 // Persistent CTAs take buckets in order from a counter and sort each one in
@@ -1062,6 +1063,18 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             __syncthreads();  // (c)
             const uint32_t bt = sm.bin_tmp[lane];
             const bool big = __any_sync(0xffffffffu, (bt & 0x80000000u) != 0);
+            if (big && bits > kWideBits) {
+                // the radix passes in shared memory would take more than five
+                // passes: the plain radix sort of the overflow rows is cheaper
+                if (tid == 0) {
+                    ov_flag[b] = 1;
+                    atomicAdd(&st->wide_buckets, 1ull);
+                    atomicAdd(&st->wide_rows, (unsigned long long)cnt);
+                }
+                __syncthreads();  // buffer 0 is read no more
+                b = nb;
+                continue;
+            }
             if (!big) {
                 uint32_t run = x - tsum;
                 for (int w = 0; w < (int)warp; ++w) run += sm.bin_tmp[w];
@@ -1932,6 +1945,8 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
         h_stats[7] = st_h.max_bucket;
         h_stats[8] = st_h.radix_buckets;
         h_stats[9] = st_h.radix_rows;
+        h_stats[10] = st_h.wide_buckets;
+        h_stats[11] = st_h.wide_rows;
     }
     return SBH_OK;
 }
