@@ -207,7 +207,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 SAMPLE_STRIDE = 100        # 1% sample for the learned partitioner
-TRAIN = dict(steps=40, batch=16384, lr=3e-5, init="quantile knots")
+TRAIN = dict(steps=40, batch=4096, lr=3e-4, init="quantile knots")
 
 
 def run_gpu(args):
