@@ -760,7 +760,7 @@ __global__ void heavy_cells_kernel(const Model* __restrict__ model, uint32_t* __
 }
 
 // The cell table is built over blocks of 1024 cells in two launches:
-// cell_cdf writes F and each block's maximum of F and number of heavy cells;
+// cell_cdf writes F and each block's maximum of F and number of heavy keys;
 // cell_table combines the blocks before its own and scans its block.
 constexpr int kTblThreads = 1024;
 constexpr uint32_t kTblBlocks = (kNCell + 1 + kTblThreads - 1) / kTblThreads;
@@ -1667,8 +1667,10 @@ struct SortLearnedScratch {
 };
 
 inline uint64_t learned_nb(uint64_t n) { return (2 * n + kCap - 1) / kCap; }
-// every id is below NB + 2 * (heavy cells) + 2, and heavy cells are cells
+// every id is below NB + 2 * (heavy keys) + 2 (at most kMaxHeavy heavy keys);
+// the bound also covers the 2^16 + 1 bucket starts the carried-id path clears
 inline uint64_t learned_max_ids(uint64_t n) { return learned_nb(n) + 2ull * kNCell + 4; }
+static_assert(2ull * kNCell + 4 >= kMaxBucketIds + 1ull, "bucket starts of the carried-id path fit");
 
 SortLearnedScratch learned_carve(void* base, uint64_t n) {
     Carver c(base);
