@@ -137,9 +137,10 @@ def test_quantile_start_matches_oracle_and_training_refines_it(S, hashed):
     assert omlp.loss(p1, ox, ot) < loss0
 
 
+@pytest.mark.parametrize("start", ["seeded", "quantile"])
 @pytest.mark.parametrize("n,kind", [(1, "mixed"), (5000, "mixed"), (3_000_017, "mixed"), (2_500_000, "uniform"),
                                     (2_100_000, "equal"), (2_200_000, "highbyte"), (3_000_001, "hashed")])
-def test_learned_sort_equals_plain_sort(S, n, kind):
+def test_learned_sort_equals_plain_sort(S, n, kind, start):
     if kind == "mixed":
         col = gen.mixed_keys(n, seed=7)
     elif kind == "hashed":  # Zipf ranks through mix64: the same multiplicities over all 64 bits
@@ -151,7 +152,10 @@ def test_learned_sort_equals_plain_sort(S, n, kind):
     else:
         col = gen.uniform(7, 2, n, 0, 256, np.uint64) << np.uint64(56)
     sample = col[::100].copy()
-    model, _ = S.learned_train(cuda(sample), n, cuda(gen.mlp_init()), steps=150, batch=4096, lr=2e-2)
+    if start == "seeded":
+        model, _ = S.learned_train(cuda(sample), n, cuda(gen.mlp_init()), steps=150, batch=4096, lr=2e-2)
+    else:  # the bench's training: quantile-knot start (also all-heavy and one-sample samples)
+        model, _ = S.learned_train(cuda(sample), n, None, steps=40, batch=4096, lr=3e-4)
     keys, ptrs = S.extract(cuda(col), 0, n)
     sk, sp, stats = S.sort_learned(keys, ptrs, model)
     ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
