@@ -104,21 +104,27 @@ struct RunCounter {
 };
 
 // Histogram of every digit position of value_of(key); positions at or above
-// npos are counted as all-zero (constant, so their passes are skipped).
+// npos are counted as all-zero (constant, so their passes are skipped).  With
+// chunk_hist, CTA c takes the rows of chunk c of the chunked passes and also
+// writes that chunk's histogram of the first digit (the first pass's count).
 template <typename ValueFn>
-__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                      uint32_t* __restrict__ ghist, ValueFn value_of, int npos) {
+__global__ void __launch_bounds__(1024) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                       uint32_t* __restrict__ ghist, ValueFn value_of, int npos,
+                                                       uint32_t chunk = 0, uint32_t* __restrict__ chunk_hist = nullptr) {
     __shared__ uint32_t h[kPositions * kRadix];
     for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
     RunCounter rc;
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t done = 0;
-    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+    // rows [lo, hi): the whole input over the grid, or this CTA's chunk
+    const uint32_t lo = chunk_hist ? blockIdx.x * chunk : 0;
+    const uint32_t hi = chunk_hist ? min(n, lo + chunk) : n;
+    const uint32_t nthreads = chunk_hist ? blockDim.x : gridDim.x * blockDim.x;
+    const uint32_t tid = chunk_hist ? threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t done = lo;
+    if (lo < hi && (reinterpret_cast<uintptr_t>(keys + lo) & 15) == 0) {
         // four keys per step with two 16-byte loads issued together
-        const uint32_t nq = n / 4;
-        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
+        const uint32_t nq = (hi - lo) / 4;
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys + lo);
         for (uint32_t i = tid; i < nq; i += nthreads) {
             const ulonglong2 a = __ldcs(q + 2 * i);
             const ulonglong2 b = __ldcs(q + 2 * i + 1);
@@ -127,13 +133,15 @@ __global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict
             rc.add(value_of(b.x), h);
             rc.add(value_of(b.y), h);
         }
-        done = nq * 4;
+        done = lo + nq * 4;
     }
-    for (uint32_t i = done + tid; i < n; i += nthreads) rc.add(value_of(ld_stream(keys + i)), h);
+    for (uint32_t i = done + tid; i < hi; i += nthreads) rc.add(value_of(ld_stream(keys + i)), h);
     rc.flush(h);
     __syncthreads();
     for (int i = threadIdx.x; i < npos * kRadix; i += blockDim.x)
         if (h[i]) atomicAdd(&ghist[i], h[i]);
+    if (chunk_hist)
+        for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int p = npos; p < kPositions; ++p) atomicAdd(&ghist[p * kRadix], n);
 }
@@ -842,18 +850,18 @@ inline SortScratch sort_carve(void* scratch, uint64_t n) {
 // The passes of a large sort: per pass, chunk digit counts -> chunk offsets
 // -> scatter.
 template <typename ValueFn, int TILE, int THREADS>
-int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, ValueFn value_of, int bulk_ok,
-                   cudaStream_t s, const std::string& n_count, const std::string& n_scan, const std::string& n_scat) {
-    ChunkGeom g;
-    const int rc = chunk_geometry<ValueFn, TILE, THREADS, false>(n32, &g);
-    if (rc) return rc;
+int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, const ChunkGeom& g, ValueFn value_of,
+                   int bulk_ok, cudaStream_t s, const std::string& n_count, const std::string& n_scan,
+                   const std::string& n_scat) {
     const uint32_t limit = spin_limit();
     uint32_t* status = status_word();
     for (int pos = 0; pos < kPositions; ++pos) {
-        SBH_TIMED(n_count.c_str(), s,
-                  chunk_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk, sc.chunk_hist,
-                                                                        value_of));
-        SBH_LAUNCHED();
+        if (pos > 0) {  // the first pass's chunk counts come from the upsweep (the same chunks, g)
+            SBH_TIMED(n_count.c_str(), s,
+                      chunk_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk,
+                                                                            sc.chunk_hist, value_of));
+            SBH_LAUNCHED();
+        }
         SBH_TIMED(n_scan.c_str(), s,
                   chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, g.nchunks, sc.gbase,
                                                        sc.chunk_base));
@@ -885,8 +893,19 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
-    const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
-    SBH_TIMED(n_up.c_str(), s, upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
+    const bool chunked = use_chunked(n);
+    ChunkGeom g;
+    if (chunked) {
+        const int rc = chunk_geometry<ValueFn, 4096, 512, false>(n32, &g);
+        if (rc) return rc;
+        SBH_TIMED(n_up.c_str(), s,
+                  upsweep_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(in_k, n32, sc.hist, value_of, npos, g.chunk,
+                                                                    sc.chunk_hist));
+    } else {
+        const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
+        SBH_TIMED(n_up.c_str(), s,
+                  upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
+    }
     SBH_LAUNCHED();
     SBH_TIMED(n_plan.c_str(), s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
     SBH_LAUNCHED();
@@ -898,8 +917,8 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
-    if (use_chunked(n)) {
-        const int rc = chunked_passes<ValueFn, 4096, 512>(b, n32, sc, value_of, bulk_ok, s, n_count, n_scan, n_scat);
+    if (chunked) {
+        const int rc = chunked_passes<ValueFn, 4096, 512>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat);
         if (rc) return rc;
     } else {
         auto kern = onesweep_kernel<ValueFn>;
