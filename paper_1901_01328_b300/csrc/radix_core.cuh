@@ -104,27 +104,21 @@ struct RunCounter {
 };
 
 // Histogram of every digit position of value_of(key); positions at or above
-// npos are counted as all-zero (constant, so their passes are skipped).  With
-// chunk_hist, CTA c takes the rows of chunk c of the chunked passes and also
-// writes that chunk's histogram of the first digit (the first pass's count).
+// npos are counted as all-zero (constant, so their passes are skipped).
 template <typename ValueFn>
-__global__ void __launch_bounds__(1024) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                       uint32_t* __restrict__ ghist, ValueFn value_of, int npos,
-                                                       uint32_t chunk = 0, uint32_t* __restrict__ chunk_hist = nullptr) {
+__global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
+                                                      uint32_t* __restrict__ ghist, ValueFn value_of, int npos) {
     __shared__ uint32_t h[kPositions * kRadix];
     for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
     RunCounter rc;
-    // rows [lo, hi): the whole input over the grid, or this CTA's chunk
-    const uint32_t lo = chunk_hist ? blockIdx.x * chunk : 0;
-    const uint32_t hi = chunk_hist ? min(n, lo + chunk) : n;
-    const uint32_t nthreads = chunk_hist ? blockDim.x : gridDim.x * blockDim.x;
-    const uint32_t tid = chunk_hist ? threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t done = lo;
-    if (lo < hi && (reinterpret_cast<uintptr_t>(keys + lo) & 15) == 0) {
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
         // four keys per step with two 16-byte loads issued together
-        const uint32_t nq = (hi - lo) / 4;
-        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys + lo);
+        const uint32_t nq = n / 4;
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys);
         for (uint32_t i = tid; i < nq; i += nthreads) {
             const ulonglong2 a = __ldcs(q + 2 * i);
             const ulonglong2 b = __ldcs(q + 2 * i + 1);
@@ -133,17 +127,114 @@ __global__ void __launch_bounds__(1024) upsweep_kernel(const uint64_t* __restric
             rc.add(value_of(b.x), h);
             rc.add(value_of(b.y), h);
         }
-        done = lo + nq * 4;
+        done = nq * 4;
     }
-    for (uint32_t i = done + tid; i < hi; i += nthreads) rc.add(value_of(ld_stream(keys + i)), h);
+    for (uint32_t i = done + tid; i < n; i += nthreads) rc.add(value_of(ld_stream(keys + i)), h);
     rc.flush(h);
     __syncthreads();
     for (int i = threadIdx.x; i < npos * kRadix; i += blockDim.x)
         if (h[i]) atomicAdd(&ghist[i], h[i]);
-    if (chunk_hist)
-        for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int p = npos; p < kPositions; ++p) atomicAdd(&ghist[p * kRadix], n);
+}
+
+// First pass of the chunked passes: CTA c counts the first digit of its
+// chunk's values and folds the values into two words, the OR of the values
+// and the OR of their complements (both zeroed beforehand): a digit position
+// is constant when no bit of it is set in both.
+template <typename ValueFn>
+__global__ void __launch_bounds__(1024)
+first_count_kernel(const uint64_t* __restrict__ keys, uint32_t n, uint32_t chunk, ValueFn value_of,
+                   uint32_t* __restrict__ chunk_hist, unsigned long long* __restrict__ vbits) {
+    __shared__ uint32_t h[kRadix];
+    __shared__ unsigned long long wor[32], wnot[32];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    unsigned long long vor = 0, vnot = 0;
+    uint32_t last = 0, run = 0;
+    auto add = [&](uint64_t k) {
+        const uint64_t v = value_of(k);
+        vor |= v;
+        vnot |= ~v;
+        const uint32_t d = static_cast<uint32_t>(v) & (kRadix - 1);
+        if (d == last) {
+            ++run;
+        } else {
+            if (run) atomicAdd(&h[last], run);
+            last = d;
+            run = 1;
+        }
+    };
+    uint32_t done = lo;
+    if (lo < hi && (reinterpret_cast<uintptr_t>(keys + lo) & 15) == 0) {
+        const uint32_t nq = (hi - lo) / 4;
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(keys + lo);
+        for (uint32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+            const ulonglong2 a = __ldcs(q + 2 * i);
+            const ulonglong2 b = __ldcs(q + 2 * i + 1);
+            add(a.x);
+            add(a.y);
+            add(b.x);
+            add(b.y);
+        }
+        done = lo + nq * 4;
+    }
+    for (uint32_t i = done + threadIdx.x; i < hi; i += blockDim.x) add(ld_stream(keys + i));
+    if (run) atomicAdd(&h[last], run);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vor |= __shfl_xor_sync(0xffffffffu, vor, o);
+        vnot |= __shfl_xor_sync(0xffffffffu, vnot, o);
+    }
+    if (lane_id() == 0) {
+        wor[threadIdx.x / 32] = vor;
+        wnot[threadIdx.x / 32] = vnot;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
+            vor |= wor[w];
+            vnot |= wnot[w];
+        }
+        atomicOr(&vbits[0], vor);
+        atomicOr(&vbits[1], vnot);
+    }
+}
+
+// The pass plan from the value bits: a pass is active when its digit is not
+// constant (a bit of it set in some value and clear in another).
+__device__ void fill_plan(const int* active, int in_place, Plan* __restrict__ plan) {
+    Plan pl;
+    int a = 0;
+    for (int p = 0; p < kPositions; ++p) a += active[p];
+    int i = 0, prev = 0;
+    for (int p = 0; p < kPositions; ++p) {
+        pl.active[p] = active[p];
+        pl.src[p] = pl.dst[p] = 0;
+        if (!active[p]) continue;
+        int dst;
+        if (in_place) dst = (i % 2 == 0) ? 1 : 2;
+        else dst = ((a - 1 - i) % 2 == 0) ? 2 : 1;
+        pl.src[p] = (i == 0) ? 0 : prev;
+        pl.dst[p] = dst;
+        prev = dst;
+        ++i;
+    }
+    if (a == 0) pl.copy_src = in_place ? -1 : 0;
+    else pl.copy_src = (prev == 2) ? -1 : prev;
+    pl.npasses = a;
+    *plan = pl;
+}
+
+__global__ void plan_bits_kernel(const unsigned long long* __restrict__ vbits, int npos, Plan* __restrict__ plan,
+                                 int in_place) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long varying = vbits[0] & vbits[1];
+    int active[kPositions];
+    for (int p = 0; p < kPositions; ++p) active[p] = p < npos && ((varying >> (p * kRadixBits)) & (kRadix - 1)) != 0;
+    fill_plan(active, in_place, plan);
 }
 
 // ------------------------------------------------------------------ plan
@@ -170,28 +261,7 @@ __global__ void __launch_bounds__(kRadix) plan_kernel(const uint32_t* __restrict
         if (d == 0) s_active[p] = !constant;
         __syncthreads();
     }
-    if (d == 0) {
-        Plan pl;
-        int a = 0;
-        for (int p = 0; p < kPositions; ++p) a += s_active[p];
-        int i = 0, prev = 0;
-        for (int p = 0; p < kPositions; ++p) {
-            pl.active[p] = s_active[p];
-            pl.src[p] = pl.dst[p] = 0;
-            if (!s_active[p]) continue;
-            int dst;
-            if (in_place) dst = (i % 2 == 0) ? 1 : 2;
-            else dst = ((a - 1 - i) % 2 == 0) ? 2 : 1;
-            pl.src[p] = (i == 0) ? 0 : prev;
-            pl.dst[p] = dst;
-            prev = dst;
-            ++i;
-        }
-        if (a == 0) pl.copy_src = in_place ? -1 : 0;
-        else pl.copy_src = (prev == 2) ? -1 : prev;
-        pl.npasses = a;
-        *plan = pl;
-    }
+    if (d == 0) fill_plan(s_active, in_place, plan);
 }
 
 // ------------------------------------------------------------------ onesweep
@@ -478,12 +548,16 @@ chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ pl
 
 // Global offset of every (chunk, digit): the digit's global base plus the
 // counts of that digit in earlier chunks.  1024 threads: digit = tid % 256,
-// one of four chunk groups = tid / 256.
+// one of four chunk groups = tid / 256.  The digit bases come from gbase, or,
+// when it is null, from the chunk counts themselves (their digit totals,
+// scanned).
 __global__ void __launch_bounds__(1024)
 chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __restrict__ chunk_hist, uint32_t nchunks,
                   const uint32_t* __restrict__ gbase, uint32_t* __restrict__ chunk_base) {
     if (!plan->active[pos]) return;
     __shared__ uint32_t gsum[4][kRadix];
+    __shared__ uint32_t base[kRadix];
+    __shared__ uint32_t wsum[kRadix / 32];
     const uint32_t d = threadIdx.x & (kRadix - 1), g = threadIdx.x / kRadix;
     const uint32_t per = (nchunks + 3) / 4;
     const uint32_t c0 = min(nchunks, g * per), c1 = min(nchunks, c0 + per);
@@ -492,7 +566,27 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
     for (uint32_t c = c0; c < c1; ++c) s += chunk_hist[c * kRadix + d];
     gsum[g][d] = s;
     __syncthreads();
-    uint32_t run = gbase[pos * kRadix + d];
+    if (!gbase) {
+        if (g == 0) {  // exclusive scan of the digit totals
+            const uint32_t t = gsum[0][d] + gsum[1][d] + gsum[2][d] + gsum[3][d];
+            uint32_t x = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane_id() >= (uint32_t)o) x += y;
+            }
+            if (lane_id() == 31) wsum[d / 32] = x;
+            base[d] = x - t;
+        }
+        __syncthreads();
+    }
+    uint32_t run;
+    if (gbase) {
+        run = gbase[pos * kRadix + d];
+    } else {
+        run = base[d];
+        for (uint32_t w = 0; w < d / 32; ++w) run += wsum[w];
+    }
     for (uint32_t gg = 0; gg < g; ++gg) run += gsum[gg][d];
 #pragma unroll 8
     for (uint32_t c = c0; c < c1; ++c) {
@@ -819,6 +913,7 @@ struct SortScratch {
     uint32_t* chunk_hist;  // kMaxChunks * kRadix
     uint32_t* chunk_base;  // kMaxChunks * kRadix
     uint32_t* hist;        // kPositions * kRadix   (zeroed)
+    unsigned long long* vbits;  // 2: OR of the values, OR of their complements (zeroed)
     uint32_t* counters;    // kPositions            (zeroed)
     uint64_t* lookback;    // ntiles * kRadix       (zeroed; onesweep only)
     char* zero_begin;
@@ -839,6 +934,7 @@ inline SortScratch sort_carve(void* scratch, uint64_t n) {
     s.chunk_base = c.take<uint32_t>(kMaxChunks * kRadix);
     s.hist = c.take<uint32_t>(kPositions * kRadix);
     const size_t zb = c.off - kPositions * kRadix * sizeof(uint32_t);
+    s.vbits = c.take<unsigned long long>(2);
     s.counters = c.take<uint32_t>(kPositions);
     s.lookback = chunked ? nullptr : c.take<uint64_t>(ntiles * kRadix);
     s.zero_begin = reinterpret_cast<char*>(s.hist);
@@ -856,14 +952,14 @@ int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, const 
     const uint32_t limit = spin_limit();
     uint32_t* status = status_word();
     for (int pos = 0; pos < kPositions; ++pos) {
-        if (pos > 0) {  // the first pass's chunk counts come from the upsweep (the same chunks, g)
+        if (pos > 0) {  // the first pass's chunk counts come from first_count_kernel (the same chunks, g)
             SBH_TIMED(n_count.c_str(), s,
                       chunk_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk,
                                                                             sc.chunk_hist, value_of));
             SBH_LAUNCHED();
         }
         SBH_TIMED(n_scan.c_str(), s,
-                  chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, g.nchunks, sc.gbase,
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, g.nchunks, nullptr,
                                                        sc.chunk_base));
         SBH_LAUNCHED();
         SBH_TIMED(n_scat.c_str(), s,
@@ -896,19 +992,25 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const bool chunked = use_chunked(n);
     ChunkGeom g;
     if (chunked) {
+        // the chunked passes find their digit bases in the chunk counts; the
+        // plan needs only which digits vary: the first pass's counts and the
+        // values' OR and AND in one read
         const int rc = chunk_geometry<ValueFn, 4096, 512, false>(n32, &g);
         if (rc) return rc;
         SBH_TIMED(n_up.c_str(), s,
-                  upsweep_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(in_k, n32, sc.hist, value_of, npos, g.chunk,
-                                                                    sc.chunk_hist));
+                  first_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, value_of, sc.chunk_hist,
+                                                                         sc.vbits));
+        SBH_LAUNCHED();
+        SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place));
+        SBH_LAUNCHED();
     } else {
         const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
         SBH_TIMED(n_up.c_str(), s,
                   upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
+        SBH_LAUNCHED();
+        SBH_TIMED(n_plan.c_str(), s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
+        SBH_LAUNCHED();
     }
-    SBH_LAUNCHED();
-    SBH_TIMED(n_plan.c_str(), s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
-    SBH_LAUNCHED();
     Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
     const size_t smem = sizeof(SortSmem);
     const uint32_t limit = spin_limit();
