@@ -1356,20 +1356,24 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 constexpr int kCarryTile = 3584;
 constexpr uint32_t kMaxBucketIds = 1u << 16;  // carried ids are 16 bits
 
-// Bucket id of every row (kept as 16 bits) and the histograms of its two
-// digits.  CTA c takes the rows of chunk c of the first digit pass, so the
-// chunk's histogram of the first digit (what that pass's count kernel would
-// produce) comes out here too.
+// Bucket id of every row (kept as 16 bits), the histogram of its low digit
+// per chunk of the first digit pass (CTA c takes the rows of chunk c: that
+// pass's count), and the OR of the ids and of their complements (vbits,
+// zeroed beforehand), from which the plan sees which digits vary.
 __global__ void __launch_bounds__(1024) ids_upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
                                                            uint32_t chunk, BucketValue16 fn,
-                                                           uint16_t* __restrict__ ids, uint32_t* __restrict__ ghist,
+                                                           uint16_t* __restrict__ ids,
+                                                           unsigned long long* __restrict__ vbits,
                                                            uint32_t* __restrict__ chunk_hist) {
-    __shared__ uint32_t h[2 * kRadix];
-    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) h[i] = 0;
+    __shared__ uint32_t h[kRadix];
+    __shared__ uint32_t wor[32], wnot[32];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
+    uint32_t vor = 0, vnot = 0;
     auto add = [&](uint32_t id) {
         atomicAdd(&h[id & 255u], 1u);
-        atomicAdd(&h[kRadix + (id >> 8)], 1u);
+        vor |= id;
+        vnot |= ~id;
     };
     const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
     uint32_t done = lo;
@@ -1396,13 +1400,27 @@ __global__ void __launch_bounds__(1024) ids_upsweep_kernel(const uint64_t* __res
         ids[i] = static_cast<uint16_t>(id);
         add(id);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) {
-        if (i < kRadix) chunk_hist[blockIdx.x * kRadix + i] = h[i];
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vor |= __shfl_xor_sync(0xffffffffu, vor, o);
+        vnot |= __shfl_xor_sync(0xffffffffu, vnot, o);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int p = 2; p < kPositions; ++p) atomicAdd(&ghist[p * kRadix], n);
+    if (lane_id() == 0) {
+        wor[threadIdx.x / 32] = vor;
+        wnot[threadIdx.x / 32] = vnot;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
+            vor |= wor[w];
+            vnot |= wnot[w];
+        }
+        if (lo < hi) {
+            atomicOr(&vbits[0], static_cast<unsigned long long>(vor));
+            atomicOr(&vbits[1], 0xFFFFFFFF00000000ull | vnot);  // the complement of the zero-extended id
+        }
+    }
 }
 
 __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
@@ -1486,11 +1504,10 @@ struct CarryScratch {
     uint16_t* ids_in;
     uint16_t* ids_tmp;
     uint16_t* ids_out;
-    uint32_t* gbase;
     Plan* plan;
     uint32_t* chunk_hist;
     uint32_t* chunk_base;
-    uint32_t* hist;  // zeroed
+    unsigned long long* vbits;  // 2: OR of the ids, OR of their complements (zeroed)
     uint32_t* bmin;  // per block of bucket starts: minimum
     size_t total;
 };
@@ -1503,11 +1520,10 @@ CarryScratch carry_carve(void* base, uint64_t n) {
     t.ids_in = c.take<uint16_t>(n);
     t.ids_tmp = c.take<uint16_t>(n);
     t.ids_out = c.take<uint16_t>(n);
-    t.gbase = c.take<uint32_t>(kPositions * kRadix);
     t.plan = c.take<Plan>(1);
     t.chunk_hist = c.take<uint32_t>(kMaxChunks * kRadix);
     t.chunk_base = c.take<uint32_t>(kMaxChunks * kRadix);
-    t.hist = c.take<uint32_t>(kPositions * kRadix);
+    t.vbits = c.take<unsigned long long>(2);
     t.bmin = c.take<uint32_t>(kMaxBucketIds / 1024 + 1);
     t.total = c.bytes();
     return t;
@@ -1591,7 +1607,7 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const
             SBH_LAUNCHED();
         }
         SBH_TIMED("learned_ids_chunk_scan", s,
-                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, cs.gbase, cs.chunk_base));
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, nullptr, cs.chunk_base));
         SBH_LAUNCHED();
         SBH_TIMED("learned_ids_scatter", s,
                   (chunk_scatter_kernel<RadixValue, TILE, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
@@ -1608,14 +1624,14 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     CarryScratch cs = carry_carve(scratch, n);
     const uint32_t n32 = static_cast<uint32_t>(n);
     const int sms = num_sms();
-    SBH_CUDA(cudaMemsetAsync(cs.hist, 0, kPositions * kRadix * sizeof(uint32_t), s));
+    SBH_CUDA(cudaMemsetAsync(cs.vbits, 0, 2 * sizeof(unsigned long long), s));
     ChunkGeom g;
     int rc = chunk_geometry<RadixValue, kCarryTile, 512, true>(n32, &g);
     if (rc) return rc;
     SBH_TIMED("learned_ids_upsweep", s,
-              ids_upsweep_kernel<<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, fn, cs.ids_in, cs.hist, cs.chunk_hist));
+              ids_upsweep_kernel<<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, fn, cs.ids_in, cs.vbits, cs.chunk_hist));
     SBH_LAUNCHED();
-    SBH_TIMED("learned_ids_plan", s, plan_kernel<<<1, kRadix, 0, s>>>(cs.hist, n32, cs.gbase, cs.plan, 0));
+    SBH_TIMED("learned_ids_plan", s, plan_bits_kernel<<<1, 32, 0, s>>>(cs.vbits, 2, cs.plan, 0));
     SBH_LAUNCHED();
     Buffers b{in_k, in_p, cs.tmp_k, cs.tmp_p, out_k, out_p};
     b.in_v = cs.ids_in;
