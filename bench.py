@@ -602,7 +602,8 @@ def row_suite(peak):
     oc = torch.empty_like(ok)
     osum = torch.empty_like(ok)
     nk = torch.empty(1, dtype=torch.uint64, device=dev)
-    ms = dev_ms(lambda: sbh.sbh_group_reduce(sk, sp, vals, ok, oc, osum, 1_000_000, nk))
+    red_scr = torch.empty(sbh.group_reduce_scratch_bytes(1_000_000, 4), dtype=torch.uint8, device=dev)
+    ms = dev_ms(lambda: sbh.sbh_group_reduce(sk, sp, vals, ok, oc, osum, 1_000_000, nk, scratch=red_scr))
     hk, hp_ = sk.cpu().numpy(), sp.cpu().numpy()
     oms = cpu_ms(lambda: oracle.group_sum_count(hk, hp_, w["vals"]))
     nkeys = int(nk.item())
