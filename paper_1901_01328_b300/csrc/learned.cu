@@ -487,28 +487,42 @@ __device__ __forceinline__ uint32_t gcd_u32(uint32_t a, uint32_t b) {
 // Training rows: row r takes sorted non-heavy sample (r * P) mod m'.
 __global__ void trainset_kernel(const uint64_t* __restrict__ nh, const uint32_t* __restrict__ m_train,
                                 float* __restrict__ X, float* __restrict__ T) {
+    __shared__ uint32_t sP;
     const uint32_t mt = *m_train;
+    if (mt == 0) return;
+    if (threadIdx.x == 0) {
+        uint32_t P = static_cast<uint32_t>(2654435761ull % mt);
+        while (gcd_u32(P, mt) != 1) ++P;
+        sP = P;
+    }
+    __syncthreads();
     const uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (r >= mt) return;
-    uint32_t P = static_cast<uint32_t>(2654435761ull % mt);
-    while (gcd_u32(P, mt) != 1) ++P;
-    const uint64_t j = (r * (uint64_t)P) % mt;
+    const uint64_t j = (r * (uint64_t)sP) % mt;
     const uint64_t key = nh[j];
-    uint64_t lo = 0, hi = mt;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) / 2;
-        if (nh[mid] < key) lo = mid + 1;
-        else hi = mid;
+    // the key's run [lt, le) in the sorted samples: usually j alone, else
+    // found by binary search on the side where it continues
+    uint64_t lt = j, le = j + 1;
+    if (j > 0 && nh[j - 1] == key) {
+        uint64_t lo = 0, hi = j;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (nh[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        lt = lo;
     }
-    const uint64_t lt = lo;
-    hi = mt;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) / 2;
-        if (nh[mid] <= key) lo = mid + 1;
-        else hi = mid;
+    if (j + 1 < mt && nh[j + 1] == key) {
+        uint64_t lo = j + 1, hi = mt;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (nh[mid] <= key) lo = mid + 1;
+            else hi = mid;
+        }
+        le = lo;
     }
     X[r] = key_feature(key);
-    T[r] = static_cast<float>(lt + lo) / (2.0f * static_cast<float>(mt));
+    T[r] = static_cast<float>(lt + le) / (2.0f * static_cast<float>(mt));
 }
 
 // Start from the piecewise-linear interpolation of the training set's CDF at
