@@ -95,3 +95,19 @@ def test_knobs_set_and_get_without_a_gpu(L):
     assert lib.sbh_kpa_sort(None, None, None, None, 1 << 22, None, ctypes.byref(nb_large), None) == 0
     L.set_knob(L.KNOB_SORT_CHUNKED_MIN, 1 << 23)
     assert nb_small.value != nb_large.value
+
+
+def test_binding_constants_match_the_header(L):
+    S = L
+    text = open(os.path.join(ROOT, "include", "sbh.h")).read()
+    defs = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define (SBH_\w+) (0x[0-9A-Fa-f]+|\d+)", text)}
+    assert defs["SBH_MLP_PARAMS"] == S.MLP_PARAMS
+    assert defs["SBH_LEARNED_MODEL_BYTES"] == S.LEARNED_MODEL_BYTES
+    assert defs["SBH_LEARNED_CAPACITY"] == S.LEARNED_CAPACITY
+    assert defs["SBH_LEARNED_MAX_HEAVY"] == S.LEARNED_MAX_HEAVY
+    assert defs["SBH_LEARNED_STATS"] == len(S.LEARNED_STATS)
+    assert defs["SBH_TOPK_MAX_K"] == S.TOPK_MAX_K
+    assert (defs["SBH_OK"], defs["SBH_EINVAL"], defs["SBH_ENOSPACE"], defs["SBH_ETIMEOUT"], defs["SBH_ECUDA"]) == (
+        S.SBH_OK, S.SBH_EINVAL, S.SBH_ENOSPACE, S.SBH_ETIMEOUT, S.SBH_ECUDA)
+    assert (defs["SBH_KNOB_SORT_CHUNKED_MIN"], defs["SBH_KNOB_MERGE_SEARCH_MIN_TILES"]) == (
+        S.KNOB_SORT_CHUNKED_MIN, S.KNOB_MERGE_SEARCH_MIN_TILES)
