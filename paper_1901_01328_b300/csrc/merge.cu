@@ -5,7 +5,7 @@
 // diagonal cuts A and B (a binary search on the merge path per tile, all
 // tiles in parallel; small merges let each CTA search its own); each CTA of
 // the merge then stages its two slices in shared memory, and each thread
-// merges 8 outputs from its own co-rank.  More than two runs are merged in rounds of
+// merges 8 outputs from its own co-rank and stores them from registers.  More than two runs are merged in rounds of
 // pairwise merges through a scratch ping-pong buffer.
 #include <vector>
 
@@ -51,7 +51,7 @@ merge_cuts_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ 
 __global__ void __launch_bounds__(kThreads)
 merge_pair_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ap, uint32_t na,
                   const uint64_t* __restrict__ bk, const uint32_t* __restrict__ bp, uint32_t nb,
-                  const uint32_t* __restrict__ cuts, uint64_t* __restrict__ ok, uint32_t* __restrict__ op) {
+                  const uint32_t* __restrict__ cuts, uint64_t* __restrict__ ok, uint32_t* __restrict__ op, int vec_ok) {
     __shared__ uint64_t sk[kTile];
     __shared__ uint32_t sp[kTile];
     __shared__ uint32_t cut[2];
@@ -92,16 +92,27 @@ merge_pair_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ 
             rp[t] = 0;
         }
     }
-    __syncthreads();
+    // this thread's kIpt outputs are consecutive: 16-byte stores straight
+    // from registers (a staging round trip through shared memory would hit
+    // the same banks from every eighth thread)
+    const uint32_t o0 = threadIdx.x * kIpt;
+    if (vec_ok && o0 + kIpt <= len) {
+        uint4* kq = reinterpret_cast<uint4*>(ok + d0 + o0);
 #pragma unroll
-    for (int t = 0; t < kIpt; ++t) {
-        const uint32_t o = threadIdx.x * kIpt + t;
-        if (o < len) { sk[o] = rk[t]; sp[o] = rp[t]; }
-    }
-    __syncthreads();
-    for (uint32_t o = threadIdx.x; o < len; o += kThreads) {
-        st_stream(ok + d0 + o, sk[o]);
-        st_stream(op + d0 + o, sp[o]);
+        for (int t = 0; t < kIpt; t += 2)
+            __stcs(kq + t / 2, make_uint4(static_cast<uint32_t>(rk[t]), static_cast<uint32_t>(rk[t] >> 32),
+                                          static_cast<uint32_t>(rk[t + 1]), static_cast<uint32_t>(rk[t + 1] >> 32)));
+        uint4* pq = reinterpret_cast<uint4*>(op + d0 + o0);
+#pragma unroll
+        for (int t = 0; t < kIpt; t += 4) __stcs(pq + t / 4, make_uint4(rp[t], rp[t + 1], rp[t + 2], rp[t + 3]));
+    } else {
+#pragma unroll
+        for (int t = 0; t < kIpt; ++t) {
+            if (o0 + t < len) {
+                st_stream(ok + d0 + o0 + t, rk[t]);
+                st_stream(op + d0 + o0 + t, rp[t]);
+            }
+        }
     }
 }
 
@@ -132,9 +143,10 @@ int merge_two(const Run& a, const Run& b, uint64_t* ok, uint32_t* op, uint32_t* 
     } else {
         cuts = nullptr;
     }
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(ok) | reinterpret_cast<uintptr_t>(op)) & 15) == 0;
     SBH_TIMED("merge_path", s,
               merge_pair_kernel<<<ntiles, kThreads, 0, s>>>(a.k, a.p, (uint32_t)a.n, b.k, b.p, (uint32_t)b.n, cuts,
-                                                            ok, op));
+                                                            ok, op, vec_ok));
     SBH_LAUNCHED();
     return SBH_OK;
 }
