@@ -65,31 +65,52 @@ merge_pair_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ 
     const uint32_t a0 = cuts ? cuts[blockIdx.x] : cut[0], a1 = cuts ? cuts[blockIdx.x + 1] : cut[1];
     const uint32_t b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = a1 - a0, lb = b1 - b0, len = d1 - d0;
-    // stage A slice then B slice
+    // stage A slice then B slice; element x sits at slot x ^ ((x >> 4) & 15),
+    // so that threads reading a few elements apart (the merge below) hit
+    // different banks
+    auto sw = [](uint32_t x) { return x ^ ((x >> 4) & 15u); };
     for (uint32_t i = threadIdx.x; i < len; i += kThreads) {
-        if (i < la) { sk[i] = ak[a0 + i]; sp[i] = ap[a0 + i]; }
-        else { sk[i] = bk[b0 + i - la]; sp[i] = bp[b0 + i - la]; }
+        if (i < la) { sk[sw(i)] = ak[a0 + i]; sp[sw(i)] = ap[a0 + i]; }
+        else { sk[sw(i)] = bk[b0 + i - la]; sp[sw(i)] = bp[b0 + i - la]; }
     }
     __syncthreads();
-    // each thread merges kIpt outputs starting at its own diagonal
+    // each thread merges kIpt outputs starting at its own diagonal (the
+    // co-rank by binary search; the two heads kept in registers)
     const uint32_t my = min(threadIdx.x * kIpt, len);
-    uint32_t i = corank(my, sk, sp, la, sk + la, sp + la, lb);
-    uint32_t j = my - i;
+    uint32_t i, j;
+    {
+        uint32_t lo = my > lb ? my - lb : 0, hi = my < la ? my : la;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            const uint32_t q = la + (my - mid - 1);
+            if (kp_less(sk[sw(q)], sp[sw(q)], sk[sw(mid)], sp[sw(mid)])) hi = mid;
+            else lo = mid + 1;
+        }
+        i = lo;
+        j = my - lo;
+    }
+    uint64_t ka = i < la ? sk[sw(i)] : 0, kb = j < lb ? sk[sw(la + j)] : 0;
+    uint32_t pa = i < la ? sp[sw(i)] : 0, pb = j < lb ? sp[sw(la + j)] : 0;
     uint64_t rk[kIpt];
     uint32_t rp[kIpt];
 #pragma unroll
     for (int t = 0; t < kIpt; ++t) {
         const bool ha = i < la, hb = j < lb;
-        bool take_a = ha && (!hb || !kp_less(sk[la + j], sp[la + j], sk[i], sp[i]));
-        if (ha || hb) {
-            const uint32_t idx = take_a ? i : la + j;
-            rk[t] = sk[idx];
-            rp[t] = sp[idx];
-            i += take_a;
-            j += !take_a;
-        } else {
-            rk[t] = 0;
-            rp[t] = 0;
+        const bool take_a = ha && (!hb || !kp_less(kb, pb, ka, pa));
+        rk[t] = take_a ? ka : (hb ? kb : 0);
+        rp[t] = take_a ? pa : (hb ? pb : 0);
+        if (take_a) {
+            ++i;
+            if (i < la) {
+                ka = sk[sw(i)];
+                pa = sp[sw(i)];
+            }
+        } else if (hb) {
+            ++j;
+            if (j < lb) {
+                kb = sk[sw(la + j)];
+                pb = sp[sw(la + j)];
+            }
         }
     }
     // this thread's kIpt outputs are consecutive: 16-byte stores straight
