@@ -46,7 +46,7 @@ CPU_SAMPLE = 4_000_000
 # scatter the mean of its two passes).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 28.15, "sort_scatter": 24.57}
+DRAM_BYTES_PER_ROW = {"sort_scatter": 24.57}
 
 
 def _dist():
@@ -354,11 +354,11 @@ def run_gpu(args):
     algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
                   "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
                   "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
-                  # per launch, the mean of the two passes: the first reads and writes the 2-byte
-                  # ids (28 B/row), the last reads them and records bucket starts (26 B/row)
-                  "learned_ids_scatter": 27 * n, "learned_ids_count": 2 * n,
-                  "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n,
-                  "learned_bounds": 2 * n}
+                  # per launch, the mean of the two passes: the first reads the 2-byte ids and
+                  # writes their high bytes (27 B/row), the last reads those and records bucket
+                  # starts (25 B/row)
+                  "learned_ids_scatter": 26 * n, "learned_ids_count": 1 * n,
+                  "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
     achieved = algo_bytes.get(dominant, 0) / (dom_avg_ms / 1e3) / 1e9

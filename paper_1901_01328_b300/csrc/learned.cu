@@ -1437,36 +1437,34 @@ __global__ void __launch_bounds__(1024) ids_upsweep_kernel(const uint64_t* __res
     }
 }
 
+// Chunk counts of the second pass: its digit is the carried high byte.
 __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
                                                          uint32_t chunk, uint32_t* __restrict__ chunk_hist) {
     if (!plan->active[pos]) return;
     __shared__ uint32_t h[kRadix];
-    const uint16_t* __restrict__ v = buf.vals(plan->src[pos]);
+    const uint8_t* __restrict__ v = buf.vals(plan->src[pos]);
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-    const int sh = pos * kRadixBits;
     uint32_t last = 0, run = 0;
-    auto add = [&](uint32_t id) {
-        const uint32_t d = (id >> sh) & (kRadix - 1);
+    auto add = [&](uint32_t d) {
         if (d == last) ++run;
         else { if (run) atomicAdd(&h[last], run); last = d; run = 1; }
     };
     uint32_t done = lo;
     if (lo < hi && (reinterpret_cast<uintptr_t>(v + lo) & 15) == 0) {
-        // eight ids per 16-byte load
-        const uint32_t nq = (hi - lo) / 8;
+        // sixteen bytes per load
+        const uint32_t nq = (hi - lo) / 16;
         const uint4* q = reinterpret_cast<const uint4*>(v + lo);
         for (uint32_t i = threadIdx.x; i < nq; i += blockDim.x) {
             const uint4 w = __ldcs(q + i);
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                add(ws[u] & 0xFFFFu);
-                add(ws[u] >> 16);
-            }
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) add((ws[u] >> (8 * y)) & 0xFFu);
         }
-        done = lo + nq * 8;
+        done = lo + nq * 16;
     }
     for (uint32_t i = done + threadIdx.x; i < hi; i += blockDim.x) add(v[i]);
     if (run) atomicAdd(&h[last], run);
@@ -1474,53 +1472,29 @@ __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) chunk_hist[blockIdx.x * kRadix + i] = h[i];
 }
 
-// Bucket bounds from the ids when no pass ran (all ids equal; otherwise the
-// last pass recorded each id's first row).  Each thread takes eight
-// consecutive rows.
-__global__ void __launch_bounds__(256) ids_bounds_kernel(Buffers buf, const Plan* __restrict__ plan, uint32_t n,
+// Bucket bounds when no pass ran: every row has the same id, the OR of the
+// ids (vbits[0]); the last pass records each id's first row otherwise.
+__global__ void __launch_bounds__(256) ids_bounds_kernel(const Plan* __restrict__ plan, uint32_t n,
                                                          const uint32_t* __restrict__ nbid_p,
+                                                         const unsigned long long* __restrict__ vbits,
                                                          uint32_t* __restrict__ bstart) {
     if (plan->npasses) return;
-    const uint16_t* __restrict__ v = buf.in_v;
     const uint32_t nbid = *nbid_p;
-    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x * 8;
-    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 8; i0 < n; i0 += stride) {
-        uint32_t id[8];
-        if (i0 + 8 <= n && (reinterpret_cast<uintptr_t>(v + i0) & 15) == 0) {
-            const uint4 w = *reinterpret_cast<const uint4*>(v + i0);
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                id[2 * u] = ws[u] & 0xFFFFu;
-                id[2 * u + 1] = ws[u] >> 16;
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) id[u] = i0 + u < n ? v[i0 + u] : 0u;
-        }
-        int64_t prev = i0 ? static_cast<int64_t>(v[i0 - 1]) : -1;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint64_t i = i0 + u;
-            if (i < n) {
-                for (int64_t b = prev + 1; b <= (int64_t)id[u]; ++b) bstart[b] = static_cast<uint32_t>(i);
-                if (i == n - 1)
-                    for (uint32_t b = id[u] + 1; b <= nbid; ++b) bstart[b] = n;
-                prev = id[u];
-            }
-        }
-    }
+    const uint32_t id = static_cast<uint32_t>(vbits[0]);
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nbid; b += gridDim.x * blockDim.x)
+        bstart[b] = b <= id ? 0u : n;
 }
 
 struct CarryScratch {
     uint64_t* tmp_k;
     uint32_t* tmp_p;
-    uint16_t* ids_in;
-    uint16_t* ids_tmp;
-    uint16_t* ids_out;
+    uint16_t* ids_in;   // the input rows' ids
+    uint8_t* hi_tmp;    // the ids' high bytes, carried by the first pass
+    uint8_t* hi_out;
     Plan* plan;
     uint32_t* chunk_hist;
-    uint32_t* chunk_base;
+    uint32_t* chunk_base;   // first pass (its first 256 entries: the low bytes' starts)
+    uint32_t* chunk_base1;  // second pass
     unsigned long long* vbits;  // 2: OR of the ids, OR of their complements (zeroed)
     uint32_t* bmin;  // per block of bucket starts: minimum
     size_t total;
@@ -1532,11 +1506,12 @@ CarryScratch carry_carve(void* base, uint64_t n) {
     t.tmp_k = c.take<uint64_t>(n);
     t.tmp_p = c.take<uint32_t>(n);
     t.ids_in = c.take<uint16_t>(n);
-    t.ids_tmp = c.take<uint16_t>(n);
-    t.ids_out = c.take<uint16_t>(n);
+    t.hi_tmp = c.take<uint8_t>(n);
+    t.hi_out = c.take<uint8_t>(n);
     t.plan = c.take<Plan>(1);
     t.chunk_hist = c.take<uint32_t>(kMaxChunks * kRadix);
     t.chunk_base = c.take<uint32_t>(kMaxChunks * kRadix);
+    t.chunk_base1 = c.take<uint32_t>(kMaxChunks * kRadix);
     t.vbits = c.take<unsigned long long>(2);
     t.bmin = c.take<uint32_t>(kMaxBucketIds / 1024 + 1);
     t.total = c.bytes();
@@ -1606,9 +1581,10 @@ __global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restric
     if (b <= nbid) bstart[b] = min(x, after);
 }
 
-// The two passes by carried bucket id: per pass, chunk counts of the id
-// digit -> chunk offsets -> scatter carrying the ids along.
-// The first pass's chunk counts come from the id upsweep (the same chunks).
+// The two passes by bucket id: per pass, chunk counts of the id digit ->
+// chunk offsets -> scatter; the first pass carries the ids' high bytes to the
+// second.  The first pass's chunk counts come from the id upsweep (the same
+// chunks).
 template <int TILE, int THREADS>
 int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const ChunkGeom& g, cudaStream_t s,
                    uint32_t* first_row) {
@@ -1620,13 +1596,14 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const
                       ids_count_kernel<<<g.nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, g.chunk, cs.chunk_hist));
             SBH_LAUNCHED();
         }
+        uint32_t* cbase = pos ? cs.chunk_base1 : cs.chunk_base;
         SBH_TIMED("learned_ids_chunk_scan", s,
-                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, nullptr, cs.chunk_base));
+                  chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, nullptr, cbase));
         SBH_LAUNCHED();
         SBH_TIMED("learned_ids_scatter", s,
                   (chunk_scatter_kernel<RadixValue, TILE, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
-                      b, n32, pos, cs.plan, g.chunk, cs.chunk_base, RadixValue{}, bulk_ok, spin_limit(),
-                      status_word(), first_row)));
+                      b, n32, pos, cs.plan, g.chunk, cbase, RadixValue{}, bulk_ok, spin_limit(), status_word(),
+                      first_row, cs.chunk_base)));
         SBH_LAUNCHED();
     }
     return SBH_OK;
@@ -1648,11 +1625,11 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_ids_plan", s, plan_bits_kernel<<<1, 32, 0, s>>>(cs.vbits, 2, cs.plan, 0));
     SBH_LAUNCHED();
     Buffers b{in_k, in_p, cs.tmp_k, cs.tmp_p, out_k, out_p};
-    b.in_v = cs.ids_in;
-    b.tmp_v = cs.ids_tmp;
-    b.out_v = cs.ids_out;
+    b.in_ids = cs.ids_in;
+    b.tmp_v = cs.hi_tmp;
+    b.out_v = cs.hi_out;
     // bucket starts: the last pass records each id's first output row, then a
-    // suffix minimum fills the empty buckets (with no pass, read the ids)
+    // suffix minimum fills the empty buckets (with no pass, from the one id)
     SBH_CUDA(cudaMemsetAsync(bstart, 0xFF, (kMaxBucketIds + 1) * sizeof(uint32_t), s));
     rc = carried_passes<kCarryTile, 512>(b, n32, cs, g, s, bstart);
     if (rc) return rc;
@@ -1660,8 +1637,7 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds", s,
-              ids_bounds_kernel<<<(unsigned)min_u64((n + 2047) / 2048, (uint64_t)sms * 8), 256, 0, s>>>(
-                  b, cs.plan, n32, nbid, bstart));
+              ids_bounds_kernel<<<kMaxBucketIds / 256 + 1, 256, 0, s>>>(cs.plan, n32, nbid, cs.vbits, bstart));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds_min", s,
               bounds_min_kernel<<<kFillBlocks, 1024, 0, s>>>(cs.plan, n32, nbid, bstart, cs.bmin));

@@ -61,13 +61,15 @@ struct Buffers {
     uint32_t* tmp_p;
     uint64_t* out_k;
     uint32_t* out_p;
-    // optional 16-bit values carried with the rows (the learned sort's bucket
-    // ids); null when the digit comes from the key
-    const uint16_t* in_v = nullptr;
-    uint16_t* tmp_v = nullptr;
-    uint16_t* out_v = nullptr;
-    __device__ __forceinline__ const uint16_t* vals(int sel) const { return sel == 0 ? in_v : (sel == 1 ? tmp_v : out_v); }
-    __device__ __forceinline__ uint16_t* wvals(int sel) const { return sel == 1 ? tmp_v : out_v; }
+    // the learned sort's 16-bit bucket ids of the input rows, and the bytes
+    // carried with the rows between its two passes (the ids' high bytes);
+    // null otherwise
+    const uint16_t* in_ids = nullptr;
+    const uint8_t* in_v = nullptr;
+    uint8_t* tmp_v = nullptr;
+    uint8_t* out_v = nullptr;
+    __device__ __forceinline__ const uint8_t* vals(int sel) const { return sel == 0 ? in_v : (sel == 1 ? tmp_v : out_v); }
+    __device__ __forceinline__ uint8_t* wvals(int sel) const { return sel == 1 ? tmp_v : out_v; }
     __device__ __forceinline__ const uint64_t* keys(int sel) const { return sel == 0 ? in_k : (sel == 1 ? tmp_k : out_k); }
     __device__ __forceinline__ const uint32_t* ptrs(int sel) const { return sel == 0 ? in_p : (sel == 1 ? tmp_p : out_p); }
     __device__ __forceinline__ uint64_t* wkeys(int sel) const { return sel == 1 ? tmp_k : out_k; }
@@ -611,7 +613,8 @@ struct ScatterSmem {
     static constexpr int kG = THREADS / 128;  // warp groups of the count scan
     uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
     uint32_t ptrs[2][TILE];  // the scatter in digit order
-    uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried values, staged the same way
+    uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried ids, staged the same way (the second
+                                                       // pass's carried bytes arrive in the first TILE bytes)
     uint8_t dig[kDig ? TILE : 16];                     // digit of each staged row (derived values only)
     // per-warp digit counts, two 16-bit counters per word (digits 2w, 2w+1;
     // word 128 holds the sentinel digit of rows past the end)
@@ -620,6 +623,8 @@ struct ScatterSmem {
     uint16_t gstart[kG][kRadix];     // first staged slot of each (group, digit)
     uint32_t run[kRadix];            // next output row of each digit in this chunk
     uint32_t gbase_rel[kRadix];      // output row minus staged slot, per digit
+    uint32_t lw[kCarry ? 4 : 1];     // low-byte walk: digit so far, next digit start, tile's first digit,
+                                     // digit starts inside the tile (listed in gsum until B1)
     uint64_t mbar[2];
 };
 
@@ -642,7 +647,8 @@ template <typename ValueFn, int TILE, int THREADS, bool kCarry = false>
 __global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value))
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
-                     uint32_t* __restrict__ status, uint32_t* __restrict__ first_row = nullptr) {
+                     uint32_t* __restrict__ status, uint32_t* __restrict__ first_row = nullptr,
+                     const uint32_t* __restrict__ low_base = nullptr) {
     constexpr bool kDig = ScatterDig<ValueFn, kCarry>::value;
     using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig>;
     constexpr int kW = Smem::kW, kG = Smem::kG, kWpg = kW / kG;
@@ -657,14 +663,24 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint32_t* __restrict__ in_p = buf.ptrs(src);
     uint64_t* __restrict__ out_k = buf.wkeys(dst);
     uint32_t* __restrict__ out_p = buf.wptrs(dst);
-    const uint16_t* __restrict__ in_v = kCarry ? buf.vals(src) : nullptr;
-    uint16_t* __restrict__ out_v = kCarry ? buf.wvals(dst) : nullptr;
-    // Carried 16-bit values, last of the two passes, first_row given: the
-    // values are not written out; instead every value's first output row is
-    // recorded (atomicMin into first_row[value]).  A staged tile of the last
-    // pass is in value order, so a row whose value differs from the staged
-    // row before it is the first of its value in this tile.
+    // Carried 16-bit ids (kCarry: two passes, low byte then high byte).  The
+    // first pass reads each input row's id (in_ids) and writes the id's high
+    // byte with the row.  The second orders by that byte and recovers the low
+    // byte from the row's position: the first pass left the rows grouped by
+    // low byte, rows [low_base[d], low_base[d + 1]) holding low byte d
+    // (low_base = the first pass's digit bases).  A second pass after no
+    // first one reads the input ids too.
+    const bool full_ids = kCarry && (pos == 0 || !plan->active[0]);
+    const bool walk = kCarry && !full_ids;
+    // Last of the passes, first_row given: the ids are not written out;
+    // instead every id's first output row is recorded (atomicMin into
+    // first_row[id]).  A staged tile of the last pass is in id order, so a
+    // row whose id differs from the staged row before it is the first of its
+    // id in this tile.
     const bool rows_pass = kCarry && first_row != nullptr && (pos == 1 || !plan->active[1]);
+    const uint16_t* __restrict__ in_ids = full_ids ? buf.in_ids : nullptr;
+    const uint8_t* __restrict__ in_v = walk ? buf.vals(src) : nullptr;
+    uint8_t* __restrict__ out_v = (kCarry && !rows_pass) ? buf.wvals(dst) : nullptr;
     const uint32_t lo = blockIdx.x * chunk;
     const uint32_t hi = min(n, lo + chunk);
     if (lo >= hi) return;
@@ -677,10 +693,12 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * TILE <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
         if (i < ntl && bulk_tile(i)) {
-            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t) + (kCarry ? sizeof(uint16_t) : 0)));
+            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t)) +
+                                            (full_ids ? TILE * sizeof(uint16_t) : (walk ? TILE : 0)));
             bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b]);
             bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
-            if (kCarry) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
+            if (full_ids) bulk_load(sm.vals[b], in_ids + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
+            if (walk) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE, &sm.mbar[b]);
         }
     };
     for (int x = tid; x < kW * (kRadix / 2 + 1); x += THREADS) (&sm.whist2[0][0])[x] = 0;
@@ -691,6 +709,10 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         fence_mbar_init();
         issue(0, 0);
         issue(1, 1);
+        if (walk) {
+            sm.lw[0] = 0;  // low_base[0] = 0: every position is in digit 0 or later
+            sm.lw[1] = low_base[1];
+        }
     }
     __syncthreads();
     uint32_t phase[2] = {0u, 0u};
@@ -699,6 +721,42 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         const int b = i & 1;
         const uint32_t base = lo + i * TILE;
         const uint32_t valid = min(hi - base, (uint32_t)TILE);
+        if constexpr (kCarry) {
+            // warp 0: the low byte of the tile's first row (d0) and the digit
+            // starts inside the tile (m of them, ascending), walking on from
+            // the previous tile; a start at or before base moves d0 on
+            if (walk && warp == 0) {
+                const uint32_t tend = base + valid - 1;
+                const uint32_t c = sm.lw[0];
+                uint32_t d0 = c, m = 0;
+                if (sm.lw[1] <= tend) {
+                    uint32_t* list = &sm.gsum[0][0];
+                    uint32_t nb = 0, na = 0, after = 0xFFFFFFFFu;
+                    for (uint32_t d = c + 1; d < (uint32_t)kRadix; d += 32) {
+                        const uint32_t v = d + lane < (uint32_t)kRadix ? low_base[d + lane] : 0xFFFFFFFFu;
+                        const uint32_t cb = __popc(__ballot_sync(0xffffffffu, v <= base));
+                        const uint32_t ca = __popc(__ballot_sync(0xffffffffu, v <= tend));
+                        nb += cb;  // final once a lane of this group starts past base
+                        if (v > base && v <= tend) list[d - c - 1 + lane - nb] = v;
+                        na += ca;
+                        if (ca < 32) {
+                            after = __shfl_sync(0xffffffffu, v, ca);
+                            break;
+                        }
+                    }
+                    d0 = c + nb;
+                    m = na - nb;
+                    if (lane == 0) {
+                        sm.lw[0] = c + na;  // the digit of the tile's last row
+                        sm.lw[1] = after;   // and where the next one starts
+                    }
+                }
+                if (lane == 0) {
+                    sm.lw[2] = d0;
+                    sm.lw[3] = m;
+                }
+            }
+        }
         bool expired = false;
         if (bulk_tile(i)) {
             uint32_t polls = 0;
@@ -712,7 +770,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             for (uint32_t s = tid; s < valid; s += THREADS) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
-                if (kCarry) sm.vals[b][s] = in_v[base + s];
+                if (full_ids) sm.vals[b][s] = in_ids[base + s];
+                if (walk) reinterpret_cast<uint8_t*>(sm.vals[b])[s] = in_v[base + s];
             }
         }
         // B0.  A tile whose data never arrived is not scattered (its rows
@@ -738,7 +797,26 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             for (int j = 0; j < kIt; ++j) {
                 k[j] = kb[wofs + j * 32];
                 p[j] = pb[wofs + j * 32];
-                if (kCarry) cv[j] = vb[wofs + j * 32];
+                if (kCarry) cv[j] = walk ? reinterpret_cast<const uint8_t*>(vb)[wofs + j * 32] : vb[wofs + j * 32];
+            }
+            if constexpr (kCarry) {
+                if (walk) {
+                    const uint32_t d0 = sm.lw[2], m = sm.lw[3];
+                    const uint32_t* list = &sm.gsum[0][0];
+#pragma unroll
+                    for (int j = 0; j < kIt; ++j) {
+                        if (full || wofs + j * 32 < valid) {  // low byte: d0 + the digit starts up to this row
+                            const uint32_t row = base + wofs + j * 32;
+                            uint32_t a = 0, z = m;
+                            while (a < z) {
+                                const uint32_t mid = (a + z) >> 1;
+                                if (list[mid] <= row) a = mid + 1;
+                                else z = mid;
+                            }
+                            cv[j] = (cv[j] << 8) | (d0 + a);
+                        }
+                    }
+                }
             }
 #pragma unroll
             for (int j = 0; j < kIt; ++j) {
@@ -864,7 +942,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                                 const uint16_t v = vb[s];
                                 if (s == 0 || vb[s - 1] != v) atomicMin(first_row + v, g);
                             } else {
-                                out_v[g] = vb[s];
+                                out_v[g] = static_cast<uint8_t>(vb[s] >> 8);
                             }
                         }
                     }

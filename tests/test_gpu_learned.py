@@ -139,7 +139,8 @@ def test_quantile_start_matches_oracle_and_training_refines_it(S, hashed):
 
 @pytest.mark.parametrize("start", ["seeded", "quantile"])
 @pytest.mark.parametrize("n,kind", [(1, "mixed"), (5000, "mixed"), (3_000_017, "mixed"), (2_500_000, "uniform"),
-                                    (2_100_000, "equal"), (2_200_000, "highbyte"), (3_000_001, "hashed")])
+                                    (2_100_000, "equal"), (2_200_000, "highbyte"), (3_000_001, "hashed"),
+                                    (600_011, "smallkeys"), (2_000_003, "smallkeys")])
 def test_learned_sort_equals_plain_sort(S, n, kind, start):
     if kind == "mixed":
         col = gen.mixed_keys(n, seed=7)
@@ -149,6 +150,8 @@ def test_learned_sort_equals_plain_sort(S, n, kind, start):
         col = gen.uniform(7, 1, n, 0, 0, np.uint64)
     elif kind == "equal":
         col = np.full(n, 12345, dtype=np.uint64)
+    elif kind == "smallkeys":  # 4096 key values, exact cells: ids below 256, one pass
+        col = gen.uniform(7, 3, n, 0, 4096, np.uint64)
     else:
         col = gen.uniform(7, 2, n, 0, 256, np.uint64) << np.uint64(56)
     sample = col[::100].copy()
@@ -161,6 +164,8 @@ def test_learned_sort_equals_plain_sort(S, n, kind, start):
     ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
     assert same(sk, ok) and same(sp, op)
     assert stats["overflow_rows"] <= n
+    if kind in ("mixed", "hashed") and n >= 3_000_000:  # both id bytes vary: the second pass runs
+        assert stats["bucket_ids"] > 256
 
 
 @pytest.mark.parametrize("hashed", [False, True])
