@@ -45,6 +45,7 @@ constexpr int kTile = kThreads * kIpt;      // keys per tile
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 56) - 1;
+constexpr int kLookWidth = 4;  // look-back records read at once
 
 struct Plan {
     int active[kPositions];
@@ -412,19 +413,32 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         }
         if (lane == 31) sm.scan_tmp[warp] = x;
 
-        uint64_t excl = 0;  // decoupled look-back over earlier tiles (bounded)
+        // decoupled look-back over earlier tiles (bounded): the records of
+        // four earlier tiles are read at once and taken in order, summing
+        // aggregates until an inclusive prefix (tile 0 always publishes one);
+        // a record not yet published is read again
+        uint64_t excl = 0;
         if (tile > 0) {
             uint32_t t = tile - 1;
             uint32_t polls = 0;
-            for (;;) {
-                const uint64_t r = ld_relaxed(lookback + (uint64_t)t * kRadix + d);
-                if ((r & (3ull << 62)) == 0 || (r & (63ull << 56)) != epoch) {
-                    if (wait_expired(polls, spin_limit, status)) break;
-                    continue;
+            for (bool done = false; !done;) {
+                uint64_t r[kLookWidth];
+#pragma unroll
+                for (int u = 0; u < kLookWidth; ++u)
+                    r[u] = t >= (uint32_t)u ? ld_relaxed(lookback + (uint64_t)(t - u) * kRadix + d) : 0ull;
+                int u = 0;
+#pragma unroll
+                for (; u < kLookWidth; ++u) {
+                    if ((r[u] & (3ull << 62)) == 0 || (r[u] & (63ull << 56)) != epoch) break;
+                    excl += r[u] & kValueMask;
+                    if ((r[u] & (3ull << 62)) == kFlagPrefix || t == (uint32_t)u) {
+                        done = true;
+                        break;
+                    }
                 }
-                excl += r & kValueMask;
-                if ((r & (3ull << 62)) == kFlagPrefix || t == 0) break;
-                --t;
+                if (done) break;
+                t -= u;  // every record before t is an aggregate taken; t is not published yet
+                if (u < kLookWidth && wait_expired(polls, spin_limit, status)) break;
             }
             st_relaxed(rec, kFlagPrefix | epoch | ((excl + cnt) & kValueMask));
         }
