@@ -46,7 +46,7 @@ CPU_SAMPLE = 4_000_000
 # scatter the mean of its two passes).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"sort_scatter": 24.57}
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 26.35, "sort_scatter": 24.57}
 
 
 def _dist():

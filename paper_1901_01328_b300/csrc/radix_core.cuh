@@ -816,18 +816,23 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             if constexpr (kCarry) {
                 if (walk) {
                     const uint32_t d0 = sm.lw[2], m = sm.lw[3];
-                    const uint32_t* list = &sm.gsum[0][0];
+                    if (m == 0) {  // the usual case: one low byte for the whole tile
 #pragma unroll
-                    for (int j = 0; j < kIt; ++j) {
-                        if (full || wofs + j * 32 < valid) {  // low byte: d0 + the digit starts up to this row
-                            const uint32_t row = base + wofs + j * 32;
-                            uint32_t a = 0, z = m;
-                            while (a < z) {
-                                const uint32_t mid = (a + z) >> 1;
-                                if (list[mid] <= row) a = mid + 1;
-                                else z = mid;
+                        for (int j = 0; j < kIt; ++j) cv[j] = (cv[j] << 8) | d0;
+                    } else {
+                        const uint32_t* list = &sm.gsum[0][0];
+#pragma unroll
+                        for (int j = 0; j < kIt; ++j) {
+                            if (full || wofs + j * 32 < valid) {  // low byte: d0 + the digit starts up to this row
+                                const uint32_t row = base + wofs + j * 32;
+                                uint32_t a = 0, z = m;
+                                while (a < z) {
+                                    const uint32_t mid = (a + z) >> 1;
+                                    if (list[mid] <= row) a = mid + 1;
+                                    else z = mid;
+                                }
+                                cv[j] = (cv[j] << 8) | (d0 + a);
                             }
-                            cv[j] = (cv[j] << 8) | (d0 + a);
                         }
                     }
                 }
