@@ -987,6 +987,9 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
     if (tid == 0) sm.next[0] = atomicAdd(counter, 1u);
     __syncthreads();
     uint32_t b = sm.next[0];
+    // the next bucket's rows are copied into buffer 0 while the current
+    // bucket is written out of buffer 1 (when the next one is sorted here)
+    bool prefetched = false;
     for (uint32_t it = 1;; ++it) {
         if (b >= nbid) break;
         // the bucket after this one; read after this bucket's first barrier,
@@ -1012,15 +1015,29 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
         if (tid == 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
         // load (buffer 0), the key range, and clear the bins
         uint64_t kmin = ~0ull, kmax = 0;
+        if (prefetched) {
+            cp_async_wait_all();  // this thread's own rows: no barrier needed to read them
 #pragma unroll
-        for (int j = 0; j < kBIpt; ++j) {
-            const uint32_t r = tid + j * kBThreads;
-            if (r < cnt) {
-                const uint64_t k = keys[s + r];
-                sm.keys[0][r] = k;
-                sm.ptrs[0][r] = ptrs[s + r];
-                kmin = min(kmin, k);
-                kmax = max(kmax, k);
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t r = tid + j * kBThreads;
+                if (r < cnt) {
+                    const uint64_t k = sm.keys[0][r];
+                    kmin = min(kmin, k);
+                    kmax = max(kmax, k);
+                }
+            }
+            prefetched = false;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t r = tid + j * kBThreads;
+                if (r < cnt) {
+                    const uint64_t k = keys[s + r];
+                    sm.keys[0][r] = k;
+                    sm.ptrs[0][r] = ptrs[s + r];
+                    kmin = min(kmin, k);
+                    kmax = max(kmax, k);
+                }
             }
         }
 #pragma unroll
@@ -1222,6 +1239,22 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 a ^= 1;
             }
             res = a;
+        }
+        if (res == 1 && nb < nbid) {  // buffer 0 is free: bring in the next bucket (a range not this one's)
+            const uint32_t s2 = bstart[nb], cnt2 = bstart[nb + 1] - s2;
+            const bool heavy2 = ((heavy_bucket_bits[nb >> 5] >> (nb & 31)) & 1u) != 0;
+            if (cnt2 > 1 && !heavy2 && cnt2 <= kCap) {
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t r = tid + j * kBThreads;
+                    if (r < cnt2) {
+                        cp_async8(&sm.keys[0][r], keys + s2 + r);
+                        cp_async4(&sm.ptrs[0][r], ptrs + s2 + r);
+                    }
+                }
+                cp_async_commit();
+                prefetched = true;
+            }
         }
 #pragma unroll
         for (int j = 0; j < kBIpt; ++j) {
