@@ -16,23 +16,39 @@ __global__ void __launch_bounds__(256) extract_kernel(const uint64_t* __restrict
     const uint32_t nthreads = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (kVec) {
+        // two groups of four rows in flight per thread; rem = (first row of
+        // the group) mod stride, advanced without dividing
         const uint32_t nq = n / 4;
-        for (uint32_t q = tid; q < nq; q += nthreads) {
+        const uint32_t step_mod = samples ? (4u * nthreads) % stride : 0u;
+        uint32_t rem = samples ? (4u * tid) % stride : 0u;
+        auto group = [&](uint32_t q, const ulonglong2& a, const ulonglong2& b) {
             const uint32_t i = q * 4;
-            ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(src + i));
-            ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(src + i + 2));
             __stcs(reinterpret_cast<ulonglong2*>(keys + i), a);
             __stcs(reinterpret_cast<ulonglong2*>(keys + i + 2), b);
-            uint4 p = make_uint4(row_begin + i, row_begin + i + 1, row_begin + i + 2, row_begin + i + 3);
+            const uint4 p = make_uint4(row_begin + i, row_begin + i + 1, row_begin + i + 2, row_begin + i + 3);
             __stcs(reinterpret_cast<uint4*>(ptrs + i), p);
             acc |= a.x | a.y | b.x | b.y;
             if (samples) {
-                uint32_t first = ((i + stride - 1) / stride) * stride;  // first sampled row >= i
-                if (first < i + 4) {
-                    uint64_t v[4] = {a.x, a.y, b.x, b.y};
-                    for (uint32_t r = first; r < i + 4; r += stride) samples[r / stride] = v[r - i];
+                const uint32_t off = rem ? stride - rem : 0u;  // first sampled row is i + off
+                if (off < 4) {
+                    const uint64_t v[4] = {a.x, a.y, b.x, b.y};
+                    for (uint64_t o = off; o < 4; o += stride) samples[(i + o) / stride] = v[o];
                 }
+                rem += step_mod;
+                if (rem >= stride) rem -= stride;
             }
+        };
+        for (uint32_t q = tid; q < nq; q += 2 * nthreads) {
+            const uint32_t q2 = q + nthreads;
+            const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(src + 4 * q));
+            const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(src + 4 * q + 2));
+            ulonglong2 c = make_ulonglong2(0, 0), d = make_ulonglong2(0, 0);
+            if (q2 < nq) {
+                c = __ldcs(reinterpret_cast<const ulonglong2*>(src + 4 * q2));
+                d = __ldcs(reinterpret_cast<const ulonglong2*>(src + 4 * q2 + 2));
+            }
+            group(q, a, b);
+            if (q2 < nq) group(q2, c, d);
         }
         for (uint32_t i = nq * 4 + tid; i < n; i += nthreads) {
             uint64_t k = src[i];

@@ -37,6 +37,17 @@ def test_extract_parity(S, n, row_begin):
         assert same(samples, ok[::100])
 
 
+@pytest.mark.parametrize("stride", [1, 3, 4, 7, 100, 4096, 2_000_000])
+def test_extract_sample_strides(S, stride):
+    # groups of four rows with zero, one or several sampled rows (16-byte path)
+    n = 1_000_003
+    col = gen.mixed_keys(n)
+    keys, ptrs, key_or, samples = S.extract(cuda(col), 0, n, sample_stride=stride)
+    ok, op = oracle.extract(col, 0, n)
+    assert same(keys, ok) and same(ptrs, op)
+    assert same(samples, ok[::stride])
+
+
 def test_extract_from_pinned_host(S):
     col = gen.join_streams(300_001, key_space=1 << 24)["L"]["keys"]
     pinned = torch.from_numpy(col).pin_memory()
