@@ -968,13 +968,15 @@ struct BucketStats {
 };
 
 // Persistent CTAs take buckets in order from a counter and sort each one in
-// shared memory: a counting placement by the top 12 bits of key - kmin and
-// insertion sorts inside the sub-buckets, or (a sub-bucket over 32 rows)
-// stable 8-bit radix passes on key - kmin.  Rows of one key stay in ptr
-// order because the scatter that formed the bucket was stable.  (Bringing
-// the next bucket in by asynchronous copies during the current sort, and
-// sorting sub-buckets of 9 to 32 rows by a warp's bitonic network, were both
-// measured and neither was faster.)
+// shared memory: a counting placement by the top 12 bits of key - kmin, after
+// which every row finds its rank among the rows of its sub-bucket (at most
+// 32) by (key, ptr) and is written straight to its output row; or (a
+// sub-bucket over 32 rows) stable 8-bit radix passes on key - kmin.  Rows of
+// one key stay in ptr order because the scatter that formed the bucket was
+// stable.  While a bucket's rows are being stored, the next bucket's are
+// copied into the free buffer.  (Per-thread insertion sorts of the
+// sub-buckets, and a warp's bitonic network for sub-buckets of 9 to 32 rows,
+// measured slower than the ranks.)
 __global__ void __launch_bounds__(kBThreads, 1)
 bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
                    const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
@@ -997,6 +999,25 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
         if (tid == 0) sm.next[it & 1] = atomicAdd(counter, 1u);
         const uint32_t s = bstart[b], e = bstart[b + 1], cnt = e - s;
         const bool heavy = ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) != 0;
+        // copies the next bucket's rows into buffer 0 once it is free (a
+        // range not this one's), if the next bucket is sorted here
+        auto prefetch_next = [&](uint32_t nxt) {
+            if (nxt >= nbid) return;
+            const uint32_t s2 = bstart[nxt], cnt2 = bstart[nxt + 1] - s2;
+            const bool heavy2 = ((heavy_bucket_bits[nxt >> 5] >> (nxt & 31)) & 1u) != 0;
+            if (cnt2 > 1 && !heavy2 && cnt2 <= kCap) {
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t r = tid + j * kBThreads;
+                    if (r < cnt2) {
+                        cp_async8(&sm.keys[0][r], keys + s2 + r);
+                        cp_async4(&sm.ptrs[0][r], ptrs + s2 + r);
+                    }
+                }
+                cp_async_commit();
+                prefetched = true;
+            }
+        };
         if (cnt <= 1 || heavy || cnt > kCap) {
             if (tid == 0) {
                 if (cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
@@ -1126,28 +1147,29 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                     }
                 }
                 __syncthreads();  // (e)
-                // bins[d] now holds the end of bin d: insertion sort by (key,
-                // ptr) inside each of this thread's bins
-#pragma unroll 1
-                for (int q = 0; q < kFinePer; ++q) {
-                    const int d = tid * kFinePer + q;
-                    const uint32_t e2 = sm.bins[d], b2 = e2 - v[q];
-                    for (uint32_t i2 = b2 + 1; i2 < e2; ++i2) {
-                        const uint64_t kk = sm.keys[1][i2];
-                        const uint32_t pp = sm.ptrs[1][i2];
-                        uint32_t j2 = i2;
-                        while (j2 > b2 && (sm.keys[1][j2 - 1] > kk ||
-                                           (sm.keys[1][j2 - 1] == kk && sm.ptrs[1][j2 - 1] > pp))) {
-                            sm.keys[1][j2] = sm.keys[1][j2 - 1];
-                            sm.ptrs[1][j2] = sm.ptrs[1][j2 - 1];
-                            --j2;
+                // bins[d] now holds the end of bin d and bins[d - 1] its
+                // start: each row's rank among its bin's rows by (key, ptr)
+                // (at most kFineMaxBin of them), and the row goes straight to
+                // its output row
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t i = tid + j * kBThreads;
+                    if (i < cnt) {
+                        const uint64_t k = sm.keys[1][i];
+                        const uint32_t p = sm.ptrs[1][i];
+                        const uint32_t d = static_cast<uint32_t>((k - kmin) >> fsh);
+                        const uint32_t e2 = sm.bins[d], b2 = d ? sm.bins[d - 1] : 0u;
+                        uint32_t r = 0;
+                        for (uint32_t x = b2; x < e2; ++x) {
+                            const uint64_t kx = sm.keys[1][x];
+                            r += (kx < k || (kx == k && sm.ptrs[1][x] < p)) ? 1u : 0u;
                         }
-                        sm.keys[1][j2] = kk;
-                        sm.ptrs[1][j2] = pp;
+                        keys[s + b2 + r] = k;
+                        ptrs[s + b2 + r] = p;
                     }
                 }
-                __syncthreads();  // (f)
-                res = 1;
+                __syncthreads();  // (f) the bins and buffer 1 are read no more
+                res = 2;  // already written out
             }
         }
         if (res < 0) {
@@ -1240,28 +1262,17 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             }
             res = a;
         }
-        if (res == 1 && nb < nbid) {  // buffer 0 is free: bring in the next bucket (a range not this one's)
-            const uint32_t s2 = bstart[nb], cnt2 = bstart[nb + 1] - s2;
-            const bool heavy2 = ((heavy_bucket_bits[nb >> 5] >> (nb & 31)) & 1u) != 0;
-            if (cnt2 > 1 && !heavy2 && cnt2 <= kCap) {
+        // buffer 0 is free: the next bucket's copies overlap this bucket's
+        // stores (issuing them during the ranking measured slower)
+        if (res >= 1) prefetch_next(nb);
+        if (res < 2) {
 #pragma unroll
-                for (int j = 0; j < kBIpt; ++j) {
-                    const uint32_t r = tid + j * kBThreads;
-                    if (r < cnt2) {
-                        cp_async8(&sm.keys[0][r], keys + s2 + r);
-                        cp_async4(&sm.ptrs[0][r], ptrs + s2 + r);
-                    }
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t r = tid + j * kBThreads;
+                if (r < cnt) {
+                    keys[s + r] = sm.keys[res][r];
+                    ptrs[s + r] = sm.ptrs[res][r];
                 }
-                cp_async_commit();
-                prefetched = true;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kBIpt; ++j) {
-            const uint32_t r = tid + j * kBThreads;
-            if (r < cnt) {
-                keys[s + r] = sm.keys[res][r];
-                ptrs[s + r] = sm.ptrs[res][r];
             }
         }
         if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
