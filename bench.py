@@ -294,6 +294,22 @@ def run_gpu(args):
     assert sbh.sync_status() == sbh.SBH_OK
     n_unique = int(nkeys.item())
 
+    def verify(src):
+        """Outside the timed region: the learned step's sorted KPA and per-key
+        counts equal the plain radix step's on the same window."""
+        step_plain(src)
+        m = int(nkeys.item())
+        ref = (sk.clone(), sp.clone(), out_keys[:m].clone(), out_counts[:m].clone())
+        step_learned(src)
+        ok = (sbh.sync_status() == sbh.SBH_OK and int(nkeys.item()) == m and torch.equal(sk, ref[0])
+              and torch.equal(sp, ref[1]) and torch.equal(out_keys[:m], ref[2])
+              and torch.equal(out_counts[:m], ref[3]))
+        del ref
+        torch.cuda.empty_cache()
+        return bool(ok)
+
+    verified = {"mixed_keys": verify(col)}
+
     # ---- device-resident timing of the headline step
     with Clocks(local) as clk:
         ms = timed(step, args.steps)
@@ -313,6 +329,7 @@ def run_gpu(args):
         variants = {}
         # the Zipf ranks through mix64: the same multiplicities, spread over all 64 bits
         col2 = torch.from_numpy(gen.mixed_keys(n, seed=window_seed(gen.SEED_MIXED, rank), hashed=True)).to(dev)
+        verified["hashed_zipf"] = verify(col2)
         for _ in range(2):
             step_learned(col2)
         ms_l2 = timed(lambda: step_learned(col2), args.steps)
@@ -396,6 +413,10 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "text": WORKLOAD_TEXT, "rows_per_gpu": n, "sort": args.sort,
                        "distinct_keys": n_unique, "l2": "inputs larger than L2 (3 GB KPA per step)",
                        "parallelism": f"replicas{ws}", "train": TRAIN, "sample_stride": SAMPLE_STRIDE},
+            "verified": all(verified.values()),
+            "verified_detail": {"check": "learned step's sorted KPA and per-key counts equal the plain radix "
+                                         "step's on the same window (torch.equal, outside the timed region)",
+                                **verified},
             "roofline": roofline,
             "cpu_baseline": cpu_baseline() if ws == 1 and not args.no_cpu else None,
             "e2e": e2e,

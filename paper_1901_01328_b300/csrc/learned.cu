@@ -29,8 +29,9 @@
 // the parity of the heavy term).  Bucket ids are therefore non-decreasing in
 // the key (integer arithmetic only), so a stable sort by bucket id followed
 // by a sort inside each bucket sorts the KPA.  Buckets of one key are already
-// in ptr order; buckets above the shared-memory capacity go to the plain
-// radix sort.
+// in input order; buckets above the shared-memory capacity go to the plain
+// radix sort.  Every step is stable, so rows of equal keys keep their input
+// order, as in the plain sort.
 #include <algorithm>
 #include <vector>
 
@@ -970,10 +971,10 @@ struct BucketStats {
 // Persistent CTAs take buckets in order from a counter and sort each one in
 // shared memory: a counting placement by the top 12 bits of key - kmin, after
 // which every row finds its rank among the rows of its sub-bucket (at most
-// 32) by (key, ptr) and is written straight to its output row; or (a
-// sub-bucket over 32 rows) stable 8-bit radix passes on key - kmin.  Rows of
-// one key stay in ptr order because the scatter that formed the bucket was
-// stable.  While a bucket's rows are being stored, the next bucket's are
+// 32) by (key, place in the bucket) and is written straight to its output
+// row; or (a sub-bucket over 32 rows) stable 8-bit radix passes on key -
+// kmin.  Rows of one key keep their input order: the scatter that formed the
+// bucket was stable, and both in-bucket sorts are.  While a bucket's rows are being stored, the next bucket's are
 // copied into the free buffer.  (Per-thread insertion sorts of the
 // sub-buckets, and a warp's bitonic network for sub-buckets of 9 to 32 rows,
 // measured slower than the ranks.)
@@ -1022,7 +1023,7 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             if (tid == 0) {
                 if (cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
                 if (cnt > 1 && heavy) {
-                    atomicAdd(&st->heavy_buckets, 1ull);  // one key: the stable scatter left it in ptr order
+                    atomicAdd(&st->heavy_buckets, 1ull);  // one key: the stable scatter left it in input order
                 } else if (cnt > 1) {
                     ov_flag[b] = 1;
                     atomicAdd(&st->overflow_buckets, 1ull);
@@ -1083,7 +1084,7 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             if (tid == 0) atomicAdd(&st->single_key_buckets, 1ull);
             __syncthreads();  // buffer 0 is read no more
             b = nb;
-            continue;  // one key value: already in ptr order, nothing to write
+            continue;  // one key value: already in input order, nothing to write
         }
         const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
         int res = -1;  // buffer holding the sorted bucket
@@ -1143,29 +1144,29 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                         const uint64_t k = sm.keys[0][r];
                         const uint32_t pos = atomicAdd(&sm.bins[static_cast<uint32_t>((k - kmin) >> fsh)], 1u);
                         sm.keys[1][pos] = k;
-                        sm.ptrs[1][pos] = sm.ptrs[0][r];
+                        sm.ptrs[1][pos] = r;  // the row's place in buffer 0: its input order
                     }
                 }
                 __syncthreads();  // (e)
                 // bins[d] now holds the end of bin d and bins[d - 1] its
-                // start: each row's rank among its bin's rows by (key, ptr)
-                // (at most kFineMaxBin of them), and the row goes straight to
-                // its output row
+                // start: each row's rank among its bin's rows (at most
+                // kFineMaxBin of them) by (key, input order), and the row,
+                // with its ptr from buffer 0, goes straight to its output row
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
                     const uint32_t i = tid + j * kBThreads;
                     if (i < cnt) {
                         const uint64_t k = sm.keys[1][i];
-                        const uint32_t p = sm.ptrs[1][i];
+                        const uint32_t q = sm.ptrs[1][i];
                         const uint32_t d = static_cast<uint32_t>((k - kmin) >> fsh);
                         const uint32_t e2 = sm.bins[d], b2 = d ? sm.bins[d - 1] : 0u;
                         uint32_t r = 0;
                         for (uint32_t x = b2; x < e2; ++x) {
                             const uint64_t kx = sm.keys[1][x];
-                            r += (kx < k || (kx == k && sm.ptrs[1][x] < p)) ? 1u : 0u;
+                            r += (kx < k || (kx == k && sm.ptrs[1][x] < q)) ? 1u : 0u;
                         }
                         keys[s + b2 + r] = k;
-                        ptrs[s + b2 + r] = p;
+                        ptrs[s + b2 + r] = sm.ptrs[0][q];
                     }
                 }
                 __syncthreads();  // (f) the bins and buffer 1 are read no more

@@ -1,8 +1,11 @@
 """sbh_group_reduce_noalloc: the keyed reduction for callers that cannot
 allocate device memory when they call (it keeps its working memory in a fixed
 device array).  Checked through the C ABI against sbh_group_reduce, which
-takes caller scratch, on two calls in a row.  This file is collected last so
-that a run stopping at its first failure has run every other test first."""
+takes caller scratch, on two calls in a row, and against the oracle's
+grouping of the oracle's own sort, up to a window of more than 4096 tiles
+(where the fixed array also holds the block totals of the tile scan).  This
+file is collected last so that a run stopping at its first failure has run
+every other test first."""
 import ctypes
 
 import numpy as np
@@ -10,6 +13,7 @@ import pytest
 import torch
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -31,9 +35,10 @@ def _run(S, sk, sp, vals, scratch_for_reference=False):
     osum = torch.full((n,), 7, dtype=torch.uint64, device=dev)
     nk = torch.full((1,), 7, dtype=torch.uint64, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
-    vb = vals.element_size()
-    args = [sk.data_ptr(), sp.data_ptr(), n, vals.data_ptr(), vb, ok.data_ptr(), oc.data_ptr(), osum.data_ptr(), n,
-            nk.data_ptr()]
+    vb = 8 if vals is None else vals.element_size()
+    vp = None if vals is None else vals.data_ptr()
+    sump = None if vals is None else osum.data_ptr()
+    args = [sk.data_ptr(), sp.data_ptr(), n, vp, vb, ok.data_ptr(), oc.data_ptr(), sump, n, nk.data_ptr()]
     if scratch_for_reference:
         nb = ctypes.c_size_t(0)
         assert lib.sbh_group_reduce(*args, None, ctypes.byref(nb), stream) == 0
@@ -61,6 +66,21 @@ def test_noalloc_matches_scratch_version_twice(S, vbytes):
         got = _run(S, sk, sp, d_vals)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b)
+        ok, oc, osum = oracle.group_sum_count(*oracle.sort(*oracle.extract(col, 0, n)), vals)
+        assert np.array_equal(got[0], ok) and np.array_equal(got[1], oc) and np.array_equal(got[2], osum)
+
+
+def test_noalloc_count_only_above_4096_tiles(S):
+    # 20M rows = 4883 tiles of 4096: the tile scan goes through block totals,
+    # which also live in the fixed array; then a small window right after
+    for seed, n in ((3, 20_000_000), (4, 5_000)):
+        col = gen.mixed_keys(n, seed=seed)
+        keys, ptrs = S.extract(torch.from_numpy(col).cuda(), 0, n)
+        sk, sp = S.sort(keys, ptrs)
+        got = _run(S, sk, sp, None)
+        ok, oc, _ = oracle.group_sum_count(col, np.arange(n, dtype=np.uint32), None)
+        assert np.array_equal(got[0], ok) and np.array_equal(got[1], oc)
+        assert int(got[1].sum()) == n
 
 
 def test_noalloc_rejects_rows_beyond_its_array(S):
