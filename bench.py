@@ -242,7 +242,7 @@ def run_gpu(args):
     out_counts = torch.empty(n, dtype=torch.uint64, device=dev)
     nkeys = torch.zeros(1, dtype=torch.uint64, device=dev)
     scr = {}
-    stats = {}
+    stats_d = torch.zeros(len(sbh.LEARNED_STATS), dtype=torch.uint64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     outs0 = (out_keys, out_counts, nkeys)
@@ -250,7 +250,7 @@ def run_gpu(args):
     def step_learned(src=col, outs=outs0):
         sbh.sbh_kpa_extract(src, 0, n, keys, ptrs, None, samples, SAMPLE_STRIDE)
         scr["train"] = sbh.sbh_learned_train(samples, n, init, TRAIN["steps"], TRAIN["batch"], TRAIN["lr"], model)
-        stats.update(sbh.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, scratch=lsort_scratch))
+        sbh.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, stats_d, scratch=lsort_scratch)
         scr["red"] = sbh.sbh_group_reduce(sk, None, None, outs[0], outs[1], None, n, outs[2], scratch=scr.get("red"))
 
     def step_plain(src=col, outs=outs0):
@@ -316,12 +316,15 @@ def run_gpu(args):
     clocks = clk.summary()
     value = whole_job_rate(args.steps, n, ws, ms)
     assert sbh.sync_status() == sbh.SBH_OK
+    stats = sbh.stats_dict(stats_d) if step is step_learned else {}
 
     # ---- the other sort path on the same window, for the comparison
     other = step_plain if step is step_learned else step_learned
     for _ in range(2):
         other()
     ms_other = timed(other, args.steps)
+    if other is step_learned:
+        stats = sbh.stats_dict(stats_d)
 
     # ---- robustness variant and an external library sort, on the same window size
     variants = None
@@ -333,7 +336,7 @@ def run_gpu(args):
         for _ in range(2):
             step_learned(col2)
         ms_l2 = timed(lambda: step_learned(col2), args.steps)
-        st2 = dict(stats)
+        st2 = sbh.stats_dict(stats_d)
         for _ in range(2):
             step_plain(col2)
         ms_p2 = timed(lambda: step_plain(col2), args.steps)

@@ -361,19 +361,25 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
 /* Sorts a KPA with the model: bucket ids from the model's CDF (monotone in
  * the key by construction), a stable scatter by bucket id, a shared-memory
  * sort of every bucket of at most SBH_LEARNED_CAPACITY rows and more than one
- * key, and the plain radix sort for the rows of larger buckets.  The output
- * is identical to sbh_kpa_sort's; input and output must not alias.  The
- * call synchronises `stream` once (the overflow size decides the last step).
- * h_stats (nullable, host, SBH_LEARNED_STATS values): bucket ids, heavy
- * keys, buckets sorted in shared memory, one-key buckets, heavy buckets,
- * overflow buckets, overflow rows, largest bucket, buckets sorted by radix
- * passes in shared memory (their sub-buckets were too uneven for the
- * counting placement) and their rows, and wide buckets and their rows (too
- * uneven, with a key range wider than 2^40: they join the overflow rows in
- * the plain radix sort, cheaper than six or more passes in shared memory).
+ * key, and the plain radix sort for the rows of larger buckets.  Every step
+ * is stable, so the output is identical to sbh_kpa_sort's for any ptrs (ties
+ * keep their input order); input and output must not alias.  Like every call
+ * here it only queues work on `stream`: the bucket count, the heavy keys in
+ * use and the number of rows left to the plain radix sort are settled on the
+ * device.  (When every bucket id fits in 16 bits, the ids travel with the
+ * rows; if the model's heavy keys would push ids past that, only the
+ * smallest of them keep a bucket of their own.)
+ * d_stats (nullable, device, SBH_LEARNED_STATS uint64 values, written by
+ * the call's last kernel): bucket ids, heavy keys used, buckets sorted in
+ * shared memory, one-key buckets, heavy buckets, overflow buckets, overflow
+ * rows, largest bucket, buckets sorted by radix passes in shared memory
+ * (their sub-buckets were too uneven for the counting placement) and their
+ * rows, and wide buckets and their rows (too uneven, with a key range wider
+ * than 2^40: they join the overflow rows in the plain radix sort, cheaper
+ * than six or more passes in shared memory).
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
-                         uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats, void* d_scratch,
+                         uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* d_stats, void* d_scratch,
                          size_t* scratch_bytes, void* stream);
 
 #ifdef __cplusplus

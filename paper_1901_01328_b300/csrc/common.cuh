@@ -202,6 +202,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Waits for the bulk copies completing the given phase of a barrier in this
+// CTA's shared memory.  A copy from this GPU's memory always lands, so unlike
+// the waits on other CTAs this one never gives up because another wait of the
+// library did: only its own poll budget bounds it.  Returns false (and records
+// a timeout) when that budget ran out; the copy may then still be in flight,
+// and the CTA must drain it (mbar_drain) before it leaves.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit, uint32_t* status) {
+    uint32_t polls = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if (++polls > limit) {
+            record_timeout(status);
+            return false;
+        }
+        if (polls > 8) __nanosleep(32);
+    }
+    return true;
+}
+
+// Lets a bulk copy that an expired wait left behind land before the CTA
+// leaves, so that it cannot write into shared memory that the SM has given to
+// the next CTA.  Bounded by its own budget (about a second), independent of
+// the test hook that shortens the other waits.
+constexpr uint32_t kDrainPolls = 1u << 24;
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    for (uint32_t polls = 0; !mbar_try_wait(bar, parity) && polls < kDrainPolls; ++polls)
+        if (polls > 8) __nanosleep(64);
+}
+
 // Shared-memory atomic add done only where pred holds, without a branch
 // (returns the old value there, 0 elsewhere).
 __device__ __forceinline__ uint32_t smem_atomic_add_if(bool pred, uint32_t* addr, uint32_t v) {

@@ -45,6 +45,7 @@ constexpr int kNP = 4 * kH + kH * kH + 1;  // 1153
 constexpr int oW1 = 0, oB1 = kH, oW2 = 2 * kH, oB2 = 2 * kH + kH * kH, oW3 = 3 * kH + kH * kH, oB3 = 4 * kH + kH * kH;
 constexpr uint32_t kNCell = 1 + 64 * 1024;
 constexpr uint32_t kMaxHeavy = SBH_LEARNED_MAX_HEAVY;
+constexpr uint32_t kMaxBucketIds = 1u << 16;  // ids carried in 16 bits
 constexpr uint32_t kHeavyDiv = 2;
 
 struct Model {
@@ -762,12 +763,35 @@ struct BucketValue16 {
     }
 };
 
+// The partition's spread-bucket count nb and the number of heavy keys that
+// keep a bucket of their own, decided on the device from the model, so that
+// the call needs no host synchronisation.  nb_n is about two buckets per
+// capacity of rows.  With carry (ids travel in 16 bits), every id must stay
+// below 2^16: up to a quarter fewer spread buckets are accepted for it, and
+// if the heavy keys still do not fit, only the smallest of them keep their
+// own bucket (the others are spread like any other key).  plan[0] = heavy
+// keys used, plan[1] = nb.
+__global__ void learned_plan_kernel(const Model* __restrict__ model, uint32_t nb_n, int carry,
+                                    uint32_t* __restrict__ plan) {
+    if (threadIdx.x != 0) return;
+    uint32_t h = min(model->heavy_count, kMaxHeavy);
+    uint32_t nb = nb_n;
+    if (carry) {
+        const uint32_t lo = nb_n - nb_n / 4;  // fewest spread buckets accepted (the host checked lo <= 65533)
+        h = min(h, (kMaxBucketIds - 2u - lo) / 2u);
+        nb = min(min(nb_n, kMaxBucketIds - 2u - 2u * h), kMaxBucketIds - 3u);
+    }
+    plan[0] = h;
+    plan[1] = nb;
+}
+
 // Heavy keys per cell: their number and the index of the first (cell_hc
-// zeroed, cell_hidx filled with 0xFF bytes beforehand).
-__global__ void heavy_cells_kernel(const Model* __restrict__ model, uint32_t* __restrict__ cell_hc,
-                                   uint32_t* __restrict__ cell_hidx) {
+// zeroed, cell_hidx filled with 0xFF bytes beforehand), for the first
+// *h_used heavy keys of the model.
+__global__ void heavy_cells_kernel(const Model* __restrict__ model, const uint32_t* __restrict__ h_used,
+                                   uint32_t* __restrict__ cell_hc, uint32_t* __restrict__ cell_hidx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= min(model->heavy_count, kMaxHeavy)) return;
+    if (i >= *h_used) return;
     uint32_t f;
     const uint32_t c = key_cell(model->heavy_keys[i], &f);
     atomicAdd(&cell_hc[c], 1u);
@@ -832,7 +856,8 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
                                                                  const uint32_t* __restrict__ cell_hidx,
                                                                  uint4* __restrict__ hcells,
                                                                  const float* __restrict__ bmax,
-                                                                 const uint32_t* __restrict__ bheavy, uint32_t nb,
+                                                                 const uint32_t* __restrict__ bheavy,
+                                                                 const uint32_t* __restrict__ nb_p,
                                                                  uint2* __restrict__ cells,
                                                                  uint32_t* __restrict__ cells16,
                                                                  uint32_t* __restrict__ heavy_bucket_bits,
@@ -885,7 +910,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
     }
     const float run_max = fmaxf(bm, m);  // max of F[0..c]
     const uint32_t heavy_incl = bh + h;  // heavy keys in the cells [0, c]
-    const float fnb = static_cast<float>(nb);
+    const float fnb = static_cast<float>(*nb_p);
     const uint32_t t = static_cast<uint32_t>(floorf(run_max * fnb)) + 2u * (heavy_incl - hv);
     // the next cell's first id (the same arithmetic as its own thread's)
     float f_next = __shfl_down_sync(0xffffffffu, f, 1);
@@ -1387,8 +1412,10 @@ __global__ void __launch_bounds__(1024) overflow_list_kernel(const uint32_t* __r
 // bucket whose offset is <= r.
 __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs,
                                      const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ list,
-                                     const uint32_t* __restrict__ offs, uint32_t nl, uint32_t rows,
-                                     uint64_t* __restrict__ ck, uint32_t* __restrict__ cp, int to_gather) {
+                                     const uint32_t* __restrict__ offs, const uint32_t* __restrict__ nl_p,
+                                     const uint32_t* __restrict__ rows_p, uint64_t* __restrict__ ck,
+                                     uint32_t* __restrict__ cp, int to_gather) {
+    const uint32_t nl = *nl_p, rows = *rows_p;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
         uint32_t lo = 0, hi = nl;  // last j with offs[j] <= r
@@ -1408,12 +1435,29 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
     }
 }
 
+// The call's statistics, in the order of the header's list.
+__global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const uint32_t* __restrict__ plan,
+                                     const BucketStats* __restrict__ st, uint64_t* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    out[0] = *nbid;
+    out[1] = plan[0];
+    out[2] = st->sorted_buckets;
+    out[3] = st->single_key_buckets;
+    out[4] = st->heavy_buckets;
+    out[5] = st->overflow_buckets;
+    out[6] = st->overflow_rows;
+    out[7] = st->max_bucket;
+    out[8] = st->radix_buckets;
+    out[9] = st->radix_rows;
+    out[10] = st->wide_buckets;
+    out[11] = st->wide_rows;
+}
+
 // ------------------------------------------------------------------ carried bucket ids
 // When every bucket id fits in 16 bits, each row's id is computed once, kept
 // in a 16-bit array, and moved with the row through both digit passes; the
 // counts and the bucket bounds then read ids instead of recomputing them.
 constexpr int kCarryTile = 3584;
-constexpr uint32_t kMaxBucketIds = 1u << 16;  // carried ids are 16 bits
 
 // Bucket id of every row (kept as 16 bits), the histogram of its low digit
 // per chunk of the first digit pass (CTA c takes the rows of chunk c: that
@@ -1708,7 +1752,7 @@ struct SortLearnedScratch {
     uint32_t* list;
     uint2* bagg;            // per block of buckets: overflow buckets, rows
     uint32_t* offs;
-    uint32_t* small;        // nbid, counter, nlist, rows_total
+    uint32_t* small;        // nbid, counter, nlist, rows_total, heavy keys used, spread buckets
     BucketStats* stats;
     uint64_t* ck;           // compact overflow rows (n)
     uint32_t* cp;
@@ -1887,7 +1931,7 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
 }  // extern "C"
 
 extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
-                                    uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* h_stats,
+                                    uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* d_stats,
                                     void* d_scratch, size_t* scratch_bytes, void* stream) {
     using namespace sbh;
     clear_error();
@@ -1895,44 +1939,40 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     bool done = false;
     int rc = scratch_check(d_scratch, scratch_bytes, learned_carve(nullptr, n).total, &done);
     if (rc || done) return rc;
-    if (h_stats)
-        for (int i = 0; i < SBH_LEARNED_STATS; ++i) h_stats[i] = 0;
-    if (n == 0) return SBH_OK;
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) {
+        if (d_stats) SBH_CUDA(cudaMemsetAsync(d_stats, 0, SBH_LEARNED_STATS * sizeof(uint64_t), s));
+        return SBH_OK;
+    }
     if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out || !d_model) { set_error("null pointer"); return SBH_EINVAL; }
     if (d_keys_in == d_keys_out) { set_error("the learned sort needs distinct input and output buffers"); return SBH_EINVAL; }
-    cudaStream_t s = as_stream(stream);
     SortLearnedScratch t = learned_carve(d_scratch, n);
     const Model* model = static_cast<const Model*>(d_model);
     SBH_CUDA(cudaMemsetAsync(t.heavy_bucket_bits, 0, t.zero_bytes, s));
     // bucket count: about two buckets per capacity; when every id can stay
-    // below 2^16 for at most a quarter fewer buckets, keep them there so the
-    // ids are carried in 16 bits through two digit passes
-    uint32_t heavy = 0;
-    SBH_CUDA(cudaMemcpyAsync(&heavy, &model->heavy_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SBH_CUDA(cudaStreamSynchronize(s));
-    uint64_t nb64 = learned_nb(n);
-    // (a cell's spread count stays below the 16-bit markers 0xFFFE, 0xFFFF)
-    if (heavy < 16384) {
-        const uint64_t fit16 = std::min<uint64_t>(65536ull - 2ull * heavy - 2ull, 65533ull);
-        if (nb64 > fit16 && fit16 >= nb64 - nb64 / 4) nb64 = fit16;
-    }
-    const uint32_t nb = (uint32_t)nb64;
-    const bool carry = nb64 + 2ull * heavy + 2ull <= 65536ull && nb64 <= 65533ull;
+    // below 2^16 with at most a quarter fewer spread buckets, the ids are
+    // carried in 16 bits through two digit passes (the count and the heavy
+    // keys used are settled on the device)
+    const uint64_t nb_n = learned_nb(n);
+    const bool carry = nb_n - nb_n / 4 <= kMaxBucketIds - 3ull;
     uint32_t* nbid = t.small + 0;
     uint32_t* counter = t.small + 1;
     uint32_t* nlist = t.small + 2;
     uint32_t* rows_total = t.small + 3;
+    uint32_t* lplan = t.small + 4;  // heavy keys used, spread buckets
+    SBH_TIMED("learned_plan", s, learned_plan_kernel<<<1, 32, 0, s>>>(model, (uint32_t)nb_n, carry ? 1 : 0, lplan));
+    SBH_LAUNCHED();
     SBH_CUDA(cudaMemsetAsync(t.cell_hc, 0, (kNCell + 1) * sizeof(uint32_t), s));
     SBH_CUDA(cudaMemsetAsync(t.cell_hidx, 0xFF, (kNCell + 1) * sizeof(uint32_t), s));
     SBH_TIMED("learned_heavy_cells", s,
-              heavy_cells_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(model, t.cell_hc, t.cell_hidx));
+              heavy_cells_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(model, lplan, t.cell_hc, t.cell_hidx));
     SBH_LAUNCHED();
     SBH_TIMED("learned_cdf", s,
               cell_cdf_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.cell_hc, t.bmax, t.bheavy));
     SBH_LAUNCHED();
     SBH_TIMED("learned_table", s,
               cell_table_kernel<<<kTblBlocks, kTblThreads, 0, s>>>(model, t.F, t.cell_hc, t.cell_hidx, t.hcells,
-                                                                   t.bmax, t.bheavy, nb, t.cells, t.cells16,
+                                                                   t.bmax, t.bheavy, lplan + 1, t.cells, t.cells16,
                                                                    t.heavy_bucket_bits, nbid));
     SBH_LAUNCHED();
     const BucketValue fn{t.cells, t.hcells, model->heavy_keys};
@@ -1964,42 +2004,24 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
               overflow_list_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nlist,
                                                            rows_total));
     SBH_LAUNCHED();
-    // the overflow is data-dependent: read its size (one stream synchronisation)
-    uint32_t small_h[4];
-    BucketStats st_h;
-    uint32_t heavy_h = 0;
-    SBH_CUDA(cudaMemcpyAsync(small_h, t.small, sizeof(small_h), cudaMemcpyDeviceToHost, s));
-    SBH_CUDA(cudaMemcpyAsync(&st_h, t.stats, sizeof(st_h), cudaMemcpyDeviceToHost, s));
-    SBH_CUDA(cudaMemcpyAsync(&heavy_h, &model->heavy_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SBH_CUDA(cudaStreamSynchronize(s));
-    const uint32_t nl = small_h[2], rows = small_h[3];
-    if (nl > 0) {
-        const unsigned mg = (unsigned)min_u64((rows + 255) / 256, (uint64_t)num_sms() * 8);
-        SBH_TIMED("learned_overflow_move", s,
-                  overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,
-                                                          t.ck, t.cp, 1));
+    // the overflow rows (their number is known only on the device): gathered
+    // into a compact buffer, sorted by the plain radix sort sized on the
+    // device, and put back
+    const unsigned mg = (unsigned)min_u64((n + 255) / 256, (uint64_t)num_sms() * 8);
+    SBH_TIMED("learned_overflow_move", s,
+              overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nlist,
+                                                      rows_total, t.ck, t.cp, 1));
+    SBH_LAUNCHED();
+    rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, n, t.sort_scratch, s, RadixValue{}, kPositions, "learned_overflow",
+                       rows_total);
+    if (rc) return rc;
+    SBH_TIMED("learned_overflow_move", s,
+              overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nlist,
+                                                      rows_total, t.ck, t.cp, 0));
+    SBH_LAUNCHED();
+    if (d_stats) {
+        SBH_TIMED("learned_stats", s, learned_stats_kernel<<<1, 32, 0, s>>>(nbid, lplan, t.stats, d_stats));
         SBH_LAUNCHED();
-        rc = sort_by_value(t.ck, t.cp, t.ck, t.cp, rows, t.sort_scratch, s, RadixValue{}, kPositions,
-                           "learned_overflow");
-        if (rc) return rc;
-        SBH_TIMED("learned_overflow_move", s,
-                  overflow_move_kernel<<<mg, 256, 0, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.list, t.offs, nl, rows,
-                                                          t.ck, t.cp, 0));
-        SBH_LAUNCHED();
-    }
-    if (h_stats) {
-        h_stats[0] = small_h[0];
-        h_stats[1] = heavy_h;
-        h_stats[2] = st_h.sorted_buckets;
-        h_stats[3] = st_h.single_key_buckets;
-        h_stats[4] = st_h.heavy_buckets;
-        h_stats[5] = st_h.overflow_buckets;
-        h_stats[6] = st_h.overflow_rows;
-        h_stats[7] = st_h.max_bucket;
-        h_stats[8] = st_h.radix_buckets;
-        h_stats[9] = st_h.radix_rows;
-        h_stats[10] = st_h.wide_buckets;
-        h_stats[11] = st_h.wide_rows;
     }
     return SBH_OK;
 }

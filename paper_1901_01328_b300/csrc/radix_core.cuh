@@ -77,6 +77,25 @@ struct Buffers {
     __device__ __forceinline__ uint32_t* wptrs(int sel) const { return sel == 1 ? tmp_p : out_p; }
 };
 
+// A sort whose size is known only on the device (the learned sort's overflow
+// rows): the chunked kernels read n from d_n and derive the chunk geometry
+// from it, the same way the host does for a known size, with G the number of
+// chunks launched for the largest size the caller allows.  d_n == nullptr:
+// the size and geometry are the launch arguments.
+struct DynN {
+    const uint32_t* d_n = nullptr;
+    uint32_t G = 0;
+    uint32_t tile = 0;
+    __device__ __forceinline__ void apply(uint32_t& n, uint32_t& chunk, uint32_t& nchunks) const {
+        if (!d_n) return;
+        n = *d_n;
+        const uint32_t ttiles = (n + tile - 1) / tile;
+        const uint32_t want = min(ttiles, G);
+        chunk = want ? ((ttiles + want - 1) / want) * tile : tile;
+        nchunks = (n + chunk - 1) / chunk;
+    }
+};
+
 // ------------------------------------------------------------------ upsweep
 // Equal digits in a row are counted in registers first: skewed keys (a heavy
 // key, constant high bytes) would otherwise serialise on one bin.
@@ -148,8 +167,11 @@ __global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict
 template <typename ValueFn>
 __global__ void __launch_bounds__(1024)
 first_count_kernel(const uint64_t* __restrict__ keys, uint32_t n, uint32_t chunk, ValueFn value_of,
-                   uint32_t* __restrict__ chunk_hist, unsigned long long* __restrict__ vbits) {
+                   uint32_t* __restrict__ chunk_hist, unsigned long long* __restrict__ vbits, DynN dn = DynN{}) {
     __shared__ uint32_t h[kRadix];
+    uint32_t nchunks = gridDim.x;
+    dn.apply(n, chunk, nchunks);
+    if (blockIdx.x >= nchunks) return;
     __shared__ unsigned long long wor[32], wnot[32];
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -350,10 +372,10 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         for (int i = tid; i < kWarps * (kRadix + 1); i += kThreads) (&sm.whist[0][0])[i] = 0;
 
         // ---- wait for the tile (bulk copy) or load it (ragged or unaligned)
+        bool expired = false;
+        const uint32_t par = phase[b];
         if (bulk_ok && tile < nfull) {
-            uint32_t polls = 0;
-            while (!mbar_try_wait(&sm.mbar[b], phase[b]))
-                if (wait_expired(polls, spin_limit, status)) break;
+            expired = !mbar_wait_bounded(&sm.mbar[b], par, spin_limit, status);
             phase[b] ^= 1u;
         } else {
             for (uint32_t s = tid; s < valid; s += kThreads) {
@@ -361,7 +383,14 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
                 sm.ptrs[b][s] = ld_stream(in_p + base + s);
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(expired)) {
+            // the tile's copy did not arrive within the budget: issue nothing
+            // more, let both buffers' copies land, and leave (the tiles after
+            // this one find no record and their bounded waits give up)
+            mbar_drain(&sm.mbar[b], par);
+            if (bulk_ok && sm.tile_of[b ^ 1] < nfull) mbar_drain(&sm.mbar[b ^ 1], phase[b ^ 1]);
+            break;
+        }
 
         // ---- registers (warp-striped: warp w owns 32*kIpt consecutive rows)
         uint64_t k[kIpt];
@@ -486,9 +515,11 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
 }
 
 // ------------------------------------------------------------------ copy
-__global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ plan) {
+__global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ plan,
+                            const uint32_t* __restrict__ d_n = nullptr) {
     const int sel = plan->copy_src;
     if (sel < 0) return;
+    if (d_n) n = *d_n;
     const uint64_t* __restrict__ sk = buf.keys(sel);
     const uint32_t* __restrict__ sp = buf.ptrs(sel);
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -522,8 +553,11 @@ inline bool use_chunked(uint64_t n) { return n >= knob(SBH_KNOB_SORT_CHUNKED_MIN
 template <typename ValueFn>
 __global__ void __launch_bounds__(1024)
 chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
-                   uint32_t* __restrict__ chunk_hist, ValueFn value_of) {
+                   uint32_t* __restrict__ chunk_hist, ValueFn value_of, DynN dn = DynN{}) {
     if (!plan->active[pos]) return;
+    uint32_t nchunks = gridDim.x;
+    dn.apply(n, chunk, nchunks);
+    if (blockIdx.x >= nchunks) return;
     __shared__ uint32_t h[kRadix];
     const DigitOf<ValueFn> digit_of{value_of, pos * kRadixBits};
     const uint64_t* __restrict__ in_k = buf.keys(plan->src[pos]);
@@ -569,8 +603,12 @@ chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ pl
 // scanned).
 __global__ void __launch_bounds__(1024)
 chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __restrict__ chunk_hist, uint32_t nchunks,
-                  const uint32_t* __restrict__ gbase, uint32_t* __restrict__ chunk_base) {
+                  const uint32_t* __restrict__ gbase, uint32_t* __restrict__ chunk_base, DynN dn = DynN{}) {
     if (!plan->active[pos]) return;
+    {
+        uint32_t n = 0, chunk = 0;
+        dn.apply(n, chunk, nchunks);
+    }
     __shared__ uint32_t gsum[4][kRadix];
     __shared__ uint32_t base[kRadix];
     __shared__ uint32_t wsum[kRadix / 32];
@@ -662,7 +700,7 @@ __global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value)
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
                      uint32_t* __restrict__ status, uint32_t* __restrict__ first_row = nullptr,
-                     const uint32_t* __restrict__ low_base = nullptr) {
+                     const uint32_t* __restrict__ low_base = nullptr, DynN dn = DynN{}) {
     constexpr bool kDig = ScatterDig<ValueFn, kCarry>::value;
     using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig>;
     constexpr int kW = Smem::kW, kG = Smem::kG, kWpg = kW / kG;
@@ -695,6 +733,10 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const uint16_t* __restrict__ in_ids = full_ids ? buf.in_ids : nullptr;
     const uint8_t* __restrict__ in_v = walk ? buf.vals(src) : nullptr;
     uint8_t* __restrict__ out_v = (kCarry && !rows_pass) ? buf.wvals(dst) : nullptr;
+    {
+        uint32_t nchunks = gridDim.x;
+        dn.apply(n, chunk, nchunks);
+    }
     const uint32_t lo = blockIdx.x * chunk;
     const uint32_t hi = min(n, lo + chunk);
     if (lo >= hi) return;
@@ -717,6 +759,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     };
     for (int x = tid; x < kW * (kRadix / 2 + 1); x += THREADS) (&sm.whist2[0][0])[x] = 0;
     for (int x = tid; x < kRadix; x += THREADS) sm.run[x] = chunk_base[blockIdx.x * kRadix + x];
+    // buffers with a bulk copy in flight (bit b), the same in every thread
+    uint32_t inflight = (bulk_tile(0) ? 1u : 0u) | ((ntl > 1 && bulk_tile(1)) ? 2u : 0u);
     if (tid == 0) {
         mbar_init(&sm.mbar[0], 1);
         mbar_init(&sm.mbar[1], 1);
@@ -772,13 +816,9 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             }
         }
         bool expired = false;
+        const uint32_t par = phase[b];
         if (bulk_tile(i)) {
-            uint32_t polls = 0;
-            while (!mbar_try_wait(&sm.mbar[b], phase[b]))
-                if (wait_expired(polls, spin_limit, status)) {
-                    expired = true;
-                    break;
-                }
+            expired = !mbar_wait_bounded(&sm.mbar[b], par, spin_limit, status);
             phase[b] ^= 1u;
         } else {
             for (uint32_t s = tid; s < valid; s += THREADS) {
@@ -788,9 +828,18 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                 if (walk) reinterpret_cast<uint8_t*>(sm.vals[b])[s] = in_v[base + s];
             }
         }
-        // B0.  A tile whose data never arrived is not scattered (its rows
-        // stay unwritten).  Tile i - 1 is done with the other buffer.
-        const bool tile_ok = !__syncthreads_or(expired);
+        // B0.  A tile whose data did not arrive within the budget ends the
+        // chunk: no copy is issued any more, the copies in flight are let
+        // land, and the rows not scattered stay unwritten (the call's output
+        // is invalid and the timeout is recorded).  Otherwise tile i - 1 is
+        // done with the other buffer, which takes tile i + 1.
+        if (__syncthreads_or(expired)) {
+            mbar_drain(&sm.mbar[b], par);
+            if (inflight & (2u >> b)) mbar_drain(&sm.mbar[b ^ 1], phase[b ^ 1]);
+            return;
+        }
+        inflight &= ~(1u << b);
+        if (i >= 1 && i + 1 < ntl && bulk_tile(i + 1)) inflight |= 2u >> b;
         if (tid == 0 && i >= 1) {
             fence_proxy_async_smem();
             issue(b ^ 1, i + 1);
@@ -943,7 +992,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             }
             __syncthreads();  // B4
 
-            if (tile_ok) {
+            {
 #pragma unroll
                 for (int j = 0; j < kIt; ++j) {
                     const uint32_t s = tid + j * THREADS;
@@ -981,6 +1030,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
 // resident CTA (at most kMaxChunks).
 struct ChunkGeom {
     uint32_t chunk = 0, nchunks = 0;
+    uint32_t want = 0;  // chunks for the largest n of this geometry (the launch grid of a device-sized sort)
     size_t smem = 0;
 };
 
@@ -996,6 +1046,7 @@ int chunk_geometry(uint64_t n, ChunkGeom* g) {
     const uint64_t want = min_u64(min_u64(ttiles, (uint64_t)num_sms() * per_sm), kMaxChunks);
     g->chunk = (uint32_t)(((ttiles + want - 1) / want) * TILE);
     g->nchunks = (uint32_t)((n + g->chunk - 1) / g->chunk);
+    g->want = (uint32_t)want;
     g->smem = smem;
     return SBH_OK;
 }
@@ -1045,33 +1096,40 @@ inline SortScratch sort_carve(void* scratch, uint64_t n) {
 template <typename ValueFn, int TILE, int THREADS>
 int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, const ChunkGeom& g, ValueFn value_of,
                    int bulk_ok, cudaStream_t s, const std::string& n_count, const std::string& n_scan,
-                   const std::string& n_scat) {
+                   const std::string& n_scat, DynN dn = DynN{}) {
     const uint32_t limit = spin_limit();
     uint32_t* status = status_word();
+    const uint32_t grid = dn.d_n ? g.want : g.nchunks;
     for (int pos = 0; pos < kPositions; ++pos) {
         if (pos > 0) {  // the first pass's chunk counts come from first_count_kernel (the same chunks, g)
             SBH_TIMED(n_count.c_str(), s,
-                      chunk_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk,
-                                                                            sc.chunk_hist, value_of));
+                      chunk_count_kernel<ValueFn><<<grid, 1024, 0, s>>>(b, n32, pos, sc.plan, g.chunk,
+                                                                       sc.chunk_hist, value_of, dn));
             SBH_LAUNCHED();
         }
         SBH_TIMED(n_scan.c_str(), s,
                   chunk_scan_kernel<<<1, 1024, 0, s>>>(sc.plan, pos, sc.chunk_hist, g.nchunks, nullptr,
-                                                       sc.chunk_base));
+                                                       sc.chunk_base, dn));
         SBH_LAUNCHED();
         SBH_TIMED(n_scat.c_str(), s,
-                  (chunk_scatter_kernel<ValueFn, TILE, THREADS, false><<<g.nchunks, THREADS, g.smem, s>>>(
-                      b, n32, pos, sc.plan, g.chunk, sc.chunk_base, value_of, bulk_ok, limit, status)));
+                  (chunk_scatter_kernel<ValueFn, TILE, THREADS, false><<<grid, THREADS, g.smem, s>>>(
+                      b, n32, pos, sc.plan, g.chunk, sc.chunk_base, value_of, bulk_ok, limit, status, nullptr,
+                      nullptr, dn)));
         SBH_LAUNCHED();
     }
     return SBH_OK;
 }
 
 // Stable sort of (in_k, in_p) by value_of(key) into (out_k, out_p); the
-// positions at or above npos of the value are treated as zero.
+// positions at or above npos of the value are treated as zero.  With d_n
+// (device) the sort has *d_n <= n pairs, known only when it runs: it takes
+// the chunked passes, launched for n pairs, with every kernel reading the
+// size and deriving its chunk geometry on the device (no host
+// synchronisation).
 template <typename ValueFn>
 int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
-                  void* scratch, cudaStream_t s, ValueFn value_of, int npos, const char* tag = "sort") {
+                  void* scratch, cudaStream_t s, ValueFn value_of, int npos, const char* tag = "sort",
+                  const uint32_t* d_n = nullptr) {
     // profile names: <tag>_upsweep, <tag>_scatter, ...
     const std::string t(tag);
     const std::string n_up = t + "_upsweep", n_plan = t + "_plan", n_count = t + "_count", n_scan = t + "_chunk_scan",
@@ -1086,17 +1144,19 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
-    const bool chunked = use_chunked(n);
+    const bool chunked = d_n || use_chunked(n);
     ChunkGeom g;
+    DynN dn{};
     if (chunked) {
         // the chunked passes find their digit bases in the chunk counts; the
         // plan needs only which digits vary: the first pass's counts and the
         // values' OR and AND in one read
         const int rc = chunk_geometry<ValueFn, 4096, 512, false>(n32, &g);
         if (rc) return rc;
+        if (d_n) dn = DynN{d_n, g.want, 4096};
         SBH_TIMED(n_up.c_str(), s,
-                  first_count_kernel<ValueFn><<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, value_of, sc.chunk_hist,
-                                                                         sc.vbits));
+                  first_count_kernel<ValueFn><<<d_n ? g.want : g.nchunks, 1024, 0, s>>>(
+                      in_k, n32, g.chunk, value_of, sc.chunk_hist, sc.vbits, dn));
         SBH_LAUNCHED();
         SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place));
         SBH_LAUNCHED();
@@ -1117,7 +1177,8 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     if (chunked) {
-        const int rc = chunked_passes<ValueFn, 4096, 512>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat);
+        const int rc =
+            chunked_passes<ValueFn, 4096, 512>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat, dn);
         if (rc) return rc;
     } else {
         auto kern = onesweep_kernel<ValueFn>;
@@ -1136,7 +1197,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
         }
     }
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
-    SBH_TIMED(n_copy.c_str(), s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan));
+    SBH_TIMED(n_copy.c_str(), s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, sc.plan, d_n));
     SBH_LAUNCHED();
     return SBH_OK;
 }

@@ -441,18 +441,23 @@ def sbh_learned_train(samples, n_rows, init_params, steps, batch, lr, model, los
     return _scratch(_lib.sbh_learned_train, args, (_stream(stream),), "sbh_learned_train", samples.device)
 
 
-def sbh_kpa_sort_learned(keys_in, ptrs_in, keys_out, ptrs_out, model, scratch=None, stream=None):
-    """Returns the stats as a dict (the call synchronises the stream once)."""
-    st = (ctypes.c_uint64 * len(LEARNED_STATS))()
-    args = (_p(keys_in), _p(ptrs_in), _p(keys_out), _p(ptrs_out), keys_in.numel(), _p(model),
-            ctypes.cast(st, ctypes.c_void_p))
+def sbh_kpa_sort_learned(keys_in, ptrs_in, keys_out, ptrs_out, model, stats=None, scratch=None, stream=None):
+    """Queues the learned sort; stats (nullable) is a device uint64 tensor of
+    len(LEARNED_STATS) entries that the call fills on the device (read it
+    with stats_dict after synchronising).  Returns the scratch used."""
+    args = (_p(keys_in), _p(ptrs_in), _p(keys_out), _p(ptrs_out), keys_in.numel(), _p(model), _p(stats))
     if scratch is None:
-        _scratch(_lib.sbh_kpa_sort_learned, args, (_stream(stream),), "sbh_kpa_sort_learned", keys_in.device)
-    else:
-        nbytes = ctypes.c_size_t(scratch.numel())
-        _check(_lib.sbh_kpa_sort_learned(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)),
-               "sbh_kpa_sort_learned")
-    return dict(zip(LEARNED_STATS, list(st)))
+        return _scratch(_lib.sbh_kpa_sort_learned, args, (_stream(stream),), "sbh_kpa_sort_learned",
+                        keys_in.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_kpa_sort_learned(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)),
+           "sbh_kpa_sort_learned")
+    return scratch
+
+
+def stats_dict(stats):
+    """The learned sort's statistics tensor as a dict (synchronises)."""
+    return dict(zip(LEARNED_STATS, [int(x) for x in stats.cpu().tolist()]))
 
 
 def sort_learned_scratch_bytes(n: int) -> int:
@@ -477,9 +482,11 @@ def model_params(model):
 
 
 def sort_learned(keys, ptrs, model):
+    """Sorted copy and the statistics as a dict (synchronises to read them)."""
     out = (torch.empty_like(keys), torch.empty_like(ptrs))
-    stats = sbh_kpa_sort_learned(keys, ptrs, out[0], out[1], model)
-    return out[0], out[1], stats
+    stats = torch.zeros(len(LEARNED_STATS), dtype=torch.uint64, device=keys.device)
+    sbh_kpa_sort_learned(keys, ptrs, out[0], out[1], model, stats)
+    return out[0], out[1], stats_dict(stats)
 
 
 # ----------------------------------------------------------------- Table 2 record primitives and per-key statistics

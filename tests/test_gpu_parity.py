@@ -155,6 +155,28 @@ def test_sort_timeout_hook_reports_and_recovers(S):
     assert same(sk, ok) and same(sp, op)
 
 
+def test_sort_chunked_path_tiny_wait_budget_reports_and_recovers(S):
+    # the chunked passes wait only on their own bulk copies; with a poll
+    # budget of one, a copy that has not landed at the first poll ends its
+    # chunk: the CTA lets its copies in flight land and leaves, the timeout
+    # is recorded, and the next sort with the normal budget is correct
+    n = (1 << 23) + 4097
+    col = _sort_case("mixed", n, seed=4)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    S.sync_status()
+    S.set_spin_limit(1)
+    try:
+        S.sort(keys, ptrs)
+        st = S.sync_status()
+    finally:
+        S.set_spin_limit(0)
+    assert st in (S.SBH_OK, S.SBH_ETIMEOUT)
+    sk, sp = S.sort(keys, ptrs)
+    assert S.sync_status() == S.SBH_OK
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+
+
 def test_sort_scratch_too_small(S):
     keys, ptrs = S.extract(cuda(_sort_case("full64", 1000)), 0, 1000)
     small = torch.empty(64, dtype=torch.uint8, device="cuda")
