@@ -293,6 +293,22 @@ int sbh_kpa_select(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, c
                    uint64_t lo, uint64_t hi, uint64_t* d_out_keys, uint32_t* d_out_ptrs, uint64_t cap,
                    uint64_t* d_count, void* d_scratch, size_t* scratch_bytes, void* stream);
 
+/* Partition (Table 2: split a KPA into sub-KPAs by ranges of its resident
+ * keys; Sec. 4.2 "Windowing" applies it to the timestamp column).  d_bounds
+ * (device, nb non-decreasing keys, nb < 2^32 - 1) cut the key space into
+ * nb + 1 ranges: part j holds the pairs with d_bounds[j - 1] <= key <
+ * d_bounds[j] (no lower limit for part 0, no upper limit for part nb).  The
+ * input KPA (n < 2^32 pairs, any order) is written to (d_keys_out,
+ * d_ptrs_out) part after part, each part in the input order, and
+ * d_offsets[j] (device, nb + 2 uint64) receives the first row of part j,
+ * d_offsets[nb + 1] = n.  The output may alias the input (both arrays).
+ * It is a stable sort by part number: one 8-bit radix pass for up to 256
+ * parts, two for up to 65536, and so on.
+ * Scratch: that of sbh_kpa_sort for n pairs. */
+int sbh_kpa_partition(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const uint64_t* d_bounds,
+                      uint64_t nb, uint64_t* d_keys_out, uint32_t* d_ptrs_out, uint64_t* d_offsets, void* d_scratch,
+                      size_t* scratch_bytes, void* stream);
+
 /* ---------------------------------------------------------------- A8
  * Join (Table 2: join two sorted KPAs by resident key; Sec. 4.2 "Temporal
  * Join" joins the KPAs of one window of each stream).  Emits every pair

@@ -20,6 +20,9 @@ Parity status of each function (what pins it, besides itself):
                              every kept value >= every dropped one
   join                    -- nested loop; cardinality = sum_k cL(k) cR(k)
   window_ranges           -- binary search on a non-decreasing column
+  partition               -- brute force on tiny inputs (a Python loop);
+                             each part's keys in its range, parts in input
+                             order, part sizes = rows per range
   mlp (forward/backward)  -- central finite differences; closed-form special
                              cases; one Adam step in closed form
 The paper prints no worked example, so nothing is pinned to printed values.
@@ -76,6 +79,8 @@ def _load():
         lib.oracle_select.restype = u64
         lib.oracle_median_unique.argtypes = [vp, vp, u64, vp, i32, vp, vp, vp]
         lib.oracle_median_unique.restype = u64
+        lib.oracle_partition.argtypes = [vp, vp, u64, vp, u64, vp, vp, vp]
+        lib.oracle_partition.restype = None
         _lib = lib
     return _lib
 
@@ -213,3 +218,17 @@ def median_unique(keys: np.ndarray, ptrs: np.ndarray, col: np.ndarray):
     ok, om, ou = np.empty(n, np.uint64), np.empty(n, np.uint64), np.empty(n, np.uint64)
     m = _load().oracle_median_unique(_p(keys), _p(ptrs), n, _p(col), col.dtype.itemsize, _p(ok), _p(om), _p(ou))
     return ok[:m], om[:m], ou[:m]
+
+
+def partition(keys: np.ndarray, ptrs: np.ndarray, bounds: np.ndarray):
+    """Partition (Table 2) by key ranges: (keys, ptrs, offsets[nb + 2]); part j
+    = records with bounds[j - 1] <= key < bounds[j], in input order."""
+    keys = _c(keys, np.uint64)
+    ptrs = _c(ptrs, np.uint32)
+    bounds = _c(bounds, np.uint64)
+    n, nb = keys.size, bounds.size
+    ok = np.empty(n, np.uint64)
+    op = np.empty(n, np.uint32)
+    off = np.empty(nb + 2, np.uint64)
+    _load().oracle_partition(_p(keys), _p(ptrs), n, _p(bounds), nb, _p(ok), _p(op), _p(off))
+    return ok, op, off

@@ -208,4 +208,27 @@ uint64_t oracle_median_unique(const uint64_t* keys, const uint32_t* ptrs, uint64
     return j;
 }
 
+/* Partition (Table 2: split a KPA by ranges of its resident keys).  bounds
+ * holds nb non-decreasing keys; part j (0 <= j <= nb) receives the records
+ * with bounds[j - 1] <= key < bounds[j] (no lower limit for part 0, no upper
+ * one for part nb), each part in the input order.  Every record is appended
+ * to the vector of its part, found by counting the bounds not above its key;
+ * the parts are then laid end to end.  offsets[j] = the first row of part j,
+ * offsets[nb + 1] = n. */
+void oracle_partition(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const uint64_t* bounds, uint64_t nb,
+                      uint64_t* out_keys, uint32_t* out_ptrs, uint64_t* offsets) {
+    std::vector<std::vector<std::pair<uint64_t, uint32_t>>> parts(nb + 1);
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t j = 0;
+        while (j < nb && bounds[j] <= keys[i]) ++j;
+        parts[j].push_back({keys[i], ptrs[i]});
+    }
+    uint64_t m = 0;
+    for (uint64_t j = 0; j <= nb; ++j) {
+        offsets[j] = m;
+        for (const auto& kp : parts[j]) { out_keys[m] = kp.first; out_ptrs[m] = kp.second; ++m; }
+    }
+    offsets[nb + 1] = m;
+}
+
 }  // extern "C"

@@ -19,14 +19,15 @@ sliding_join  the temporal join of two streams over sliding windows built
 ad_campaign_counts  a chain of operators over a 7-column ad-event stream
     (Extract -> Select -> KeySwap through a lookup table -> Sort -> Keyed
     count per window), the kind of pipeline the paper's declarative API
-    builds (Sec. 4.3), with Materialize fused into the key swap.
+    builds (Sec. 4.3), composed from operators.py, with Materialize fused
+    into the key swap.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
 
-from . import sbh
+from . import operators, sbh
 
 
 def _u64(n, dev):
@@ -194,50 +195,21 @@ def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, p
     return JoinResults(out_l, out_r, counts, pair_cap), wl
 
 
-def ad_campaign_counts(cols, campaign_of_ad, window_ns, view=0):
+def ad_campaign_counts(cols, campaign_of_ad, window_ns, view=0, trace=None):
     """A chained pipeline over a 7-column ad-event stream (device columns;
     event_time non-decreasing): per tumbling window of event time, the
-    number of view events of every campaign.  Per window the chain is
+    number of view events of every campaign.  Built from the operator layer
+    (operators.py), whose Listing 2 rule inserts the steps: per window,
     Extract (a KPA keyed by event type) -> Select (event type == view) ->
-    KeySwap through the ad -> campaign table (Materialize of the ad column
-    fused with the Extract of the new key, Sec. 4.2) -> Sort -> Keyed count.
-    Returns [(window, campaigns, counts)] as host arrays."""
-    ts = cols["event_time"]
-    etype, ads = cols["event_type"], cols["ad_id"]
-    dev = ts.device
-    n = ts.numel()
-    if n == 0:
-        return []
-    last = int(ts[-1].item())
-    nwin = last // window_ns + 1
-    starts = (torch.arange(nwin, dtype=torch.int64, device=dev) * window_ns).view(torch.uint64)
-    rb, re_ = _u64(nwin, dev), _u64(nwin, dev)
-    sbh.sbh_window_ranges(ts, starts, window_ns, rb[:nwin], re_[:nwin])
-    rb, re_ = rb[:nwin].cpu().numpy(), re_[:nwin].cpu().numpy()
-    big = int((re_ - rb).max())
-    keys, ptrs, sk, sp = _u64(big, dev), _u32(big, dev), _u64(big, dev), _u32(big, dev)
-    camp = _u64(big, dev)
-    cnt = _u64(1, dev)
-    ok, oc, nk = _u64(big, dev), _u64(big, dev), _u64(1, dev)
-    sel_scr = sort_scr = red_scr = None
+    KeySwap to the campaign (the ad column gathered through the ad ->
+    campaign table: Materialize fused with the Extract of the new key,
+    Sec. 4.3) -> Sort -> Keyed count.  Returns [(window, campaigns,
+    counts)] as host arrays."""
+    b = operators.Bundle(cols)
+    campaign = operators.Lookup("campaign_id", "ad_id", campaign_of_ad)
     out = []
-    for w in range(nwin):
-        lo, m = int(rb[w]), int(re_[w] - rb[w])
-        if m == 0:
-            out.append((w, np.zeros(0, np.uint64), np.zeros(0, np.uint64)))
-            continue
-        sbh.sbh_kpa_extract(etype, lo, m, keys, ptrs)
-        sel_scr = sbh.sbh_kpa_select(keys[:m], ptrs[:m], etype, view, view + 1, sk, sp, m, cnt,
-                                     scratch=_fit(sel_scr, sbh.select_scratch_bytes(m), dev))
-        v = int(cnt.item())
-        if v == 0:
-            out.append((w, np.zeros(0, np.uint64), np.zeros(0, np.uint64)))
-            continue
-        sbh.sbh_kpa_keyswap_lookup(sp[:v], ads, campaign_of_ad, camp)
-        sort_scr = _fit(sort_scr, sbh.sort_scratch_bytes(v), dev)
-        sbh.sbh_kpa_sort(camp[:v], sp[:v], keys[:v], ptrs[:v], scratch=sort_scr)
-        red_scr = sbh.sbh_group_reduce(keys[:v], ptrs[:v], None, ok, oc, None, big, nk,
-                                       scratch=_fit(red_scr, sbh.group_reduce_scratch_bytes(v, 8), dev))
-        u = int(nk.item())
-        out.append((w, ok[:u].cpu().numpy(), oc[:u].cpu().numpy()))
+    for w, wb in b.windows("event_time", window_ns, trace):
+        views = operators.select(wb, "event_type", view, view + 1, trace)
+        k, c = operators.count_per_key(views, campaign, trace)
+        out.append((w, k, c))
     return out

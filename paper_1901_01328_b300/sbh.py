@@ -78,6 +78,7 @@ def _load() -> ctypes.CDLL:
         "sbh_mlp_grad": ([vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
         "sbh_learned_train": ([vp, u64, u64, vp, i32, i32, ctypes.c_float, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort_learned": ([vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
+        "sbh_kpa_partition": ([vp, vp, u64, vp, u64, vp, vp, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -96,7 +97,7 @@ EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_li
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
             "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_keyswap_lookup",
             "sbh_kpa_select",
-            "sbh_median_unique",
+            "sbh_median_unique", "sbh_kpa_partition",
             "sbh_topk", "sbh_join")
 
 
@@ -338,6 +339,19 @@ def sbh_median_unique(keys, ptrs, vals, out_keys, out_median, out_unique, cap, n
     return scratch
 
 
+def sbh_kpa_partition(keys, ptrs, bounds, keys_out, ptrs_out, offsets, scratch=None, stream=None):
+    """bounds: device uint64 tensor of nb non-decreasing keys; offsets: device
+    uint64 tensor of nb + 2 entries."""
+    nb = 0 if bounds is None else bounds.numel()
+    assert offsets.numel() == nb + 2
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(bounds), nb, _p(keys_out), _p(ptrs_out), _p(offsets))
+    if scratch is None:
+        return _scratch(_lib.sbh_kpa_partition, args, (_stream(stream),), "sbh_kpa_partition", offsets.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_kpa_partition(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_kpa_partition")
+    return scratch
+
+
 # ----------------------------------------------------------------- conveniences
 def _u64(n, dev):
     return torch.empty(n, dtype=torch.uint64, device=dev)
@@ -415,6 +429,15 @@ def join(lkeys, lptrs, rkeys, rptrs, cap=None):
     sbh_join(lkeys, lptrs, rkeys, rptrs, ol, orr, cap, npairs)
     m = min(int(npairs.item()), cap)
     return ol[:m], orr[:m]
+
+
+def partition(keys, ptrs, bounds):
+    """(keys, ptrs, offsets) of the KPA split by the key ranges that bounds cut."""
+    dev = keys.device
+    ok, op = _u64(keys.numel(), dev), _u32(keys.numel(), dev)
+    off = _u64(bounds.numel() + 2, dev)
+    sbh_kpa_partition(keys, ptrs, bounds, ok, op, off)
+    return ok, op, off
 
 
 def window_ranges(ts, starts, length):

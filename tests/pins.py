@@ -153,3 +153,38 @@ def check_join(lkeys_by_ptr, rkeys_by_ptr, out_l, out_r, cardinality):
     assert np.array_equal(order, np.arange(out_l.size)), "pair order"
     packed = out_l * (1 << 32) + out_r
     assert np.unique(packed).size == packed.size, "duplicate pair"
+
+
+def brute_partition(keys, ptrs, bounds):
+    """Partition by key ranges in plain Python: one pass over the parts, each
+    collecting, in input order, the records whose key lies in its range."""
+    keys = [int(k) for k in keys]
+    ptrs = [int(p) for p in ptrs]
+    bounds = [int(b) for b in bounds]
+    ok, op, off = [], [], []
+    for j in range(len(bounds) + 1):
+        lo = bounds[j - 1] if j > 0 else None
+        hi = bounds[j] if j < len(bounds) else None
+        off.append(len(ok))
+        for k, p in zip(keys, ptrs):
+            if (lo is None or k >= lo) and (hi is None or k < hi):
+                ok.append(k)
+                op.append(p)
+    off.append(len(ok))
+    return np.array(ok, np.uint64), np.array(op, np.uint32), np.array(off, np.uint64)
+
+
+def check_partition(keys, ptrs, bounds, out_keys, out_ptrs, offsets):
+    """Invariants of a partition at any size: the offsets cut the output into
+    one part per range, every part's keys lie in its range, each part lists
+    exactly the input records of its range in their input order."""
+    keys, ptrs = np.asarray(keys, np.uint64), np.asarray(ptrs, np.uint32)
+    bounds, offsets = np.asarray(bounds, np.uint64), np.asarray(offsets, np.uint64)
+    assert offsets.size == bounds.size + 2 and offsets[0] == 0 and int(offsets[-1]) == keys.size
+    assert np.all(offsets[1:] >= offsets[:-1])
+    part = np.searchsorted(bounds, keys, side="right")  # bounds not above the key
+    for j in range(bounds.size + 1):
+        a, b = int(offsets[j]), int(offsets[j + 1])
+        sel = part == j
+        assert np.array_equal(out_keys[a:b], keys[sel]), f"part {j} keys"
+        assert np.array_equal(out_ptrs[a:b], ptrs[sel]), f"part {j} ptrs"

@@ -266,3 +266,40 @@ def test_oracle_reproduces_the_worked_example():
     w = g["window_2_4"]
     b, e = oracle.window_ranges(np.array(w["ts"], np.uint64), np.array([w["start"]], np.uint64), w["len"])
     assert [int(b[0]), int(e[0])] == w["rows"]
+    q = g["partition_3_6"]
+    pk, pp, po = oracle.partition(keys, np.arange(keys.size, dtype=np.uint32), np.array(q["bounds"], np.uint64))
+    assert pk.tolist() == q["keys"] and pp.tolist() == q["ptrs"] and po.tolist() == q["offsets"]
+
+
+# ------------------------------------------------------------- partition (Table 2)
+@pytest.mark.parametrize("n", [0, 1, 5, 64])
+@pytest.mark.parametrize("bounds", [[], [3], [2, 2, 9], [0, 1 << 63, M64]])
+def test_partition_matches_brute_force(n, bounds):
+    k, _ = _tiny(n, 12, 40 + n)
+    p = gen.uniform(40, 3, n, 0, 50, np.uint32)  # arbitrary, repeated ptrs: parts keep input order
+    b = np.array(bounds, np.uint64)
+    ok, op, off = oracle.partition(k, p, b)
+    bk, bp, boff = pins.brute_partition(k, p, b)
+    assert np.array_equal(ok, bk) and np.array_equal(op, bp) and np.array_equal(off, boff)
+
+
+def test_partition_invariants_and_planted_mistakes():
+    n = 50_000
+    col = gen.mixed_keys(n, seed=12)
+    ptrs = np.arange(n, dtype=np.uint32)
+    bounds = np.sort(gen.mixed_keys(300, seed=13))
+    ok, op, off = oracle.partition(col, ptrs, bounds)
+    pins.check_partition(col, ptrs, bounds, ok, op, off)
+    big = [j for j in range(1, bounds.size) if off[j + 1] - off[j] >= 2]
+    j0, j1 = big[0], big[1]
+    a = op.copy(); a[[int(off[j0]), int(off[j0]) + 1]] = a[[int(off[j0]) + 1, int(off[j0])]]  # order in a part
+    b = off.copy(); b[j1] += np.uint64(1)                                                  # a row in the wrong part
+    c = ok.copy(); c[int(off[j1])] = bounds[j1]                                            # a key out of its range
+    for kk, pp, oo in ((ok, a, off), (ok, op, b), (c, op, off)):
+        with pytest.raises(AssertionError):
+            pins.check_partition(col, ptrs, bounds, kk, pp, oo)
+    # the part sizes are the numbers of keys per range, counted directly
+    sizes = np.diff(off)
+    assert int(sizes[0]) == int(np.sum(col < bounds[0]))
+    assert int(sizes[100]) == int(np.sum((col >= bounds[99]) & (col < bounds[100])))
+    assert int(sizes[300]) == int(np.sum(col >= bounds[299]))
