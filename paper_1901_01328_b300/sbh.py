@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "sbh_learned_train": ([vp, u64, u64, vp, i32, i32, ctypes.c_float, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort_learned": ([vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_partition": ([vp, vp, u64, vp, u64, vp, vp, vp, vp, sz, vp], i32),
+        "sbh_copy_counted": ([vp, vp, i32, vp, u64, u64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -97,7 +98,7 @@ EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_li
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
             "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_keyswap_lookup",
             "sbh_kpa_select",
-            "sbh_median_unique", "sbh_kpa_partition",
+            "sbh_median_unique", "sbh_kpa_partition", "sbh_copy_counted",
             "sbh_topk", "sbh_join")
 
 
@@ -307,6 +308,14 @@ def sbh_join(lkeys, lptrs, rkeys, rptrs, out_l, out_r, cap, npairs, scratch=None
 def sbh_kpa_materialize(ptrs, col, out, stream=None):
     _check(_lib.sbh_kpa_materialize(_p(ptrs), ptrs.numel(), _p(col), col.element_size(), _p(out), _stream(stream)),
            "sbh_kpa_materialize")
+
+
+def sbh_copy_counted(src, dst, count, per=1, cap=None, stream=None):
+    """dst[:min(count, cap) * per] = src[...]; count is a device uint64
+    tensor; dst may be a page-locked CPU tensor."""
+    cap = src.numel() // per if cap is None else cap
+    _check(_lib.sbh_copy_counted(_p(src), _p(dst), src.element_size(), _p(count), per, cap, _stream(stream)),
+           "sbh_copy_counted")
 
 
 def sbh_kpa_keyswap(ptrs, key_col, keys_out, stream=None):

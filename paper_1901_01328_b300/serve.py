@@ -14,7 +14,8 @@ the two slots by timestamp (`sbh_kpa_split_ts`, no host synchronisation).
 When the watermark (max timestamp seen minus the allowed lateness) passes a
 window's end, the window closes: its slot is sorted, reduced (sum and count)
 and top-K'd against the arena, the results are copied to the host, and the
-slot is emptied for the window after next.
+slot is emptied for the window after next.  `WindowClock` decides when
+windows close, including, with an idle timeout, when the source stalls.
 
 Memory is fixed at start-up from the HBM budget: a bundle that does not fit
 in the arena is shed (counted); a slot that would pass its capacity sets an
@@ -87,11 +88,73 @@ class ArenaRing:
             self.head = 0
 
 
+class WindowClock:
+    """When windows close (host logic only; no device state).
+
+    A watermark promises that no record still to come is older than it
+    (Sec. 3).  Here it is the largest timestamp seen minus the allowed
+    lateness, and window [w L, (w + 1) L) closes once the watermark reaches
+    its end.  A source that stops sending would leave the watermark, and so
+    every open window, stuck.  The idle rule: after idle_ns of processing
+    time without a bundle, event time is taken to advance at the rate of
+    processing time from the last bundle's largest timestamp, and the
+    watermark follows it; windows up to the newest one that holds rows then
+    close.  So once the source stalls, every open window has closed within
+    max(idle_ns, L + lateness) of processing time after the last bundle (plus
+    the interval between ticks).  Records that arrive later than the
+    watermark are dropped and counted by the split."""
+
+    def __init__(self, win_len, lateness, idle_ns=None):
+        self.L, self.lateness = int(win_len), int(lateness)
+        self.idle_ns = None if idle_ns is None else int(idle_ns)
+        self.wm = None         # watermark (event time, ns)
+        self.first_win = None  # oldest open window
+        self.last_ts = None    # largest timestamp seen
+        self.last_wall = None  # processing time (ns) of the last bundle
+
+    def _due(self, wm, limit=None):
+        out = []
+        while (self.first_win + 1) * self.L <= wm and (limit is None or self.first_win <= limit):
+            out.append(self.first_win)
+            self.first_win += 1
+        return out
+
+    def on_bundle(self, min_ts, max_ts, wall_ns):
+        """A bundle with timestamps in [min_ts, max_ts] arrives: the windows
+        that close before it lands, oldest first."""
+        if self.first_win is None:
+            self.first_win = max(0, min_ts) // self.L
+        new_wm = max_ts - self.lateness if self.wm is None else max(self.wm, max_ts - self.lateness)
+        due = self._due(new_wm)
+        self.wm = new_wm
+        self.last_ts = max_ts if self.last_ts is None else max(self.last_ts, max_ts)
+        self.last_wall = wall_ns
+        return due
+
+    def on_idle(self, wall_ns):
+        """Processing time wall_ns with no bundle since the last: the windows
+        the idle rule closes now."""
+        if self.idle_ns is None or self.last_wall is None or wall_ns - self.last_wall < self.idle_ns:
+            return []
+        wm = self.last_ts + (wall_ns - self.last_wall) - self.lateness
+        if wm <= self.wm:
+            return []
+        self.wm = wm
+        return self._due(wm, limit=self.last_ts // self.L)
+
+    def open_windows(self):
+        """Windows still open (the oldest up to the newest holding rows)."""
+        if self.first_win is None or self.last_ts is None:
+            return []
+        return list(range(self.first_win, self.last_ts // self.L + 1))
+
+
 class WindowServer:
     def __init__(self, win_len, lateness, slot_rows, arena_rows, max_bundle, K=3, device="cuda", keep=True,
-                 out_rows=None):
+                 out_rows=None, idle_ns=None):
         dev = torch.device(device)
         self.dev, self.win_len, self.lateness, self.K = dev, int(win_len), int(lateness), K
+        self.clock = WindowClock(win_len, lateness, idle_ns)
         self.slots = [(_u64(slot_rows, dev), _u32(slot_rows, dev)) for _ in range(2)]
         self.fill = torch.zeros(2, dtype=torch.uint64, device=dev)
         self.dropped = torch.zeros(1, dtype=torch.uint64, device=dev)
@@ -117,8 +180,6 @@ class WindowServer:
                      torch.empty(out, dtype=torch.uint64).pin_memory(), torch.empty(out, dtype=torch.uint8).pin_memory(),
                      torch.empty(out * K, dtype=torch.uint64).pin_memory(),
                      torch.empty(out * K, dtype=torch.uint32).pin_memory())
-        self.wm = None
-        self.first_win = None  # oldest open window
         self.ring = ArenaRing(arena_rows)
         self.log = []          # (arena offset, rows, ts_base) of every admitted bundle
         self.results = []
@@ -130,20 +191,25 @@ class WindowServer:
         self.truncated = 0
 
     # ---------------------------------------------------------------- bundles
-    def admit(self, keys_h, vals_h, ts_rel_h, ts_base, max_ts):
+    @property
+    def first_win(self):
+        return self.clock.first_win
+
+    @property
+    def wm(self):
+        return self.clock.wm
+
+    def admit(self, keys_h, vals_h, ts_rel_h, ts_base, max_ts, wall_ns=None):
         """keys_h, vals_h (uint64) and ts_rel_h (int64) are page-locked host
         tensors of one bundle; row i has timestamp ts_base + ts_rel_h[i] and
-        max_ts is the largest.  Returns False when the bundle is shed."""
+        max_ts is the largest; wall_ns is the processing time of its arrival
+        (default: now).  Returns False when the bundle is shed."""
         n = keys_h.numel()
         t_admit = time.perf_counter()
-        new_wm = max_ts - self.lateness if self.wm is None else max(self.wm, max_ts - self.lateness)
-        if self.first_win is None:
-            self.first_win = max(0, (ts_base + int(ts_rel_h.min()) if n else ts_base)) // self.win_len
+        min_ts = ts_base + int(ts_rel_h.min()) if n and self.clock.first_win is None else ts_base
         # windows whose end the watermark has passed close before this bundle lands
-        while (self.first_win + 1) * self.win_len <= new_wm:
-            self._close(self.first_win, t_admit)
-            self.first_win += 1
-        self.wm = new_wm
+        for w in self.clock.on_bundle(min_ts, max_ts, time.perf_counter_ns() if wall_ns is None else wall_ns):
+            self._close(w, t_admit)
         w_new = max_ts // self.win_len
         # admission: the arena must have room, and the bundle's newest
         # window must stay below its slot's capacity (2% kept for late rows)
@@ -168,27 +234,43 @@ class WindowServer:
         self.admitted_rows += n
         return True
 
+    def tick(self, wall_ns=None):
+        """Processing time passes with no bundle (the source may have
+        stalled): closes the windows that the clock's idle rule releases.
+        Returns how many closed."""
+        due = self.clock.on_idle(time.perf_counter_ns() if wall_ns is None else wall_ns)
+        t = time.perf_counter()
+        for w in due:
+            self._close(w, t)
+        return len(due)
+
     def finish(self, t_now=None):
         """Close every open window (end of stream)."""
         t = time.perf_counter() if t_now is None else t_now
-        if self.first_win is None:
-            return
-        last = (self.wm + self.lateness) // self.win_len if self.wm is not None else self.first_win
-        while self.first_win <= last:
-            self._close(self.first_win, t)
-            self.first_win += 1
+        for w in self.clock.open_windows():
+            self._close(w, t)
+        if self.clock.first_win is not None and self.clock.last_ts is not None:
+            self.clock.first_win = max(self.clock.first_win, self.clock.last_ts // self.win_len + 1)
 
     # ---------------------------------------------------------------- window close
     def _close(self, w, t_trigger):
+        """Closes window w: two host synchronisations, one to read the slot's
+        size (it sizes the sort) and one when the results are in host memory
+        (they are copied by kernels that read the number of keys on the
+        device)."""
         s = w & 1
         keys, ptrs = self.slots[s]
+        stream = torch.cuda.current_stream(self.dev)
         self.fill_h.copy_(self.fill, non_blocking=True)
-        torch.cuda.current_stream(self.dev).synchronize()
+        stream.synchronize()
+        t1 = time.perf_counter()
         m = int(self.fill_h[s])
         K = self.K
         res = None
-        t_dev = None
+        dev_s = None
         if m:
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
             ok, op = keys[:m], ptrs[:m]
             sbh.sbh_kpa_sort(ok, op, ok, op, scratch=self.sort_scr)  # in place
             cap = self.out_rows
@@ -196,17 +278,17 @@ class WindowServer:
             sbh.sbh_group_reduce(ok, op, self.arena, rk, rc, rs, cap, rn, scratch=self.red_scr)
             tk, tn, tv, tp, tnk = self.top
             sbh.sbh_topk(ok, op, self.arena, K, tk, tn, tv, tp, cap, tnk, scratch=self.top_scr)
+            ev1.record(stream)
+            hk, hc, hs, hn, hv, hp = self.host
+            for h, d, per in ((hk, rk, 1), (hc, rc, 1), (hs, rs, 1), (hn, tn, 1), (hv, tv, K), (hp, tp, K)):
+                sbh.sbh_copy_counted(d, h, rn, per, cap)
             self.nk_h.copy_(rn, non_blocking=True)
-            torch.cuda.current_stream(self.dev).synchronize()
-            t_dev = time.perf_counter()
+            stream.synchronize()
+            dev_s = (t1 - t_trigger) + ev0.elapsed_time(ev1) / 1e3
             u = int(self.nk_h[0])
             if u > cap:
                 self.truncated += 1
                 u = cap
-            hk, hc, hs, hn, hv, hp = self.host
-            for h, d, m_ in ((hk, rk, u), (hc, rc, u), (hs, rs, u), (hn, tn, u), (hv, tv, u * K), (hp, tp, u * K)):
-                h[:m_].copy_(d[:m_], non_blocking=True)
-            torch.cuda.current_stream(self.dev).synchronize()
             if self.keep:
                 res = [hk[:u].clone(), hc[:u].clone(), hs[:u].clone(), hn[:u].clone(), hv[:u * K].clone().view(u, K),
                        hp[:u * K].clone().view(u, K)]
@@ -214,7 +296,7 @@ class WindowServer:
         self.fill[s:s + 1].zero_()
         r = (WindowResult(w, *(x.numpy() for x in res), lat, m) if res else
              WindowResult(w, None, None, None, None, None, None, lat, m))
-        r.device_latency_s = (t_dev - t_trigger) if m else lat
+        r.device_latency_s = dev_s if m else lat
         self.results.append(r)
         self.ring.release(w)
         self.est.pop(w, None)
@@ -273,14 +355,21 @@ def poisson_schedule(gen, seed, duration_ns, load, mean_rows):
     return t[t < duration_ns].astype(np.int64)
 
 
-def run_loop(server, pool, arrivals, realtime=True, t0_ns=0):
-    """Feeds the bundles at their arrival times (wall clock when realtime)."""
+def run_loop(server, pool, arrivals, realtime=True, t0_ns=0, tick_ns=1_000_000):
+    """Feeds the bundles at their arrival times (wall clock when realtime),
+    letting the server's clock tick about every tick_ns while it waits (so
+    an idle rule, when the server has one, can close windows of a stalled
+    source); closes every open window at the end of the stream."""
     start = time.perf_counter()
+    last_tick = time.perf_counter_ns()
     for i, a in enumerate(arrivals):
         if realtime:
             due = start + (a - arrivals[0]) * 1e-9
             while time.perf_counter() < due:
-                pass
+                now = time.perf_counter_ns()
+                if now - last_tick >= tick_ns:
+                    server.tick(now)
+                    last_tick = now
         k, v, t = pool.get(i)
         base = int(t0_ns + a)
         server.admit(k, v, t, base, base)

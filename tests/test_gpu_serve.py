@@ -128,3 +128,43 @@ def test_split_by_timestamp_slots_capacity_and_drops(V):
         assert np.array_equal(sp[:m].cpu().numpy(), (idx[:m] + 7).astype(np.uint32))
     assert int(dropped.item()) == int(np.sum((w == 0) | (w == 3)))
     assert int(over.item()) == (1 if max(np.sum(w == 1), np.sum(w == 2)) > cap else 0) == 1
+
+
+def test_serving_stalled_source_closes_windows_by_idle_rule(V):
+    # the source stops after ~6 of 8 windows and never signals the end: the
+    # server's idle rule (processing time = event time - t0 here) closes every
+    # open window within max(idle, window + lateness) of processing time, and
+    # the windows' results match the oracle
+    win, late, idle = 1_000_000, 100_000, 300_000
+    arena_rows = 900_000
+    pool = V.BundlePool(gen, 8, 2000, 20_000, 0.8, 50_000_000, 0.05, late, SEED)
+    arr = V.poisson_schedule(gen, SEED, 8 * win, 3.3e8, float(pool.sizes.mean()))
+    arr = arr[arr < 6 * win + win // 3]
+    server = V.WindowServer(win, late, slot_rows=1 << 20, arena_rows=arena_rows, max_bundle=20_000, K=3,
+                            idle_ns=idle)
+    t0 = 10 * win
+    admitted = []
+    for i, a in enumerate(arr):
+        k, v, t = pool.get(i)
+        base = int(t0 + a)
+        if server.admit(k, v, t, base, base, wall_ns=int(a)):
+            admitted.append(i)
+        assert server.tick(int(a) + 1) == 0  # the source is not idle yet
+    last_wall, last_ts = int(arr[-1]), int(t0 + arr[-1])
+    open_before = server.clock.open_windows()
+    assert open_before and len(server.results) > 0
+    t = last_wall
+    while server.clock.open_windows():
+        t += 50_000
+        server.tick(t)
+        assert t - last_wall <= max(idle, win + late) + 50_000
+    closed = {r.w for r in server.results}
+    assert set(open_before) <= closed
+    exp = _oracle_windows(server, pool, admitted, win, arena_rows)
+    got = {r.w: r for r in server.results}
+    for w, (uk, uc, us, tn, tv, tp, n) in exp.items():
+        r = got[w]
+        assert r.rows == n and np.array_equal(r.keys, uk) and np.array_equal(r.sums, us)
+        assert np.array_equal(r.tvals, tv) and np.array_equal(r.tptrs, tp)
+    st = server.stats()
+    assert st["dropped_rows"] == 0 and sum(r.rows for r in server.results) == st["admitted_rows"]
