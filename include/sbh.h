@@ -92,12 +92,19 @@ void sbh_set_fault(int fault);
  *                                    (default 2^23);
  *   SBH_KNOB_MERGE_SEARCH_MIN_TILES  merges of more than this many 2048-row
  *                                    output tiles find the tiles' cuts in a
- *                                    separate parallel search (default 2047).
+ *                                    separate parallel search (default 2047);
+ *   SBH_KNOB_SCATTER_GEOM            tile and CTA of the plain sort's chunked
+ *                                    scatter: 0 = 4096 rows, 512 threads,
+ *                                    two CTAs per SM (default); 1 = 2048
+ *                                    rows, 256 threads, four; 2 = 8192 rows,
+ *                                    1024 threads, one.
  * A sort's scratch size depends on the first knob: size it after setting.
- * sbh_set_knob returns SBH_EINVAL for an unknown knob; sbh_get_knob 0. */
+ * sbh_set_knob returns SBH_EINVAL for an unknown knob or an out-of-range
+ * geometry; sbh_get_knob 0 for an unknown knob. */
 #define SBH_KNOB_SORT_CHUNKED_MIN 0
 #define SBH_KNOB_MERGE_SEARCH_MIN_TILES 1
-#define SBH_KNOB_COUNT 2
+#define SBH_KNOB_SCATTER_GEOM 2
+#define SBH_KNOB_COUNT 3
 int sbh_set_knob(int knob, uint64_t value);
 uint64_t sbh_get_knob(int knob);
 
@@ -195,6 +202,24 @@ int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t*
 int sbh_kpa_merge(int nruns, const uint64_t* const* d_run_keys, const uint32_t* const* d_run_ptrs,
                   const uint64_t* run_lens, uint64_t* d_keys_out, uint32_t* d_ptrs_out, void* d_scratch,
                   size_t* scratch_bytes, void* stream);
+
+/* Many independent merges in one pass (Sec. 4.2 "Temporal Join" merges
+ * the sorted KPAs of each window; with sliding windows built from panes,
+ * every window merges its panes, and all windows are merged at once here).
+ * Segment g merges A rows [a_start[g], a_start[g] + a_len[g]) of (d_a_keys,
+ * d_a_ptrs) with B rows [b_start[g], b_start[g] + b_len[g]) of (d_b_keys,
+ * d_b_ptrs), each sorted in (key, ptr) order, into (key, ptr) order; the
+ * segments' outputs lie end to end in (d_keys_out, d_ptrs_out) in segment
+ * order.  The four segment arrays are host arrays of nseg values; segments
+ * may overlap in the inputs (A and B may be the same arrays); every row
+ * index and the total output stay below 2^32.  Two kernels: the co-rank of
+ * every output tile (a binary search per 2048-row tile) and the merge path
+ * of every tile.  The output must not overlap the inputs.
+ * Scratch: 48 bytes per segment plus 4 bytes per 2048 output rows. */
+int sbh_kpa_merge_segments(int nseg, const uint64_t* d_a_keys, const uint32_t* d_a_ptrs, const uint64_t* d_b_keys,
+                           const uint32_t* d_b_ptrs, const uint64_t* a_start, const uint64_t* a_len,
+                           const uint64_t* b_start, const uint64_t* b_len, uint64_t* d_keys_out,
+                           uint32_t* d_ptrs_out, void* d_scratch, size_t* scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------- A6
  * Keyed reduction (Table 2; Sec. 4.2 "Reduction primitives": scan a sorted
@@ -330,6 +355,23 @@ int sbh_kpa_partition(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n
 int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, const uint64_t* d_rkeys,
              const uint32_t* d_rptrs, uint64_t nr, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
              uint64_t* d_npairs, void* d_scratch, size_t* scratch_bytes, void* stream);
+
+/* Many independent joins in one pass (Sec. 4.2 "Temporal Join", every
+ * window of a sliding-window join at once).  Segment g joins L rows
+ * [l_off[g], l_off[g + 1]) of (d_lkeys, d_lptrs) with R rows [r_start[g],
+ * r_start[g] + r_len[g]) of (d_rkeys, d_rptrs), each sorted in (key, ptr)
+ * order; the pairs of segment g, in (key, ptrL, ptrR) order, are output rows
+ * [d_seg_pairs[g], d_seg_pairs[g + 1]) of (d_out_l, d_out_r).  l_off (host,
+ * nseg + 1 non-decreasing values from 0), r_start and r_len (host, nseg
+ * values) describe the segments; R segments may overlap.  *d_npairs and
+ * d_seg_pairs[nseg] receive the total; only the first cap pairs are
+ * written.  L below 2^32 rows.
+ * Scratch: about 8 bytes per L row plus 24 bytes per segment. */
+int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs, const uint64_t* l_off,
+                      const uint64_t* d_rkeys, const uint32_t* d_rptrs, const uint64_t* r_start,
+                      const uint64_t* r_len, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
+                      uint64_t* d_npairs, uint64_t* d_seg_pairs, void* d_scratch, size_t* scratch_bytes,
+                      void* stream);
 
 /* ---------------------------------------------------------------- A4
  * Learned MSD partition sort.  The paper has no learned component (its Sort

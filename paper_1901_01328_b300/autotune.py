@@ -10,6 +10,16 @@ current GPU and sets the knobs (sbh_set_knob) to the fastest.
   merge cuts   small merges let each CTA search its own cuts; large ones
                search them in a separate parallel kernel first.  The tuner
                times both and sets SBH_KNOB_MERGE_SEARCH_MIN_TILES.
+  scatter      the chunked scatter's tile and CTA shape (4096 rows x 512
+               threads, 2048 x 256, 8192 x 1024: more rows per tile mean
+               fewer tiles and barriers, fewer mean more CTAs per SM to hide
+               latency).  The tuner times the plain sort with each on large
+               sorts and sets SBH_KNOB_SCATTER_GEOM to the fastest.
+  digit width  stays 8 bits: a digit's per-warp counters, packed two per
+               word, and its 256-entry scans fit the two-CTA shared-memory
+               budget of the scatter; 11-bit digits (2048 counters per warp)
+               would not, and would save passes only on keys of more than
+               about 40 significant bits.
   schedule     for many small windows, `batched_schedule` times the batched
                (composite-key) and per-window schedules of
                pipeline.batched_windows on a sample and returns the faster.
@@ -105,6 +115,31 @@ def tune_merge_search(totals=(1 << 20, 1 << 21, 1 << 22, 1 << 23), seed=12):
     return {"knob": "SBH_KNOB_MERGE_SEARCH_MIN_TILES", "value": choice, "timings_ms": timings}
 
 
+def tune_scatter_geometry(sizes=(1 << 25, 1 << 26), seed=13):
+    """Times the plain sort of mixed 64-bit keys (chunked passes) with each
+    scatter geometry; sets and returns the fastest over the sizes."""
+    old = sbh.get_knob(sbh.KNOB_SCATTER_GEOM)
+    timings = {}
+    try:
+        for n in sizes:
+            keys, ptrs = sbh.extract(_keys(n, seed), 0, n)
+            out = (torch.empty_like(keys), torch.empty_like(ptrs))
+            scr = torch.empty(sbh.sort_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+            row = {}
+            for geom in sorted(sbh.SCATTER_GEOMS):
+                sbh.set_knob(sbh.KNOB_SCATTER_GEOM, geom)
+                row[geom] = _time(lambda: sbh.sbh_kpa_sort(keys, ptrs, out[0], out[1], scratch=scr))
+            timings[n] = row
+            del keys, ptrs, out, scr
+    finally:
+        sbh.set_knob(sbh.KNOB_SCATTER_GEOM, old)
+    total = {g: sum(timings[n][g] for n in sizes) for g in sbh.SCATTER_GEOMS}
+    choice = min(total, key=total.get)
+    sbh.set_knob(sbh.KNOB_SCATTER_GEOM, choice)
+    return {"knob": "SBH_KNOB_SCATTER_GEOM", "value": choice, "geometry": sbh.SCATTER_GEOMS[choice],
+            "timings_ms": timings}
+
+
 def batched_schedule(key_col, val_col, offsets, K=3, sample_windows=64):
     """Times both schedules of pipeline.batched_windows on the first
     sample_windows windows and returns ("batched" | "loop", timings)."""
@@ -126,19 +161,22 @@ def batched_schedule(key_col, val_col, offsets, K=3, sample_windows=64):
     return min(t, key=t.get), t
 
 
-def autotune(cache=None):
+def autotune(cache=None, quick=False):
     """Tunes every knob (or loads them from `cache`, a JSON file, when it
-    holds this device's values); returns the chosen values."""
+    holds this device's values); returns the chosen values.  quick: smaller
+    sorts for the scatter geometry."""
     dev = torch.cuda.get_device_name()
     if cache and os.path.exists(cache):
         with open(cache) as f:
             saved = json.load(f).get(dev)
-        if saved:
+        if saved and "SBH_KNOB_SCATTER_GEOM" in saved:
             sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, saved["SBH_KNOB_SORT_CHUNKED_MIN"])
             sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, saved["SBH_KNOB_MERGE_SEARCH_MIN_TILES"])
+            sbh.set_knob(sbh.KNOB_SCATTER_GEOM, saved["SBH_KNOB_SCATTER_GEOM"])
             return saved
     res = {"SBH_KNOB_SORT_CHUNKED_MIN": tune_sort_threshold()["value"],
-           "SBH_KNOB_MERGE_SEARCH_MIN_TILES": tune_merge_search()["value"]}
+           "SBH_KNOB_MERGE_SEARCH_MIN_TILES": tune_merge_search()["value"],
+           "SBH_KNOB_SCATTER_GEOM": tune_scatter_geometry(sizes=(1 << 24,) if quick else (1 << 25, 1 << 26))["value"]}
     if cache:
         data = {}
         if os.path.exists(cache):

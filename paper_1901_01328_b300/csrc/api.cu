@@ -25,7 +25,7 @@ constexpr uint32_t kDefaultSpinLimit = 1u << 22;  // a few seconds of polls
 std::atomic<uint32_t> g_spin_limit{kDefaultSpinLimit};
 // tuning knobs (sbh_set_knob): the sorts' chunked-pass threshold and the
 // merges' separate cut-search threshold
-std::atomic<uint64_t> g_knob[SBH_KNOB_COUNT] = {{1ull << 23}, {2047}};  // measured on B300
+std::atomic<uint64_t> g_knob[SBH_KNOB_COUNT] = {{1ull << 23}, {2047}, {0}};  // measured on B300
 std::atomic<int> g_fault{SBH_FAULT_NONE};
 
 struct ProfRecord {
@@ -111,6 +111,7 @@ int sbh_set_knob(int k, uint64_t value) {
     using namespace sbh;
     clear_error();
     if (k < 0 || k >= SBH_KNOB_COUNT) { set_error("unknown knob %d", k); return SBH_EINVAL; }
+    if (k == SBH_KNOB_SCATTER_GEOM && value > 2) { set_error("scatter geometry must be 0, 1 or 2"); return SBH_EINVAL; }
     g_knob[k].store(value);
     return SBH_OK;
 }

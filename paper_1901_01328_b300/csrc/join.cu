@@ -138,8 +138,126 @@ join_emit_kernel(const uint32_t* __restrict__ lp, uint32_t nl, const uint32_t* _
     }
 }
 
+// ---------------------------------------------------------------- many independent joins
+// L rows [l_off[g], l_off[g + 1]) join R rows [r_start[g], r_start[g] +
+// r_len[g]) (segment g).  Row i of L finds its segment by binary search on
+// l_off, then its key's range in its R segment; rlo holds absolute R rows, so
+// the emit kernel above serves unchanged.
+__global__ void __launch_bounds__(kThreads)
+join_seg_count_kernel(const uint64_t* __restrict__ lk, uint32_t nl, const uint64_t* __restrict__ rk,
+                      const uint64_t* __restrict__ l_off, const uint64_t* __restrict__ r_start,
+                      const uint64_t* __restrict__ r_len, uint32_t nseg, uint32_t* __restrict__ rlo,
+                      uint32_t* __restrict__ cnt, uint64_t* __restrict__ bsum) {
+    __shared__ uint64_t red[kThreads / 32];
+    const uint32_t base = blockIdx.x * kTile;
+    uint64_t local = 0;
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        const uint32_t i = base + t * kThreads + threadIdx.x;
+        if (i < nl) {
+            uint32_t a = 0, b = nseg;  // last segment with l_off <= i
+            while (b - a > 1) {
+                const uint32_t mid = (a + b) / 2;
+                if (l_off[mid] <= i) a = mid;
+                else b = mid;
+            }
+            const uint64_t k = lk[i];
+            const uint64_t* seg = rk + r_start[a];
+            const uint32_t n = static_cast<uint32_t>(r_len[a]);
+            const uint32_t lo = lower_bound_key(seg, n, k);
+            const uint32_t hi = upper_bound_key(seg, lo, n, k);
+            rlo[i] = static_cast<uint32_t>(r_start[a]) + lo;
+            cnt[i] = hi - lo;
+            local += hi - lo;
+        }
+    }
+    const uint64_t t = block_sum(local, red);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+// seg_pairs[g] = the first output pair of segment g (the pairs of all L rows
+// before l_off[g]), from the scanned block offsets and the counts of the
+// rows before it in its block; one warp per segment; seg_pairs[nseg] = total.
+__global__ void join_seg_offsets_kernel(const uint64_t* __restrict__ l_off, uint32_t nseg, uint32_t nl,
+                                        const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ boff,
+                                        const uint64_t* __restrict__ total, uint64_t* __restrict__ seg_pairs) {
+    const uint32_t g = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (g > nseg) return;
+    const uint64_t row = g < nseg ? l_off[g] : nl;
+    if (row >= nl) {
+        if (lane_id() == 0) seg_pairs[g] = *total;
+        return;
+    }
+    const uint32_t blk = static_cast<uint32_t>(row / kTile);
+    uint64_t v = 0;
+    for (uint32_t i = blk * kTile + lane_id(); i < row; i += 32) v += cnt[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane_id() == 0) seg_pairs[g] = boff[blk] + v;
+}
+
 }  // namespace
 }  // namespace sbh
+
+extern "C" int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs, const uint64_t* l_off,
+                                 const uint64_t* d_rkeys, const uint32_t* d_rptrs, const uint64_t* r_start,
+                                 const uint64_t* r_len, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
+                                 uint64_t* d_npairs, uint64_t* d_seg_pairs, void* d_scratch, size_t* scratch_bytes,
+                                 void* stream) {
+    using namespace sbh;
+    clear_error();
+    if (nseg < 1 || !l_off || !r_start || !r_len) { set_error("bad segment arrays"); return SBH_EINVAL; }
+    if (l_off[0] != 0) { set_error("l_off[0] must be 0"); return SBH_EINVAL; }
+    for (int g = 0; g < nseg; ++g) {
+        if (l_off[g + 1] < l_off[g]) { set_error("l_off must be non-decreasing"); return SBH_EINVAL; }
+        if (r_start[g] + r_len[g] > 0xFFFFFFFFull) { set_error("segment %d of R reaches past 2^32 rows", g); return SBH_EINVAL; }
+    }
+    const uint64_t nl = l_off[nseg];
+    if (nl > 0xFFFFFFFFull) { set_error("L must have < 2^32 rows"); return SBH_EINVAL; }
+    const uint64_t nblocks = (nl + kTile - 1) / kTile;
+    Carver c(nullptr);
+    c.take<uint32_t>(nl);
+    c.take<uint32_t>(nl);
+    c.take<uint64_t>(nblocks + 1);
+    c.take<uint64_t>(3 * (size_t)nseg + 1);
+    bool done = false;
+    int rc = scratch_check(d_scratch, scratch_bytes, c.bytes(), &done);
+    if (rc || done) return rc;
+    if (!d_npairs || !d_seg_pairs) { set_error("d_npairs or d_seg_pairs is NULL"); return SBH_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    if (nl == 0) {
+        SBH_CUDA(cudaMemsetAsync(d_npairs, 0, sizeof(uint64_t), s));
+        SBH_CUDA(cudaMemsetAsync(d_seg_pairs, 0, (nseg + 1) * sizeof(uint64_t), s));
+        return SBH_OK;
+    }
+    if (!d_lkeys || !d_lptrs || !d_rkeys || !d_rptrs || (cap && (!d_out_l || !d_out_r))) {
+        set_error("null pointer");
+        return SBH_EINVAL;
+    }
+    Carver w(d_scratch);
+    uint32_t* rlo = w.take<uint32_t>(nl);
+    uint32_t* cnt = w.take<uint32_t>(nl);
+    uint64_t* bsum = w.take<uint64_t>(nblocks + 1);
+    uint64_t* segs = w.take<uint64_t>(3 * (size_t)nseg + 1);  // l_off (nseg + 1), r_start, r_len
+    SBH_CUDA(cudaMemcpyAsync(segs, l_off, (nseg + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    SBH_CUDA(cudaMemcpyAsync(segs + nseg + 1, r_start, nseg * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    SBH_CUDA(cudaMemcpyAsync(segs + 2 * nseg + 1, r_len, nseg * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    SBH_TIMED("join_seg_count", s,
+              join_seg_count_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lkeys, (uint32_t)nl, d_rkeys, segs,
+                                                                           segs + nseg + 1, segs + 2 * nseg + 1,
+                                                                           (uint32_t)nseg, rlo, cnt, bsum));
+    SBH_LAUNCHED();
+    SBH_TIMED("join_scan", s, scan_blocks_kernel<<<1, 1024, 0, s>>>(bsum, (uint32_t)nblocks, d_npairs));
+    SBH_LAUNCHED();
+    SBH_TIMED("join_seg_offsets", s,
+              join_seg_offsets_kernel<<<(unsigned)((nseg + 1 + 7) / 8), 256, 0, s>>>(segs, (uint32_t)nseg,
+                                                                                    (uint32_t)nl, cnt, bsum, d_npairs,
+                                                                                    d_seg_pairs));
+    SBH_LAUNCHED();
+    SBH_TIMED("join_emit", s, join_emit_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lptrs, (uint32_t)nl, d_rptrs, rlo, cnt, bsum, d_out_l,
+                                                             d_out_r, cap));
+    SBH_LAUNCHED();
+    return SBH_OK;
+}
 
 extern "C" int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, const uint64_t* d_rkeys,
                         const uint32_t* d_rptrs, uint64_t nr, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,

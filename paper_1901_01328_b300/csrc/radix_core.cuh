@@ -1120,6 +1120,32 @@ int chunked_passes(const Buffers& b, uint32_t n32, const SortScratch& sc, const 
     return SBH_OK;
 }
 
+// The chunked passes of one sort with one scatter geometry (TILE rows per
+// tile, THREADS threads per CTA): chunk geometry, first count with the
+// values' bits, plan, then per pass count -> scan -> scatter.
+template <typename ValueFn, int TILE, int THREADS>
+int chunked_sort(const Buffers& b, uint32_t n32, const SortScratch& sc, ValueFn value_of, int npos, int in_place,
+                 int bulk_ok, cudaStream_t s, const uint32_t* d_n, const std::string& n_up, const std::string& n_plan,
+                 const std::string& n_count, const std::string& n_scan, const std::string& n_scat) {
+    ChunkGeom g;
+    int rc = chunk_geometry<ValueFn, TILE, THREADS, false>(n32, &g);
+    if (rc) return rc;
+    DynN dn{};
+    if (d_n) dn = DynN{d_n, g.want, (uint32_t)TILE};
+    SBH_TIMED(n_up.c_str(), s,
+              first_count_kernel<ValueFn><<<d_n ? g.want : g.nchunks, 1024, 0, s>>>(
+                  b.in_k, n32, g.chunk, value_of, sc.chunk_hist, sc.vbits, dn));
+    SBH_LAUNCHED();
+    SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place));
+    SBH_LAUNCHED();
+    return chunked_passes<ValueFn, TILE, THREADS>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat, dn);
+}
+
+// Scatter geometries of the plain sort's chunked passes (the knob
+// SBH_KNOB_SCATTER_GEOM): 0 = 4096-row tiles, 512 threads (two CTAs per SM);
+// 1 = 2048 rows, 256 threads (four); 2 = 8192 rows, 1024 threads (one).
+constexpr int kScatterGeoms = 3;
+
 // Stable sort of (in_k, in_p) by value_of(key) into (out_k, out_p); the
 // positions at or above npos of the value are treated as zero.  With d_n
 // (device) the sort has *d_n <= n pairs, known only when it runs: it takes
@@ -1145,22 +1171,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
     const bool chunked = d_n || use_chunked(n);
-    ChunkGeom g;
-    DynN dn{};
-    if (chunked) {
-        // the chunked passes find their digit bases in the chunk counts; the
-        // plan needs only which digits vary: the first pass's counts and the
-        // values' OR and AND in one read
-        const int rc = chunk_geometry<ValueFn, 4096, 512, false>(n32, &g);
-        if (rc) return rc;
-        if (d_n) dn = DynN{d_n, g.want, 4096};
-        SBH_TIMED(n_up.c_str(), s,
-                  first_count_kernel<ValueFn><<<d_n ? g.want : g.nchunks, 1024, 0, s>>>(
-                      in_k, n32, g.chunk, value_of, sc.chunk_hist, sc.vbits, dn));
-        SBH_LAUNCHED();
-        SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place));
-        SBH_LAUNCHED();
-    } else {
+    if (!chunked) {
         const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
         SBH_TIMED(n_up.c_str(), s,
                   upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
@@ -1177,8 +1188,27 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
     const uint64_t ntiles = (n + kTile - 1) / kTile;
     if (chunked) {
-        const int rc =
-            chunked_passes<ValueFn, 4096, 512>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat, dn);
+        // the chunked passes find their digit bases in the chunk counts; the
+        // plan needs only which digits vary: the first pass's counts and the
+        // values' OR and AND in one read.  The plain sort's scatter geometry
+        // is a knob; derived values keep the default.
+        int rc;
+        const uint64_t geom = std::is_same<ValueFn, RadixValue>::value ? knob(SBH_KNOB_SCATTER_GEOM) : 0;
+        if constexpr (std::is_same<ValueFn, RadixValue>::value) {
+            if (geom == 1)
+                rc = chunked_sort<ValueFn, 2048, 256>(b, n32, sc, value_of, npos, in_place, bulk_ok, s, d_n, n_up,
+                                                      n_plan, n_count, n_scan, n_scat);
+            else if (geom == 2)
+                rc = chunked_sort<ValueFn, 8192, 1024>(b, n32, sc, value_of, npos, in_place, bulk_ok, s, d_n, n_up,
+                                                       n_plan, n_count, n_scan, n_scat);
+            else
+                rc = chunked_sort<ValueFn, 4096, 512>(b, n32, sc, value_of, npos, in_place, bulk_ok, s, d_n, n_up,
+                                                      n_plan, n_count, n_scan, n_scat);
+        } else {
+            (void)geom;
+            rc = chunked_sort<ValueFn, 4096, 512>(b, n32, sc, value_of, npos, in_place, bulk_ok, s, d_n, n_up, n_plan,
+                                                  n_count, n_scan, n_scat);
+        }
         if (rc) return rc;
     } else {
         auto kern = onesweep_kernel<ValueFn>;

@@ -14,8 +14,9 @@ batched_windows  per-key count, sum and top-K inside each of many tumbling
 sliding_join  the temporal join of two streams over sliding windows built
     from panes (Sec. 4.2 "Temporal Join" and "Windowing"): every pane of
     every stream is extracted (from page-locked host memory when the key
-    column lives there) and sorted once; each window merges its panes per
-    side and joins the two sides.
+    column lives there) and sorted once; the windows' panes are merged and
+    the two sides joined, for all windows at once (a few launches per merge
+    level and one segmented join) or window by window.
 ad_campaign_counts  a chain of operators over a 7-column ad-event stream
     (Extract -> Select -> KeySwap through a lookup table -> Sort -> Keyed
     count per window), the kind of pipeline the paper's declarative API
@@ -141,27 +142,93 @@ def _fit(buf, nbytes, dev):
 
 
 class JoinResults:
-    """Pairs of every window: window w's pairs are rows [w * cap, w * cap +
-    npairs[w]) of ptr_l / ptr_r, in (key, ptrL, ptrR) order."""
+    """Pairs of every window: window i's pairs are rows [begin[i], end[i]) of
+    ptr_l / ptr_r, in (key, ptrL, ptrR) order."""
 
-    def __init__(self, ptr_l, ptr_r, npairs, cap):
-        self.ptr_l, self.ptr_r, self.npairs, self.cap = ptr_l, ptr_r, npairs, cap
+    def __init__(self, ptr_l, ptr_r, begin, end):
+        self.ptr_l, self.ptr_r = ptr_l, ptr_r
+        self.begin, self.end = np.asarray(begin, np.int64), np.asarray(end, np.int64)
+        self.npairs = self.end - self.begin
 
-    def window(self, w):
-        b = w * self.cap
-        e = b + int(self.npairs[w])
+    def window(self, i):
+        b, e = int(self.begin[i]), int(self.end[i])
         return self.ptr_l[b:e].cpu().numpy(), self.ptr_r[b:e].cpu().numpy()
 
 
-def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, pair_cap=262_144, windows=None):
+def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, pair_cap=262_144, windows=None,
+                 schedule="batched"):
     """Equi-join of L and R inside every sliding window [w * stride, w *
     stride + window) of the first n_rows rows (ts = row index).  Key columns
-    may be device tensors or page-locked host tensors.  `windows` (an
-    iterable of window indices) restricts the windows joined; all panes are
-    still prepared.  Returns JoinResults."""
-    dev = torch.device("cuda")
+    may be device tensors or page-locked host tensors.  Returns (JoinResults,
+    the windows joined).
+
+    "batched" (when window / stride is a power of two and every window is
+    joined): each side's key column crosses the host link once; all its
+    panes are sorted by one sort of composite (pane, key) keys; the panes are
+    merged level by level, every merge of a level in one launch (run i of
+    level r + 1 merges runs i and i + 2^r of level r, so the last level holds
+    every window's merged KPA); one segmented join joins every window.
+    "loop" (or `windows` given: only those windows are joined): the panes are
+    sorted one by one and each window merges and joins on its own, at most
+    pair_cap pairs per window."""
+    per = window // stride
     if window % stride:
         raise ValueError("window must be a multiple of stride")
+    if schedule == "batched" and windows is None and per & (per - 1) == 0:
+        res = _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride)
+        if res is not None:
+            return res
+    return _sliding_join_loop(lkey_col, rkey_col, n_rows, window, stride, pair_cap, windows)
+
+
+def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride):
+    dev = torch.device("cuda")
+    per = window // stride
+    npanes = n_rows // stride
+    nwin = npanes - per + 1
+    if nwin <= 0:
+        return JoinResults(_u32(0, dev), _u32(0, dev), [], []), []
+    rows = npanes * stride
+    shift = 64 - sbh.window_bits(npanes)
+    offs = (torch.arange(npanes + 1, dtype=torch.int64, device=dev) * stride).view(torch.uint64)
+    sides = []
+    for col in (lkey_col, rkey_col):
+        keys, ptrs = _u64(rows, dev), _u32(rows, dev)
+        sbh.sbh_kpa_extract(col, 0, rows, keys, ptrs)  # over the host link once when col is host memory
+        ck, cp, key_or = _u64(rows, dev), _u32(rows, dev), _u64(1, dev)
+        sbh.sbh_kpa_extract_windows(keys, offs, 0, rows, ck, cp, key_or)
+        if shift < 64 and int(key_or.item()) >> shift:
+            return None  # a key uses the pane bits: the loop schedule instead
+        sbh.sbh_kpa_sort(ck[:rows], cp[:rows], ck[:rows], cp[:rows])  # every pane sorted, pane after pane
+        sbh.sbh_kpa_keyswap(cp[:rows], keys, ck)                         # the plain keys back
+        del keys, ptrs
+        run_k, run_p, run_len, nruns = ck, cp, stride, npanes
+        gap = 1
+        while gap < per:
+            nnext = nruns - gap
+            ok, op = _u64(nnext * 2 * run_len, dev), _u32(nnext * 2 * run_len, dev)
+            a_start = [i * run_len for i in range(nnext)]
+            b_start = [(i + gap) * run_len for i in range(nnext)]
+            lens = [run_len] * nnext
+            sbh.sbh_kpa_merge_segments((run_k, run_p), (run_k, run_p), a_start, lens, b_start, lens, ok, op)
+            run_k, run_p, run_len, nruns = ok, op, 2 * run_len, nnext
+            gap *= 2
+        sides.append((run_k, run_p))
+    (lk, lp), (rk, rp) = sides
+    l_off = [w * window for w in range(nwin + 1)]
+    r_start, r_len = l_off[:-1], [window] * nwin
+    npairs = _u64(1, dev)
+    seg = _u64(nwin + 1, dev)
+    scr = sbh.sbh_join_segments((lk, lp), l_off, (rk, rp), r_start, r_len, None, None, 0, npairs, seg)
+    total = int(npairs.item())
+    out_l, out_r = _u32(total, dev), _u32(total, dev)
+    sbh.sbh_join_segments((lk, lp), l_off, (rk, rp), r_start, r_len, out_l, out_r, total, npairs, seg, scratch=scr)
+    off = seg[: nwin + 1].cpu().numpy().astype(np.int64)
+    return JoinResults(out_l, out_r, off[:-1], off[1:]), list(range(nwin))
+
+
+def _sliding_join_loop(lkey_col, rkey_col, n_rows, window, stride, pair_cap, windows):
+    dev = torch.device("cuda")
     per = window // stride
     npanes = n_rows // stride
     nwin = max(0, npanes - per + 1)
@@ -188,11 +255,12 @@ def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, p
             merged.append((mk, mp))
         join_scr = sbh.sbh_join(*merged[0], *merged[1], out_l[i * pair_cap:], out_r[i * pair_cap:], pair_cap,
                                 npairs[i:i + 1], scratch=_fit(join_scr, sbh.join_scratch_bytes(window, window), dev))
-    counts = npairs.cpu().numpy()[:len(wl)]
+    counts = npairs.cpu().numpy()[:len(wl)].astype(np.int64)
     if len(wl) and counts.max() > pair_cap:
         over = [w for w, c in zip(wl, counts) if c > pair_cap]
         raise RuntimeError(f"windows {over[:4]} have more than pair_cap={pair_cap} pairs; raise pair_cap")
-    return JoinResults(out_l, out_r, counts, pair_cap), wl
+    begin = np.arange(len(wl), dtype=np.int64) * pair_cap
+    return JoinResults(out_l, out_r, begin, begin + counts), wl
 
 
 def ad_campaign_counts(cols, campaign_of_ad, window_ns, view=0, trace=None):

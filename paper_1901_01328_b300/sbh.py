@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(HERE, "libsbh.so")
 
 SBH_OK, SBH_EINVAL, SBH_ENOSPACE, SBH_ETIMEOUT, SBH_ECUDA = 0, 1, 2, 3, 4
 SBH_FAULT_NONE, SBH_FAULT_SKIP_PUBLISH = 0, 1
-KNOB_SORT_CHUNKED_MIN, KNOB_MERGE_SEARCH_MIN_TILES = 0, 1
+KNOB_SORT_CHUNKED_MIN, KNOB_MERGE_SEARCH_MIN_TILES, KNOB_SCATTER_GEOM = 0, 1, 2
+SCATTER_GEOMS = {0: (4096, 512), 1: (2048, 256), 2: (8192, 1024)}  # tile rows, CTA threads
 TOPK_PAD_VAL = 0
 TOPK_PAD_PTR = 0xFFFFFFFF
 TOPK_MAX_K = 8
@@ -80,6 +81,8 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_sort_learned": ([vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_partition": ([vp, vp, u64, vp, u64, vp, vp, vp, vp, sz, vp], i32),
         "sbh_copy_counted": ([vp, vp, i32, vp, u64, u64, vp], i32),
+        "sbh_kpa_merge_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
+        "sbh_join_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -98,7 +101,8 @@ EXPORTED = ("sbh_version", "sbh_last_error", "sbh_sync_status", "sbh_set_spin_li
             "sbh_group_reduce_noalloc", "sbh_mlp_forward", "sbh_mlp_grad", "sbh_learned_train",
             "sbh_kpa_sort_learned", "sbh_kpa_materialize", "sbh_kpa_keyswap", "sbh_kpa_keyswap_lookup",
             "sbh_kpa_select",
-            "sbh_median_unique", "sbh_kpa_partition", "sbh_copy_counted",
+            "sbh_median_unique", "sbh_kpa_partition", "sbh_copy_counted", "sbh_kpa_merge_segments",
+            "sbh_join_segments",
             "sbh_topk", "sbh_join")
 
 
@@ -272,6 +276,35 @@ def sbh_kpa_merge(runs, keys_out, ptrs_out, stream=None):
     args = (r, ctypes.cast(kp, ctypes.c_void_p), ctypes.cast(pp, ctypes.c_void_p), ctypes.cast(ln, ctypes.c_void_p),
             _p(keys_out), _p(ptrs_out))
     _scratch(_lib.sbh_kpa_merge, args, (_stream(stream),), "sbh_kpa_merge", keys_out.device)
+
+
+def _host_u64(values):
+    a = (ctypes.c_uint64 * max(1, len(values)))(*[int(v) for v in values])
+    return a, ctypes.cast(a, ctypes.c_void_p)
+
+
+def sbh_kpa_merge_segments(a, b, a_start, a_len, b_start, b_len, keys_out, ptrs_out, stream=None):
+    """a, b: (keys, ptrs) device tensors; the four segment lists are host
+    sequences.  Segment g's merge lands after those of segments < g."""
+    nseg = len(a_start)
+    hold = [_host_u64(x) for x in (a_start, a_len, b_start, b_len)]
+    args = (nseg, _p(a[0]), _p(a[1]), _p(b[0]), _p(b[1]), *[h[1] for h in hold], _p(keys_out), _p(ptrs_out))
+    _scratch(_lib.sbh_kpa_merge_segments, args, (_stream(stream),), "sbh_kpa_merge_segments", keys_out.device)
+
+
+def sbh_join_segments(L, l_off, R, r_start, r_len, out_l, out_r, cap, npairs, seg_pairs, scratch=None,
+                      stream=None):
+    """L, R: (keys, ptrs) device tensors; l_off (nseg + 1), r_start, r_len:
+    host sequences; seg_pairs: device uint64 tensor of nseg + 1 entries."""
+    nseg = len(r_start)
+    hold = [_host_u64(x) for x in (l_off, r_start, r_len)]
+    args = (nseg, _p(L[0]), _p(L[1]), hold[0][1], _p(R[0]), _p(R[1]), hold[1][1], hold[2][1], _p(out_l), _p(out_r),
+            cap, _p(npairs), _p(seg_pairs))
+    if scratch is None:
+        return _scratch(_lib.sbh_join_segments, args, (_stream(stream),), "sbh_join_segments", npairs.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_join_segments(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_join_segments")
+    return scratch
 
 
 def sbh_group_reduce(keys, ptrs, vals, out_keys, out_counts, out_sums, cap, nkeys, scratch=None, stream=None):

@@ -20,6 +20,7 @@ def A():
     yield autotune
     sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 23)
     sbh.set_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES, 2047)
+    sbh.set_knob(sbh.KNOB_SCATTER_GEOM, 0)
 
 
 def test_tuning_sets_knobs_from_measurements(A, tmp_path):
@@ -32,7 +33,7 @@ def test_tuning_sets_knobs_from_measurements(A, tmp_path):
     assert sbh.get_knob(sbh.KNOB_MERGE_SEARCH_MIN_TILES) == m["value"]
     # a cache file round trip
     cache = str(tmp_path / "knobs.json")
-    saved = A.autotune(cache)
+    saved = A.autotune(cache, quick=True)
     sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 7)
     assert A.autotune(cache) == saved and sbh.get_knob(sbh.KNOB_SORT_CHUNKED_MIN) == saved["SBH_KNOB_SORT_CHUNKED_MIN"]
 
@@ -62,3 +63,31 @@ def test_batched_schedule_choice(A):
     b = gen.batched_windows(32, 8, size_hi=50_000)
     choice, t = A.batched_schedule(cuda(b["keys"]), cuda(b["vals"]), b["offsets"], sample_windows=16)
     assert choice in ("batched", "loop") and t[choice] == min(t.values())
+
+
+def test_scatter_geometry_tuning_and_every_geometry_is_exact(A):
+    from paper_1901_01328_b300 import sbh
+    r = A.tune_scatter_geometry(sizes=(1 << 22,))
+    assert r["value"] in sbh.SCATTER_GEOMS and sbh.get_knob(sbh.KNOB_SCATTER_GEOM) == r["value"]
+    assert r["timings_ms"][1 << 22][r["value"]] == min(r["timings_ms"][1 << 22].values())
+    with pytest.raises(sbh.SbhError):
+        sbh.set_knob(sbh.KNOB_SCATTER_GEOM, 3)
+    old = sbh.get_knob(sbh.KNOB_SORT_CHUNKED_MIN)
+    sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, 1 << 20)  # the chunked passes from 2^20 pairs
+    try:
+        n = (1 << 21) + 4097  # ragged last tile in every geometry
+        for kind, col in (("mixed", gen.mixed_keys(n, seed=33)), ("uniform20", gen.uniform(33, 1, n, 0, 1 << 20,
+                                                                                              np.uint64))):
+            ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+            for geom in sbh.SCATTER_GEOMS:
+                sbh.set_knob(sbh.KNOB_SCATTER_GEOM, geom)
+                sk, sp = sbh.sort(*sbh.extract(cuda(col), 0, n))
+                assert same(sk, ok) and same(sp, op), (kind, geom)
+            # in place
+            sbh.set_knob(sbh.KNOB_SCATTER_GEOM, 2)
+            k, p = sbh.extract(cuda(col), 0, n)
+            sbh.sort(k, p, out=(k, p))
+            assert same(k, ok) and same(p, op)
+    finally:
+        sbh.set_knob(sbh.KNOB_SORT_CHUNKED_MIN, old)
+        sbh.set_knob(sbh.KNOB_SCATTER_GEOM, 0)

@@ -147,3 +147,89 @@ def test_keyswap_lookup_misses(P):
     miss = torch.zeros(1, dtype=torch.uint64, device="cuda")
     sbh.sbh_kpa_keyswap_lookup(cuda(ptrs), cuda(col), cuda(table), out, miss)
     assert out.cpu().numpy().tolist() == [11, 2**64 - 1, 12, 15, 10] and int(miss.item()) == 1
+
+
+def test_sliding_join_batched_equals_loop_schedule(P):
+    s = gen.join_streams(2_000_000, key_space=1 << 18)
+    lcol, rcol = s["L"]["keys"], s["R"]["keys"]
+    a, wa = P.sliding_join(cuda(lcol), cuda(rcol), 2_000_000, window=500_000, stride=125_000, schedule="batched")
+    b, wb = P.sliding_join(cuda(lcol), cuda(rcol), 2_000_000, window=500_000, stride=125_000, schedule="loop",
+                           pair_cap=1 << 21)
+    assert wa == wb == list(range(13))
+    for i in range(13):
+        ga, gb = a.window(i), b.window(i)
+        assert np.array_equal(ga[0], gb[0]) and np.array_equal(ga[1], gb[1])
+    _check_join(a, 12, 12, lcol, rcol, 500_000, 125_000)
+
+
+def _sorted_runs(col, starts, lens):
+    out = []
+    for st, ln in zip(starts, lens):
+        out.append(oracle.sort(*oracle.extract(col, st, ln)))
+    return out
+
+
+def test_merge_segments_parity():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import sbh
+    # A and B: concatenations of sorted runs of uneven length (empty ones,
+    # ragged tails, one long run), merged pairwise, in a shuffled order of
+    # segments that also reuse runs
+    col = gen.mixed_keys(3_000_000, seed=41)
+    lens = [0, 1, 2047, 2048, 2049, 100_003, 5, 700_000, 0, 31_111]
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    runs = _sorted_runs(col, starts, lens)
+    ak = np.concatenate([r[0] for r in runs]); ap = np.concatenate([r[1] for r in runs])
+    segs = [(0, 1), (2, 3), (4, 5), (7, 6), (9, 3), (8, 8), (5, 5), (1, 7)]
+    a_start = [int(starts[i]) for i, _ in segs]; a_len = [lens[i] for i, _ in segs]
+    b_start = [int(starts[j]) for _, j in segs]; b_len = [lens[j] for _, j in segs]
+    total = sum(a_len) + sum(b_len)
+    ok = torch.empty(total, dtype=torch.uint64, device="cuda")
+    op = torch.empty(total, dtype=torch.uint32, device="cuda")
+    A = (cuda(ak), cuda(ap))
+    sbh.sbh_kpa_merge_segments(A, A, a_start, a_len, b_start, b_len, ok, op)
+    gk, gp = ok.cpu().numpy(), op.cpu().numpy()
+    o = 0
+    for (i, j), la, lb in zip(segs, a_len, b_len):
+        ek, ep = oracle.merge([runs[i], runs[j]])
+        assert np.array_equal(gk[o:o + la + lb], ek) and np.array_equal(gp[o:o + la + lb], ep), (i, j)
+        o += la + lb
+
+
+def test_join_segments_parity():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_01328_b300 import sbh
+    lcol = gen.uniform(42, 1, 900_000, 0, 1 << 12, np.uint64)
+    rcol = gen.uniform(42, 2, 800_000, 0, 1 << 12, np.uint64)
+    l_lens = [0, 5, 4097, 300_000, 1, 595_897]
+    r_specs = [(0, 10), (0, 800_000), (100, 4096), (0, 0), (700_000, 100_000), (250_000, 300_000)]  # overlapping
+    l_off = np.concatenate([[0], np.cumsum(l_lens)]).astype(np.int64)
+    Lr = _sorted_runs(lcol, l_off[:-1], l_lens)
+    Rr = _sorted_runs(rcol, [a for a, _ in r_specs], [b for _, b in r_specs])
+    lk = np.concatenate([r[0] for r in Lr]); lp = np.concatenate([r[1] for r in Lr])
+    # R segments are sorted runs laid out where their specs say (overlapping specs share rows)
+    rk, rp = oracle.sort(*oracle.extract(rcol, 0, 800_000))
+    r_start, r_len = [], []
+    rk_all, rp_all = [rk], [rp]
+    base = 800_000
+    for (a, b), run in zip(r_specs, Rr):
+        r_start.append(base); r_len.append(b)
+        rk_all.append(run[0]); rp_all.append(run[1])
+        base += b
+    RK, RP = np.concatenate(rk_all), np.concatenate(rp_all)
+    npairs = torch.empty(1, dtype=torch.uint64, device="cuda")
+    seg = torch.empty(len(l_lens) + 1, dtype=torch.uint64, device="cuda")
+    L, R = (cuda(lk), cuda(lp)), (cuda(RK), cuda(RP))
+    scr = sbh.sbh_join_segments(L, l_off, R, r_start, r_len, None, None, 0, npairs, seg)
+    total = int(npairs.item())
+    ol = torch.empty(max(1, total), dtype=torch.uint32, device="cuda")
+    orr = torch.empty(max(1, total), dtype=torch.uint32, device="cuda")
+    sbh.sbh_join_segments(L, l_off, R, r_start, r_len, ol, orr, total, npairs, seg, scratch=scr)
+    so = seg.cpu().numpy().astype(np.int64)
+    gl, gr = ol.cpu().numpy(), orr.cpu().numpy()
+    assert so[0] == 0 and so[-1] == total
+    for g in range(len(l_lens)):
+        el, er = oracle.join(Lr[g][0], Lr[g][1], Rr[g][0], Rr[g][1])
+        assert np.array_equal(gl[so[g]:so[g + 1]], el) and np.array_equal(gr[so[g]:so[g + 1]], er), g
