@@ -310,9 +310,54 @@ def run_gpu(args):
 
     verified = {"mixed_keys": verify(col)}
 
+    # ---- the step as one CUDA graph: every call of the step only queues work
+    # on the stream (no host synchronisation), so it is captured once and
+    # replayed; the replay's output is checked against the eager step's
+    graphs = {}
+    graph_note = None
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            fn()  # allocations the step makes happen before the capture
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize(dev)
+        return g
+
+    if not args.no_graph:
+        try:
+            for name, fn in (("learned", step_learned), ("plain", step_plain)):
+                step_plain()
+                m = int(nkeys.item())
+                ref = (sk.clone(), sp.clone(), out_keys[:m].clone(), out_counts[:m].clone())
+                graphs[name] = capture(fn)
+                sk.zero_()
+                sp.zero_()
+                out_counts.zero_()
+                graphs[name].replay()
+                torch.cuda.synchronize(dev)
+                ok = (int(nkeys.item()) == m and torch.equal(sk, ref[0]) and torch.equal(sp, ref[1])
+                      and torch.equal(out_keys[:m], ref[2]) and torch.equal(out_counts[:m], ref[3]))
+                del ref
+                if not ok:
+                    raise RuntimeError(f"the replayed {name} graph differs from the eager step")
+                verified[f"{name}_graph"] = True
+        except Exception as e:  # capture refused: time the eager steps
+            graphs = {}
+            graph_note = f"eager (capture failed: {type(e).__name__}: {str(e)[:160]})"
+        torch.cuda.empty_cache()
+    timed_learned = (lambda: graphs["learned"].replay()) if "learned" in graphs else step_learned
+    timed_plain = (lambda: graphs["plain"].replay()) if "plain" in graphs else step_plain
+    headline = timed_plain if args.sort == "radix" else timed_learned
+
     # ---- device-resident timing of the headline step
     with Clocks(local) as clk:
-        ms = timed(step, args.steps)
+        ms = timed(headline, args.steps)
     clocks = clk.summary()
     value = whole_job_rate(args.steps, n, ws, ms)
     assert sbh.sync_status() == sbh.SBH_OK
@@ -320,9 +365,10 @@ def run_gpu(args):
 
     # ---- the other sort path on the same window, for the comparison
     other = step_plain if step is step_learned else step_learned
+    timed_other = timed_plain if step is step_learned else timed_learned
     for _ in range(2):
-        other()
-    ms_other = timed(other, args.steps)
+        timed_other()
+    ms_other = timed(timed_other, args.steps)
     if other is step_learned:
         stats = sbh.stats_dict(stats_d)
 
@@ -346,7 +392,8 @@ def run_gpu(args):
             "learned_ms_per_step": ms_l2 / args.steps, "radix_ms_per_step": ms_p2 / args.steps,
             "speedup": ms_p2 / ms_l2, "learned_stats": st2, "overflow_row_rate": st2.get("overflow_rows", 0) / n,
             "stages_ms": {k: sum(v) / args.steps for k, v in per2.items() if sum(v) / args.steps >= 0.05},
-            "text": "the headline window with each Zipf rank r replaced by mix64(r) (SplitMix64 output function)"}
+            "text": "the headline window with each Zipf rank r replaced by mix64(r) (SplitMix64 output function); "
+                    "both steps launched eagerly"}
         del col2
         # a library sort for context: PyTorch's stable sort of the same keys, mapped order-preservingly
         # to int64 (top bit flipped), with int64 indices (16 B per pair against the KPA's 12)
@@ -414,6 +461,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "text": WORKLOAD_TEXT, "rows_per_gpu": n, "sort": args.sort,
+                       "launch": ("one CUDA graph per step (captured once, replayed; output checked against the "
+                                  "eager step)" if graphs else (graph_note or "eager")),
                        "distinct_keys": n_unique, "l2": "inputs larger than L2 (3 GB KPA per step)",
                        "parallelism": f"replicas{ws}", "train": TRAIN, "sample_stride": SAMPLE_STRIDE},
             "verified": all(verified.values()),
@@ -936,6 +985,7 @@ def main():
     ap.add_argument("--rows", type=int, default=N_FULL)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the eager steps instead of one CUDA graph per step")
     ap.add_argument("--sort", default="learned", choices=["learned", "radix"])
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--serve-windows", type=int, default=62,

@@ -237,3 +237,49 @@ def test_learned_sort_headline_window_256m(S, hashed):
         kk, pv = sk[int(lp[i])], int(lp[i])
         below = int((sk < kk).sum()) + int(((sk == kk) & (rows < pv)).sum())
         assert below == int(i)
+
+
+def test_learned_step_replays_as_a_cuda_graph(S):
+    # extract + training + learned sort + per-key count queue their work
+    # without host synchronisation, so the whole step is captured once and
+    # replayed; every replay equals the plain sort and the eager count
+    n = 3_000_017
+    col = cuda(gen.mixed_keys(n, seed=17))
+    keys = torch.empty(n, dtype=torch.uint64, device="cuda")
+    ptrs = torch.empty(n, dtype=torch.uint32, device="cuda")
+    samples = torch.empty((n + 99) // 100, dtype=torch.uint64, device="cuda")
+    model = torch.zeros(S.LEARNED_MODEL_BYTES, dtype=torch.uint8, device="cuda")
+    sk, sp = torch.empty_like(keys), torch.empty_like(ptrs)
+    ok_, oc_ = torch.empty_like(keys), torch.empty_like(keys)
+    nk = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    st = torch.zeros(len(S.LEARNED_STATS), dtype=torch.uint64, device="cuda")
+    lscr = torch.empty(S.sort_learned_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    rscr = torch.empty(S.group_reduce_scratch_bytes(n, 8), dtype=torch.uint8, device="cuda")
+    tscr = {}
+
+    def step():
+        S.sbh_kpa_extract(col, 0, n, keys, ptrs, None, samples, 100)
+        tscr["t"] = S.sbh_learned_train(samples, n, None, 40, 4096, 3e-4, model)
+        S.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, st, scratch=lscr)
+        S.sbh_group_reduce(sk, None, None, ok_, oc_, None, n, nk, scratch=rscr)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    pk, pp = S.sort(*S.extract(col, 0, n))
+    ek, ec, _ = S.group_reduce(pk, pp, None)
+    for _ in range(2):
+        sk.zero_()
+        oc_.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(sk, pk) and torch.equal(sp, pp)
+        m = int(nk.item())
+        assert m == ek.numel() and torch.equal(ok_[:m], ek) and torch.equal(oc_[:m], ec)
+    assert S.sync_status() == S.SBH_OK
