@@ -1790,7 +1790,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.zero_bytes = c.off - z0;
     t.ck = c.take<uint64_t>(n);
     t.cp = c.take<uint32_t>(n);
-    t.sort_scratch = c.take<char>(std::max(sort_carve(nullptr, n).total, carry_carve(nullptr, n).total));
+    t.sort_scratch = c.take<char>(std::max(sort_carve(nullptr, n, true).total, carry_carve(nullptr, n).total));
     t.total = c.bytes();
     return t;
 }

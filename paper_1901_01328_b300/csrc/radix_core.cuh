@@ -82,10 +82,16 @@ struct Buffers {
 // from it, the same way the host does for a known size, with G the number of
 // chunks launched for the largest size the caller allows.  d_n == nullptr:
 // the size and geometry are the launch arguments.
+// Both the onesweep and the chunked kernels are queued for such a sort; each
+// returns at once unless the size selects its path (chunked from thr pairs).
 struct DynN {
     const uint32_t* d_n = nullptr;
     uint32_t G = 0;
     uint32_t tile = 0;
+    uint32_t thr = 0;
+    __device__ __forceinline__ bool skip(bool chunked_path) const {
+        return d_n && ((*d_n >= thr) != chunked_path);
+    }
     __device__ __forceinline__ void apply(uint32_t& n, uint32_t& chunk, uint32_t& nchunks) const {
         if (!d_n) return;
         n = *d_n;
@@ -129,7 +135,10 @@ struct RunCounter {
 // npos are counted as all-zero (constant, so their passes are skipped).
 template <typename ValueFn>
 __global__ void __launch_bounds__(256) upsweep_kernel(const uint64_t* __restrict__ keys, uint32_t n,
-                                                      uint32_t* __restrict__ ghist, ValueFn value_of, int npos) {
+                                                      uint32_t* __restrict__ ghist, ValueFn value_of, int npos,
+                                                      DynN dn = DynN{}) {
+    if (dn.skip(false)) return;
+    if (dn.d_n) n = *dn.d_n;
     __shared__ uint32_t h[kPositions * kRadix];
     for (int i = threadIdx.x; i < kPositions * kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -168,6 +177,7 @@ template <typename ValueFn>
 __global__ void __launch_bounds__(1024)
 first_count_kernel(const uint64_t* __restrict__ keys, uint32_t n, uint32_t chunk, ValueFn value_of,
                    uint32_t* __restrict__ chunk_hist, unsigned long long* __restrict__ vbits, DynN dn = DynN{}) {
+    if (dn.skip(true)) return;
     __shared__ uint32_t h[kRadix];
     uint32_t nchunks = gridDim.x;
     dn.apply(n, chunk, nchunks);
@@ -254,8 +264,8 @@ __device__ void fill_plan(const int* active, int in_place, Plan* __restrict__ pl
 }
 
 __global__ void plan_bits_kernel(const unsigned long long* __restrict__ vbits, int npos, Plan* __restrict__ plan,
-                                 int in_place) {
-    if (threadIdx.x != 0) return;
+                                 int in_place, DynN dn = DynN{}) {
+    if (threadIdx.x != 0 || dn.skip(true)) return;
     const unsigned long long varying = vbits[0] & vbits[1];
     int active[kPositions];
     for (int p = 0; p < kPositions; ++p) active[p] = p < npos && ((varying >> (p * kRadixBits)) & (kRadix - 1)) != 0;
@@ -265,7 +275,9 @@ __global__ void plan_bits_kernel(const unsigned long long* __restrict__ vbits, i
 // ------------------------------------------------------------------ plan
 __global__ void __launch_bounds__(kRadix) plan_kernel(const uint32_t* __restrict__ ghist, uint32_t n,
                                                       uint32_t* __restrict__ gbase, Plan* __restrict__ plan,
-                                                      int in_place) {
+                                                      int in_place, DynN dn = DynN{}) {
+    if (dn.skip(false)) return;
+    if (dn.d_n) n = *dn.d_n;
     __shared__ uint32_t warp_sums[kRadix / 32];
     __shared__ int s_active[kPositions];
     const int d = threadIdx.x;
@@ -323,8 +335,11 @@ template <typename ValueFn>
 __global__ void __launch_bounds__(kThreads, 2)
 onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, const uint32_t* __restrict__ gbase,
                 uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter, uint32_t spin_limit,
-                int skip_publish_tile0, uint32_t* __restrict__ status, ValueFn value_of, int bulk_ok) {
+                int skip_publish_tile0, uint32_t* __restrict__ status, ValueFn value_of, int bulk_ok,
+                DynN dn = DynN{}) {
     const DigitOf<ValueFn> digit_of{value_of, pos * kRadixBits};
+    if (dn.skip(false)) return;
+    if (dn.d_n) n = *dn.d_n;
     if (!plan->active[pos]) return;
     const int src = plan->src[pos], dst = plan->dst[pos];
     const uint64_t* __restrict__ in_k = buf.keys(src);
@@ -554,7 +569,7 @@ template <typename ValueFn>
 __global__ void __launch_bounds__(1024)
 chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                    uint32_t* __restrict__ chunk_hist, ValueFn value_of, DynN dn = DynN{}) {
-    if (!plan->active[pos]) return;
+    if (dn.skip(true) || !plan->active[pos]) return;
     uint32_t nchunks = gridDim.x;
     dn.apply(n, chunk, nchunks);
     if (blockIdx.x >= nchunks) return;
@@ -604,7 +619,7 @@ chunk_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ pl
 __global__ void __launch_bounds__(1024)
 chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __restrict__ chunk_hist, uint32_t nchunks,
                   const uint32_t* __restrict__ gbase, uint32_t* __restrict__ chunk_base, DynN dn = DynN{}) {
-    if (!plan->active[pos]) return;
+    if (dn.skip(true) || !plan->active[pos]) return;
     {
         uint32_t n = 0, chunk = 0;
         dn.apply(n, chunk, nchunks);
@@ -707,7 +722,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     constexpr int kIt = TILE / THREADS;
     static_assert(TILE % THREADS == 0 && THREADS % 128 == 0 && THREADS <= 1024, "tile geometry");
     static_assert(TILE < 65536, "16-bit counters");
-    if (!plan->active[pos]) return;
+    if (dn.skip(true) || !plan->active[pos]) return;
     const int shift = pos * kRadixBits;
     const DigitOf<ValueFn> digit_of{value_of, shift};
     const int src = plan->src[pos], dst = plan->dst[pos];
@@ -1069,11 +1084,14 @@ struct SortScratch {
     size_t total;
 };
 
-inline SortScratch sort_carve(void* scratch, uint64_t n) {
+// dyn: a sort sized on the device (up to n pairs), whose onesweep path needs
+// look-back records for sizes below the chunked threshold.
+inline SortScratch sort_carve(void* scratch, uint64_t n, bool dyn = false) {
     Carver c(scratch);
     SortScratch s;
-    const bool chunked = use_chunked(n);
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    const bool chunked = use_chunked(n) && !dyn;
+    const uint64_t lb_rows = dyn ? min_u64(n, knob(SBH_KNOB_SORT_CHUNKED_MIN)) : n;
+    const uint64_t ntiles = (lb_rows + kTile - 1) / kTile;
     s.tmp_k = c.take<uint64_t>(n);
     s.tmp_p = c.take<uint32_t>(n);
     s.gbase = c.take<uint32_t>(kPositions * kRadix);
@@ -1131,12 +1149,12 @@ int chunked_sort(const Buffers& b, uint32_t n32, const SortScratch& sc, ValueFn 
     int rc = chunk_geometry<ValueFn, TILE, THREADS, false>(n32, &g);
     if (rc) return rc;
     DynN dn{};
-    if (d_n) dn = DynN{d_n, g.want, (uint32_t)TILE};
+    if (d_n) dn = DynN{d_n, g.want, (uint32_t)TILE, (uint32_t)min_u64(knob(SBH_KNOB_SORT_CHUNKED_MIN), 0xFFFFFFFFull)};
     SBH_TIMED(n_up.c_str(), s,
               first_count_kernel<ValueFn><<<d_n ? g.want : g.nchunks, 1024, 0, s>>>(
                   b.in_k, n32, g.chunk, value_of, sc.chunk_hist, sc.vbits, dn));
     SBH_LAUNCHED();
-    SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place));
+    SBH_TIMED(n_plan.c_str(), s, plan_bits_kernel<<<1, 32, 0, s>>>(sc.vbits, npos, sc.plan, in_place, dn));
     SBH_LAUNCHED();
     return chunked_passes<ValueFn, TILE, THREADS>(b, n32, sc, g, value_of, bulk_ok, s, n_count, n_scan, n_scat, dn);
 }
@@ -1148,10 +1166,11 @@ constexpr int kScatterGeoms = 3;
 
 // Stable sort of (in_k, in_p) by value_of(key) into (out_k, out_p); the
 // positions at or above npos of the value are treated as zero.  With d_n
-// (device) the sort has *d_n <= n pairs, known only when it runs: it takes
-// the chunked passes, launched for n pairs, with every kernel reading the
-// size and deriving its chunk geometry on the device (no host
-// synchronisation).
+// (device) the sort has *d_n <= n pairs, known only when it runs: both
+// paths are queued (the onesweep kernels sized for the chunked threshold,
+// the chunked ones for n pairs), every kernel reads the size, the chunked
+// ones derive their chunk geometry from it, and the kernels of the path the
+// size does not select return at once (no host synchronisation).
 template <typename ValueFn>
 int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
                   void* scratch, cudaStream_t s, ValueFn value_of, int npos, const char* tag = "sort",
@@ -1166,17 +1185,26 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
         set_error("an in-place sort needs both keys and ptrs aliased");
         return SBH_EINVAL;
     }
-    SortScratch sc = sort_carve(scratch, n);
+    SortScratch sc = sort_carve(scratch, n, d_n != nullptr);
     SBH_CUDA(cudaMemsetAsync(sc.zero_begin, 0, sc.zero_bytes, s));
     const int sms = num_sms();
     const uint32_t n32 = static_cast<uint32_t>(n);
-    const bool chunked = d_n || use_chunked(n);
-    if (!chunked) {
-        const unsigned up_blocks = (unsigned)min_u64((n + 1023) / 1024, (uint64_t)sms * 8);
+    // which kernels are queued: a known size takes one path; a size known
+    // only on the device queues the onesweep kernels for sizes below the
+    // chunked threshold and the chunked ones from it, and each returns at
+    // once unless the size selects it
+    const uint64_t thr = knob(SBH_KNOB_SORT_CHUNKED_MIN);
+    const bool run_one = d_n ? thr > 0 : !use_chunked(n);
+    const bool run_chunked = d_n ? n >= thr : use_chunked(n);
+    const DynN dn_one = d_n ? DynN{d_n, 0, 0, (uint32_t)min_u64(thr, 0xFFFFFFFFull)} : DynN{};
+    const uint64_t n_osw = d_n ? min_u64(n, thr) : n;  // the largest size the onesweep kernels see
+    if (run_one) {
+        const unsigned up_blocks = (unsigned)min_u64((n_osw + 1023) / 1024, (uint64_t)sms * 8);
         SBH_TIMED(n_up.c_str(), s,
-                  upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos));
+                  upsweep_kernel<ValueFn><<<up_blocks, 256, 0, s>>>(in_k, n32, sc.hist, value_of, npos, dn_one));
         SBH_LAUNCHED();
-        SBH_TIMED(n_plan.c_str(), s, plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place));
+        SBH_TIMED(n_plan.c_str(), s,
+                  plan_kernel<<<1, kRadix, 0, s>>>(sc.hist, n32, sc.gbase, sc.plan, in_place, dn_one));
         SBH_LAUNCHED();
     }
     Buffers b{in_k, in_p, sc.tmp_k, sc.tmp_p, out_k, out_p};
@@ -1186,8 +1214,8 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
     // bulk copies need 16-byte aligned tile starts in every buffer a pass may read
     const int bulk_ok = ((reinterpret_cast<uintptr_t>(in_k) | reinterpret_cast<uintptr_t>(in_p) |
                           reinterpret_cast<uintptr_t>(out_k) | reinterpret_cast<uintptr_t>(out_p)) & 15) == 0;
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    if (chunked) {
+    const uint64_t ntiles = (n_osw + kTile - 1) / kTile;
+    if (run_chunked) {
         // the chunked passes find their digit bases in the chunk counts; the
         // plan needs only which digits vary: the first pass's counts and the
         // values' OR and AND in one read.  The plain sort's scatter geometry
@@ -1210,7 +1238,8 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                                                   n_count, n_scan, n_scat);
         }
         if (rc) return rc;
-    } else {
+    }
+    if (run_one) {
         auto kern = onesweep_kernel<ValueFn>;
         SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
@@ -1222,7 +1251,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
             SBH_TIMED(n_one.c_str(), s,
                       kern<<<grid, kThreads, smem, s>>>(b, n32, pos, sc.plan, sc.gbase, sc.lookback, sc.counters, limit,
                                                         fault == SBH_FAULT_SKIP_PUBLISH ? 1 : 0, status, value_of,
-                                                        bulk_ok));
+                                                        bulk_ok, dn_one));
             SBH_LAUNCHED();
         }
     }

@@ -283,3 +283,23 @@ def test_learned_step_replays_as_a_cuda_graph(S):
         m = int(nk.item())
         assert m == ek.numel() and torch.equal(ok_[:m], ek) and torch.equal(oc_[:m], ec)
     assert S.sync_status() == S.SBH_OK
+
+
+@pytest.mark.parametrize("thr", [0, 1 << 16, 1 << 23, 1 << 40])
+def test_overflow_sort_takes_either_path_on_the_device(S, thr):
+    # the rows of oversized buckets are sorted with their count known only on
+    # the device: below the chunked threshold by the onesweep kernels, from
+    # it by the chunked ones (an untrained network overflows ~half the rows)
+    n = 3_000_017
+    col = gen.mixed_keys(n, seed=19)
+    untrained, _ = S.learned_train(cuda(col[::100].copy()), n, cuda(gen.mlp_init()), steps=0, batch=4096, lr=1e-3)
+    old = S.get_knob(S.KNOB_SORT_CHUNKED_MIN)
+    S.set_knob(S.KNOB_SORT_CHUNKED_MIN, thr)
+    try:
+        keys, ptrs = S.extract(cuda(col), 0, n)
+        sk, sp, st = S.sort_learned(keys, ptrs, untrained)
+    finally:
+        S.set_knob(S.KNOB_SORT_CHUNKED_MIN, old)
+    assert st["overflow_rows"] > 1 << 16
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
