@@ -46,7 +46,7 @@ CPU_SAMPLE = 4_000_000
 # scatter the mean of its two passes).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 26.35, "sort_scatter": 24.57}
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 26.41, "sort_scatter": 24.55}
 
 
 def _dist():
@@ -421,10 +421,10 @@ def run_gpu(args):
     algo_bytes = {"sort_scatter": PAIR_BYTES * 2 * n, "sort_onesweep": PAIR_BYTES * 2 * n,
                   "sort_count": 8 * n, "extract": (8 + PAIR_BYTES) * n, "sort_upsweep": 8 * n,
                   "keyed_tile_agg": 8 * n, "keyed_emit": 8 * n + 16 * n_unique,
-                  # per launch, the mean of the two passes: the first reads the 2-byte ids and
-                  # writes their high bytes (27 B/row), the last reads those and records bucket
-                  # starts (25 B/row)
-                  "learned_ids_scatter": 26 * n, "learned_ids_count": 1 * n,
+                  # a scatter pass of the learned sort moves a pair in and out (24 B/row); the
+                  # kernel's own carried id bytes (the first pass reads 2 and writes 1, the last
+                  # reads 1) are not counted
+                  "learned_ids_scatter": PAIR_BYTES * 2 * n, "learned_ids_count": 1 * n,
                   "learned_ids_upsweep": (8 + 2) * n, "learned_bucket_sort": PAIR_BYTES * 2 * n}
     peak, peak_kind = _peaks()
     dom_avg_ms = statistics.mean(per[dominant])
@@ -432,6 +432,8 @@ def run_gpu(args):
     traffic = DRAM_BYTES_PER_ROW.get(dominant)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_row": algo_bytes.get(dominant, 0) / n,
+                "launch_ms": dom_avg_ms,
                 "traffic": traffic * n if traffic else None,
                 "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 16M rows, "
                                    "per row, times the rows of a launch" if traffic else None),
