@@ -100,6 +100,30 @@ def backward(p: np.ndarray, x: np.ndarray, t: np.ndarray) -> np.ndarray:
     return g
 
 
+def abs_terms(p: np.ndarray, x: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """Per parameter, the sum over rows of the magnitudes of the row terms
+    whose sum is the gradient (each term of ``backward`` taken in absolute
+    value before the sum over rows).  A sum of such terms computed in FP32
+    is off by at most a small multiple of the unit roundoff times this, so it
+    scales the tolerance of each parameter's gradient."""
+    W1, b1, W2, b2, w3, b3 = unpack(p)
+    x = np.asarray(x, dtype=np.float64)
+    y, (a1, h1, a2, h2) = forward(p, x)
+    B = x.size
+    dy = np.abs(2.0 * (y - np.asarray(t, dtype=np.float64)) / B)
+    A = np.zeros(N_PARAMS, dtype=np.float64)
+    A[SLICES["w3"]] = h2.T @ dy
+    A[SLICES["b3"]] = dy.sum()
+    da2 = (dy[:, None] * np.abs(w3)[None, :]) * (a2 > 0)
+    A[SLICES["W2"]] = (da2.T @ h1).reshape(-1)
+    A[SLICES["b2"]] = da2.sum(axis=0)
+    # |da1| of each row is bounded by the sum of its terms' magnitudes
+    da1 = (da2 @ np.abs(W2)) * (a1 > 0)
+    A[SLICES["W1"]] = da1.T @ np.abs(x)
+    A[SLICES["b1"]] = da1.sum(axis=0)
+    return A
+
+
 def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update with bias correction (step counts from 1).  Returns
     new (p, m, v)."""

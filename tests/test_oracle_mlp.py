@@ -166,3 +166,21 @@ def test_quantile_init_passes_through_its_knots():
     # a single key value: the constant network
     p1 = mlp.quantile_init(np.full(10, 7, dtype=np.uint64))
     assert np.allclose(mlp.forward(p1, np.array([0.0, 0.5, 1.0]))[0], 0.5)
+
+
+def test_abs_terms_bound_the_gradient():
+    # the sum of the row terms' magnitudes is at least the magnitude of their
+    # sum (every parameter), and equals it when every term has one sign
+    rng = np.random.default_rng(7)
+    p = rng.normal(0, 0.5, mlp.N_PARAMS)
+    x = rng.random(300)
+    t = rng.random(300)
+    g = mlp.backward(p, x, t)
+    A = mlp.abs_terms(p, x, t)
+    assert np.all(A + 1e-15 >= np.abs(g))
+    assert np.any(A > 10 * np.abs(g))  # cancellation happens: A is the scale, not g
+    y, _ = mlp.forward(p, x)
+    g2 = mlp.backward(p, x, y + 1.0)  # every residual -1: the b3 and w3 terms have one sign
+    A2 = mlp.abs_terms(p, x, y + 1.0)
+    sl = mlp.SLICES
+    assert np.allclose(A2[sl["b3"]], np.abs(g2[sl["b3"]])) and np.allclose(A2[sl["w3"]], np.abs(g2[sl["w3"]]))
