@@ -558,7 +558,7 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
 
 
 def serving_rows(loads, n_windows, budget=40e9, n_windows_rest=None):
-    """The serving loop (cfg5) in real time: Poisson bundles of U[64K, 1M]
+    """The serving loop in real time: Poisson bundles of U[64K, 1M]
     rows (keys Zipf(0.8) over 50M, u64 values, 5% of rows up to 100 ms
     late), 1 s tumbling windows closed by watermark, per-key sum, count and
     top-3 of every window copied back, memory planned for a 40 GB HBM
