@@ -971,7 +971,9 @@ constexpr int kFineBits = 12;
 constexpr int kFineBins = 1 << kFineBits;
 constexpr int kFinePer = kFineBins / kBThreads;  // bins scanned by each thread
 constexpr uint32_t kFineMaxBin = 32;             // larger sub-buckets take the radix passes
-constexpr int kWideBits = 40;  // ... unless the key range is wider: then the bucket overflows
+constexpr int kWideBits = 40;  // ... unless the key range is wider: then a group sort and ranks
+constexpr int kGroupSubBits = 4;  // a big fine bin splits into 2^kGroupSubBits groups
+constexpr int kGroupPasses = (kFineBits + kGroupSubBits + kRadixBits - 1) / kRadixBits;
 
 struct BucketSmem {
     uint64_t keys[2][kCap];
@@ -984,6 +986,7 @@ struct BucketSmem {
     uint16_t gstart[kBGroups][kRadix];
     uint64_t red[2][kBWarps];
     uint32_t bin_tmp[kBWarps];
+    uint32_t bigbins[kFineBins / 32];  // fine bins over kFineMaxBin rows (uneven wide buckets)
     uint32_t next[2];  // the bucket taken after the current one (alternating slots)
 };
 static_assert(sizeof(BucketSmem) <= 232448, "bucket sort shared memory");
@@ -998,7 +1001,11 @@ struct BucketStats {
 // which every row finds its rank among the rows of its sub-bucket (at most
 // 32) by (key, place in the bucket) and is written straight to its output
 // row; or (a sub-bucket over 32 rows) stable 8-bit radix passes on key -
-// kmin, the last of which stores every row at its output row.  Rows of one
+// kmin, the last of which stores every row at its output row; or (a
+// sub-bucket over 32 rows and a range over 40 bits) two radix passes on a
+// 16-bit group of the key and ranks within the groups, the bucket
+// overflowing to the plain sort if a group of over 32 rows holds two keys.
+// Rows of one
 // key keep their input order: the scatter that formed the bucket was stable,
 // and both in-bucket sorts are.  Once a bucket is written, the next bucket's
 // rows are copied into the free buffer by per-thread asynchronous copies.
@@ -1116,9 +1123,10 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             continue;  // one key value: already in input order, nothing to write
         }
         const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
-        bool ranked = false;  // sorted and written out by the ranks
+        const int fsh = bits > kFineBits ? bits - kFineBits : 0;
+        bool ranked = false;   // sorted and written out by the ranks
+        bool binsort = false;  // uneven and wide: sort by fine bin first
         if (bits > kRadixBits) {
-            const int fsh = bits > kFineBits ? bits - kFineBits : 0;
 #pragma unroll
             for (int j = 0; j < kBIpt; ++j) {
                 const uint32_t r = tid + j * kBThreads;
@@ -1145,17 +1153,14 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             __syncthreads();  // (c)
             const uint32_t bt = sm.bin_tmp[lane];
             const bool big = __any_sync(0xffffffffu, (bt & 0x80000000u) != 0);
-            if (big && bits > kWideBits) {
-                // the radix passes in shared memory would take more than five
-                // passes: the plain radix sort of the overflow rows is cheaper
-                if (tid == 0) {
-                    ov_flag[b] = 1;
-                    atomicAdd(&st->wide_buckets, 1ull);
-                    atomicAdd(&st->wide_rows, (unsigned long long)cnt);
-                }
-                __syncthreads();  // buffer 0 is read no more
-                b = nb;
-                continue;
+            binsort = big && bits > kWideBits;
+            if (binsort) {
+                if (tid < kFineBins / 32) sm.bigbins[tid] = 0;
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < kFinePer; ++q)
+                    if (v[q] > kFineMaxBin) atomicOr(&sm.bigbins[(tid * kFinePer + q) >> 5], 1u << ((tid * kFinePer + q) & 31));
+                __syncthreads();
             }
             if (!big) {
                 uint32_t run = x - tsum;
@@ -1202,28 +1207,30 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 ranked = true;
             }
         }
-        if (!ranked) {
-            // stable radix passes on key - kmin, ping-pong from buffer 0;
-            // the last pass stores the rows at their output rows
-            const int passes = (bits + kRadixBits - 1) / kRadixBits;
-            if (tid == 0) {
-                atomicAdd(&st->radix_buckets, 1ull);
-                atomicAdd(&st->radix_rows, (unsigned long long)cnt);
-            }
+        // stable radix passes on value_of(key), ping-pong from buffer 0; with
+        // direct_last the last pass stores the rows at their output rows;
+        // returns the buffer holding the result otherwise
+        // Each warp takes ipt x 32 consecutive rows (ipt = rows per thread,
+        // from the bucket's size), so that a small bucket keeps every warp
+        // busy and no warp ranks empty slots.
+        const uint32_t ipt = (cnt + kBThreads - 1) / kBThreads;
+        auto radix_passes = [&](int passes, auto value_of, bool direct_last) -> int {
             int a = 0;
             for (int pass = 0; pass < passes; ++pass) {
                 const int sh = pass * kRadixBits;
                 for (int x = tid; x < kBWarps * (kRadix / 2 + 1); x += kBThreads) (&sm.whist2[0][0])[x] = 0;
                 __syncthreads();
                 uint32_t dg[kBIpt], rank[kBIpt];
-                const uint32_t wofs = warp * 32 * kBIpt + lane;
+                const uint32_t wofs = warp * 32 * ipt + lane;
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
                     const uint32_t r = wofs + j * 32;
-                    dg[j] = r < cnt ? static_cast<uint32_t>((sm.keys[a][r] - kmin) >> sh) & (kRadix - 1) : kRadix;
+                    dg[j] = (j < (int)ipt && r < cnt) ? static_cast<uint32_t>(value_of(sm.keys[a][r]) >> sh) & (kRadix - 1)
+                                                      : kRadix;
                 }
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
+                    if (j >= (int)ipt) break;
                     const uint32_t peers = warp_peers<kRadixBits + 1>(dg[j]);
                     const int leader = __ffs(peers) - 1;
                     const uint32_t hs = (dg[j] & 1u) * 16u;
@@ -1278,7 +1285,7 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 }
                 __syncthreads();
                 const uint32_t grp = warp / kBWpg;
-                const bool last = pass == passes - 1;
+                const bool last = direct_last && pass == passes - 1;
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
                     if (dg[j] < kRadix) {
@@ -1297,6 +1304,106 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 __syncthreads();
                 a ^= 1;
             }
+            return a;
+        };
+        if (binsort) {
+            // Uneven (a fine bin over kFineMaxBin rows) and wider than
+            // kWideBits: stable passes order the rows by a group, the fine
+            // bin and, inside a big bin, the next kGroupSubBits bits of the
+            // key, each group in input order.  A group's bounds come from a
+            // binary search on the groups; a group of more than kFineMaxBin
+            // rows must hold one key, so that its rows are in place, and the
+            // rows of the others rank themselves by (key, input order); every
+            // row then goes to its output row.  A key repeated in a big bin is
+            // mostly alone in its group.  (A 24-bit group, three passes, left
+            // fewer buckets to the plain sort but was slower: with hashed
+            // Zipf keys 16.0 against 15.5 ms for the 256M-row step.)
+            const int subsh = fsh - kGroupSubBits;  // fsh > kWideBits - kFineBits
+            auto group_of = [&](uint64_t k) -> uint64_t {
+                const uint64_t off = k - kmin;
+                const uint32_t bin = static_cast<uint32_t>(off >> fsh);
+                const bool bigbin = (sm.bigbins[bin >> 5] >> (bin & 31)) & 1u;
+                return (static_cast<uint64_t>(bin) << kGroupSubBits) |
+                       (bigbin ? static_cast<uint32_t>(off >> subsh) & ((1u << kGroupSubBits) - 1) : 0u);
+            };
+            const int ga = radix_passes(kGroupPasses, group_of, false);
+            // the rows' groups, in order, in the keys of the free buffer
+            uint64_t* grp = sm.keys[ga ^ 1];
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t i = tid + j * kBThreads;
+                if (i < cnt) grp[i] = group_of(sm.keys[ga][i]);
+            }
+            __syncthreads();
+            auto lower = [&](uint64_t g, bool upper) {  // first row of a group above (or not below) g
+                uint32_t lo = 0, hi = cnt;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) / 2;
+                    const uint64_t gm = grp[mid];
+                    if (gm < g || (upper && gm == g)) lo = mid + 1;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            uint32_t gb[kBIpt], ge[kBIpt];
+            bool multi = false;
+#pragma unroll
+            for (int j = 0; j < kBIpt; ++j) {
+                const uint32_t i = tid + j * kBThreads;
+                gb[j] = ge[j] = 0;
+                if (i < cnt) {
+                    const uint64_t g = grp[i];
+                    gb[j] = lower(g, false);
+                    ge[j] = lower(g, true);
+                    if (ge[j] - gb[j] > kFineMaxBin && sm.keys[ga][i] != sm.keys[ga][gb[j]]) multi = true;
+                }
+            }
+            if (!__syncthreads_or(multi)) {
+#pragma unroll
+                for (int j = 0; j < kBIpt; ++j) {
+                    const uint32_t i = tid + j * kBThreads;
+                    if (i < cnt) {
+                        const uint64_t k = sm.keys[ga][i];
+                        uint32_t r = 0;
+                        if (ge[j] - gb[j] > kFineMaxBin) {
+                            r = i - gb[j];  // one key: input order
+                        } else {
+                            for (uint32_t x = gb[j]; x < ge[j]; ++x) {
+                                const uint64_t kx = sm.keys[ga][x];
+                                r += (kx < k || (kx == k && x < i)) ? 1u : 0u;
+                            }
+                        }
+                        keys[s + gb[j] + r] = k;
+                        ptrs[s + gb[j] + r] = sm.ptrs[ga][i];
+                    }
+                }
+                __syncthreads();  // the buffers are read no more
+                ranked = true;
+                if (tid == 0) {
+                    atomicAdd(&st->radix_buckets, 1ull);
+                    atomicAdd(&st->radix_rows, (unsigned long long)cnt);
+                }
+            } else {
+                // more than five passes on the key would be needed: the plain
+                // radix sort of the overflow rows is cheaper (the bucket's
+                // rows in global memory are untouched)
+                if (tid == 0) {
+                    ov_flag[b] = 1;
+                    atomicAdd(&st->wide_buckets, 1ull);
+                    atomicAdd(&st->wide_rows, (unsigned long long)cnt);
+                }
+                b = nb;
+                continue;
+            }
+        }
+        if (!ranked) {
+            // stable radix passes on key - kmin; the last stores the rows at
+            // their output rows
+            if (tid == 0) {
+                atomicAdd(&st->radix_buckets, 1ull);
+                atomicAdd(&st->radix_rows, (unsigned long long)cnt);
+            }
+            radix_passes((bits + kRadixBits - 1) / kRadixBits, [&](uint64_t k) { return k - kmin; }, true);
         }
         // the bucket is written out and buffer 0 is free: the next bucket's
         // copies start now (issuing them during the ranking measured slower)

@@ -311,3 +311,34 @@ def test_overflow_sort_takes_either_path_on_the_device(S, thr):
     assert st["overflow_rows"] > 1 << 16
     ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
     assert same(sk, ok) and same(sp, op)
+
+
+@pytest.mark.parametrize("bins", ["one_key", "two_keys"])
+@pytest.mark.parametrize("span_bits", [30, 50])
+def test_learned_sort_uneven_wide_buckets(S, bins, span_bits):
+    # spread keys plus keys repeated 60-150 times: every bucket holding one
+    # is uneven (a fine bin over 32 rows).  Spanning 30 bits, it takes the
+    # radix passes on the key; spanning ~44 bits (50-bit keys), it is sorted
+    # by a 16-bit group of the key and ranked, unless a group of over 32 rows
+    # holds two keys: then it joins the overflow rows.  A repeated key and its
+    # neighbour always share a group; a spread key shares one with a
+    # repeated key now and then
+    rng_keys = gen.uniform(23, 1, 300_000, 0, 1 << span_bits, np.uint64)
+    reps = gen.uniform(23, 2, 400, 0, 1 << span_bits, np.uint64)
+    parts = [rng_keys, np.repeat(reps, 150)]
+    if bins == "two_keys":
+        parts.append(np.repeat(reps + np.uint64(1), 60))  # a neighbour key in the same fine bin
+    col = np.concatenate(parts)
+    col = col[np.argsort(gen.uniform(23, 3, col.size, 0, 0, np.uint64), kind="stable")]
+    n = col.size
+    model, _ = S.learned_train(cuda(col[::100].copy()), n, None, steps=40, batch=4096, lr=3e-4)
+    keys, ptrs = S.extract(cuda(col), 0, n)
+    sk, sp, st = S.sort_learned(keys, ptrs, model)
+    ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+    assert same(sk, ok) and same(sp, op)
+    if span_bits == 30:
+        assert st["radix_buckets"] > 0 and st["wide_rows"] == 0
+    elif bins == "two_keys":
+        assert st["wide_rows"] >= 400 * 210 and st["wide_buckets"] > 0
+    else:  # every bucket holds a repeated key: without the group sort all would be wide
+        assert st["radix_rows"] > n // 2 and st["wide_rows"] < n // 3
