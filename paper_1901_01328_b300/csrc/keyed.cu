@@ -63,6 +63,23 @@ __device__ __forceinline__ void load_rows(const uint64_t* __restrict__ keys, con
                                           uint32_t lane, uint64_t (&k)[kIpt], uint64_t (&v)[kIpt],
                                           uint32_t& hmask) {
     const uint32_t first = base + wofs;  // first row of this warp
+    if (!kVals && first < n) {
+        // Counts only: when the warp's first and last rows hold one key (the
+        // rows are sorted), all of them do, and only the first can be a head;
+        // the other rows are not read.  (With Zipf-skewed keys about half of
+        // the 512-row warp ranges are one key.)
+        const uint32_t last = min(first + 32 * kIpt, n) - 1;
+        const uint64_t kf = keys[first], kl = keys[last];
+        if (kf == kl) {
+#pragma unroll
+            for (int j = 0; j < kIpt; ++j) {
+                k[j] = kf;
+                v[j] = 0;
+            }
+            hmask = (lane == 0 && (first == 0 || keys[first - 1] != kf)) ? 1u : 0u;
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
         const uint32_t r = first + j * 32 + lane;

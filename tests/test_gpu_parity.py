@@ -239,6 +239,22 @@ def test_group_reduce_heavy_key_spans_tiles_and_cap(S):
     assert same(out_k, ok[:cap]) and same(out_c, oc[:cap]) and same(out_s, osum[:cap])
 
 
+@pytest.mark.parametrize("offset", [0, 1, 511])
+def test_group_count_runs_at_warp_range_boundaries(S, offset):
+    # a warp reads 512 consecutive rows; counts-only skips the rows of a
+    # range whose first and last keys are equal.  Runs that start, end or
+    # fill a range exactly (and one that ends at the last row) must still
+    # give every key its head and count
+    lengths = [offset or 1, 512, 511, 513, 1, 1024, 4096, 4097, 3, 512 * 9, 1, 1, 700, 512 + 511]
+    lengths = lengths * 6 + [2 * 4096 + 5]
+    col = np.repeat(np.arange(len(lengths), dtype=np.uint64) * 7 + 3, lengths)
+    n = col.size
+    sk, sp = _sorted_kpa(S, col)
+    gk, gc, _ = S.group_reduce(sk, sp, None)
+    ok, oc, _ = oracle.group_sum_count(*_oracle_sorted(col), None)
+    assert same(gk, ok) and same(gc, oc) and int(oc.sum()) == n
+
+
 def test_group_count_mixed_keys_16m(S):
     n = 16_000_000
     col = gen.mixed_keys(n)
