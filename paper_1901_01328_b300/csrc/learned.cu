@@ -963,6 +963,7 @@ __global__ void __launch_bounds__(256) bucket_bounds_kernel(const uint64_t* __re
 constexpr uint32_t kCap = SBH_LEARNED_CAPACITY;
 constexpr int kBThreads = 1024;
 constexpr int kBWarps = kBThreads / 32;
+static_assert(kBWarps == 32, "the bucket sort scans its warps' totals one per lane");
 constexpr int kBIpt = kCap / kBThreads;
 constexpr int kBGroups = kBThreads / 128;  // warp groups of the radix passes' count scan
 constexpr int kBWpg = kBWarps / kBGroups;
@@ -972,6 +973,9 @@ constexpr int kFineBins = 1 << kFineBits;
 constexpr int kFinePer = kFineBins / kBThreads;  // bins scanned by each thread
 constexpr uint32_t kFineMaxBin = 32;             // larger sub-buckets take the radix passes
 constexpr int kWideBits = 40;  // ... unless the key range is wider: then a group sort and ranks
+// Consecutive buckets are sorted together as one run of at most kCap rows
+// (their key ranges are consecutive, so sorting the run sorts each bucket);
+// a heavy bucket, or one of more than kCap rows, is a run of its own.
 constexpr int kGroupSubBits = 4;  // a big fine bin splits into 2^kGroupSubBits groups
 constexpr int kGroupPasses = (kFineBits + kGroupSubBits + kRadixBits - 1) / kRadixBits;
 
@@ -996,53 +1000,68 @@ struct BucketStats {
         max_bucket, radix_buckets, radix_rows, wide_buckets, wide_rows;
 };
 
-// Persistent CTAs take buckets in order from a counter and sort each one in
-// shared memory: a counting placement by the top 12 bits of key - kmin, after
-// which every row finds its rank among the rows of its sub-bucket (at most
-// 32) by (key, place in the bucket) and is written straight to its output
-// row; or (a sub-bucket over 32 rows) stable 8-bit radix passes on key -
-// kmin, the last of which stores every row at its output row; or (a
-// sub-bucket over 32 rows and a range over 40 bits) two radix passes on a
-// 16-bit group of the key and ranks within the groups, the bucket
-// overflowing to the plain sort if a group of over 32 rows holds two keys.
-// Rows of one
-// key keep their input order: the scatter that formed the bucket was stable,
-// and both in-bucket sorts are.  Once a bucket is written, the next bucket's
-// rows are copied into the free buffer by per-thread asynchronous copies.
-// (Loading the next bucket's bounds while this one is sorted measured slower:
-// 3.12 vs 2.97 ms at 256M rows; the last radix pass storing straight to the
-// output rows instead of staging a sorted copy, 2.92 ms.)  (Per-thread insertion
-// sorts of the sub-buckets, and a warp's bitonic network for sub-buckets of 9
-// to 32 rows, measured slower than the ranks.)
+// Persistent CTAs take runs of buckets (a run: one bucket, or consecutive
+// buckets of at most kCap rows together, listed by their first bucket) in
+// order from a counter and sort each run in shared memory.  A bucket of the
+// headline window holds ~2,200 rows and a run ~6,900: the CTA's fixed work
+// per iteration (its barriers, the 4096-bin scan, the warps' reductions) is
+// spread over three times the rows (2.75 to 2.0 ms for 256M rows).
+//
+// A run's rows are sorted by a counting placement by the top 12 bits of
+// key - kmin, after which every row finds its rank among the rows of its
+// sub-bucket (at most 32) by (key, place in the run) and is written straight
+// to its output row; or (a sub-bucket over 32 rows) stable 8-bit radix
+// passes on key - kmin, the last of which stores every row at its output
+// row; or (a sub-bucket over 32 rows and a range over 40 bits) two radix
+// passes on a 16-bit group of the key and ranks within the groups.  If a
+// group of over 32 rows then holds two keys, a run of several buckets is
+// retried bucket by bucket (a second launch, singles != 0), and a bucket
+// alone joins the overflow rows.  Rows of one key keep their input order:
+// the scatter that formed the buckets was stable, and every in-run sort is.
+// Once a run is written, the next run's rows are copied into the free
+// buffer by per-thread asynchronous copies.  (Loading the next bucket's
+// bounds while this one is sorted measured slower: 3.12 vs 2.97 ms at 256M
+// rows; the last radix pass storing straight to the output rows instead of
+// staging a sorted copy, 2.92 ms.  Per-thread insertion sorts of the
+// sub-buckets, and a warp's bitonic network for sub-buckets of 9 to 32 rows,
+// measured slower than the ranks.)
 __global__ void __launch_bounds__(kBThreads, 1)
 bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
                    const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
-                   uint32_t* __restrict__ counter, uint32_t* __restrict__ ov_flag, BucketStats* __restrict__ st) {
+                   const uint32_t* __restrict__ runs, const uint32_t* __restrict__ nruns_p, int singles,
+                   uint32_t* __restrict__ counter, uint32_t* __restrict__ ov_flag, uint32_t* __restrict__ retry_flag,
+                   BucketStats* __restrict__ st) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BucketSmem& sm = *reinterpret_cast<BucketSmem*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    const uint32_t nbid = *nbid_p;
+    const uint32_t nbid = *nbid_p, nruns = *nruns_p;
     const uint32_t lt = lanemask_lt();
+    // run x: buckets [runs[x], run_end(x)) (singles: each listed bucket alone)
+    auto run_end = [&](uint32_t x) { return singles ? runs[x] + 1 : (x + 1 < nruns ? runs[x + 1] : nbid); };
+    auto heavy_one = [&](uint32_t b0, uint32_t b1) {  // a run of one heavy bucket
+        return b1 == b0 + 1 && ((heavy_bucket_bits[b0 >> 5] >> (b0 & 31)) & 1u) != 0;
+    };
     if (tid == 0) sm.next[0] = atomicAdd(counter, 1u);
     __syncthreads();
-    uint32_t b = sm.next[0];
-    // the next bucket's rows are copied into buffer 0 while the current
-    // bucket is written out of buffer 1 (when the next one is sorted here)
+    uint32_t rq = sm.next[0];
+    // the next run's rows are copied into buffer 0 while the current run is
+    // written out of buffer 1 (when the next one is sorted here)
     bool prefetched = false;
     for (uint32_t it = 1;; ++it) {
-        if (b >= nbid) break;
-        // the bucket after this one; read after this bucket's first barrier,
-        // rewritten two buckets later
+        if (rq >= nruns) break;
+        // the run after this one; read after this run's first barrier,
+        // rewritten two runs later
         if (tid == 0) sm.next[it & 1] = atomicAdd(counter, 1u);
-        const uint32_t s = bstart[b], e = bstart[b + 1], cnt = e - s;
-        const bool heavy = ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) != 0;
-        // copies the next bucket's rows into buffer 0 once it is free (a
-        // range not this one's), if the next bucket is sorted here
-        auto prefetch_next = [&](uint32_t nxt) {
-            if (nxt >= nbid) return;
-            const uint32_t s2 = bstart[nxt], cnt2 = bstart[nxt + 1] - s2;
-            const bool heavy2 = ((heavy_bucket_bits[nxt >> 5] >> (nxt & 31)) & 1u) != 0;
-            if (cnt2 > 1 && !heavy2 && cnt2 <= kCap) {
+        const uint32_t b = runs[rq], bend = run_end(rq), nbk = bend - b;
+        const uint32_t s = bstart[b], e = bstart[bend], cnt = e - s;
+        const bool heavy = heavy_one(b, bend);
+        // copies the next run's rows into buffer 0 once it is free (a range
+        // not this one's), if the next run is sorted here
+        auto prefetch_next = [&](uint32_t nq) {
+            if (nq >= nruns) return;
+            const uint32_t b2 = runs[nq], bend2 = run_end(nq);
+            const uint32_t s2 = bstart[b2], cnt2 = bstart[bend2] - s2;
+            if (cnt2 > 1 && !heavy_one(b2, bend2) && cnt2 <= kCap) {
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
                     const uint32_t r = tid + j * kBThreads;
@@ -1055,9 +1074,13 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 prefetched = true;
             }
         };
-        if (cnt <= 1 || heavy || cnt > kCap) {
+        if (tid == 0) {  // the largest bucket of the run
+            uint32_t mx = 0;
+            for (uint32_t x = b; x < bend; ++x) mx = max(mx, bstart[x + 1] - bstart[x]);
+            if (mx > 0) atomicMax(&st->max_bucket, (unsigned long long)mx);
+        }
+        if (cnt <= 1 || heavy || cnt > kCap) {  // (cnt > kCap: a run of one bucket)
             if (tid == 0) {
-                if (cnt > 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
                 if (cnt > 1 && heavy) {
                     atomicAdd(&st->heavy_buckets, 1ull);  // one key: the stable scatter left it in input order
                 } else if (cnt > 1) {
@@ -1067,10 +1090,9 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 }
             }
             __syncthreads();
-            b = sm.next[it & 1];
+            rq = sm.next[it & 1];
             continue;
         }
-        if (tid == 0) atomicMax(&st->max_bucket, (unsigned long long)cnt);
         // load (buffer 0), the key range, and clear the bins
         uint64_t kmin = ~0ull, kmax = 0;
         if (prefetched) {
@@ -1109,7 +1131,7 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             sm.red[1][warp] = kmax;
         }
         __syncthreads();  // (a)
-        const uint32_t nb = sm.next[it & 1];
+        const uint32_t nq = sm.next[it & 1];
         kmin = sm.red[0][lane];
         kmax = sm.red[1][lane];
         for (int o = 16; o > 0; o >>= 1) {
@@ -1117,9 +1139,9 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         }
         if (kmin == kmax) {
-            if (tid == 0) atomicAdd(&st->single_key_buckets, 1ull);
+            if (tid == 0) atomicAdd(&st->single_key_buckets, (unsigned long long)nbk);
             __syncthreads();  // buffer 0 is read no more
-            b = nb;
+            rq = nq;
             continue;  // one key value: already in input order, nothing to write
         }
         const int bits = 64 - __clzll(static_cast<long long>(kmax - kmin));
@@ -1163,8 +1185,15 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 __syncthreads();
             }
             if (!big) {
-                uint32_t run = x - tsum;
-                for (int w = 0; w < (int)warp; ++w) run += sm.bin_tmp[w];
+                // this thread's first row: the warps before it (an exclusive
+                // scan of the warp totals, one a lane), then the lanes before
+                uint32_t wx = bt;  // no flag bits: no bin is big
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, wx, o);
+                    if (lane >= (uint32_t)o) wx += y;
+                }
+                uint32_t run = __shfl_sync(0xffffffffu, wx - bt, warp) + x - tsum;
 #pragma unroll
                 for (int q = 0; q < kFinePer; ++q) {
                     sm.bins[tid * kFinePer + q] = run;  // next free row of the bin
@@ -1380,19 +1409,25 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 __syncthreads();  // the buffers are read no more
                 ranked = true;
                 if (tid == 0) {
-                    atomicAdd(&st->radix_buckets, 1ull);
+                    atomicAdd(&st->radix_buckets, (unsigned long long)nbk);
                     atomicAdd(&st->radix_rows, (unsigned long long)cnt);
                 }
             } else {
-                // more than five passes on the key would be needed: the plain
-                // radix sort of the overflow rows is cheaper (the bucket's
+                // a big group holds two keys: more than five passes on the
+                // key would be needed.  A run of several buckets is retried
+                // bucket by bucket (a second launch); a bucket alone joins
+                // the overflow rows, whose plain radix sort is cheaper (its
                 // rows in global memory are untouched)
                 if (tid == 0) {
-                    ov_flag[b] = 1;
-                    atomicAdd(&st->wide_buckets, 1ull);
-                    atomicAdd(&st->wide_rows, (unsigned long long)cnt);
+                    if (nbk > 1) {
+                        for (uint32_t x = b; x < bend; ++x) retry_flag[x] = 1;
+                    } else {
+                        ov_flag[b] = 1;
+                        atomicAdd(&st->wide_buckets, 1ull);
+                        atomicAdd(&st->wide_rows, (unsigned long long)cnt);
+                    }
                 }
-                b = nb;
+                rq = nq;
                 continue;
             }
         }
@@ -1400,25 +1435,67 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             // stable radix passes on key - kmin; the last stores the rows at
             // their output rows
             if (tid == 0) {
-                atomicAdd(&st->radix_buckets, 1ull);
+                atomicAdd(&st->radix_buckets, (unsigned long long)nbk);
                 atomicAdd(&st->radix_rows, (unsigned long long)cnt);
             }
             radix_passes((bits + kRadixBits - 1) / kRadixBits, [&](uint64_t k) { return k - kmin; }, true);
         }
         // the bucket is written out and buffer 0 is free: the next bucket's
         // copies start now (issuing them during the ranking measured slower)
-        prefetch_next(nb);
-        if (tid == 0) atomicAdd(&st->sorted_buckets, 1ull);
-        b = nb;
+        prefetch_next(nq);
+        if (tid == 0) atomicAdd(&st->sorted_buckets, (unsigned long long)nbk);
+        rq = nq;
     }
 }
 
-// Ordered list of overflow buckets with their row offsets in a compact
+// Flags the first bucket of every run the bucket sort takes: greedily, each
+// run as long as it stays within kCap rows, from the first bucket of each
+// segment of kRunSeg buckets (a warp walks a segment's bounds, held in shared
+// memory, 32 buckets a step).
+constexpr uint32_t kRunSeg = 128;
+__global__ void __launch_bounds__(1024) run_start_kernel(const uint32_t* __restrict__ bstart,
+                                                         const uint32_t* __restrict__ nbid_p,
+                                                         const uint32_t* __restrict__ heavy_bucket_bits,
+                                                         uint32_t* __restrict__ run_flag) {
+    __shared__ uint32_t sb[1025], shw[32], flag[1024];
+    const uint32_t nbid = *nbid_p, b0 = blockIdx.x * 1024u;
+    if (b0 >= nbid) return;
+    const uint32_t m = min(1024u, nbid - b0), tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
+    for (uint32_t i = tid; i <= m; i += 1024u) sb[i] = bstart[b0 + i];
+    if (tid < 32) shw[tid] = heavy_bucket_bits[(b0 >> 5) + tid];
+    flag[tid] = 0;
+    __syncthreads();
+    const uint32_t lo = warp * kRunSeg, hi = min(m, lo + kRunSeg);  // this warp's segment
+    if (warp < 1024 / kRunSeg && lo < hi) {
+        auto alone = [&](uint32_t x) { return ((shw[x >> 5] >> (x & 31)) & 1u) != 0 || sb[x + 1] - sb[x] > kCap; };
+        uint32_t cur = lo;
+        while (cur < hi) {
+            if (lane == 0) flag[cur] = 1;
+            uint32_t end = cur + 1;  // first bucket after the run
+            if (!alone(cur)) {
+                for (;;) {  // lanes try end + lane
+                    const uint32_t x = end + lane;
+                    const bool ok = x < hi && !alone(x) && sb[x + 1] - sb[cur] <= kCap;
+                    const uint32_t fit = __ballot_sync(0xffffffffu, ok);
+                    const uint32_t nfit = fit == 0xffffffffu ? 32u : (uint32_t)(__ffs(~fit) - 1);
+                    end += nfit;
+                    if (nfit < 32) break;
+                }
+            }
+            cur = end;
+        }
+    }
+    __syncthreads();
+    if (tid < m) run_flag[b0 + tid] = flag[tid];
+}
+
+// Ordered list of flagged buckets (the overflow buckets, or the first
+// buckets of the bucket sort's runs) with their row offsets in a compact
 // buffer, in two launches over blocks of 1024 buckets: each block's count of
-// overflow buckets and rows, then each block's exclusive scan from the totals
+// flagged buckets and rows, then each block's exclusive scan from the totals
 // of the blocks before it.  The last block writes the totals to nlist and
-// ov_rows_total.
-__global__ void __launch_bounds__(1024) overflow_count_kernel(const uint32_t* __restrict__ ov_flag,
+// rows_total.
+__global__ void __launch_bounds__(1024) flag_count_kernel(const uint32_t* __restrict__ ov_flag,
                                                               const uint32_t* __restrict__ nbid_p,
                                                               const uint32_t* __restrict__ bstart,
                                                               uint2* __restrict__ bagg) {
@@ -1449,7 +1526,7 @@ __global__ void __launch_bounds__(1024) overflow_count_kernel(const uint32_t* __
     }
 }
 
-__global__ void __launch_bounds__(1024) overflow_list_kernel(const uint32_t* __restrict__ ov_flag,
+__global__ void __launch_bounds__(1024) flag_list_kernel(const uint32_t* __restrict__ ov_flag,
                                                              const uint32_t* __restrict__ nbid_p,
                                                              const uint32_t* __restrict__ bstart,
                                                              const uint2* __restrict__ bagg,
@@ -1858,7 +1935,10 @@ struct SortLearnedScratch {
     uint32_t* list;
     uint2* bagg;            // per block of buckets: overflow buckets, rows
     uint32_t* offs;
-    uint32_t* small;        // nbid, counter, nlist, rows_total, heavy keys used, spread buckets
+    uint32_t* retry_flag;   // buckets of runs the bucket sort retries one by one
+    uint32_t* small;        // nbid, counter, nlist, rows_total, heavy keys used, spread buckets, runs, (rows),
+                            // second counter, retried buckets, (rows)
+    uint32_t* run_flag;     // first buckets of the bucket sort's runs
     BucketStats* stats;
     uint64_t* ck;           // compact overflow rows (n)
     uint32_t* cp;
@@ -1892,9 +1972,11 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.heavy_bucket_bits = c.take<uint32_t>(ids / 32 + 1);
     const size_t z0 = c.off - (ids / 32 + 1) * sizeof(uint32_t);
     t.ov_flag = c.take<uint32_t>(ids);
-    t.small = c.take<uint32_t>(8);
+    t.retry_flag = c.take<uint32_t>(ids);
+    t.small = c.take<uint32_t>(16);
     t.stats = c.take<BucketStats>(1);
     t.zero_bytes = c.off - z0;
+    t.run_flag = c.take<uint32_t>(ids);  // written for every bucket id in use
     t.ck = c.take<uint64_t>(n);
     t.cp = c.take<uint32_t>(n);
     t.sort_scratch = c.take<char>(std::max(sort_carve(nullptr, n, true).total, carry_carve(nullptr, n).total));
@@ -2095,20 +2177,44 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                                                                                    t.bstart));
         SBH_LAUNCHED();
     }
+    // the bucket sort's runs, listed in t.list (free until the overflow list)
+    const unsigned lblocks = (unsigned)(learned_max_ids(n) / 1024 + 1);
+    uint32_t* nruns = t.small + 6;
+    SBH_TIMED("learned_runs", s, run_start_kernel<<<lblocks, 1024, 0, s>>>(t.bstart, nbid, t.heavy_bucket_bits, t.run_flag));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_runs_count", s, flag_count_kernel<<<lblocks, 1024, 0, s>>>(t.run_flag, nbid, t.bstart, t.bagg));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_runs_list", s,
+              flag_list_kernel<<<lblocks, 1024, 0, s>>>(t.run_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nruns,
+                                                        t.small + 7));
+    SBH_LAUNCHED();
     const size_t smem = sizeof(BucketSmem);
     SBH_CUDA(cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SBH_TIMED("learned_bucket_sort", s,
               bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, nbid,
-                                                                    t.heavy_bucket_bits, counter, t.ov_flag,
-                                                                    t.stats));
+                                                                    t.heavy_bucket_bits, t.list, nruns, 0, counter,
+                                                                    t.ov_flag, t.retry_flag, t.stats));
     SBH_LAUNCHED();
-    const unsigned lblocks = (unsigned)(learned_max_ids(n) / 1024 + 1);
+    // runs whose group sort failed: their buckets one by one (usually none)
+    uint32_t* nretry = t.small + 9;
+    SBH_TIMED("learned_retry_count", s,
+              flag_count_kernel<<<lblocks, 1024, 0, s>>>(t.retry_flag, nbid, t.bstart, t.bagg));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_retry_list", s,
+              flag_list_kernel<<<lblocks, 1024, 0, s>>>(t.retry_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nretry,
+                                                        t.small + 10));
+    SBH_LAUNCHED();
+    SBH_TIMED("learned_bucket_retry", s,
+              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, nbid,
+                                                                    t.heavy_bucket_bits, t.list, nretry, 1,
+                                                                    t.small + 8, t.ov_flag, t.retry_flag, t.stats));
+    SBH_LAUNCHED();
     SBH_TIMED("learned_overflow_count", s,
-              overflow_count_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg));
+              flag_count_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg));
     SBH_LAUNCHED();
     SBH_TIMED("learned_overflow_list", s,
-              overflow_list_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nlist,
-                                                           rows_total));
+              flag_list_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nlist,
+                                                        rows_total));
     SBH_LAUNCHED();
     // the overflow rows (their number is known only on the device): gathered
     // into a compact buffer, sorted by the plain radix sort sized on the
