@@ -976,6 +976,7 @@ constexpr int kWideBits = 40;  // ... unless the key range is wider: then a grou
 // Consecutive buckets are sorted together as one run of at most kCap rows
 // (their key ranges are consecutive, so sorting the run sorts each bucket);
 // a heavy bucket, or one of more than kCap rows, is a run of its own.
+constexpr uint32_t kRunHeavy = 1u << 31, kRunEnd = kRunHeavy - 1;
 constexpr int kGroupSubBits = 4;  // a big fine bin splits into 2^kGroupSubBits groups
 constexpr int kGroupPasses = (kFineBits + kGroupSubBits + kRadixBits - 1) / kRadixBits;
 
@@ -1027,20 +1028,16 @@ struct BucketStats {
 // measured slower than the ranks.)
 __global__ void __launch_bounds__(kBThreads, 1)
 bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, const uint32_t* __restrict__ bstart,
-                   const uint32_t* __restrict__ nbid_p, const uint32_t* __restrict__ heavy_bucket_bits,
-                   const uint32_t* __restrict__ runs, const uint32_t* __restrict__ nruns_p, int singles,
+                   const uint4* __restrict__ runrec, const uint32_t* __restrict__ nruns_p,
                    uint32_t* __restrict__ counter, uint32_t* __restrict__ ov_flag, uint32_t* __restrict__ retry_flag,
                    BucketStats* __restrict__ st) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BucketSmem& sm = *reinterpret_cast<BucketSmem*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid / 32;
-    const uint32_t nbid = *nbid_p, nruns = *nruns_p;
+    const uint32_t nruns = *nruns_p;
     const uint32_t lt = lanemask_lt();
-    // run x: buckets [runs[x], run_end(x)) (singles: each listed bucket alone)
-    auto run_end = [&](uint32_t x) { return singles ? runs[x] + 1 : (x + 1 < nruns ? runs[x + 1] : nbid); };
-    auto heavy_one = [&](uint32_t b0, uint32_t b1) {  // a run of one heavy bucket
-        return b1 == b0 + 1 && ((heavy_bucket_bits[b0 >> 5] >> (b0 & 31)) & 1u) != 0;
-    };
+    // run x: buckets [rec.x, rec.y & kRunEnd), rows [rec.z, rec.w); bit 31
+    // of rec.y: a run of one heavy bucket
     if (tid == 0) sm.next[0] = atomicAdd(counter, 1u);
     __syncthreads();
     uint32_t rq = sm.next[0];
@@ -1052,16 +1049,17 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
         // the run after this one; read after this run's first barrier,
         // rewritten two runs later
         if (tid == 0) sm.next[it & 1] = atomicAdd(counter, 1u);
-        const uint32_t b = runs[rq], bend = run_end(rq), nbk = bend - b;
-        const uint32_t s = bstart[b], e = bstart[bend], cnt = e - s;
-        const bool heavy = heavy_one(b, bend);
+        const uint4 rr = runrec[rq];
+        const uint32_t b = rr.x, bend = rr.y & kRunEnd, nbk = bend - b;
+        const uint32_t s = rr.z, e = rr.w, cnt = e - s;
+        const bool heavy = (rr.y & kRunHeavy) != 0;
         // copies the next run's rows into buffer 0 once it is free (a range
         // not this one's), if the next run is sorted here
         auto prefetch_next = [&](uint32_t nq) {
             if (nq >= nruns) return;
-            const uint32_t b2 = runs[nq], bend2 = run_end(nq);
-            const uint32_t s2 = bstart[b2], cnt2 = bstart[bend2] - s2;
-            if (cnt2 > 1 && !heavy_one(b2, bend2) && cnt2 <= kCap) {
+            const uint4 r2 = runrec[nq];
+            const uint32_t s2 = r2.z, cnt2 = r2.w - r2.z;
+            if (cnt2 > 1 && !(r2.y & kRunHeavy) && cnt2 <= kCap) {
 #pragma unroll
                 for (int j = 0; j < kBIpt; ++j) {
                     const uint32_t r = tid + j * kBThreads;
@@ -1075,8 +1073,11 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
             }
         };
         if (tid == 0) {  // the largest bucket of the run
-            uint32_t mx = 0;
-            for (uint32_t x = b; x < bend; ++x) mx = max(mx, bstart[x + 1] - bstart[x]);
+            uint32_t mx = cnt;
+            if (nbk > 1) {
+                mx = 0;
+                for (uint32_t x = b; x < bend; ++x) mx = max(mx, bstart[x + 1] - bstart[x]);
+            }
             if (mx > 0) atomicMax(&st->max_bucket, (unsigned long long)mx);
         }
         if (cnt <= 1 || heavy || cnt > kCap) {  // (cnt > kCap: a run of one bucket)
@@ -1487,6 +1488,22 @@ __global__ void __launch_bounds__(1024) run_start_kernel(const uint32_t* __restr
     }
     __syncthreads();
     if (tid < m) run_flag[b0 + tid] = flag[tid];
+}
+
+// The bucket sort's run records from a list of first buckets (singles: every
+// listed bucket a run of its own): first bucket, end bucket (bit 31: one
+// heavy bucket), first row, end row.
+__global__ void __launch_bounds__(1024) run_records_kernel(const uint32_t* __restrict__ list,
+                                                           const uint32_t* __restrict__ n_p, int singles,
+                                                           const uint32_t* __restrict__ nbid_p,
+                                                           const uint32_t* __restrict__ bstart,
+                                                           const uint32_t* __restrict__ heavy_bucket_bits,
+                                                           uint4* __restrict__ rec) {
+    const uint32_t n = *n_p, i = blockIdx.x * 1024u + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = list[i], bend = singles ? b + 1 : (i + 1 < n ? list[i + 1] : *nbid_p);
+    const bool heavy = bend == b + 1 && ((heavy_bucket_bits[b >> 5] >> (b & 31)) & 1u) != 0;
+    rec[i] = make_uint4(b, bend | (heavy ? kRunHeavy : 0u), bstart[b], bstart[bend]);
 }
 
 // Ordered list of flagged buckets (the overflow buckets, or the first
@@ -1939,6 +1956,7 @@ struct SortLearnedScratch {
     uint32_t* small;        // nbid, counter, nlist, rows_total, heavy keys used, spread buckets, runs, (rows),
                             // second counter, retried buckets, (rows)
     uint32_t* run_flag;     // first buckets of the bucket sort's runs
+    uint4* runrec;          // the runs' records
     BucketStats* stats;
     uint64_t* ck;           // compact overflow rows (n)
     uint32_t* cp;
@@ -1977,6 +1995,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.stats = c.take<BucketStats>(1);
     t.zero_bytes = c.off - z0;
     t.run_flag = c.take<uint32_t>(ids);  // written for every bucket id in use
+    t.runrec = c.take<uint4>(ids);
     t.ck = c.take<uint64_t>(n);
     t.cp = c.take<uint32_t>(n);
     t.sort_scratch = c.take<char>(std::max(sort_carve(nullptr, n, true).total, carry_carve(nullptr, n).total));
@@ -2188,12 +2207,16 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
               flag_list_kernel<<<lblocks, 1024, 0, s>>>(t.run_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nruns,
                                                         t.small + 7));
     SBH_LAUNCHED();
+    SBH_TIMED("learned_runs_rec", s,
+              run_records_kernel<<<lblocks, 1024, 0, s>>>(t.list, nruns, 0, nbid, t.bstart, t.heavy_bucket_bits,
+                                                          t.runrec));
+    SBH_LAUNCHED();
     const size_t smem = sizeof(BucketSmem);
     SBH_CUDA(cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SBH_TIMED("learned_bucket_sort", s,
-              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, nbid,
-                                                                    t.heavy_bucket_bits, t.list, nruns, 0, counter,
-                                                                    t.ov_flag, t.retry_flag, t.stats));
+              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.runrec,
+                                                                    nruns, counter, t.ov_flag, t.retry_flag,
+                                                                    t.stats));
     SBH_LAUNCHED();
     // runs whose group sort failed: their buckets one by one (usually none)
     uint32_t* nretry = t.small + 9;
@@ -2204,10 +2227,14 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
               flag_list_kernel<<<lblocks, 1024, 0, s>>>(t.retry_flag, nbid, t.bstart, t.bagg, t.list, t.offs, nretry,
                                                         t.small + 10));
     SBH_LAUNCHED();
+    SBH_TIMED("learned_retry_rec", s,
+              run_records_kernel<<<lblocks, 1024, 0, s>>>(t.list, nretry, 1, nbid, t.bstart, t.heavy_bucket_bits,
+                                                          t.runrec));
+    SBH_LAUNCHED();
     SBH_TIMED("learned_bucket_retry", s,
-              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, nbid,
-                                                                    t.heavy_bucket_bits, t.list, nretry, 1,
-                                                                    t.small + 8, t.ov_flag, t.retry_flag, t.stats));
+              bucket_sort_kernel<<<num_sms(), kBThreads, smem, s>>>(d_keys_out, d_ptrs_out, t.bstart, t.runrec,
+                                                                    nretry, t.small + 8, t.ov_flag, t.retry_flag,
+                                                                    t.stats));
     SBH_LAUNCHED();
     SBH_TIMED("learned_overflow_count", s,
               flag_count_kernel<<<lblocks, 1024, 0, s>>>(t.ov_flag, nbid, t.bstart, t.bagg));
