@@ -131,6 +131,10 @@ int sbh_window_ranges(const void* d_ts, int ts_bytes, uint64_t n, const uint64_t
  * Optional by-products (pass NULL to skip):
  *   d_key_or   one uint64: bitwise OR of the n keys (significant bits).
  *   d_samples  ceil(n / sample_stride) keys: d_samples[j] = d_keys[j*stride].
+ * With d_keys and d_ptrs both NULL (and d_key_or NULL) only the samples are
+ * written, read straight from the column: the sample a learned sort of the
+ * column trains on when the sort reads the column itself (see
+ * sbh_kpa_sort).
  * No scratch. */
 int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uint64_t* d_keys, uint32_t* d_ptrs,
                     uint64_t* d_key_or, uint64_t* d_samples, uint64_t sample_stride, void* stream);
@@ -188,6 +192,10 @@ int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n,
  * Extract makes them); in general ties keep input order.
  * In/out: (d_keys_in, d_ptrs_in) -> (d_keys_out, d_ptrs_out), n pairs,
  * n < 2^32.  The output may alias the input (in-place sort).
+ * d_ptrs_in may be NULL (not in place): input row i's ptr is then i.  A
+ * resident key column is sorted this way without an Extract pass: the first
+ * digit pass reads the column and makes each ptr from its row number, and
+ * the output is what Extract (row_begin 0) followed by this sort gives.
  * Scratch: about 12 n bytes plus 2 MiB (the sizing call gives the exact figure). */
 int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out, uint32_t* d_ptrs_out,
                  uint64_t n, void* d_scratch, size_t* scratch_bytes, void* stream);
@@ -432,20 +440,27 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * sort of every bucket of at most SBH_LEARNED_CAPACITY rows and more than one
  * key, and the plain radix sort for the rows of larger buckets.  Every step
  * is stable, so the output is identical to sbh_kpa_sort's for any ptrs (ties
- * keep their input order); input and output must not alias.  Like every call
+ * keep their input order); input and output must not alias.  d_ptrs_in may
+ * be NULL, as for sbh_kpa_sort: row i's ptr is i (the key column sorted
+ * without an Extract pass; train on the column's samples, see
+ * sbh_kpa_extract).  Like every call
  * here it only queues work on `stream`: the bucket count, the heavy keys in
  * use and the number of rows left to the plain radix sort are settled on the
  * device.  (When every bucket id fits in 16 bits, the ids travel with the
  * rows; if the model's heavy keys would push ids past that, only the
  * smallest of them keep a bucket of their own.)
+ * Consecutive buckets of at most SBH_LEARNED_CAPACITY rows together are
+ * sorted in shared memory as one run.
  * d_stats (nullable, device, SBH_LEARNED_STATS uint64 values, written by
  * the call's last kernel): bucket ids, heavy keys used, buckets sorted in
- * shared memory, one-key buckets, heavy buckets, overflow buckets, overflow
- * rows, largest bucket, buckets sorted by radix passes in shared memory
- * (their sub-buckets were too uneven for the counting placement) and their
- * rows, and wide buckets and their rows (too uneven, with a key range wider
- * than 2^40: they join the overflow rows in the plain radix sort, cheaper
- * than six or more passes in shared memory).
+ * shared memory, one-key buckets (in runs of one key), heavy buckets,
+ * overflow buckets, overflow rows, largest bucket, buckets sorted by radix
+ * passes in shared memory (their runs were too uneven for the counting
+ * placement) and their rows, and wide buckets and their rows (too uneven,
+ * with a key range wider than 2^40, and a repeated key sharing its 16-bit
+ * group of the key with another key even in a run of its bucket alone: they
+ * join the overflow rows in the plain radix sort, cheaper than six or more
+ * passes in shared memory).
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
                          uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* d_stats, void* d_scratch,

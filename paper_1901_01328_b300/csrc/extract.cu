@@ -72,6 +72,13 @@ __global__ void __launch_bounds__(256) extract_kernel(const uint64_t* __restrict
     }
 }
 
+// Only the sample: samples[j] = src[j * stride].
+__global__ void __launch_bounds__(256) sample_kernel(const uint64_t* __restrict__ src, uint32_t m, uint32_t stride,
+                                                      uint64_t* __restrict__ samples) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) samples[j] = __ldg(reinterpret_cast<const unsigned long long*>(src) + (uint64_t)j * stride);
+}
+
 // ---------------------------------------------------------------- Extract of many windows
 // Row r of window w (offsets[w] <= r < offsets[w + 1]) becomes the pair
 // ((w << wshift) | key_col[r], r).  The window of a row is found by binary
@@ -299,7 +306,11 @@ int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uin
         if (d_key_or) SBH_CUDA(cudaMemsetAsync(d_key_or, 0, sizeof(uint64_t), as_stream(stream)));
         return SBH_OK;
     }
-    if (!key_col || !d_keys || !d_ptrs) { set_error("null pointer"); return SBH_EINVAL; }
+    const bool sample_only = !d_keys && !d_ptrs;
+    if (!key_col || (!sample_only && (!d_keys || !d_ptrs)) || (sample_only && (!d_samples || d_key_or))) {
+        set_error("null pointer");
+        return SBH_EINVAL;
+    }
     if (row_begin + n > 0xFFFFFFFFull || row_begin + n < row_begin) {
         set_error("row_begin + n must be < 2^32 with 32-bit pointers");
         return SBH_EINVAL;
@@ -310,6 +321,14 @@ int sbh_kpa_extract(const uint64_t* key_col, uint64_t row_begin, uint64_t n, uin
     if (rc) return rc;
     const uint64_t* src = col + row_begin;
     cudaStream_t s = as_stream(stream);
+    if (sample_only) {
+        const uint64_t m = (n + sample_stride - 1) / sample_stride;
+        SBH_TIMED("extract_sample", s,
+                  sample_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(src, (uint32_t)m, (uint32_t)sample_stride,
+                                                                          d_samples));
+        SBH_LAUNCHED();
+        return SBH_OK;
+    }
     if (d_key_or) SBH_CUDA(cudaMemsetAsync(d_key_or, 0, sizeof(uint64_t), s));
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(d_keys) |
                        reinterpret_cast<uintptr_t>(d_ptrs)) & 15) == 0;

@@ -2151,7 +2151,7 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
         if (d_stats) SBH_CUDA(cudaMemsetAsync(d_stats, 0, SBH_LEARNED_STATS * sizeof(uint64_t), s));
         return SBH_OK;
     }
-    if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out || !d_model) { set_error("null pointer"); return SBH_EINVAL; }
+    if (!d_keys_in || !d_keys_out || !d_ptrs_out || !d_model) { set_error("null pointer"); return SBH_EINVAL; }
     if (d_keys_in == d_keys_out) { set_error("the learned sort needs distinct input and output buffers"); return SBH_EINVAL; }
     SortLearnedScratch t = learned_carve(d_scratch, n);
     const Model* model = static_cast<const Model*>(d_model);

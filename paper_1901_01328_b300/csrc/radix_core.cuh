@@ -57,7 +57,7 @@ struct Plan {
 
 struct Buffers {
     const uint64_t* in_k;
-    const uint32_t* in_p;
+    const uint32_t* in_p;  // null: input row i's ptr is i (a key column sorted without an extract)
     uint64_t* tmp_k;
     uint32_t* tmp_p;
     uint64_t* out_k;
@@ -356,9 +356,9 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
 
     auto issue = [&](int b, uint32_t t) {  // thread 0 only
         if (t < ntiles && bulk_ok && t < nfull) {
-            mbar_expect_tx(&sm.mbar[b], kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
+            mbar_expect_tx(&sm.mbar[b], kTile * (sizeof(uint64_t) + (in_p ? sizeof(uint32_t) : 0)));
             bulk_load(sm.keys[b], in_k + (size_t)t * kTile, kTile * sizeof(uint64_t), &sm.mbar[b]);
-            bulk_load(sm.ptrs[b], in_p + (size_t)t * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
+            if (in_p) bulk_load(sm.ptrs[b], in_p + (size_t)t * kTile, kTile * sizeof(uint32_t), &sm.mbar[b]);
         }
     };
 
@@ -395,7 +395,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         } else {
             for (uint32_t s = tid; s < valid; s += kThreads) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
-                sm.ptrs[b][s] = ld_stream(in_p + base + s);
+                if (in_p) sm.ptrs[b][s] = ld_stream(in_p + base + s);
             }
         }
         if (__syncthreads_or(expired)) {
@@ -415,7 +415,7 @@ onesweep_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
         for (int j = 0; j < kIpt; ++j) {
             const uint32_t s = wofs + j * 32;
             k[j] = sm.keys[b][s];
-            p[j] = sm.ptrs[b][s];
+            p[j] = in_p ? sm.ptrs[b][s] : base + s;
         }
 
         // ---- warp multisplit: rank of each key among equal digits of its warp.
@@ -540,7 +540,7 @@ __global__ void copy_kernel(Buffers buf, uint32_t n, const Plan* __restrict__ pl
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         buf.out_k[i] = sk[i];
-        buf.out_p[i] = sp[i];
+        buf.out_p[i] = sp ? sp[i] : i;
     }
 }
 
@@ -764,10 +764,10 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     auto bulk_tile = [&](uint32_t i) { return bulk_ok && lo + (i + 1) * TILE <= hi; };
     auto issue = [&](int b, uint32_t i) {  // thread 0 only
         if (i < ntl && bulk_tile(i)) {
-            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + sizeof(uint32_t)) +
+            mbar_expect_tx(&sm.mbar[b], TILE * (sizeof(uint64_t) + (in_p ? sizeof(uint32_t) : 0)) +
                                             (full_ids ? TILE * sizeof(uint16_t) : (walk ? TILE : 0)));
             bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b]);
-            bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
+            if (in_p) bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
             if (full_ids) bulk_load(sm.vals[b], in_ids + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
             if (walk) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE, &sm.mbar[b]);
         }
@@ -838,7 +838,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         } else {
             for (uint32_t s = tid; s < valid; s += THREADS) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
-                sm.ptrs[b][s] = ld_stream(in_p + base + s);
+                if (in_p) sm.ptrs[b][s] = ld_stream(in_p + base + s);
                 if (full_ids) sm.vals[b][s] = in_ids[base + s];
                 if (walk) reinterpret_cast<uint8_t*>(sm.vals[b])[s] = in_v[base + s];
             }
@@ -874,7 +874,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
 #pragma unroll
             for (int j = 0; j < kIt; ++j) {
                 k[j] = kb[wofs + j * 32];
-                p[j] = pb[wofs + j * 32];
+                p[j] = in_p ? pb[wofs + j * 32] : base + wofs + j * 32;
                 if (kCarry) cv[j] = walk ? reinterpret_cast<const uint8_t*>(vb)[wofs + j * 32] : vb[wofs + j * 32];
             }
             if constexpr (kCarry) {
@@ -1181,7 +1181,7 @@ int sort_by_value(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, u
                       n_scat = t + "_scatter", n_one = t + "_onesweep", n_copy = t + "_copy";
     if (n == 0) return SBH_OK;
     const int in_place = (in_k == out_k);
-    if (in_place != (in_p == out_p)) {
+    if (in_place != (in_p == out_p) || (in_place && !in_p)) {
         set_error("an in-place sort needs both keys and ptrs aliased");
         return SBH_EINVAL;
     }

@@ -17,7 +17,8 @@ extern "C" int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in
     int rc = scratch_check(d_scratch, scratch_bytes, radix_sort_scratch(n), &done);
     if (rc || done) return rc;
     if (n == 0) return SBH_OK;
-    if (!d_keys_in || !d_ptrs_in || !d_keys_out || !d_ptrs_out) { set_error("null pointer"); return SBH_EINVAL; }
+    if (!d_keys_in || !d_keys_out || !d_ptrs_out) { set_error("null pointer"); return SBH_EINVAL; }
+    if (!d_ptrs_in && d_keys_in == d_keys_out) { set_error("row-number ptrs need a separate output"); return SBH_EINVAL; }
     return sort_by_value(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, d_scratch, as_stream(stream), RadixValue{},
                          kPositions);
 }

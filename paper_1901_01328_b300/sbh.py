@@ -416,10 +416,21 @@ def extract(key_col, row_begin=0, n=None, device="cuda", sample_stride=0):
     return keys, ptrs
 
 
+def sample(key_col, stride, row_begin=0, n=None):
+    """Every stride-th key of rows [row_begin, row_begin + n), read straight
+    from the column (no Extract)."""
+    if n is None:
+        n = key_col.numel() - row_begin
+    samples = _u64((n + stride - 1) // stride, key_col.device)
+    sbh_kpa_extract(key_col, row_begin, n, None, None, None, samples, stride)
+    return samples
+
+
 def sort(keys, ptrs, out=None):
-    """Sorted copy (or into out=(keys_out, ptrs_out), which may alias the input)."""
+    """Sorted copy (or into out=(keys_out, ptrs_out), which may alias the
+    input).  ptrs=None: keys is a key column, row i's ptr is i (no Extract)."""
     if out is None:
-        out = (torch.empty_like(keys), torch.empty_like(ptrs))
+        out = (torch.empty_like(keys), _u32(keys.numel(), keys.device) if ptrs is None else torch.empty_like(ptrs))
     sbh_kpa_sort(keys, ptrs, out[0], out[1])
     return out
 
@@ -547,8 +558,9 @@ def model_params(model):
 
 
 def sort_learned(keys, ptrs, model):
-    """Sorted copy and the statistics as a dict (synchronises to read them)."""
-    out = (torch.empty_like(keys), torch.empty_like(ptrs))
+    """Sorted copy and the statistics as a dict (synchronises to read them).
+    ptrs=None: keys is a key column, row i's ptr is i (no Extract)."""
+    out = (torch.empty_like(keys), _u32(keys.numel(), keys.device) if ptrs is None else torch.empty_like(ptrs))
     stats = torch.zeros(len(LEARNED_STATS), dtype=torch.uint64, device=keys.device)
     sbh_kpa_sort_learned(keys, ptrs, out[0], out[1], model, stats)
     return out[0], out[1], stats_dict(stats)

@@ -66,6 +66,14 @@ def test_host_side_argument_errors(L):
     # scratch_bytes missing
     assert lib.sbh_group_reduce(None, None, 10, None, 8, None, None, None, 0, None, None, None, None) == L.SBH_EINVAL
     assert lib.sbh_kpa_extract(fake, (1 << 32) - 5, 10, fake, fake, None, None, 0, None) == L.SBH_EINVAL
+    # a key column sorted without an Extract (ptrs_in NULL) cannot be sorted in place
+    need = ctypes.c_size_t(0)
+    assert lib.sbh_kpa_sort(None, None, None, None, 100_000, None, ctypes.byref(need), None) == L.SBH_OK
+    assert lib.sbh_kpa_sort(fake, None, fake, fake, 100_000, fake, ctypes.byref(need), None) == L.SBH_EINVAL
+    # Extract: keys and ptrs both or neither; samples only, without the OR
+    assert lib.sbh_kpa_extract(fake, 0, 10, None, fake, None, None, 0, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract(fake, 0, 10, None, None, None, None, 0, None) == L.SBH_EINVAL
+    assert lib.sbh_kpa_extract(fake, 0, 10, None, None, fake, fake, 2, None) == L.SBH_EINVAL
     assert lib.sbh_window_ranges(fake, 3, 10, fake, 5, 2, fake, fake, None) == L.SBH_EINVAL
 
 

@@ -176,6 +176,24 @@ def test_learned_sort_equals_plain_sort(S, n, kind, start):
         assert stats["bucket_ids"] > 256
 
 
+@pytest.mark.parametrize("n,kind", [(1, "mixed"), (4097, "mixed"), (3_000_017, "mixed"), (2_000_003, "smallkeys"),
+                                    (2_100_000, "equal")])
+def test_learned_sort_of_a_key_column_without_extract(S, n, kind):
+    # ptrs_in = None: the learned sort reads the key column itself and row
+    # i's ptr is i; it trains on the column's samples (no Extract at all)
+    if kind == "mixed":
+        col = gen.mixed_keys(n, seed=8)
+    elif kind == "smallkeys":
+        col = gen.uniform(8, 3, n, 0, 4096, np.uint64)
+    else:
+        col = np.full(n, 777, dtype=np.uint64)
+    d = cuda(col)
+    model, _ = S.learned_train(S.sample(d, 100), n, None, steps=40, batch=4096, lr=3e-4)
+    sk, sp, _ = S.sort_learned(d, None, model)
+    ok, op = oracle.sort(*oracle.extract(col, 0, n))
+    assert same(sk, ok) and same(sp, op)
+
+
 @pytest.mark.parametrize("hashed", [False, True])
 def test_learned_sort_mixed_keys_32m_and_trained_vs_untrained(S, hashed):
     n = 32_000_000
@@ -217,22 +235,24 @@ def test_learned_sort_keeps_input_order_of_ties(S, ptr_kind):
 
 @pytest.mark.parametrize("hashed", [False, True])
 def test_learned_sort_headline_window_256m(S, hashed):
-    # the benchmark's exact step at full size: 256M mixed keys, extract with
-    # the 1% sample, quantile start, 40 Adam steps of 4096 rows at lr 3e-4,
-    # then the learned sort; its output equals the plain sort's and satisfies
-    # every sorted-KPA invariant (bit-exact parity with the oracle at this
-    # size is out of the oracle's reach; sampled ranks are checked below)
+    # the benchmark's exact step at full size: 256M mixed keys, the 1%
+    # sample read from the column, quantile start, 40 Adam steps of 4096 rows
+    # at lr 3e-4, then the learned sort of the key column (the extract fused
+    # into its first pass); its output equals an explicit extract followed by
+    # the plain sort and satisfies every sorted-KPA invariant (bit-exact
+    # parity with the oracle at this size is out of the oracle's reach;
+    # sampled ranks are checked below)
     from tests.gpu_util import sorted_kpa_on_device
     n = 256_000_000
     col_h = torch.empty(n, dtype=torch.uint64)
     gen.mixed_keys(n, out=col_h.numpy(), hashed=hashed)
     col = col_h.cuda()
     del col_h
-    keys, ptrs, _, samples = S.extract(col, 0, n, sample_stride=100)
-    model, _ = S.learned_train(samples, n, None, steps=40, batch=4096, lr=3e-4)
-    lk, lp, stats = S.sort_learned(keys, ptrs, model)
+    model, _ = S.learned_train(S.sample(col, 100), n, None, steps=40, batch=4096, lr=3e-4)
+    lk, lp, stats = S.sort_learned(col, None, model)
     assert S.sync_status() == S.SBH_OK
     assert stats["bucket_ids"] > 256 and stats["overflow_rows"] < 0.05 * n
+    keys, ptrs = S.extract(col, 0, n)
     pk, pp = S.sort(keys, ptrs)
     assert torch.equal(lk, pk) and torch.equal(lp, pp)
     del pk, pp, keys, ptrs
@@ -247,10 +267,13 @@ def test_learned_sort_headline_window_256m(S, hashed):
         assert below == int(i)
 
 
-def test_learned_step_replays_as_a_cuda_graph(S):
+@pytest.mark.parametrize("fused", [False, True])
+def test_learned_step_replays_as_a_cuda_graph(S, fused):
     # extract + training + learned sort + per-key count queue their work
     # without host synchronisation, so the whole step is captured once and
     # replayed; every replay equals the plain sort and the eager count
+    # (fused: the benchmark's step, the sample read from the column and the
+    # sort reading the column itself)
     n = 3_000_017
     col = cuda(gen.mixed_keys(n, seed=17))
     keys = torch.empty(n, dtype=torch.uint64, device="cuda")
@@ -266,9 +289,12 @@ def test_learned_step_replays_as_a_cuda_graph(S):
     tscr = {}
 
     def step():
-        S.sbh_kpa_extract(col, 0, n, keys, ptrs, None, samples, 100)
+        if fused:
+            S.sbh_kpa_extract(col, 0, n, None, None, None, samples, 100)
+        else:
+            S.sbh_kpa_extract(col, 0, n, keys, ptrs, None, samples, 100)
         tscr["t"] = S.sbh_learned_train(samples, n, None, 40, 4096, 3e-4, model)
-        S.sbh_kpa_sort_learned(keys, ptrs, sk, sp, model, st, scratch=lscr)
+        S.sbh_kpa_sort_learned(col if fused else keys, None if fused else ptrs, sk, sp, model, st, scratch=lscr)
         S.sbh_group_reduce(sk, None, None, ok_, oc_, None, n, nk, scratch=rscr)
 
     side = torch.cuda.Stream()

@@ -73,6 +73,28 @@ def _sort_case(kind, n, seed=1):
     raise ValueError(kind)
 
 
+@pytest.mark.parametrize("kind,n,offset", [("full64", 3 * 4096 + 5, 0), ("mixed", 100_003, 1), ("equal", 10_000, 0),
+                                           ("highbyte", 4097, 0), ("mixed", (1 << 23) + 3, 0),
+                                           ("mixed", (1 << 23) + 4099, 1)])
+def test_sort_key_column_without_extract(S, kind, n, offset):
+    # ptrs_in = None: the sort reads the key column and row i's ptr is i,
+    # as an Extract of the column would make it; offset 1 starts the column
+    # 8 bytes past a 16-byte boundary (no bulk copies: plain loads)
+    col = _sort_case(kind, n + offset)
+    d = cuda(col)[offset:]
+    sk, sp = S.sort(d, None)
+    ok, op = oracle.sort(*oracle.extract(col[offset:], 0, n))
+    assert same(sk, ok) and same(sp, op)
+
+
+def test_extract_samples_only(S):
+    n, stride = 1_000_003, 100
+    col = gen.mixed_keys(n, seed=3)
+    _, _, _, smp = S.extract(cuda(col), 7, n - 7, sample_stride=stride)
+    assert same(S.sample(cuda(col), stride, 7, n - 7), smp)
+    assert same(smp, col[7::stride])
+
+
 @pytest.mark.parametrize("kind", ["uniform20", "mixed", "equal", "extremes", "highbyte", "full64"])
 @pytest.mark.parametrize("n", [0, 1, 2, 4095, 4096, 4097, 100_003])
 def test_sort_parity(S, kind, n):
