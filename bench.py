@@ -743,8 +743,10 @@ def early_aggregation_rows(load=2.5e8, seed_off=5):
 # ------------------------------------------------------------------ per-row measurements
 def row_suite(peak):
     """Each remaining row of the path on its workload shape: device time by
-    CUDA events (median of 5 after 2 warm-ups), algorithmic GB/s against the
-    HBM peak, and the oracle on the same input (one host thread)."""
+    CUDA events (the call captured in a CUDA graph, the median of 9 replays,
+    each after a 256 MB write that flushes L2: device time from HBM, without
+    the host's per-call work), algorithmic GB/s against the HBM peak, and the
+    oracle on the same input (one host thread)."""
     import torch
 
     import gen
@@ -754,16 +756,34 @@ def row_suite(peak):
     dev = torch.device("cuda")
     out = {}
 
-    def dev_ms(fn, reps=5):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # twice the L2
+
+    def dev_ms(fn, reps=9):
+        """Device time of one call: the call (which only queues work) is
+        captured once in a CUDA graph and replayed, so that the host's
+        per-call work (argument marshalling, launches) is not timed; the
+        median of reps replays, each after an L2 flush."""
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            fn()  # first-call work (scratch sizing) outside the capture
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        g.replay()
+        torch.cuda.synchronize(dev)
         ts = []
-        for r in range(reps + 2):
+        for _ in range(reps):
+            flush.zero_()  # L2 flushed: every replay reads its inputs from HBM
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            fn()
+            g.replay()
             e1.record()
-            torch.cuda.synchronize()
-            if r >= 2:
-                ts.append(e0.elapsed_time(e1))
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        del g
         return statistics.median(ts)
 
     def cpu_ms(fn):
@@ -886,7 +906,7 @@ def row_suite(peak):
     oms = cpu_ms(lambda: oracle.median_unique(hk_, hp_, bv_))
     out["median_unique"] = entry(ms, None, "4M-row window, Zipf(1.0) keys: lower median and distinct values per key "
                                  "(two stable radix sorts)", oms)
-    del L, R, jl, jr, tsk, tsp, tv, tk, tn, tvo, tpo, mat, sel_k, sel_p, mk_, mm_, mu_, scr_sel, scr_mu
+    del L, R, jl, jr, tsk, tsp, tv, tk, tn, tvo, tpo, mat, sel_k, sel_p, mk_, mm_, mu_, scr_sel, scr_mu, flush
     out.update(pipeline_rows())
     return out
 
