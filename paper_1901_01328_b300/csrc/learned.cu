@@ -630,6 +630,11 @@ struct TrainArgs {
     uint32_t* status;
 };
 
+// (One thread-block cluster of 16 CTAs, 256 rows each, summing the
+// gradients through distributed shared memory between two cluster barriers
+// a step, measured slower: 0.66 against 0.60 ms for the bench's 40 steps of
+// 4096 rows; the gradient of 256 rows on one SM costs more than the two grid
+// barriers it saves.)
 __global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
