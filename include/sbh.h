@@ -394,7 +394,7 @@ int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs
 #define SBH_LEARNED_MODEL_BYTES 139264
 #define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
 #define SBH_LEARNED_MAX_HEAVY 16384 /* heavy keys a model holds */
-#define SBH_LEARNED_STATS 12
+#define SBH_LEARNED_STATS 13
 
 /* y[i] = MLP(x[i]) for i < m.  No scratch. */
 int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream);
@@ -460,7 +460,8 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * with a key range wider than 2^40, and a repeated key sharing its 16-bit
  * group of the key with another key even in a run of its bucket alone: they
  * join the overflow rows in the plain radix sort, cheaper than six or more
- * passes in shared memory).
+ * passes in shared memory), and the buckets of runs whose group sort failed
+ * and that were retried bucket by bucket.
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
                          uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* d_stats, void* d_scratch,

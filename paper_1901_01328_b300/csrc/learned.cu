@@ -1003,7 +1003,7 @@ static_assert(sizeof(BucketSmem) <= 232448, "bucket sort shared memory");
 
 struct BucketStats {
     unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
-        max_bucket, radix_buckets, radix_rows, wide_buckets, wide_rows;
+        max_bucket, radix_buckets, radix_rows, wide_buckets, wide_rows, retried_buckets;
 };
 
 // Persistent CTAs take runs of buckets (a run: one bucket, or consecutive
@@ -1427,6 +1427,7 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 if (tid == 0) {
                     if (nbk > 1) {
                         for (uint32_t x = b; x < bend; ++x) retry_flag[x] = 1;
+                        atomicAdd(&st->retried_buckets, (unsigned long long)nbk);
                     } else {
                         ov_flag[b] = 1;
                         atomicAdd(&st->wide_buckets, 1ull);
@@ -1656,6 +1657,7 @@ __global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const ui
     out[9] = st->radix_rows;
     out[10] = st->wide_buckets;
     out[11] = st->wide_rows;
+    out[12] = st->retried_buckets;
 }
 
 // ------------------------------------------------------------------ carried bucket ids
