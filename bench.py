@@ -240,7 +240,7 @@ def run_gpu(args):
     lsort_scratch = torch.empty(sbh.sort_learned_scratch_bytes(n), dtype=torch.uint8, device=dev)
     model = torch.zeros(sbh.LEARNED_MODEL_BYTES, dtype=torch.uint8, device=dev)
     out_keys = torch.empty(n, dtype=torch.uint64, device=dev)
-    out_counts = torch.empty(n, dtype=torch.uint64, device=dev)
+    out_counts = torch.empty(n, dtype=torch.uint32, device=dev)  # a count is below 2^32: 4 bytes hold it
     nkeys = torch.zeros(1, dtype=torch.uint64, device=dev)
     scr = {}
     stats_d = torch.zeros(len(sbh.LEARNED_STATS), dtype=torch.uint64, device=dev)
@@ -519,7 +519,7 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
     cols = [col, torch.empty_like(col)]
     outs = [outs0, tuple(torch.empty_like(t) for t in outs0)]
     res_k = torch.empty(n, dtype=torch.uint64).pin_memory()
-    res_c = torch.empty(n, dtype=torch.uint64).pin_memory()
+    res_c = torch.empty(n, dtype=outs0[1].dtype).pin_memory()
     nk_h = torch.empty(2, dtype=torch.uint64).pin_memory()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
@@ -543,7 +543,7 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
             res_k[:m].copy_(outs[b][0][:m], non_blocking=True)
             res_c[:m].copy_(outs[b][1][:m], non_blocking=True)
             ev_out[b].record(s_out)
-        d2h[0] += 8 + 16 * m
+        d2h[0] += 8 + (8 + outs[b][1].element_size()) * m
 
     barrier()
     t0 = time.perf_counter()

@@ -234,7 +234,8 @@ int sbh_kpa_merge_segments(int nseg, const uint64_t* d_a_keys, const uint32_t* d
  * KPA, find each contiguous key range, and coalesce a nonresident column
  * reached through the pointers).  For each distinct key, in key order:
  *   d_out_keys[j]   the key,
- *   d_out_counts[j] its number of records,
+ *   d_out_counts[j] its number of records, count_bytes = 4 or 8 bytes each
+ *                   (a count is below 2^32, so 4 bytes always hold it),
  *   d_out_sums[j]   the sum of d_val_col[ptr] over its records, modulo 2^64
  *                   (d_val_col has val_bytes = 4 or 8 bytes per row).
  * d_val_col == NULL (or d_out_sums == NULL) computes counts only and reads
@@ -242,7 +243,7 @@ int sbh_kpa_merge_segments(int nseg, const uint64_t* d_a_keys, const uint32_t* d
  * cap entries are written.  The input must be sorted by key.
  * Scratch: about 64 * (n / 4096) bytes. */
 int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
-                     int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
+                     int val_bytes, uint64_t* d_out_keys, void* d_out_counts, int count_bytes, uint64_t* d_out_sums,
                      uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes, void* stream);
 
 /* The keyed reduction above without the scratch argument, for callers that
@@ -262,8 +263,8 @@ int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n,
  * calls whose work overlaps on the GPU race and give wrong results, so
  * serialise them, e.g. on one stream. */
 int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
-                             int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
-                             uint64_t cap, uint64_t* d_nkeys, void* stream);
+                             int val_bytes, uint64_t* d_out_keys, void* d_out_counts, int count_bytes,
+                             uint64_t* d_out_sums, uint64_t cap, uint64_t* d_nkeys, void* stream);
 
 /* ---------------------------------------------------------------- A7
  * Top-K per key (Sec. 7, benchmark 1 "TopK Per Key": the K largest values of

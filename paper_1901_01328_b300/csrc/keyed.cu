@@ -258,11 +258,17 @@ __global__ void __launch_bounds__(1024) tile_scan_add_kernel(Agg* __restrict__ a
     if (i < ntiles) aggs[i] = agg_combine(bpre[blockIdx.x], excl);
 }
 
+// A count as 8 or 4 bytes (counts are below 2^32: n < 2^32).
+__device__ __forceinline__ void store_count(void* out, int count_bytes, uint64_t i, uint64_t c) {
+    if (count_bytes == 4) static_cast<uint32_t*>(out)[i] = static_cast<uint32_t>(c);
+    else static_cast<uint64_t*>(out)[i] = c;
+}
+
 template <int kVals>
 __global__ void __launch_bounds__(kThreads)
 emit_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs, uint32_t n,
             const void* __restrict__ val_col, const Agg* __restrict__ tile_prefix, uint32_t ntiles,
-            uint64_t* __restrict__ out_keys, uint64_t* __restrict__ out_counts, uint64_t* __restrict__ out_sums,
+            uint64_t* __restrict__ out_keys, void* __restrict__ out_counts, int count_bytes, uint64_t* __restrict__ out_sums,
             uint64_t cap, uint64_t* __restrict__ nkeys_out) {
     __shared__ Agg warp_agg[kWarps];
     const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
@@ -314,7 +320,7 @@ emit_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs
             const uint64_t pp = below ? p_src : prev_p;
             if (g < cap) out_keys[g] = k[j];
             if (g >= 1 && g - 1 < cap) {
-                if (out_counts) out_counts[g - 1] = row - pr;
+                if (out_counts) store_count(out_counts, count_bytes, g - 1, row - pr);
                 if (kVals && out_sums) out_sums[g - 1] = p_row - pp;
             }
         }
@@ -333,7 +339,7 @@ emit_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs
         if (total_heads) {
             const uint64_t g = total_heads - 1;
             if (g < cap) {
-                if (out_counts) out_counts[g] = n - prev_row;
+                if (out_counts) store_count(out_counts, count_bytes, g, n - prev_row);
                 if (kVals && out_sums) out_sums[g] = run_p - prev_p;
             }
         }
@@ -343,7 +349,7 @@ emit_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ptrs
 
 template <int kVals>
 int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* vals, uint64_t* ok,
-                 uint64_t* oc, uint64_t* os, uint64_t cap, uint64_t* nkeys, void* scratch, cudaStream_t s) {
+                 void* oc, int cb, uint64_t* os, uint64_t cap, uint64_t* nkeys, void* scratch, cudaStream_t s) {
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     Carver c(scratch);
     Agg* aggs = c.take<Agg>(ntiles);
@@ -363,7 +369,7 @@ int launch_keyed(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const v
     }
     SBH_LAUNCHED();
     SBH_TIMED("keyed_emit", s,
-              emit_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs, ntiles, ok, oc, os,
+              emit_kernel<kVals><<<ntiles, kThreads, 0, s>>>(keys, ptrs, (uint32_t)n, vals, aggs, ntiles, ok, oc, cb, os,
                                                              cap, nkeys));
     SBH_LAUNCHED();
     return SBH_OK;
@@ -381,9 +387,9 @@ size_t keyed_scratch(uint64_t n) {
 }  // namespace sbh
 
 extern "C" int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n, const void* d_val_col,
-                                int val_bytes, uint64_t* d_out_keys, uint64_t* d_out_counts, uint64_t* d_out_sums,
-                                uint64_t cap, uint64_t* d_nkeys, void* d_scratch, size_t* scratch_bytes,
-                                void* stream) {
+                                int val_bytes, uint64_t* d_out_keys, void* d_out_counts, int count_bytes,
+                                uint64_t* d_out_sums, uint64_t cap, uint64_t* d_nkeys, void* d_scratch,
+                                size_t* scratch_bytes, void* stream) {
     using namespace sbh;
     clear_error();
     if (n > 0xFFFFFFFFull) { set_error("n must be < 2^32"); return SBH_EINVAL; }
@@ -397,13 +403,19 @@ extern "C" int sbh_group_reduce(const uint64_t* d_keys, const uint32_t* d_ptrs, 
         return SBH_OK;
     }
     if (!d_keys || (cap && !d_out_keys)) { set_error("null pointer"); return SBH_EINVAL; }
+    if (d_out_counts && count_bytes != 4 && count_bytes != 8) { set_error("count_bytes must be 4 or 8"); return SBH_EINVAL; }
     const bool with_vals = d_val_col && d_out_sums;
     if (with_vals && val_bytes != 4 && val_bytes != 8) { set_error("val_bytes must be 4 or 8"); return SBH_EINVAL; }
     if (with_vals && !d_ptrs) { set_error("d_ptrs is NULL"); return SBH_EINVAL; }
-    if (!with_vals) return launch_keyed<0>(d_keys, d_ptrs, n, nullptr, d_out_keys, d_out_counts, nullptr, cap, d_nkeys, d_scratch, s);
+    const int cb = count_bytes;
+    if (!with_vals)
+        return launch_keyed<0>(d_keys, d_ptrs, n, nullptr, d_out_keys, d_out_counts, cb, nullptr, cap, d_nkeys,
+                               d_scratch, s);
     if (val_bytes == 8)
-        return launch_keyed<8>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, d_out_sums, cap, d_nkeys, d_scratch, s);
-    return launch_keyed<4>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, d_out_sums, cap, d_nkeys, d_scratch, s);
+        return launch_keyed<8>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, cb, d_out_sums, cap, d_nkeys,
+                               d_scratch, s);
+    return launch_keyed<4>(d_keys, d_ptrs, n, d_val_col, d_out_keys, d_out_counts, cb, d_out_sums, cap, d_nkeys,
+                           d_scratch, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,7 +465,7 @@ int noalloc_scratch(void** out) {
 
 extern "C" int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* d_ptrs, uint64_t n,
                                         const void* d_val_col, int val_bytes, uint64_t* d_out_keys,
-                                        uint64_t* d_out_counts, uint64_t* d_out_sums, uint64_t cap,
+                                        void* d_out_counts, int count_bytes, uint64_t* d_out_sums, uint64_t cap,
                                         uint64_t* d_nkeys, void* stream) {
     using namespace sbh;
     clear_error();
@@ -466,6 +478,6 @@ extern "C" int sbh_group_reduce_noalloc(const uint64_t* d_keys, const uint32_t* 
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     size_t bytes = kNoAllocBytes;
-    return sbh_group_reduce(d_keys, d_ptrs, n, d_val_col, val_bytes, d_out_keys, d_out_counts, d_out_sums, cap,
-                            d_nkeys, scratch, &bytes, stream);
+    return sbh_group_reduce(d_keys, d_ptrs, n, d_val_col, val_bytes, d_out_keys, d_out_counts, count_bytes,
+                            d_out_sums, cap, d_nkeys, scratch, &bytes, stream);
 }

@@ -581,7 +581,7 @@ MuScratch mu_carve(void* base, uint64_t n) {
     t.nseg = c.take<uint64_t>(1);
     size_t sb = 0, rb = 0;
     sbh_kpa_sort(nullptr, nullptr, nullptr, nullptr, n, nullptr, &sb, nullptr);
-    sbh_group_reduce(nullptr, nullptr, n, nullptr, 4, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &rb, nullptr);
+    sbh_group_reduce(nullptr, nullptr, n, nullptr, 4, nullptr, nullptr, 8, nullptr, 0, nullptr, nullptr, &rb, nullptr);
     t.sort_bytes = sb;
     t.red_bytes = rb;
     t.sort_scr = c.take<char>(sb);
@@ -611,7 +611,7 @@ int mu_run(const uint64_t* keys, const uint32_t* ptrs, uint64_t n, const void* c
     SBH_LAUNCHED();
     // distinct values per key: the keyed sum of the flags (also writes the keys)
     size_t rb = t.red_bytes;
-    rc = sbh_group_reduce(t.k3, t.iota, n, t.f, 4, ok, t.counts, ouni, cap, nkeys, t.red_scr, &rb, s);
+    rc = sbh_group_reduce(t.k3, t.iota, n, t.f, 4, ok, t.counts, 8, ouni, cap, nkeys, t.red_scr, &rb, s);
     if (rc) return rc;
     // the runs of the re-ordered KPA, then each run's middle row
     SBH_CUDA(cudaMemsetAsync(t.small, 0, 2 * sizeof(uint32_t), s));

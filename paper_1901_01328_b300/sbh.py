@@ -71,8 +71,8 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_split_ts": ([vp, vp, u64, i64, u64, u64, u32, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort": ([vp, vp, vp, vp, u64, vp, sz, vp], i32),
         "sbh_kpa_merge": ([i32, vp, vp, vp, vp, vp, vp, sz, vp], i32),
-        "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp, sz, vp], i32),
-        "sbh_group_reduce_noalloc": ([vp, vp, u64, vp, i32, vp, vp, vp, u64, vp, vp], i32),
+        "sbh_group_reduce": ([vp, vp, u64, vp, i32, vp, vp, i32, vp, u64, vp, vp, sz, vp], i32),
+        "sbh_group_reduce_noalloc": ([vp, vp, u64, vp, i32, vp, vp, i32, vp, u64, vp, vp], i32),
         "sbh_topk": ([vp, vp, u64, vp, i32, i32, vp, vp, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_join": ([vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, sz, vp], i32),
         "sbh_mlp_forward": ([vp, vp, u64, vp, vp], i32),
@@ -248,8 +248,8 @@ def sort_scratch_bytes(n: int) -> int:
 
 def group_reduce_scratch_bytes(n: int, val_bytes: int = 8) -> int:
     nbytes = ctypes.c_size_t(0)
-    _check(_lib.sbh_group_reduce(None, None, n, None, val_bytes, None, None, None, 0, None, None, ctypes.byref(nbytes),
-                                 None), "sbh_group_reduce")
+    _check(_lib.sbh_group_reduce(None, None, n, None, val_bytes, None, None, 8, None, 0, None, None,
+                                 ctypes.byref(nbytes), None), "sbh_group_reduce")
     return nbytes.value
 
 
@@ -308,8 +308,10 @@ def sbh_join_segments(L, l_off, R, r_start, r_len, out_l, out_r, cap, npairs, se
 
 
 def sbh_group_reduce(keys, ptrs, vals, out_keys, out_counts, out_sums, cap, nkeys, scratch=None, stream=None):
+    """out_counts: uint64 or uint32 (each count is below 2^32)."""
     vb = 0 if vals is None else vals.element_size()
-    args = (_p(keys), _p(ptrs), keys.numel(), _p(vals), vb, _p(out_keys), _p(out_counts), _p(out_sums), cap,
+    cb = 8 if out_counts is None else out_counts.element_size()
+    args = (_p(keys), _p(ptrs), keys.numel(), _p(vals), vb, _p(out_keys), _p(out_counts), cb, _p(out_sums), cap,
             _p(nkeys))
     if scratch is None:
         return _scratch(_lib.sbh_group_reduce, args, (_stream(stream),), "sbh_group_reduce", keys.device)

@@ -43,7 +43,7 @@ def test_scratch_size_queries_need_no_gpu(L):
     assert lib.sbh_kpa_sort(None, None, None, None, 256_000_000, None, ctypes.byref(nb), None) == 0
     # ping-pong copy (12 B per pair) plus look-back records
     assert 256_000_000 * 12 <= nb.value < 256_000_000 * 12 + 200_000_000
-    for fn, args in ((lib.sbh_group_reduce, (None, None, 10_000, None, 8, None, None, None, 0, None)),
+    for fn, args in ((lib.sbh_group_reduce, (None, None, 10_000, None, 8, None, None, 8, None, 0, None)),
                      (lib.sbh_topk, (None, None, 10_000, None, 8, 3, None, None, None, None, 0, None)),
                      (lib.sbh_join, (None, None, 10_000, None, None, 10, None, None, 0, None))):
         nb = ctypes.c_size_t(0)
@@ -64,7 +64,7 @@ def test_host_side_argument_errors(L):
     small = ctypes.c_size_t(16)
     assert lib.sbh_kpa_sort(fake, fake, fake, fake, 100_000, fake, ctypes.byref(small), None) == L.SBH_ENOSPACE
     # scratch_bytes missing
-    assert lib.sbh_group_reduce(None, None, 10, None, 8, None, None, None, 0, None, None, None, None) == L.SBH_EINVAL
+    assert lib.sbh_group_reduce(None, None, 10, None, 8, None, None, 8, None, 0, None, None, None, None) == L.SBH_EINVAL
     assert lib.sbh_kpa_extract(fake, (1 << 32) - 5, 10, fake, fake, None, None, 0, None) == L.SBH_EINVAL
     # a key column sorted without an Extract (ptrs_in NULL) cannot be sorted in place
     need = ctypes.c_size_t(0)

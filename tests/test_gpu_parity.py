@@ -277,6 +277,26 @@ def test_group_count_runs_at_warp_range_boundaries(S, offset):
     assert same(gk, ok) and same(gc, oc) and int(oc.sum()) == n
 
 
+def test_group_reduce_four_byte_counts(S):
+    # counts written as uint32 equal the uint64 ones (every count is below 2^32)
+    n = 300_001
+    col = gen.mixed_keys(n, seed=13)
+    vals = gen.uniform(6, 6, n, 0, 0, np.uint64)
+    sk, sp = _sorted_kpa(S, col)
+    ok, oc, osum = oracle.group_sum_count(*_oracle_sorted(col), vals)
+    for with_vals in (False, True):
+        out_k = torch.zeros(n, dtype=torch.uint64, device="cuda")
+        out_c = torch.zeros(n, dtype=torch.uint32, device="cuda")
+        out_s = torch.zeros(n, dtype=torch.uint64, device="cuda") if with_vals else None
+        nk = torch.zeros(1, dtype=torch.uint64, device="cuda")
+        S.sbh_group_reduce(sk, sp, cuda(vals) if with_vals else None, out_k, out_c, out_s, n, nk)
+        m = int(host(nk)[0])
+        assert m == ok.size and same(out_k[:m], ok) and same(out_c[:m], oc.astype(np.uint32))
+        assert int(host(out_c)[m]) == 0  # nothing written past the last key
+        if with_vals:
+            assert same(out_s[:m], osum)
+
+
 def test_group_count_mixed_keys_16m(S):
     n = 16_000_000
     col = gen.mixed_keys(n)

@@ -38,7 +38,7 @@ def _run(S, sk, sp, vals, scratch_for_reference=False):
     vb = 8 if vals is None else vals.element_size()
     vp = None if vals is None else vals.data_ptr()
     sump = None if vals is None else osum.data_ptr()
-    args = [sk.data_ptr(), sp.data_ptr(), n, vp, vb, ok.data_ptr(), oc.data_ptr(), sump, n, nk.data_ptr()]
+    args = [sk.data_ptr(), sp.data_ptr(), n, vp, vb, ok.data_ptr(), oc.data_ptr(), 8, sump, n, nk.data_ptr()]
     if scratch_for_reference:
         nb = ctypes.c_size_t(0)
         assert lib.sbh_group_reduce(*args, None, ctypes.byref(nb), stream) == 0
@@ -87,7 +87,7 @@ def test_noalloc_rejects_rows_beyond_its_array(S):
     lib = S.lib()
     dummy = torch.empty(1, dtype=torch.uint64, device="cuda")
     p = dummy.data_ptr()
-    rc = lib.sbh_group_reduce_noalloc(p, p, (1 << 28) + 1, None, 8, p, p, None, 0, p,
+    rc = lib.sbh_group_reduce_noalloc(p, p, (1 << 28) + 1, None, 8, p, p, 8, None, 0, p,
                                       torch.cuda.current_stream().cuda_stream)
     assert rc == S.SBH_EINVAL
     assert b"at most" in lib.sbh_last_error()
