@@ -374,13 +374,16 @@ int sbh_join(const uint64_t* d_lkeys, const uint32_t* d_lptrs, uint64_t nl, cons
  * nseg + 1 non-decreasing values from 0), r_start and r_len (host, nseg
  * values) describe the segments; R segments may overlap.  *d_npairs and
  * d_seg_pairs[nseg] receive the total; only the first cap pairs are
- * written.  L below 2^32 rows.
+ * written (cap 0: only the counts).  reuse_counts != 0: the scratch holds
+ * the counts of an earlier call with the same inputs and segments (made
+ * with cap 0 to size the output), and only the pairs are written (the
+ * matches are not searched again).  L below 2^32 rows.
  * Scratch: about 8 bytes per L row plus 24 bytes per segment. */
 int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs, const uint64_t* l_off,
                       const uint64_t* d_rkeys, const uint32_t* d_rptrs, const uint64_t* r_start,
                       const uint64_t* r_len, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
-                      uint64_t* d_npairs, uint64_t* d_seg_pairs, void* d_scratch, size_t* scratch_bytes,
-                      void* stream);
+                      uint64_t* d_npairs, uint64_t* d_seg_pairs, int reuse_counts, void* d_scratch,
+                      size_t* scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------- A4
  * Learned MSD partition sort.  The paper has no learned component (its Sort

@@ -1,8 +1,12 @@
 // A8 Join of two KPAs sorted in (key, ptr) order: every (ptrL, ptrR) with
 // equal keys, in (key, ptrL, ptrR) order.
 //
-//   count  each row i of L finds its key's row range [lo, hi) in R by binary
-//          search; per-block sums of the match counts hi - lo.
+//   count  each row i of L finds its key's row range [lo, hi) in R; a thread
+//          takes kIpt consecutive rows of L, searches the first row's range
+//          by bisection and every later row's by galloping on from the
+//          previous row's range (the keys ascend, so a range starts where the
+//          previous one ended; with the windows' key densities a step or
+//          two); per-block sums of the match counts hi - lo.
 //   scan   one block scans the block sums; the grand total is the pair count.
 //   emit   each block rescans its rows' counts from its block offset; row i
 //          writes (ptrL[i], ptrR[lo + j]) for j < hi - lo.  Rows of L come in
@@ -36,6 +40,76 @@ __device__ __forceinline__ uint32_t upper_bound_key(const uint64_t* a, uint32_t 
     return lo;
 }
 
+// First i in [from, n) with a[i] >= v (or > v when kUpper), for a sorted
+// ascending and every a[i] with from <= i < the answer below (above) v:
+// doubling steps, then bisection of the last step.
+template <bool kUpper>
+__device__ __forceinline__ uint32_t gallop(const uint64_t* a, uint32_t n, uint32_t from, uint64_t v) {
+    uint32_t lo = from, hi = from, step = 1;
+    while (hi < n && (kUpper ? a[hi] <= v : a[hi] < v)) {
+        lo = hi + 1;
+        hi = (n - hi > step) ? hi + step : n;
+        step <<= 1;
+    }
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (kUpper ? a[mid] <= v : a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The R range [lo, hi) of every row of this thread's kIpt consecutive rows
+// of one sorted L segment set (the single-window join: one segment).
+// seg_of(i) returns the segment of row i; segments change only forward.
+__device__ __forceinline__ uint64_t count_rows(const uint64_t* __restrict__ lk, uint32_t nl, uint32_t i0,
+                                               const uint64_t* __restrict__ rk, const uint64_t* __restrict__ l_off,
+                                               const uint64_t* __restrict__ r_start,
+                                               const uint64_t* __restrict__ r_len, uint32_t nseg, uint32_t nr,
+                                               uint32_t* __restrict__ rlo, uint32_t* __restrict__ cnt) {
+    uint64_t local = 0;
+    uint32_t a = 0, seg_end = 0, lo = 0, hi = 0, n = 0, rs = 0;
+    const uint64_t* seg = rk;
+    uint64_t prevk = 0;
+    bool have = false;
+#pragma unroll
+    for (int t = 0; t < kIpt; ++t) {
+        const uint32_t i = i0 + t;
+        if (i >= nl) break;
+        const uint64_t k = lk[i];
+        if (!have || i >= seg_end) {  // the first row, or a row of a later segment
+            if (l_off) {
+                uint32_t x = have ? a : 0, y = nseg;  // last segment with l_off <= i
+                while (y - x > 1) {
+                    const uint32_t mid = (x + y) / 2;
+                    if (l_off[mid] <= i) x = mid;
+                    else y = mid;
+                }
+                a = x;
+                seg_end = a + 1 < nseg ? static_cast<uint32_t>(l_off[a + 1]) : nl;
+                rs = static_cast<uint32_t>(r_start[a]);
+                n = static_cast<uint32_t>(r_len[a]);
+            } else {
+                seg_end = nl;
+                rs = 0;
+                n = nr;
+            }
+            seg = rk + rs;
+            lo = lower_bound_key(seg, n, k);
+            hi = upper_bound_key(seg, lo, n, k);
+            have = true;
+        } else if (k != prevk) {  // k > prevk: its range starts at or after hi
+            lo = gallop<false>(seg, n, hi, k);
+            hi = gallop<true>(seg, n, lo, k);
+        }
+        prevk = k;
+        rlo[i] = rs + lo;
+        cnt[i] = hi - lo;
+        local += hi - lo;
+    }
+    return local;
+}
+
 __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane_id() == 0) red[threadIdx.x / 32] = v;
@@ -50,19 +124,8 @@ join_count_kernel(const uint64_t* __restrict__ lk, uint32_t nl, const uint64_t* 
                   uint32_t* __restrict__ rlo, uint32_t* __restrict__ cnt, uint64_t* __restrict__ bsum) {
     __shared__ uint64_t red[kThreads / 32];
     const uint32_t base = blockIdx.x * kTile;
-    uint64_t local = 0;
-#pragma unroll
-    for (int t = 0; t < kIpt; ++t) {
-        const uint32_t i = base + t * kThreads + threadIdx.x;
-        if (i < nl) {
-            const uint64_t k = lk[i];
-            const uint32_t lo = lower_bound_key(rk, nr, k);
-            const uint32_t hi = upper_bound_key(rk, lo, nr, k);
-            rlo[i] = lo;
-            cnt[i] = hi - lo;
-            local += hi - lo;
-        }
-    }
+    const uint64_t local =
+        count_rows(lk, nl, base + threadIdx.x * kIpt, rk, nullptr, nullptr, nullptr, 1, nr, rlo, cnt);
     const uint64_t t = block_sum(local, red);
     if (threadIdx.x == 0) bsum[blockIdx.x] = t;
 }
@@ -150,27 +213,8 @@ join_seg_count_kernel(const uint64_t* __restrict__ lk, uint32_t nl, const uint64
                       uint32_t* __restrict__ cnt, uint64_t* __restrict__ bsum) {
     __shared__ uint64_t red[kThreads / 32];
     const uint32_t base = blockIdx.x * kTile;
-    uint64_t local = 0;
-#pragma unroll
-    for (int t = 0; t < kIpt; ++t) {
-        const uint32_t i = base + t * kThreads + threadIdx.x;
-        if (i < nl) {
-            uint32_t a = 0, b = nseg;  // last segment with l_off <= i
-            while (b - a > 1) {
-                const uint32_t mid = (a + b) / 2;
-                if (l_off[mid] <= i) a = mid;
-                else b = mid;
-            }
-            const uint64_t k = lk[i];
-            const uint64_t* seg = rk + r_start[a];
-            const uint32_t n = static_cast<uint32_t>(r_len[a]);
-            const uint32_t lo = lower_bound_key(seg, n, k);
-            const uint32_t hi = upper_bound_key(seg, lo, n, k);
-            rlo[i] = static_cast<uint32_t>(r_start[a]) + lo;
-            cnt[i] = hi - lo;
-            local += hi - lo;
-        }
-    }
+    const uint64_t local =
+        count_rows(lk, nl, base + threadIdx.x * kIpt, rk, l_off, r_start, r_len, nseg, 0, rlo, cnt);
     const uint64_t t = block_sum(local, red);
     if (threadIdx.x == 0) bsum[blockIdx.x] = t;
 }
@@ -201,8 +245,8 @@ __global__ void join_seg_offsets_kernel(const uint64_t* __restrict__ l_off, uint
 extern "C" int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs, const uint64_t* l_off,
                                  const uint64_t* d_rkeys, const uint32_t* d_rptrs, const uint64_t* r_start,
                                  const uint64_t* r_len, uint32_t* d_out_l, uint32_t* d_out_r, uint64_t cap,
-                                 uint64_t* d_npairs, uint64_t* d_seg_pairs, void* d_scratch, size_t* scratch_bytes,
-                                 void* stream) {
+                                 uint64_t* d_npairs, uint64_t* d_seg_pairs, int reuse_counts, void* d_scratch,
+                                 size_t* scratch_bytes, void* stream) {
     using namespace sbh;
     clear_error();
     if (nseg < 1 || !l_off || !r_start || !r_len) { set_error("bad segment arrays"); return SBH_EINVAL; }
@@ -238,6 +282,15 @@ extern "C" int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32
     uint32_t* cnt = w.take<uint32_t>(nl);
     uint64_t* bsum = w.take<uint64_t>(nblocks + 1);
     uint64_t* segs = w.take<uint64_t>(3 * (size_t)nseg + 1);  // l_off (nseg + 1), r_start, r_len
+    if (reuse_counts) {  // the counts, scanned offsets and totals of an earlier call are in the scratch
+        if (cap) {
+            SBH_TIMED("join_emit", s,
+                      join_emit_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lptrs, (uint32_t)nl, d_rptrs, rlo, cnt,
+                                                                              bsum, d_out_l, d_out_r, cap));
+            SBH_LAUNCHED();
+        }
+        return SBH_OK;
+    }
     SBH_CUDA(cudaMemcpyAsync(segs, l_off, (nseg + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     SBH_CUDA(cudaMemcpyAsync(segs + nseg + 1, r_start, nseg * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     SBH_CUDA(cudaMemcpyAsync(segs + 2 * nseg + 1, r_len, nseg * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
@@ -253,9 +306,12 @@ extern "C" int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32
                                                                                     (uint32_t)nl, cnt, bsum, d_npairs,
                                                                                     d_seg_pairs));
     SBH_LAUNCHED();
-    SBH_TIMED("join_emit", s, join_emit_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lptrs, (uint32_t)nl, d_rptrs, rlo, cnt, bsum, d_out_l,
-                                                             d_out_r, cap));
-    SBH_LAUNCHED();
+    if (cap) {
+        SBH_TIMED("join_emit", s,
+                  join_emit_kernel<<<(unsigned)nblocks, kThreads, 0, s>>>(d_lptrs, (uint32_t)nl, d_rptrs, rlo, cnt,
+                                                                          bsum, d_out_l, d_out_r, cap));
+        SBH_LAUNCHED();
+    }
     return SBH_OK;
 }
 

@@ -191,29 +191,46 @@ def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride):
     rows = npanes * stride
     shift = 64 - sbh.window_bits(npanes)
     offs = (torch.arange(npanes + 1, dtype=torch.int64, device=dev) * stride).view(torch.uint64)
-    sides = []
-    for col in (lkey_col, rkey_col):
-        keys, ptrs = _u64(rows, dev), _u32(rows, dev)
-        sbh.sbh_kpa_extract(col, 0, rows, keys, ptrs)  # over the host link once when col is host memory
-        ck, cp, key_or = _u64(rows, dev), _u32(rows, dev), _u64(1, dev)
-        sbh.sbh_kpa_extract_windows(keys, offs, 0, rows, ck, cp, key_or)
-        if shift < 64 and int(key_or.item()) >> shift:
-            return None  # a key uses the pane bits: the loop schedule instead
-        sbh.sbh_kpa_sort(ck[:rows], cp[:rows], ck[:rows], cp[:rows])  # every pane sorted, pane after pane
-        sbh.sbh_kpa_keyswap(cp[:rows], keys, ck)                         # the plain keys back
-        del keys, ptrs
-        run_k, run_p, run_len, nruns = ck, cp, stride, npanes
-        gap = 1
-        while gap < per:
-            nnext = nruns - gap
-            ok, op = _u64(nnext * 2 * run_len, dev), _u32(nnext * 2 * run_len, dev)
-            a_start = [i * run_len for i in range(nnext)]
-            b_start = [(i + gap) * run_len for i in range(nnext)]
-            lens = [run_len] * nnext
-            sbh.sbh_kpa_merge_segments((run_k, run_p), (run_k, run_p), a_start, lens, b_start, lens, ok, op)
-            run_k, run_p, run_len, nruns = ok, op, 2 * run_len, nnext
-            gap *= 2
-        sides.append((run_k, run_p))
+    # the two sides on two streams: one side's columns cross the host link
+    # while the other side sorts and merges (no host synchronisation until
+    # both are queued)
+    main = torch.cuda.current_stream(dev)
+    streams = (main, torch.cuda.Stream(dev))
+    streams[1].wait_stream(main)
+    sides, key_ors = [], []
+    for col, st in zip((lkey_col, rkey_col), streams):
+        with torch.cuda.stream(st):
+            # the key column on the device: a host column crosses the link
+            # once, by DMA (a kernel reading page-locked memory measured
+            # 36 GB/s against the copy engines' ~50)
+            if col.is_cuda:
+                keys = col[:rows]
+            else:
+                keys = _u64(rows, dev)
+                keys.copy_(col[:rows], non_blocking=True)
+            ck, cp, key_or = _u64(rows, dev), _u32(rows, dev), _u64(1, dev)
+            sbh.sbh_kpa_extract_windows(keys, offs, 0, rows, ck, cp, key_or)
+            key_ors.append(key_or)
+            sbh.sbh_kpa_sort(ck[:rows], cp[:rows], ck[:rows], cp[:rows])  # every pane sorted, pane after pane
+            sbh.sbh_kpa_keyswap(cp[:rows], keys, ck)                         # the plain keys back
+            del keys
+            run_k, run_p, run_len, nruns = ck, cp, stride, npanes
+            gap = 1
+            while gap < per:
+                nnext = nruns - gap
+                ok, op = _u64(nnext * 2 * run_len, dev), _u32(nnext * 2 * run_len, dev)
+                a_start = [i * run_len for i in range(nnext)]
+                b_start = [(i + gap) * run_len for i in range(nnext)]
+                lens = [run_len] * nnext
+                sbh.sbh_kpa_merge_segments((run_k, run_p), (run_k, run_p), a_start, lens, b_start, lens, ok, op)
+                run_k, run_p, run_len, nruns = ok, op, 2 * run_len, nnext
+                gap *= 2
+            sides.append((run_k, run_p))
+    main.wait_stream(streams[1])
+    for t in (*sides[1], key_ors[1]):
+        t.record_stream(main)  # made on the second stream, read on the main one
+    if shift < 64 and any(int(o.item()) >> shift for o in key_ors):
+        return None  # a key uses the pane bits: the loop schedule instead
     (lk, lp), (rk, rp) = sides
     l_off = [w * window for w in range(nwin + 1)]
     r_start, r_len = l_off[:-1], [window] * nwin
@@ -222,7 +239,8 @@ def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride):
     scr = sbh.sbh_join_segments((lk, lp), l_off, (rk, rp), r_start, r_len, None, None, 0, npairs, seg)
     total = int(npairs.item())
     out_l, out_r = _u32(total, dev), _u32(total, dev)
-    sbh.sbh_join_segments((lk, lp), l_off, (rk, rp), r_start, r_len, out_l, out_r, total, npairs, seg, scratch=scr)
+    sbh.sbh_join_segments((lk, lp), l_off, (rk, rp), r_start, r_len, out_l, out_r, total, npairs, seg, scratch=scr,
+                          reuse_counts=True)
     off = seg[: nwin + 1].cpu().numpy().astype(np.int64)
     return JoinResults(out_l, out_r, off[:-1], off[1:]), list(range(nwin))
 

@@ -82,7 +82,7 @@ def _load() -> ctypes.CDLL:
         "sbh_kpa_partition": ([vp, vp, u64, vp, u64, vp, vp, vp, vp, sz, vp], i32),
         "sbh_copy_counted": ([vp, vp, i32, vp, u64, u64, vp], i32),
         "sbh_kpa_merge_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
-        "sbh_join_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
+        "sbh_join_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, i32, vp, sz, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -293,13 +293,15 @@ def sbh_kpa_merge_segments(a, b, a_start, a_len, b_start, b_len, keys_out, ptrs_
 
 
 def sbh_join_segments(L, l_off, R, r_start, r_len, out_l, out_r, cap, npairs, seg_pairs, scratch=None,
-                      stream=None):
+                      stream=None, reuse_counts=False):
     """L, R: (keys, ptrs) device tensors; l_off (nseg + 1), r_start, r_len:
-    host sequences; seg_pairs: device uint64 tensor of nseg + 1 entries."""
+    host sequences; seg_pairs: device uint64 tensor of nseg + 1 entries.
+    reuse_counts: scratch holds the counts of an earlier call (cap 0) with
+    the same inputs; only the pairs are written."""
     nseg = len(r_start)
     hold = [_host_u64(x) for x in (l_off, r_start, r_len)]
     args = (nseg, _p(L[0]), _p(L[1]), hold[0][1], _p(R[0]), _p(R[1]), hold[1][1], hold[2][1], _p(out_l), _p(out_r),
-            cap, _p(npairs), _p(seg_pairs))
+            cap, _p(npairs), _p(seg_pairs), 1 if reuse_counts else 0)
     if scratch is None:
         return _scratch(_lib.sbh_join_segments, args, (_stream(stream),), "sbh_join_segments", npairs.device)
     nbytes = ctypes.c_size_t(scratch.numel())

@@ -197,7 +197,8 @@ def test_merge_segments_parity():
         o += la + lb
 
 
-def test_join_segments_parity():
+@pytest.mark.parametrize("reuse", [False, True])
+def test_join_segments_parity(reuse):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1901_01328_b300 import sbh
@@ -226,7 +227,8 @@ def test_join_segments_parity():
     total = int(npairs.item())
     ol = torch.empty(max(1, total), dtype=torch.uint32, device="cuda")
     orr = torch.empty(max(1, total), dtype=torch.uint32, device="cuda")
-    sbh.sbh_join_segments(L, l_off, R, r_start, r_len, ol, orr, total, npairs, seg, scratch=scr)
+    # reuse: the pairs from the first call's counts, without searching again
+    sbh.sbh_join_segments(L, l_off, R, r_start, r_len, ol, orr, total, npairs, seg, scratch=scr, reuse_counts=reuse)
     so = seg.cpu().numpy().astype(np.int64)
     gl, gr = ol.cpu().numpy(), orr.cpu().numpy()
     assert so[0] == 0 and so[-1] == total
