@@ -235,7 +235,7 @@ def test_learned_sort_keeps_input_order_of_ties(S, ptr_kind):
 
 @pytest.mark.parametrize("hashed", [False, True])
 def test_learned_sort_headline_window_256m(S, hashed):
-    # the benchmark's exact step at full size: 256M mixed keys, the 1%
+    # the benchmark's exact step at full size: 256M mixed keys, the 0.25%
     # sample read from the column, quantile start, 40 Adam steps of 4096 rows
     # at lr 3e-4, then the learned sort of the key column (the extract fused
     # into its first pass); its output equals an explicit extract followed by
@@ -248,7 +248,7 @@ def test_learned_sort_headline_window_256m(S, hashed):
     gen.mixed_keys(n, out=col_h.numpy(), hashed=hashed)
     col = col_h.cuda()
     del col_h
-    model, _ = S.learned_train(S.sample(col, 100), n, None, steps=40, batch=4096, lr=3e-4)
+    model, _ = S.learned_train(S.sample(col, 400), n, None, steps=40, batch=4096, lr=3e-4)
     lk, lp, stats = S.sort_learned(col, None, model)
     assert S.sync_status() == S.SBH_OK
     assert stats["bucket_ids"] > 256 and stats["overflow_rows"] < 0.05 * n
