@@ -320,14 +320,17 @@ int sbh_kpa_keyswap_lookup(const uint32_t* d_ptrs, uint64_t n, const uint64_t* d
 
 /* Counted copy: dst[i] = d_src[i] for i < min(*d_count, cap) * per, with
  * elements of elem_bytes = 1, 4 or 8 bytes, where the count is known only on
- * the device (the number of distinct keys a reduction wrote).  dst may be
+ * the device (the number of distinct keys a reduction wrote).  dst_bytes is
+ * elem_bytes, or 4 with elem_bytes 8: each value is stored as its low 4
+ * bytes (per-key counts, which are below 2^32, copied back in half the
+ * bytes).  dst may be
  * page-locked host memory (cudaHostAlloc / cudaHostRegister), written by the
  * kernel over the host link, so that a window's per-key results reach the
  * host without a host synchronisation between the reduction and the copy
  * (Sec. 4.2 "Keyed Aggregation" emits them when the window closes).  The
  * paper has no such primitive; it is plumbing of this library.  No scratch. */
-int sbh_copy_counted(const void* d_src, void* dst, int elem_bytes, const uint64_t* d_count, uint64_t per,
-                     uint64_t cap, void* stream);
+int sbh_copy_counted(const void* d_src, void* dst, int elem_bytes, int dst_bytes, const uint64_t* d_count,
+                     uint64_t per, uint64_t cap, void* stream);
 
 /* Select (Table 2: filter the records of a KPA): the pairs whose value
  * d_col[ptr] (col_bytes 4 or 8) lies in [lo, hi), in KPA order, to

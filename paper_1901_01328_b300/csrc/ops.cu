@@ -27,14 +27,16 @@ __global__ void __launch_bounds__(256) gather_kernel(const uint32_t* __restrict_
 
 // ---------------------------------------------------------------- counted copy
 // dst[i] = src[i] for i < min(*count, cap) * per, the count read on the
-// device; dst may be page-locked host memory (written over the host link).
-template <typename T>
-__global__ void __launch_bounds__(256) copy_counted_kernel(const T* __restrict__ src, T* __restrict__ dst,
+// device; dst may be page-locked host memory (written over the host link);
+// D narrower than T keeps the low bytes.
+template <typename T, typename D>
+__global__ void __launch_bounds__(256) copy_counted_kernel(const T* __restrict__ src, D* __restrict__ dst,
                                                            const uint64_t* __restrict__ count, uint64_t per,
                                                            uint64_t cap) {
     const uint64_t m = min_u64(*count, cap) * per;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride) dst[i] = src[i];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
+        dst[i] = static_cast<D>(src[i]);
 }
 
 // ---------------------------------------------------------------- KeySwap through a lookup
@@ -219,27 +221,35 @@ int sbh_kpa_materialize(const uint32_t* d_ptrs, uint64_t n, const void* d_col, i
     return SBH_OK;
 }
 
-int sbh_copy_counted(const void* d_src, void* dst, int elem_bytes, const uint64_t* d_count, uint64_t per,
-                     uint64_t cap, void* stream) {
+int sbh_copy_counted(const void* d_src, void* dst, int elem_bytes, int dst_bytes, const uint64_t* d_count,
+                     uint64_t per, uint64_t cap, void* stream) {
     using namespace sbh;
     clear_error();
     if (!d_src || !dst || !d_count) { set_error("null pointer"); return SBH_EINVAL; }
     if (elem_bytes != 1 && elem_bytes != 4 && elem_bytes != 8) { set_error("elem_bytes must be 1, 4 or 8"); return SBH_EINVAL; }
+    if (dst_bytes != elem_bytes && !(elem_bytes == 8 && dst_bytes == 4)) {
+        set_error("dst_bytes must equal elem_bytes, or be 4 when elem_bytes is 8");
+        return SBH_EINVAL;
+    }
     if (per == 0 || cap == 0) return SBH_OK;
     cudaStream_t s = as_stream(stream);
     const unsigned grid = (unsigned)min_u64((cap * per + 255) / 256, (uint64_t)num_sms() * 8);
-    if (elem_bytes == 8)
-        SBH_TIMED("copy_counted", s, copy_counted_kernel<uint64_t><<<grid, 256, 0, s>>>(
+    if (elem_bytes == 8 && dst_bytes == 4)
+        SBH_TIMED("copy_counted", s, (copy_counted_kernel<uint64_t, uint32_t><<<grid, 256, 0, s>>>(
+                                         static_cast<const uint64_t*>(d_src), static_cast<uint32_t*>(dst), d_count,
+                                         per, cap)));
+    else if (elem_bytes == 8)
+        SBH_TIMED("copy_counted", s, (copy_counted_kernel<uint64_t, uint64_t><<<grid, 256, 0, s>>>(
                                          static_cast<const uint64_t*>(d_src), static_cast<uint64_t*>(dst), d_count,
-                                         per, cap));
+                                         per, cap)));
     else if (elem_bytes == 4)
-        SBH_TIMED("copy_counted", s, copy_counted_kernel<uint32_t><<<grid, 256, 0, s>>>(
+        SBH_TIMED("copy_counted", s, (copy_counted_kernel<uint32_t, uint32_t><<<grid, 256, 0, s>>>(
                                          static_cast<const uint32_t*>(d_src), static_cast<uint32_t*>(dst), d_count,
-                                         per, cap));
+                                         per, cap)));
     else
-        SBH_TIMED("copy_counted", s, copy_counted_kernel<uint8_t><<<grid, 256, 0, s>>>(
+        SBH_TIMED("copy_counted", s, (copy_counted_kernel<uint8_t, uint8_t><<<grid, 256, 0, s>>>(
                                          static_cast<const uint8_t*>(d_src), static_cast<uint8_t*>(dst), d_count,
-                                         per, cap));
+                                         per, cap)));
     SBH_LAUNCHED();
     return SBH_OK;
 }

@@ -80,7 +80,7 @@ def _load() -> ctypes.CDLL:
         "sbh_learned_train": ([vp, u64, u64, vp, i32, i32, ctypes.c_float, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_sort_learned": ([vp, vp, vp, vp, u64, vp, vp, vp, sz, vp], i32),
         "sbh_kpa_partition": ([vp, vp, u64, vp, u64, vp, vp, vp, vp, sz, vp], i32),
-        "sbh_copy_counted": ([vp, vp, i32, vp, u64, u64, vp], i32),
+        "sbh_copy_counted": ([vp, vp, i32, i32, vp, u64, u64, vp], i32),
         "sbh_kpa_merge_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
         "sbh_join_segments": ([i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, i32, vp, sz, vp], i32),
     }
@@ -349,10 +349,11 @@ def sbh_kpa_materialize(ptrs, col, out, stream=None):
 
 def sbh_copy_counted(src, dst, count, per=1, cap=None, stream=None):
     """dst[:min(count, cap) * per] = src[...]; count is a device uint64
-    tensor; dst may be a page-locked CPU tensor."""
+    tensor; dst may be a page-locked CPU tensor; a 4-byte dst of an 8-byte
+    src keeps each value's low 4 bytes."""
     cap = src.numel() // per if cap is None else cap
-    _check(_lib.sbh_copy_counted(_p(src), _p(dst), src.element_size(), _p(count), per, cap, _stream(stream)),
-           "sbh_copy_counted")
+    _check(_lib.sbh_copy_counted(_p(src), _p(dst), src.element_size(), dst.element_size(), _p(count), per, cap,
+                                 _stream(stream)), "sbh_copy_counted")
 
 
 def sbh_kpa_keyswap(ptrs, key_col, keys_out, stream=None):

@@ -297,6 +297,19 @@ def test_group_reduce_four_byte_counts(S):
             assert same(out_s[:m], osum)
 
 
+def test_copy_counted_narrows_counts(S):
+    # the counted copy of 8-byte counts into 4 bytes (page-locked host memory
+    # and device memory), only the first count rows
+    n = 100_000
+    src = cuda(gen.uniform(8, 8, n, 0, 1 << 31, np.uint64))
+    cnt = torch.tensor([77_777], dtype=torch.uint64, device="cuda")
+    for dst in (torch.zeros(n, dtype=torch.uint32).pin_memory(), torch.zeros(n, dtype=torch.uint32, device="cuda")):
+        S.sbh_copy_counted(src, dst, cnt)
+        torch.cuda.synchronize()
+        got = host(dst)
+        assert same(got[:77_777], host(src)[:77_777].astype(np.uint32)) and not got[77_777:].any()
+
+
 def test_group_count_mixed_keys_16m(S):
     n = 16_000_000
     col = gen.mixed_keys(n)
