@@ -240,7 +240,7 @@ def run_gpu(args):
     lsort_scratch = torch.empty(sbh.sort_learned_scratch_bytes(n), dtype=torch.uint8, device=dev)
     model = torch.zeros(sbh.LEARNED_MODEL_BYTES, dtype=torch.uint8, device=dev)
     out_keys = torch.empty(n, dtype=torch.uint64, device=dev)
-    out_counts = torch.empty(n, dtype=torch.uint64, device=dev)
+    out_counts = torch.empty(n, dtype=torch.uint32, device=dev)  # a count is below 2^32: 4 bytes hold it
     nkeys = torch.zeros(1, dtype=torch.uint64, device=dev)
     scr = {}
     stats_d = torch.zeros(len(sbh.LEARNED_STATS), dtype=torch.uint64, device=dev)
@@ -508,24 +508,18 @@ def run_gpu(args):
 
 def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, ws):
     """The step through the public API with the key column in page-locked
-    host memory and the grouped result (distinct keys and their counts, the
-    counts narrowed to 4 bytes on the device) read back, every step.  Steps are pipelined over three streams: the copy-in of
+    host memory and the grouped result (distinct keys and their 4-byte
+    counts) read back, every step.  Steps are pipelined over three streams: the copy-in of
     step i + 1 and the copy-out of step i - 1 run while step i computes (the
     input column and the outputs are double-buffered)."""
     import torch
-
-    from paper_1901_01328_b300 import sbh
 
     cur = torch.cuda.current_stream(dev)
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     cols = [col, torch.empty_like(col)]
     outs = [outs0, tuple(torch.empty_like(t) for t in outs0)]
     res_k = torch.empty(n, dtype=torch.uint64).pin_memory()
-    # the counts cross the link as 4 bytes (a count is below 2^32): narrowed
-    # on the device after the step (writing 4-byte counts from the keyed emit
-    # itself measured 0.25 ms slower there than 8-byte ones)
-    c32 = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in range(2)]
-    res_c = torch.empty(n, dtype=torch.uint32).pin_memory()
+    res_c = torch.empty(n, dtype=outs0[1].dtype).pin_memory()
     nk_h = torch.empty(2, dtype=torch.uint64).pin_memory()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
@@ -547,9 +541,9 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[b])
             res_k[:m].copy_(outs[b][0][:m], non_blocking=True)
-            res_c[:m].copy_(c32[b][:m], non_blocking=True)
+            res_c[:m].copy_(outs[b][1][:m], non_blocking=True)
             ev_out[b].record(s_out)
-        d2h[0] += 8 + (8 + c32[b].element_size()) * m
+        d2h[0] += 8 + (8 + outs[b][1].element_size()) * m
 
     barrier()
     t0 = time.perf_counter()
@@ -564,7 +558,6 @@ def end_to_end(step, col, col_h, outs0, n, steps, dev, barrier, max_over_ranks, 
         if i >= 2:
             cur.wait_event(ev_out[b])  # the copy-out of step i - 2 has read these outputs
         step(cols[b], outs[b])
-        sbh.sbh_copy_counted(outs[b][1], c32[b], outs[b][2])
         nk_h[b:b + 1].copy_(outs[b][2], non_blocking=True)
         ev_done[b].record(cur)
     copy_out(steps - 1)
