@@ -516,10 +516,24 @@ def sbh_mlp_grad(params, x, t, grad, loss=None, stream=None):
 
 
 def sbh_learned_train(samples, n_rows, init_params, steps, batch, lr, model, losses=None, train_x=None,
-                      train_t=None, stream=None):
+                      train_t=None, scratch=None, stream=None):
+    """Allocates scratch if none is given (see learned_train_scratch_bytes);
+    returns the scratch used."""
     args = (_p(samples), samples.numel(), n_rows, _p(init_params), steps, batch, ctypes.c_float(lr), _p(model),
             _p(losses), _p(train_x), _p(train_t))
-    return _scratch(_lib.sbh_learned_train, args, (_stream(stream),), "sbh_learned_train", samples.device)
+    if scratch is None:
+        return _scratch(_lib.sbh_learned_train, args, (_stream(stream),), "sbh_learned_train", samples.device)
+    nbytes = ctypes.c_size_t(scratch.numel())
+    _check(_lib.sbh_learned_train(*args, _p(scratch), ctypes.byref(nbytes), _stream(stream)), "sbh_learned_train")
+    return scratch
+
+
+def learned_train_scratch_bytes(m: int) -> int:
+    """Scratch of a training call on m samples (it grows with m)."""
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.sbh_learned_train(None, m, m, None, 0, 4096, ctypes.c_float(0.0), None, None, None, None, None,
+                                  ctypes.byref(nbytes), None), "sbh_learned_train")
+    return nbytes.value
 
 
 def sbh_kpa_sort_learned(keys_in, ptrs_in, keys_out, ptrs_out, model, stats=None, scratch=None, stream=None):

@@ -150,9 +150,22 @@ class WindowClock:
 
 
 class WindowServer:
+    # the learned close trains on every SAMPLE_STRIDE-th key of the window
+    SAMPLE_STRIDE = 400
+    TRAIN = dict(steps=40, batch=4096, lr=3e-4)
+
     def __init__(self, win_len, lateness, slot_rows, arena_rows, max_bundle, K=3, device="cuda", keep=True,
-                 out_rows=None, idle_ns=None):
+                 out_rows=None, idle_ns=None, sort="radix"):
+        """sort: "radix" sorts a closing window in place; "learned" trains the
+        partition network on the window's sample and sorts into a second
+        KPA (about 24 more bytes a slot row: see plan).  The learned close
+        pays for keys that span most of the 64 bits; keys of a few bytes
+        take few radix passes (Zipf ranks over 50M: four passes, 27.4 ms of
+        device time per 250M-row window against 30.6 ms learned)."""
+        if sort not in ("radix", "learned"):
+            raise ValueError("sort must be 'radix' or 'learned'")
         dev = torch.device(device)
+        self.sort = sort
         self.dev, self.win_len, self.lateness, self.K = dev, int(win_len), int(lateness), K
         self.clock = WindowClock(win_len, lateness, idle_ns)
         self.slots = [(_u64(slot_rows, dev), _u32(slot_rows, dev)) for _ in range(2)]
@@ -167,7 +180,16 @@ class WindowServer:
         self.slot_rows = slot_rows
         out = slot_rows if out_rows is None else min(out_rows, slot_rows)  # distinct keys a window may have
         self.out_rows = out
-        self.sort_scr = torch.empty(max(1, sbh.sort_scratch_bytes(slot_rows)), dtype=torch.uint8, device=dev)
+        if sort == "learned":
+            self.lsorted = (_u64(slot_rows, dev), _u32(slot_rows, dev))
+            self.sort_scr = torch.empty(max(1, sbh.sort_learned_scratch_bytes(slot_rows)), dtype=torch.uint8,
+                                        device=dev)
+            self.samples = _u64(slot_rows // self.SAMPLE_STRIDE + 1, dev)
+            self.model = torch.zeros(sbh.LEARNED_MODEL_BYTES, dtype=torch.uint8, device=dev)
+            self.train_scr = torch.empty(max(1, sbh.learned_train_scratch_bytes(self.samples.numel())),
+                                         dtype=torch.uint8, device=dev)
+        else:
+            self.sort_scr = torch.empty(max(1, sbh.sort_scratch_bytes(slot_rows)), dtype=torch.uint8, device=dev)
         self.red = (_u64(out, dev), _u64(out, dev), _u64(out, dev), _u64(1, dev))
         self.red_scr = torch.empty(max(1, sbh.group_reduce_scratch_bytes(slot_rows, 8)), dtype=torch.uint8, device=dev)
         self.top = (_u64(out, dev), torch.empty(max(1, out), dtype=torch.uint8, device=dev),
@@ -272,7 +294,17 @@ class WindowServer:
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             ok, op = keys[:m], ptrs[:m]
-            sbh.sbh_kpa_sort(ok, op, ok, op, scratch=self.sort_scr)  # in place
+            if self.sort == "learned":
+                smp = self.samples[:(m + self.SAMPLE_STRIDE - 1) // self.SAMPLE_STRIDE]
+                sbh.sbh_kpa_extract(ok, 0, m, None, None, None, smp, self.SAMPLE_STRIDE)
+                t = self.TRAIN
+                self.train_scr = sbh.sbh_learned_train(smp, m, None, t["steps"], t["batch"], t["lr"], self.model,
+                                                       scratch=self.train_scr)
+                lk, lp = self.lsorted[0][:m], self.lsorted[1][:m]
+                sbh.sbh_kpa_sort_learned(ok, op, lk, lp, self.model, scratch=self.sort_scr)
+                ok, op = lk, lp
+            else:
+                sbh.sbh_kpa_sort(ok, op, ok, op, scratch=self.sort_scr)  # in place
             cap = self.out_rows
             rk, rc, rs, rn = self.red
             sbh.sbh_group_reduce(ok, op, self.arena, rk, rc, rs, cap, rn, scratch=self.red_scr)
@@ -307,17 +339,18 @@ class WindowServer:
                 "overflow": int(self.overflow.item()), "truncated_windows": self.truncated}
 
 
-def plan(budget_bytes, load, win_len_ns, lateness_ns, max_keys, K=3):
+def plan(budget_bytes, load, win_len_ns, lateness_ns, max_keys, K=3, learned=False):
     """Slot, arena and output sizes (rows) that fit the HBM budget for an
     offered load (rows/s): each slot row costs 12 B (KPA) x 2 slots + 12 B
-    of sort scratch + about 5 B of top-K scratch; the arena holds a window
-    plus the lateness and a margin (8 B a row); outputs hold max_keys keys
-    (24 B for count and sum, 9 + 12 K B for the top-K)."""
+    of sort scratch + about 5 B of top-K scratch (learned: + 12 B for the
+    sorted KPA and 12 B more of sort scratch); the arena holds a window plus
+    the lateness and a margin (8 B a row); outputs hold max_keys keys (24 B
+    for count and sum, 9 + 12 K B for the top-K)."""
     win_rows = load * (win_len_ns + lateness_ns) * 1e-9
     arena_rows = int(1.3 * win_rows)
     out_rows = int(max_keys * 1.02) + 1024
     out_bytes = out_rows * (24 + 9 + 12 * K)
-    slot_rows = int((budget_bytes - 8 * arena_rows - out_bytes) / 41)
+    slot_rows = int((budget_bytes - 8 * arena_rows - out_bytes) / (65 if learned else 41))
     slot_rows = max(0, min(slot_rows, int(1.15 * load * win_len_ns * 1e-9) + (1 << 20)))
     return slot_rows, arena_rows, out_rows
 

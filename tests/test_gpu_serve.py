@@ -22,11 +22,11 @@ def V():
     return serve
 
 
-def _run(V, arena_rows, n_windows=8, load=3.3e8, slot_rows=1 << 20):
+def _run(V, arena_rows, n_windows=8, load=3.3e8, slot_rows=1 << 20, sort="radix"):
     win, late = 1_000_000, 100_000  # 1 ms windows, 0.1 ms allowed lateness (ns)
     pool = V.BundlePool(gen, 8, 2000, 20_000, 0.8, 50_000_000, 0.05, late, SEED)
     arr = V.poisson_schedule(gen, SEED, n_windows * win, load, float(pool.sizes.mean()))
-    server = V.WindowServer(win, late, slot_rows=slot_rows, arena_rows=arena_rows, max_bundle=20_000, K=3)
+    server = V.WindowServer(win, late, slot_rows=slot_rows, arena_rows=arena_rows, max_bundle=20_000, K=3, sort=sort)
     t0 = 10 * win
     admitted = []
     for i, a in enumerate(arr):
@@ -62,9 +62,13 @@ def _oracle_windows(server, pool, admitted, win, arena_rows):
     return out
 
 
-def test_serving_windows_match_oracle(V):
+@pytest.mark.parametrize("sort", ["radix", "learned"])
+def test_serving_windows_match_oracle(V, sort):
+    # radix: each closing window sorted in place; learned: the partition
+    # network trained on the window's sample, the window sorted into a
+    # second KPA
     arena_rows = 900_000  # about 2.7 windows of rows: the arena ring wraps
-    server, pool, admitted, win = _run(V, arena_rows)
+    server, pool, admitted, win = _run(V, arena_rows, sort=sort)
     st = server.stats()
     assert st["overflow"] == 0 and st["dropped_rows"] == 0 and st["shed_bundles"] == 0
     exp = _oracle_windows(server, pool, admitted, win, arena_rows)
