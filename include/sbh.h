@@ -187,7 +187,9 @@ int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n,
  * staged through shared memory.  From 2^23 pairs each pass is three kernels:
  * per-chunk digit counts, their scan, and a scatter in which every CTA walks
  * its own chunk of tiles (bulk-copied, ranked, staged) with its digit offsets
- * known up front.  Because the sort is stable and ties keep their input
+ * known up front; each scatter also stores every row's digit of the next
+ * pass (one byte), which that pass's chunk counts read instead of the keys.
+ * Because the sort is stable and ties keep their input
  * order, the output is in (key, ptr) order when the input ptrs ascend (as
  * Extract makes them); in general ties keep input order.
  * In/out: (d_keys_in, d_ptrs_in) -> (d_keys_out, d_ptrs_out), n pairs,
@@ -196,7 +198,7 @@ int sbh_kpa_split_ts(const uint64_t* key_col, const int64_t* ts_rel, uint64_t n,
  * resident key column is sorted this way without an Extract pass: the first
  * digit pass reads the column and makes each ptr from its row number, and
  * the output is what Extract (row_begin 0) followed by this sort gives.
- * Scratch: about 12 n bytes plus 2 MiB (the sizing call gives the exact figure). */
+ * Scratch: about 13 n bytes plus 2 MiB (the sizing call gives the exact figure). */
 int sbh_kpa_sort(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out, uint32_t* d_ptrs_out,
                  uint64_t n, void* d_scratch, size_t* scratch_bytes, void* stream);
 
@@ -401,7 +403,7 @@ int sbh_join_segments(int nseg, const uint64_t* d_lkeys, const uint32_t* d_lptrs
 #define SBH_LEARNED_MODEL_BYTES 139264
 #define SBH_LEARNED_CAPACITY 8192 /* rows a bucket may hold to be sorted in shared memory */
 #define SBH_LEARNED_MAX_HEAVY 16384 /* heavy keys a model holds */
-#define SBH_LEARNED_STATS 13
+#define SBH_LEARNED_STATS 14
 
 /* y[i] = MLP(x[i]) for i < m.  No scratch. */
 int sbh_mlp_forward(const float* d_params, const float* d_x, uint64_t m, float* d_y, void* stream);
@@ -467,8 +469,10 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
  * with a key range wider than 2^40, and a repeated key sharing its 16-bit
  * group of the key with another key even in a run of its bucket alone: they
  * join the overflow rows in the plain radix sort, cheaper than six or more
- * passes in shared memory), and the buckets of runs whose group sort failed
- * and that were retried bucket by bucket.
+ * passes in shared memory), the buckets of runs whose group sort failed
+ * and that were retried bucket by bucket, and the scatter passes on the
+ * 16-bit bucket ids that ran (bit 0: the low byte, bit 1: the high byte; 0
+ * when the ids were wider than 16 bits and not carried).
  * Scratch: about 24 n bytes. */
 int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d_ptrs_in, uint64_t* d_keys_out,
                          uint32_t* d_ptrs_out, uint64_t n, const void* d_model, uint64_t* d_stats, void* d_scratch,

@@ -1643,7 +1643,8 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
 
 // The call's statistics, in the order of the header's list.
 __global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const uint32_t* __restrict__ plan,
-                                     const BucketStats* __restrict__ st, uint64_t* __restrict__ out) {
+                                     const BucketStats* __restrict__ st, const uint32_t* __restrict__ id_passes,
+                                     uint64_t* __restrict__ out) {
     if (threadIdx.x != 0) return;
     out[0] = *nbid;
     out[1] = plan[0];
@@ -1658,6 +1659,7 @@ __global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const ui
     out[10] = st->wide_buckets;
     out[11] = st->wide_rows;
     out[12] = st->retried_buckets;
+    out[13] = *id_passes;
 }
 
 // ------------------------------------------------------------------ carried bucket ids
@@ -1735,62 +1737,28 @@ __global__ void __launch_bounds__(1024) ids_upsweep_kernel(const uint64_t* __res
     }
 }
 
-// Chunk counts of the second pass: its digit is the carried high byte.
-// Each warp counts into its own histogram (the bytes are in random order:
-// one shared histogram made the warps' atomics collide, 0.19 against 0.094
-// ms for 256M rows), summed at the end.
+// Chunk counts of the second pass: its digit is the high byte carried by the
+// first pass, or, when no first pass ran (every id has the same low byte),
+// the high byte of the input rows' ids.  The bytes are in random order and
+// are counted into a [digit][lane] table (nd_count): 0.055 ms for 256M rows,
+// against 0.094 with a histogram per warp and 0.19 with one shared one.
 __global__ void __launch_bounds__(1024) ids_count_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan,
                                                          uint32_t chunk, uint32_t* __restrict__ chunk_hist) {
     if (!plan->active[pos]) return;
-    __shared__ uint32_t h[32][kRadix];
-    const uint8_t* __restrict__ v = buf.vals(plan->src[pos]);
-    const uint32_t warp = threadIdx.x / 32;
-    for (int i = threadIdx.x; i < 32 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    uint32_t* hw = h[warp];
     const uint32_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-    auto add4 = [&](uint32_t w) {
-#pragma unroll
-        for (int y = 0; y < 4; ++y) atomicAdd(&hw[(w >> (8 * y)) & 0xFFu], 1u);
-    };
-    uint32_t done = lo;
-    if (lo < hi && (reinterpret_cast<uintptr_t>(v + lo) & 15) == 0) {
-        // sixteen bytes per load, two loads in flight
-        const uint32_t nq = (hi - lo) / 16;
-        const uint4* q = reinterpret_cast<const uint4*>(v + lo);
-        for (uint32_t i = threadIdx.x; i < nq; i += 2 * blockDim.x) {
-            const uint4 w = __ldcs(q + i);
-            const bool two = i + blockDim.x < nq;
-            const uint4 w2 = two ? __ldcs(q + i + blockDim.x) : make_uint4(0, 0, 0, 0);
-            add4(w.x);
-            add4(w.y);
-            add4(w.z);
-            add4(w.w);
-            if (two) {
-                add4(w2.x);
-                add4(w2.y);
-                add4(w2.z);
-                add4(w2.w);
-            }
-        }
-        done = lo + nq * 16;
-    }
-    for (uint32_t i = done + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&hw[v[i]], 1u);
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-        uint32_t c = 0;
-#pragma unroll 8
-        for (int w = 0; w < 32; ++w) c += h[w][d];
-        chunk_hist[blockIdx.x * kRadix + d] = c;
-    }
+    uint32_t* out = chunk_hist + (size_t)blockIdx.x * kRadix;
+    if (plan->active[0]) nd_count(buf.vals(plan->src[pos]), lo, hi, out);
+    else nd_count<true>(buf.in_ids, lo, hi, out);
 }
 
 // Bucket bounds when no pass ran: every row has the same id, the OR of the
 // ids (vbits[0]); the last pass records each id's first row otherwise.
+// Also records which id passes ran (bit p: the pass on byte p of the ids).
 __global__ void __launch_bounds__(256) ids_bounds_kernel(const Plan* __restrict__ plan, uint32_t n,
                                                          const uint32_t* __restrict__ nbid_p,
                                                          const unsigned long long* __restrict__ vbits,
-                                                         uint32_t* __restrict__ bstart) {
+                                                         uint32_t* __restrict__ bstart, uint32_t* __restrict__ passes) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *passes = (plan->active[0] ? 1u : 0u) | (plan->active[1] ? 2u : 0u);
     if (plan->npasses) return;
     const uint32_t nbid = *nbid_p;
     const uint32_t id = static_cast<uint32_t>(vbits[0]);
@@ -1924,7 +1892,8 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const
 
 // Stable sort by 16-bit bucket id with the ids carried along; fills bstart.
 int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* out_k, uint32_t* out_p, uint64_t n,
-                        void* scratch, cudaStream_t s, BucketValue16 fn, const uint32_t* nbid, uint32_t* bstart) {
+                        void* scratch, cudaStream_t s, BucketValue16 fn, const uint32_t* nbid, uint32_t* bstart,
+                        uint32_t* id_passes) {
     CarryScratch cs = carry_carve(scratch, n);
     const uint32_t n32 = static_cast<uint32_t>(n);
     const int sms = num_sms();
@@ -1950,7 +1919,8 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds", s,
-              ids_bounds_kernel<<<kMaxBucketIds / 256 + 1, 256, 0, s>>>(cs.plan, n32, nbid, cs.vbits, bstart));
+              ids_bounds_kernel<<<kMaxBucketIds / 256 + 1, 256, 0, s>>>(cs.plan, n32, nbid, cs.vbits, bstart,
+                                                                        id_passes));
     SBH_LAUNCHED();
     SBH_TIMED("learned_bounds_min", s,
               bounds_min_kernel<<<kFillBlocks, 1024, 0, s>>>(cs.plan, n32, nbid, bstart, cs.bmin));
@@ -1978,7 +1948,7 @@ struct SortLearnedScratch {
     uint32_t* offs;
     uint32_t* retry_flag;   // buckets of runs the bucket sort retries one by one
     uint32_t* small;        // nbid, counter, nlist, rows_total, heavy keys used, spread buckets, runs, (rows),
-                            // second counter, retried buckets, (rows)
+                            // second counter, retried buckets, (rows), -, id passes (bits)
     uint32_t* run_flag;     // first buckets of the bucket sort's runs
     uint4* runrec;          // the runs' records
     BucketStats* stats;
@@ -2209,7 +2179,8 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
     const BucketValue fn{t.cells, t.hcells, model->heavy_keys};
     if (carry) {
         rc = sort_by_carried_ids(d_keys_in, d_ptrs_in, d_keys_out, d_ptrs_out, n, t.sort_scratch, s,
-                                 BucketValue16{t.cells16, t.hcells, model->heavy_keys}, nbid, t.bstart);
+                                 BucketValue16{t.cells16, t.hcells, model->heavy_keys}, nbid, t.bstart,
+                                 t.small + 12);
         if (rc) return rc;
     } else {
         // stable scatter by bucket id computed from the key (ids below 2^24)
@@ -2283,7 +2254,7 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                                                       rows_total, t.ck, t.cp, 0));
     SBH_LAUNCHED();
     if (d_stats) {
-        SBH_TIMED("learned_stats", s, learned_stats_kernel<<<1, 32, 0, s>>>(nbid, lplan, t.stats, d_stats));
+        SBH_TIMED("learned_stats", s, learned_stats_kernel<<<1, 32, 0, s>>>(nbid, lplan, t.stats, t.small + 12, d_stats));
         SBH_LAUNCHED();
     }
     return SBH_OK;

@@ -32,7 +32,7 @@ LEARNED_CAPACITY = 8192
 LEARNED_MAX_HEAVY = 16384
 LEARNED_STATS = ("bucket_ids", "heavy_keys", "sorted_buckets", "one_key_buckets", "heavy_buckets",
                  "overflow_buckets", "overflow_rows", "largest_bucket", "radix_buckets", "radix_rows",
-                 "wide_buckets", "wide_rows", "retried_buckets")
+                 "wide_buckets", "wide_rows", "retried_buckets", "id_passes")
 
 _ERRNAMES = {1: "SBH_EINVAL", 2: "SBH_ENOSPACE", 3: "SBH_ETIMEOUT", 4: "SBH_ECUDA"}
 

@@ -341,16 +341,16 @@ class WindowServer:
 
 def plan(budget_bytes, load, win_len_ns, lateness_ns, max_keys, K=3, learned=False):
     """Slot, arena and output sizes (rows) that fit the HBM budget for an
-    offered load (rows/s): each slot row costs 12 B (KPA) x 2 slots + 12 B
+    offered load (rows/s): each slot row costs 12 B (KPA) x 2 slots + 13 B
     of sort scratch + about 5 B of top-K scratch (learned: + 12 B for the
-    sorted KPA and 12 B more of sort scratch); the arena holds a window plus
+    sorted KPA and 11 B more of sort scratch); the arena holds a window plus
     the lateness and a margin (8 B a row); outputs hold max_keys keys (24 B
     for count and sum, 9 + 12 K B for the top-K)."""
     win_rows = load * (win_len_ns + lateness_ns) * 1e-9
     arena_rows = int(1.3 * win_rows)
     out_rows = int(max_keys * 1.02) + 1024
     out_bytes = out_rows * (24 + 9 + 12 * K)
-    slot_rows = int((budget_bytes - 8 * arena_rows - out_bytes) / (65 if learned else 41))
+    slot_rows = int((budget_bytes - 8 * arena_rows - out_bytes) / (65 if learned else 42))
     slot_rows = max(0, min(slot_rows, int(1.15 * load * win_len_ns * 1e-9) + (1 << 20)))
     return slot_rows, arena_rows, out_rows
 

@@ -41,8 +41,8 @@ def test_scratch_size_queries_need_no_gpu(L):
     lib = L.lib()
     nb = ctypes.c_size_t(0)
     assert lib.sbh_kpa_sort(None, None, None, None, 256_000_000, None, ctypes.byref(nb), None) == 0
-    # ping-pong copy (12 B per pair) plus look-back records
-    assert 256_000_000 * 12 <= nb.value < 256_000_000 * 12 + 200_000_000
+    # ping-pong copy (12 B per pair), the next pass's digit byte and the chunk tables
+    assert 256_000_000 * 13 <= nb.value < 256_000_000 * 13 + 200_000_000
     for fn, args in ((lib.sbh_group_reduce, (None, None, 10_000, None, 8, None, None, 8, None, 0, None)),
                      (lib.sbh_topk, (None, None, 10_000, None, 8, 3, None, None, None, None, 0, None)),
                      (lib.sbh_join, (None, None, 10_000, None, None, 10, None, None, 0, None))):

@@ -370,3 +370,32 @@ def test_learned_sort_uneven_wide_buckets(S, bins, span_bits):
         assert st["radix_rows"] > n // 2 and st["wide_rows"] < n // 3
         # runs of several buckets whose group sort failed were retried bucket by bucket
         assert st["retried_buckets"] > 0
+
+
+def test_learned_sort_ids_sharing_their_low_byte(S):
+    # a model trained on uniform 32-bit keys, applied to a window of two keys
+    # (2M rows: about 490 buckets): for some second key both keys' bucket ids
+    # have the same low byte, so only the pass on the ids' high byte runs,
+    # and its chunk counts read the high bytes of the input ids.  The sweep
+    # over the second key crosses such ids (found at j = 133-136 of these
+    # steps); every window must sort exactly
+    n = 2_000_000
+    train = cuda(gen.uniform(41, 1, n, 0, 1 << 32, np.uint64))
+    model, _ = S.learned_train(train[::100].contiguous(), n, None, steps=40, batch=4096, lr=3e-4)
+    order = np.argsort(gen.uniform(41, 2, n, 0, 0, np.uint64), kind="stable")
+    k1 = np.uint64(int(0.1 * 2**32))
+    step = 2**32 / 488 / 4
+    high_only = 0
+    for j in range(128, 142):
+        k2 = np.uint64(int(0.55 * 2**32 + j * step))
+        col = np.where(np.arange(n) < n // 2, k1, k2).astype(np.uint64)[order]
+        sk, sp, st = S.sort_learned(cuda(col), None, model)
+        assert st["id_passes"] in (2, 3) and st["bucket_ids"] > 256
+        if st["id_passes"] == 2:
+            high_only += 1
+            ok, op = oracle.sort(col, np.arange(n, dtype=np.uint32))
+            assert same(sk, ok) and same(sp, op)
+        else:  # two keys, stable: each key's rows in input order
+            assert same(sp, np.concatenate([np.flatnonzero(col == k1), np.flatnonzero(col == k2)]).astype(np.uint32))
+            assert same(sk, np.sort(col))
+    assert high_only > 0
