@@ -1,10 +1,11 @@
 """Benchmark of the KPA grouping path on B300.
 
 One step = one pass of the hot path over one window of the mixed-key
-workload: Extract of 256M (uint64 key, uint32 row) pairs from a device key
-column with a 1% key sample, training of the learned partitioner's network on
-that sample, the learned partition sort, and per-key count (Keyed
-reduction).  The plain radix sort step is timed on the same window for the
+workload: a 0.25% key sample (every 400th key) read from a device key column
+of 256M uint64 keys, training of the learned partitioner's network on that
+sample, the learned partition sort of the window's (key, row) pairs (the
+Extract fused into its first pass: it reads the column and makes each ptr
+from its row number), and per-key count (Keyed reduction).  The plain radix sort step is timed on the same window for the
 comparison (--sort radix makes it the headline).  Keys are the seeded
 mixture of 70% Zipf(1.1) ranks over 2^24 ids and 30% floor(lognormal(30, 4))
 below 2^64.  The KPA (3 GB) is larger than the 126 MB L2, so no flush is
@@ -44,10 +45,11 @@ UNIT = "records/s"
 CPU_SAMPLE = 4_000_000
 # DRAM bytes per row of one launch (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum on the 16M-row mixed-key window; for the carried-id
-# scatter the mean of its two passes).
+# scatter the mean of its two passes, for the radix scatter the mean of the
+# second and third passes of a plain sort).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 26.41, "sort_scatter": 24.55}
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 23.47, "sort_scatter": 23.65}
 
 
 def _dist():
