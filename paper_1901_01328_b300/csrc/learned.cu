@@ -1667,6 +1667,7 @@ __global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const ui
 // in a 16-bit array, and moved with the row through both digit passes; the
 // counts and the bucket bounds then read ids instead of recomputing them.
 constexpr int kCarryTile = 3584;
+constexpr int kCarryIdxTile = 4096;
 
 // Bucket id of every row (kept as 16 bits), the histogram of its low digit
 // per chunk of the first digit pass (CTA c takes the rows of chunk c: that
@@ -1865,13 +1866,17 @@ __global__ void __launch_bounds__(1024) bounds_fill_kernel(const Plan* __restric
 // The two passes by bucket id: per pass, chunk counts of the id digit ->
 // chunk offsets -> scatter; the first pass carries the ids' high bytes to the
 // second.  The first pass's chunk counts come from the id upsweep (the same
-// chunks).
-template <int TILE, int THREADS>
-int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const ChunkGeom& g, cudaStream_t s,
-                   uint32_t* first_row) {
+// chunks, geometry g0); the second pass has its own chunks (g1).  A key
+// column (no ptrs) goes through a first pass that stages 16-bit places in the
+// tile instead of ptrs, in tiles of kCarryIdxTile rows (the shared memory the
+// ptrs left free): 4096 rows a tile instead of 3584.
+template <int THREADS>
+int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const ChunkGeom& g0, const ChunkGeom& g1,
+                   bool idx0, cudaStream_t s, uint32_t* first_row) {
     const int bulk_ok = ((reinterpret_cast<uintptr_t>(b.in_k) | reinterpret_cast<uintptr_t>(b.in_p) |
                           reinterpret_cast<uintptr_t>(b.out_k) | reinterpret_cast<uintptr_t>(b.out_p)) & 15) == 0;
     for (int pos = 0; pos < 2; ++pos) {
+        const ChunkGeom& g = pos ? g1 : g0;
         if (pos > 0) {
             SBH_TIMED("learned_ids_count", s,
                       ids_count_kernel<<<g.nchunks, 1024, 0, s>>>(b, n32, pos, cs.plan, g.chunk, cs.chunk_hist));
@@ -1881,10 +1886,18 @@ int carried_passes(const Buffers& b, uint32_t n32, const CarryScratch& cs, const
         SBH_TIMED("learned_ids_chunk_scan", s,
                   chunk_scan_kernel<<<1, 1024, 0, s>>>(cs.plan, pos, cs.chunk_hist, g.nchunks, nullptr, cbase));
         SBH_LAUNCHED();
-        SBH_TIMED("learned_ids_scatter", s,
-                  (chunk_scatter_kernel<RadixValue, TILE, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
-                      b, n32, pos, cs.plan, g.chunk, cbase, RadixValue{}, bulk_ok, spin_limit(), status_word(),
-                      first_row, cs.chunk_base)));
+        if (pos == 0 && idx0) {
+            SBH_TIMED("learned_ids_scatter", s,
+                      (chunk_scatter_kernel<RadixValue, kCarryIdxTile, THREADS, true, true>
+                       <<<g.nchunks, THREADS, g.smem, s>>>(b, n32, pos, cs.plan, g.chunk, cbase, RadixValue{},
+                                                            bulk_ok, spin_limit(), status_word(), first_row,
+                                                            cs.chunk_base)));
+        } else {
+            SBH_TIMED("learned_ids_scatter", s,
+                      (chunk_scatter_kernel<RadixValue, kCarryTile, THREADS, true><<<g.nchunks, THREADS, g.smem, s>>>(
+                          b, n32, pos, cs.plan, g.chunk, cbase, RadixValue{}, bulk_ok, spin_limit(), status_word(),
+                          first_row, cs.chunk_base)));
+        }
         SBH_LAUNCHED();
     }
     return SBH_OK;
@@ -1898,11 +1911,16 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     const uint32_t n32 = static_cast<uint32_t>(n);
     const int sms = num_sms();
     SBH_CUDA(cudaMemsetAsync(cs.vbits, 0, 2 * sizeof(unsigned long long), s));
-    ChunkGeom g;
-    int rc = chunk_geometry<RadixValue, kCarryTile, 512, true>(n32, &g);
+    const bool idx0 = in_p == nullptr;  // a key column: the first pass stages places in the tile
+    ChunkGeom g0, g1;
+    int rc = chunk_geometry<RadixValue, kCarryTile, 512, true>(n32, &g1);
+    if (rc) return rc;
+    if (idx0) rc = chunk_geometry<RadixValue, kCarryIdxTile, 512, true, true>(n32, &g0);
+    else g0 = g1;
     if (rc) return rc;
     SBH_TIMED("learned_ids_upsweep", s,
-              ids_upsweep_kernel<<<g.nchunks, 1024, 0, s>>>(in_k, n32, g.chunk, fn, cs.ids_in, cs.vbits, cs.chunk_hist));
+              ids_upsweep_kernel<<<g0.nchunks, 1024, 0, s>>>(in_k, n32, g0.chunk, fn, cs.ids_in, cs.vbits,
+                                                              cs.chunk_hist));
     SBH_LAUNCHED();
     SBH_TIMED("learned_ids_plan", s, plan_bits_kernel<<<1, 32, 0, s>>>(cs.vbits, 2, cs.plan, 0));
     SBH_LAUNCHED();
@@ -1913,7 +1931,7 @@ int sort_by_carried_ids(const uint64_t* in_k, const uint32_t* in_p, uint64_t* ou
     // bucket starts: the last pass records each id's first output row, then a
     // suffix minimum fills the empty buckets (with no pass, from the one id)
     SBH_CUDA(cudaMemsetAsync(bstart, 0xFF, (kMaxBucketIds + 1) * sizeof(uint32_t), s));
-    rc = carried_passes<kCarryTile, 512>(b, n32, cs, g, s, bstart);
+    rc = carried_passes<512>(b, n32, cs, g0, g1, idx0, s, bstart);
     if (rc) return rc;
     const unsigned cblocks = (unsigned)min_u64((n + 255) / 256, (uint64_t)sms * 4);
     SBH_TIMED("learned_ids_copy", s, copy_kernel<<<cblocks, 256, 0, s>>>(b, n32, cs.plan));

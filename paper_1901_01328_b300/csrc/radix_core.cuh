@@ -740,12 +740,13 @@ chunk_scan_kernel(const Plan* __restrict__ plan, int pos, const uint32_t* __rest
 //   B3  per (group, digit): first staged slot; per digit: global offset
 //   B4  staged in digit order; then the coalesced scatter (and the counters
 //       are cleared for the next tile)
-template <int TILE, int THREADS, bool kCarry, bool kDig>
+template <int TILE, int THREADS, bool kCarry, bool kDig, bool kIdx = false>
 struct ScatterSmem {
     static constexpr int kW = THREADS / 32;
     static constexpr int kG = THREADS / 128;  // warp groups of the count scan
     uint64_t keys[2][TILE];  // double-buffered input tiles, reused to stage
-    uint32_t ptrs[2][TILE];  // the scatter in digit order
+    uint32_t ptrs[kIdx ? 1 : 2][kIdx ? 4 : TILE];  // the scatter in digit order
+    uint16_t idx[kIdx ? TILE : 8];  // kIdx (ptr = row number): each staged row's place in its tile
     uint16_t vals[kCarry ? 2 : 1][kCarry ? TILE : 8];  // carried ids, staged the same way (the second
                                                        // pass's carried bytes arrive in the first TILE bytes)
     uint8_t dig[kDig ? TILE : 16];                     // digit of each staged row (derived values only)
@@ -776,7 +777,13 @@ struct ScatterBlocks {  // CTAs per SM the launch bounds ask for (64 registers a
 // rows j of a thread (j % 8) whose peers come from match.any, the others from
 // digit ballots: one in two measured fastest (the two run on different pipes)
 constexpr uint32_t kMatchMask = 0xAA;
-template <typename ValueFn, int TILE, int THREADS, bool kCarry = false>
+// kIdx: the pass reads the sort's input with no ptrs (ptrs_in NULL: a row's
+// ptr is its row number), so no ptrs are loaded and the staging keeps each
+// row's 16-bit place in its tile instead of a 4-byte ptr.  The learned sort
+// launches it for its first carried-id pass over a key column, whose tiles
+// then fit 4096 rows instead of 3584 (the two id passes at 256M rows 4.75 to
+// 4.61 ms); for the plain sort's first pass it measured no faster.
+template <typename ValueFn, int TILE, int THREADS, bool kCarry = false, bool kIdx = false>
 __global__ void __launch_bounds__(THREADS, (ScatterBlocks<TILE, THREADS>::value))
 chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ plan, uint32_t chunk,
                      const uint32_t* __restrict__ chunk_base, ValueFn value_of, int bulk_ok, uint32_t spin_limit,
@@ -784,7 +791,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                      const uint32_t* __restrict__ low_base = nullptr, DynN dn = DynN{}) {
     constexpr bool kDig = ScatterDig<ValueFn, kCarry>::value;
     constexpr bool kNext = !kCarry && std::is_same<ValueFn, RadixValue>::value;
-    using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig>;
+    using Smem = ScatterSmem<TILE, THREADS, kCarry, kDig, kIdx>;
     constexpr int kW = Smem::kW, kG = Smem::kG, kWpg = kW / kG;
     constexpr int kIt = TILE / THREADS;
     static_assert(TILE % THREADS == 0 && THREADS % 128 == 0 && THREADS <= 1024, "tile geometry");
@@ -794,7 +801,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
     const DigitOf<ValueFn> digit_of{value_of, shift};
     const int src = plan->src[pos], dst = plan->dst[pos];
     const uint64_t* __restrict__ in_k = buf.keys(src);
-    const uint32_t* __restrict__ in_p = buf.ptrs(src);
+    const uint32_t* __restrict__ in_p = kIdx ? nullptr : buf.ptrs(src);
     uint64_t* __restrict__ out_k = buf.wkeys(dst);
     uint32_t* __restrict__ out_p = buf.wptrs(dst);
     // Carried 16-bit ids (kCarry: two passes, low byte then high byte).  The
@@ -846,11 +853,14 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             // carried-id passes keep the default (evict-first was no faster)
             if constexpr (kCarry) {
                 bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b]);
-                if (in_p) bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
+                if constexpr (!kIdx)
+                    if (in_p) bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b]);
             } else {
                 const uint64_t pol = l2_evict_first();
                 bulk_load(sm.keys[b], in_k + lo + (size_t)i * TILE, TILE * sizeof(uint64_t), &sm.mbar[b], pol);
-                if (in_p) bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b], pol);
+                if constexpr (!kIdx)
+                    if (in_p)
+                        bulk_load(sm.ptrs[b], in_p + lo + (size_t)i * TILE, TILE * sizeof(uint32_t), &sm.mbar[b], pol);
             }
             if (full_ids) bulk_load(sm.vals[b], in_ids + lo + (size_t)i * TILE, TILE * sizeof(uint16_t), &sm.mbar[b]);
             if (walk) bulk_load(sm.vals[b], in_v + lo + (size_t)i * TILE, TILE, &sm.mbar[b]);
@@ -922,7 +932,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         } else {
             for (uint32_t s = tid; s < valid; s += THREADS) {
                 sm.keys[b][s] = ld_stream(in_k + base + s);
-                if (in_p) sm.ptrs[b][s] = ld_stream(in_p + base + s);
+                if constexpr (!kIdx)
+                    if (in_p) sm.ptrs[b][s] = ld_stream(in_p + base + s);
                 if (full_ids) sm.vals[b][s] = in_ids[base + s];
                 if (walk) reinterpret_cast<uint8_t*>(sm.vals[b])[s] = in_v[base + s];
             }
@@ -949,7 +960,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
         auto tile = [&](auto full_tag) {
             constexpr bool full = decltype(full_tag)::value;
             uint64_t* __restrict__ kb = sm.keys[b];
-            uint32_t* __restrict__ pb = sm.ptrs[b];
+            uint32_t* __restrict__ pb = sm.ptrs[kIdx ? 0 : b];
             uint16_t* __restrict__ vb = sm.vals[kCarry ? b : 0];
             // rows of this thread: warp w owns 32 * kIt consecutive rows
             uint64_t k[kIt];
@@ -958,7 +969,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
 #pragma unroll
             for (int j = 0; j < kIt; ++j) {
                 k[j] = kb[wofs + j * 32];
-                p[j] = in_p ? pb[wofs + j * 32] : base + wofs + j * 32;
+                if constexpr (kIdx) p[j] = wofs + j * 32;  // the row's place in the tile
+                else p[j] = in_p ? pb[wofs + j * 32] : base + wofs + j * 32;
                 if (kCarry) cv[j] = walk ? reinterpret_cast<const uint8_t*>(vb)[wofs + j * 32] : vb[wofs + j * 32];
             }
             if constexpr (kCarry) {
@@ -1083,7 +1095,8 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                         const uint32_t wo = (sm.whist2[warp][dg[j] >> 1] >> ((dg[j] & 1u) * 16u)) & 0xFFFFu;
                         const uint32_t slot = sm.gstart[grp][dg[j]] + wo + rank[j];
                         kb[slot] = k[j];
-                        pb[slot] = p[j];
+                        if constexpr (kIdx) sm.idx[slot] = static_cast<uint16_t>(p[j]);
+                        else pb[slot] = p[j];
                         if (kCarry) vb[slot] = static_cast<uint16_t>(cv[j]);
                         if (kDig) sm.dig[slot] = static_cast<uint8_t>(dg[j]);
                     }
@@ -1103,7 +1116,7 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
                         else d = static_cast<uint32_t>(key >> shift) & (kRadix - 1);
                         const uint32_t g = sm.gbase_rel[d] + s;
                         out_k[g] = key;
-                        out_p[g] = pb[s];
+                        out_p[g] = kIdx ? base + sm.idx[s] : pb[s];
                         // (one byte a row, in runs under a sector: evict-last as for the carried ids)
                         if (kNext && nxt >= 0)
                             st_hint(buf.nd + g, static_cast<uint32_t>(key >> (nxt * kRadixBits)) & (kRadix - 1),
@@ -1141,10 +1154,10 @@ struct ChunkGeom {
     size_t smem = 0;
 };
 
-template <typename ValueFn, int TILE, int THREADS, bool kCarry>
+template <typename ValueFn, int TILE, int THREADS, bool kCarry, bool kIdx = false>
 int chunk_geometry(uint64_t n, ChunkGeom* g) {
-    auto kern = chunk_scatter_kernel<ValueFn, TILE, THREADS, kCarry>;
-    const size_t smem = sizeof(ScatterSmem<TILE, THREADS, kCarry, ScatterDig<ValueFn, kCarry>::value>);
+    auto kern = chunk_scatter_kernel<ValueFn, TILE, THREADS, kCarry, kIdx>;
+    const size_t smem = sizeof(ScatterSmem<TILE, THREADS, kCarry, ScatterDig<ValueFn, kCarry>::value, kIdx>);
     SBH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));

@@ -70,12 +70,19 @@ def _sort_case(kind, n, seed=1):
         return gen.uniform(seed, 3, n, 0, 256, np.uint64) << np.uint64(56)
     if kind == "full64":
         return gen.uniform(seed, 4, n, 0, 0, np.uint64)
+    if kind == "gaps":  # bytes 0, 2 and 6 vary, the others are constant (not zero): passes 1, 3-5, 7 skipped
+        r = gen.uniform(seed, 5, n, 0, 1 << 24, np.uint64)
+        return ((r & np.uint64(0xFF)) | (((r >> np.uint64(8)) & np.uint64(0xFF)) << np.uint64(16))
+                | ((r >> np.uint64(16)) << np.uint64(48)) | np.uint64(0x5A00_A5A5_5A00_5A00))
+    if kind == "lowconst":  # byte 0 constant: the first pass that runs is the second
+        return (gen.uniform(seed, 6, n, 0, 0, np.uint64) & ~np.uint64(0xFF)) | np.uint64(0x33)
     raise ValueError(kind)
 
 
 @pytest.mark.parametrize("kind,n,offset", [("full64", 3 * 4096 + 5, 0), ("mixed", 100_003, 1), ("equal", 10_000, 0),
                                            ("highbyte", 4097, 0), ("mixed", (1 << 23) + 3, 0),
-                                           ("mixed", (1 << 23) + 4099, 1)])
+                                           ("mixed", (1 << 23) + 4099, 1), ("lowconst", (1 << 23) + 3, 0),
+                                           ("gaps", (1 << 23) + 5, 0)])
 def test_sort_key_column_without_extract(S, kind, n, offset):
     # ptrs_in = None: the sort reads the key column and row i's ptr is i,
     # as an Extract of the column would make it; offset 1 starts the column
@@ -439,10 +446,12 @@ def chunked_from_2m(S):
     S.set_knob(S.KNOB_SORT_CHUNKED_MIN, old)
 
 
-@pytest.mark.parametrize("kind", ["uniform20", "mixed", "highbyte", "extremes"])
+@pytest.mark.parametrize("kind", ["uniform20", "mixed", "highbyte", "extremes", "gaps", "lowconst"])
 def test_sort_chunked_path_ragged(S, kind, chunked_from_2m):
     # above the size where passes switch to per-chunk count/scan/scatter,
-    # with a ragged last tile
+    # with a ragged last tile.  Each scatter pass leaves every row's digit
+    # of the next pass that runs for that pass's chunk counts: "gaps" skips
+    # passes between the ones that run, "lowconst" skips the first
     n = (1 << 21) + 4097
     col = _sort_case(kind, n, seed=3)
     keys, ptrs = S.extract(cuda(col), 0, n)
