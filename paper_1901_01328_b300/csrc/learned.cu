@@ -118,9 +118,9 @@ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, float x) 
 
 constexpr int kGThreads = 1024;
 constexpr int kMaxSlice = 256;
-constexpr int kTrainCtas = 128;  // batch rows per CTA = batch / 128
-constexpr int kRedParams = (kNP + kTrainCtas - 1) / kTrainCtas;  // parameters each training CTA updates
-static_assert(kRedParams < kGThreads / 32, "one warp per updated parameter, and one for the loss");
+constexpr int kTrainCtas = 32;  // batch rows per CTA = batch / 32, in slices of at most kMaxSlice
+constexpr int kBatchUnit = 128, kMaxBatch = 32768;  // the batch sizes the training takes
+static_assert(kBatchUnit % kTrainCtas == 0, "whole rows per CTA");
 
 struct GradSmem {
     float P[kNP];
@@ -132,7 +132,8 @@ struct GradSmem {
     float D2[kMaxSlice][kH + 1];  // dL/da2
     float part[4][kNP];           // gradient sums over the rows s = k (mod 4), laid out like G
     float red[kGThreads / 32];
-    float gred[kRedParams][kTrainCtas];  // training: the partial gradients of this CTA's parameters
+    float GA[kNP];           // training: the gradient over this CTA's rows (its slices summed)
+    float AM[kNP], AV[kNP];  // training: Adam's moments (the same in every CTA)
 };
 
 // Gradient of sum_s (y_s - t_s)^2 / norm over the S rows in sm.X, sm.T into
@@ -352,11 +353,9 @@ struct TrainScratch {
     uint64_t* block_sums;
     float* X;
     float* T;
-    float* partial;      // G * kNP
-    float* partial_sq;   // G
-    float* adam_m;
-    float* adam_v;
-    float* params;       // current parameters (global copy)
+    float* partial;      // 2 x G x kNP (by step parity)
+    float* partial_sq;   // 2 x G
+    float* params;       // initial, then trained parameters
     uint32_t* bar;       // grid barrier: count, generation
     uint32_t* m_train;
     void* sort_scratch;
@@ -376,10 +375,8 @@ TrainScratch train_carve(void* base, uint64_t m) {
     t.block_sums = c.take<uint64_t>((m + kCompactTile - 1) / kCompactTile + 1);
     t.X = c.take<float>(m);
     t.T = c.take<float>(m);
-    t.partial = c.take<float>(kTrainCtas * (size_t)kNP);
-    t.partial_sq = c.take<float>(kTrainCtas);
-    t.adam_m = c.take<float>(kNP);
-    t.adam_v = c.take<float>(kNP);
+    t.partial = c.take<float>(2 * kTrainCtas * (size_t)kNP);
+    t.partial_sq = c.take<float>(2 * kTrainCtas);
     t.params = c.take<float>(kNP);
     t.bar = c.take<uint32_t>(2);
     t.m_train = c.take<uint32_t>(1);
@@ -616,11 +613,9 @@ struct TrainArgs {
     const float* X;
     const float* T;
     const uint32_t* m_train;
-    float* params;   // global parameter copy, starts at the initial weights
-    float* adam_m;
-    float* adam_v;
-    float* partial;
-    float* partial_sq;
+    float* params;      // initial weights in, trained weights out
+    float* partial;     // 2 x G x kNP: each CTA's gradient, by step parity
+    float* partial_sq;  // 2 x G
     uint32_t* bar;
     float* losses;   // nullable, one per step
     int steps;
@@ -630,73 +625,73 @@ struct TrainArgs {
     uint32_t* status;
 };
 
-// (One thread-block cluster of 16 CTAs, 256 rows each, summing the
-// gradients through distributed shared memory between two cluster barriers
-// a step, measured slower: 0.66 against 0.60 ms for the bench's 40 steps of
-// 4096 rows; the gradient of 256 rows on one SM costs more than the two grid
-// barriers it saves.)
+// Adam on the batch gradient with one grid barrier a step: each CTA takes
+// batch / G rows (slices of at most kMaxSlice), writes its gradient to the
+// buffer of the step's parity, and after the barrier every CTA sums the G
+// gradients in CTA order and applies the same Adam update to its own copy of
+// the parameters in shared memory, so the copies stay identical and no second
+// barrier is needed.  A CTA writes the other parity's buffer next step only
+// after every CTA has reached this step's barrier, that is, after all of them
+// have read the previous step's gradients.  (128 CTAs of 32 rows, each
+// updating ten parameters between two grid barriers a step, took 0.60 ms for
+// the bench's 40 steps of 4096 rows; one cluster of 16 CTAs of 256 rows,
+// summing through distributed shared memory, 0.66 ms.)
 __global__ void __launch_bounds__(kGThreads) train_kernel(TrainArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
     const uint32_t mt = *a.m_train;
-    const int G = gridDim.x, c = blockIdx.x;
+    const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
     const int S = a.batch / G;
-    const int chunk = (kNP + G - 1) / G;
-    const int p0 = min(kNP, c * chunk), p1 = min(kNP, p0 + chunk);
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     float b1t = 1.f, b2t = 1.f;
     if (mt == 0) return;
+    for (int i = tid; i < kNP; i += kGThreads) {
+        sm.P[i] = a.params[i];
+        sm.AM[i] = 0.f;
+        sm.AV[i] = 0.f;
+    }
     for (int step = 0; step < a.steps; ++step) {
-        for (int i = threadIdx.x; i < kNP; i += kGThreads) sm.P[i] = a.params[i];
-        for (int s = threadIdx.x; s < S; s += kGThreads) {
-            const uint64_t row = ((uint64_t)step * a.batch + (uint64_t)c * S + s) % mt;
-            sm.X[s] = a.X[row];
-            sm.T[s] = a.T[row];
+        const int par = step & 1;
+        float sq = 0.f;
+        for (int s0 = 0; s0 < S; s0 += kMaxSlice) {
+            const int ns = min(kMaxSlice, S - s0);
+            __syncthreads();  // the previous slice (or step) is done with X, T, G and P
+            for (int s = tid; s < ns; s += kGThreads) {
+                const uint64_t row = ((uint64_t)step * a.batch + (uint64_t)c * S + s0 + s) % mt;
+                sm.X[s] = a.X[row];
+                sm.T[s] = a.T[row];
+            }
+            __syncthreads();
+            sq += slice_grad(sm, ns, static_cast<float>(a.batch));
+            __syncthreads();
+            for (int i = tid; i < kNP; i += kGThreads) sm.GA[i] = s0 ? sm.GA[i] + sm.G[i] : sm.G[i];
         }
-        __syncthreads();
-        const float sq = slice_grad(sm, S, static_cast<float>(a.batch));
-        __syncthreads();
-        for (int i = threadIdx.x; i < kNP; i += kGThreads) a.partial[c * (size_t)kNP + i] = sm.G[i];
-        if (threadIdx.x == 0) a.partial_sq[c] = sq;
+        float* part = a.partial + (size_t)par * G * kNP;
+        for (int i = tid; i < kNP; i += kGThreads) part[(size_t)c * kNP + i] = sm.GA[i];
+        if (tid == 0) a.partial_sq[par * G + c] = sq;
         __threadfence();
         if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
         b1t *= b1;
         b2t *= b2;
-        // this CTA's parameters: the partial gradients of every CTA, loaded
-        // by all threads at once, then one warp per parameter sums them
-        // (lane q sums CTAs q, q + 32, ..., then a butterfly)
-        const int np = p1 - p0;
-        for (int e = threadIdx.x; e < np * G; e += kGThreads) {
-            const int pi = e / G, q = e - pi * G;
-            sm.gred[pi][q] = a.partial[q * (size_t)kNP + p0 + pi];
-        }
-        __syncthreads();
-        const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-        if (warp < np) {
+        for (int i = tid; i < kNP; i += kGThreads) {
             float g = 0.f;
-            for (int q = lane; q < G; q += 32) g += sm.gred[warp][q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-            if (lane == 0) {
-                const int i = p0 + warp;
-                const float mi = b1 * a.adam_m[i] + (1.f - b1) * g;
-                const float vi = b2 * a.adam_v[i] + (1.f - b2) * g * g;
-                a.adam_m[i] = mi;
-                a.adam_v[i] = vi;
-                const float mhat = mi / (1.f - b1t), vhat = vi / (1.f - b2t);
-                a.params[i] -= a.lr * mhat / (sqrtf(vhat) + eps);
-            }
+            for (int q = 0; q < G; ++q) g += part[(size_t)q * kNP + i];
+            const float mi = b1 * sm.AM[i] + (1.f - b1) * g;
+            const float vi = b2 * sm.AV[i] + (1.f - b2) * g * g;
+            sm.AM[i] = mi;
+            sm.AV[i] = vi;
+            const float mhat = mi / (1.f - b1t), vhat = vi / (1.f - b2t);
+            sm.P[i] -= a.lr * mhat / (sqrtf(vhat) + eps);
         }
-        if (c == 0 && warp == kGThreads / 32 - 1 && a.losses) {
+        if (c == 0 && tid == 0 && a.losses) {
             float l = 0.f;
-            for (int q = lane; q < G; q += 32) l += a.partial_sq[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-            if (lane == 0) a.losses[step] = l / static_cast<float>(a.batch);
+            for (int q = 0; q < G; ++q) l += a.partial_sq[par * G + q];
+            a.losses[step] = l / static_cast<float>(a.batch);
         }
-        __threadfence();
-        if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
     }
+    __syncthreads();
+    if (c == 0)
+        for (int i = tid; i < kNP; i += kGThreads) a.params[i] = sm.P[i];
 }
 
 __global__ void finish_model_kernel(const float* __restrict__ params, const uint32_t* __restrict__ m_train,
@@ -2074,8 +2069,8 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     int rc = scratch_check(d_scratch, scratch_bytes, train_carve(nullptr, m).total, &done);
     if (rc || done) return rc;
     if (m == 0 || !d_samples || !d_model) { set_error("empty sample or null pointer"); return SBH_EINVAL; }
-    if (steps < 0 || batch < kTrainCtas || batch % kTrainCtas || batch / kTrainCtas > kMaxSlice) {
-        set_error("batch must be a multiple of %d in [%d, %d]", kTrainCtas, kTrainCtas, kTrainCtas * kMaxSlice);
+    if (steps < 0 || batch < kBatchUnit || batch % kBatchUnit || batch > kMaxBatch) {
+        set_error("batch must be a multiple of %d in [%d, %d]", kBatchUnit, kBatchUnit, kMaxBatch);
         return SBH_EINVAL;
     }
     cudaStream_t s = as_stream(stream);
@@ -2083,8 +2078,6 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     Model* model = static_cast<Model*>(d_model);
     SBH_CUDA(cudaMemsetAsync(model, 0, sizeof(Model), s));
     SBH_CUDA(cudaMemsetAsync(t.bar, 0, 2 * sizeof(uint32_t), s));
-    SBH_CUDA(cudaMemsetAsync(t.adam_m, 0, kNP * sizeof(float), s));
-    SBH_CUDA(cudaMemsetAsync(t.adam_v, 0, kNP * sizeof(float), s));
     if (d_init_params)
         SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // sort the sample
@@ -2127,7 +2120,7 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     if (d_train_t) SBH_CUDA(cudaMemcpyAsync(d_train_t, t.T, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // train
     if (steps > 0) {
-        TrainArgs a{t.X, t.T, t.m_train, t.params, t.adam_m, t.adam_v, t.partial, t.partial_sq, t.bar, d_losses,
+        TrainArgs a{t.X, t.T, t.m_train, t.params, t.partial, t.partial_sq, t.bar, d_losses,
                     steps, batch, lr, spin_limit(), status_word()};
         const size_t smem = sizeof(GradSmem);
         SBH_CUDA(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
