@@ -143,7 +143,9 @@ struct GradSmem {
 // (k0 + k1) + (k2 + k3); a sum over units runs in unit order.  The three
 // 32-wide products (second layer forward, its weight gradient and the
 // gradient back to the first layer) take 4 x 4 register tiles, so each
-// shared-memory load feeds four multiply-adds.
+// shared-memory load feeds four multiply-adds.  (2 x 2 tiles, which keep all
+// 1024 threads busy at 128 rows, measured slower: the bench's training 0.65
+// against 0.57 ms.)
 __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     const int tid = threadIdx.x;
     const int stiles = (S + 3) / 4;  // groups of four rows
