@@ -210,7 +210,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 SAMPLE_STRIDE = 400        # 0.25% sample for the learned partitioner (1%: 0.3 ms more a step, more overflow rows)
-TRAIN = dict(steps=40, batch=4096, lr=3e-4, init="quantile knots")
+TRAIN = dict(steps=30, batch=4096, lr=3e-4, init="quantile knots")
 
 
 def run_gpu(args):
