@@ -49,7 +49,7 @@ CPU_SAMPLE = 4_000_000
 # second and third passes of a plain sort).
 # Traffic grows in proportion to the rows, so a launch on n rows moves about
 # n times these.
-DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 23.47, "sort_scatter": 23.65}
+DRAM_BYTES_PER_ROW = {"learned_ids_scatter": 23.29, "sort_scatter": 23.65}
 
 
 def _dist():
