@@ -747,7 +747,10 @@ struct BucketValue {
 // The same ids from a 4-byte entry per cell (half the table, so more of it
 // stays in L1), usable when every id is below 2^16: first id (or first heavy
 // key index) in the low 16 bits, spread buckets (at most 2^16 - 2 then) or
-// kHeavyCell16 / kHeavyExact16 in the high.
+// kHeavyCell16 / kHeavyExact16 in the high.  (A 2-byte first-id table read
+// after a bit of a heavy-cell bitmap, a quarter of the 8-byte table's size,
+// measured slower: the id upsweep for 256M mixed keys 0.90 against 0.65 ms,
+// the bitmap load lengthening each lookup's chain of dependent loads.)
 constexpr uint32_t kHeavyCell16 = 0xFFFFu;
 constexpr uint32_t kHeavyExact16 = 0xFFFEu;
 
