@@ -711,21 +711,34 @@ __global__ void finish_model_kernel(const float* __restrict__ params, const uint
 // One 8-byte entry per cell, so an id mostly costs a single table load:
 // x = the cell's first bucket id, y = its number of spread buckets; a cell
 // holding heavy keys has y = kHeavyCell and x = the index of its first heavy
-// key, under which hcells keeps (first bucket id, spread buckets, first heavy
-// key, heavy keys in the cell).  An exact cell (one key value) that is heavy
+// key, under which hcells keeps the cell's HeavyCell entry.  An exact cell
+// (one key value) that is heavy
 // has y = kHeavyExact: its key's bucket is x + 1.
 constexpr uint32_t kHeavyCell = 0xFFFFFFFFu;
 constexpr uint32_t kHeavyExact = 0xFFFFFFFEu;
 
+// A cell holding heavy keys: first bucket id, spread buckets, heavy keys in
+// the cell, and the first two of them (one 32-byte sector: most such cells
+// hold one or two, and then the id needs no load of the heavy-key list; the
+// id upsweep for 256M hashed keys, whose heavy keys share cells with most
+// rows, 1.28 to 1.15 ms, for the mixed keys 0.645 to 0.630 ms).
+struct HeavyCell {
+    uint32_t t, y, hv, pad;
+    uint64_t k0, k1;
+};
+
 // The id of key k (offset f) in a cell holding heavy keys.
-__device__ __forceinline__ uint32_t heavy_cell_id(const uint4* __restrict__ hcells,
+__device__ __forceinline__ uint32_t heavy_cell_id(const HeavyCell* __restrict__ hcells,
                                                   const uint64_t* __restrict__ hkeys, uint32_t idx, uint32_t f,
                                                   uint64_t k) {
-    const uint4 h = hcells[idx];
+    const uint4 h = __ldg(reinterpret_cast<const uint4*>(hcells + idx));
+    const ulonglong2 hk2 = __ldg(reinterpret_cast<const ulonglong2*>(hcells + idx) + 1);
     uint32_t id = h.x + static_cast<uint32_t>((static_cast<uint64_t>(f) * h.y) >> 32);
+    id += hk2.x < k ? 2u : (hk2.x == k ? 1u : 0u);
+    if (h.z > 1) id += hk2.y < k ? 2u : (hk2.y == k ? 1u : 0u);
 #pragma unroll 4
-    for (uint32_t j = 0; j < h.w; ++j) {  // no early exit: the loads are independent
-        const uint64_t hk = hkeys[h.z + j];
+    for (uint32_t j = 2; j < h.z; ++j) {  // no early exit: the loads are independent
+        const uint64_t hk = hkeys[idx + j];
         id += hk < k ? 2u : (hk == k ? 1u : 0u);
     }
     return id;
@@ -733,7 +746,7 @@ __device__ __forceinline__ uint32_t heavy_cell_id(const uint4* __restrict__ hcel
 
 struct BucketValue {
     const uint2* cells;      // kNCell + 1 entries
-    const uint4* hcells;     // by first heavy key index
+    const HeavyCell* hcells;  // by first heavy key index
     const uint64_t* hkeys;   // the model's heavy keys
     __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
         uint32_t f;
@@ -756,7 +769,7 @@ constexpr uint32_t kHeavyExact16 = 0xFFFEu;
 
 struct BucketValue16 {
     const uint32_t* cells;   // kNCell + 1 entries
-    const uint4* hcells;
+    const HeavyCell* hcells;
     const uint64_t* hkeys;
     __device__ __forceinline__ uint64_t operator()(uint64_t k) const {
         uint32_t f;
@@ -859,7 +872,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
                                                                  const float* __restrict__ F,
                                                                  const uint32_t* __restrict__ cell_hc,
                                                                  const uint32_t* __restrict__ cell_hidx,
-                                                                 uint4* __restrict__ hcells,
+                                                                 HeavyCell* __restrict__ hcells,
                                                                  const float* __restrict__ bmax,
                                                                  const uint32_t* __restrict__ bheavy,
                                                                  const uint32_t* __restrict__ nb_p,
@@ -930,7 +943,7 @@ __global__ void __launch_bounds__(kTblThreads) cell_table_kernel(const Model* __
         atomicOr(&heavy_bucket_bits[(t + 1) >> 5], 1u << ((t + 1) & 31));
     } else if (hv) {
         const uint32_t idx = cell_hidx[c];
-        hcells[idx] = make_uint4(t, y, idx, hv);
+        hcells[idx] = HeavyCell{t, y, hv, 0u, model->heavy_keys[idx], hv > 1 ? model->heavy_keys[idx + 1] : 0ull};
         e = make_uint2(idx, kHeavyCell);
         for (uint32_t j = 0; j < hv; ++j) {  // the heavy keys' own buckets
             uint32_t fh;
@@ -1956,7 +1969,7 @@ struct SortLearnedScratch {
     uint32_t* cells16;      // kNCell + 1
     uint32_t* cell_hc;      // kNCell + 1: heavy keys per cell (zeroed)
     uint32_t* cell_hidx;    // kNCell + 1: first heavy key per cell (0xFF bytes)
-    uint4* hcells;          // kMaxHeavy: cells holding heavy keys, by first heavy key
+    HeavyCell* hcells;      // kMaxHeavy: cells holding heavy keys, by first heavy key
     float* F;               // kNCell + 1
     uint32_t* heavy_bucket_bits;
     uint32_t* bstart;       // max ids + 1
@@ -1993,7 +2006,7 @@ SortLearnedScratch learned_carve(void* base, uint64_t n) {
     t.cells16 = c.take<uint32_t>(kNCell + 1);
     t.cell_hc = c.take<uint32_t>(kNCell + 1);
     t.cell_hidx = c.take<uint32_t>(kNCell + 1);
-    t.hcells = c.take<uint4>(kMaxHeavy);
+    t.hcells = c.take<HeavyCell>(kMaxHeavy);
     t.F = c.take<float>(kNCell + 1);
     t.list = c.take<uint32_t>(ids);
     t.bagg = c.take<uint2>(ids / 1024 + 1);
