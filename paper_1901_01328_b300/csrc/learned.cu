@@ -145,7 +145,8 @@ struct GradSmem {
 // gradient back to the first layer) take 4 x 4 register tiles, so each
 // shared-memory load feeds four multiply-adds.  (2 x 2 tiles, which keep all
 // 1024 threads busy at 128 rows, measured slower: the bench's training 0.65
-// against 0.57 ms.)
+// against 0.57 ms; so did splitting each 32-term sum between the two lanes
+// of a pair, 0.58 ms with the weights' rows padded against bank conflicts.)
 __device__ float slice_grad(GradSmem& sm, int S, float norm) {
     const int tid = threadIdx.x;
     const int stiles = (S + 3) / 4;  // groups of four rows

@@ -469,6 +469,20 @@ def test_sort_chunked_path_default_threshold(S):
     assert same(sk, ok) and same(sp, op)
 
 
+@pytest.mark.parametrize("kind", ["mixed", "uniform20", "gaps"])
+def test_sort_chunked_in_place(S, kind, chunked_from_2m):
+    # in place through the chunked passes (the passes alternate between the
+    # scratch and the output, and each leaves the next pass's digit bytes);
+    # arbitrary pointers: ties keep input order
+    n = (1 << 21) + 777
+    col = _sort_case(kind, n, seed=11)
+    ptrs = gen.uniform(11, 9, n, 0, 1 << 31, np.uint32)
+    k, p = cuda(col), cuda(ptrs)
+    S.sort(k, p, out=(k, p))
+    order = np.argsort(col, kind="stable")
+    assert same(k, col[order]) and same(p, ptrs[order])
+
+
 def test_sort_unaligned_views(S, chunked_from_2m):
     # views that start 8 bytes into a buffer cannot use bulk copies (both paths)
     for n in (50_001, (1 << 21) + 11):
