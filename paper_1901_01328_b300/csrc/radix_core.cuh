@@ -1007,7 +1007,9 @@ chunk_scatter_kernel(Buffers buf, uint32_t n, int pos, const Plan* __restrict__ 
             // match.any or from digit-bit ballots (a ninth bit when the tile has
             // rows past the end); the group leader adds the group's size to the
             // warp's counter, predicated rather than branched, and the old value
-            // is broadcast.
+            // is broadcast.  (Finding every row's peers first and then issuing
+            // the counter atomics back to back measured slower: 15.31 against
+            // 14.82 ms for the plain sort's eight passes at 256M rows.)
             const uint32_t lt = lanemask_lt();
 #pragma unroll
             for (int j = 0; j < kIt; ++j) {
