@@ -1017,7 +1017,7 @@ static_assert(sizeof(BucketSmem) <= 232448, "bucket sort shared memory");
 
 struct BucketStats {
     unsigned long long sorted_buckets, single_key_buckets, heavy_buckets, overflow_buckets, overflow_rows,
-        max_bucket, radix_buckets, radix_rows, wide_buckets, wide_rows, retried_buckets;
+        radix_buckets, radix_rows, wide_buckets, wide_rows, retried_buckets;
 };
 
 // Persistent CTAs take runs of buckets (a run: one bucket, or consecutive
@@ -1091,14 +1091,6 @@ bucket_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ptrs, con
                 prefetched = true;
             }
         };
-        if (tid == 0) {  // the largest bucket of the run
-            uint32_t mx = cnt;
-            if (nbk > 1) {
-                mx = 0;
-                for (uint32_t x = b; x < bend; ++x) mx = max(mx, bstart[x + 1] - bstart[x]);
-            }
-            if (mx > 0) atomicMax(&st->max_bucket, (unsigned long long)mx);
-        }
         if (cnt <= 1 || heavy || cnt > kCap) {  // (cnt > kCap: a run of one bucket)
             if (tid == 0) {
                 if (cnt > 1 && heavy) {
@@ -1655,19 +1647,33 @@ __global__ void overflow_move_kernel(uint64_t* __restrict__ keys, uint32_t* __re
     }
 }
 
-// The call's statistics, in the order of the header's list.
-__global__ void learned_stats_kernel(const uint32_t* __restrict__ nbid, const uint32_t* __restrict__ plan,
-                                     const BucketStats* __restrict__ st, const uint32_t* __restrict__ id_passes,
-                                     uint64_t* __restrict__ out) {
+// The call's statistics, in the order of the header's list; the largest
+// bucket from the bucket starts (a block reduction here: thread 0 of the
+// bucket sort scanning each run's buckets took a tenth of that kernel).
+__global__ void __launch_bounds__(1024) learned_stats_kernel(const uint32_t* __restrict__ nbid,
+                                                             const uint32_t* __restrict__ plan,
+                                                             const uint32_t* __restrict__ bstart,
+                                                             const BucketStats* __restrict__ st,
+                                                             const uint32_t* __restrict__ id_passes,
+                                                             uint64_t* __restrict__ out) {
+    __shared__ uint32_t wmax[32];
+    const uint32_t nb = *nbid;
+    uint32_t mx = 0;
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) mx = max(mx, bstart[b + 1] - bstart[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane_id() == 0) wmax[threadIdx.x / 32] = mx;
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    out[0] = *nbid;
+    for (uint32_t w = 1; w < blockDim.x / 32; ++w) mx = max(mx, wmax[w]);
+    out[0] = nb;
     out[1] = plan[0];
     out[2] = st->sorted_buckets;
     out[3] = st->single_key_buckets;
     out[4] = st->heavy_buckets;
     out[5] = st->overflow_buckets;
     out[6] = st->overflow_rows;
-    out[7] = st->max_bucket;
+    out[7] = mx;
     out[8] = st->radix_buckets;
     out[9] = st->radix_rows;
     out[10] = st->wide_buckets;
@@ -2284,7 +2290,7 @@ extern "C" int sbh_kpa_sort_learned(const uint64_t* d_keys_in, const uint32_t* d
                                                       rows_total, t.ck, t.cp, 0));
     SBH_LAUNCHED();
     if (d_stats) {
-        SBH_TIMED("learned_stats", s, learned_stats_kernel<<<1, 32, 0, s>>>(nbid, lplan, t.stats, t.small + 12, d_stats));
+        SBH_TIMED("learned_stats", s, learned_stats_kernel<<<1, 1024, 0, s>>>(nbid, lplan, t.bstart, t.stats, t.small + 12, d_stats));
         SBH_LAUNCHED();
     }
     return SBH_OK;

@@ -192,9 +192,13 @@ def test_learned_sort_of_a_key_column_without_extract(S, n, kind, offset):
         col = np.full(n + offset, 777, dtype=np.uint64)
     d = cuda(col)[offset:]
     model, _ = S.learned_train(S.sample(d, 100), n, None, steps=40, batch=4096, lr=3e-4)
-    sk, sp, _ = S.sort_learned(d, None, model)
+    sk, sp, st = S.sort_learned(d, None, model)
     ok, op = oracle.sort(*oracle.extract(col[offset:], 0, n))
     assert same(sk, ok) and same(sp, op)
+    if kind == "mixed" and n > 1_000_000:
+        # the most frequent key (about 8% of the rows) has a bucket of its own,
+        # the largest one
+        assert st["largest_bucket"] == int(np.unique(col[offset:], return_counts=True)[1].max())
 
 
 @pytest.mark.parametrize("hashed", [False, True])
