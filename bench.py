@@ -988,8 +988,9 @@ def pipeline_rows():
     out["sliding_join_509"] = {
         "rows_per_side": int(lcol.size), "windows": 509, "ms": ms_j, "windows_per_s": 509 / (ms_j / 1e3),
         "loop_ms": ms_loop,
-        "schedule": "batched: one composite-key sort of all panes per side, one segmented merge launch per level, "
-                    "one segmented join for all windows (loop_ms: per-pane sorts and per-window merge + join)",
+        "schedule": "batched, in eight groups of windows whose host copies overlap the earlier groups' work: per "
+                    "group and side one composite-key sort of its panes, one segmented merge launch per level, one "
+                    "segmented join for its windows (loop_ms: per-pane sorts and per-window merge + join)",
         "pairs": pairs, "h2d_bytes": 2 * 8 * int(lcol.size), "oracle_ms_per_window": oms,
         "shape": "2 x 128M keys U[0, 2^24) in pinned host memory; 1M-row windows, stride 250K; panes sorted once"}
 
