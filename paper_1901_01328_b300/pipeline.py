@@ -218,8 +218,9 @@ def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride, groups=8):
                     ev.record(copy_st)
                 copied[g][si] = ev
         done = end
-    for c in cols:
-        c.record_stream(copy_st)
+    for c, col in zip(cols, (lkey_col, rkey_col)):
+        if not col.is_cuda:
+            c.record_stream(copy_st)  # written on the copy stream
     key_ors, parts = [], []
     for g in range(ngroups):
         p0, p1 = wb[g], wb[g + 1] + per - 1  # the group's panes
