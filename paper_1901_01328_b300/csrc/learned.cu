@@ -349,8 +349,7 @@ __global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, const flo
 // ------------------------------------------------------------------ training data
 struct TrainScratch {
     uint64_t* s_keys;    // sorted sample (m)
-    uint32_t* s_ptrs;
-    uint32_t* i_ptrs;    // 0 .. m-1, the sort's input pointers
+    uint32_t* s_ptrs;    // the sort's pointers (not used)
     uint64_t* nh;        // non-heavy sorted samples (m)
     uint32_t* flags;     // m + 1 (compaction)
     uint64_t* block_sums;
@@ -372,7 +371,6 @@ TrainScratch train_carve(void* base, uint64_t m) {
     TrainScratch t;
     t.s_keys = c.take<uint64_t>(m);
     t.s_ptrs = c.take<uint32_t>(m);
-    t.i_ptrs = c.take<uint32_t>(m);
     t.nh = c.take<uint64_t>(m);
     t.flags = c.take<uint32_t>(m + 1);
     t.block_sums = c.take<uint64_t>((m + kCompactTile - 1) / kCompactTile + 1);
@@ -386,11 +384,6 @@ TrainScratch train_carve(void* base, uint64_t m) {
     t.sort_scratch = c.take<char>(sort_carve(nullptr, m).total);
     t.total = c.bytes();
     return t;
-}
-
-__global__ void iota_kernel(uint32_t* p, uint64_t m) {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i < m) p[i] = static_cast<uint32_t>(i);
 }
 
 // Heavy keys from the sorted sample: a run of count samples is heavy when
@@ -2105,11 +2098,10 @@ int sbh_learned_train(const uint64_t* d_samples, uint64_t m, uint64_t n_rows, co
     SBH_CUDA(cudaMemsetAsync(t.bar, 0, 2 * sizeof(uint32_t), s));
     if (d_init_params)
         SBH_CUDA(cudaMemcpyAsync(t.params, d_init_params, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    // sort the sample
+    // sort the sample (its pointers are not needed: row numbers, made by the
+    // sort's first pass)
     const unsigned gm = (unsigned)((m + 255) / 256);
-    SBH_TIMED("learned_iota", s, iota_kernel<<<gm, 256, 0, s>>>(t.i_ptrs, m));
-    SBH_LAUNCHED();
-    rc = sort_by_value(d_samples, t.i_ptrs, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions,
+    rc = sort_by_value(d_samples, nullptr, t.s_keys, t.s_ptrs, m, t.sort_scratch, s, RadixValue{}, kPositions,
                        "learned_sample");
     if (rc) return rc;
     // heavy keys (in key order, the first kMaxHeavy), the non-heavy samples,
