@@ -182,6 +182,22 @@ def sliding_join(lkey_col, rkey_col, n_rows, window=1_000_000, stride=250_000, p
     return _sliding_join_loop(lkey_col, rkey_col, n_rows, window, stride, pair_cap, windows)
 
 
+def window_groups(nwin, per, stride, groups):
+    """The batched sliding join's groups of windows: for group g, (first
+    window, end window, first pane, end pane, first row to copy, end row to
+    copy).  Window w covers panes [w, w + per); a group's panes are its
+    windows' panes; the rows to copy are the group's rows that no earlier
+    group copied, so the copy ranges tile [0, (nwin + per - 1) * stride)."""
+    ngroups = max(1, min(groups, nwin))
+    wb = [nwin * g // ngroups for g in range(ngroups + 1)]
+    out, done = [], 0
+    for g in range(ngroups):
+        p0, p1 = wb[g], wb[g + 1] + per - 1
+        out.append((wb[g], wb[g + 1], p0, p1, done, p1 * stride))
+        done = p1 * stride
+    return out
+
+
 def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride, groups=8):
     dev = torch.device("cuda")
     per = window // stride
@@ -202,29 +218,24 @@ def _sliding_join_batched(lkey_col, rkey_col, n_rows, window, stride, groups=8):
     main = torch.cuda.current_stream(dev)
     copy_st = torch.cuda.Stream(dev)
     copy_st.wait_stream(main)
-    ngroups = max(1, min(groups, nwin))
-    wb = [nwin * g // ngroups for g in range(ngroups + 1)]
-    cols, copied = [], [[None, None] for _ in range(ngroups)]
+    grp = window_groups(nwin, per, stride, groups)
+    cols, copied = [], [[None, None] for _ in grp]
     for col in (lkey_col, rkey_col):
         cols.append(col[:rows] if col.is_cuda else _u64(rows, dev))
-    done = 0
-    for g in range(ngroups):
-        end = (wb[g + 1] + per - 1) * stride
+    for g, (_, _, _, _, c0, c1) in enumerate(grp):
         for si, col in enumerate((lkey_col, rkey_col)):
             if not col.is_cuda:
                 with torch.cuda.stream(copy_st):
-                    cols[si][done:end].copy_(col[done:end], non_blocking=True)
+                    cols[si][c0:c1].copy_(col[c0:c1], non_blocking=True)
                     ev = torch.cuda.Event()
                     ev.record(copy_st)
                 copied[g][si] = ev
-        done = end
     for c, col in zip(cols, (lkey_col, rkey_col)):
         if not col.is_cuda:
             c.record_stream(copy_st)  # written on the copy stream
     key_ors, parts = [], []
-    for g in range(ngroups):
-        p0, p1 = wb[g], wb[g + 1] + per - 1  # the group's panes
-        nwg, npg = wb[g + 1] - wb[g], p1 - p0
+    for g, (w0, w1, p0, p1, _, _) in enumerate(grp):
+        nwg, npg = w1 - w0, p1 - p0
         r0, ng = p0 * stride, (p1 - p0) * stride
         offs = (torch.arange(p0, p1 + 1, dtype=torch.int64, device=dev) * stride).view(torch.uint64)
         sides = []
